@@ -1,0 +1,369 @@
+"""Plain FP64 CPU oracle of the el-ph RTA linewidth path.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module.  It shares no code
+with the CUDA library: it reads the same seeded inputs (``workloads``) and
+nothing else.
+
+Each function follows one step of the paper (arXiv 2111.14999), in the
+paper's order and notation, with numpy FP64 arithmetic.  Library primitives
+used as steps: ``numpy.linalg.eigh`` (Hermitian eigenproblem), ``@`` (matrix
+products), ``numpy.exp``/``expm1``.  No blocking or fusion beyond what the
+equations state; the one re-association used by default (R_e sum first, then
+R_p, Sec. 5.5 Eq. 71) is checked against the direct double sum of Eq. 13.
+
+Readings of points the paper leaves open (units, dagger placement, prefactor,
+delta cutoff, zero modes, window, degenerate averaging) are listed at the top
+of each function that applies them.
+
+Units: eV, Angstrom, amu.  k, q in crystal coordinates; k.R = 2 pi sum_i k_i n_i.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# Physical constants (CODATA 2018 derived), carried here as literals.
+KB_EV = 8.617333262e-5                 # Boltzmann constant, eV/K
+HBAR_OMEGA_EV = 0.06465415130134121    # hbar*sqrt(eV/(A^2 amu)) in eV
+HBAR2_AMU_EV_A2 = 0.004180159280496722  # hbar^2/(amu eV A^2), dimensionless
+
+__all__ = [
+    "KB_EV", "HBAR_OMEGA_EV", "HBAR2_AMU_EV_A2",
+    "grid_points", "grid_index", "phases",
+    "wannier_hamiltonian", "electron_bands",
+    "dynamical_matrix", "phonon_modes", "mode_factors",
+    "bose_einstein", "fermi_dirac", "gaussian_delta",
+    "coupling_wannier_direct", "coupling_stage1", "coupling_stage2",
+    "rotate_final", "bloch_coupling", "couplings_for_pairs",
+    "active_states", "fine_grid", "electron_table", "linewidths_rta",
+]
+
+
+# ---------------------------------------------------------------- grids (Sec. 5.1)
+
+def grid_points(n) -> np.ndarray:
+    """Gamma-centred Monkhorst-Pack points k = (i1/N1, i2/N2, i3/N3).
+
+    Sec. 5.1 (Points class): points are sorted by incrementing z, then y, then
+    x, i.e. index (i1*N2 + i2)*N3 + i3.
+    """
+    n1, n2, n3 = (int(x) for x in n)
+    out = np.empty((n1 * n2 * n3, 3))
+    idx = 0
+    for i1 in range(n1):
+        for i2 in range(n2):
+            for i3 in range(n3):
+                out[idx] = (i1 / n1, i2 / n2, i3 / n3)
+                idx += 1
+    return out
+
+
+def grid_index(frac: np.ndarray, n) -> np.ndarray:
+    """Index of crystal-coordinate points on the grid n (points wrapped into [0,1))."""
+    n = np.asarray(n, dtype=np.int64)
+    i = np.rint(np.asarray(frac) * n).astype(np.int64) % n
+    return (i[..., 0] * n[1] + i[..., 1]) * n[2] + i[..., 2]
+
+
+def phases(k: np.ndarray, R: np.ndarray) -> np.ndarray:
+    """e^{i k.R} with k.R = 2 pi sum_i k_i n_i (k crystal, R integer lattice coords)."""
+    return np.exp(2j * np.pi * (np.asarray(k, dtype=np.float64) @ np.asarray(R, dtype=np.float64).T))
+
+
+# ------------------------------------------------------- electrons (Sec. 3.2, Eqs. 10-11)
+
+def wannier_hamiltonian(k: np.ndarray, mat) -> np.ndarray:
+    """H^W_k[n][m] = sum_R w_R e^{i k.R} <0n|H|Rm>   (Sec. 3.2, Eq. 10).
+
+    Optional per-R weights w_R (Wigner-Seitz degeneracy) multiply each term.
+    """
+    P = phases(np.atleast_2d(k), mat.R_H) * mat.w_H[None, :]     # (nk, nR)
+    return (P @ mat.H.reshape(len(mat.R_H), -1)).reshape(P.shape[0], mat.nw, mat.nw)
+
+
+def electron_bands(k: np.ndarray, mat):
+    """Diagonalise H^W_k: U_k^dagger H^W_k U_k = diag(eps_k)   (Sec. 3.2, Eq. 11).
+
+    Returns eps (nk, nw) ascending and U (nk, nw, nw) with columns = eigenvectors
+    (U[m, b]: Wannier index m, band b).
+    """
+    Hk = wannier_hamiltonian(k, mat)
+    eps, U = np.linalg.eigh(Hk)
+    return eps, U
+
+
+# -------------------------------------------------------- phonons (Sec. 3.1, Eqs. 3-4)
+
+def dynamical_matrix(q: np.ndarray, mat) -> np.ndarray:
+    """D[s a][s' a'](q) = sum_R w_R Phi(s a 0 | s' a' R) e^{i q.R} / sqrt(M_s M_s')   (Eq. 3).
+
+    Reading: Eq. 3 omits the masses, yet Eq. 4 makes its eigenvalues (hbar omega)^2,
+    so D is the mass-scaled matrix; the phase carries no atomic positions,
+    as written in Eq. 3.
+    """
+    P = phases(np.atleast_2d(q), mat.R_fc) * mat.w_fc[None, :]
+    nm = 3 * mat.na
+    D = (P @ mat.Phi.reshape(len(mat.R_fc), -1).astype(np.complex128)).reshape(P.shape[0], nm, nm)
+    m = np.repeat(np.asarray(mat.mass_amu, dtype=np.float64), 3)
+    return D / np.sqrt(np.outer(m, m))[None, :, :]
+
+
+def phonon_modes(q: np.ndarray, mat):
+    """Diagonalise D(q): D z = (hbar omega)^2 z   (Sec. 3.1, Eq. 4).
+
+    With D in eV/(A^2 amu), hbar omega [eV] = HBAR_OMEGA_EV * sqrt(lambda).
+    Negative rounding noise at acoustic zeros is clipped to 0.
+    Returns omega (nq, 3na) ascending, z (nq, 3na, 3na) columns = modes.
+    """
+    lam, z = np.linalg.eigh(dynamical_matrix(q, mat))
+    omega = HBAR_OMEGA_EV * np.sqrt(np.clip(lam, 0.0, None))
+    return omega, z
+
+
+def mode_factors(omega: np.ndarray, z: np.ndarray, mass_amu: np.ndarray,
+                 omega_cut: float) -> np.ndarray:
+    """Z_q[s a, nu] = z_q[s a, nu] * sqrt(hbar^2 / (2 M_s hbar omega_q nu))   (Eq. 7).
+
+    Reading: the single mass m of Eq. 7 is the mass of the displaced atom s, so
+    the factor sits inside the contraction over (s, a).  Modes with
+    hbar omega < omega_cut are dead: their factor is 0.  Units: Angstrom.
+    """
+    m = np.repeat(np.asarray(mass_amu, dtype=np.float64), 3)      # (3na,)
+    alive = omega >= omega_cut
+    safe = np.where(alive, omega, 1.0)
+    fac = np.sqrt(HBAR2_AMU_EV_A2 / (2.0 * m[None, :, None] * safe[:, None, :]))
+    return np.where(alive[:, None, :], z * fac, 0.0)
+
+
+# -------------------------------------------------- statistics and smearing (Secs. 4.1, 4.2, 4.7)
+
+def bose_einstein(omega: np.ndarray, T: float) -> np.ndarray:
+    """n = 1/(e^{hbar omega / k_B T} - 1)   (Sec. 4.1).  Zero for omega = 0 entries."""
+    x = np.asarray(omega) / (KB_EV * T)
+    with np.errstate(divide="ignore"):
+        return np.where(x > 0, 1.0 / np.expm1(np.where(x > 0, x, 1.0)), 0.0)
+
+
+def fermi_dirac(eps: np.ndarray, mu: float, T: float) -> np.ndarray:
+    """f = 1/(e^{(eps - mu)/k_B T} + 1)   (Sec. 4.2)."""
+    x = (np.asarray(eps) - mu) / (KB_EV * T)
+    with np.errstate(over="ignore"):
+        return 1.0 / (np.exp(x) + 1.0)
+
+
+def gaussian_delta(x: np.ndarray, sigma: float, cut_sigmas: float) -> np.ndarray:
+    """delta(x) ~ e^{-x^2/sigma^2} / (sqrt(pi) sigma)   (Sec. 4.7, Eq. 61).
+
+    Reading: the Gaussian is truncated to 0 for |x| >= cut_sigmas * sigma
+    (the paper states no truncation; at 6 sigma the dropped tail is e^{-36}).
+    """
+    x = np.asarray(x)
+    val = np.exp(-(x / sigma) ** 2) / (np.sqrt(np.pi) * sigma)
+    return np.where(np.abs(x) < cut_sigmas * sigma, val, 0.0)
+
+
+# ------------------------------------------------------- couplings (Sec. 3.2 Eq. 13, Sec. 5.5)
+
+def coupling_wannier_direct(k: np.ndarray, q: np.ndarray, mat) -> np.ndarray:
+    """G^W(k,q) = sum_{Re,Rp} w_e w_p e^{i k.Re + i q.Rp} g(Re,Rp)   (Eq. 13, direct double sum).
+
+    Reading: the 1/N_e of Eq. 13 is folded into the input g(Re,Rp).
+    Returns (npairs, nw(m), nw(n), 3na).
+    """
+    k = np.atleast_2d(k)
+    q = np.atleast_2d(q)
+    out = np.zeros((len(k), mat.nw, mat.nw, mat.nmodes), dtype=np.complex128)
+    Pe = phases(k, mat.Re) * mat.we[None, :]
+    Pp = phases(q, mat.Rp) * mat.wp[None, :]
+    for p in range(len(k)):
+        for ie in range(len(mat.Re)):
+            for ip in range(len(mat.Rp)):
+                out[p] += Pe[p, ie] * Pp[p, ip] * mat.g[ie, ip]
+    return out
+
+
+def coupling_stage1(k: np.ndarray, mat, U_k: np.ndarray | None = None) -> np.ndarray:
+    """f~(k, Rp) = sum_Re w_e e^{i k.Re} g(Re, Rp) [U_k]   (Sec. 5.5, Eq. 71: precompute at fixed k).
+
+    Eq. 71 folds the k-side rotation U_k into the precomputed quantity; pass
+    ``U_k`` (nw, nb) to apply it to the second Wannier index (n -> b).
+    Returns (nRp, nw(m), nw or nb, 3na) for one k.
+    """
+    Pe = phases(np.atleast_2d(k), mat.Re)[0] * mat.we
+    f1 = (Pe @ mat.g.reshape(len(mat.Re), -1)).reshape(mat.g.shape[1:])
+    if U_k is not None:
+        f1 = np.einsum("pmns,nb->pmbs", f1, U_k)
+    return f1
+
+
+def coupling_stage2(f1: np.ndarray, q: np.ndarray, mat) -> np.ndarray:
+    """sum_Rp w_p e^{i q.Rp} f~(k, Rp) for one k and many q (Sec. 5.5, Eq. 70, R' sum).
+
+    f1: (nRp, ...) for one k.  Returns (nq, ...).
+    """
+    Pp = phases(np.atleast_2d(q), mat.Rp) * mat.wp[None, :]
+    return (Pp @ f1.reshape(len(mat.Rp), -1)).reshape((Pp.shape[0],) + f1.shape[1:])
+
+
+def rotate_final(G: np.ndarray, U_kq: np.ndarray, Zq: np.ndarray) -> np.ndarray:
+    """g[m' b nu] = sum_{m, s a} [U_{k+q}^dagger]_{m' m} G[m][b][s a] Z_q[s a, nu]   (Eq. 13 with Eq. 7).
+
+    Reading of the daggers: the Wannier-to-Bloch rotation is U^dagger X U as
+    for H^B = U^dagger H^W U in Eq. 11; the first Wannier index (m) is the k+q
+    side because Eq. 7 puts psi_{k+q} in the bra.
+    Shapes: G (..., nw, nb, 3na), U_kq (..., nw, nw), Zq (..., 3na, 3na).
+    """
+    nb, ns = G.shape[-2], G.shape[-1]
+    lead = G.shape[:-3]
+    UH = np.conj(np.swapaxes(U_kq, -1, -2))
+    t = UH @ G.reshape(lead + (G.shape[-3], nb * ns))               # (..., m', nb*3na)
+    t = t.reshape(lead + (G.shape[-3] * nb, ns)) @ Zq                # (..., m'*nb, nu)
+    return t.reshape(lead + (G.shape[-3], nb, Zq.shape[-1]))
+
+
+def bloch_coupling(GW: np.ndarray, U_kq: np.ndarray, U_k: np.ndarray, Zq: np.ndarray) -> np.ndarray:
+    """g_{m' n nu}(k,q) = sum [U_{k+q}^dagger]_{m' m} G^W[m][n'][s a] [U_k]_{n' n} Z_q[s a, nu].
+
+    The full Wannier-to-Bloch rotation of Eq. 13 (all bands n), used with the
+    direct double sum.  Returns (..., nw(m'), nw(n), 3na(nu)).
+    """
+    t = np.einsum("...mns,...nb->...mbs", GW, U_k)
+    return rotate_final(t, U_kq, Zq)
+
+
+def couplings_for_pairs(k: np.ndarray, q: np.ndarray, mat, omega_cut: float = 1e-4,
+                        direct: bool = False):
+    """|g_{m' n nu}(k,q)|^2 for explicit (k,q) pairs, plus eps_k, eps_{k+q}, omega_q.
+
+    H(k), H(k+q) and D(q) are built and diagonalised for every pair.
+    Returns g2 (npairs, nw(m'), nw(n), 3na), eps_k, eps_kq (npairs, nw), omega (npairs, 3na).
+    """
+    k = np.atleast_2d(np.asarray(k, dtype=np.float64))
+    q = np.atleast_2d(np.asarray(q, dtype=np.float64))
+    eps_k, U_k = electron_bands(k, mat)
+    eps_kq, U_kq = electron_bands(k + q, mat)
+    omega, z = phonon_modes(q, mat)
+    Zq = mode_factors(omega, z, mat.mass_amu, omega_cut)
+    if direct:
+        g = bloch_coupling(coupling_wannier_direct(k, q, mat), U_kq, U_k, Zq)
+    else:
+        g = np.empty((len(k), mat.nw, mat.nw, mat.nmodes), dtype=np.complex128)
+        for p in range(len(k)):
+            G = coupling_stage2(coupling_stage1(k[p], mat, U_k[p]), q[p], mat)[0]
+            g[p] = rotate_final(G, U_kq[p], Zq[p])
+    return np.abs(g) ** 2, eps_k, eps_kq, omega
+
+
+# ------------------------------------------------------- windows (Sec. 5.2) and linewidths (Eq. 29)
+
+def active_states(eps_k: np.ndarray, mu: float, window: float):
+    """Energy window of Sec. 5.2: keep (k, b) with |eps_kb - mu| < window (window <= 0: all).
+
+    Reading: the window applies to initial states only; final states at k+q
+    range over all bands.  Returns (k_index, band) arrays ordered by k then band.
+    """
+    nk, nb = eps_k.shape
+    ks, bs = [], []
+    for ik in range(nk):
+        for b in range(nb):
+            if window <= 0 or abs(eps_k[ik, b] - mu) < window:
+                ks.append(ik)
+                bs.append(b)
+    return np.array(ks, dtype=np.int64), np.array(bs, dtype=np.int64)
+
+
+def fine_grid(nk, nq):
+    """The grid holding every k and every k+q: per axis the finer of nk, nq (one must divide the other)."""
+    out = []
+    for a, b in zip(nk, nq):
+        a, b = int(a), int(b)
+        if max(a, b) % min(a, b) != 0:
+            raise ValueError("k and q grids are not commensurate")
+        out.append(max(a, b))
+    return tuple(out)
+
+
+def electron_table(mat, params):
+    """eps and U on the fine grid, plus the k-grid -> fine-grid index map."""
+    nk = tuple(int(x) for x in params.nk)
+    F = fine_grid(nk, params.nq)
+    eps_F, U_F = electron_bands(grid_points(F), mat)
+    k_to_F = grid_index(grid_points(nk), F)
+    return F, eps_F, U_F, k_to_F
+
+
+def linewidths_rta(mat, params, k_indices=None, direct: bool = False, return_raw: bool = False,
+                   table=None):
+    """RTA linewidths Gamma_nk = hbar/tau_nk of the active states   (Sec. 4.2 Eq. 29, Sec. 4.3.2).
+
+    Gamma_nk = (2 pi / N_q) sum_q sum_{m' nu} |g_{m' n nu}(k,q)|^2
+               [ (n_q nu + 1 - f_{m',k+q}) delta(eps_nk - hbar w_q nu - eps_{m',k+q})
+               + (n_q nu + f_{m',k+q})     delta(eps_nk + hbar w_q nu - eps_{m',k+q}) ]
+
+    Readings: the sum over k' with delta(k - k' + q) in Eq. 29 is a sum over q
+    with k' = k + q (looked up on the grid, Sec. 5.1); the prefactor
+    2 pi/(N_k V) becomes 2 pi/N_q with hbar = 1 energy units (Gamma in eV), no
+    cell volume and no spin factor; f is the equilibrium Fermi-Dirac
+    occupation; delta is the truncated Gaussian of Eq. 61; dead modes
+    (hbar omega < omega_cut) contribute nothing; Gamma is finally averaged over
+    active bands degenerate within degen_tol at the same k.
+
+    ``k_indices``: optional k-grid indices restricting the initial k points.
+    ``direct``: use the direct double sum of Eq. 13 instead of Eqs. 70-71.
+    Returns (k_index, band, gamma) ordered by k index then band.
+    """
+    nk = tuple(int(x) for x in params.nk)
+    nq = tuple(int(x) for x in params.nq)
+    qpts = grid_points(nq)
+    kpts = grid_points(nk)
+    Nq = len(qpts)
+    T, mu, sigma = params.T_K, params.mu_eV, params.sigma_eV
+    cut = params.delta_cut_sigmas
+
+    F, eps_F, U_F, k_to_F = table if table is not None else electron_table(mat, params)
+    eps_grid = eps_F[k_to_F]
+    ks, bs = active_states(eps_grid, mu, params.window_eV)
+    if k_indices is not None:
+        keep = np.isin(ks, np.asarray(k_indices))
+        ks, bs = ks[keep], bs[keep]
+
+    omega, z = phonon_modes(qpts, mat)
+    Zq = mode_factors(omega, z, mat.mass_amu, params.omega_cut_eV)
+    nB = bose_einstein(omega, T)
+    alive = omega >= params.omega_cut_eV
+
+    raw = np.zeros(len(ks))
+    for ik in np.unique(ks):
+        sel = np.nonzero(ks == ik)[0]
+        bands = bs[sel]
+        k = kpts[ik]
+        U_k = U_F[k_to_F[ik]]
+        kq = grid_index(k[None, :] + qpts, F)
+        eps_kq, U_kq = eps_F[kq], U_F[kq]
+        f_kq = fermi_dirac(eps_kq, mu, T)
+        if direct:
+            GW = coupling_wannier_direct(np.repeat(k[None, :], Nq, axis=0), qpts, mat)
+            g = bloch_coupling(GW, U_kq, np.repeat(U_k[None], Nq, axis=0)[:, :, bands], Zq)
+        else:
+            G = coupling_stage2(coupling_stage1(k, mat, U_k[:, bands]), qpts, mat)  # (Nq, m, b, s)
+            g = rotate_final(G, U_kq, Zq)                                           # (Nq, m', b, nu)
+        g2 = np.abs(g) ** 2
+        for jb, (j, b) in enumerate(zip(sel, bands)):
+            e = eps_grid[ik, b]
+            x_em = e - omega[:, None, :] - eps_kq[:, :, None]            # (Nq, m', nu)
+            x_ab = e + omega[:, None, :] - eps_kq[:, :, None]
+            w = ((nB[:, None, :] + 1.0 - f_kq[:, :, None]) * gaussian_delta(x_em, sigma, cut)
+                 + (nB[:, None, :] + f_kq[:, :, None]) * gaussian_delta(x_ab, sigma, cut))
+            w = np.where(alive[:, None, :], w, 0.0)
+            raw[j] = 2.0 * np.pi / Nq * np.sum(g2[:, :, jb, :] * w)
+
+    out = raw.copy()
+    for ik in np.unique(ks):
+        sel = np.nonzero(ks == ik)[0]
+        e = eps_grid[ik, bs[sel]]
+        for a, j in enumerate(sel):
+            grp = sel[np.abs(e - e[a]) < params.degen_tol_eV]
+            out[j] = raw[grp].mean()
+    if return_raw:
+        return ks, bs, out, raw
+    return ks, bs, out
