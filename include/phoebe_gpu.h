@@ -1,0 +1,184 @@
+/*
+ * phoebe_gpu.h -- C ABI of the B300 (sm_103a) el-ph coupling interpolation and
+ * RTA linewidth library.
+ *
+ * What it computes (arXiv 2111.14999):
+ *   - electronic bands by Wannier interpolation, H^W_k = sum_R e^{ik.R} <0n|H|Rm>,
+ *     U_k^dagger H^W_k U_k = diag(eps_k)                         (Sec. 3.2, Eqs. 10-11)
+ *   - phonons from the dynamical matrix, D(q) z = (hbar w)^2 z     (Sec. 3.1, Eqs. 3-4)
+ *   - el-ph couplings interpolated from the Wannier representation
+ *     g(k,q) = U_{k+q}^dagger [sum_{Re,Rp} e^{i(k.Re + q.Rp)} g(Re,Rp)] U_k z_q / sqrt(2 M w)
+ *                                                                  (Sec. 3.2, Eqs. 7 and 13;
+ *                                                                   factorised as Sec. 5.5, Eqs. 70-71)
+ *   - RTA linewidths Gamma_nk = hbar/tau_nk, Gaussian-smeared        (Sec. 4.2 Eq. 29, Sec. 4.7 Eq. 61)
+ *
+ * Units: energies eV, lengths Angstrom, masses amu, force constants eV/A^2,
+ * Wannier couplings eV/A, output couplings eV.  k, q are crystal (fractional)
+ * coordinates; R are integer lattice coordinates; k.R = 2 pi sum_i k_i n_i.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns a phoebe_gpu_status; none aborts or exits.  The
+ *     text of the last error of a context is returned by phoebe_gpu_last_error.
+ *   - Host buffers are owned by the caller.  set_* copy them into device memory
+ *     owned by the context before returning; outputs go to caller buffers.
+ *   - A context belongs to one device and one CUDA stream and is not
+ *     thread-safe.  All work of a call is ordered on that stream.
+ *   - Complex arrays are interleaved (re, im) pairs of double.
+ *   - Every wait inside a kernel is bounded; a wait that runs out returns
+ *     PHOEBE_GPU_ERR_TIMEOUT and leaves the context usable.
+ */
+#ifndef PHOEBE_GPU_H
+#define PHOEBE_GPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct phoebe_gpu_ctx phoebe_gpu_ctx;
+
+typedef enum {
+  PHOEBE_GPU_OK = 0,
+  PHOEBE_GPU_ERR_ARG = -1,            /* NULL pointer, non-positive size, bad enum value */
+  PHOEBE_GPU_ERR_ORDER = -2,          /* a required set_* call has not been made */
+  PHOEBE_GPU_ERR_SHAPE = -3,          /* sizes of the set_* inputs disagree with each other */
+  PHOEBE_GPU_ERR_GRID = -4,           /* k and q grids not commensurate, or a bad k_subset index */
+  PHOEBE_GPU_ERR_NOMEM = -5,          /* device allocation failed or exceeds the memory cap */
+  PHOEBE_GPU_ERR_CUDA = -6,           /* a CUDA runtime call failed (text in last_error) */
+  PHOEBE_GPU_ERR_TIMEOUT = -7,        /* a bounded device-side wait ran out */
+  PHOEBE_GPU_ERR_NOTCONVERGED = -8,   /* a Jacobi eigensolve hit its sweep cap */
+  PHOEBE_GPU_ERR_UNSUPPORTED = -9     /* valid request this build does not implement */
+} phoebe_gpu_status;
+
+typedef enum {
+  PHOEBE_PREC_FP64 = 0,        /* every step in FP64 */
+  PHOEBE_PREC_SPLIT_BF16 = 1,  /* R_p (and R_e) phase contractions on tcgen05 tensor cores as
+                                  3-product split BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulate;
+                                  eigensolves, statistics and the Gamma reduction in FP64 */
+  PHOEBE_PREC_SPLIT_TF32 = 2,  /* same with 3-product split TF32 */
+  PHOEBE_PREC_BF16 = 3,        /* single-pass BF16 contractions (reported, not within 1e-5) */
+  PHOEBE_PREC_TF32 = 4         /* single-pass TF32 contractions (reported, not within 1e-5) */
+} phoebe_gpu_precision;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (may be NULL: the context creates its own non-blocking stream).  The
+ * library never destroys a stream it did not create. */
+int phoebe_gpu_create(phoebe_gpu_ctx** out, int device, void* cuda_stream);
+/* Release every device buffer of the context.  NULL is accepted. */
+int phoebe_gpu_destroy(phoebe_gpu_ctx* ctx);
+/* Text of the last error raised on this context ("" if none).  Valid until the next call. */
+const char* phoebe_gpu_last_error(const phoebe_gpu_ctx* ctx);
+
+/* Electronic Hamiltonian in the Wannier basis (Sec. 3.2, Eq. 10).
+ *   nw  number of Wannier functions, 1..32
+ *   R   n_R x 3 int32 lattice coordinates; the set must be closed under -R
+ *   w   n_R weights (Wigner-Seitz 1/degeneracy) or NULL for all 1
+ *   H   n_R x nw x nw complex (re,im doubles), H[R][n][m] = <0 n|H|R m> in eV;
+ *       H(-R) must equal H(R)^dagger so that H^W_k is Hermitian.
+ * Replaces any previous Hamiltonian and invalidates cached band structures. */
+int phoebe_gpu_set_hamiltonian(phoebe_gpu_ctx* ctx, int nw, int n_R, const int32_t* R,
+                               const double* w, const double* H);
+
+/* Harmonic force constants (Sec. 3.1, Eq. 3).
+ *   na        atoms per cell, 1..10 (3*na phonon modes)
+ *   mass_amu  na masses in amu
+ *   R, w      n_R lattice vectors (int32 x3) and weights (NULL = 1)
+ *   Phi       n_R x (3na) x (3na) real, eV/A^2, Phi[R][s*3+a][s'*3+b] = d2E/du(s a 0)du(s' b R).
+ * The dynamical matrix is mass-scaled: D = sum_R w_R Phi(R) e^{iq.R} / sqrt(M_s M_s'). */
+int phoebe_gpu_set_force_constants(phoebe_gpu_ctx* ctx, int na, const double* mass_amu, int n_R,
+                                   const int32_t* R, const double* w, const double* Phi);
+
+/* Electron-phonon coupling in the Wannier representation (Sec. 3.2, Eq. 13).
+ *   Re, we  n_Re electron lattice vectors and weights (NULL = 1)
+ *   Rp, wp  n_Rp phonon lattice vectors and weights (NULL = 1)
+ *   g       n_Re x n_Rp x nw(m) x nw(n) x 3na complex, eV/A.  m is the k+q (final-state)
+ *           Wannier index, n the k (initial-state) index.  Any 1/N_e normalisation of
+ *           Eq. 13 is folded into g.
+ * Requires set_hamiltonian (for nw) and set_force_constants (for na) first. */
+int phoebe_gpu_set_elph_wannier(phoebe_gpu_ctx* ctx, int n_Re, const int32_t* Re, const double* we,
+                                int n_Rp, const int32_t* Rp, const double* wp, const double* g);
+
+/* Couplings at explicit (k, q) pairs (need not lie on a grid).
+ *   k, q     n_pairs x 3 crystal coordinates
+ *   precision  PHOEBE_PREC_FP64 only in this build (others return ERR_UNSUPPORTED)
+ *   g2       n_pairs x nw(m') x nw(n) x 3na |g_{m' n nu}(k,q)|^2 in eV^2 (or NULL)
+ *   eps_k, eps_kq  n_pairs x nw band energies at k and k+q, ascending (or NULL)
+ *   omega_q  n_pairs x 3na phonon energies hbar w in eV, ascending (or NULL)
+ * Eigenvector phases are arbitrary, so only gauge-invariant combinations of g2
+ * (sums over degenerate subspaces) are meaningful.  Modes with hbar w below
+ * 1e-4 eV get g2 = 0. */
+int phoebe_gpu_interpolate_couplings(phoebe_gpu_ctx* ctx, int n_pairs, const double* k, const double* q,
+                                     int precision, double* g2, double* eps_k, double* eps_kq,
+                                     double* omega_q);
+
+typedef struct {
+  int nk[3], nq[3];          /* Gamma-centred grids; per axis one of nk[i], nq[i] divides the other */
+  double T_K;                /* temperature, K (> 0) */
+  double mu_eV;              /* chemical potential */
+  double sigma_eV;           /* Gaussian smearing width (> 0), Eq. 61 */
+  double window_eV;          /* initial states with |eps - mu| < window; <= 0: all states */
+  double delta_cut_sigmas;   /* delta(x) = 0 for |x| >= cut*sigma (default 6) */
+  double omega_cut_eV;       /* modes with hbar w < cut contribute nothing (default 1e-4) */
+  double degen_tol_eV;       /* Gamma averaged over bands within tol at the same k (default 1e-6) */
+  int precision;             /* phoebe_gpu_precision */
+  int n_k_subset;            /* > 0: restrict initial k points to k_subset (host, ascending, unique) */
+  const int32_t* k_subset;   /*       k-grid indices (i1*N2+i2)*N3+i3 */
+  int max_batch_states;      /* states per stage-1/stage-2 batch, 0 = automatic */
+  int reserved[8];           /* must be zero */
+} phoebe_gpu_rta_params;
+
+/* Fill *p with the defaults (cut 6 sigma, omega_cut 1e-4, degen 1e-6, FP64, T=300). */
+void phoebe_gpu_rta_params_default(phoebe_gpu_rta_params* p);
+
+/* RTA linewidths of all active (k, n) states on the k grid (Sec. 4.2 Eq. 29):
+ *   Gamma_nk = (2 pi/N_q) sum_{q m' nu} |g_{m' n nu}(k,q)|^2
+ *              [(n_{q nu} + 1 - f_{m',k+q}) delta(eps_nk - hbar w_{q nu} - eps_{m',k+q})
+ *             + (n_{q nu} + f_{m',k+q})     delta(eps_nk + hbar w_{q nu} - eps_{m',k+q})]
+ * in eV, k+q looked up on the finer of the two grids, then averaged over
+ * degenerate active bands at the same k.
+ * Two-call pattern: with gamma_eV == NULL only *n_states is written.  Otherwise
+ * *n_states must hold the capacity of the outputs on entry (ERR_ARG if too
+ * small) and holds the count on return.  Outputs (host, caller-owned): k_index
+ * (grid index), band (0-based, ascending energy), gamma_eV; ordered by k then
+ * band.  k_index/band may be NULL. */
+int phoebe_gpu_linewidths_rta(phoebe_gpu_ctx* ctx, const phoebe_gpu_rta_params* params, int* n_states,
+                              int32_t* k_index, int32_t* band, double* gamma_eV);
+/* Same with device output buffers (on the context's device), written in stream order;
+ * the call returns after the work is queued and *n_states is known. */
+int phoebe_gpu_linewidths_rta_dev(phoebe_gpu_ctx* ctx, const phoebe_gpu_rta_params* params, int* n_states,
+                                  int32_t* k_index_dev, int32_t* band_dev, double* gamma_dev);
+
+/* Work and timing record of the last linewidths_rta call. */
+typedef struct {
+  int64_t n_states;            /* active states computed */
+  int64_t n_k;                 /* distinct initial k points */
+  int64_t n_q;                 /* q points */
+  int64_t pairs_dense;         /* sum over states of N_q */
+  int64_t pairs_executed;      /* (state, q) pairs whose contraction ran */
+  int64_t couplings_dense;     /* pairs_dense * nw * 3na */
+  int64_t couplings_executed;  /* pairs_executed * nw * 3na */
+  int64_t kernel_launches;     /* kernels this library launched in the call */
+  int64_t stage2_launches;     /* launches of the dominant (R_p contraction) kernel */
+  double stage2_flops;         /* algorithmic real flops of the R_p contraction (8 per cMAC) */
+  double stage2_ms;            /* event-timed device time of the R_p contraction launches */
+  double bands_ms, phonons_ms, window_ms, stage1_ms, rotate_ms, delta_ms, total_ms;
+} phoebe_gpu_stats;
+
+/* Turn per-stage event timing on (1) or off (0, default). */
+int phoebe_gpu_set_profiling(phoebe_gpu_ctx* ctx, int on);
+int phoebe_gpu_get_stats(const phoebe_gpu_ctx* ctx, phoebe_gpu_stats* out);
+
+/* Cap on the context's device memory (bytes, 0 = none); exceeding it returns ERR_NOMEM. */
+int phoebe_gpu_set_memory_cap(phoebe_gpu_ctx* ctx, int64_t bytes);
+
+/* Physical constants compiled into the library: out[0] = k_B (eV/K),
+ * out[1] = hbar*sqrt(eV/(A^2 amu)) (eV), out[2] = hbar^2/(amu eV A^2).  Needs no GPU. */
+void phoebe_gpu_constants(double out[3]);
+/* Library version string.  Needs no GPU. */
+const char* phoebe_gpu_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PHOEBE_GPU_H */

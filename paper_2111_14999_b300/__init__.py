@@ -1,0 +1,10 @@
+"""B300 (sm_103a) el-ph coupling interpolation and RTA linewidths.
+
+Python face of the C ABI in include/phoebe_gpu.h (libphoebe_gpu.so, built
+in-tree by ``python -m paper_2111_14999_b300.build``).  Importing raises if
+the library is missing: there is no CPU fallback.
+"""
+from .binding import (  # noqa: F401
+    EXPORTED, PREC_BF16, PREC_FP64, PREC_SPLIT_BF16, PREC_SPLIT_TF32, PREC_TF32,
+    LIB_PATH, PhoebeGPU, PhoebeGPUError, RTAParams, constants, lib, make_params, version,
+)

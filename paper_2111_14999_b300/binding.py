@@ -1,0 +1,270 @@
+"""ctypes binding of libphoebe_gpu.so (argument marshalling only).
+
+Every step of the computation runs in the CUDA library; this module converts
+numpy arrays / torch tensors to pointers and sizes and raises on a non-zero
+status.  There is no CPU fallback: if the shared library is missing or fails
+to load, importing the package raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libphoebe_gpu.so")
+
+STATUS = {
+    0: "OK", -1: "ERR_ARG", -2: "ERR_ORDER", -3: "ERR_SHAPE", -4: "ERR_GRID", -5: "ERR_NOMEM",
+    -6: "ERR_CUDA", -7: "ERR_TIMEOUT", -8: "ERR_NOTCONVERGED", -9: "ERR_UNSUPPORTED",
+}
+PREC_FP64, PREC_SPLIT_BF16, PREC_SPLIT_TF32, PREC_BF16, PREC_TF32 = 0, 1, 2, 3, 4
+
+# symbols declared in include/phoebe_gpu.h
+EXPORTED = (
+    "phoebe_gpu_create", "phoebe_gpu_destroy", "phoebe_gpu_last_error",
+    "phoebe_gpu_set_hamiltonian", "phoebe_gpu_set_force_constants", "phoebe_gpu_set_elph_wannier",
+    "phoebe_gpu_interpolate_couplings", "phoebe_gpu_rta_params_default",
+    "phoebe_gpu_linewidths_rta", "phoebe_gpu_linewidths_rta_dev",
+    "phoebe_gpu_set_profiling", "phoebe_gpu_get_stats", "phoebe_gpu_set_memory_cap",
+    "phoebe_gpu_constants", "phoebe_gpu_version",
+)
+
+
+class PhoebeGPUError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+class RTAParams(C.Structure):
+    _fields_ = [
+        ("nk", C.c_int * 3), ("nq", C.c_int * 3),
+        ("T_K", C.c_double), ("mu_eV", C.c_double), ("sigma_eV", C.c_double), ("window_eV", C.c_double),
+        ("delta_cut_sigmas", C.c_double), ("omega_cut_eV", C.c_double), ("degen_tol_eV", C.c_double),
+        ("precision", C.c_int),
+        ("n_k_subset", C.c_int), ("k_subset", C.POINTER(C.c_int32)),
+        ("max_batch_states", C.c_int),
+        ("reserved", C.c_int * 8),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("n_states", C.c_int64), ("n_k", C.c_int64), ("n_q", C.c_int64),
+        ("pairs_dense", C.c_int64), ("pairs_executed", C.c_int64),
+        ("couplings_dense", C.c_int64), ("couplings_executed", C.c_int64),
+        ("kernel_launches", C.c_int64), ("stage2_launches", C.c_int64),
+        ("stage2_flops", C.c_double), ("stage2_ms", C.c_double),
+        ("bands_ms", C.c_double), ("phonons_ms", C.c_double), ("window_ms", C.c_double),
+        ("stage1_ms", C.c_double), ("rotate_ms", C.c_double), ("delta_ms", C.c_double),
+        ("total_ms", C.c_double),
+    ]
+
+
+def _load() -> C.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2111_14999_b300.build`")
+    lib = C.CDLL(LIB_PATH)
+    P, I, D, I64 = C.c_void_p, C.c_int, C.c_double, C.c_int64
+    sig = {
+        "phoebe_gpu_create": (I, [C.POINTER(P), I, P]),
+        "phoebe_gpu_destroy": (I, [P]),
+        "phoebe_gpu_last_error": (C.c_char_p, [P]),
+        "phoebe_gpu_set_hamiltonian": (I, [P, I, I, P, P, P]),
+        "phoebe_gpu_set_force_constants": (I, [P, I, P, I, P, P, P]),
+        "phoebe_gpu_set_elph_wannier": (I, [P, I, P, P, I, P, P, P]),
+        "phoebe_gpu_interpolate_couplings": (I, [P, I, P, P, I, P, P, P, P]),
+        "phoebe_gpu_rta_params_default": (None, [C.POINTER(RTAParams)]),
+        "phoebe_gpu_linewidths_rta": (I, [P, C.POINTER(RTAParams), C.POINTER(I), P, P, P]),
+        "phoebe_gpu_linewidths_rta_dev": (I, [P, C.POINTER(RTAParams), C.POINTER(I), P, P, P]),
+        "phoebe_gpu_set_profiling": (I, [P, I]),
+        "phoebe_gpu_get_stats": (I, [P, C.POINTER(Stats)]),
+        "phoebe_gpu_set_memory_cap": (I, [P, I64]),
+        "phoebe_gpu_constants": (None, [C.POINTER(D)]),
+        "phoebe_gpu_version": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def constants() -> tuple:
+    out = (C.c_double * 3)()
+    lib.phoebe_gpu_constants(out)
+    return tuple(out)
+
+
+def version() -> str:
+    return lib.phoebe_gpu_version().decode()
+
+
+def _ptr(a) -> C.c_void_p | None:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return C.c_void_p(a.ctypes.data)
+    if hasattr(a, "data_ptr"):          # torch tensor
+        return C.c_void_p(a.data_ptr())
+    if isinstance(a, int):
+        return C.c_void_p(a)
+    raise TypeError(f"cannot pass {type(a)} as a pointer")
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _c128_as_f64(a) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    return a.view(np.float64)
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def make_params(p=None, **kw) -> RTAParams:
+    """Build the C params struct from a workloads.RTAParams-like object and/or keywords."""
+    s = RTAParams()
+    lib.phoebe_gpu_rta_params_default(C.byref(s))
+    src = dict(p.__dict__) if p is not None else {}
+    src.update(kw)
+    keep = []
+    for key, val in src.items():
+        if val is None:
+            continue
+        if key in ("nk", "nq"):
+            getattr(s, key)[:] = [int(v) for v in val]
+        elif key == "k_subset":
+            arr = _i32(val)
+            keep.append(arr)
+            s.n_k_subset = len(arr)
+            s.k_subset = arr.ctypes.data_as(C.POINTER(C.c_int32))
+        elif key in ("T_K", "mu_eV", "sigma_eV", "window_eV", "delta_cut_sigmas", "omega_cut_eV", "degen_tol_eV"):
+            setattr(s, key, float(val))
+        elif key in ("precision", "max_batch_states"):
+            setattr(s, key, int(val))
+    s._keep = keep  # keep the subset array alive with the struct
+    return s
+
+
+class PhoebeGPU:
+    """One library context on one CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._ctx = C.c_void_p()
+        handle = None
+        if stream is not None:
+            handle = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        st = lib.phoebe_gpu_create(C.byref(self._ctx), int(device), handle)
+        if st != 0:
+            raise PhoebeGPUError(st, f"phoebe_gpu_create(device={device}) failed")
+
+    # -------------------------------------------------------------- plumbing
+    def _check(self, st: int):
+        if st != 0:
+            raise PhoebeGPUError(st, lib.phoebe_gpu_last_error(self._ctx).decode())
+
+    def close(self):
+        if self._ctx:
+            lib.phoebe_gpu_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -------------------------------------------------------------- inputs
+    def set_hamiltonian(self, nw, R, w, H):
+        R, H = _i32(R), _c128_as_f64(H)
+        w = None if w is None else _f64(w)
+        self._check(lib.phoebe_gpu_set_hamiltonian(self._ctx, int(nw), len(R), _ptr(R), _ptr(w), _ptr(H)))
+
+    def set_force_constants(self, na, mass_amu, R, w, Phi):
+        m, R, Phi = _f64(mass_amu), _i32(R), _f64(Phi)
+        w = None if w is None else _f64(w)
+        self._check(lib.phoebe_gpu_set_force_constants(self._ctx, int(na), _ptr(m), len(R), _ptr(R), _ptr(w),
+                                                       _ptr(Phi)))
+
+    def set_elph_wannier(self, Re, we, Rp, wp, g):
+        Re, Rp = _i32(Re), _i32(Rp)
+        we = None if we is None else _f64(we)
+        wp = None if wp is None else _f64(wp)
+        g = _c128_as_f64(g)
+        self._check(lib.phoebe_gpu_set_elph_wannier(self._ctx, len(Re), _ptr(Re), _ptr(we), len(Rp), _ptr(Rp),
+                                                    _ptr(wp), _ptr(g)))
+
+    def set_material(self, mat):
+        """All three set_* calls from an object with the workloads.Material fields."""
+        self.set_hamiltonian(mat.nw, mat.R_H, mat.w_H, mat.H)
+        self.set_force_constants(mat.na, mat.mass_amu, mat.R_fc, mat.w_fc, mat.Phi)
+        self.set_elph_wannier(mat.Re, mat.we, mat.Rp, mat.wp, mat.g)
+        self.nw, self.na = int(mat.nw), int(mat.na)
+
+    # -------------------------------------------------------------- compute
+    def interpolate_couplings(self, k, q, precision: int = PREC_FP64, nw: int | None = None,
+                              na: int | None = None):
+        k, q = _f64(k).reshape(-1, 3), _f64(q).reshape(-1, 3)
+        n = len(k)
+        nw = nw or self.nw
+        nm = 3 * (na or self.na)
+        g2 = np.empty((n, nw, nw, nm))
+        ek = np.empty((n, nw))
+        ekq = np.empty((n, nw))
+        om = np.empty((n, nm))
+        self._check(lib.phoebe_gpu_interpolate_couplings(self._ctx, n, _ptr(k), _ptr(q), int(precision), _ptr(g2),
+                                                         _ptr(ek), _ptr(ekq), _ptr(om)))
+        return g2, ek, ekq, om
+
+    def count_states(self, params) -> int:
+        s = params if isinstance(params, RTAParams) else make_params(params)
+        n = C.c_int(0)
+        self._check(lib.phoebe_gpu_linewidths_rta(self._ctx, C.byref(s), C.byref(n), None, None, None))
+        return n.value
+
+    def linewidths_rta(self, params, **kw):
+        """Host-buffer call: returns (k_index, band, gamma_eV) numpy arrays."""
+        s = params if isinstance(params, RTAParams) else make_params(params, **kw)
+        n = self.count_states(s)
+        ki = np.empty(max(n, 1), dtype=np.int32)
+        bd = np.empty(max(n, 1), dtype=np.int32)
+        gm = np.empty(max(n, 1), dtype=np.float64)
+        nn = C.c_int(max(n, 1))
+        self._check(lib.phoebe_gpu_linewidths_rta(self._ctx, C.byref(s), C.byref(nn), _ptr(ki), _ptr(bd), _ptr(gm)))
+        m = nn.value
+        return ki[:m], bd[:m], gm[:m]
+
+    def linewidths_rta_dev(self, params, k_index_dev, band_dev, gamma_dev, capacity: int) -> int:
+        """Device-buffer call (torch tensors or raw device pointers); returns the state count."""
+        s = params if isinstance(params, RTAParams) else make_params(params)
+        nn = C.c_int(int(capacity))
+        self._check(lib.phoebe_gpu_linewidths_rta_dev(self._ctx, C.byref(s), C.byref(nn), _ptr(k_index_dev),
+                                                      _ptr(band_dev), _ptr(gamma_dev)))
+        return nn.value
+
+    def set_profiling(self, on: bool = True):
+        self._check(lib.phoebe_gpu_set_profiling(self._ctx, 1 if on else 0))
+
+    def set_memory_cap(self, nbytes: int):
+        self._check(lib.phoebe_gpu_set_memory_cap(self._ctx, int(nbytes)))
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(lib.phoebe_gpu_get_stats(self._ctx, C.byref(s)))
+        return {name: getattr(s, name) for name, _ in Stats._fields_}

@@ -1,0 +1,435 @@
+// C ABI of the phoebe_gpu library: context, input upload, argument checks and
+// the orchestration of the linewidth path.  Declarations and the contract of
+// every entry point are in include/phoebe_gpu.h.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <numeric>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "pipeline.h"
+
+using namespace phx;
+
+// ------------------------------------------------------------------ errors
+int phx::fail(phoebe_gpu_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+int phx::cuda_fail(phoebe_gpu_ctx* c, cudaError_t e, const char* what, int line) {
+  return fail(c, PHOEBE_GPU_ERR_CUDA, "CUDA error in %s (line %d): %s", what, line, cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------------ device memory
+void* phx::ensure(phoebe_gpu_ctx* c, const char* name, size_t bytes, int* status) {
+  *status = PHOEBE_GPU_OK;
+  DBuf& b = c->bufs[name];
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return b.p;
+  if (b.p) {
+    cudaFree(b.p);
+    c->mem_used -= (int64_t)b.bytes;
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  if (c->mem_cap > 0 && c->mem_used + (int64_t)bytes > c->mem_cap) {
+    *status = fail(c, PHOEBE_GPU_ERR_NOMEM, "buffer '%s' of %zu bytes exceeds the memory cap (%lld used of %lld)",
+                   name, bytes, (long long)c->mem_used, (long long)c->mem_cap);
+    return nullptr;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *status = fail(c, PHOEBE_GPU_ERR_NOMEM, "cudaMalloc of %zu bytes for '%s' failed: %s", bytes, name,
+                   cudaGetErrorString(e));
+    return nullptr;
+  }
+  b.p = p;
+  b.bytes = bytes;
+  c->mem_used += (int64_t)bytes;
+  return p;
+}
+
+void phx::release(phoebe_gpu_ctx* c, const char* name) {
+  auto it = c->bufs.find(name);
+  if (it == c->bufs.end()) return;
+  if (it->second.p) {
+    cudaFree(it->second.p);
+    c->mem_used -= (int64_t)it->second.bytes;
+  }
+  c->bufs.erase(it);
+}
+
+int phx::upload(phoebe_gpu_ctx* c, const char* name, const void* host, size_t bytes, void** dev) {
+  int st;
+  void* p = ensure(c, name, bytes, &st);
+  if (!p) return st;
+  CK(c, cudaMemcpyAsync(p, host, bytes, cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  *dev = p;
+  return PHOEBE_GPU_OK;
+}
+
+// ------------------------------------------------------------------ timing
+void phx::Timer::begin(phoebe_gpu_ctx* c) {
+  if (!c->profiling) return;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaEventRecord(a, c->stream);
+  on = true;
+}
+void phx::Timer::end(phoebe_gpu_ctx* c, double* acc) {
+  if (!on) return;
+  cudaEventRecord(b, c->stream);
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  *acc += ms;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  on = false;
+}
+
+// ------------------------------------------------------------------ grid helpers
+static int gcd_i(int a, int b) { return b == 0 ? a : gcd_i(b, a % b); }
+static int lcm_i(int a, int b) { return a / gcd_i(a, b) * b; }
+
+GridPhase phx::make_phase(const int n[3]) {
+  GridPhase g;
+  int L = lcm_i(lcm_i(n[0], n[1]), n[2]);
+  for (int i = 0; i < 3; ++i) {
+    g.n[i] = n[i];
+    g.mult[i] = L / n[i];
+  }
+  g.L = L;
+  return g;
+}
+
+int phx::cis_table(phoebe_gpu_ctx* c, const GridPhase& gp, const char* name, cplx** out) {
+  int st;
+  cplx* p = (cplx*)ensure(c, name, sizeof(cplx) * gp.L, &st);
+  if (!p) return st;
+  k_cis_table<<<(gp.L + 255) / 256, 256, 0, c->stream>>>(p, gp.L);
+  c->launches++;
+  CK(c, cudaGetLastError());
+  *out = p;
+  return PHOEBE_GPU_OK;
+}
+
+// ------------------------------------------------------------------ band structures
+// eps[P][nw], U[P][nw][nw] (columns = eigenvectors) on the grid n.
+int phx::electron_grid(phoebe_gpu_ctx* c, const int n[3], double** eps, cplx** U) {
+  GridPhase gp = make_phase(n);
+  int64_t P = (int64_t)n[0] * n[1] * n[2];
+  int nw = c->nw, E = nw * nw, st;
+  cplx* cis;
+  if ((st = cis_table(c, gp, "cis_el", &cis))) return st;
+  cplx* A = (cplx*)ensure(c, "jac_A", sizeof(cplx) * P * E, &st);
+  if (!A) return st;
+  cplx* V = (cplx*)ensure(c, "jac_V", sizeof(cplx) * P * E, &st);
+  if (!V) return st;
+  double* e = (double*)ensure(c, "epsF", sizeof(double) * P * nw, &st);
+  if (!e) return st;
+  cplx* u = (cplx*)ensure(c, "UF", sizeof(cplx) * P * E, &st);
+  if (!u) return st;
+  int* status = (int*)ensure(c, "status", 64, &st);
+  if (!status) return st;
+  CK(c, cudaMemsetAsync(status, 0, 64, c->stream));
+  dim3 g((unsigned)((P + 127) / 128), (unsigned)E);
+  k_fourier_grid_c<<<g, 128, 0, c->stream>>>((const cplx*)c->bufs["H"].p, (const int*)c->bufs["RH"].p,
+                                               (const double*)c->bufs["wH"].p, c->nRH, E, gp, cis, P, A);
+  k_jacobi_herm<<<(unsigned)((P + 127) / 128), 128, 0, c->stream>>>(A, V, nw, P, kJacobiSweeps, e, u, status);
+  c->launches += 2;
+  CK(c, cudaGetLastError());
+  int hs = 0;
+  CK(c, cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (hs) return fail(c, PHOEBE_GPU_ERR_NOTCONVERGED, "Jacobi eigensolve of H(k) did not converge in %d sweeps",
+                      kJacobiSweeps);
+  *eps = e;
+  *U = u;
+  return PHOEBE_GPU_OK;
+}
+
+// omega, nB [Q][nm], Z [Q][nm][nm] on the grid n (or at explicit points qpts_dev if non-NULL).
+int phx::phonon_modes(phoebe_gpu_ctx* c, const int n[3], const double* qpts_dev, int64_t Q, double T,
+                      double omega_cut, double** omega, double** nB, cplx** Z, const char* tag) {
+  GridPhase gp = make_phase(n);
+  int nm = 3 * c->na, E = nm * nm, st;
+  cplx* cis = nullptr;
+  if (!qpts_dev)
+    if ((st = cis_table(c, gp, "cis_ph", &cis))) return st;
+  std::string t(tag);
+  cplx* A = (cplx*)ensure(c, (t + "_jA").c_str(), sizeof(cplx) * Q * E, &st);
+  if (!A) return st;
+  cplx* V = (cplx*)ensure(c, (t + "_jV").c_str(), sizeof(cplx) * Q * E, &st);
+  if (!V) return st;
+  double* lam = (double*)ensure(c, (t + "_lam").c_str(), sizeof(double) * Q * nm, &st);
+  if (!lam) return st;
+  cplx* z = (cplx*)ensure(c, (t + "_z").c_str(), sizeof(cplx) * Q * E, &st);
+  if (!z) return st;
+  double* om = (double*)ensure(c, (t + "_omega").c_str(), sizeof(double) * Q * nm, &st);
+  if (!om) return st;
+  double* nb = (double*)ensure(c, (t + "_nB").c_str(), sizeof(double) * Q * nm, &st);
+  if (!nb) return st;
+  cplx* Zq = (cplx*)ensure(c, (t + "_Z").c_str(), sizeof(cplx) * Q * E, &st);
+  if (!Zq) return st;
+  int* status = (int*)ensure(c, "status", 64, &st);
+  if (!status) return st;
+  CK(c, cudaMemsetAsync(status, 0, 64, c->stream));
+  dim3 g((unsigned)((Q + 127) / 128), (unsigned)E);
+  k_dynmat_grid<<<g, 128, 0, c->stream>>>((const double*)c->bufs["Phi"].p, (const int*)c->bufs["Rf"].p,
+                                            (const double*)c->bufs["wf"].p, c->nRf, nm,
+                                            (const double*)c->bufs["inv_sqrt_m"].p, gp, cis, qpts_dev, Q, A);
+  k_jacobi_herm<<<(unsigned)((Q + 127) / 128), 128, 0, c->stream>>>(A, V, nm, Q, kJacobiSweeps, lam, z, status);
+  k_phonon_factors<<<(unsigned)((Q * nm + 127) / 128), 128, 0, c->stream>>>(
+      lam, z, nm, Q, (const double*)c->bufs["mass_of_row"].p, T, omega_cut, om, nb, Zq);
+  c->launches += 3;
+  CK(c, cudaGetLastError());
+  int hs = 0;
+  CK(c, cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (hs) return fail(c, PHOEBE_GPU_ERR_NOTCONVERGED, "Jacobi eigensolve of D(q) did not converge in %d sweeps",
+                      kJacobiSweeps);
+  *omega = om;
+  *nB = nb;
+  *Z = Zq;
+  return PHOEBE_GPU_OK;
+}
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+const char* phoebe_gpu_version(void) { return "phoebe_gpu 0.1 (sm_103a)"; }
+
+void phoebe_gpu_constants(double out[3]) {
+  if (!out) return;
+  out[0] = kBoltzmannEV;
+  out[1] = kHbarOmegaEV;
+  out[2] = kHbar2AmuEvA2;
+}
+
+void phoebe_gpu_rta_params_default(phoebe_gpu_rta_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  for (int i = 0; i < 3; ++i) p->nk[i] = p->nq[i] = 8;
+  p->T_K = 300.0;
+  p->sigma_eV = 0.05;
+  p->delta_cut_sigmas = 6.0;
+  p->omega_cut_eV = 1e-4;
+  p->degen_tol_eV = 1e-6;
+  p->precision = PHOEBE_PREC_FP64;
+}
+
+int phoebe_gpu_create(phoebe_gpu_ctx** out, int device, void* cuda_stream) {
+  if (!out) return PHOEBE_GPU_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+    cudaGetLastError();
+    return PHOEBE_GPU_ERR_CUDA;
+  }
+  if (device < 0 || device >= ndev) return PHOEBE_GPU_ERR_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return PHOEBE_GPU_ERR_CUDA;
+  phoebe_gpu_ctx* c = new phoebe_gpu_ctx();
+  c->device = device;
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+    c->own_stream = false;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return PHOEBE_GPU_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
+  c->cc = major * 10 + minor;
+  *out = c;
+  return PHOEBE_GPU_OK;
+}
+
+int phoebe_gpu_destroy(phoebe_gpu_ctx* c) {
+  if (!c) return PHOEBE_GPU_OK;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (auto& kv : c->bufs)
+    if (kv.second.p) cudaFree(kv.second.p);
+  c->bufs.clear();
+  destroy_tc_state(c);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return PHOEBE_GPU_OK;
+}
+
+const char* phoebe_gpu_last_error(const phoebe_gpu_ctx* c) { return c ? c->err.c_str() : "no context"; }
+
+int phoebe_gpu_set_profiling(phoebe_gpu_ctx* c, int on) {
+  if (!c) return PHOEBE_GPU_ERR_ARG;
+  c->profiling = on != 0;
+  return PHOEBE_GPU_OK;
+}
+
+int phoebe_gpu_get_stats(const phoebe_gpu_ctx* c, phoebe_gpu_stats* out) {
+  if (!c || !out) return PHOEBE_GPU_ERR_ARG;
+  *out = c->stats;
+  return PHOEBE_GPU_OK;
+}
+
+int phoebe_gpu_set_memory_cap(phoebe_gpu_ctx* c, int64_t bytes) {
+  if (!c || bytes < 0) return PHOEBE_GPU_ERR_ARG;
+  c->mem_cap = bytes;
+  return PHOEBE_GPU_OK;
+}
+
+static bool closed_under_minus(int n, const int32_t* R, std::vector<int>* minus) {
+  std::map<std::tuple<int, int, int>, int> idx;
+  for (int i = 0; i < n; ++i) idx[std::make_tuple(R[3 * i], R[3 * i + 1], R[3 * i + 2])] = i;
+  if (minus) minus->assign(n, -1);
+  for (int i = 0; i < n; ++i) {
+    auto it = idx.find(std::make_tuple(-R[3 * i], -R[3 * i + 1], -R[3 * i + 2]));
+    if (it == idx.end()) return false;
+    if (minus) (*minus)[i] = it->second;
+  }
+  return true;
+}
+
+static std::vector<double> weights_or_ones(int n, const double* w) {
+  std::vector<double> v(n, 1.0);
+  if (w) v.assign(w, w + n);
+  return v;
+}
+
+int phoebe_gpu_set_hamiltonian(phoebe_gpu_ctx* c, int nw, int n_R, const int32_t* R, const double* w,
+                               const double* H) {
+  if (!c) return PHOEBE_GPU_ERR_ARG;
+  cudaSetDevice(c->device);
+  if (nw < 1 || nw > kMaxNw) return fail(c, PHOEBE_GPU_ERR_ARG, "nw=%d outside 1..%d", nw, kMaxNw);
+  if (n_R < 1 || !R || !H) return fail(c, PHOEBE_GPU_ERR_ARG, "set_hamiltonian: n_R < 1 or NULL array");
+  std::vector<int> minus;
+  if (!closed_under_minus(n_R, R, &minus))
+    return fail(c, PHOEBE_GPU_ERR_ARG, "set_hamiltonian: the R set is not closed under -R");
+  std::vector<double> wv = weights_or_ones(n_R, w);
+  double hmax = 0.0, herr = 0.0;
+  for (int r = 0; r < n_R; ++r) {
+    int rm = minus[r];
+    if (fabs(wv[r] - wv[rm]) > 1e-12) return fail(c, PHOEBE_GPU_ERR_ARG, "set_hamiltonian: w(R) != w(-R)");
+    for (int i = 0; i < nw; ++i)
+      for (int j = 0; j < nw; ++j) {
+        const double* a = H + 2 * (((int64_t)r * nw + i) * nw + j);
+        const double* b = H + 2 * (((int64_t)rm * nw + j) * nw + i);
+        hmax = fmax(hmax, fabs(a[0]) + fabs(a[1]));
+        herr = fmax(herr, fabs(a[0] - b[0]) + fabs(a[1] + b[1]));
+      }
+  }
+  if (herr > 1e-10 * fmax(hmax, 1e-300))
+    return fail(c, PHOEBE_GPU_ERR_ARG, "set_hamiltonian: H(-R) != H(R)^dagger (max deviation %g)", herr);
+  void* d;
+  int st;
+  if ((st = upload(c, "RH", R, sizeof(int32_t) * 3 * n_R, &d))) return st;
+  if ((st = upload(c, "wH", wv.data(), sizeof(double) * n_R, &d))) return st;
+  if ((st = upload(c, "H", H, sizeof(double) * 2 * (size_t)n_R * nw * nw, &d))) return st;
+  if (c->have_g && c->nw != nw) c->have_g = false;  // stale couplings of another size
+  c->nw = nw;
+  c->nRH = n_R;
+  c->have_H = true;
+  c->tc_g_valid = false;
+  return PHOEBE_GPU_OK;
+}
+
+int phoebe_gpu_set_force_constants(phoebe_gpu_ctx* c, int na, const double* mass_amu, int n_R,
+                                   const int32_t* R, const double* w, const double* Phi) {
+  if (!c) return PHOEBE_GPU_ERR_ARG;
+  cudaSetDevice(c->device);
+  if (na < 1 || 3 * na > kMaxModes) return fail(c, PHOEBE_GPU_ERR_ARG, "na=%d outside 1..%d", na, kMaxModes / 3);
+  if (!mass_amu || n_R < 1 || !R || !Phi) return fail(c, PHOEBE_GPU_ERR_ARG, "set_force_constants: bad arguments");
+  for (int i = 0; i < na; ++i)
+    if (!(mass_amu[i] > 0.0)) return fail(c, PHOEBE_GPU_ERR_ARG, "set_force_constants: mass[%d] <= 0", i);
+  if (!closed_under_minus(n_R, R, nullptr))
+    return fail(c, PHOEBE_GPU_ERR_ARG, "set_force_constants: the R set is not closed under -R");
+  std::vector<double> wv = weights_or_ones(n_R, w);
+  std::vector<double> inv(3 * na), mrow(3 * na);
+  for (int i = 0; i < 3 * na; ++i) {
+    mrow[i] = mass_amu[i / 3];
+    inv[i] = 1.0 / sqrt(mass_amu[i / 3]);
+  }
+  void* d;
+  int st;
+  int nm = 3 * na;
+  if ((st = upload(c, "Rf", R, sizeof(int32_t) * 3 * n_R, &d))) return st;
+  if ((st = upload(c, "wf", wv.data(), sizeof(double) * n_R, &d))) return st;
+  if ((st = upload(c, "Phi", Phi, sizeof(double) * (size_t)n_R * nm * nm, &d))) return st;
+  if ((st = upload(c, "inv_sqrt_m", inv.data(), sizeof(double) * nm, &d))) return st;
+  if ((st = upload(c, "mass_of_row", mrow.data(), sizeof(double) * nm, &d))) return st;
+  if (c->have_g && c->na != na) c->have_g = false;
+  c->na = na;
+  c->nRf = n_R;
+  c->have_Phi = true;
+  c->tc_g_valid = false;
+  return PHOEBE_GPU_OK;
+}
+
+int phoebe_gpu_set_elph_wannier(phoebe_gpu_ctx* c, int n_Re, const int32_t* Re, const double* we, int n_Rp,
+                                const int32_t* Rp, const double* wp, const double* g) {
+  if (!c) return PHOEBE_GPU_ERR_ARG;
+  cudaSetDevice(c->device);
+  if (!c->have_H || !c->have_Phi)
+    return fail(c, PHOEBE_GPU_ERR_ORDER, "set_elph_wannier needs set_hamiltonian and set_force_constants first");
+  if (n_Re < 1 || n_Rp < 1 || !Re || !Rp || !g) return fail(c, PHOEBE_GPU_ERR_ARG, "set_elph_wannier: bad arguments");
+  std::vector<double> wev = weights_or_ones(n_Re, we), wpv = weights_or_ones(n_Rp, wp);
+  void* d;
+  int st;
+  size_t gbytes = sizeof(double) * 2 * (size_t)n_Re * n_Rp * c->nw * c->nw * 3 * c->na;
+  if ((st = upload(c, "Re", Re, sizeof(int32_t) * 3 * n_Re, &d))) return st;
+  if ((st = upload(c, "we", wev.data(), sizeof(double) * n_Re, &d))) return st;
+  if ((st = upload(c, "Rp", Rp, sizeof(int32_t) * 3 * n_Rp, &d))) return st;
+  if ((st = upload(c, "wp", wpv.data(), sizeof(double) * n_Rp, &d))) return st;
+  if ((st = upload(c, "g", g, gbytes, &d))) return st;
+  c->nRe = n_Re;
+  c->nRp = n_Rp;
+  c->g_nw = c->nw;
+  c->g_na = c->na;
+  c->have_g = true;
+  c->tc_g_valid = false;
+  return PHOEBE_GPU_OK;
+}
+
+int phoebe_gpu_interpolate_couplings(phoebe_gpu_ctx* c, int n_pairs, const double* k, const double* q,
+                                     int precision, double* g2, double* eps_k, double* eps_kq, double* omega_q) {
+  if (!c) return PHOEBE_GPU_ERR_ARG;
+  cudaSetDevice(c->device);
+  return interpolate_pairs(c, n_pairs, k, q, precision, g2, eps_k, eps_kq, omega_q);
+}
+
+int phoebe_gpu_linewidths_rta(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, int* n_states, int32_t* k_index,
+                              int32_t* band, double* gamma_eV) {
+  if (!c) return PHOEBE_GPU_ERR_ARG;
+  cudaSetDevice(c->device);
+  return linewidths(c, p, n_states, k_index, band, gamma_eV, false);
+}
+
+int phoebe_gpu_linewidths_rta_dev(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, int* n_states,
+                                  int32_t* k_index_dev, int32_t* band_dev, double* gamma_dev) {
+  if (!c) return PHOEBE_GPU_ERR_ARG;
+  cudaSetDevice(c->device);
+  return linewidths(c, p, n_states, k_index_dev, band_dev, gamma_dev, true);
+}
+
+}  // extern "C"

@@ -1,0 +1,280 @@
+// Band structures on grids and point lists: Wannier/force-constant Fourier
+// sums (Sec. 3.2 Eq. 10, Sec. 3.1 Eq. 3), batched Hermitian Jacobi
+// eigensolves (Eqs. 4, 11), phonon mode factors (Eq. 7), occupations
+// (Secs. 4.1-4.2) and the energy window compaction (Sec. 5.2).
+//
+// Matrices being diagonalised are kept "structure of arrays": element (i,j)
+// of matrix b lives at [(i*n + j) * B + b], so a warp touching 32 matrices
+// reads 32 consecutive complex numbers.
+#include "kernels.cuh"
+
+namespace phx {
+
+// cis[r] = e^{2 pi i r / L}
+__global__ void k_cis_table(cplx* cis, int L) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= L) return;
+  double s, c;
+  sincospi(2.0 * (double)r / (double)L, &s, &c);
+  cis[r] = {c, s};
+}
+
+// Grid Fourier sum, complex input: out[e][p] = sum_R w_R e^{2 pi i k_p.R} in[R][e]
+// (SoA output).  One thread per (point p, entry e = blockIdx.y).
+__global__ void k_fourier_grid_c(const cplx* __restrict__ in, const int* __restrict__ R,
+                                 const double* __restrict__ w, int nR, int E, GridPhase gp,
+                                 const cplx* __restrict__ cis, int64_t P, cplx* __restrict__ out) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int e = blockIdx.y;
+  if (p >= P) return;
+  int j[3];
+  grid_coords(p, gp.n, j);
+  cplx acc = {0.0, 0.0};
+  for (int r = 0; r < nR; ++r) {
+    int Rv[3] = {__ldg(R + 3 * r), __ldg(R + 3 * r + 1), __ldg(R + 3 * r + 2)};
+    cplx ph = ldc(cis + phase_index(j, Rv, gp.mult, gp.L));
+    cplx h = ldc(in + (int64_t)r * E + e);
+    double wr = __ldg(w + r);
+    cfma(acc, {ph.re * wr, ph.im * wr}, h);
+  }
+  out[(int64_t)e * P + p] = acc;
+}
+
+// Point-list Fourier sum (off-grid k): phases from sincospi(2 frac(k.R)).
+__global__ void k_fourier_points_c(const cplx* __restrict__ in, const int* __restrict__ R,
+                                   const double* __restrict__ w, int nR, int E,
+                                   const double* __restrict__ kpts, int64_t P, cplx* __restrict__ out) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int e = blockIdx.y;
+  if (p >= P) return;
+  double k0 = kpts[3 * p], k1 = kpts[3 * p + 1], k2 = kpts[3 * p + 2];
+  cplx acc = {0.0, 0.0};
+  for (int r = 0; r < nR; ++r) {
+    double x = k0 * __ldg(R + 3 * r) + k1 * __ldg(R + 3 * r + 1) + k2 * __ldg(R + 3 * r + 2);
+    x -= floor(x);
+    double s, c;
+    sincospi(2.0 * x, &s, &c);
+    double wr = __ldg(w + r);
+    cfma(acc, {c * wr, s * wr}, ldc(in + (int64_t)r * E + e));
+  }
+  out[(int64_t)e * P + p] = acc;
+}
+
+// Real force constants -> mass-scaled dynamical matrix entry e = (i, j):
+// D[e][p] = sum_R w_R Phi[R][e] e^{2 pi i q_p.R} / sqrt(M_i M_j).
+__global__ void k_dynmat_grid(const double* __restrict__ Phi, const int* __restrict__ R,
+                              const double* __restrict__ w, int nR, int nm,
+                              const double* __restrict__ inv_sqrt_m, GridPhase gp,
+                              const cplx* __restrict__ cis, const double* __restrict__ qpts,
+                              int64_t P, cplx* __restrict__ out) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int e = blockIdx.y;
+  if (p >= P) return;
+  int E = nm * nm;
+  int j[3];
+  if (!qpts) grid_coords(p, gp.n, j);
+  cplx acc = {0.0, 0.0};
+  for (int r = 0; r < nR; ++r) {
+    int Rv[3] = {__ldg(R + 3 * r), __ldg(R + 3 * r + 1), __ldg(R + 3 * r + 2)};
+    cplx ph;
+    if (qpts) {
+      double x = qpts[3 * p] * Rv[0] + qpts[3 * p + 1] * Rv[1] + qpts[3 * p + 2] * Rv[2];
+      x -= floor(x);
+      sincospi(2.0 * x, &ph.im, &ph.re);
+    } else {
+      ph = ldc(cis + phase_index(j, Rv, gp.mult, gp.L));
+    }
+    double v = __ldg(Phi + (int64_t)r * E + e) * __ldg(w + r);
+    acc.re = fma(v, ph.re, acc.re);
+    acc.im = fma(v, ph.im, acc.im);
+  }
+  double s = inv_sqrt_m[e / nm] * inv_sqrt_m[e % nm];
+  out[(int64_t)e * P + p] = {acc.re * s, acc.im * s};
+}
+
+// Cyclic complex Jacobi on B Hermitian n x n matrices (SoA, in place).
+// Rotation for the pair (p,q) with A_pq = r e^{i phi}: first remove the phase
+// (D = diag(1, e^{-i phi})), then the real symmetric 2x2 Schur rotation
+// (tau = (a_qq - a_pp)/(2r), t = sgn(tau)/(|tau| + sqrt(1+tau^2)), c = 1/sqrt(1+t^2),
+// s = t c), so Q = [[c, s], [-s e^{-i phi}, c e^{-i phi}]] and A <- Q^dagger A Q, V <- V Q.
+// Eigenvalues ascending -> evals[b][n]; eigenvectors as columns -> evecs[b][n][n].
+__global__ void k_jacobi_herm(cplx* __restrict__ A, cplx* __restrict__ V, int n, int64_t B,
+                              int max_sweeps, double* __restrict__ evals, cplx* __restrict__ evecs,
+                              int* __restrict__ status) {
+  int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= B) return;
+#define AE(i, j) A[((int64_t)(i) * n + (j)) * B + b]
+#define VE(i, j) V[((int64_t)(i) * n + (j)) * B + b]
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) VE(i, j) = {i == j ? 1.0 : 0.0, 0.0};
+    // exact Hermitian symmetry on entry
+    cplx d = AE(i, i);
+    AE(i, i) = {d.re, 0.0};
+    for (int j = i + 1; j < n; ++j) {
+      cplx u = AE(i, j), l = AE(j, i);
+      cplx m = {0.5 * (u.re + l.re), 0.5 * (u.im - l.im)};
+      AE(i, j) = m;
+      AE(j, i) = {m.re, -m.im};
+    }
+  }
+  // Rotate only entries above 1e-15 of the Frobenius norm (invariant under the
+  // rotations); below that they are rounding noise.  Converged when a whole
+  // sweep performs no rotation.
+  double norm2 = 0.0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) norm2 += cabs2(AE(i, j));
+  const double thr = 1e-15 * sqrt(norm2);
+  bool converged = norm2 == 0.0;
+  for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
+    bool rotated = false;
+    for (int p = 0; p < n - 1; ++p) {
+      for (int q = p + 1; q < n; ++q) {
+        cplx apq = AE(p, q);
+        double r = sqrt(cabs2(apq));
+        if (r <= thr) continue;
+        rotated = true;
+        double app = AE(p, p).re, aqq = AE(q, q).re;
+        double tau = (aqq - app) / (2.0 * r);
+        double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        double c = 1.0 / sqrt(1.0 + t * t);
+        double s = t * c;
+        cplx phc = {apq.re / r, -apq.im / r};  // e^{-i phi}
+        for (int k = 0; k < n; ++k) {
+          if (k == p || k == q) continue;
+          cplx akp = AE(k, p), akq = AE(k, q);
+          cplx x = cmul(akq, phc);
+          cplx nkp = {c * akp.re - s * x.re, c * akp.im - s * x.im};
+          cplx nkq = {s * akp.re + c * x.re, s * akp.im + c * x.im};
+          AE(k, p) = nkp;
+          AE(p, k) = {nkp.re, -nkp.im};
+          AE(k, q) = nkq;
+          AE(q, k) = {nkq.re, -nkq.im};
+        }
+        AE(p, p) = {app - t * r, 0.0};
+        AE(q, q) = {aqq + t * r, 0.0};
+        AE(p, q) = {0.0, 0.0};
+        AE(q, p) = {0.0, 0.0};
+        for (int k = 0; k < n; ++k) {
+          cplx vkp = VE(k, p), vkq = VE(k, q);
+          cplx x = cmul(vkq, phc);
+          VE(k, p) = {c * vkp.re - s * x.re, c * vkp.im - s * x.im};
+          VE(k, q) = {s * vkp.re + c * x.re, s * vkp.im + c * x.im};
+        }
+      }
+    }
+    if (!rotated) converged = true;
+  }
+  if (!converged && status) atomicOr(status, 1);
+  // selection sort of eigenvalues (ascending) with their columns; output AoS
+  int order[kMaxNw];
+  for (int i = 0; i < n; ++i) order[i] = i;
+  for (int i = 0; i < n; ++i) {
+    int best = i;
+    for (int j = i + 1; j < n; ++j)
+      if (AE(order[j], order[j]).re < AE(order[best], order[best]).re) best = j;
+    int tmp = order[i];
+    order[i] = order[best];
+    order[best] = tmp;
+  }
+  for (int i = 0; i < n; ++i) {
+    int src = order[i];
+    evals[b * n + i] = AE(src, src).re;
+    if (evecs)
+      for (int k = 0; k < n; ++k) evecs[(b * n + k) * n + i] = VE(k, src);
+  }
+#undef AE
+#undef VE
+}
+
+// Phonon energies, Bose factors and mode factors Z = z sqrt(hbar^2/(2 M_s hbar w)) (Eq. 7);
+// dead modes (hbar w < omega_cut) get Z = 0 and n = 0.
+__global__ void k_phonon_factors(const double* __restrict__ lam, const cplx* __restrict__ z, int nm,
+                                 int64_t Q, const double* __restrict__ mass_of_row, double T,
+                                 double omega_cut, double* __restrict__ omega, double* __restrict__ nB,
+                                 cplx* __restrict__ Z) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= Q * nm) return;
+  int64_t q = i / nm;
+  int nu = (int)(i % nm);
+  double l = lam[i];
+  double w = kHbarOmegaEV * sqrt(l > 0.0 ? l : 0.0);
+  omega[i] = w;
+  bool alive = w >= omega_cut;
+  nB[i] = alive ? 1.0 / expm1(w / (kBoltzmannEV * T)) : 0.0;
+  for (int r = 0; r < nm; ++r) {
+    cplx v = z[(q * nm + r) * nm + nu];
+    double f = alive ? sqrt(kHbar2AmuEvA2 / (2.0 * mass_of_row[r] * w)) : 0.0;
+    Z[(q * nm + r) * nm + nu] = {v.re * f, v.im * f};
+  }
+}
+
+// f = 1/(e^{(eps-mu)/kT}+1)  (Sec. 4.2)
+__global__ void k_fermi(const double* __restrict__ eps, int64_t N, double mu, double T,
+                        double* __restrict__ f) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  f[i] = 1.0 / (exp((eps[i] - mu) / (kBoltzmannEV * T)) + 1.0);
+}
+
+// ------------------------------------------------------------------ window (Sec. 5.2)
+// count[c] = number of bands of candidate k point c (k-grid index kidx[c], or c itself)
+// with |eps - mu| < window (all bands if window <= 0).
+__global__ void k_window_count(const double* __restrict__ epsF, const int* __restrict__ kidx, int64_t NC, int nw, GridMap gm,
+                               double mu, double window, int* __restrict__ count) {
+  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= NC) return;
+  int64_t k = kidx ? kidx[c] : c;
+  int64_t f = gm.k_to_fine(k);
+  int cnt = 0;
+  for (int b = 0; b < nw; ++b) {
+    double e = epsF[f * nw + b];
+    if (window <= 0.0 || fabs(e - mu) < window) ++cnt;
+  }
+  count[c] = cnt;
+}
+
+// Single-block exclusive scan of count[0..N) into offset[0..N], offset[N] = total.
+__global__ void k_scan_single_block(const int* __restrict__ count, int64_t N, int64_t* __restrict__ offset) {
+  __shared__ int64_t part[1024];
+  int t = threadIdx.x;
+  int64_t chunk = (N + blockDim.x - 1) / blockDim.x;
+  int64_t lo = t * chunk, hi = lo + chunk < N ? lo + chunk : N;
+  int64_t s = 0;
+  for (int64_t i = lo; i < hi; ++i) s += count[i];
+  part[t] = s;
+  __syncthreads();
+  for (int d = 1; d < (int)blockDim.x; d <<= 1) {
+    int64_t v = (t >= d) ? part[t - d] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int64_t base = part[t] - s;
+  for (int64_t i = lo; i < hi; ++i) {
+    offset[i] = base;
+    base += count[i];
+  }
+  if (t == blockDim.x - 1) offset[N] = part[t];
+}
+
+// Write the active states (k grid index, band) in k-then-band order.
+__global__ void k_window_write(const double* __restrict__ epsF, const int* __restrict__ kidx, int64_t NC,
+                               int nw, GridMap gm, double mu, double window,
+                               const int64_t* __restrict__ offset, int* __restrict__ st_k,
+                               int* __restrict__ st_b) {
+  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= NC) return;
+  int64_t k = kidx ? kidx[c] : c;
+  int64_t f = gm.k_to_fine(k);
+  int64_t o = offset[c];
+  for (int b = 0; b < nw; ++b) {
+    double e = epsF[f * nw + b];
+    if (window <= 0.0 || fabs(e - mu) < window) {
+      st_k[o] = (int)k;
+      st_b[o] = b;
+      ++o;
+    }
+  }
+}
+
+}  // namespace phx

@@ -1,0 +1,86 @@
+// Host-side context and orchestration interfaces of the phoebe_gpu library.
+#pragma once
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct TcState;  // tensor-core path state (tc_gemm.cu)
+
+struct phoebe_gpu_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 0;
+  int cc = 0;
+  std::string err;
+  int64_t mem_cap = 0, mem_used = 0;
+  bool profiling = false;
+  int64_t launches = 0;
+  phoebe_gpu_stats stats{};
+  std::map<std::string, DBuf> bufs;
+  // inputs
+  bool have_H = false, have_Phi = false, have_g = false;
+  int nw = 0, nRH = 0;
+  int na = 0, nRf = 0;
+  int nRe = 0, nRp = 0, g_nw = 0, g_na = 0;
+  // tensor-core operands derived from g (invalidated by set_*)
+  bool tc_g_valid = false;
+  TcState* tc = nullptr;
+};
+
+namespace phx {
+
+constexpr int kJacobiSweeps = 40;
+
+int fail(phoebe_gpu_ctx* c, int code, const char* fmt, ...);
+int cuda_fail(phoebe_gpu_ctx* c, cudaError_t e, const char* what, int line);
+
+#define CK(ctx, call)                                       \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) {                                \
+      cudaGetLastError();                                   \
+      return phx::cuda_fail((ctx), e_, #call, __LINE__);    \
+    }                                                       \
+  } while (0)
+
+#define TRY(expr)                \
+  do {                           \
+    int st_ = (expr);            \
+    if (st_ != PHOEBE_GPU_OK) return st_; \
+  } while (0)
+
+void* ensure(phoebe_gpu_ctx* c, const char* name, size_t bytes, int* status);
+void release(phoebe_gpu_ctx* c, const char* name);
+int upload(phoebe_gpu_ctx* c, const char* name, const void* host, size_t bytes, void** dev);
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  bool on = false;
+  void begin(phoebe_gpu_ctx* c);
+  void end(phoebe_gpu_ctx* c, double* acc);
+};
+
+GridPhase make_phase(const int n[3]);
+int cis_table(phoebe_gpu_ctx* c, const GridPhase& gp, const char* name, cplx** out);
+int electron_grid(phoebe_gpu_ctx* c, const int n[3], double** eps, cplx** U);
+int phonon_modes(phoebe_gpu_ctx* c, const int n[3], const double* qpts_dev, int64_t Q, double T,
+                 double omega_cut, double** omega, double** nB, cplx** Z, const char* tag);
+
+int linewidths(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, int* n_states, int32_t* k_index,
+               int32_t* band, double* gamma, bool device_out);
+int interpolate_pairs(phoebe_gpu_ctx* c, int n_pairs, const double* k, const double* q, int precision,
+                      double* g2, double* eps_k, double* eps_kq, double* omega_q);
+
+// tensor-core path (tc_gemm.cu)
+void destroy_tc_state(phoebe_gpu_ctx* c);
+
+}  // namespace phx
