@@ -53,12 +53,16 @@ typedef enum {
 
 typedef enum {
   PHOEBE_PREC_FP64 = 0,        /* every step in FP64 */
-  PHOEBE_PREC_SPLIT_BF16 = 1,  /* R_p (and R_e) phase contractions on tcgen05 tensor cores as
-                                  3-product split BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulate;
-                                  eigensolves, statistics and the Gamma reduction in FP64 */
-  PHOEBE_PREC_SPLIT_TF32 = 2,  /* same with 3-product split TF32 */
+  PHOEBE_PREC_SPLIT_BF16 = 1,  /* R_e and R_p phase contractions on tcgen05 tensor cores with each
+                                  FP32 operand split into three BF16 parts (hi + mid + lo) and the six
+                                  leading cross products, FP32 accumulate; eigensolves, occupations,
+                                  the delta arguments and the Gamma reduction in FP64 */
+  PHOEBE_PREC_SPLIT_TF32 = 2,  /* same with two TF32 parts (big + small) and three products */
   PHOEBE_PREC_BF16 = 3,        /* single-pass BF16 contractions (reported, not within 1e-5) */
-  PHOEBE_PREC_TF32 = 4         /* single-pass TF32 contractions (reported, not within 1e-5) */
+  PHOEBE_PREC_TF32 = 4,        /* single-pass TF32 contractions (reported, not within 1e-5) */
+  PHOEBE_PREC_SPLIT_FP16 = 5,  /* two FP16 parts (hi + lo) of power-of-two scaled operands, three
+                                  products: 22 significant bits at the cost of three BF16 passes */
+  PHOEBE_PREC_BF16X3 = 6       /* two BF16 parts, three products (reported, ~1e-5) */
 } phoebe_gpu_precision;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t

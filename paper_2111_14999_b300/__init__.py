@@ -5,6 +5,6 @@ in-tree by ``python -m paper_2111_14999_b300.build``).  Importing raises if
 the library is missing: there is no CPU fallback.
 """
 from .binding import (  # noqa: F401
-    EXPORTED, PREC_BF16, PREC_FP64, PREC_SPLIT_BF16, PREC_SPLIT_TF32, PREC_TF32,
+    EXPORTED, PREC_BF16, PREC_BF16X3, PREC_FP64, PREC_SPLIT_BF16, PREC_SPLIT_FP16, PREC_SPLIT_TF32, PREC_TF32,
     LIB_PATH, PhoebeGPU, PhoebeGPUError, RTAParams, constants, lib, make_params, version,
 )

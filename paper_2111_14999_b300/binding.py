@@ -19,7 +19,7 @@ STATUS = {
     0: "OK", -1: "ERR_ARG", -2: "ERR_ORDER", -3: "ERR_SHAPE", -4: "ERR_GRID", -5: "ERR_NOMEM",
     -6: "ERR_CUDA", -7: "ERR_TIMEOUT", -8: "ERR_NOTCONVERGED", -9: "ERR_UNSUPPORTED",
 }
-PREC_FP64, PREC_SPLIT_BF16, PREC_SPLIT_TF32, PREC_BF16, PREC_TF32 = 0, 1, 2, 3, 4
+PREC_FP64, PREC_SPLIT_BF16, PREC_SPLIT_TF32, PREC_BF16, PREC_TF32, PREC_SPLIT_FP16, PREC_BF16X3 = 0, 1, 2, 3, 4, 5, 6
 
 # symbols declared in include/phoebe_gpu.h
 EXPORTED = (

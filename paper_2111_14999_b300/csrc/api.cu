@@ -404,6 +404,10 @@ int phoebe_gpu_set_elph_wannier(phoebe_gpu_ctx* c, int n_Re, const int32_t* Re, 
   if ((st = upload(c, "g", g, gbytes, &d))) return st;
   c->nRe = n_Re;
   c->nRp = n_Rp;
+  c->we_max = 0.0;
+  c->wp_max = 0.0;
+  for (double v : wev) c->we_max = fmax(c->we_max, fabs(v));
+  for (double v : wpv) c->wp_max = fmax(c->wp_max, fabs(v));
   c->g_nw = c->nw;
   c->g_na = c->na;
   c->have_g = true;

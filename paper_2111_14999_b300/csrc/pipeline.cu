@@ -51,7 +51,7 @@ int interpolate_pairs(phoebe_gpu_ctx* c, int n_pairs, const double* k, const dou
                       double* g2, double* eps_k, double* eps_kq, double* omega_q) {
   c->launches = 0;
   if (n_pairs < 1 || !k || !q) return fail(c, PHOEBE_GPU_ERR_ARG, "interpolate_couplings: n_pairs < 1 or NULL k/q");
-  if (precision < PHOEBE_PREC_FP64 || precision > PHOEBE_PREC_TF32)
+  if (precision < PHOEBE_PREC_FP64 || precision > PHOEBE_PREC_BF16X3)
     return fail(c, PHOEBE_GPU_ERR_ARG, "interpolate_couplings: unknown precision %d", precision);
   if (precision != PHOEBE_PREC_FP64)
     return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "interpolate_couplings: only PHOEBE_PREC_FP64 is implemented");
@@ -135,7 +135,7 @@ static int check_params(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, GridM
   if (!(p->delta_cut_sigmas > 0.0)) return fail(c, PHOEBE_GPU_ERR_ARG, "delta_cut_sigmas must be > 0");
   if (!(p->omega_cut_eV >= 0.0)) return fail(c, PHOEBE_GPU_ERR_ARG, "omega_cut_eV must be >= 0");
   if (!(p->degen_tol_eV >= 0.0)) return fail(c, PHOEBE_GPU_ERR_ARG, "degen_tol_eV must be >= 0");
-  if (p->precision < PHOEBE_PREC_FP64 || p->precision > PHOEBE_PREC_TF32)
+  if (p->precision < PHOEBE_PREC_FP64 || p->precision > PHOEBE_PREC_BF16X3)
     return fail(c, PHOEBE_GPU_ERR_ARG, "unknown precision %d", p->precision);
   for (int i = 0; i < 8; ++i)
     if (p->reserved[i] != 0) return fail(c, PHOEBE_GPU_ERR_ARG, "reserved fields must be zero");

@@ -31,6 +31,7 @@ struct phoebe_gpu_ctx {
   int nw = 0, nRH = 0;
   int na = 0, nRf = 0;
   int nRe = 0, nRp = 0, g_nw = 0, g_na = 0;
+  double we_max = 1.0, wp_max = 1.0;  // max |weight| of the R_e / R_p sets
   // tensor-core operands derived from g (invalidated by set_*)
   bool tc_g_valid = false;
   TcState* tc = nullptr;
@@ -52,9 +53,9 @@ int cuda_fail(phoebe_gpu_ctx* c, cudaError_t e, const char* what, int line);
     }                                                       \
   } while (0)
 
-#define TRY(expr)                \
+#define TRY(...)                 \
   do {                           \
-    int st_ = (expr);            \
+    int st_ = (__VA_ARGS__);     \
     if (st_ != PHOEBE_GPU_OK) return st_; \
   } while (0)
 
