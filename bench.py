@@ -1,0 +1,377 @@
+"""Benchmark: RTA linewidths of the Si-like 40^3 x 40^3 workload on B300.
+
+One step = one full ``phoebe_gpu_linewidths_rta`` pass (grid band structure,
+phonons, window, stage 1, stage 2 with the fused rotation/delta epilogue,
+degenerate averaging) over all active states of the synthetic Si-like crystal
+(8 Wannier functions, 2 atoms, 429 R_e and 429 R_p vectors, 40^3 k x 40^3 q,
+T = 300 K, sigma = 0.02 eV, window +-0.5 eV), inputs already resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P] [--impl reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+PREC_NAMES = {0: "fp64", 1: "split_bf16", 2: "split_tf32", 3: "bf16", 4: "tf32", 5: "split_fp16", 6: "bf16x3"}
+PREC_DTYPE = {0: "f64", 1: "bf16x6+f32acc", 2: "tf32x3+f32acc", 3: "bf16+f32acc", 4: "tf32+f32acc",
+              5: "f16x3+f32acc", 6: "bf16x3+f32acc"}
+METRIC = "Gamma_nk linewidths/s (el-ph RTA, Si-like 40^3 k x 40^3 q)"
+WORKLOAD = "si_like_fcc_nw8_na2_R429_k40x40x40_q40x40x40_T300_sigma0.02_window0.5"
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        power = [num(r[3]) for r in rows if num(r[3]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+def _blas_threads() -> int:
+    """Threads numpy's BLAS uses (the oracle's matrix products)."""
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        if info:
+            return int(max(i.get("num_threads", 1) for i in info))
+    except ImportError:
+        pass
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(var, "").isdigit():
+            return int(os.environ[var])
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def cpu_baseline_oracle(n_k: int, seed: int = 0) -> dict:
+    """The FP64 oracle as it stands, on a bounded sample of the workload (n_k active k points)."""
+    from oracle import elph
+    from workloads import synthetic as W
+    mat, prm = W.si_like(seed=seed)
+    t0 = time.perf_counter()
+    tab = elph.electron_table(mat, prm)
+    eg = tab[1][tab[3]]
+    ks, _ = elph.active_states(eg, prm.mu_eV, prm.window_eV)
+    pick = np.sort(np.random.default_rng(seed).choice(np.unique(ks), n_k, replace=False))
+    k2, b2, g = elph.linewidths_rta(mat, prm, k_indices=pick, table=tab)
+    el = time.perf_counter() - t0
+    threads = _blas_threads()
+    return {"value": len(g) / el, "unit": "linewidths/s", "cores": int(threads), "kind": "oracle",
+            "sample": f"{len(g)} active states on {n_k} seeded k points of the Si-like 40^3 x 40^3 workload, "
+                      f"including the oracle's own band structure on the 40^3 grid ({el:.1f} s)",
+            "seconds": el, "states": int(len(g))}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    steps, warmup = args.steps, args.warmup
+    from oracle import elph
+    from workloads import synthetic as W
+    mat, prm = W.si_like(seed=0)
+    tab = elph.electron_table(mat, prm)
+    eg = tab[1][tab[3]]
+    ks, _ = elph.active_states(eg, prm.mu_eV, prm.window_eV)
+    uk = np.unique(ks)
+    rng = np.random.default_rng(1)
+    per_step_k = max(1, args.ref_k_per_step)
+    for _ in range(warmup):
+        elph.linewidths_rta(mat, prm, k_indices=np.sort(rng.choice(uk, per_step_k, replace=False)), table=tab)
+    n_states = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        _, _, g = elph.linewidths_rta(mat, prm, k_indices=np.sort(rng.choice(uk, per_step_k, replace=False)),
+                                      table=tab)
+        n_states += len(g)
+    el = time.perf_counter() - t0
+    threads = _blas_threads()
+    value = n_states / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "linewidths/s", "n_gpus": world,
+        "steps": steps, "warmup": warmup, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_per_step": f"{per_step_k} seeded active k points (all their states)",
+                   "precision": "fp64 (CPU oracle)"},
+        "cpu_baseline": {"value": value, "unit": "linewidths/s", "cores": int(threads), "kind": "oracle",
+                         "sample": f"{n_states} states over {steps} steps of {per_step_k} k points each; "
+                                   "grid band structure precomputed once outside the timed steps"},
+        "e2e": {"value": value, "unit": "linewidths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", type=int, default=5, help="0 fp64, 1 split bf16, 2 split tf32, 5 split fp16")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-k-per-step", type=int, default=2)
+    ap.add_argument("--cpu-k", type=int, default=4, help="k points of the CPU-oracle baseline sample")
+    ap.add_argument("--fp64-k", type=int, default=48, help="k points of the FP64 GPU comparison sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--k-limit", type=int, default=0,
+                    help="profiling case: restrict to this many seeded active k points (0 = whole grid)")
+    ap.add_argument("--main-only", action="store_true", help="only the timed device leg (for ncu captures)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2111_14999_b300 as pg
+    from workloads import synthetic as W
+
+    world, rank, local = _dist()
+    dist = None
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist = td
+    dev = local if torch.cuda.is_available() else 0
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+
+    mat, prm = W.si_like(seed=rank)   # independent problem instance per rank (weak scaling)
+    ctx = pg.PhoebeGPU(dev, stream=stream)
+    ctx.set_material(mat)
+    params = pg.make_params(prm, precision=args.precision)
+    if args.k_limit > 0:
+        kgrid = np.arange(prm.nk[0] * prm.nk[1] * prm.nk[2])
+        pick = np.sort(np.random.default_rng(11).choice(kgrid, args.k_limit, replace=False))
+        params = pg.make_params(prm, precision=args.precision, k_subset=pick)
+    n = ctx.count_states(params)
+    k_out = torch.empty(n, dtype=torch.int32, device="cuda")
+    b_out = torch.empty(n, dtype=torch.int32, device="cuda")
+    g_out = torch.empty(n, dtype=torch.float64, device="cuda")
+    ctx.set_profiling(True)
+    for _ in range(args.warmup):
+        ctx.linewidths_rta_dev(params, k_out, b_out, g_out, n)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(dev)
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.linewidths_rta_dev(params, k_out, b_out, g_out, n)
+        stats.append(ctx.stats())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * n * args.steps / (ms / 1e3)
+    couplings = world * stats[-1]["couplings_dense"] * args.steps / (ms / 1e3)
+    launches = int(sum(s["kernel_launches"] for s in stats))
+
+    # roofline of the dominant kernel: stage-2 tcgen05 GEMM with the fused el-ph epilogue
+    peaks, peak_src = _peaks()
+    s2_ms = sum(s["stage2_ms"] for s in stats)
+    s2_launch = sum(s["stage2_launches"] for s in stats)
+    s2_flops = sum(s["stage2_flops"] for s in stats)
+    achieved = s2_flops / (s2_ms / 1e3) / 1e12 if s2_ms > 0 else None
+    split_factor = {0: 1, 1: 6, 2: 3, 3: 1, 4: 1, 5: 3, 6: 3}[args.precision]
+    kpad = (-(-2 * 429 // 64) * 64) / (2 * 429)
+    if args.precision == 0:
+        roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
+                "frac": achieved / 1.25 if achieved else None, "traffic": None,
+                "peak_source": "nominal FP64 1.25 TFLOP/s"}
+    else:
+        peak = peaks.get("bf16_tflops_sustained", 1400.0)
+        if args.precision in (2, 4):
+            peak *= 0.5     # TF32 dense rate is half the BF16 rate (nominal ratio)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "peak_source": f"{peak_src} bf16_tflops_sustained" + (" x 0.5 (tf32)" if args.precision in (2, 4) else ""),
+                "kernel": "k_tc_gemm<ElphEpi<8,6>> (stage 2, R_p contraction + fused epilogue)",
+                "algorithmic_flops_per_launch": s2_flops / max(s2_launch, 1),
+                "avg_launch_ms": s2_ms / max(s2_launch, 1),
+                "issued_tensor_tflops": achieved * split_factor * kpad if achieved else None,
+                "issued_frac": achieved * split_factor * kpad / peak if achieved else None}
+    traffic_path = os.path.join(ROOT, "profiles", "stage2_traffic.json")
+    if os.path.exists(traffic_path) and args.precision == 5:
+        with open(traffic_path) as f:
+            roof["traffic"] = json.load(f).get("dram_bytes_per_launch_full")
+
+    extra = {}
+    if args.main_only:
+        line = {"metric": METRIC, "value": value, "unit": "linewidths/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "states_per_step": n, "roofline": roof,
+                "gpu_launches": launches, "clocks": clocks, "note": "main leg only (profiling case)"}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        ctx.close()
+        return
+    # FP64 GPU comparison on a sample + error of this precision against it
+    if rank == 0 and args.fp64_k > 0:
+        ks_all = k_out.cpu().numpy()
+        g_all = g_out.cpu().numpy()
+        uk = np.unique(ks_all)
+        pick = np.sort(np.random.default_rng(5).choice(uk, min(args.fp64_k, len(uk)), replace=False))
+        ctx.set_profiling(True)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        k64, b64, g64 = ctx.linewidths_rta(prm, precision=0, k_subset=pick)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        fp64_ms = t0.elapsed_time(t1)
+        st64 = ctx.stats()
+        sel = np.isin(ks_all, pick)
+        floor = 1e-6 * np.median(np.abs(g64))
+        err = float(np.max(np.abs(g_all[sel] - g64) / np.maximum(np.abs(g64), floor)))
+        fp64_rate = len(g64) / (fp64_ms / 1e3)
+        extra["fp64_gpu"] = {"value": fp64_rate, "unit": "linewidths/s",
+                             "sample": f"{len(g64)} states on {len(pick)} seeded k points",
+                             "stage2_tflops": st64["stage2_flops"] / st64["stage2_ms"] / 1e9 if st64["stage2_ms"] else None}
+        extra["speedup_vs_fp64_gpu"] = (value / world) / fp64_rate
+        extra["max_rel_err_vs_fp64"] = err
+
+    # end to end through the public host-buffer API, inputs from pinned host memory every step
+    def pinned(a):
+        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory() if a.dtype != np.complex128 else \
+            torch.from_numpy(np.ascontiguousarray(a).view(np.float64)).pin_memory()
+        return t
+    pin = {name: pinned(getattr(mat, name)) for name in ("R_H", "w_H", "H", "mass_amu", "R_fc", "w_fc", "Phi",
+                                                       "Re", "we", "Rp", "wp", "g")}
+    h2d = int(sum(t.numel() * t.element_size() for t in pin.values()))
+    lib = pg.lib
+    import ctypes as C
+
+    def e2e_step():
+        c = ctx._ctx
+        ctx._check(lib.phoebe_gpu_set_hamiltonian(c, mat.nw, len(mat.R_H), C.c_void_p(pin["R_H"].data_ptr()),
+                                                  C.c_void_p(pin["w_H"].data_ptr()), C.c_void_p(pin["H"].data_ptr())))
+        ctx._check(lib.phoebe_gpu_set_force_constants(c, mat.na, C.c_void_p(pin["mass_amu"].data_ptr()),
+                                                      len(mat.R_fc), C.c_void_p(pin["R_fc"].data_ptr()),
+                                                      C.c_void_p(pin["w_fc"].data_ptr()),
+                                                      C.c_void_p(pin["Phi"].data_ptr())))
+        ctx._check(lib.phoebe_gpu_set_elph_wannier(c, len(mat.Re), C.c_void_p(pin["Re"].data_ptr()),
+                                                   C.c_void_p(pin["we"].data_ptr()), len(mat.Rp),
+                                                   C.c_void_p(pin["Rp"].data_ptr()), C.c_void_p(pin["wp"].data_ptr()),
+                                                   C.c_void_p(pin["g"].data_ptr())))
+        return ctx.linewidths_rta(params)
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        kk, bb, gg = e2e_step()
+    el = time.perf_counter() - t0
+    d2h = int(len(gg) * (8 + 4 + 4))
+    e2e_value = world * len(gg) * args.steps / el
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "linewidths/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": PREC_DTYPE[args.precision], "data": "synthetic",
+        "config": {"workload": WORKLOAD, "states_per_step": n, "q_points": 64000,
+                   "precision": PREC_NAMES[args.precision],
+                   "l2": "inputs larger than L2 (stage-1 operand from g: 1.2 GB, q-phase operand 0.23 GB)",
+                   "parallelism": f"{world} independent instance(s), one per GPU"},
+        "couplings_per_s": couplings,
+        "gpu_launches": launches,
+        "roofline": roof,
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": "linewidths/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        **extra,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_oracle(args.cpu_k)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
