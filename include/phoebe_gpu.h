@@ -176,6 +176,32 @@ int phoebe_gpu_get_stats(const phoebe_gpu_ctx* ctx, phoebe_gpu_stats* out);
 /* Cap on the context's device memory (bytes, 0 = none); exceeding it returns ERR_NOMEM. */
 int phoebe_gpu_set_memory_cap(phoebe_gpu_ctx* ctx, int64_t bytes);
 
+/* Allocation-free band energies at explicit k points.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory -- host
+ * programs sharing the GPU with a framework that has already reserved nearly all of
+ * it for its own pool (cudaMalloc would fail), and latency-sensitive callers that
+ * cannot accept the device-wide synchronisation cudaMalloc/cudaFree may imply.
+ * It computes H^W_k = sum_R w_R e^{ik.R} H(R) and eps_k, U_k of Eq. 11 like the
+ * grid path, needs no context, and allocates nothing: its only scratch is a static
+ * 16 MiB device array that every GPU loading the library holds until exit.
+ *   nw, n_R      as for set_hamiltonian (nw <= 32)
+ *   R, w, H      DEVICE arrays: n_R x 3 int32, n_R weights (not NULL), n_R x nw x nw
+ *                complex (interleaved doubles), caller-owned
+ *   n_k, k       n_k points, DEVICE array n_k x 3 crystal coordinates
+ *   eps          DEVICE output n_k x nw, ascending
+ *   U            DEVICE output n_k x nw x nw complex (columns = eigenvectors) or NULL
+ *   cuda_stream  cudaStream_t of the work (NULL = default stream); the call returns
+ *                after the stream has finished it.
+ * Returns PHOEBE_GPU_ERR_NOMEM without launching anything when 2 * n_k * nw^2 * 16
+ * bytes exceed the 16 MiB scratch, PHOEBE_GPU_ERR_ARG for bad sizes or NULL
+ * pointers, PHOEBE_GPU_ERR_NOTCONVERGED if an eigensolve hit its sweep cap.
+ * The first call on each device looks up the scratch address on the current device
+ * (one-time set-up); make that first call before any stream capture begins.  All
+ * calls on a device share the one scratch array: calls that overlap on the GPU
+ * (other streams, other host threads) race on it. */
+int phoebe_gpu_bands_noalloc(int nw, int n_R, const int32_t* R, const double* w, const double* H, int n_k,
+                             const double* k, double* eps, double* U, void* cuda_stream);
+
 /* Physical constants compiled into the library: out[0] = k_B (eV/K),
  * out[1] = hbar*sqrt(eV/(A^2 amu)) (eV), out[2] = hbar^2/(amu eV A^2).  Needs no GPU. */
 void phoebe_gpu_constants(double out[3]);

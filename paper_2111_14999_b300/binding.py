@@ -28,7 +28,7 @@ EXPORTED = (
     "phoebe_gpu_interpolate_couplings", "phoebe_gpu_rta_params_default",
     "phoebe_gpu_linewidths_rta", "phoebe_gpu_linewidths_rta_dev",
     "phoebe_gpu_set_profiling", "phoebe_gpu_get_stats", "phoebe_gpu_set_memory_cap",
-    "phoebe_gpu_constants", "phoebe_gpu_version",
+    "phoebe_gpu_constants", "phoebe_gpu_version", "phoebe_gpu_bands_noalloc",
 )
 
 
@@ -85,6 +85,7 @@ def _load() -> C.CDLL:
         "phoebe_gpu_set_memory_cap": (I, [P, I64]),
         "phoebe_gpu_constants": (None, [C.POINTER(D)]),
         "phoebe_gpu_version": (C.c_char_p, []),
+        "phoebe_gpu_bands_noalloc": (I, [I, I, P, P, P, I, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
