@@ -13,7 +13,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libphoebe_gpu.so")
+# PHOEBE_GPU_LIB may name another build of the library (same ABI)
+LIB_PATH = os.environ.get("PHOEBE_GPU_LIB") or os.path.join(_HERE, "libphoebe_gpu.so")
 
 STATUS = {
     0: "OK", -1: "ERR_ARG", -2: "ERR_ORDER", -3: "ERR_SHAPE", -4: "ERR_GRID", -5: "ERR_NOMEM",

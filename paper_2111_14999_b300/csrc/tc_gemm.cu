@@ -42,6 +42,10 @@ struct TcState {
   float g_scale = 1.f;
 };
 
+#ifndef PHX_KB_PER_CHUNK
+#define PHX_KB_PER_CHUNK 2  // K blocks accumulated per TMEM partial
+#endif
+
 namespace phx {
 
 using namespace tc;
@@ -52,7 +56,9 @@ struct TcGemmArgs {
   int kb_per_chunk; // K blocks accumulated per TMEM partial
   int b_row_step;   // B rows advanced per n tile
   int group_m;      // m tiles per scheduling group (L2 reuse)
-  int ntiles;       // m_tiles * n_tiles
+  int ntiles;       // m_tiles * n_tiles (dense order) when tile_list is NULL
+  const int2* tile_list;   // optional (m, n) list; its length is read from *ntiles_dev
+  const int64_t* ntiles_dev;
   int* err;         // set to 1 if any bounded wait ran out
 };
 
@@ -67,24 +73,29 @@ __host__ __device__ inline float pow2_scale(float maxabs) {
 // Epilogues receive the finished FP32 tile row of their thread in registers (acc[BN],
 // column c of the tile = acc[c]) and the tile coordinates.
 struct StoreEpi {
-  static constexpr int BN = 128;
+  static constexpr int BNW = 128;      // columns per epilogue warpgroup
+  static constexpr int BN = 2 * BNW;   // MMA N
+  static constexpr uint32_t SMEM_BYTES = 0;
+  struct Pre {};
   struct Params {
     float* C;
     int64_t ldc;
     int M, N;  // valid rows / columns of C
   };
-  static __device__ __forceinline__ void tile(const Params& p, int m, int n, int b_row_step, const float* acc,
-                                              int row) {
+  static __device__ __forceinline__ const void* smem_src(const Params&, int) { return nullptr; }
+  static __device__ __forceinline__ void prefetch(const Params&, int, int, int, int, Pre&) {}
+  static __device__ __forceinline__ void tile(const Params& p, int m, int n, int wg, int row, const float* acc,
+                                              const Pre&, const float2*) {
     const int64_t grow = (int64_t)m * 128 + row;
     if (grow >= p.M) return;
-    const int64_t gcol0 = (int64_t)n * b_row_step;
+    const int64_t gcol0 = (int64_t)n * BN + wg * BNW;
     float* dst = p.C + grow * p.ldc + gcol0;
-    if (gcol0 + BN <= p.N) {
+    if (gcol0 + BNW <= p.N) {
 #pragma unroll
-      for (int i = 0; i < BN; i += 4) *reinterpret_cast<float4*>(dst + i) = make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
+      for (int i = 0; i < BNW; i += 4) *reinterpret_cast<float4*>(dst + i) = make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
     } else {
 #pragma unroll
-      for (int i = 0; i < BN; ++i)
+      for (int i = 0; i < BNW; ++i)
         if (gcol0 + i < p.N) dst[i] = acc[i];
     }
   }
@@ -92,105 +103,128 @@ struct StoreEpi {
 
 template <int NW, int NM>
 struct ElphEpi {
-  static constexpr int CPS = 2 * NW * NM;                        // tile columns per state
-  static constexpr int SPT = (128 / CPS) > 0 ? (128 / CPS) : 1;  // states per tile
-  static constexpr int BN = (SPT * CPS + 15) / 16 * 16;
+  static constexpr int CPS = 2 * NW * NM;  // tile columns per state
+  // states per epilogue warpgroup: the most whose columns fit 128 and are a multiple of 16
+  static constexpr int spw_pick() {
+    for (int w = 128 / CPS; w >= 1; --w)
+      if ((w * CPS) % 16 == 0) return w;
+    return 0;
+  }
+  static constexpr int SPW = spw_pick();
+  static_assert(SPW >= 1, "state column count not supported by the tile layout");
+  static constexpr int SPT = 2 * SPW;      // states per tile
+  static constexpr int BNW = SPW * CPS;    // columns per epilogue warpgroup
+  static constexpr int BN = 2 * BNW;       // MMA N
+  static constexpr int ZROW = NM * NM;     // complex mode factors per q row
+  static constexpr uint32_t SMEM_BYTES = 128u * ZROW * 8u;  // the tile's Z_q block
   struct Params {
-    int Mq;                 // valid q rows
+    int Mq;                 // A-operand rows (q rows incl. padding)
     int S;                  // states in this batch
-    const int* st_k;        // batch-local state -> k grid index
-    const int* st_b;        // batch-local state -> band
+    const int4* sinfo;      // per batch state: (k_f x, y, z on the fine grid, band)
+    const double* eps_n;    // per batch state: initial-state energy
     int64_t s_base;         // batch offset into gamma
     GridMap gm;
-    const double* epsF;     // [NF][NW]
+    const int4* qinfo;      // per A row: (q x, y, z on the fine grid (q * sq), q or -1)
+    const float2* eps2;     // [NF][NW] band energies as (hi, lo) float pairs
     const float* fF;        // [NF][NW] Fermi occupations
     const float2* UH;       // [NF][NW(m')][NW(m)] = conj(U[m][m'])
-    const float2* Z;        // [Nq][NM(sa)][NM(nu)]
-    const float* om;        // [Nq][NM]
-    const float* nB;        // [Nq][NM]
-    double reach;           // omega_max + cut*sigma: |eps_n - eps_m'| beyond it contributes 0
+    const float2* Zr;       // [A row][NM(sa)][NM(nu)] mode factors in A-row order
+    const float* omr;       // [A row][NM]
+    const float* nBr;       // [A row][NM]
+    float reach;            // omega_max + cut*sigma: |eps_n - eps_m'| beyond it contributes 0
     float inv_sigma, cut2;  // 1/sigma, cut^2
     double scale_base;      // (2 pi / N_q) / (sqrt(pi) sigma) / s_A^2
     const unsigned* tmax;   // max |T| of the batch (float bits): B operand scale pow2_scale(tmax)
     double* gamma;
   };
-  static __device__ __forceinline__ void tile(const Params& p, int m, int n, int b_row_step, const float* acc,
-                                              int row) {
+  // Per-thread values loaded before the tile's reductions so their latency is hidden.
+  struct Pre {
+    int4 qi;
+    float om[NM], nb[NM];
+  };
+  static __device__ __forceinline__ const void* smem_src(const Params& p, int m) { return p.Zr + (int64_t)m * 128 * ZROW; }
+  static __device__ __forceinline__ void prefetch(const Params& p, int m, int n, int wg, int row, Pre& pre) {
+    const int qrow = m * 128 + row;
+    pre.qi = qrow < p.Mq ? __ldg(p.qinfo + qrow) : make_int4(0, 0, 0, -1);
+#pragma unroll
+    for (int v = 0; v < NM; ++v) {
+      pre.om[v] = __ldg(p.omr + (int64_t)qrow * NM + v);
+      pre.nb[v] = __ldg(p.nBr + (int64_t)qrow * NM + v);
+    }
+  }
+  // acc[j*CPS + 2*(sa*NW + m) + {0,1}] = G_s(q)[m][sa] (Re, Im) of state j of this warpgroup's half;
+  // zs = the tile's Z_q rows in shared memory.
+  static __device__ __forceinline__ void tile(const Params& p, int m, int n, int wg, int row, const float* acc,
+                                              const Pre& pre, const float2* zs) {
     const float sT = pow2_scale(__uint_as_float(__ldg(p.tmax)));
     const double scale = p.scale_base / ((double)sT * (double)sT);
-    const int qrow = m * 128 + row;
-    const bool valid = qrow < p.Mq;
-    const int q = valid ? qrow : 0;
+    const bool valid = pre.qi.w >= 0;
+    const float2* zrow = zs + row * ZROW;
 #pragma unroll
-    for (int j = 0; j < SPT; ++j) {
-      const int s = n * SPT + j;
-      if (s >= p.S) break;  // uniform across the block
-      const int k = __ldg(p.st_k + s);
-      const int b = __ldg(p.st_b + s);
-      const double eps_n = __ldg(p.epsF + p.gm.k_to_fine(k) * NW + b);
-      const int64_t kq = p.gm.kq_to_fine(k, q);
-      float d[NW];
-      bool need = false;
+    for (int j = 0; j < SPW; ++j) {
+      const int s = n * SPT + wg * SPW + j;
+      if (s >= p.S) break;  // uniform across the warpgroup
+      const int4 si = __ldg(p.sinfo + s);
+      const double e_n = __ldg(p.eps_n + s);
+      int f0 = si.x + pre.qi.x, f1 = si.y + pre.qi.y, f2 = si.z + pre.qi.z;  // k + q on the fine grid
+      f0 -= f0 >= p.gm.nf[0] ? p.gm.nf[0] : 0;
+      f1 -= f1 >= p.gm.nf[1] ? p.gm.nf[1] : 0;
+      f2 -= f2 >= p.gm.nf[2] ? p.gm.nf[2] : 0;
+      const int kq = (f0 * p.gm.nf[1] + f1) * p.gm.nf[2] + f2;
+      const float en_hi = (float)e_n, en_lo = (float)(e_n - (double)en_hi);
+      unsigned need = 0;
 #pragma unroll
       for (int mp = 0; mp < NW; ++mp) {
-        double dd = eps_n - __ldg(p.epsF + kq * NW + mp);
-        d[mp] = (float)dd;
-        need |= valid && fabs(dd) < p.reach;
+        const float2 e = __ldg(p.eps2 + (int64_t)kq * NW + mp);
+        const float dm = (en_hi - e.x) + (en_lo - e.y);  // eps_n - eps_{m', k+q}
+        if (valid && fabsf(dm) < p.reach) need |= 1u << mp;
       }
+      const unsigned wneed = __reduce_or_sync(0xffffffffu, need);
       float part = 0.f;
-      if (need) {
-        // gz[m][nu] = sum_sa G[m][sa] Z_q[sa][nu], G[m][sa] = acc[j*CPS + 2*(sa*NW + m) + re/im]
-        float2 gz[NW][NM];
+#pragma unroll 1
+      for (int mp = 0; mp < NW; ++mp) {
+        if (!((wneed >> mp) & 1u)) continue;  // warp-uniform
+        // t[sa] = sum_m conj(U_{k+q}[m][m']) G[m][sa]
+        float2 u[NW];
+        const float2* uh = p.UH + ((int64_t)kq * NW + mp) * NW;
 #pragma unroll
-        for (int mm = 0; mm < NW; ++mm)
-#pragma unroll
-          for (int v = 0; v < NM; ++v) gz[mm][v] = make_float2(0.f, 0.f);
+        for (int mm = 0; mm < NW; ++mm) u[mm] = __ldg(uh + mm);
+        float2 t[NM];
 #pragma unroll
         for (int sa = 0; sa < NM; ++sa) {
-          float2 z[NM];
-#pragma unroll
-          for (int v = 0; v < NM; ++v) z[v] = __ldg(p.Z + ((int64_t)q * NM + sa) * NM + v);
+          t[sa] = make_float2(0.f, 0.f);
 #pragma unroll
           for (int mm = 0; mm < NW; ++mm) {
             const float gr = acc[j * CPS + 2 * (sa * NW + mm)], gi = acc[j * CPS + 2 * (sa * NW + mm) + 1];
-#pragma unroll
-            for (int v = 0; v < NM; ++v) {
-              gz[mm][v].x = fmaf(gr, z[v].x, fmaf(-gi, z[v].y, gz[mm][v].x));
-              gz[mm][v].y = fmaf(gr, z[v].y, fmaf(gi, z[v].x, gz[mm][v].y));
-            }
+            t[sa].x = fmaf(u[mm].x, gr, fmaf(-u[mm].y, gi, t[sa].x));
+            t[sa].y = fmaf(u[mm].x, gi, fmaf(u[mm].y, gr, t[sa].y));
           }
         }
-        float om[NM], nb[NM];
+        if (!((need >> mp) & 1u)) continue;
+        // g[nu] = sum_sa t[sa] Z_q[sa][nu]  (Z_q from shared memory)
+        float2 g[NM];
 #pragma unroll
-        for (int v = 0; v < NM; ++v) {
-          om[v] = __ldg(p.om + (int64_t)q * NM + v);
-          nb[v] = __ldg(p.nB + (int64_t)q * NM + v);
-        }
-        for (int mp = 0; mp < NW; ++mp) {
-          if (!(fabsf(d[mp]) < (float)p.reach)) continue;
-          const float f = __ldg(p.fF + kq * NW + mp);
-          const float2* uh = p.UH + (kq * NW + mp) * NW;
-          float2 gv[NM];
+        for (int v = 0; v < NM; ++v) g[v] = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int v = 0; v < NM; ++v) gv[v] = make_float2(0.f, 0.f);
-#pragma unroll
-          for (int mm = 0; mm < NW; ++mm) {
-            const float2 u = __ldg(uh + mm);
-#pragma unroll
-            for (int v = 0; v < NM; ++v) {
-              gv[v].x = fmaf(u.x, gz[mm][v].x, fmaf(-u.y, gz[mm][v].y, gv[v].x));
-              gv[v].y = fmaf(u.x, gz[mm][v].y, fmaf(u.y, gz[mm][v].x, gv[v].y));
-            }
-          }
+        for (int sa = 0; sa < NM; ++sa) {
 #pragma unroll
           for (int v = 0; v < NM; ++v) {
-            const float t1 = (d[mp] - om[v]) * p.inv_sigma;
-            const float t2 = (d[mp] + om[v]) * p.inv_sigma;
-            float w = 0.f;
-            if (t1 * t1 < p.cut2) w += (nb[v] + 1.f - f) * expf(-t1 * t1);
-            if (t2 * t2 < p.cut2) w += (nb[v] + f) * expf(-t2 * t2);
-            part = fmaf(gv[v].x * gv[v].x + gv[v].y * gv[v].y, w, part);
+            const float2 z = zrow[sa * NM + v];
+            g[v].x = fmaf(t[sa].x, z.x, fmaf(-t[sa].y, z.y, g[v].x));
+            g[v].y = fmaf(t[sa].x, z.y, fmaf(t[sa].y, z.x, g[v].y));
           }
+        }
+        const float f = __ldg(p.fF + (int64_t)kq * NW + mp);
+        const float2 e = __ldg(p.eps2 + (int64_t)kq * NW + mp);
+        const float dm = (en_hi - e.x) + (en_lo - e.y);
+#pragma unroll
+        for (int v = 0; v < NM; ++v) {
+          const float t1 = (dm - pre.om[v]) * p.inv_sigma;
+          const float t2 = (dm + pre.om[v]) * p.inv_sigma;
+          float w = 0.f;
+          if (t1 * t1 < p.cut2) w += (pre.nb[v] + 1.f - f) * expf(-t1 * t1);
+          if (t2 * t2 < p.cut2) w += (pre.nb[v] + f) * expf(-t2 * t2);
+          part = fmaf(g[v].x * g[v].x + g[v].y * g[v].y, w, part);
         }
       }
 #pragma unroll
@@ -207,11 +241,29 @@ struct ElphEpi {
 // small cross products of the split parts are issued before the dominant hi*hi
 // product, so the truncating steps see small accumulators.  The epilogue warps add
 // the chunk partials into FP32 registers with round-to-nearest.
-constexpr int kTcThreads = 192;
-constexpr uint32_t kTileABytes = 128 * 128;  // 128 rows x 128 bytes (64 BF16/FP16 or 32 TF32)
-constexpr int kMaxPartials = 8;
+constexpr int kEpiGroups = 2;                      // epilogue warpgroups, each owning half the columns
+constexpr int kTcThreads = 64 + 128 * kEpiGroups;  // producer warp, MMA warp, epilogue warps
+constexpr uint32_t kTileABytes = 128 * 128;        // 128 rows x 128 bytes (64 BF16/FP16 or 32 TF32)
+constexpr int kMaxPartials = 4;                    // TMEM partial buffers
+
+__host__ __device__ __forceinline__ void dense_tile_coords(int group_m, int m_tiles, int n_tiles, int t, int& m,
+                                                           int& n) {
+  const int per_group = group_m * n_tiles;
+  const int g = t / per_group;
+  const int first_m = g * group_m;
+  const int gm = min(group_m, m_tiles - first_m);
+  const int r = t - g * per_group;
+  m = first_m + r % gm;
+  n = r / gm;
+}
 
 __device__ __forceinline__ void tile_coords(const TcGemmArgs& a, int t, int& m, int& n) {
+  if (a.tile_list) {
+    const int2 v = a.tile_list[t];
+    m = v.x;
+    n = v.y;
+    return;
+  }
   const int per_group = a.group_m * a.n_tiles;
   const int g = t / per_group;
   const int first_m = g * a.group_m;
@@ -226,39 +278,53 @@ __device__ constexpr int kProdA[6] = {0, 0, 1, 0, 2, 1};
 __device__ constexpr int kProdB[6] = {0, 1, 0, 2, 0, 1};
 
 // FMT: 0 = FP16, 1 = BF16 (tcgen05 kind::f16), 2 = TF32 (kind::tf32).  NSPLIT parts per
-// operand, NPROD leading products of the parts (1, 3 or 6).
-template <class Epi, int FMT, int NSPLIT, int NPROD>
+// operand, NPROD leading products of the parts (1, 3 or 6).  CN > 1: the CN CTAs of a
+// cluster work on the same 128-row A tile and CN consecutive n tiles; each CTA loads
+// 128/CN rows of every A K-block and multicasts them to the whole cluster, so L2 delivers
+// each A tile once per cluster instead of once per CTA.
+template <class Epi, int FMT, int NSPLIT, int NPROD, int CN>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
               const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB0,
               const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ CUtensorMap tmB2, TcGemmArgs a,
               typename Epi::Params ep) {
   constexpr int KIND = FMT == 2 ? 1 : 0;
-  constexpr int BN = Epi::BN;
+  constexpr int BN = Epi::BN, BNW = Epi::BNW;
   constexpr uint32_t B_BYTES = (uint32_t)BN * 128u;
   constexpr uint32_t STAGE = (uint32_t)NSPLIT * (kTileABytes + B_BYTES);
-  constexpr int NPART = (512 / BN) < kMaxPartials ? (512 / BN) : kMaxPartials;  // TMEM partial buffers
+  constexpr int NPART = (512 / BN) < kMaxPartials ? (512 / BN) : kMaxPartials;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)a.stages * STAGE);
+  constexpr uint32_t ZB = (Epi::SMEM_BYTES + 1023u) & ~1023u;  // epilogue smem block
+  uint8_t* zblk = smem + (size_t)a.stages * STAGE;
+  uint64_t* full = reinterpret_cast<uint64_t*>(zblk + ZB);
   uint64_t* empty = full + a.stages;
   uint64_t* pfull = empty + a.stages;
   uint64_t* pempty = pfull + NPART;
-  uint64_t* drain = pempty + NPART;
+  uint64_t* zfull = pempty + NPART;   // epilogue block landed
+  uint64_t* zempty = zfull + 1;       // every epilogue thread finished with it
+  uint64_t* drain = zempty + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nchunk = (a.kblocks + a.kb_per_chunk - 1) / a.kb_per_chunk;
+  if (a.tile_list) a.ntiles = (int)*a.ntiles_dev;  // same value in every thread
+  const int rank = CN > 1 ? (int)cluster_ctarank() : 0;
+  const int cid = blockIdx.x / CN, nclu = gridDim.x / CN;  // cluster id / count
+  constexpr uint16_t kMask = (uint16_t)((1u << CN) - 1u);
+  constexpr int kArows = 128 / CN;                          // A rows this CTA loads per K block
   if (threadIdx.x == 0) {
     for (int i = 0; i < a.stages; ++i) {
       mbar_init(full + i, 1);
-      mbar_init(empty + i, 1);
+      mbar_init(empty + i, CN);  // released by the MMA of every CTA that reads the slot
     }
     for (int i = 0; i < NPART; ++i) {
       mbar_init(pfull + i, 1);
-      mbar_init(pempty + i, 128);
+      mbar_init(pempty + i, 128 * kEpiGroups);  // every epilogue thread releases its columns
     }
+    mbar_init(zfull, 1);
+    mbar_init(zempty, 128 * kEpiGroups);
     mbar_init(drain, 1);
     *abort_flag = 0;
     fence_mbar_init();
@@ -278,7 +344,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tmem_relinquish();
   }
   tc_fence_before();
-  __syncthreads();
+  if (CN > 1)
+    cluster_sync();  // peers multicast into this CTA's smem and arrive on its barriers
+  else
+    __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
@@ -290,9 +359,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int i = 0; i < 16; ++i) armed[i] = false;
       uint32_t it = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+      for (int t = cid; t < a.ntiles && ok; t += nclu) {
         int m, n;
         tile_coords(a, t, m, n);
+        n = n * CN + rank;
         for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
           const int s = (int)(it % (uint32_t)a.stages);
           const uint32_t ph = (it / (uint32_t)a.stages) & 1u;
@@ -304,16 +374,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           mbar_arrive_expect_tx(full + s, STAGE);
           const int kx = kb * (KIND == 0 ? 64 : 32);
           uint8_t* bbase = base + NSPLIT * kTileABytes;
-          tma_load_2d(base, &tmA0, full + s, kx, m * 128);
+          uint8_t* aslice = base + rank * kArows * 128;
+          const int ay = m * 128 + rank * kArows;
+          if (CN > 1) {
+            tma_load_2d_mc(aslice, &tmA0, full + s, kx, ay, kMask);
+            if (NSPLIT > 1) tma_load_2d_mc(aslice + kTileABytes, &tmA1, full + s, kx, ay, kMask);
+            if (NSPLIT > 2) tma_load_2d_mc(aslice + 2 * kTileABytes, &tmA2, full + s, kx, ay, kMask);
+          } else {
+            tma_load_2d(aslice, &tmA0, full + s, kx, ay);
+            if (NSPLIT > 1) tma_load_2d(aslice + kTileABytes, &tmA1, full + s, kx, ay);
+            if (NSPLIT > 2) tma_load_2d(aslice + 2 * kTileABytes, &tmA2, full + s, kx, ay);
+          }
           tma_load_2d(bbase, &tmB0, full + s, kx, n * a.b_row_step);
-          if (NSPLIT > 1) {
-            tma_load_2d(base + kTileABytes, &tmA1, full + s, kx, m * 128);
-            tma_load_2d(bbase + B_BYTES, &tmB1, full + s, kx, n * a.b_row_step);
-          }
-          if (NSPLIT > 2) {
-            tma_load_2d(base + 2 * kTileABytes, &tmA2, full + s, kx, m * 128);
-            tma_load_2d(bbase + 2 * B_BYTES, &tmB2, full + s, kx, n * a.b_row_step);
-          }
+          if (NSPLIT > 1) tma_load_2d(bbase + B_BYTES, &tmB1, full + s, kx, n * a.b_row_step);
+          if (NSPLIT > 2) tma_load_2d(bbase + 2 * B_BYTES, &tmB2, full + s, kx, n * a.b_row_step);
           last_parity[s] = (int)ph;
           armed[s] = true;
         }
@@ -336,10 +410,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const uint32_t idesc = idesc_m128((uint32_t)BN, (uint32_t)FMT);
       uint32_t it = 0, pc = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+      for (int t = cid; t < a.ntiles && ok; t += nclu) {
         for (int ch = 0; ch < nchunk && ok; ++ch, ++pc) {
           const uint32_t pb = pc % (uint32_t)NPART, pph = (pc / (uint32_t)NPART) & 1u;
-          if (pc >= (uint32_t)NPART && !mbar_wait(pempty + pb, pph ^ 1u, abort_flag)) {
+          uint64_t* pf = pfull + pb;
+          uint64_t* pe = pempty + pb;
+          if (pc >= (uint32_t)NPART && !mbar_wait(pe, pph ^ 1u, abort_flag)) {
             ok = false;
             break;
           }
@@ -379,8 +455,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               }
             }
           }
-          for (uint32_t i2 = it0; i2 < it; ++i2) mma_commit(empty + (int)(i2 % (uint32_t)a.stages));
-          mma_commit(pfull + pb);
+          for (uint32_t i2 = it0; i2 < it; ++i2) {
+            if (CN > 1)
+              mma_commit_mc(empty + (int)(i2 % (uint32_t)a.stages), kMask);
+            else
+              mma_commit(empty + (int)(i2 % (uint32_t)a.stages));
+          }
+          mma_commit(pf);
         }
       }
       // drain: no MMA may be in flight when TMEM is released
@@ -394,15 +475,32 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     }
   } else {
-    // ---------------- epilogue: warps 2..5 -> TMEM lane quarters (warp % 4)
+    // ---------------- epilogue: warpgroup wg = (warp-2)/4 owns columns [wg*BNW, (wg+1)*BNW) of
+    // every tile; warp w reads TMEM lanes 32*(w%4) .. 32*(w%4)+31 = tile rows of its quarter
+    const int wg = (warp - 2) >> 2;
     const int quarter = warp & 3;
     const int row = quarter * 32 + lane;
+    const bool zissuer = warp == 2 && lane == 0;  // loads the per-tile epilogue block
+    bool zpending = false;
+    uint32_t zcount = 0;
+    if (Epi::SMEM_BYTES > 0 && zissuer && cid < a.ntiles) {
+      int m0, n0;
+      tile_coords(a, cid, m0, n0);
+      mbar_arrive_expect_tx(zfull, Epi::SMEM_BYTES);
+      bulk_load(zblk, Epi::smem_src(ep, m0), Epi::SMEM_BYTES, zfull);
+      zpending = true;
+    }
     uint32_t pc = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
-      float acc[BN];
+    for (int t = cid; t < a.ntiles && ok; t += nclu, ++zcount) {
+      int m, n;
+      tile_coords(a, t, m, n);
+      n = n * CN + rank;
+      typename Epi::Pre pre;
+      Epi::prefetch(ep, m, n, wg, row, pre);
+      float acc[BNW];
 #pragma unroll
-      for (int i = 0; i < BN; ++i) acc[i] = 0.f;
+      for (int i = 0; i < BNW; ++i) acc[i] = 0.f;
       for (int ch = 0; ch < nchunk; ++ch, ++pc) {
         const uint32_t pb = pc % (uint32_t)NPART, pph = (pc / (uint32_t)NPART) & 1u;
         int w = 1;
@@ -413,9 +511,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + pb * (uint32_t)BN;
+        const uint32_t taddr =
+            tmem_base + ((uint32_t)(quarter * 32) << 16) + pb * (uint32_t)BN + (uint32_t)(wg * BNW);
 #pragma unroll
-        for (int c0 = 0; c0 < BN; c0 += 16) {
+        for (int c0 = 0; c0 < BNW; c0 += 16) {
           float v[16];
           tmem_ld16(taddr + c0, v);
 #pragma unroll
@@ -425,9 +524,41 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         mbar_arrive(pempty + pb);
       }
       if (!ok) break;
-      int m, n;
-      tile_coords(a, t, m, n);
-      Epi::tile(ep, m, n, a.b_row_step, acc, row);
+      if (Epi::SMEM_BYTES > 0) {
+        int w = 1;
+        if (lane == 0) w = mbar_wait(zfull, zcount & 1u, abort_flag) ? 1 : 0;
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (!w) {
+          ok = false;
+          break;
+        }
+        if (zissuer) zpending = false;
+      }
+      Epi::tile(ep, m, n, wg, row, acc, pre, reinterpret_cast<const float2*>(zblk));
+      if (Epi::SMEM_BYTES > 0) {
+        mbar_arrive(zempty);
+        if (zissuer && t + nclu < a.ntiles) {
+          // the next tile's block may replace this one once every epilogue thread is done
+          if (!mbar_wait(zempty, zcount & 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          int m1, n1;
+          tile_coords(a, t + nclu, m1, n1);
+          mbar_arrive_expect_tx(zfull, Epi::SMEM_BYTES);
+          bulk_load(zblk, Epi::smem_src(ep, m1), Epi::SMEM_BYTES, zfull);
+          zpending = true;
+        }
+      }
+    }
+    if (zpending) {  // never leave with a bulk copy in flight
+      unsigned long long t0 = globaltimer();
+      while (!mbar_try_wait(zfull, zcount & 1u)) {
+        if (globaltimer() - t0 > kWaitLimitNs) {
+          *abort_flag = 1;
+          break;
+        }
+      }
     }
   }
   tc_fence_before();
@@ -437,6 +568,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tmem_dealloc(tmem_base, 512);
   }
   if (threadIdx.x == 0 && *abort_flag) atomicOr(a.err, 1);
+  if (CN > 1) cluster_sync();  // no CTA leaves while a peer may still write into its smem
 }
 
 // ------------------------------------------------------------------ operand packing
@@ -493,8 +625,8 @@ __global__ void k_pack_phase(const int* __restrict__ pts, int64_t npts, const in
   int64_t i = t / (Kp / 2);
   int r = (int)(t % (Kp / 2));
   float re = 0.f, im = 0.f;
-  if (r < nR) {
-    int64_t idx = pts ? pts[i] : i;
+  const int64_t idx = pts ? pts[i] : i;  // < 0: padding row
+  if (r < nR && idx >= 0) {
     int j[3];
     grid_coords(idx, gp.n, j);
     int Rv[3] = {R[3 * r], R[3 * r + 1], R[3 * r + 2]};
@@ -586,16 +718,128 @@ __global__ void k_split_t(const float2* __restrict__ T, int S, int nRp, int nw, 
   split_store<FMT, NSPLIT>(re, P, o1 + 1);
 }
 
+// ------------------------------------------------------------------ screening (exact under the delta cutoff)
+// q rows of the stage-2 A operand are ordered in compact blocks of bx x by x bz q points (z fastest
+// inside a block, blocks lexicographic), each padded to 128 rows.  A (block, state) pair whose
+// final-state band energies cannot come within omega_max + cut*sigma of eps_n contributes nothing.
+struct QBlocks {
+  int b[3];   // block shape in q-grid units
+  int nb[3];  // blocks per axis
+  int B[3];   // matching F-grid box shape (b * sq)
+  int nbox[3];
+};
+
+// lo/hi[box][band]: min / max band energy over each aligned F-grid box.
+__global__ void k_box_bounds(const double* __restrict__ epsF, GridMap gm, int nw, QBlocks qb, double* __restrict__ lo,
+                             double* __restrict__ hi) {
+  const int64_t nbox = (int64_t)qb.nbox[0] * qb.nbox[1] * qb.nbox[2];
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nbox * nw) return;
+  const int64_t box = t / nw;
+  const int band = (int)(t % nw);
+  int c[3];
+  grid_coords(box, qb.nbox, c);
+  double mn = 1e300, mx = -1e300;
+  for (int x = c[0] * qb.B[0]; x < min(gm.nf[0], (c[0] + 1) * qb.B[0]); ++x)
+    for (int y = c[1] * qb.B[1]; y < min(gm.nf[1], (c[1] + 1) * qb.B[1]); ++y)
+      for (int z = c[2] * qb.B[2]; z < min(gm.nf[2], (c[2] + 1) * qb.B[2]); ++z) {
+        int f[3] = {x, y, z};
+        double e = epsF[grid_flat(f, gm.nf) * nw + band];
+        mn = fmin(mn, e);
+        mx = fmax(mx, e);
+      }
+  lo[t] = mn;
+  hi[t] = mx;
+}
+
+// flag[s][blk] = 1 if some band at some k+q, q in block blk, lies within reach of eps_n(s).
+__global__ void k_screen(const int* __restrict__ st_k, const int* __restrict__ st_b, int S,
+                         const double* __restrict__ epsF, GridMap gm, int nw, QBlocks qb,
+                         const double* __restrict__ lo, const double* __restrict__ hi, double reach,
+                         unsigned char* __restrict__ flag) {
+  const int nblk = qb.nb[0] * qb.nb[1] * qb.nb[2];
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)S * nblk) return;
+  const int s = (int)(t / nblk), blk = (int)(t % nblk);
+  int kc[3], bc[3];
+  grid_coords(st_k[s], gm.nk, kc);
+  grid_coords(blk, qb.nb, bc);
+  int kf[3];
+  for (int i = 0; i < 3; ++i) kf[i] = kc[i] * gm.sk[i];
+  const double e_n = epsF[grid_flat(kf, gm.nf) * nw + st_b[s]];
+  // per axis, the distinct boxes holding (k + q) of the block
+  int boxes[3][8], nbx[3];
+  for (int i = 0; i < 3; ++i) {
+    nbx[i] = 0;
+    const int q0 = bc[i] * qb.b[i], ext = min(qb.b[i], gm.nq[i] - q0);
+    for (int u = 0; u < ext && u < 8; ++u) {
+      const int f = (kf[i] + (q0 + u) * gm.sq[i]) % gm.nf[i];
+      const int bx = f / qb.B[i];
+      bool seen = false;
+      for (int v = 0; v < nbx[i]; ++v) seen |= boxes[i][v] == bx;
+      if (!seen) boxes[i][nbx[i]++] = bx;
+    }
+  }
+  unsigned char need = 0;
+  for (int a = 0; a < nbx[0] && !need; ++a)
+    for (int b = 0; b < nbx[1] && !need; ++b)
+      for (int c = 0; c < nbx[2] && !need; ++c) {
+        const int64_t box = ((int64_t)boxes[0][a] * qb.nbox[1] + boxes[1][b]) * qb.nbox[2] + boxes[2][c];
+        for (int m = 0; m < nw; ++m)
+          if (hi[box * nw + m] >= e_n - reach && lo[box * nw + m] <= e_n + reach) {
+            need = 1;
+            break;
+          }
+      }
+  flag[t] = need;
+}
+
+// Dense stage-2 tile t (grouped order) -> 1 if any of its states needs its q block.
+__global__ void k_tile_flags(const unsigned char* __restrict__ flag, int S, int nblk, int spt, int group_m,
+                             int m_tiles, int n_tiles, int* __restrict__ tflag) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)m_tiles * n_tiles) return;
+  int m, n;
+  dense_tile_coords(group_m, m_tiles, n_tiles, (int)t, m, n);
+  int need = 0;
+  for (int s = n * spt; s < min(S, n * spt + spt); ++s) need |= flag[(int64_t)s * nblk + m];
+  tflag[t] = need;
+}
+
+// Compacted tile list and the executed (q, state) pair count.
+__global__ void k_tile_write(const int* __restrict__ tflag, const int64_t* __restrict__ off, int S, int spt,
+                             int group_m, int m_tiles, int n_tiles, QBlocks qb, int nq0, int nq1, int nq2,
+                             int2* __restrict__ list, unsigned long long* __restrict__ pairs) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)m_tiles * n_tiles || !tflag[t]) return;
+  int m, n;
+  dense_tile_coords(group_m, m_tiles, n_tiles, (int)t, m, n);
+  list[off[t]] = make_int2(m, n);
+  int bc[3];
+  grid_coords(m, qb.nb, bc);
+  const int nqg[3] = {nq0, nq1, nq2};
+  int rows = 1;
+  for (int i = 0; i < 3; ++i) rows *= min(qb.b[i], nqg[i] - bc[i] * qb.b[i]);
+  const int states = min(S, n * spt + spt) - n * spt;
+  atomicAdd(pairs, (unsigned long long)rows * (unsigned long long)states);
+}
+
 // FP32 epilogue tables: conj-transposed U, Fermi factors, mode factors, omega, Bose factors.
-__global__ void k_tables_el(const cplx* __restrict__ UF, const double* __restrict__ fF, int64_t NF, int nw,
-                            float2* __restrict__ UH, float* __restrict__ f32) {
+__global__ void k_tables_el(const cplx* __restrict__ UF, const double* __restrict__ fF,
+                            const double* __restrict__ epsF, int64_t NF, int nw, float2* __restrict__ UH,
+                            float* __restrict__ f32, float2* __restrict__ eps2) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= NF * nw * nw) return;
   int64_t f = t / (nw * nw);
   int mp = (int)((t / nw) % nw), m = (int)(t % nw);
   cplx u = UF[(f * nw + m) * nw + mp];
   UH[t] = make_float2((float)u.re, (float)-u.im);
-  if (m == 0) f32[f * nw + mp] = (float)fF[f * nw + mp];
+  if (m == 0) {
+    f32[f * nw + mp] = (float)fF[f * nw + mp];
+    double e = epsF[f * nw + mp];
+    float hi = (float)e;
+    eps2[f * nw + mp] = make_float2(hi, (float)(e - (double)hi));
+  }
 }
 
 __global__ void k_tables_ph(const cplx* __restrict__ Z, const double* __restrict__ om, const double* __restrict__ nB,
@@ -611,6 +855,36 @@ __global__ void k_tables_ph(const cplx* __restrict__ Z, const double* __restrict
 
 
 // max over |x_i| of a double array -> *out (bits of a non-negative double, atomicMax-ordered)
+// Mode factors, energies and Bose factors in stage-2 A-row order (padding rows zero).
+__global__ void k_tables_ph_rows(const cplx* __restrict__ Z, const double* __restrict__ om,
+                                 const double* __restrict__ nB, const int* __restrict__ q_of_row, int64_t rows,
+                                 int nm, float2* __restrict__ Zr, float* __restrict__ omr, float* __restrict__ nBr) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= rows * nm * nm) return;
+  const int64_t r = t / (nm * nm);
+  const int e = (int)(t % (nm * nm));
+  const int q = q_of_row[r];
+  cplx z = q >= 0 ? Z[(int64_t)q * nm * nm + e] : cplx{0.0, 0.0};
+  Zr[t] = make_float2((float)z.re, (float)z.im);
+  if (e < nm) {
+    omr[r * nm + e] = q >= 0 ? (float)om[(int64_t)q * nm + e] : 0.f;
+    nBr[r * nm + e] = q >= 0 ? (float)nB[(int64_t)q * nm + e] : 0.f;
+  }
+}
+
+// Per batch state: k on the fine grid, band, and the initial-state energy.
+__global__ void k_state_info(const int* __restrict__ st_k, const int* __restrict__ st_b, int S, GridMap gm,
+                             const double* __restrict__ epsF, int nw, int4* __restrict__ sinfo,
+                             double* __restrict__ eps_n) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  int kc[3];
+  grid_coords(st_k[s], gm.nk, kc);
+  int f[3] = {kc[0] * gm.sk[0], kc[1] * gm.sk[1], kc[2] * gm.sk[2]};
+  sinfo[s] = make_int4(f[0], f[1], f[2], st_b[s]);
+  eps_n[s] = epsF[grid_flat(f, gm.nf) * nw + st_b[s]];
+}
+
 __global__ void k_absmax_f64(const double* __restrict__ x, int64_t n, unsigned long long* __restrict__ out) {
   __shared__ double red[256];
   double m = 0.0;
@@ -665,21 +939,45 @@ static int make_tmap(phoebe_gpu_ctx* c, CUtensorMap* tm, const void* base, int f
 }
 
 static int stage_bytes(int BN, int nsplit) { return nsplit * (16384 + BN * 128); }
-static int pick_stages(int BN, int nsplit) {
-  int st = (227 * 1024 - 1024 - 512) / stage_bytes(BN, nsplit);
+static int pick_stages(int BN, int nsplit, int extra) {
+  int st = (227 * 1024 - 1024 - 512 - extra) / stage_bytes(BN, nsplit);
   return std::max(1, std::min(st, 8));
 }
 
+constexpr int kClusterN = 1;  // CTAs sharing each A tile through TMA multicast (1: off)
+
+// a.n_tiles on entry: n tiles of the problem; padded to whole clusters here.
 template <class Epi, int FMT, int NSPLIT, int NPROD>
 static int launch_gemm(phoebe_gpu_ctx* c, const CUtensorMap* A, const CUtensorMap* B, TcGemmArgs a,
                        const typename Epi::Params& ep) {
-  auto kern = k_tc_gemm<Epi, FMT, NSPLIT, NPROD>;
-  a.stages = pick_stages(Epi::BN, NSPLIT);
-  int sm = a.stages * stage_bytes(Epi::BN, NSPLIT) + 1024 + 512;
+  constexpr int CN = kClusterN;
+  auto kern = k_tc_gemm<Epi, FMT, NSPLIT, NPROD, CN>;
+  a.stages = pick_stages(Epi::BN, NSPLIT, (int)((Epi::SMEM_BYTES + 1023u) & ~1023u));
+  a.kb_per_chunk = std::max(1, std::min(a.kb_per_chunk, a.stages));  // a chunk must fit in the smem ring
+  a.n_tiles = (a.n_tiles + CN - 1) / CN;                              // cluster-level n groups
+  a.group_m = std::min(a.group_m, a.m_tiles);
+  a.ntiles = a.m_tiles * a.n_tiles;
+  int sm = a.stages * stage_bytes(Epi::BN, NSPLIT) + (int)((Epi::SMEM_BYTES + 1023u) & ~1023u) + 1024 + 512;
   CK(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  int grid = std::min(a.ntiles, c->num_sms > 0 ? c->num_sms : 148);
-  if (grid <= 0) return PHOEBE_GPU_OK;
-  kern<<<grid, kTcThreads, sm, c->stream>>>(A[0], A[1], A[2], B[0], B[1], B[2], a, ep);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CN;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(kTcThreads, 1, 1);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = c->stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3((unsigned)((c->num_sms > 0 ? c->num_sms : 148) / CN * CN), 1, 1);
+  int max_clusters = 0;
+  CK(c, cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg));
+  if (max_clusters <= 0) return fail(c, PHOEBE_GPU_ERR_CUDA, "no %d-CTA cluster of this kernel fits on the GPU", CN);
+  int clusters = std::min(max_clusters, a.ntiles);
+  if (clusters <= 0) return PHOEBE_GPU_OK;
+  cfg.gridDim = dim3((unsigned)(clusters * CN), 1, 1);
+  CK(c, cudaLaunchKernelEx(&cfg, kern, A[0], A[1], A[2], B[0], B[1], B[2], a, ep));
   c->launches++;
   CK(c, cudaGetLastError());
   return PHOEBE_GPU_OK;
@@ -780,49 +1078,105 @@ static int run_tc_typed(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const
   if (!UH) return st;
   float* f32 = (float*)ensure(c, "tc_f32", sizeof(float) * NF * nw, &st);
   if (!f32) return st;
-  float2* Zf = (float2*)ensure(c, "tc_Z", sizeof(float2) * Nq * nm * nm, &st);
-  if (!Zf) return st;
-  float* omf = (float*)ensure(c, "tc_om", sizeof(float) * Nq * nm, &st);
-  if (!omf) return st;
-  float* nBf = (float*)ensure(c, "tc_nB", sizeof(float) * Nq * nm, &st);
-  if (!nBf) return st;
+  float2* eps2 = (float2*)ensure(c, "tc_eps2", sizeof(float2) * NF * nw, &st);
+  if (!eps2) return st;
   unsigned long long* dmax = (unsigned long long*)ensure(c, "tc_max", 64, &st);
   if (!dmax) return st;
-  k_tables_el<<<(unsigned)((NF * nw * nw + 255) / 256), 256, 0, c->stream>>>(UF, fF, NF, nw, UH, f32);
-  k_tables_ph<<<(unsigned)((Nq * nm * nm + 255) / 256), 256, 0, c->stream>>>(Zq, omega, nB, Nq, nm, Zf, omf, nBf);
+  k_tables_el<<<(unsigned)((NF * nw * nw + 255) / 256), 256, 0, c->stream>>>(UF, fF, epsF, NF, nw, UH, f32,
+                                                                             eps2);
   CK(c, cudaMemsetAsync(dmax, 0, 64, c->stream));
   k_absmax_f64<<<64, 256, 0, c->stream>>>(omega, Nq * nm, dmax);
-  c->launches += 3;
+  c->launches += 2;
   CK(c, cudaGetLastError());
   unsigned long long ombits = 0;
   CK(c, cudaMemcpyAsync(&ombits, dmax, sizeof(ombits), cudaMemcpyDeviceToHost, c->stream));
 
-  // stage-2 A operand: q phases
+  // stage-2 A operand: q phases, rows in compact q blocks padded to 128
   GridPhase gq = make_phase(gm.nq), gk = make_phase(gm.nk);
   cplx *cis_q, *cis_k;
   TRY(cis_table(c, gq, "cis_q", &cis_q));
   TRY(cis_table(c, gk, "cis_k", &cis_k));
-  Parts PAq;
-  TRY(ensure_parts(c, "tc_Aq", NSPLIT, (size_t)Nq * Kp2, esz, &PAq));
+  QBlocks qb;
   {
-    int64_t nt = Nq * (Kp2 / 2);
+    const int shape[3] = {4, 4, 8};
+    for (int i = 0; i < 3; ++i) {
+      qb.b[i] = std::min(shape[i], gm.nq[i]);
+      qb.nb[i] = (gm.nq[i] + qb.b[i] - 1) / qb.b[i];
+      qb.B[i] = qb.b[i] * gm.sq[i];
+      qb.nbox[i] = (gm.nf[i] + qb.B[i] - 1) / qb.B[i];
+    }
+  }
+  const int nblk = qb.nb[0] * qb.nb[1] * qb.nb[2];
+  const int64_t Mrows = (int64_t)nblk * 128;
+  {
+    std::vector<int> q_of_row((size_t)Mrows, -1);
+    std::vector<int4> qinfo((size_t)Mrows, make_int4(0, 0, 0, -1));
+    for (int blk = 0; blk < nblk; ++blk) {
+      int bc[3];
+      grid_coords(blk, qb.nb, bc);
+      int r = 0;
+      for (int x = 0; x < qb.b[0]; ++x)
+        for (int y = 0; y < qb.b[1]; ++y)
+          for (int z = 0; z < qb.b[2]; ++z, ++r) {
+            int qc3[3] = {bc[0] * qb.b[0] + x, bc[1] * qb.b[1] + y, bc[2] * qb.b[2] + z};
+            if (qc3[0] < gm.nq[0] && qc3[1] < gm.nq[1] && qc3[2] < gm.nq[2]) {
+              const int q = (int)grid_flat(qc3, gm.nq);
+              q_of_row[(size_t)blk * 128 + r] = q;
+              qinfo[(size_t)blk * 128 + r] =
+                  make_int4(qc3[0] * gm.sq[0], qc3[1] * gm.sq[1], qc3[2] * gm.sq[2], q);
+            }
+          }
+    }
+    void* d;
+    TRY(upload(c, "tc_q_of_row", q_of_row.data(), sizeof(int) * Mrows, &d));
+    TRY(upload(c, "tc_qinfo", qinfo.data(), sizeof(int4) * Mrows, &d));
+  }
+  const int* q_of_row_d = (const int*)c->bufs["tc_q_of_row"].p;
+  const int4* qinfo_d = (const int4*)c->bufs["tc_qinfo"].p;
+  float2* Zr = (float2*)ensure(c, "tc_Zr", sizeof(float2) * Mrows * nm * nm, &st);
+  if (!Zr) return st;
+  float* omr = (float*)ensure(c, "tc_omr", sizeof(float) * Mrows * nm, &st);
+  if (!omr) return st;
+  float* nBr = (float*)ensure(c, "tc_nBr", sizeof(float) * Mrows * nm, &st);
+  if (!nBr) return st;
+  k_tables_ph_rows<<<(unsigned)((Mrows * nm * nm + 255) / 256), 256, 0, c->stream>>>(Zq, omega, nB, q_of_row_d, Mrows,
+                                                                                     nm, Zr, omr, nBr);
+  c->launches++;
+  CK(c, cudaGetLastError());
+  Parts PAq;
+  TRY(ensure_parts(c, "tc_Aq", NSPLIT, (size_t)Mrows * Kp2, esz, &PAq));
+  {
+    int64_t nt = Mrows * (Kp2 / 2);
     k_pack_phase<FMT, NSPLIT><<<(unsigned)((nt + 255) / 256), 256, 0, c->stream>>>(
-        nullptr, Nq, (const int*)c->bufs["Rp"].p, (const double*)c->bufs["wp"].p, nRp, gq, cis_q, Kp2, sA2, PAq);
+        q_of_row_d, Mrows, (const int*)c->bufs["Rp"].p, (const double*)c->bufs["wp"].p, nRp, gq, cis_q, Kp2, sA2, PAq);
     c->launches++;
     CK(c, cudaGetLastError());
   }
+  // band-energy bounds of the F-grid boxes matching the q blocks
+  const int64_t nbox = (int64_t)qb.nbox[0] * qb.nbox[1] * qb.nbox[2];
+  double* box_lo = (double*)ensure(c, "tc_box_lo", sizeof(double) * nbox * nw, &st);
+  if (!box_lo) return st;
+  double* box_hi = (double*)ensure(c, "tc_box_hi", sizeof(double) * nbox * nw, &st);
+  if (!box_hi) return st;
+  k_box_bounds<<<(unsigned)((nbox * nw + 127) / 128), 128, 0, c->stream>>>(epsF, gm, nw, qb, box_lo, box_hi);
+  unsigned long long* exec_pairs = (unsigned long long*)ensure(c, "tc_exec_pairs", 64, &st);
+  if (!exec_pairs) return st;
+  CK(c, cudaMemsetAsync(exec_pairs, 0, 64, c->stream));
+  c->launches++;
+  CK(c, cudaGetLastError());
   CK(c, cudaStreamSynchronize(c->stream));
   double omega_max;
   memcpy(&omega_max, &ombits, sizeof(double));
+  const double reach = omega_max + p->delta_cut_sigmas * p->sigma_eV;
   tm.end(c, &c->stats.stage1_ms);
   CUtensorMap tAq[3];
-  TRY(part_maps(c, tAq, PAq, NSPLIT, FMT, Kp2, Nq, 128));
+  TRY(part_maps(c, tAq, PAq, NSPLIT, FMT, Kp2, Mrows, 128 / kClusterN));
 
   // stage-2 tiling: whole states per n tile
   using EE = ElphEpi<NW, NM>;
   const int cps = EE::CPS, spt = EE::SPT;
   const int BN1 = StoreEpi::BN, BN2 = EE::BN;
-  const int kb_chunk = 2;
+  const int kb_chunk = PHX_KB_PER_CHUNK;
   unsigned* tmaxp = (unsigned*)ensure(c, "tc_tmax", 64, &st);
   if (!tmaxp) return st;
 
@@ -865,7 +1219,7 @@ static int run_tc_typed(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const
       CK(c, cudaGetLastError());
     }
     CUtensorMap tAk[3], tG[3];
-    TRY(part_maps(c, tAk, PAk, NSPLIT, FMT, Kp1, nkb, 128));
+    TRY(part_maps(c, tAk, PAk, NSPLIT, FMT, Kp1, nkb, 128 / kClusterN));
     TRY(part_maps(c, tG, Pg, NSPLIT, FMT, Kp1, 2 * C, BN1));
     {
       TcGemmArgs a;
@@ -876,6 +1230,8 @@ static int run_tc_typed(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const
       a.b_row_step = BN1;
       a.group_m = std::max(1, a.m_tiles);
       a.ntiles = a.m_tiles * a.n_tiles;
+      a.tile_list = nullptr;
+      a.ntiles_dev = nullptr;
       a.err = err;
       StoreEpi::Params ep{X, 2 * C, nkb, (int)(2 * C)};
       TRY(launch_gemm<StoreEpi, FMT, NSPLIT, NPROD>(c, tAk, tG, a, ep));
@@ -899,34 +1255,69 @@ static int run_tc_typed(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const
     }
     tm.end(c, &c->stats.stage1_ms);
 
-    // ---- stage 2 with the fused el-ph epilogue
+    // ---- screening: (q block, state) pairs that can contribute, compacted into a tile list
+    tm.begin(c);
+    const int n_tiles2 = (S + spt - 1) / spt;
+    const int group_m2 = std::min(nblk, 64);
+    const int64_t dense = (int64_t)nblk * n_tiles2;
+    unsigned char* flag = (unsigned char*)ensure(c, "tc_flag", (size_t)S * nblk, &st);
+    if (!flag) return st;
+    int* tflag = (int*)ensure(c, "tc_tflag", sizeof(int) * dense, &st);
+    if (!tflag) return st;
+    int64_t* toff = (int64_t*)ensure(c, "tc_toff", sizeof(int64_t) * (dense + 1), &st);
+    if (!toff) return st;
+    int2* tlist = (int2*)ensure(c, "tc_tlist", sizeof(int2) * dense, &st);
+    if (!tlist) return st;
+    k_screen<<<(unsigned)(((int64_t)S * nblk + 127) / 128), 128, 0, c->stream>>>(
+        st_k + i0, st_b + i0, S, epsF, gm, nw, qb, box_lo, box_hi, reach, flag);
+    k_tile_flags<<<(unsigned)((dense + 255) / 256), 256, 0, c->stream>>>(flag, S, nblk, spt, group_m2, nblk,
+                                                                           n_tiles2, tflag);
+    k_scan_single_block<<<1, 1024, 0, c->stream>>>(tflag, dense, toff);
+    k_tile_write<<<(unsigned)((dense + 255) / 256), 256, 0, c->stream>>>(
+        tflag, toff, S, spt, group_m2, nblk, n_tiles2, qb, gm.nq[0], gm.nq[1], gm.nq[2], tlist, exec_pairs);
+    c->launches += 4;
+    CK(c, cudaGetLastError());
+    tm.end(c, &c->stats.window_ms);
+
+    int4* sinfo = (int4*)ensure(c, "tc_sinfo", sizeof(int4) * S, &st);
+    if (!sinfo) return st;
+    double* seps = (double*)ensure(c, "tc_seps", sizeof(double) * S, &st);
+    if (!seps) return st;
+    k_state_info<<<(S + 127) / 128, 128, 0, c->stream>>>(st_k + i0, st_b + i0, S, gm, epsF, nw, sinfo, seps);
+    c->launches++;
+    CK(c, cudaGetLastError());
+
+    // ---- stage 2 with the fused el-ph epilogue over the screened tiles
     CUtensorMap tB[3];
     TRY(part_maps(c, tB, PB, NSPLIT, FMT, Kp2, rows2, BN2));
     tm.begin(c);
     {
       TcGemmArgs a;
-      a.m_tiles = (int)((Nq + 127) / 128);
-      a.n_tiles = (S + spt - 1) / spt;
+      a.m_tiles = nblk;
+      a.n_tiles = n_tiles2;
       a.kblocks = Kp2 / KB;
       a.kb_per_chunk = kb_chunk;
       a.b_row_step = spt * cps;
-      a.group_m = std::min(a.m_tiles, 64);
-      a.ntiles = a.m_tiles * a.n_tiles;
+      a.group_m = group_m2;
+      a.ntiles = (int)dense;
+      a.tile_list = tlist;
+      a.ntiles_dev = toff + dense;
       a.err = err;
       typename EE::Params ep;
-      ep.Mq = (int)Nq;
+      ep.Mq = (int)Mrows;
       ep.S = S;
-      ep.st_k = st_k + i0;
-      ep.st_b = st_b + i0;
+      ep.sinfo = sinfo;
+      ep.eps_n = seps;
       ep.s_base = i0;
       ep.gm = gm;
-      ep.epsF = epsF;
+      ep.qinfo = qinfo_d;
+      ep.eps2 = eps2;
       ep.fF = f32;
       ep.UH = UH;
-      ep.Z = Zf;
-      ep.om = omf;
-      ep.nB = nBf;
-      ep.reach = omega_max + p->delta_cut_sigmas * p->sigma_eV;
+      ep.Zr = Zr;
+      ep.omr = omr;
+      ep.nBr = nBr;
+      ep.reach = (float)reach * 1.0001f;
       ep.inv_sigma = (float)(1.0 / p->sigma_eV);
       ep.cut2 = (float)(p->delta_cut_sigmas * p->delta_cut_sigmas);
       ep.scale_base = (2.0 * kPi / (double)Nq) / (kSqrtPi * p->sigma_eV) / ((double)sA2 * (double)sA2);
@@ -942,8 +1333,11 @@ static int run_tc_typed(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const
   CK(c, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   if (herr) return fail(c, PHOEBE_GPU_ERR_TIMEOUT, "a tensor-core pipeline wait ran out; results discarded");
-  c->stats.pairs_executed = ns * Nq;
-  c->stats.stage2_flops = 8.0 * (double)Nq * nRp * (double)ns * nw * nm;
+  unsigned long long executed = 0;
+  CK(c, cudaMemcpyAsync(&executed, exec_pairs, sizeof(executed), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->stats.pairs_executed = (int64_t)executed;
+  c->stats.stage2_flops = 8.0 * (double)executed * nRp * nw * nm;  // executed algorithmic flops
   return PHOEBE_GPU_OK;
 }
 
