@@ -422,8 +422,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           tc_fence_after();
           const uint32_t d_tmem = tmem_base + pb * (uint32_t)BN;
           const int kb0 = ch * a.kb_per_chunk, kb1 = min(a.kblocks, kb0 + a.kb_per_chunk);
-          // smem slots of this chunk: wait for all of them, corrections first, then hi*hi
-          uint32_t it0 = it;
+          // per K block: its small cross products first, then the dominant hi*hi, then release its slot
+          uint32_t first = 1;  // the chunk's first MMA starts the partial from zero
           for (int kb = kb0; kb < kb1; ++kb, ++it) {
             const int s = (int)(it % (uint32_t)a.stages);
             const uint32_t ph = (it / (uint32_t)a.stages) & 1u;
@@ -431,16 +431,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               ok = false;
               break;
             }
-          }
-          if (!ok) break;
-          tc_fence_after();
-          uint32_t first = 1;
+            tc_fence_after();
+            const uint32_t abase = smem_u32(smem + (size_t)s * STAGE);
+            const uint32_t bbase = abase + NSPLIT * kTileABytes;
 #pragma unroll
-          for (int pass = 0; pass < 2; ++pass) {  // pass 0: corrections, pass 1: dominant product
-            for (uint32_t i2 = it0; i2 < it; ++i2) {
-              const int s = (int)(i2 % (uint32_t)a.stages);
-              const uint32_t abase = smem_u32(smem + (size_t)s * STAGE);
-              const uint32_t bbase = abase + NSPLIT * kTileABytes;
+            for (int pass = 0; pass < 2; ++pass) {  // pass 0: corrections, pass 1: dominant product
 #pragma unroll
               for (int pr = 0; pr < NPROD; ++pr) {
                 if ((pass == 0) == (pr == 0)) continue;
@@ -454,13 +449,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
               }
             }
-          }
-          for (uint32_t i2 = it0; i2 < it; ++i2) {
             if (CN > 1)
-              mma_commit_mc(empty + (int)(i2 % (uint32_t)a.stages), kMask);
+              mma_commit_mc(empty + s, kMask);
             else
-              mma_commit(empty + (int)(i2 % (uint32_t)a.stages));
+              mma_commit(empty + s);
           }
+          if (!ok) break;
           mma_commit(pf);
         }
       }
@@ -513,12 +507,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tc_fence_after();
         const uint32_t taddr =
             tmem_base + ((uint32_t)(quarter * 32) << 16) + pb * (uint32_t)BN + (uint32_t)(wg * BNW);
+        if constexpr (BNW % 32 == 0) {
 #pragma unroll
-        for (int c0 = 0; c0 < BNW; c0 += 16) {
-          float v[16];
-          tmem_ld16(taddr + c0, v);
+          for (int c0 = 0; c0 < BNW; c0 += 32) {
+            float v[32];
+            tmem_ld32(taddr + c0, v);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) acc[c0 + i] += v[i];
+            for (int i = 0; i < 32; ++i) acc[c0 + i] += v[i];
+          }
+        } else {
+#pragma unroll
+          for (int c0 = 0; c0 < BNW; c0 += 16) {
+            float v[16];
+            tmem_ld16(taddr + c0, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[c0 + i] += v[i];
+          }
         }
         tc_fence_before();
         mbar_arrive(pempty + pb);
