@@ -35,7 +35,7 @@ __all__ = [
     "bose_einstein", "fermi_dirac", "gaussian_delta",
     "coupling_wannier_direct", "coupling_stage1", "coupling_stage2",
     "rotate_final", "bloch_coupling", "couplings_for_pairs",
-    "active_states", "fine_grid", "electron_table", "linewidths_rta",
+    "active_states", "fine_grid", "electron_table", "linewidths_rta", "contributions",
 ]
 
 
@@ -366,4 +366,54 @@ def linewidths_rta(mat, params, k_indices=None, direct: bool = False, return_raw
             out[j] = raw[grp].mean()
     if return_raw:
         return ks, bs, out, raw
+    return ks, bs, out
+
+
+def contributions(mat, params, k_indices=None, q_indices=None, table=None):
+    """Per-q terms of Eq. 29: c_nk(q) with Gamma_nk(before degenerate averaging) = (1/N_q) sum_q c_nk(q).
+
+    c_nk(q) = 2 pi sum_{m' nu} |g_{m' n nu}(k,q)|^2
+              [ (n_q nu + 1 - f_{m',k+q}) delta(eps_nk - hbar w_q nu - eps_{m',k+q})
+              + (n_q nu + f_{m',k+q})     delta(eps_nk + hbar w_q nu - eps_{m',k+q}) ]
+    (Sec. 4.2 Eq. 29, Sec. 4.7 Eq. 61), with the readings of ``linewidths_rta``.
+    These are the per-q weights an importance sampler over q needs: both the
+    training targets of a learned proposal and the samples of its estimate.
+
+    ``q_indices``: None (every q of the grid, result (n_states, N_q)) or an
+    integer array (n_states, S) of q-grid indices per state (result (n_states, S)).
+    Returns (k_index, band, c).
+    """
+    nk = tuple(int(x) for x in params.nk)
+    nq = tuple(int(x) for x in params.nq)
+    qpts = grid_points(nq)
+    kpts = grid_points(nk)
+    T, mu, sigma = params.T_K, params.mu_eV, params.sigma_eV
+    cut = params.delta_cut_sigmas
+    F, eps_F, U_F, k_to_F = table if table is not None else electron_table(mat, params)
+    eps_grid = eps_F[k_to_F]
+    ks, bs = active_states(eps_grid, mu, params.window_eV)
+    if k_indices is not None:
+        keep = np.isin(ks, np.asarray(k_indices))
+        ks, bs = ks[keep], bs[keep]
+    omega, z = phonon_modes(qpts, mat)
+    Zq = mode_factors(omega, z, mat.mass_amu, params.omega_cut_eV)
+    nB = bose_einstein(omega, T)
+    alive = omega >= params.omega_cut_eV
+    width = len(qpts) if q_indices is None else np.asarray(q_indices).shape[1]
+    out = np.zeros((len(ks), width))
+    for j, (ik, b) in enumerate(zip(ks, bs)):
+        qi = np.arange(len(qpts)) if q_indices is None else np.asarray(q_indices[j], dtype=np.int64)
+        k = kpts[ik]
+        U_k = U_F[k_to_F[ik]]
+        kq = grid_index(k[None, :] + qpts[qi], F)
+        eps_kq, U_kq = eps_F[kq], U_F[kq]
+        f_kq = fermi_dirac(eps_kq, mu, T)
+        G = coupling_stage2(coupling_stage1(k, mat, U_k[:, [b]]), qpts[qi], mat)   # (S, m, 1, s)
+        g2 = np.abs(rotate_final(G, U_kq, Zq[qi]))[:, :, 0, :] ** 2                # (S, m', nu)
+        e = eps_grid[ik, b]
+        om, nb_ = omega[qi][:, None, :], nB[qi][:, None, :]
+        w = ((nb_ + 1.0 - f_kq[:, :, None]) * gaussian_delta(e - om - eps_kq[:, :, None], sigma, cut)
+             + (nb_ + f_kq[:, :, None]) * gaussian_delta(e + om - eps_kq[:, :, None], sigma, cut))
+        w = np.where(alive[qi][:, None, :], w, 0.0)
+        out[j] = 2.0 * np.pi * np.sum(g2 * w, axis=(1, 2))
     return ks, bs, out
