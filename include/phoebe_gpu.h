@@ -129,10 +129,23 @@ typedef struct {
   int n_k_subset;            /* > 0: restrict initial k points to k_subset (host, ascending, unique) */
   const int32_t* k_subset;   /*       k-grid indices (i1*N2+i2)*N3+i3 */
   int max_batch_states;      /* states per stage-1/stage-2 batch, 0 = automatic */
-  int reserved[8];           /* must be zero */
+  int sampler;               /* phoebe_gpu_sampler: how the q sum of Eq. 29 is evaluated (default full) */
+  double sample_fraction;    /* sampler LEARNED/UNIFORM: draws per initial k = ceil(fraction * N_q),
+                                0 < fraction <= 1 (default 0.05) */
+  double mix_alpha;          /* sampler LEARNED: weight of the uniform part of the proposal,
+                                0 < alpha <= 1 (default 0.1) */
+  uint64_t seed;             /* sampler LEARNED/UNIFORM: key of the Philox4x32-10 draws */
+  int reserved[4];           /* must be zero */
 } phoebe_gpu_rta_params;
 
-/* Fill *p with the defaults (cut 6 sigma, omega_cut 1e-4, degen 1e-6, FP64, T=300). */
+typedef enum {
+  PHOEBE_SAMPLER_FULL = 0,     /* every q of the grid (the paper's sum) */
+  PHOEBE_SAMPLER_LEARNED = 1,  /* importance sampling from the learned proposal (see below) */
+  PHOEBE_SAMPLER_UNIFORM = 2   /* importance sampling from the uniform proposal */
+} phoebe_gpu_sampler;
+
+/* Fill *p with the defaults (cut 6 sigma, omega_cut 1e-4, degen 1e-6, FP64, T=300, full q sum,
+ * sample fraction 0.05, alpha 0.1, seed 0). */
 void phoebe_gpu_rta_params_default(phoebe_gpu_rta_params* p);
 
 /* RTA linewidths of all active (k, n) states on the k grid (Sec. 4.2 Eq. 29):
@@ -167,6 +180,7 @@ typedef struct {
   double stage2_flops;         /* algorithmic real flops of the R_p contraction (8 per cMAC) */
   double stage2_ms;            /* event-timed device time of the R_p contraction launches */
   double bands_ms, phonons_ms, window_ms, stage1_ms, rotate_ms, delta_ms, total_ms;
+  double sampler_ms;           /* sampled q sums: network scores, proposal and draws */
 } phoebe_gpu_stats;
 
 /* Turn per-stage event timing on (1) or off (0, default). */
@@ -175,6 +189,71 @@ int phoebe_gpu_get_stats(const phoebe_gpu_ctx* ctx, phoebe_gpu_stats* out);
 
 /* Cap on the context's device memory (bytes, 0 = none); exceeding it returns ERR_NOMEM. */
 int phoebe_gpu_set_memory_cap(phoebe_gpu_ctx* ctx, int64_t bytes);
+
+/* ------------------------------------------------------------------------------------------
+ * Importance-sampled q sums with a learned proposal.  The paper has no counterpart: Eq. 29
+ * sums every q of the grid.  Write c_nk(q) for N_q times the q term of Eq. 29, so that
+ * Gamma_nk = (1/N_q) sum_q c_nk(q).  With params->sampler = PHOEBE_SAMPLER_LEARNED,
+ * linewidths_rta draws, per initial k, S = ceil(sample_fraction * N_q) q points i.i.d. from
+ *     p_k(q) = (1 - alpha) mean_{n active at k} softmax_q z_nk(q) + alpha / N_q
+ * (inverse CDF in q-index order, FP64, Philox4x32-10 uniforms: draw j of k-grid index k uses
+ * counter (j, k, 0x4953, 0), key (seed low word, seed high word), u = ((x1 << 32 | x0) >> 11) 2^-53)
+ * and returns the unbiased estimate
+ *     Gamma^_nk = (1/S) sum_j c_nk(q_j) / (N_q p_k(q_j)),
+ * then averages degenerate bands as the full sum does.  PHOEBE_SAMPLER_UNIFORM uses
+ * p_k = 1/N_q (no network).  Both need a tensor-core precision (1..6) and (nw, 3na) in
+ * {(8,6), (2,3), (1,3)} with N_Rp * 3na * nw * 8 bytes <= 200 KB.
+ * The network z = MLP(x), x = (q~, eps_nk - mu, v_nk): q~ is q wrapped into [-1/2, 1/2) per
+ * axis, v_nk = <n| sum_R w_R i R e^{ik.R} H(R) |n> = (1/2 pi) d eps_nk / dk (eV, crystal axes);
+ * 7 -> 128 -> 128 -> 128 -> 1 with SiLU after each hidden layer.  The context keeps FP32
+ * master parameters; every evaluation uses them rounded to BF16 (ties to even), with FP32
+ * activations and accumulation.  Parameter blob (float32, PHOEBE_GPU_MLP_NPARAM numbers):
+ *     W1[128][7], b1[128], W2[128][128], b2[128], W3[128][128], b3[128], w4[128], b4.
+ * ------------------------------------------------------------------------------------------ */
+#define PHOEBE_GPU_MLP_NPARAM 34177
+
+/* Seeded initialisation: weights uniform in +-1/sqrt(fan_in), biases 0; resets the optimiser. */
+int phoebe_gpu_sampler_init(phoebe_gpu_ctx* ctx, uint64_t seed);
+/* Set / read the FP32 master parameters (host blob of n = PHOEBE_GPU_MLP_NPARAM floats). */
+int phoebe_gpu_sampler_load(phoebe_gpu_ctx* ctx, const float* params, int64_t n);
+int phoebe_gpu_sampler_save(phoebe_gpu_ctx* ctx, float* params, int64_t n);
+
+typedef struct {
+  int epochs;                /* passes over the training states (default 20) */
+  int states_per_step;       /* states per Adam step (default 16) */
+  double lr, beta1, beta2, eps;  /* Adam (defaults 2e-3, 0.9, 0.999, 1e-8) */
+  uint64_t seed;             /* order of the states in each epoch */
+  int reserved[4];           /* must be zero */
+} phoebe_gpu_train_opts;
+void phoebe_gpu_train_opts_default(phoebe_gpu_train_opts* o);
+
+/* Train the network on one full-grid run: computes c_nk(q) for every active state of `grid`
+ * (its sampler field is ignored; its precision must be 1..6) and minimises, with Adam, the
+ * mean over states of the cross entropy between t(q) = c_nk(q) / sum_q c_nk(q) and
+ * softmax_q z_nk(q).  States with sum_q c = 0 are skipped.  loss_per_epoch (host, `epochs`
+ * doubles, may be NULL) receives the mean loss of each epoch.  Needs init or load first. */
+int phoebe_gpu_sampler_train(phoebe_gpu_ctx* ctx, const phoebe_gpu_rta_params* grid,
+                             const phoebe_gpu_train_opts* opts, double* loss_per_epoch);
+
+/* c_nk(q) for every active state and every q (host float [n_states][N_q], q in grid-index order)
+ * and the state features (host float [n_states][4]: eps - mu, v[3]; may be NULL).  Two-call
+ * pattern as linewidths_rta; precision must be 1..6. */
+int phoebe_gpu_q_contributions(phoebe_gpu_ctx* ctx, const phoebe_gpu_rta_params* params, int* n_states,
+                               int32_t* k_index, int32_t* band, float* c, float* features);
+
+/* The network and its training loss on explicit rows, for checking the kernels.
+ *   x       host float [n_rows][7]
+ *   group_off  host int64 [n_groups + 1] row offsets of the softmax groups (0 = first, n_rows = last)
+ *   target  host float [n_rows] non-negative, or NULL (then only logits are computed)
+ *   logits  host float [n_rows] or NULL
+ *   loss    mean over groups of -sum t log softmax(z), t = target / its group sum (or NULL)
+ *   grad    host float [PHOEBE_GPU_MLP_NPARAM] dloss/dparameters at the BF16-rounded values (or NULL) */
+int phoebe_gpu_mlp_loss_grad(phoebe_gpu_ctx* ctx, int64_t n_rows, const float* x, int n_groups,
+                             const int64_t* group_off, const float* target, float* logits, double* loss,
+                             float* grad);
+
+/* The uniforms u_j, j < n, of the draws for k-grid index k (as described above), host double [n]. */
+int phoebe_gpu_is_uniforms(phoebe_gpu_ctx* ctx, uint64_t seed, int32_t k, int64_t n, double* u);
 
 /* Allocation-free band energies at explicit k points.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory -- host

@@ -21,6 +21,8 @@ STATUS = {
     -6: "ERR_CUDA", -7: "ERR_TIMEOUT", -8: "ERR_NOTCONVERGED", -9: "ERR_UNSUPPORTED",
 }
 PREC_FP64, PREC_SPLIT_BF16, PREC_SPLIT_TF32, PREC_BF16, PREC_TF32, PREC_SPLIT_FP16, PREC_BF16X3 = 0, 1, 2, 3, 4, 5, 6
+SAMPLER_FULL, SAMPLER_LEARNED, SAMPLER_UNIFORM = 0, 1, 2
+MLP_NPARAM = 34177
 
 # symbols declared in include/phoebe_gpu.h
 EXPORTED = (
@@ -30,6 +32,9 @@ EXPORTED = (
     "phoebe_gpu_linewidths_rta", "phoebe_gpu_linewidths_rta_dev",
     "phoebe_gpu_set_profiling", "phoebe_gpu_get_stats", "phoebe_gpu_set_memory_cap",
     "phoebe_gpu_constants", "phoebe_gpu_version", "phoebe_gpu_bands_noalloc",
+    "phoebe_gpu_sampler_init", "phoebe_gpu_sampler_load", "phoebe_gpu_sampler_save",
+    "phoebe_gpu_train_opts_default", "phoebe_gpu_sampler_train", "phoebe_gpu_q_contributions",
+    "phoebe_gpu_mlp_loss_grad", "phoebe_gpu_is_uniforms",
 )
 
 
@@ -48,7 +53,18 @@ class RTAParams(C.Structure):
         ("precision", C.c_int),
         ("n_k_subset", C.c_int), ("k_subset", C.POINTER(C.c_int32)),
         ("max_batch_states", C.c_int),
-        ("reserved", C.c_int * 8),
+        ("sampler", C.c_int),
+        ("sample_fraction", C.c_double), ("mix_alpha", C.c_double), ("seed", C.c_uint64),
+        ("reserved", C.c_int * 4),
+    ]
+
+
+class TrainOpts(C.Structure):
+    _fields_ = [
+        ("epochs", C.c_int), ("states_per_step", C.c_int),
+        ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
+        ("seed", C.c_uint64),
+        ("reserved", C.c_int * 4),
     ]
 
 
@@ -61,7 +77,7 @@ class Stats(C.Structure):
         ("stage2_flops", C.c_double), ("stage2_ms", C.c_double),
         ("bands_ms", C.c_double), ("phonons_ms", C.c_double), ("window_ms", C.c_double),
         ("stage1_ms", C.c_double), ("rotate_ms", C.c_double), ("delta_ms", C.c_double),
-        ("total_ms", C.c_double),
+        ("total_ms", C.c_double), ("sampler_ms", C.c_double),
     ]
 
 
@@ -87,6 +103,14 @@ def _load() -> C.CDLL:
         "phoebe_gpu_constants": (None, [C.POINTER(D)]),
         "phoebe_gpu_version": (C.c_char_p, []),
         "phoebe_gpu_bands_noalloc": (I, [I, I, P, P, P, I, P, P, P, P]),
+        "phoebe_gpu_sampler_init": (I, [P, C.c_uint64]),
+        "phoebe_gpu_sampler_load": (I, [P, P, I64]),
+        "phoebe_gpu_sampler_save": (I, [P, P, I64]),
+        "phoebe_gpu_train_opts_default": (None, [C.POINTER(TrainOpts)]),
+        "phoebe_gpu_sampler_train": (I, [P, C.POINTER(RTAParams), C.POINTER(TrainOpts), P]),
+        "phoebe_gpu_q_contributions": (I, [P, C.POINTER(RTAParams), C.POINTER(I), P, P, P, P]),
+        "phoebe_gpu_mlp_loss_grad": (I, [P, I64, P, I, P, P, P, P, P]),
+        "phoebe_gpu_is_uniforms": (I, [P, C.c_uint64, C.c_int32, I64, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -152,8 +176,10 @@ def make_params(p=None, **kw) -> RTAParams:
             s.k_subset = arr.ctypes.data_as(C.POINTER(C.c_int32))
         elif key in ("T_K", "mu_eV", "sigma_eV", "window_eV", "delta_cut_sigmas", "omega_cut_eV", "degen_tol_eV"):
             setattr(s, key, float(val))
-        elif key in ("precision", "max_batch_states"):
+        elif key in ("precision", "max_batch_states", "sampler", "seed"):
             setattr(s, key, int(val))
+        elif key in ("sample_fraction", "mix_alpha"):
+            setattr(s, key, float(val))
     s._keep = keep  # keep the subset array alive with the struct
     return s
 
@@ -270,3 +296,65 @@ class PhoebeGPU:
         s = Stats()
         self._check(lib.phoebe_gpu_get_stats(self._ctx, C.byref(s)))
         return {name: getattr(s, name) for name, _ in Stats._fields_}
+
+    # -------------------------------------------------------------- learned q proposal
+    def sampler_init(self, seed: int = 0):
+        self._check(lib.phoebe_gpu_sampler_init(self._ctx, int(seed)))
+
+    def sampler_load(self, params):
+        a = np.ascontiguousarray(params, dtype=np.float32).ravel()
+        self._check(lib.phoebe_gpu_sampler_load(self._ctx, _ptr(a), a.size))
+
+    def sampler_save(self) -> np.ndarray:
+        a = np.empty(MLP_NPARAM, dtype=np.float32)
+        self._check(lib.phoebe_gpu_sampler_save(self._ctx, _ptr(a), a.size))
+        return a
+
+    def sampler_train(self, grid_params, **opts) -> np.ndarray:
+        """Train on one full-grid run; returns the mean loss of each epoch."""
+        s = grid_params if isinstance(grid_params, RTAParams) else make_params(grid_params)
+        o = TrainOpts()
+        lib.phoebe_gpu_train_opts_default(C.byref(o))
+        for key, val in opts.items():
+            setattr(o, key, type(getattr(o, key))(val))
+        loss = np.zeros(o.epochs)
+        self._check(lib.phoebe_gpu_sampler_train(self._ctx, C.byref(s), C.byref(o), _ptr(loss)))
+        return loss
+
+    def q_contributions(self, params, nq_total: int | None = None, **kw):
+        """c_nk(q) for every active state and q: returns (k_index, band, c [n][N_q] float32, features [n][4])."""
+        s = params if isinstance(params, RTAParams) else make_params(params, **kw)
+        n = C.c_int(0)
+        self._check(lib.phoebe_gpu_q_contributions(self._ctx, C.byref(s), C.byref(n), None, None, None, None))
+        Nq = int(s.nq[0]) * int(s.nq[1]) * int(s.nq[2])
+        m = max(n.value, 1)
+        ki = np.empty(m, dtype=np.int32)
+        bd = np.empty(m, dtype=np.int32)
+        cq = np.empty((m, Nq), dtype=np.float32)
+        ft = np.empty((m, 4), dtype=np.float32)
+        nn = C.c_int(m)
+        self._check(lib.phoebe_gpu_q_contributions(self._ctx, C.byref(s), C.byref(nn), _ptr(ki), _ptr(bd), _ptr(cq),
+                                                   _ptr(ft)))
+        k = nn.value
+        return ki[:k], bd[:k], cq[:k], ft[:k]
+
+    def mlp_loss_grad(self, x, group_off=None, target=None):
+        """Network logits, and with targets the loss and gradient, on explicit rows x [n][7]."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        n = len(x)
+        logits = np.empty(n, dtype=np.float32)
+        if target is None:
+            self._check(lib.phoebe_gpu_mlp_loss_grad(self._ctx, n, _ptr(x), 0, None, None, _ptr(logits), None, None))
+            return logits
+        off = np.ascontiguousarray(group_off, dtype=np.int64)
+        t = np.ascontiguousarray(target, dtype=np.float32)
+        loss = C.c_double(0.0)
+        grad = np.empty(MLP_NPARAM, dtype=np.float32)
+        self._check(lib.phoebe_gpu_mlp_loss_grad(self._ctx, n, _ptr(x), len(off) - 1, _ptr(off), _ptr(t),
+                                                 _ptr(logits), C.byref(loss), _ptr(grad)))
+        return logits, loss.value, grad
+
+    def is_uniforms(self, seed: int, k: int, n: int) -> np.ndarray:
+        u = np.empty(int(n), dtype=np.float64)
+        self._check(lib.phoebe_gpu_is_uniforms(self._ctx, int(seed), int(k), int(n), _ptr(u)))
+        return u

@@ -233,6 +233,9 @@ void phoebe_gpu_rta_params_default(phoebe_gpu_rta_params* p) {
   p->omega_cut_eV = 1e-4;
   p->degen_tol_eV = 1e-6;
   p->precision = PHOEBE_PREC_FP64;
+  p->sampler = PHOEBE_SAMPLER_FULL;
+  p->sample_fraction = 0.05;
+  p->mix_alpha = 0.1;
 }
 
 int phoebe_gpu_create(phoebe_gpu_ctx** out, int device, void* cuda_stream) {

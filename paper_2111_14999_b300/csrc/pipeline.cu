@@ -137,8 +137,20 @@ static int check_params(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, GridM
   if (!(p->degen_tol_eV >= 0.0)) return fail(c, PHOEBE_GPU_ERR_ARG, "degen_tol_eV must be >= 0");
   if (p->precision < PHOEBE_PREC_FP64 || p->precision > PHOEBE_PREC_BF16X3)
     return fail(c, PHOEBE_GPU_ERR_ARG, "unknown precision %d", p->precision);
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < 4; ++i)
     if (p->reserved[i] != 0) return fail(c, PHOEBE_GPU_ERR_ARG, "reserved fields must be zero");
+  if (p->sampler < PHOEBE_SAMPLER_FULL || p->sampler > PHOEBE_SAMPLER_UNIFORM)
+    return fail(c, PHOEBE_GPU_ERR_ARG, "unknown sampler %d", p->sampler);
+  if (p->sampler != PHOEBE_SAMPLER_FULL) {
+    if (!(p->sample_fraction > 0.0 && p->sample_fraction <= 1.0))
+      return fail(c, PHOEBE_GPU_ERR_ARG, "sample_fraction must be in (0, 1]");
+    if (p->sampler == PHOEBE_SAMPLER_LEARNED && !(p->mix_alpha > 0.0 && p->mix_alpha <= 1.0))
+      return fail(c, PHOEBE_GPU_ERR_ARG, "mix_alpha must be in (0, 1]");
+    if (p->precision == PHOEBE_PREC_FP64)
+      return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "sampled q sums need a tensor-core precision (1..6)");
+    if (p->sampler == PHOEBE_SAMPLER_LEARNED && !c->have_mlp)
+      return fail(c, PHOEBE_GPU_ERR_ORDER, "the learned sampler needs sampler_init/load/train first");
+  }
   if (p->max_batch_states < 0) return fail(c, PHOEBE_GPU_ERR_ARG, "max_batch_states must be >= 0");
   int64_t Nk = (int64_t)p->nk[0] * p->nk[1] * p->nk[2];
   if (p->n_k_subset < 0) return fail(c, PHOEBE_GPU_ERR_ARG, "n_k_subset must be >= 0");
@@ -245,6 +257,25 @@ static int run_fp64(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Gri
   return PHOEBE_GPU_OK;
 }
 
+namespace {
+// Installs an importance-sampling request for one call when the parameters ask for one.
+struct IsGuard {
+  phoebe_gpu_ctx* c;
+  IsRequest req;
+  bool own = false;
+  IsGuard(phoebe_gpu_ctx* ctx, const phoebe_gpu_rta_params* p) : c(ctx) {
+    if (!c->isreq && p && p->sampler != PHOEBE_SAMPLER_FULL) {
+      req.mode = 1;
+      c->isreq = &req;
+      own = true;
+    }
+  }
+  ~IsGuard() {
+    if (own) c->isreq = nullptr;
+  }
+};
+}  // namespace
+
 int linewidths(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, int* n_states, int32_t* k_index, int32_t* band,
                double* gamma, bool device_out) {
   c->launches = 0;
@@ -252,6 +283,9 @@ int linewidths(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, int* n_states,
   if (!n_states) return fail(c, PHOEBE_GPU_ERR_ARG, "n_states is NULL");
   GridMap gm;
   TRY(check_params(c, p, &gm));
+  IsGuard is_guard(c, p);
+  if (c->isreq && p->precision == PHOEBE_PREC_FP64)
+    return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "sampled q sums need a tensor-core precision (1..6)");
   if (!c->have_H || !c->have_Phi || !c->have_g)
     return fail(c, PHOEBE_GPU_ERR_ORDER, "linewidths_rta needs all three set_* calls first");
   if (c->g_nw != c->nw || c->g_na != c->na)

@@ -35,6 +35,18 @@ struct phoebe_gpu_ctx {
   // tensor-core operands derived from g (invalidated by set_*)
   bool tc_g_valid = false;
   TcState* tc = nullptr;
+  // learned q proposal: FP32 master parameters and Adam state live in bufs "mlp_*"
+  bool have_mlp = false;
+  int64_t adam_t = 0;
+  // set by the sampler entry points for the duration of one pipeline call
+  struct IsRequest* isreq = nullptr;
+};
+
+// What the sampled q sums of one pipeline call must produce (sampler.cu).
+struct IsRequest {
+  int mode = 0;             // 1: importance-sampled Gamma into the raw accumulator; 2: c_nk(q) of every q
+  float* c_out = nullptr;   // mode 2: device [n_states][N_q]
+  float* feat_out = nullptr;  // optional: device [n_states][4] (eps - mu, v)
 };
 
 namespace phx {

@@ -32,6 +32,7 @@
 #include <stdio.h>
 
 #include "tc.h"
+#include "sampler.h"
 #include "tc_ptx.cuh"
 
 struct TcState {
@@ -1017,6 +1018,121 @@ static int part_maps(phoebe_gpu_ctx* c, CUtensorMap* tm, const Parts& P, int nsp
 
 static float host_pow2_scale(double maxabs) { return pow2_scale((float)maxabs); }
 
+// Sampled q sums: stage 1 on the tensor cores per batch of whole k points, then the
+// importance-sampled pairs of each batch (sampler.cu) in place of the full-grid stage 2.
+template <int NW, int NM, int FMT, int NSPLIT, int NPROD>
+static int run_sampled(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& gm, int64_t ns,
+                       const std::vector<int>& hk, const int* st_k, const int* st_b, const double* epsF,
+                       const cplx* UF, const double* omega, const double* nB, const cplx* Zq, double* raw,
+                       const float2* UH, const float* f32, const float2* eps2, double omega_max, const Parts& Pg,
+                       float sA1, const cplx* cis_k, const GridPhase& gk, int* err) {
+  const int nw = NW, nm = NM, nRe = c->nRe, nRp = c->nRp;
+  const int esz = FMT == 2 ? 4 : 2;
+  const int KB = 128 / esz;
+  const int Kp1 = (2 * nRe + KB - 1) / KB * KB;
+  const int64_t C = (int64_t)nRp * nw * nw * nm;
+  const int BN1 = StoreEpi::BN;
+  int st;
+  Timer tm;
+  IsTables it;
+  it.epsF = epsF;
+  it.UF = UF;
+  it.eps2 = eps2;
+  it.f32 = f32;
+  it.UH = UH;
+  it.omega = omega;
+  it.nB = nB;
+  it.Zq = Zq;
+  it.omega_max = omega_max;
+  unsigned* tmaxp = (unsigned*)ensure(c, "tc_tmax", 64, &st);
+  if (!tmaxp) return st;
+  // batches of whole k points: the proposal of a k mixes all its active bands
+  const int max_states = p->max_batch_states > 0 ? p->max_batch_states : 1024;
+  std::vector<int> kb_list, st_kb;
+  int64_t i0 = 0;
+  while (i0 < ns) {
+    int64_t i1 = i0;
+    kb_list.clear();
+    st_kb.clear();
+    while (i1 < ns) {
+      if (kb_list.empty() || kb_list.back() != hk[i1]) {
+        int64_t j = i1;
+        while (j < ns && hk[j] == hk[i1]) ++j;
+        if (!kb_list.empty() && (i1 - i0) + (j - i1) > max_states) break;
+        kb_list.push_back(hk[i1]);
+      }
+      st_kb.push_back((int)kb_list.size() - 1);
+      ++i1;
+    }
+    const int S = (int)(i1 - i0);
+    const int nkb = (int)kb_list.size();
+    void *d_kb, *d_stkb;
+    TRY(upload(c, "tc_batch_k", kb_list.data(), sizeof(int) * nkb, &d_kb));
+    TRY(upload(c, "tc_batch_stkb", st_kb.data(), sizeof(int) * S, &d_stkb));
+    tm.begin(c);
+    Parts PAk;
+    TRY(ensure_parts(c, "tc_Ak", NSPLIT, (size_t)nkb * Kp1, esz, &PAk));
+    float* X = (float*)ensure(c, "tc_X", sizeof(float) * nkb * 2 * C, &st);
+    if (!X) return st;
+    {
+      int64_t nt = (int64_t)nkb * (Kp1 / 2);
+      k_pack_phase<FMT, NSPLIT><<<(unsigned)((nt + 255) / 256), 256, 0, c->stream>>>(
+          (const int*)d_kb, nkb, (const int*)c->bufs["Re"].p, (const double*)c->bufs["we"].p, nRe, gk, cis_k, Kp1,
+          sA1, PAk);
+      c->launches++;
+      CK(c, cudaGetLastError());
+    }
+    CUtensorMap tAk[3], tG[3];
+    TRY(part_maps(c, tAk, PAk, NSPLIT, FMT, Kp1, nkb, 128 / kClusterN));
+    TRY(part_maps(c, tG, Pg, NSPLIT, FMT, Kp1, 2 * C, BN1));
+    {
+      TcGemmArgs a;
+      a.m_tiles = (nkb + 127) / 128;
+      a.n_tiles = (int)((2 * C + BN1 - 1) / BN1);
+      a.kblocks = Kp1 / KB;
+      a.kb_per_chunk = PHX_KB_PER_CHUNK;
+      a.b_row_step = BN1;
+      a.group_m = std::max(1, a.m_tiles);
+      a.ntiles = a.m_tiles * a.n_tiles;
+      a.tile_list = nullptr;
+      a.ntiles_dev = nullptr;
+      a.err = err;
+      StoreEpi::Params ep{X, 2 * C, nkb, (int)(2 * C)};
+      TRY(launch_gemm<StoreEpi, FMT, NSPLIT, NPROD>(c, tAk, tG, a, ep));
+    }
+    float2* Tb = (float2*)ensure(c, "tc_T", sizeof(float2) * (size_t)S * nRp * nm * nw, &st);
+    if (!Tb) return st;
+    CK(c, cudaMemsetAsync(tmaxp, 0, 64, c->stream));
+    {
+      int64_t nt = (int64_t)S * nRp * nm * nw;
+      const float unscale1 = 1.0f / (sA1 * c->tc->g_scale);
+      k_pack_t<<<(unsigned)((nt + 255) / 256), 256, 0, c->stream>>>(X, 2 * C, unscale1, (const int*)d_stkb, st_k + i0,
+                                                                     st_b + i0, gm, UF, S, nRp, nw, nm, Tb, tmaxp);
+      c->launches++;
+      CK(c, cudaGetLastError());
+    }
+    tm.end(c, &c->stats.stage1_ms);
+    IsBatch ib;
+    ib.S = S;
+    ib.nkb = nkb;
+    ib.s_base = i0;
+    ib.st_k = st_k + i0;
+    ib.st_b = st_b + i0;
+    ib.st_kb = (const int*)d_stkb;
+    ib.kb = (const int*)d_kb;
+    ib.st_kb_host = &st_kb;
+    ib.kb_host = &kb_list;
+    ib.T = Tb;
+    TRY(is_batch<NW, NM>(c, p, gm, ib, it, raw));
+    i0 = i1;
+  }
+  int herr = 0;
+  CK(c, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (herr) return fail(c, PHOEBE_GPU_ERR_TIMEOUT, "a tensor-core pipeline wait ran out; results discarded");
+  return PHOEBE_GPU_OK;
+}
+
 template <int NW, int NM, int FMT, int NSPLIT, int NPROD>
 static int run_tc_typed(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& gm, int64_t ns,
                         const std::vector<int>& hk, const int* st_k, const int* st_b, const double* epsF,
@@ -1095,12 +1211,22 @@ static int run_tc_typed(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const
   unsigned long long ombits = 0;
   CK(c, cudaMemcpyAsync(&ombits, dmax, sizeof(ombits), cudaMemcpyDeviceToHost, c->stream));
 
+  // sampled q sums (learned or uniform proposal) replace the full-grid stage 2
+  const bool sampled = c->isreq != nullptr;
   // stage-2 A operand: q phases, rows in compact q blocks padded to 128
   GridPhase gq = make_phase(gm.nq), gk = make_phase(gm.nk);
   cplx *cis_q, *cis_k;
   TRY(cis_table(c, gq, "cis_q", &cis_q));
   TRY(cis_table(c, gk, "cis_k", &cis_k));
   QBlocks qb;
+  if (sampled) {
+    CK(c, cudaStreamSynchronize(c->stream));
+    double omega_max;
+    memcpy(&omega_max, &ombits, sizeof(double));
+    tm.end(c, &c->stats.stage1_ms);
+    return run_sampled<NW, NM, FMT, NSPLIT, NPROD>(c, p, gm, ns, hk, st_k, st_b, epsF, UF, omega, nB, Zq, raw, UH,
+                                                    f32, eps2, omega_max, Pg, sA1, cis_k, gk, err);
+  }
   {
     const int shape[3] = {4, 4, 8};
     for (int i = 0; i < 3; ++i) {

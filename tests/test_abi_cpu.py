@@ -38,6 +38,10 @@ def test_params_struct_defaults_and_layout():
     s = pg.make_params(W.toy()[1], k_subset=[1, 2, 5])
     assert list(s.nk) == [8, 8, 8] and s.delta_cut_sigmas == 6.0 and s.omega_cut_eV == 1e-4
     assert s.n_k_subset == 3 and s.k_subset[2] == 5
+    assert s.sampler == 0 and s.sample_fraction == 0.05 and s.mix_alpha == 0.1
+    o = pg.binding.TrainOpts()
+    pg.lib.phoebe_gpu_train_opts_default(ctypes.byref(o))
+    assert o.epochs > 0 and o.states_per_step > 0 and o.lr > 0
 
 
 def _c_layout(struct, fields, tmp_path):
@@ -58,7 +62,8 @@ def _c_layout(struct, fields, tmp_path):
 
 def test_ctypes_structs_mirror_the_header(tmp_path):
     import paper_2111_14999_b300 as pg
-    for py, cname in ((pg.RTAParams, "phoebe_gpu_rta_params"), (pg.binding.Stats, "phoebe_gpu_stats")):
+    for py, cname in ((pg.RTAParams, "phoebe_gpu_rta_params"), (pg.binding.Stats, "phoebe_gpu_stats"),
+                      (pg.binding.TrainOpts, "phoebe_gpu_train_opts")):
         names = [f for f, _ in py._fields_]
         got = _c_layout(cname, names, tmp_path)
         assert got[0] == ctypes.sizeof(py), cname

@@ -1,0 +1,148 @@
+"""Learned q proposal on the GPU against the oracle (importance-sampled q sums of Eq. 29).
+
+Checks, each through the C ABI: the Philox draws (bit-exact), the network's logits, loss and
+gradient (1e-3 relative, the BF16-parameter / FP32-activation budget), the per-state features
+and the q-resolved terms c_nk(q) (split-FP16 contraction tolerance), and the sampled Gamma:
+draw for draw equal to the oracle's estimate with the same seed and parameters, and unbiased
+against the full q sum.
+"""
+import numpy as np
+import pytest
+
+from oracle import elph
+from oracle import sampler as S
+from workloads import synthetic as W
+
+pytestmark = pytest.mark.gpu
+
+PREC = 5  # split FP16 contractions (the tolerance below is that mode's)
+C_RTOL = 2e-5
+
+
+def _pg():
+    import paper_2111_14999_b300 as pg
+    return pg
+
+
+def _blob(seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    th = {}
+    for name, shape in S.SHAPES:
+        fan_in = shape[1] if len(shape) == 2 else S.NH
+        th[name] = rng.uniform(-1, 1, shape) * scale / np.sqrt(fan_in)
+    return S.pack(th).astype(np.float32)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    pg = _pg()
+    with pg.PhoebeGPU(0) as c:
+        yield c
+
+
+def test_philox_uniforms_bit_exact(ctx):
+    for seed, k, n in ((0, 0, 1000), (0xDEADBEEF12345678, 63999, 4097), (7, 12, 1)):
+        assert np.array_equal(ctx.is_uniforms(seed, k, n), S.is_uniforms(seed, k, n))
+
+
+def test_network_logits_loss_gradient_vs_oracle(ctx):
+    blob = _blob(3, scale=2.0)
+    ctx.sampler_load(blob)
+    assert np.array_equal(ctx.sampler_save(), blob)
+    rng = np.random.default_rng(4)
+    n = 3000                                   # 24 row tiles of 128 plus a ragged tail
+    x = rng.uniform(-1, 1, (n, S.NIN)).astype(np.float32)
+    x[:, 3:] *= 2.0
+    off = np.array([0, 1000, 1001, 2200, n])  # includes a one-row group
+    t = (rng.uniform(0, 1, n) ** 6).astype(np.float32)
+    z, loss, grad = ctx.mlp_loss_grad(x, off, t)
+    lo, go, zo = S.loss_and_grad(blob, x.astype(np.float64), off, t.astype(np.float64))
+    assert np.max(np.abs(z - zo)) <= 1e-3 * np.max(np.abs(zo))
+    assert loss == pytest.approx(lo, rel=1e-3)
+    th_g, th_o = S.unpack(grad), S.unpack(go)
+    floor = 1e-6 * np.linalg.norm(go)          # d loss / d b4 is exactly 0 (softmax shift invariance)
+    for name, _ in S.SHAPES:
+        a, b = th_g[name].ravel(), th_o[name].ravel()
+        assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b) + floor, name
+    assert abs(th_o["b4"][0]) <= 1e-12 * np.linalg.norm(go)
+    # logits only
+    z2 = ctx.mlp_loss_grad(x[:130])
+    assert np.max(np.abs(z2 - zo[:130])) <= 1e-3 * np.max(np.abs(zo))
+
+
+@pytest.mark.parametrize("which", ["toy", "si_like"])
+def test_features_and_q_terms_vs_oracle(ctx, which):
+    if which == "toy":
+        mat, prm = W.toy(seed=0)
+        kk = np.array([0, 5, 77, 300, 511])
+    else:
+        mat, prm = W.si_like(seed=0, nk=8)
+        kk = np.array([3, 40, 111, 260, 401])
+    prm = prm.with_(k_subset=kk, precision=PREC)
+    ctx.set_material(mat)
+    ki, bd, c, feat = ctx.q_contributions(prm)
+    tab = elph.electron_table(mat, prm)
+    ks, bs, co = elph.contributions(mat, prm, k_indices=kk, table=tab)
+    assert np.array_equal(ki, ks) and np.array_equal(bd, bs)
+    assert len(ks) > 0
+    scale = np.max(np.abs(co))
+    assert scale > 0
+    assert np.max(np.abs(c - co)) <= C_RTOL * scale
+    fo = S.state_features(mat, prm, ks, bs, table=tab)
+    assert np.allclose(feat, fo, rtol=1e-5, atol=1e-6 * np.max(np.abs(fo)))
+    # the q terms average to the full-grid linewidth of the same precision (before degenerate averaging)
+    st = ctx.linewidths_rta(prm)
+    assert np.array_equal(st[0], ki)
+    raw = c.astype(np.float64).mean(axis=1)
+    nondeg = np.array([np.sum((ks == k) & (np.abs(fo[:, 0] - f) < 1e-5)) == 1 for k, f in zip(ks, fo[:, 0])])
+    assert np.allclose(st[2][nondeg], raw[nondeg], rtol=1e-4)
+
+
+@pytest.mark.parametrize("uniform", [True, False])
+def test_sampled_gamma_equals_oracle_estimate(ctx, uniform):
+    # same seed, same parameters: the same draws, so the estimates agree to the contraction tolerance
+    mat, prm = W.toy(seed=0)
+    kk = np.array([1, 22, 43, 130, 400])
+    blob = _blob(11, scale=3.0)
+    ctx.set_material(mat)
+    ctx.sampler_load(blob)
+    frac, alpha, seed = 0.25, 0.1, 12345
+    prm2 = prm.with_(k_subset=kk, precision=PREC, sampler=2 if uniform else 1, sample_fraction=frac,
+                     mix_alpha=alpha, seed=seed)
+    ki, bd, g = ctx.linewidths_rta(prm2)
+    ks, bs, go = S.linewidths_is(mat, prm, blob, frac, alpha, seed, k_indices=kk, uniform=uniform)
+    assert np.array_equal(ki, ks) and np.array_equal(bd, bs)
+    rel = np.abs(g - go) / np.maximum(np.abs(go), 1e-6 * np.max(np.abs(go)))
+    # a draw may differ where a uniform falls within rounding of a CDF step (FP32 vs FP64 network)
+    assert np.mean(rel < 1e-4) >= 0.9
+    assert np.median(rel) < 1e-5
+
+
+def test_sampled_gamma_is_unbiased(ctx):
+    mat, prm = W.toy(seed=0)
+    kk = np.array([1, 22, 43, 130, 400, 511])
+    ctx.set_material(mat)
+    ctx.sampler_load(_blob(5, scale=3.0))
+    base = prm.with_(k_subset=kk, precision=PREC)
+    _, _, full = ctx.linewidths_rta(base)
+    for sampler in (1, 2):
+        runs = np.array([ctx.linewidths_rta(base.with_(sampler=sampler, sample_fraction=0.1, seed=s))[2]
+                         for s in range(48)])
+        mean, se = runs.mean(0), runs.std(0, ddof=1) / np.sqrt(len(runs))
+        assert np.all(np.abs(mean - full) <= 4 * se + 1e-9 * np.max(full)), sampler
+        assert np.all(se > 0)
+
+
+def test_sampler_argument_errors(ctx):
+    pg = _pg()
+    mat, prm = W.toy(seed=0)
+    ctx.set_material(mat)
+    with pytest.raises(pg.PhoebeGPUError) as e:
+        ctx.linewidths_rta(prm.with_(precision=0, sampler=2))
+    assert e.value.status == -9
+    with pytest.raises(pg.PhoebeGPUError) as e:
+        ctx.linewidths_rta(prm.with_(precision=PREC, sampler=2, sample_fraction=0.0))
+    assert e.value.status == -1
+    with pytest.raises(pg.PhoebeGPUError) as e:
+        ctx.sampler_load(np.zeros(10, dtype=np.float32))
+    assert e.value.status == -1

@@ -78,6 +78,10 @@ class RTAParams:
     degen_tol_eV: float = 1e-6
     precision: int = 0           # 0 FP64, 1 split BF16, 2 split TF32, 3 BF16, 4 TF32
     k_subset: np.ndarray | None = None   # optional k-grid indices of initial states
+    sampler: int = 0             # 0 full q sum, 1 learned proposal, 2 uniform proposal (importance sampling)
+    sample_fraction: float = 0.05
+    mix_alpha: float = 0.1
+    seed: int = 0
 
     def with_(self, **kw) -> "RTAParams":
         return replace(self, **kw)
