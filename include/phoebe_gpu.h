@@ -219,9 +219,9 @@ int phoebe_gpu_sampler_load(phoebe_gpu_ctx* ctx, const float* params, int64_t n)
 int phoebe_gpu_sampler_save(phoebe_gpu_ctx* ctx, float* params, int64_t n);
 
 typedef struct {
-  int epochs;                /* passes over the training states (default 20) */
-  int states_per_step;       /* states per Adam step (default 16) */
-  double lr, beta1, beta2, eps;  /* Adam (defaults 2e-3, 0.9, 0.999, 1e-8) */
+  int epochs;                /* passes over the training states (default 60) */
+  int states_per_step;       /* states per Adam step (default 64) */
+  double lr, beta1, beta2, eps;  /* Adam (defaults 3e-3, 0.9, 0.999, 1e-8) */
   uint64_t seed;             /* order of the states in each epoch */
   int reserved[4];           /* must be zero */
 } phoebe_gpu_train_opts;

@@ -1084,9 +1084,9 @@ extern "C" int phoebe_gpu_sampler_save(phoebe_gpu_ctx* c, float* params, int64_t
 extern "C" void phoebe_gpu_train_opts_default(phoebe_gpu_train_opts* o) {
   if (!o) return;
   memset(o, 0, sizeof(*o));
-  o->epochs = 20;
-  o->states_per_step = 16;
-  o->lr = 2e-3;
+  o->epochs = 60;
+  o->states_per_step = 64;
+  o->lr = 3e-3;
   o->beta1 = 0.9;
   o->beta2 = 0.999;
   o->eps = 1e-8;
