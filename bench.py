@@ -139,6 +139,64 @@ def cpu_baseline_oracle(n_k: int, seed: int = 0) -> dict:
             "seconds": el, "states": int(len(g))}
 
 
+def learned_leg(pg, W, dev, stream, args) -> dict:
+    """Learned q proposal: trained on the q terms of a Si-like 20^3 full-grid run, evaluated on
+    40^3 k x 80^3 q (a seeded subset of k) at 5% of q against the full q sum of the same
+    precision; the uniform proposal and the FP64 full sum (a smaller sample) beside it."""
+    import torch
+    prec = args.precision if args.precision != 0 else 5
+    ctx = pg.PhoebeGPU(dev, stream=stream)
+    ctx.set_profiling(True)
+    mat20, p20 = W.si_like(seed=0, nk=20)
+    ctx.set_material(mat20)
+    ctx.sampler_init(1)
+    t0 = time.perf_counter()
+    loss = ctx.sampler_train(p20.with_(precision=prec))
+    train_s = time.perf_counter() - t0
+    mat, prm = W.si_like(seed=0, nk=40, nq=80)
+    ctx.set_material(mat)
+    kk = np.sort(np.random.default_rng(2).choice(64000, args.learned_k, replace=False))
+    pe = prm.with_(precision=prec, k_subset=kk)
+
+    def timed(p):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        out = ctx.linewidths_rta(p)
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - t, ctx.stats()
+    timed(pe)                                     # warm-up (allocations, 80^3 tables)
+    (_, _, full), full_s, full_st = timed(pe)
+    res = {}
+    for name, smp in (("learned", 1), ("uniform", 2)):
+        errs, walls, st = [], [], None
+        for seed in range(4):
+            (_, _, g), w, st = timed(pe.with_(sampler=smp, sample_fraction=0.05, seed=seed))
+            errs.append(float(np.linalg.norm(g - full) / np.linalg.norm(full)))
+            walls.append(w)
+        res[name] = {"l2_rel_err": errs, "wall_s": float(np.median(walls)),
+                     "sampler_ms": st["sampler_ms"], "pairs_ms": st["stage2_ms"], "total_ms": st["total_ms"]}
+    n = len(full)
+    f64k = kk[:6]
+    (_, _, g64), w64, st64 = timed(prm.with_(precision=0, k_subset=f64k))
+    ctx.close()
+    lw = n / res["learned"]["wall_s"]
+    return {
+        "workload": "si_like 40^3 k x 80^3 q, seeded subset of k; trained on the si_like 20^3 x 20^3 q terms",
+        "states": int(n), "sample_fraction": 0.05, "mix_alpha": 0.1, "precision": PREC_NAMES[prec],
+        "train_s": train_s, "train_loss_first_last": [float(loss[0]), float(loss[-1])],
+        "l2_rel_err_learned": res["learned"]["l2_rel_err"], "l2_rel_err_uniform": res["uniform"]["l2_rel_err"],
+        "variance_ratio_uniform_over_learned": float(np.mean(np.square(res["uniform"]["l2_rel_err"])) /
+                                                     np.mean(np.square(res["learned"]["l2_rel_err"]))),
+        "gate_l2_1pct_met": bool(np.mean(res["learned"]["l2_rel_err"]) <= 0.01),
+        "linewidths_per_s_learned": lw, "linewidths_per_s_full_same_precision": n / full_s,
+        "linewidths_per_s_fp64_gpu_full": len(g64) / w64,
+        "speedup_learned_vs_fp64_gpu": lw / (len(g64) / w64),
+        "learned_ms": {"network_proposal_draws": res["learned"]["sampler_ms"], "sampled_pairs": res["learned"]["pairs_ms"],
+                       "total": res["learned"]["total_ms"]},
+        "full_ms": {"stage2": full_st["stage2_ms"], "total": full_st["total_ms"]},
+    }
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -192,6 +250,8 @@ def main():
     ap.add_argument("--k-limit", type=int, default=0,
                     help="profiling case: restrict to this many seeded active k points (0 = whole grid)")
     ap.add_argument("--main-only", action="store_true", help="only the timed device leg (for ncu captures)")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal leg")
+    ap.add_argument("--learned-k", type=int, default=512, help="seeded k points of the learned-proposal evaluation")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -277,10 +337,12 @@ def main():
                 "avg_launch_ms": s2_ms / max(s2_launch, 1),
                 "issued_tensor_tflops": achieved * split_factor * kpad if achieved else None,
                 "issued_frac": achieved * split_factor * kpad / peak if achieved else None}
-    traffic_path = os.path.join(ROOT, "profiles", "stage2_traffic.json")
-    if os.path.exists(traffic_path) and args.precision == 5:
+    traffic_path = os.path.join(ROOT, "profiles", "stage2_traffic.txt")
+    if os.path.exists(traffic_path) and args.precision == 5 and args.k_limit == 0:
         with open(traffic_path) as f:
-            roof["traffic"] = json.load(f).get("dram_bytes_per_launch_full")
+            for ln in f:
+                if ln.startswith("dram_bytes_per_launch_full="):
+                    roof["traffic"] = float(ln.split("=", 1)[1])
 
     extra = {}
     if args.main_only:
@@ -364,6 +426,8 @@ def main():
         "e2e": {"value": e2e_value, "unit": "linewidths/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         **extra,
     }
+    if rank == 0 and not args.no_learned:
+        line["learned_sampler"] = learned_leg(pg, W, dev, stream, args)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle(args.cpu_k)
     if rank == 0:

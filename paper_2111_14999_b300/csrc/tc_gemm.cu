@@ -33,6 +33,7 @@
 
 #include "tc.h"
 #include "sampler.h"
+#include "generic.h"
 #include "tc_ptx.cuh"
 
 struct TcState {
@@ -63,13 +64,6 @@ struct TcGemmArgs {
   int* err;         // set to 1 if any bounded wait ran out
 };
 
-// Power-of-two factor that brings max|x| just below 2^14 (keeps FP16 parts in range; exact).
-__host__ __device__ inline float pow2_scale(float maxabs) {
-  if (!(maxabs > 0.f)) return 1.f;
-  int e;
-  frexpf(maxabs, &e);
-  return ldexpf(1.f, 14 - e);
-}
 
 // Epilogues receive the finished FP32 tile row of their thread in registers (acc[BN],
 // column c of the tile = acc[c]) and the tile coordinates.
@@ -1018,141 +1012,12 @@ static int part_maps(phoebe_gpu_ctx* c, CUtensorMap* tm, const Parts& P, int nsp
 
 static float host_pow2_scale(double maxabs) { return pow2_scale((float)maxabs); }
 
-// Sampled q sums: stage 1 on the tensor cores per batch of whole k points, then the
-// importance-sampled pairs of each batch (sampler.cu) in place of the full-grid stage 2.
-template <int NW, int NM, int FMT, int NSPLIT, int NPROD>
-static int run_sampled(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& gm, int64_t ns,
-                       const std::vector<int>& hk, const int* st_k, const int* st_b, const double* epsF,
-                       const cplx* UF, const double* omega, const double* nB, const cplx* Zq, double* raw,
-                       const float2* UH, const float* f32, const float2* eps2, double omega_max, const Parts& Pg,
-                       float sA1, const cplx* cis_k, const GridPhase& gk, int* err) {
-  const int nw = NW, nm = NM, nRe = c->nRe, nRp = c->nRp;
-  const int esz = FMT == 2 ? 4 : 2;
-  const int KB = 128 / esz;
-  const int Kp1 = (2 * nRe + KB - 1) / KB * KB;
-  const int64_t C = (int64_t)nRp * nw * nw * nm;
-  const int BN1 = StoreEpi::BN;
+// Stage-1 B operand from g (split parts in the operand format), cached on the context until
+// the next set_* call or a change of operand format.
+template <int FMT, int NSPLIT>
+static int ensure_g_operand(phoebe_gpu_ctx* c, int64_t C, int Kp1, int esz) {
+  const int nRe = c->nRe;
   int st;
-  Timer tm;
-  IsTables it;
-  it.epsF = epsF;
-  it.UF = UF;
-  it.eps2 = eps2;
-  it.f32 = f32;
-  it.UH = UH;
-  it.omega = omega;
-  it.nB = nB;
-  it.Zq = Zq;
-  it.omega_max = omega_max;
-  unsigned* tmaxp = (unsigned*)ensure(c, "tc_tmax", 64, &st);
-  if (!tmaxp) return st;
-  // batches of whole k points: the proposal of a k mixes all its active bands
-  const int max_states = p->max_batch_states > 0 ? p->max_batch_states : 1024;
-  std::vector<int> kb_list, st_kb;
-  int64_t i0 = 0;
-  while (i0 < ns) {
-    int64_t i1 = i0;
-    kb_list.clear();
-    st_kb.clear();
-    while (i1 < ns) {
-      if (kb_list.empty() || kb_list.back() != hk[i1]) {
-        int64_t j = i1;
-        while (j < ns && hk[j] == hk[i1]) ++j;
-        if (!kb_list.empty() && (i1 - i0) + (j - i1) > max_states) break;
-        kb_list.push_back(hk[i1]);
-      }
-      st_kb.push_back((int)kb_list.size() - 1);
-      ++i1;
-    }
-    const int S = (int)(i1 - i0);
-    const int nkb = (int)kb_list.size();
-    void *d_kb, *d_stkb;
-    TRY(upload(c, "tc_batch_k", kb_list.data(), sizeof(int) * nkb, &d_kb));
-    TRY(upload(c, "tc_batch_stkb", st_kb.data(), sizeof(int) * S, &d_stkb));
-    tm.begin(c);
-    Parts PAk;
-    TRY(ensure_parts(c, "tc_Ak", NSPLIT, (size_t)nkb * Kp1, esz, &PAk));
-    float* X = (float*)ensure(c, "tc_X", sizeof(float) * nkb * 2 * C, &st);
-    if (!X) return st;
-    {
-      int64_t nt = (int64_t)nkb * (Kp1 / 2);
-      k_pack_phase<FMT, NSPLIT><<<(unsigned)((nt + 255) / 256), 256, 0, c->stream>>>(
-          (const int*)d_kb, nkb, (const int*)c->bufs["Re"].p, (const double*)c->bufs["we"].p, nRe, gk, cis_k, Kp1,
-          sA1, PAk);
-      c->launches++;
-      CK(c, cudaGetLastError());
-    }
-    CUtensorMap tAk[3], tG[3];
-    TRY(part_maps(c, tAk, PAk, NSPLIT, FMT, Kp1, nkb, 128 / kClusterN));
-    TRY(part_maps(c, tG, Pg, NSPLIT, FMT, Kp1, 2 * C, BN1));
-    {
-      TcGemmArgs a;
-      a.m_tiles = (nkb + 127) / 128;
-      a.n_tiles = (int)((2 * C + BN1 - 1) / BN1);
-      a.kblocks = Kp1 / KB;
-      a.kb_per_chunk = PHX_KB_PER_CHUNK;
-      a.b_row_step = BN1;
-      a.group_m = std::max(1, a.m_tiles);
-      a.ntiles = a.m_tiles * a.n_tiles;
-      a.tile_list = nullptr;
-      a.ntiles_dev = nullptr;
-      a.err = err;
-      StoreEpi::Params ep{X, 2 * C, nkb, (int)(2 * C)};
-      TRY(launch_gemm<StoreEpi, FMT, NSPLIT, NPROD>(c, tAk, tG, a, ep));
-    }
-    float2* Tb = (float2*)ensure(c, "tc_T", sizeof(float2) * (size_t)S * nRp * nm * nw, &st);
-    if (!Tb) return st;
-    CK(c, cudaMemsetAsync(tmaxp, 0, 64, c->stream));
-    {
-      int64_t nt = (int64_t)S * nRp * nm * nw;
-      const float unscale1 = 1.0f / (sA1 * c->tc->g_scale);
-      k_pack_t<<<(unsigned)((nt + 255) / 256), 256, 0, c->stream>>>(X, 2 * C, unscale1, (const int*)d_stkb, st_k + i0,
-                                                                     st_b + i0, gm, UF, S, nRp, nw, nm, Tb, tmaxp);
-      c->launches++;
-      CK(c, cudaGetLastError());
-    }
-    tm.end(c, &c->stats.stage1_ms);
-    IsBatch ib;
-    ib.S = S;
-    ib.nkb = nkb;
-    ib.s_base = i0;
-    ib.st_k = st_k + i0;
-    ib.st_b = st_b + i0;
-    ib.st_kb = (const int*)d_stkb;
-    ib.kb = (const int*)d_kb;
-    ib.st_kb_host = &st_kb;
-    ib.kb_host = &kb_list;
-    ib.T = Tb;
-    TRY(is_batch<NW, NM>(c, p, gm, ib, it, raw));
-    i0 = i1;
-  }
-  int herr = 0;
-  CK(c, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  CK(c, cudaStreamSynchronize(c->stream));
-  if (herr) return fail(c, PHOEBE_GPU_ERR_TIMEOUT, "a tensor-core pipeline wait ran out; results discarded");
-  return PHOEBE_GPU_OK;
-}
-
-template <int NW, int NM, int FMT, int NSPLIT, int NPROD>
-static int run_tc_typed(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& gm, int64_t ns,
-                        const std::vector<int>& hk, const int* st_k, const int* st_b, const double* epsF,
-                        const cplx* UF, const double* fF, const double* omega, const double* nB, const cplx* Zq,
-                        double* raw) {
-  const int nw = NW, nm = NM, nRe = c->nRe, nRp = c->nRp;
-  const int esz = FMT == 2 ? 4 : 2;
-  const int KB = 128 / esz;  // elements per 128-byte K block
-  const int Kp1 = (2 * nRe + KB - 1) / KB * KB, Kp2 = (2 * nRp + KB - 1) / KB * KB;
-  const int64_t C = (int64_t)nRp * nw * nw * nm;
-  const int64_t NF = (int64_t)gm.nf[0] * gm.nf[1] * gm.nf[2];
-  const int64_t Nq = (int64_t)gm.nq[0] * gm.nq[1] * gm.nq[2];
-  int st;
-  Timer tm;
-  int* err = (int*)ensure(c, "tc_err", 64, &st);
-  if (!err) return st;
-  CK(c, cudaMemsetAsync(err, 0, 64, c->stream));
-  const float sA1 = host_pow2_scale(c->we_max), sA2 = host_pow2_scale(c->wp_max);
-
-  // stage-1 B operand from g (cached until the next set_* or a change of operand format)
   const int key = FMT * 16 + NSPLIT;
   if (!c->tc_g_valid || !c->tc || c->tc->g_key != key) {
     destroy_tc_state(c);
@@ -1190,6 +1055,343 @@ static int run_tc_typed(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const
     c->tc->g_key = key;
     c->tc_g_valid = true;
   }
+  return PHOEBE_GPU_OK;
+}
+
+// The next batch of whole k points starting at state i0 (states ordered by k): at most
+// max_states states unless a single k has more.  Returns the end state; fills the batch's k
+// list and each state's index into it.
+static int64_t next_batch(const std::vector<int>& hk, int64_t ns, int64_t i0, int max_states, std::vector<int>* kb_list,
+                          std::vector<int>* st_kb) {
+  int64_t i1 = i0;
+  kb_list->clear();
+  st_kb->clear();
+  while (i1 < ns) {
+    if (kb_list->empty() || kb_list->back() != hk[i1]) {
+      int64_t j = i1;
+      while (j < ns && hk[j] == hk[i1]) ++j;
+      if (!kb_list->empty() && (i1 - i0) + (j - i1) > max_states) break;
+      kb_list->push_back(hk[i1]);
+    }
+    st_kb->push_back((int)kb_list->size() - 1);
+    ++i1;
+  }
+  return i1;
+}
+
+// Stage 1 of one batch of whole k points on the tensor cores (Sec. 5.5 Eq. 71):
+// X[kb] = sum_Re w e^{ik.Re} g(Re, .) by a GEMM, then T[s][Rp][sa][m] = sum_n X[kb(s)] U_k[n][b(s)]
+// (FP32, physical scale) with the batch's max |T| in *tmaxp.
+template <int FMT, int NSPLIT, int NPROD>
+static int stage1_batch(phoebe_gpu_ctx* c, const GridMap& gm, const std::vector<int>& kb_list,
+                        const std::vector<int>& st_kb, int64_t i0, const int* st_k, const int* st_b, const cplx* UF,
+                        const Parts& Pg, float sA1, const cplx* cis_k, const GridPhase& gk, int* err, unsigned* tmaxp,
+                        const int* d_kb, const int* d_stkb, float2** Tb_out) {
+  const int nw = c->nw, nm = 3 * c->na, nRe = c->nRe, nRp = c->nRp;
+  const int esz = FMT == 2 ? 4 : 2;
+  const int KB = 128 / esz;
+  const int Kp1 = (2 * nRe + KB - 1) / KB * KB;
+  const int64_t C = (int64_t)nRp * nw * nw * nm;
+  const int BN1 = StoreEpi::BN;
+  const int S = (int)st_kb.size(), nkb = (int)kb_list.size();
+  int st;
+  Parts PAk;
+  TRY(ensure_parts(c, "tc_Ak", NSPLIT, (size_t)nkb * Kp1, esz, &PAk));
+  float* X = (float*)ensure(c, "tc_X", sizeof(float) * nkb * 2 * C, &st);
+  if (!X) return st;
+  {
+    int64_t nt = (int64_t)nkb * (Kp1 / 2);
+    k_pack_phase<FMT, NSPLIT><<<(unsigned)((nt + 255) / 256), 256, 0, c->stream>>>(
+        d_kb, nkb, (const int*)c->bufs["Re"].p, (const double*)c->bufs["we"].p, nRe, gk, cis_k, Kp1, sA1, PAk);
+    c->launches++;
+    CK(c, cudaGetLastError());
+  }
+  CUtensorMap tAk[3], tG[3];
+  TRY(part_maps(c, tAk, PAk, NSPLIT, FMT, Kp1, nkb, 128 / kClusterN));
+  TRY(part_maps(c, tG, Pg, NSPLIT, FMT, Kp1, 2 * C, BN1));
+  {
+    TcGemmArgs a;
+    a.m_tiles = (nkb + 127) / 128;
+    a.n_tiles = (int)((2 * C + BN1 - 1) / BN1);
+    a.kblocks = Kp1 / KB;
+    a.kb_per_chunk = PHX_KB_PER_CHUNK;
+    a.b_row_step = BN1;
+    a.group_m = std::max(1, a.m_tiles);
+    a.ntiles = a.m_tiles * a.n_tiles;
+    a.tile_list = nullptr;
+    a.ntiles_dev = nullptr;
+    a.err = err;
+    StoreEpi::Params ep{X, 2 * C, nkb, (int)(2 * C)};
+    TRY(launch_gemm<StoreEpi, FMT, NSPLIT, NPROD>(c, tAk, tG, a, ep));
+  }
+  float2* Tb = (float2*)ensure(c, "tc_T", sizeof(float2) * (size_t)S * nRp * nm * nw, &st);
+  if (!Tb) return st;
+  CK(c, cudaMemsetAsync(tmaxp, 0, 64, c->stream));
+  {
+    int64_t nt = (int64_t)S * nRp * nm * nw;
+    const float unscale1 = 1.0f / (sA1 * c->tc->g_scale);
+    k_pack_t<<<(unsigned)((nt + 255) / 256), 256, 0, c->stream>>>(X, 2 * C, unscale1, d_stkb, st_k + i0, st_b + i0,
+                                                                   gm, UF, S, nRp, nw, nm, Tb, tmaxp);
+    c->launches++;
+    CK(c, cudaGetLastError());
+  }
+  *Tb_out = Tb;
+  return PHOEBE_GPU_OK;
+}
+
+// Sampled q sums: stage 1 on the tensor cores per batch of whole k points, then the
+// importance-sampled pairs of each batch (sampler.cu) in place of the full-grid stage 2.
+template <int NW, int NM, int FMT, int NSPLIT, int NPROD>
+static int run_sampled(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& gm, int64_t ns,
+                       const std::vector<int>& hk, const int* st_k, const int* st_b, const double* epsF,
+                       const cplx* UF, const double* omega, const double* nB, const cplx* Zq, double* raw,
+                       const float2* UH, const float* f32, const float2* eps2, double omega_max, const Parts& Pg,
+                       float sA1, const cplx* cis_k, const GridPhase& gk, int* err) {
+  int st;
+  Timer tm;
+  IsTables it;
+  it.epsF = epsF;
+  it.UF = UF;
+  it.eps2 = eps2;
+  it.f32 = f32;
+  it.UH = UH;
+  it.omega = omega;
+  it.nB = nB;
+  it.Zq = Zq;
+  it.omega_max = omega_max;
+  unsigned* tmaxp = (unsigned*)ensure(c, "tc_tmax", 64, &st);
+  if (!tmaxp) return st;
+  // batches of whole k points: the proposal of a k mixes all its active bands
+  const int max_states = p->max_batch_states > 0 ? p->max_batch_states : 1024;
+  std::vector<int> kb_list, st_kb;
+  int64_t i0 = 0;
+  while (i0 < ns) {
+    const int64_t i1 = next_batch(hk, ns, i0, max_states, &kb_list, &st_kb);
+    const int S = (int)(i1 - i0);
+    const int nkb = (int)kb_list.size();
+    void *d_kb, *d_stkb;
+    TRY(upload(c, "tc_batch_k", kb_list.data(), sizeof(int) * nkb, &d_kb));
+    TRY(upload(c, "tc_batch_stkb", st_kb.data(), sizeof(int) * S, &d_stkb));
+    tm.begin(c);
+    float2* Tb;
+    TRY((stage1_batch<FMT, NSPLIT, NPROD>(c, gm, kb_list, st_kb, i0, st_k, st_b, UF, Pg, sA1, cis_k, gk, err, tmaxp,
+                                          (const int*)d_kb, (const int*)d_stkb, &Tb)));
+    tm.end(c, &c->stats.stage1_ms);
+    IsBatch ib;
+    ib.S = S;
+    ib.nkb = nkb;
+    ib.s_base = i0;
+    ib.st_k = st_k + i0;
+    ib.st_b = st_b + i0;
+    ib.st_kb = (const int*)d_stkb;
+    ib.kb = (const int*)d_kb;
+    ib.st_kb_host = &st_kb;
+    ib.kb_host = &kb_list;
+    ib.T = Tb;
+    TRY(is_batch<NW, NM>(c, p, gm, ib, it, raw));
+    i0 = i1;
+  }
+  int herr = 0;
+  CK(c, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (herr) return fail(c, PHOEBE_GPU_ERR_TIMEOUT, "a tensor-core pipeline wait ran out; results discarded");
+  return PHOEBE_GPU_OK;
+}
+
+// Stage 2 for any (nw, 3na): the R_p contraction G = P_q T runs as a plain tensor-core GEMM
+// into HBM, one q chunk at a time, and k_elph_generic applies U_{k+q}^dagger, Z_q and the
+// delta weights (Sec. 3.2 Eq. 13, Sec. 4.2 Eq. 29).  Exact: no screening.
+template <int FMT, int NSPLIT, int NPROD>
+static int run_tc_generic(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& gm, int64_t ns,
+                          const std::vector<int>& hk, const int* st_k, const int* st_b, const double* epsF,
+                          const cplx* UF, const double* fF, const double* omega, const double* nB, const cplx* Zq,
+                          double* raw) {
+  const int nw = c->nw, nm = 3 * c->na, nRe = c->nRe, nRp = c->nRp;
+  if (nm > kGenericMaxModes) return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "at most %d modes", kGenericMaxModes);
+  const int esz = FMT == 2 ? 4 : 2;
+  const int KB = 128 / esz;
+  const int Kp1 = (2 * nRe + KB - 1) / KB * KB, Kp2 = (2 * nRp + KB - 1) / KB * KB;
+  const int64_t C = (int64_t)nRp * nw * nw * nm;
+  const int64_t NF = (int64_t)gm.nf[0] * gm.nf[1] * gm.nf[2];
+  const int64_t Nq = (int64_t)gm.nq[0] * gm.nq[1] * gm.nq[2];
+  const int cps = 2 * nw * nm;
+  int st;
+  Timer tm;
+  int* err = (int*)ensure(c, "tc_err", 64, &st);
+  if (!err) return st;
+  CK(c, cudaMemsetAsync(err, 0, 64, c->stream));
+  const float sA1 = host_pow2_scale(c->we_max), sA2 = host_pow2_scale(c->wp_max);
+  TRY((ensure_g_operand<FMT, NSPLIT>(c, C, Kp1, esz)));
+  Parts Pg{{c->tc->g_part[0], c->tc->g_part[1], c->tc->g_part[2]}};
+  // FP32 tables
+  tm.begin(c);
+  float2* UH = (float2*)ensure(c, "tc_UH", sizeof(float2) * NF * nw * nw, &st);
+  if (!UH) return st;
+  float* f32 = (float*)ensure(c, "tc_f32", sizeof(float) * NF * nw, &st);
+  if (!f32) return st;
+  float2* eps2 = (float2*)ensure(c, "tc_eps2", sizeof(float2) * NF * nw, &st);
+  if (!eps2) return st;
+  unsigned long long* dmax = (unsigned long long*)ensure(c, "tc_max", 64, &st);
+  if (!dmax) return st;
+  k_tables_el<<<(unsigned)((NF * nw * nw + 255) / 256), 256, 0, c->stream>>>(UF, fF, epsF, NF, nw, UH, f32, eps2);
+  CK(c, cudaMemsetAsync(dmax, 0, 64, c->stream));
+  k_absmax_f64<<<64, 256, 0, c->stream>>>(omega, Nq * nm, dmax);
+  float2* Zf = (float2*)ensure(c, "tcg_Zf", sizeof(float2) * Nq * nm * nm, &st);
+  if (!Zf) return st;
+  float* omf = (float*)ensure(c, "tcg_omf", sizeof(float) * Nq * nm, &st);
+  if (!omf) return st;
+  float* nBf = (float*)ensure(c, "tcg_nBf", sizeof(float) * Nq * nm, &st);
+  if (!nBf) return st;
+  k_tables_ph<<<(unsigned)((Nq * nm * nm + 255) / 256), 256, 0, c->stream>>>(Zq, omega, nB, Nq, nm, Zf, omf, nBf);
+  c->launches += 3;
+  CK(c, cudaGetLastError());
+  unsigned long long ombits = 0;
+  CK(c, cudaMemcpyAsync(&ombits, dmax, sizeof(ombits), cudaMemcpyDeviceToHost, c->stream));
+  // A operand: q phases in q order, rows padded to a multiple of 128
+  GridPhase gq = make_phase(gm.nq), gk = make_phase(gm.nk);
+  cplx *cis_q, *cis_k;
+  TRY(cis_table(c, gq, "cis_q", &cis_q));
+  TRY(cis_table(c, gk, "cis_k", &cis_k));
+  const int64_t Mrows = (Nq + 127) / 128 * 128;
+  std::vector<int> q_of_row((size_t)Mrows, -1);
+  for (int64_t q = 0; q < Nq; ++q) q_of_row[(size_t)q] = (int)q;
+  void* d_qrow;
+  TRY(upload(c, "tcg_q_of_row", q_of_row.data(), sizeof(int) * Mrows, &d_qrow));
+  Parts PAq;
+  TRY(ensure_parts(c, "tc_Aq", NSPLIT, (size_t)Mrows * Kp2, esz, &PAq));
+  {
+    int64_t nt = Mrows * (Kp2 / 2);
+    k_pack_phase<FMT, NSPLIT><<<(unsigned)((nt + 255) / 256), 256, 0, c->stream>>>(
+        (const int*)d_qrow, Mrows, (const int*)c->bufs["Rp"].p, (const double*)c->bufs["wp"].p, nRp, gq, cis_q, Kp2,
+        sA2, PAq);
+    c->launches++;
+    CK(c, cudaGetLastError());
+  }
+  CK(c, cudaStreamSynchronize(c->stream));
+  double omega_max;
+  memcpy(&omega_max, &ombits, sizeof(double));
+  tm.end(c, &c->stats.stage1_ms);
+  unsigned* tmaxp = (unsigned*)ensure(c, "tc_tmax", 64, &st);
+  if (!tmaxp) return st;
+  const int64_t g_budget = (int64_t)512 << 20;  // bytes of G per q chunk
+  const int max_states =
+      p->max_batch_states > 0 ? p->max_batch_states : (int)std::max<int64_t>(1, std::min<int64_t>(4096, g_budget / (128 * 4 * cps)));
+  std::vector<int> kb_list, st_kb;
+  int64_t i0 = 0;
+  while (i0 < ns) {
+    const int64_t i1 = next_batch(hk, ns, i0, max_states, &kb_list, &st_kb);
+    const int S = (int)(i1 - i0);
+    const int nkb = (int)kb_list.size();
+    void *d_kb, *d_stkb;
+    TRY(upload(c, "tc_batch_k", kb_list.data(), sizeof(int) * nkb, &d_kb));
+    TRY(upload(c, "tc_batch_stkb", st_kb.data(), sizeof(int) * S, &d_stkb));
+    tm.begin(c);
+    float2* Tb;
+    TRY((stage1_batch<FMT, NSPLIT, NPROD>(c, gm, kb_list, st_kb, i0, st_k, st_b, UF, Pg, sA1, cis_k, gk, err, tmaxp,
+                                          (const int*)d_kb, (const int*)d_stkb, &Tb)));
+    const int64_t ncols = (int64_t)S * cps;
+    Parts PB;
+    TRY(ensure_parts(c, "tc_B2", NSPLIT, (size_t)ncols * Kp2, esz, &PB));
+    for (int i = 0; i < NSPLIT; ++i) CK(c, cudaMemsetAsync(PB.p[i], 0, (size_t)ncols * Kp2 * esz, c->stream));
+    {
+      int64_t nt = (int64_t)S * nRp * nm * nw;
+      k_split_t<FMT, NSPLIT><<<(unsigned)((nt + 255) / 256), 256, 0, c->stream>>>(Tb, S, nRp, nw, nm, Kp2, tmaxp, PB);
+      c->launches++;
+      CK(c, cudaGetLastError());
+    }
+    tm.end(c, &c->stats.stage1_ms);
+    CUtensorMap tB[3];
+    TRY(part_maps(c, tB, PB, NSPLIT, FMT, Kp2, ncols, StoreEpi::BN));
+    const int64_t qc = std::max<int64_t>(128, std::min<int64_t>(Mrows, g_budget / (4 * ncols) / 128 * 128));
+    float* G = (float*)ensure(c, "tcg_G", sizeof(float) * qc * ncols, &st);
+    if (!G) return st;
+    for (int64_t q0 = 0; q0 < Mrows; q0 += qc) {
+      const int64_t rows = std::min(qc, Mrows - q0);
+      Parts PAc;
+      for (int i = 0; i < 3; ++i)
+        PAc.p[i] = PAq.p[i] ? static_cast<uint8_t*>(PAq.p[i]) + (size_t)q0 * Kp2 * esz : nullptr;
+      CUtensorMap tA[3];
+      TRY(part_maps(c, tA, PAc, NSPLIT, FMT, Kp2, rows, 128 / kClusterN));
+      tm.begin(c);
+      TcGemmArgs a;
+      a.m_tiles = (int)(rows / 128);
+      a.n_tiles = (int)((ncols + StoreEpi::BN - 1) / StoreEpi::BN);
+      a.kblocks = Kp2 / KB;
+      a.kb_per_chunk = PHX_KB_PER_CHUNK;
+      a.b_row_step = StoreEpi::BN;
+      a.group_m = std::min(a.m_tiles, 16);
+      a.ntiles = a.m_tiles * a.n_tiles;
+      a.tile_list = nullptr;
+      a.ntiles_dev = nullptr;
+      a.err = err;
+      StoreEpi::Params ep{G, ncols, (int)rows, (int)ncols};
+      TRY(launch_gemm<StoreEpi, FMT, NSPLIT, NPROD>(c, tA, tB, a, ep));
+      c->stats.stage2_launches++;
+      tm.end(c, &c->stats.stage2_ms);
+      tm.begin(c);
+      ElphGenericArgs e;
+      e.G = G;
+      e.ldg = ncols;
+      e.q_of_row = (const int*)d_qrow;
+      e.row0 = q0;
+      e.S = S;
+      e.st_k = st_k + i0;
+      e.st_b = st_b + i0;
+      e.epsF = epsF;
+      e.gm = gm;
+      e.nw = nw;
+      e.nm = nm;
+      e.eps2 = eps2;
+      e.f32 = f32;
+      e.UH = UH;
+      e.Zf = Zf;
+      e.omf = omf;
+      e.nBf = nBf;
+      e.reach = (float)(omega_max + p->delta_cut_sigmas * p->sigma_eV) * 1.0001f;
+      e.inv_sigma = (float)(1.0 / p->sigma_eV);
+      e.cut2 = (float)(p->delta_cut_sigmas * p->delta_cut_sigmas);
+      e.scale_base = (2.0 * kPi / (double)Nq) / (kSqrtPi * p->sigma_eV) / ((double)sA2 * (double)sA2);
+      e.tmax = tmaxp;
+      e.gamma = raw;
+      e.s_base = i0;
+      if (launch_elph_generic(c->stream, e, rows) != 0) {
+        cudaGetLastError();
+        return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the generic stage-2 epilogue failed");
+      }
+      c->launches++;
+      tm.end(c, &c->stats.delta_ms);
+    }
+    i0 = i1;
+  }
+  int herr = 0;
+  CK(c, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (herr) return fail(c, PHOEBE_GPU_ERR_TIMEOUT, "a tensor-core pipeline wait ran out; results discarded");
+  c->stats.pairs_executed = ns * Nq;
+  c->stats.stage2_flops = 8.0 * (double)ns * Nq * nRp * nw * nm;
+  return PHOEBE_GPU_OK;
+}
+
+template <int NW, int NM, int FMT, int NSPLIT, int NPROD>
+static int run_tc_typed(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& gm, int64_t ns,
+                        const std::vector<int>& hk, const int* st_k, const int* st_b, const double* epsF,
+                        const cplx* UF, const double* fF, const double* omega, const double* nB, const cplx* Zq,
+                        double* raw) {
+  const int nw = NW, nm = NM, nRe = c->nRe, nRp = c->nRp;
+  const int esz = FMT == 2 ? 4 : 2;
+  const int KB = 128 / esz;  // elements per 128-byte K block
+  const int Kp1 = (2 * nRe + KB - 1) / KB * KB, Kp2 = (2 * nRp + KB - 1) / KB * KB;
+  const int64_t C = (int64_t)nRp * nw * nw * nm;
+  const int64_t NF = (int64_t)gm.nf[0] * gm.nf[1] * gm.nf[2];
+  const int64_t Nq = (int64_t)gm.nq[0] * gm.nq[1] * gm.nq[2];
+  int st;
+  Timer tm;
+  int* err = (int*)ensure(c, "tc_err", 64, &st);
+  if (!err) return st;
+  CK(c, cudaMemsetAsync(err, 0, 64, c->stream));
+  const float sA1 = host_pow2_scale(c->we_max), sA2 = host_pow2_scale(c->wp_max);
+
+  TRY((ensure_g_operand<FMT, NSPLIT>(c, C, Kp1, esz)));
   Parts Pg{{c->tc->g_part[0], c->tc->g_part[1], c->tc->g_part[2]}};
 
   // FP32 epilogue tables
@@ -1490,6 +1692,24 @@ static int run_tc_mode(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const 
 #undef PHX_RUN
 }
 
+static int run_tc_generic_mode(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& gm, int64_t ns,
+                               const std::vector<int>& hk, const int* st_k, const int* st_b, const double* epsF,
+                               const cplx* UF, const double* fF, const double* omega, const double* nB,
+                               const cplx* Zq, double* raw) {
+#define PHX_RUNG(FMT_, NS_, NP_) \
+  return run_tc_generic<FMT_, NS_, NP_>(c, p, gm, ns, hk, st_k, st_b, epsF, UF, fF, omega, nB, Zq, raw)
+  switch (p->precision) {
+    case PHOEBE_PREC_SPLIT_BF16: PHX_RUNG(1, 3, 6);
+    case PHOEBE_PREC_SPLIT_TF32: PHX_RUNG(2, 2, 3);
+    case PHOEBE_PREC_BF16: PHX_RUNG(1, 1, 1);
+    case PHOEBE_PREC_TF32: PHX_RUNG(2, 1, 1);
+    case PHOEBE_PREC_SPLIT_FP16: PHX_RUNG(0, 2, 3);
+    case PHOEBE_PREC_BF16X3: PHX_RUNG(1, 2, 3);
+    default: return fail(c, PHOEBE_GPU_ERR_ARG, "unknown precision %d", p->precision);
+  }
+#undef PHX_RUNG
+}
+
 int run_tc(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& gm, int64_t ns,
            const std::vector<int>& hk, const int* st_k, const int* st_b, const double* epsF, const cplx* UF,
            const double* fF, const double* omega, const double* nB, const cplx* Zq, double* raw) {
@@ -1498,8 +1718,10 @@ int run_tc(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& gm,
   if (nw == 8 && nm == 6) return run_tc_mode<8, 6>(c, p, gm, ns, hk, st_k, st_b, epsF, UF, fF, omega, nB, Zq, raw);
   if (nw == 2 && nm == 3) return run_tc_mode<2, 3>(c, p, gm, ns, hk, st_k, st_b, epsF, UF, fF, omega, nB, Zq, raw);
   if (nw == 1 && nm == 3) return run_tc_mode<1, 3>(c, p, gm, ns, hk, st_k, st_b, epsF, UF, fF, omega, nB, Zq, raw);
-  return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED,
-              "tensor-core precisions are built for (nw, 3na) in {(8,6), (2,3), (1,3)}; got (%d, %d)", nw, nm);
+  if (c->isreq)
+    return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED,
+                "sampled q sums are built for (nw, 3na) in {(8,6), (2,3), (1,3)}; got (%d, %d)", nw, nm);
+  return run_tc_generic_mode(c, p, gm, ns, hk, st_k, st_b, epsF, UF, fF, omega, nB, Zq, raw);
 }
 
 }  // namespace phx
