@@ -9,8 +9,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libphoebe_gpu.so")
-SOURCES = ["api.cu", "pipeline.cu", "bands.cu", "couple_fp64.cu", "tc_gemm.cu", "noalloc.cu", "sampler.cu"]
-HEADERS = ["common.cuh", "kernels.cuh", "pipeline.h", "tc.h", "tc_ptx.cuh", "sampler.h"]
+SOURCES = ["api.cu", "pipeline.cu", "bands.cu", "couple_fp64.cu", "tc_gemm.cu", "noalloc.cu", "sampler.cu", "generic.cu"]
+HEADERS = ["common.cuh", "kernels.cuh", "pipeline.h", "tc.h", "tc_ptx.cuh", "sampler.h", "generic.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -34,7 +34,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
     srcs = [os.path.join(CSRC, f) for f in SOURCES]
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "--shared", "-Xcompiler", "-fPIC",
+    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "--shared", "-Xcompiler", "-fPIC", "-Xlinker", "--no-undefined",
            "-Xptxas", "-v" if verbose else "-O3", "-o", LIB + ".tmp", *srcs]
     proc = subprocess.run(cmd, capture_output=True, text=True)
     if proc.returncode != 0:

@@ -85,7 +85,7 @@ struct StoreEpi {
     if (grow >= p.M) return;
     const int64_t gcol0 = (int64_t)n * BN + wg * BNW;
     float* dst = p.C + grow * p.ldc + gcol0;
-    if (gcol0 + BNW <= p.N) {
+    if (gcol0 + BNW <= p.N && (p.ldc & 3) == 0) {  // 16-byte aligned rows: vector stores
 #pragma unroll
       for (int i = 0; i < BNW; i += 4) *reinterpret_cast<float4*>(dst + i) = make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
     } else {
@@ -1095,9 +1095,10 @@ static int stage1_batch(phoebe_gpu_ctx* c, const GridMap& gm, const std::vector<
   const int BN1 = StoreEpi::BN;
   const int S = (int)st_kb.size(), nkb = (int)kb_list.size();
   int st;
+  const int64_t ldx = (2 * C + 3) / 4 * 4;  // row stride of X, 16-byte aligned
   Parts PAk;
   TRY(ensure_parts(c, "tc_Ak", NSPLIT, (size_t)nkb * Kp1, esz, &PAk));
-  float* X = (float*)ensure(c, "tc_X", sizeof(float) * nkb * 2 * C, &st);
+  float* X = (float*)ensure(c, "tc_X", sizeof(float) * nkb * ldx, &st);
   if (!X) return st;
   {
     int64_t nt = (int64_t)nkb * (Kp1 / 2);
@@ -1121,7 +1122,7 @@ static int stage1_batch(phoebe_gpu_ctx* c, const GridMap& gm, const std::vector<
     a.tile_list = nullptr;
     a.ntiles_dev = nullptr;
     a.err = err;
-    StoreEpi::Params ep{X, 2 * C, nkb, (int)(2 * C)};
+    StoreEpi::Params ep{X, ldx, nkb, (int)(2 * C)};
     TRY(launch_gemm<StoreEpi, FMT, NSPLIT, NPROD>(c, tAk, tG, a, ep));
   }
   float2* Tb = (float2*)ensure(c, "tc_T", sizeof(float2) * (size_t)S * nRp * nm * nw, &st);
@@ -1130,7 +1131,7 @@ static int stage1_batch(phoebe_gpu_ctx* c, const GridMap& gm, const std::vector<
   {
     int64_t nt = (int64_t)S * nRp * nm * nw;
     const float unscale1 = 1.0f / (sA1 * c->tc->g_scale);
-    k_pack_t<<<(unsigned)((nt + 255) / 256), 256, 0, c->stream>>>(X, 2 * C, unscale1, d_stkb, st_k + i0, st_b + i0,
+    k_pack_t<<<(unsigned)((nt + 255) / 256), 256, 0, c->stream>>>(X, ldx, unscale1, d_stkb, st_k + i0, st_b + i0,
                                                                    gm, UF, S, nRp, nw, nm, Tb, tmaxp);
     c->launches++;
     CK(c, cudaGetLastError());
@@ -1302,8 +1303,9 @@ static int run_tc_generic(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, con
     tm.end(c, &c->stats.stage1_ms);
     CUtensorMap tB[3];
     TRY(part_maps(c, tB, PB, NSPLIT, FMT, Kp2, ncols, StoreEpi::BN));
-    const int64_t qc = std::max<int64_t>(128, std::min<int64_t>(Mrows, g_budget / (4 * ncols) / 128 * 128));
-    float* G = (float*)ensure(c, "tcg_G", sizeof(float) * qc * ncols, &st);
+    const int64_t ldg = (ncols + 3) / 4 * 4;  // row stride of G, 16-byte aligned
+    const int64_t qc = std::max<int64_t>(128, std::min<int64_t>(Mrows, g_budget / (4 * ldg) / 128 * 128));
+    float* G = (float*)ensure(c, "tcg_G", sizeof(float) * qc * ldg, &st);
     if (!G) return st;
     for (int64_t q0 = 0; q0 < Mrows; q0 += qc) {
       const int64_t rows = std::min(qc, Mrows - q0);
@@ -1324,14 +1326,14 @@ static int run_tc_generic(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, con
       a.tile_list = nullptr;
       a.ntiles_dev = nullptr;
       a.err = err;
-      StoreEpi::Params ep{G, ncols, (int)rows, (int)ncols};
+      StoreEpi::Params ep{G, ldg, (int)rows, (int)ncols};
       TRY(launch_gemm<StoreEpi, FMT, NSPLIT, NPROD>(c, tA, tB, a, ep));
       c->stats.stage2_launches++;
       tm.end(c, &c->stats.stage2_ms);
       tm.begin(c);
       ElphGenericArgs e;
       e.G = G;
-      e.ldg = ncols;
+      e.ldg = ldg;
       e.q_of_row = (const int*)d_qrow;
       e.row0 = q0;
       e.S = S;
@@ -1538,9 +1540,10 @@ static int run_tc_typed(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const
 
     // ---- stage 1: X[kb][2C] = sum_Re phases * g   (tensor cores, StoreEpi)
     tm.begin(c);
+    const int64_t ldx = (2 * C + 3) / 4 * 4;  // row stride of X, 16-byte aligned
     Parts PAk;
     TRY(ensure_parts(c, "tc_Ak", NSPLIT, (size_t)nkb * Kp1, esz, &PAk));
-    float* X = (float*)ensure(c, "tc_X", sizeof(float) * nkb * 2 * C, &st);
+    float* X = (float*)ensure(c, "tc_X", sizeof(float) * nkb * ldx, &st);
     if (!X) return st;
     {
       int64_t nt = (int64_t)nkb * (Kp1 / 2);
@@ -1565,7 +1568,7 @@ static int run_tc_typed(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const
       a.tile_list = nullptr;
       a.ntiles_dev = nullptr;
       a.err = err;
-      StoreEpi::Params ep{X, 2 * C, nkb, (int)(2 * C)};
+      StoreEpi::Params ep{X, ldx, nkb, (int)(2 * C)};
       TRY(launch_gemm<StoreEpi, FMT, NSPLIT, NPROD>(c, tAk, tG, a, ep));
     }
     // ---- U_k rotation -> T (FP32), then the scaled split stage-2 B operand
@@ -1579,7 +1582,7 @@ static int run_tc_typed(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const
     {
       int64_t nt = (int64_t)S * nRp * nm * nw;
       const float unscale1 = 1.0f / (sA1 * c->tc->g_scale);
-      k_pack_t<<<(unsigned)((nt + 255) / 256), 256, 0, c->stream>>>(X, 2 * C, unscale1, (const int*)d_stkb, st_k + i0,
+      k_pack_t<<<(unsigned)((nt + 255) / 256), 256, 0, c->stream>>>(X, ldx, unscale1, (const int*)d_stkb, st_k + i0,
                                                                      st_b + i0, gm, UF, S, nRp, nw, nm, Tb, tmaxp);
       k_split_t<FMT, NSPLIT><<<(unsigned)((nt + 255) / 256), 256, 0, c->stream>>>(Tb, S, nRp, nw, nm, Kp2, tmaxp, PB);
       c->launches += 2;

@@ -299,34 +299,43 @@ def tb_einstein(eps0: float = 0.0, t: float = 0.25, lam: float = 0.215,
                           sigma_eV=sigma, window_eV=0.0)
 
 
-def batch_material(index: int, seed: int = 0) -> tuple[Material, RTAParams]:
-    """One of the uneven materials of the batching workload.
+def material_of_shape(name: str, nw: int, na: int, nR_target: int, n: int, rng: np.random.Generator,
+                      g_budget_bytes: float = 256e6) -> tuple[Material, RTAParams]:
+    """A crystal of a given shape built by the Si-like rules (fcc lattice, decaying seeded H and g).
 
-    Shape draws (uniform, seeded by (seed, index)): nw in [4,24], na in [1,6],
-    target |R| count in [100,1200] (nearest whole-shell cut of the fcc 8^3
-    Wigner-Seitz set, 617 vectors max, else of the 12^3 set), grid n in [16,40].
-    Atoms sit at seeded positions in the fcc cell; springs between all atom
-    pairs closer than 0.5 a with constants uniform in [2,12] eV/A^2.
+    H(R) and the force constants use the whole-shell cut of the fcc Wigner-Seitz set (8^3
+    supercell, 617 vectors, else 12^3) nearest to nR_target vectors.  The el-ph coupling
+    g(Re,Rp) uses the largest whole-shell prefix of that set whose complex128 tensor
+    (nRe * nRp * nw^2 * 3na * 16 bytes) stays within g_budget_bytes (at least R = 0): a
+    1200-vector set with 24 Wannier functions and 6 atoms would need 239 GB.
+    Atoms sit at seeded positions in the fcc cell, >= 0.2 a apart; springs between every
+    distinct bond length below 0.75 a with constants uniform in [2,12] eV/A^2.
+    Grid n^3 for k and q, T = 300 K, sigma = 0.02 eV, window +-0.5 eV around mu = tr H(0)/nw.
     """
-    rng = np.random.default_rng([seed, index])
-    nw = int(rng.integers(4, 25))
-    na = int(rng.integers(1, 7))
-    nR_target = int(rng.integers(100, 1201))
-    n = int(rng.integers(16, 41))
     a = SI_A
     lat = 0.5 * a * np.array([[0, 1, 1], [1, 0, 1], [1, 1, 0]], dtype=np.float64)
     nsup = 8 if nR_target <= 617 else 12
     Rall, _ = wigner_seitz_set(lat, nsup)
     Lall = np.linalg.norm(Rall @ lat, axis=1)
-    shells = np.unique(np.round(Lall, 6))
-    counts = np.array([np.sum(np.round(Lall, 6) <= s) for s in shells])
+    Lr = np.round(Lall, 6)
+    shells = np.unique(Lr)
+    counts = np.array([np.sum(Lr <= s) for s in shells])
     cut = shells[int(np.argmin(np.abs(counts - nR_target)))]
-    sel = np.round(Lall, 6) <= cut
+    order = np.argsort(Lr, kind="stable")
+    Rall, Lall, Lr = Rall[order], Lall[order], Lr[order]
+    sel = Lr <= cut
     R = Rall[sel]
     L = Lall[sel]
     minus = _minus_index(R)
+    per_pair = float(nw * nw * 3 * na * 16)
+    g_cut = shells[0]
+    for sh, cnt in zip(shells, counts):
+        if sh <= cut and cnt * cnt * per_pair <= g_budget_bytes:
+            g_cut = sh
+    gsel = np.round(L, 6) <= g_cut
+    Rg, Lg = R[gsel], L[gsel]
+    minus_g = _minus_index(Rg)
     ell = 0.7 * a / np.sqrt(2.0)
-    # atoms: a seeded arrangement inside the cell, kept >= 0.2 a apart
     pos = [np.zeros(3)]
     while len(pos) < na:
         p = rng.uniform(0.0, 1.0, 3) @ lat
@@ -336,11 +345,10 @@ def batch_material(index: int, seed: int = 0) -> tuple[Material, RTAParams]:
     mass = rng.uniform(10.0, 120.0, na)
     XH = _cnormal(rng, (len(R), nw, nw)) * np.exp(-L / ell)[:, None, None]
     H = _hermitian_pair_sym(XH, minus)
-    Xg = _cnormal(rng, (len(R), len(R), nw, nw, 3 * na))
-    Xg *= np.exp(-(L[:, None] + L[None, :]) / ell)[:, :, None, None, None]
-    g = _coupling_sym(Xg, minus, minus)
+    Xg = _cnormal(rng, (len(Rg), len(Rg), nw, nw, 3 * na))
+    Xg *= np.exp(-(Lg[:, None] + Lg[None, :]) / ell)[:, :, None, None, None]
+    g = _coupling_sym(Xg, minus_g, minus_g)
     del Xg
-    # springs: every distinct bond length below 0.75 a gets a seeded constant
     bonds = set()
     for R3 in itertools.product(range(-2, 3), repeat=3):
         Rc = np.array(R3, dtype=float) @ lat
@@ -352,8 +360,25 @@ def batch_material(index: int, seed: int = 0) -> tuple[Material, RTAParams]:
     springs = [(b, float(rng.uniform(2.0, 12.0))) for b in sorted(bonds)]
     Rf, wf, Phi = _central_springs(lat, pos, springs, search=2)
     w = np.ones(len(R))
-    mat = Material(f"batch{index}", nw, na, mass, lat, pos, R.astype(np.int32), w, H,
-                   Rf, wf, Phi, R.astype(np.int32), w.copy(), R.astype(np.int32), w.copy(), g)
+    wg = np.ones(len(Rg))
+    mat = Material(name, nw, na, mass, lat, pos, R.astype(np.int32), w, H,
+                   Rf, wf, Phi, Rg.astype(np.int32), wg, Rg.astype(np.int32), wg.copy(), g)
     mu = float(np.real(np.trace(H[_index_of(R)[(0, 0, 0)]])) / nw)
     return mat, RTAParams(nk=(n, n, n), nq=(n, n, n), T_K=300.0, mu_eV=mu,
                           sigma_eV=0.02, window_eV=0.5)
+
+
+def batch_shape(index: int, seed: int = 0) -> tuple[int, int, int, int]:
+    """Shape (nw, na, nR_target, n) of material `index` of the batching workload: uniform draws
+    nw in [4,24], na in [1,6], |R| in [100,1200], grid n in [16,40], seeded by (seed, index)."""
+    rng = np.random.default_rng([seed, index])
+    return (int(rng.integers(4, 25)), int(rng.integers(1, 7)), int(rng.integers(100, 1201)),
+            int(rng.integers(16, 41)))
+
+
+def batch_material(index: int, seed: int = 0, g_budget_bytes: float = 256e6) -> tuple[Material, RTAParams]:
+    """One of the uneven materials of the batching workload (shape from ``batch_shape``)."""
+    rng = np.random.default_rng([seed, index])
+    nw, na, nR_target, n = (int(rng.integers(4, 25)), int(rng.integers(1, 7)), int(rng.integers(100, 1201)),
+                            int(rng.integers(16, 41)))
+    return material_of_shape(f"batch{index}", nw, na, nR_target, n, rng, g_budget_bytes)
