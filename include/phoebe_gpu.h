@@ -255,6 +255,45 @@ int phoebe_gpu_mlp_loss_grad(phoebe_gpu_ctx* ctx, int64_t n_rows, const float* x
 /* The uniforms u_j, j < n, of the draws for k-grid index k (as described above), host double [n]. */
 int phoebe_gpu_is_uniforms(phoebe_gpu_ctx* ctx, uint64_t seed, int32_t k, int64_t n, double* u);
 
+/* ------------------------------------------------------------------------------------------
+ * Many materials in one call.  The paper has no counterpart (it treats one crystal per run).
+ * Each item names a context holding one material (set_* done; all contexts on one device)
+ * and its parameters (precision 1..6, sampler FULL).  Phase 1 runs, per material on its own
+ * context and stream, the grid band structure, phonons, window, stage 1 and the stage-2
+ * operands, and records the material's stage-2 launches; with autotune on, the tile width
+ * (128 or 256 columns) and the K blocks per TMEM partial (1, 2 or 4) of its stage-2 GEMM are
+ * chosen by timing each candidate once on the material's first q chunk.  Phase 2 captures
+ * the recorded launches of all materials into one CUDA graph (materials spread round-robin
+ * over n_streams parallel branches) and launches it once.  Phase 3 averages degenerate
+ * bands and writes each item's host outputs as linewidths_rta does.  Every shape uses the
+ * stage 2 that writes G to HBM (the fused epilogue is not used in a batch); all of a
+ * material's active states form one batch, so its operands must fit in device memory.
+ * Two-call pattern: if any gamma_eV is NULL, only every n_states is written. */
+typedef struct {
+  phoebe_gpu_ctx* ctx;                  /* the material */
+  const phoebe_gpu_rta_params* params;
+  int n_states;                         /* in: output capacity; out: active states */
+  int32_t* k_index;                     /* host outputs (may be NULL) */
+  int32_t* band;
+  double* gamma_eV;
+  int tile_n, tile_kb;                  /* out: stage-2 tile columns and K blocks per partial used */
+} phoebe_gpu_batch_item;
+
+typedef struct {
+  int autotune;              /* 1: time the tile candidates per material (default 1) */
+  int n_streams;             /* parallel branches of the graph, 1..64 (default 4) */
+  int64_t g_chunk_bytes;     /* stage-2 result buffer per material and q chunk (default 128 MiB) */
+  double plan_ms;            /* out: phase 1 wall time (including the autotuner) */
+  double graph_ms;           /* out: device time of the graph launch (every material's stage 2) */
+  double finish_ms;          /* out: phase 3 wall time */
+  int64_t graph_nodes;       /* out: nodes of the captured graph */
+  int64_t recorded_launches; /* out: recorded stage-2 chunks (each a GEMM and an epilogue launch) */
+  int reserved[4];           /* must be zero */
+} phoebe_gpu_batch_opts;
+
+void phoebe_gpu_batch_opts_default(phoebe_gpu_batch_opts* o);
+int phoebe_gpu_linewidths_rta_batch(phoebe_gpu_batch_item* items, int n, phoebe_gpu_batch_opts* opts);
+
 /* Allocation-free band energies at explicit k points.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory -- host
  * programs sharing the GPU with a framework that has already reserved nearly all of

@@ -35,6 +35,7 @@ EXPORTED = (
     "phoebe_gpu_sampler_init", "phoebe_gpu_sampler_load", "phoebe_gpu_sampler_save",
     "phoebe_gpu_train_opts_default", "phoebe_gpu_sampler_train", "phoebe_gpu_q_contributions",
     "phoebe_gpu_mlp_loss_grad", "phoebe_gpu_is_uniforms",
+    "phoebe_gpu_batch_opts_default", "phoebe_gpu_linewidths_rta_batch",
 )
 
 
@@ -64,6 +65,23 @@ class TrainOpts(C.Structure):
         ("epochs", C.c_int), ("states_per_step", C.c_int),
         ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
         ("seed", C.c_uint64),
+        ("reserved", C.c_int * 4),
+    ]
+
+
+class BatchItem(C.Structure):
+    _fields_ = [
+        ("ctx", C.c_void_p), ("params", C.c_void_p), ("n_states", C.c_int),
+        ("k_index", C.c_void_p), ("band", C.c_void_p), ("gamma_eV", C.c_void_p),
+        ("tile_n", C.c_int), ("tile_kb", C.c_int),
+    ]
+
+
+class BatchOpts(C.Structure):
+    _fields_ = [
+        ("autotune", C.c_int), ("n_streams", C.c_int), ("g_chunk_bytes", C.c_int64),
+        ("plan_ms", C.c_double), ("graph_ms", C.c_double), ("finish_ms", C.c_double),
+        ("graph_nodes", C.c_int64), ("recorded_launches", C.c_int64),
         ("reserved", C.c_int * 4),
     ]
 
@@ -111,6 +129,8 @@ def _load() -> C.CDLL:
         "phoebe_gpu_q_contributions": (I, [P, C.POINTER(RTAParams), C.POINTER(I), P, P, P, P]),
         "phoebe_gpu_mlp_loss_grad": (I, [P, I64, P, I, P, P, P, P, P]),
         "phoebe_gpu_is_uniforms": (I, [P, C.c_uint64, C.c_int32, I64, P]),
+        "phoebe_gpu_batch_opts_default": (None, [C.POINTER(BatchOpts)]),
+        "phoebe_gpu_linewidths_rta_batch": (I, [C.POINTER(BatchItem), I, C.POINTER(BatchOpts)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -358,3 +378,40 @@ class PhoebeGPU:
         u = np.empty(int(n), dtype=np.float64)
         self._check(lib.phoebe_gpu_is_uniforms(self._ctx, int(seed), int(k), int(n), _ptr(u)))
         return u
+
+
+def linewidths_rta_batch(jobs, **opts):
+    """Linewidths of several materials in one call.
+
+    ``jobs``: list of (PhoebeGPU context holding the material, params).  Returns
+    (list of (k_index, band, gamma_eV) per job, dict of the batch timings and the
+    stage-2 tile shape chosen per job)."""
+    n = len(jobs)
+    params = [p if isinstance(p, RTAParams) else make_params(p) for _, p in jobs]
+    items = (BatchItem * n)()
+    for i, (ctx, _) in enumerate(jobs):
+        items[i].ctx = ctx._ctx.value
+        items[i].params = C.cast(C.pointer(params[i]), C.c_void_p).value
+    o = BatchOpts()
+    lib.phoebe_gpu_batch_opts_default(C.byref(o))
+    for key, val in opts.items():
+        setattr(o, key, type(getattr(o, key))(val))
+
+    def check(st):
+        if st != 0:
+            msgs = [lib.phoebe_gpu_last_error(ctx._ctx).decode() for ctx, _ in jobs]
+            raise PhoebeGPUError(st, "; ".join(m for m in msgs if m) or "batch failed")
+    check(lib.phoebe_gpu_linewidths_rta_batch(items, n, C.byref(o)))     # counts
+    outs = []
+    for i in range(n):
+        m = max(items[i].n_states, 1)
+        ki, bd, gm = np.empty(m, dtype=np.int32), np.empty(m, dtype=np.int32), np.empty(m)
+        outs.append((ki, bd, gm))
+        items[i].n_states = m
+        items[i].k_index, items[i].band, items[i].gamma_eV = ki.ctypes.data, bd.ctypes.data, gm.ctypes.data
+    check(lib.phoebe_gpu_linewidths_rta_batch(items, n, C.byref(o)))
+    res = [(ki[:items[i].n_states], bd[:items[i].n_states], gm[:items[i].n_states]) for i, (ki, bd, gm) in
+           enumerate(outs)]
+    info = {name: getattr(o, name) for name, _ in BatchOpts._fields_ if name != "reserved"}
+    info["tiles"] = [(items[i].tile_n, items[i].tile_kb) for i in range(n)]
+    return res, info

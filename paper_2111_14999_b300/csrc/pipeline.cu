@@ -257,6 +257,31 @@ static int run_fp64(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Gri
   return PHOEBE_GPU_OK;
 }
 
+// Degenerate averaging (a12) of the raw accumulator into the outputs.
+static int finish_outputs(phoebe_gpu_ctx* c, const GridMap& gm, int64_t ns, double degen_tol, int32_t* k_index,
+                          int32_t* band, double* gamma, bool device_out) {
+  int st;
+  const int nw = c->nw;
+  const double* raw = (const double*)c->bufs["gamma_raw"].p;
+  const int* st_k = (const int*)c->bufs["st_k"].p;
+  const int* st_b = (const int*)c->bufs["st_b"].p;
+  const double* epsF = (const double*)c->bufs["epsF"].p;
+  double* out = gamma;
+  if (!device_out) {
+    out = (double*)ensure(c, "gamma_out", sizeof(double) * ns, &st);
+    if (!out) return st;
+  }
+  k_degenerate_average<<<(unsigned)((ns + 255) / 256), 256, 0, c->stream>>>(raw, st_k, st_b, ns, epsF, gm, nw,
+                                                                            degen_tol, out);
+  TRY(launch_check(c, 1));
+  cudaMemcpyKind kind = device_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (!device_out) CK(c, cudaMemcpyAsync(gamma, out, sizeof(double) * ns, kind, c->stream));
+  if (k_index) CK(c, cudaMemcpyAsync(k_index, st_k, sizeof(int) * ns, kind, c->stream));
+  if (band) CK(c, cudaMemcpyAsync(band, st_b, sizeof(int) * ns, kind, c->stream));
+  if (!device_out) CK(c, cudaStreamSynchronize(c->stream));
+  return PHOEBE_GPU_OK;
+}
+
 namespace {
 // Installs an importance-sampling request for one call when the parameters ask for one.
 struct IsGuard {
@@ -370,28 +395,32 @@ int linewidths(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, int* n_states,
   double* raw = (double*)ensure(c, "gamma_raw", sizeof(double) * ns, &st);
   if (!raw) return st;
   CK(c, cudaMemsetAsync(raw, 0, sizeof(double) * ns, c->stream));
+  if (c->defer && p->precision == PHOEBE_PREC_FP64)
+    return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "batched linewidths need a tensor-core precision (1..6)");
   if (p->precision == PHOEBE_PREC_FP64) {
     TRY(run_fp64(c, p, gm, ns, hk, st_k, st_b, epsF, UF, fF, omega, nB, Zq, raw));
   } else {
     TRY(run_tc(c, p, gm, ns, hk, st_k, st_b, epsF, UF, fF, omega, nB, Zq, raw));
   }
   c->stats.couplings_executed = c->stats.pairs_executed * nw * nm;
-  double* out = gamma;
-  if (!device_out) {
-    out = (double*)ensure(c, "gamma_out", sizeof(double) * ns, &st);
-    if (!out) return st;
+  if (c->defer) {  // stage 2 recorded, not run: finish later
+    c->defer->ns = ns;
+    c->defer->gm = gm;
+    c->defer->degen_tol = p->degen_tol_eV;
+    total.end(c, &c->stats.total_ms);
+    c->stats.kernel_launches = c->launches;
+    return PHOEBE_GPU_OK;
   }
-  k_degenerate_average<<<(unsigned)((ns + 255) / 256), 256, 0, c->stream>>>(raw, st_k, st_b, ns, epsF, gm, nw,
-                                                                            p->degen_tol_eV, out);
-  TRY(launch_check(c, 1));
-  cudaMemcpyKind kind = device_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  if (!device_out) CK(c, cudaMemcpyAsync(gamma, out, sizeof(double) * ns, kind, c->stream));
-  if (k_index) CK(c, cudaMemcpyAsync(k_index, st_k, sizeof(int) * ns, kind, c->stream));
-  if (band) CK(c, cudaMemcpyAsync(band, st_b, sizeof(int) * ns, kind, c->stream));
-  if (!device_out) CK(c, cudaStreamSynchronize(c->stream));
+  TRY(finish_outputs(c, gm, ns, p->degen_tol_eV, k_index, band, gamma, device_out));
   total.end(c, &c->stats.total_ms);
   c->stats.kernel_launches = c->launches;
   return PHOEBE_GPU_OK;
+}
+
+int linewidths_finish(phoebe_gpu_ctx* c, int32_t* k_index, int32_t* band, double* gamma, bool device_out) {
+  if (!c->defer) return fail(c, PHOEBE_GPU_ERR_ORDER, "no deferred linewidth call to finish");
+  if (c->defer->ns == 0) return PHOEBE_GPU_OK;
+  return finish_outputs(c, c->defer->gm, c->defer->ns, c->defer->degen_tol, k_index, band, gamma, device_out);
 }
 
 }  // namespace phx

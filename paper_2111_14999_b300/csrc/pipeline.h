@@ -1,6 +1,7 @@
 // Host-side context and orchestration interfaces of the phoebe_gpu library.
 #pragma once
 
+#include <functional>
 #include <map>
 #include <string>
 #include <vector>
@@ -40,6 +41,22 @@ struct phoebe_gpu_ctx {
   int64_t adam_t = 0;
   // set by the sampler entry points for the duration of one pipeline call
   struct IsRequest* isreq = nullptr;
+  // set by the batch entry point: stage 2 is recorded instead of launched
+  struct Deferred* defer = nullptr;
+};
+
+// Stage-2 work of one material recorded for later issue (batch.cu): each op launches
+// on the context's stream at the time it is called, so a caller can capture it.
+struct Deferred {
+  std::vector<std::function<int()>> ops;
+  bool autotune = true;
+  int bn = 0, kb = 0;              // stage-2 tile columns and K blocks per TMEM partial (0: default)
+  int64_t g_budget = (int64_t)128 << 20;  // bytes of the G buffer per q chunk
+  double tune_ms[6] = {0, 0, 0, 0, 0, 0};  // candidates (bn, kb) in {128, 256} x {1, 2, 4}
+  // what the finishing step needs
+  int64_t ns = 0;
+  phx::GridMap gm{};
+  double degen_tol = 0.0;
 };
 
 // What the sampled q sums of one pipeline call must produce (sampler.cu).
@@ -90,6 +107,9 @@ int phonon_modes(phoebe_gpu_ctx* c, const int n[3], const double* qpts_dev, int6
 
 int linewidths(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, int* n_states, int32_t* k_index,
                int32_t* band, double* gamma, bool device_out);
+// Degenerate averaging of the raw accumulator of the last (deferred) linewidths call and the
+// copy of its outputs.
+int linewidths_finish(phoebe_gpu_ctx* c, int32_t* k_index, int32_t* band, double* gamma, bool device_out);
 int interpolate_pairs(phoebe_gpu_ctx* c, int n_pairs, const double* k, const double* q, int precision,
                       double* g2, double* eps_k, double* eps_kq, double* omega_q);
 

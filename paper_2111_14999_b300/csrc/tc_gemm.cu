@@ -67,16 +67,19 @@ struct TcGemmArgs {
 
 // Epilogues receive the finished FP32 tile row of their thread in registers (acc[BN],
 // column c of the tile = acc[c]) and the tile coordinates.
-struct StoreEpi {
-  static constexpr int BNW = 128;      // columns per epilogue warpgroup
+struct StoreParams {
+  float* C;
+  int64_t ldc;
+  int M, N;  // valid rows / columns of C
+};
+
+template <int BNW_>
+struct StoreEpiT {
+  static constexpr int BNW = BNW_;     // columns per epilogue warpgroup
   static constexpr int BN = 2 * BNW;   // MMA N
   static constexpr uint32_t SMEM_BYTES = 0;
   struct Pre {};
-  struct Params {
-    float* C;
-    int64_t ldc;
-    int M, N;  // valid rows / columns of C
-  };
+  using Params = StoreParams;
   static __device__ __forceinline__ const void* smem_src(const Params&, int) { return nullptr; }
   static __device__ __forceinline__ void prefetch(const Params&, int, int, int, int, Pre&) {}
   static __device__ __forceinline__ void tile(const Params& p, int m, int n, int wg, int row, const float* acc,
@@ -95,6 +98,8 @@ struct StoreEpi {
     }
   }
 };
+using StoreEpi = StoreEpiT<128>;     // 256-column tiles
+using StoreEpi128 = StoreEpiT<64>;   // 128-column tiles
 
 template <int NW, int NM>
 struct ElphEpi {
@@ -1199,6 +1204,14 @@ static int run_sampled(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const 
   return PHOEBE_GPU_OK;
 }
 
+// Plain GEMM into HBM with 256- or 128-column tiles.
+template <int FMT, int NSPLIT, int NPROD>
+static int launch_store(phoebe_gpu_ctx* c, int bn, const CUtensorMap* A, const CUtensorMap* B, TcGemmArgs a,
+                        const StoreParams& ep) {
+  if (bn == 128) return launch_gemm<StoreEpi128, FMT, NSPLIT, NPROD>(c, A, B, a, ep);
+  return launch_gemm<StoreEpi, FMT, NSPLIT, NPROD>(c, A, B, a, ep);
+}
+
 // Stage 2 for any (nw, 3na): the R_p contraction G = P_q T runs as a plain tensor-core GEMM
 // into HBM, one q chunk at a time, and k_elph_generic applies U_{k+q}^dagger, Z_q and the
 // delta weights (Sec. 3.2 Eq. 13, Sec. 4.2 Eq. 29).  Exact: no screening.
@@ -1274,9 +1287,13 @@ static int run_tc_generic(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, con
   tm.end(c, &c->stats.stage1_ms);
   unsigned* tmaxp = (unsigned*)ensure(c, "tc_tmax", 64, &st);
   if (!tmaxp) return st;
-  const int64_t g_budget = (int64_t)512 << 20;  // bytes of G per q chunk
+  Deferred* df = c->defer;
+  const int64_t g_budget = df ? df->g_budget : (int64_t)512 << 20;  // bytes of G per q chunk
+  // a deferred call keeps every state in one batch: its recorded launches use the batch's buffers
   const int max_states =
-      p->max_batch_states > 0 ? p->max_batch_states : (int)std::max<int64_t>(1, std::min<int64_t>(4096, g_budget / (128 * 4 * cps)));
+      df ? (int)ns
+         : p->max_batch_states > 0 ? p->max_batch_states
+                                   : (int)std::max<int64_t>(1, std::min<int64_t>(4096, g_budget / (128 * 4 * cps)));
   std::vector<int> kb_list, st_kb;
   int64_t i0 = 0;
   while (i0 < ns) {
@@ -1301,36 +1318,76 @@ static int run_tc_generic(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, con
       CK(c, cudaGetLastError());
     }
     tm.end(c, &c->stats.stage1_ms);
-    CUtensorMap tB[3];
-    TRY(part_maps(c, tB, PB, NSPLIT, FMT, Kp2, ncols, StoreEpi::BN));
     const int64_t ldg = (ncols + 3) / 4 * 4;  // row stride of G, 16-byte aligned
     const int64_t qc = std::max<int64_t>(128, std::min<int64_t>(Mrows, g_budget / (4 * ldg) / 128 * 128));
     float* G = (float*)ensure(c, "tcg_G", sizeof(float) * qc * ldg, &st);
     if (!G) return st;
-    for (int64_t q0 = 0; q0 < Mrows; q0 += qc) {
+    // GEMM arguments of the q chunk starting at row q0 for a tile width bn and K blocks per partial kb
+    auto chunk_args = [&](int64_t q0, int bn, int kb, CUtensorMap* tA, CUtensorMap* tB, TcGemmArgs* a,
+                          StoreParams* ep) -> int {
       const int64_t rows = std::min(qc, Mrows - q0);
       Parts PAc;
       for (int i = 0; i < 3; ++i)
         PAc.p[i] = PAq.p[i] ? static_cast<uint8_t*>(PAq.p[i]) + (size_t)q0 * Kp2 * esz : nullptr;
-      CUtensorMap tA[3];
       TRY(part_maps(c, tA, PAc, NSPLIT, FMT, Kp2, rows, 128 / kClusterN));
-      tm.begin(c);
+      TRY(part_maps(c, tB, PB, NSPLIT, FMT, Kp2, ncols, (uint32_t)bn));
+      a->m_tiles = (int)(rows / 128);
+      a->n_tiles = (int)((ncols + bn - 1) / bn);
+      a->kblocks = Kp2 / KB;
+      a->kb_per_chunk = kb;
+      a->b_row_step = bn;
+      a->group_m = std::min(a->m_tiles, 16);
+      a->ntiles = a->m_tiles * a->n_tiles;
+      a->tile_list = nullptr;
+      a->ntiles_dev = nullptr;
+      a->err = err;
+      *ep = StoreParams{G, ldg, (int)rows, (int)ncols};
+      return PHOEBE_GPU_OK;
+    };
+    int bn = StoreEpi::BN, kbc = PHX_KB_PER_CHUNK;
+    if (df && df->autotune) {
+      // autotuner: time every (tile width, K blocks per partial) candidate on the first q chunk
+      static const int cand_bn[2] = {128, 256}, cand_kb[3] = {1, 2, 4};
+      cudaEvent_t e0, e1;
+      CK(c, cudaEventCreate(&e0));
+      CK(c, cudaEventCreate(&e1));
+      float best = 1e30f;
+      for (int ib = 0; ib < 2; ++ib)
+        for (int ik = 0; ik < 3; ++ik) {
+          CUtensorMap tA[3], tB[3];
+          TcGemmArgs a;
+          StoreParams ep;
+          TRY(chunk_args(0, cand_bn[ib], cand_kb[ik], tA, tB, &a, &ep));
+          TRY((launch_store<FMT, NSPLIT, NPROD>(c, cand_bn[ib], tA, tB, a, ep)));  // warm-up
+          CK(c, cudaEventRecord(e0, c->stream));
+          TRY((launch_store<FMT, NSPLIT, NPROD>(c, cand_bn[ib], tA, tB, a, ep)));
+          CK(c, cudaEventRecord(e1, c->stream));
+          CK(c, cudaEventSynchronize(e1));
+          float ms = 0.f;
+          CK(c, cudaEventElapsedTime(&ms, e0, e1));
+          df->tune_ms[ib * 3 + ik] = ms;
+          if (ms < best) {
+            best = ms;
+            bn = cand_bn[ib];
+            kbc = cand_kb[ik];
+          }
+        }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    } else if (df) {
+      if (df->bn) bn = df->bn;
+      if (df->kb) kbc = df->kb;
+    }
+    if (df) {
+      df->bn = bn;
+      df->kb = kbc;
+    }
+    for (int64_t q0 = 0; q0 < Mrows; q0 += qc) {
+      const int64_t rows = std::min(qc, Mrows - q0);
+      CUtensorMap tA[3], tB[3];
       TcGemmArgs a;
-      a.m_tiles = (int)(rows / 128);
-      a.n_tiles = (int)((ncols + StoreEpi::BN - 1) / StoreEpi::BN);
-      a.kblocks = Kp2 / KB;
-      a.kb_per_chunk = PHX_KB_PER_CHUNK;
-      a.b_row_step = StoreEpi::BN;
-      a.group_m = std::min(a.m_tiles, 16);
-      a.ntiles = a.m_tiles * a.n_tiles;
-      a.tile_list = nullptr;
-      a.ntiles_dev = nullptr;
-      a.err = err;
-      StoreEpi::Params ep{G, ldg, (int)rows, (int)ncols};
-      TRY(launch_gemm<StoreEpi, FMT, NSPLIT, NPROD>(c, tA, tB, a, ep));
-      c->stats.stage2_launches++;
-      tm.end(c, &c->stats.stage2_ms);
-      tm.begin(c);
+      StoreParams ep;
+      TRY(chunk_args(q0, bn, kbc, tA, tB, &a, &ep));
       ElphGenericArgs e;
       e.G = G;
       e.ldg = ldg;
@@ -1356,6 +1413,31 @@ static int run_tc_generic(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, con
       e.tmax = tmaxp;
       e.gamma = raw;
       e.s_base = i0;
+      if (df) {
+        struct Maps {
+          CUtensorMap A[3], B[3];
+        } mp;
+        for (int i = 0; i < 3; ++i) {
+          mp.A[i] = tA[i];
+          mp.B[i] = tB[i];
+        }
+        df->ops.push_back([c, mp, a, ep, e, rows, bn]() -> int {
+          TRY((launch_store<FMT, NSPLIT, NPROD>(c, bn, mp.A, mp.B, a, ep)));
+          if (launch_elph_generic(c->stream, e, rows) != 0) {
+            cudaGetLastError();
+            return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the generic stage-2 epilogue failed");
+          }
+          c->launches++;
+          return PHOEBE_GPU_OK;
+        });
+        c->stats.stage2_launches++;
+        continue;
+      }
+      tm.begin(c);
+      TRY((launch_store<FMT, NSPLIT, NPROD>(c, bn, tA, tB, a, ep)));
+      c->stats.stage2_launches++;
+      tm.end(c, &c->stats.stage2_ms);
+      tm.begin(c);
       if (launch_elph_generic(c->stream, e, rows) != 0) {
         cudaGetLastError();
         return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the generic stage-2 epilogue failed");
@@ -1365,12 +1447,13 @@ static int run_tc_generic(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, con
     }
     i0 = i1;
   }
+  c->stats.pairs_executed = ns * Nq;
+  c->stats.stage2_flops = 8.0 * (double)ns * Nq * nRp * nw * nm;
+  if (df) return PHOEBE_GPU_OK;  // the batch checks the wait flag after its launch
   int herr = 0;
   CK(c, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   if (herr) return fail(c, PHOEBE_GPU_ERR_TIMEOUT, "a tensor-core pipeline wait ran out; results discarded");
-  c->stats.pairs_executed = ns * Nq;
-  c->stats.stage2_flops = 8.0 * (double)ns * Nq * nRp * nw * nm;
   return PHOEBE_GPU_OK;
 }
 
@@ -1718,6 +1801,10 @@ int run_tc(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& gm,
            const double* fF, const double* omega, const double* nB, const cplx* Zq, double* raw) {
   if (c->cc < 100) return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "tensor-core precisions need an sm_10x GPU");
   const int nw = c->nw, nm = 3 * c->na;
+  if (c->defer) {  // batched materials: one stage-2 form for every shape, recorded for later issue
+    if (c->isreq) return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "batched linewidths use the full q sum");
+    return run_tc_generic_mode(c, p, gm, ns, hk, st_k, st_b, epsF, UF, fF, omega, nB, Zq, raw);
+  }
   if (nw == 8 && nm == 6) return run_tc_mode<8, 6>(c, p, gm, ns, hk, st_k, st_b, epsF, UF, fF, omega, nB, Zq, raw);
   if (nw == 2 && nm == 3) return run_tc_mode<2, 3>(c, p, gm, ns, hk, st_k, st_b, epsF, UF, fF, omega, nB, Zq, raw);
   if (nw == 1 && nm == 3) return run_tc_mode<1, 3>(c, p, gm, ns, hk, st_k, st_b, epsF, UF, fF, omega, nB, Zq, raw);
