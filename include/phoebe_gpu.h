@@ -135,7 +135,9 @@ typedef struct {
   double mix_alpha;          /* sampler LEARNED: weight of the uniform part of the proposal,
                                 0 < alpha <= 1 (default 0.1) */
   uint64_t seed;             /* sampler LEARNED/UNIFORM: key of the Philox4x32-10 draws */
-  int reserved[4];           /* must be zero */
+  int sampler_fp32_network;  /* sampler LEARNED: 1 scores q with the FP32 CUDA-core forward pass,
+                                0 (default) with the tensor-core kernel (FP16 operands) on sm_10x */
+  int reserved[3];           /* must be zero */
 } phoebe_gpu_rta_params;
 
 typedef enum {
@@ -251,6 +253,14 @@ int phoebe_gpu_q_contributions(phoebe_gpu_ctx* ctx, const phoebe_gpu_rta_params*
 int phoebe_gpu_mlp_loss_grad(phoebe_gpu_ctx* ctx, int64_t n_rows, const float* x, int n_groups,
                              const int64_t* group_off, const float* target, float* logits, double* loss,
                              float* grad);
+
+/* Network scores z for n_states feature rows (host float [n_states][4]: eps - mu, v[3]) over
+ * every q of the grid nq (host float output [n_states][N_q], q in grid-index order).
+ * tensor_cores = 1: the tcgen05 inference kernel the learned sampler uses (FP16 operands,
+ * FP32 accumulation, SiLU from tanh.approx.f16x2; sm_10x only); 0: the CUDA-core forward
+ * pass of the training kernels (FP32 activations). */
+int phoebe_gpu_mlp_scores(phoebe_gpu_ctx* ctx, int n_states, const float* features, const int32_t nq[3],
+                          int tensor_cores, float* z);
 
 /* The uniforms u_j, j < n, of the draws for k-grid index k (as described above), host double [n]. */
 int phoebe_gpu_is_uniforms(phoebe_gpu_ctx* ctx, uint64_t seed, int32_t k, int64_t n, double* u);

@@ -34,7 +34,7 @@ EXPORTED = (
     "phoebe_gpu_constants", "phoebe_gpu_version", "phoebe_gpu_bands_noalloc",
     "phoebe_gpu_sampler_init", "phoebe_gpu_sampler_load", "phoebe_gpu_sampler_save",
     "phoebe_gpu_train_opts_default", "phoebe_gpu_sampler_train", "phoebe_gpu_q_contributions",
-    "phoebe_gpu_mlp_loss_grad", "phoebe_gpu_is_uniforms",
+    "phoebe_gpu_mlp_loss_grad", "phoebe_gpu_is_uniforms", "phoebe_gpu_mlp_scores",
     "phoebe_gpu_batch_opts_default", "phoebe_gpu_linewidths_rta_batch",
 )
 
@@ -56,7 +56,8 @@ class RTAParams(C.Structure):
         ("max_batch_states", C.c_int),
         ("sampler", C.c_int),
         ("sample_fraction", C.c_double), ("mix_alpha", C.c_double), ("seed", C.c_uint64),
-        ("reserved", C.c_int * 4),
+        ("sampler_fp32_network", C.c_int),
+        ("reserved", C.c_int * 3),
     ]
 
 
@@ -129,6 +130,7 @@ def _load() -> C.CDLL:
         "phoebe_gpu_q_contributions": (I, [P, C.POINTER(RTAParams), C.POINTER(I), P, P, P, P]),
         "phoebe_gpu_mlp_loss_grad": (I, [P, I64, P, I, P, P, P, P, P]),
         "phoebe_gpu_is_uniforms": (I, [P, C.c_uint64, C.c_int32, I64, P]),
+        "phoebe_gpu_mlp_scores": (I, [P, I, P, P, I, P]),
         "phoebe_gpu_batch_opts_default": (None, [C.POINTER(BatchOpts)]),
         "phoebe_gpu_linewidths_rta_batch": (I, [C.POINTER(BatchItem), I, C.POINTER(BatchOpts)]),
     }
@@ -196,7 +198,7 @@ def make_params(p=None, **kw) -> RTAParams:
             s.k_subset = arr.ctypes.data_as(C.POINTER(C.c_int32))
         elif key in ("T_K", "mu_eV", "sigma_eV", "window_eV", "delta_cut_sigmas", "omega_cut_eV", "degen_tol_eV"):
             setattr(s, key, float(val))
-        elif key in ("precision", "max_batch_states", "sampler", "seed"):
+        elif key in ("precision", "max_batch_states", "sampler", "seed", "sampler_fp32_network"):
             setattr(s, key, int(val))
         elif key in ("sample_fraction", "mix_alpha"):
             setattr(s, key, float(val))
@@ -286,10 +288,11 @@ class PhoebeGPU:
         self._check(lib.phoebe_gpu_linewidths_rta(self._ctx, C.byref(s), C.byref(n), None, None, None))
         return n.value
 
-    def linewidths_rta(self, params, **kw):
-        """Host-buffer call: returns (k_index, band, gamma_eV) numpy arrays."""
+    def linewidths_rta(self, params, capacity: int | None = None, **kw):
+        """Host-buffer call: returns (k_index, band, gamma_eV) numpy arrays.  With `capacity`
+        (an upper bound of the active-state count) the counting call is skipped."""
         s = params if isinstance(params, RTAParams) else make_params(params, **kw)
-        n = self.count_states(s)
+        n = self.count_states(s) if capacity is None else int(capacity)
         ki = np.empty(max(n, 1), dtype=np.int32)
         bd = np.empty(max(n, 1), dtype=np.int32)
         gm = np.empty(max(n, 1), dtype=np.float64)
@@ -374,17 +377,26 @@ class PhoebeGPU:
                                                  _ptr(logits), C.byref(loss), _ptr(grad)))
         return logits, loss.value, grad
 
+    def mlp_scores(self, features, nq, tensor_cores: bool = True) -> np.ndarray:
+        """Network scores [n_states][N_q] of feature rows (eps - mu, v[3]) over every q of the grid nq."""
+        f = np.ascontiguousarray(features, dtype=np.float32).reshape(-1, 4)
+        g = np.ascontiguousarray(nq, dtype=np.int32)
+        z = np.empty((len(f), int(np.prod(g))), dtype=np.float32)
+        self._check(lib.phoebe_gpu_mlp_scores(self._ctx, len(f), _ptr(f), _ptr(g), 1 if tensor_cores else 0, _ptr(z)))
+        return z
+
     def is_uniforms(self, seed: int, k: int, n: int) -> np.ndarray:
         u = np.empty(int(n), dtype=np.float64)
         self._check(lib.phoebe_gpu_is_uniforms(self._ctx, int(seed), int(k), int(n), _ptr(u)))
         return u
 
 
-def linewidths_rta_batch(jobs, **opts):
+def linewidths_rta_batch(jobs, capacities=None, **opts):
     """Linewidths of several materials in one call.
 
-    ``jobs``: list of (PhoebeGPU context holding the material, params).  Returns
-    (list of (k_index, band, gamma_eV) per job, dict of the batch timings and the
+    ``jobs``: list of (PhoebeGPU context holding the material, params).  ``capacities``:
+    optional upper bounds of each job's active-state count (skips the counting call).
+    Returns (list of (k_index, band, gamma_eV) per job, dict of the batch timings and the
     stage-2 tile shape chosen per job)."""
     n = len(jobs)
     params = [p if isinstance(p, RTAParams) else make_params(p) for _, p in jobs]
@@ -401,10 +413,11 @@ def linewidths_rta_batch(jobs, **opts):
         if st != 0:
             msgs = [lib.phoebe_gpu_last_error(ctx._ctx).decode() for ctx, _ in jobs]
             raise PhoebeGPUError(st, "; ".join(m for m in msgs if m) or "batch failed")
-    check(lib.phoebe_gpu_linewidths_rta_batch(items, n, C.byref(o)))     # counts
+    if capacities is None:
+        check(lib.phoebe_gpu_linewidths_rta_batch(items, n, C.byref(o)))     # counts
     outs = []
     for i in range(n):
-        m = max(items[i].n_states, 1)
+        m = max(items[i].n_states if capacities is None else int(capacities[i]), 1)
         ki, bd, gm = np.empty(m, dtype=np.int32), np.empty(m, dtype=np.int32), np.empty(m)
         outs.append((ki, bd, gm))
         items[i].n_states = m

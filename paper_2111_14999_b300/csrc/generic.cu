@@ -8,11 +8,15 @@
 
 namespace phx {
 
-// One block per (q row, group of 8 states); one warp per (q, state) pair, lane = final band m'.
+// One block per (q row, group of kGenericStatesPerBlock states); each warp takes every 8th
+// state of the group, one (q, state) pair at a time, lane = final band m'.  MAXNM bounds
+// the mode count; the loops over modes are unrolled to it (exact when MAXNM == nm).
+template <int MAXNM>
 __global__ void __launch_bounds__(256) k_elph_generic(ElphGenericArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nw = a.nw, nm = a.nm;
+  // instantiations below kGenericMaxModes are launched only for nm == MAXNM
+  const int nw = a.nw, nm = MAXNM < kGenericMaxModes ? MAXNM : a.nm;
   const int cps = 2 * nw * nm;
   float2* zs = reinterpret_cast<float2*>(smem);                 // [nm][nm] mode factors of this q
   float* gs = reinterpret_cast<float*>(zs + nm * nm) + warp * cps;  // this warp's G row
@@ -29,70 +33,72 @@ __global__ void __launch_bounds__(256) k_elph_generic(ElphGenericArgs a) {
   __syncthreads();
   int qc[3];
   grid_coords(q, a.gm.nq, qc);
-  const int s = blockIdx.y * 8 + warp;
-  if (s >= a.S) return;
-  // stage the warp's G row (FP32 pairs) in shared memory
-  const float* grow = a.G + r * a.ldg + (int64_t)s * cps;
-  for (int i = lane; i < cps; i += 32) gs[i] = grow[i];
-  __syncwarp();
-  const int64_t kf = a.gm.k_to_fine(a.st_k[s]);
-  int kc[3];
-  grid_coords(kf, a.gm.nf, kc);
-  int fc[3];
+  const int s_end = min(a.S, (int)(blockIdx.y + 1) * kGenericStatesPerBlock);
+  for (int s = blockIdx.y * kGenericStatesPerBlock + warp; s < s_end; s += 8) {
+    // stage the warp's G row (FP32 pairs) in shared memory
+    const float* grow = a.G + r * a.ldg + (int64_t)s * cps;
+    __syncwarp();
+    for (int i = lane; i < cps; i += 32) gs[i] = grow[i];
+    __syncwarp();
+    const int64_t kf = a.gm.k_to_fine(a.st_k[s]);
+    int kc[3];
+    grid_coords(kf, a.gm.nf, kc);
+    int fc[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) fc[d] = (kc[d] + qc[d] * a.gm.sq[d]) % a.gm.nf[d];
-  const int64_t kq = grid_flat(fc, a.gm.nf);
-  const double e_n = a.epsF[kf * nw + a.st_b[s]];
-  const float en_hi = (float)e_n, en_lo = (float)(e_n - (double)en_hi);
-  float part = 0.f;
-  const int mp = lane;
-  bool need = false;
-  float dm = 0.f;
-  if (mp < nw) {
-    const float2 e = a.eps2[kq * nw + mp];
-    dm = (en_hi - e.x) + (en_lo - e.y);
-    need = fabsf(dm) < a.reach;
-  }
-  if (need) {
-    // t[sa] = sum_m conj(U_{k+q}[m][m']) G[sa][m]
-    float2 t[kGenericMaxModes];
+    for (int d = 0; d < 3; ++d) fc[d] = (kc[d] + qc[d] * a.gm.sq[d]) % a.gm.nf[d];
+    const int64_t kq = grid_flat(fc, a.gm.nf);
+    const double e_n = a.epsF[kf * nw + a.st_b[s]];
+    const float en_hi = (float)e_n, en_lo = (float)(e_n - (double)en_hi);
+    float part = 0.f;
+    const int mp = lane;
+    bool need = false;
+    float dm = 0.f;
+    if (mp < nw) {
+      const float2 e = a.eps2[kq * nw + mp];
+      dm = (en_hi - e.x) + (en_lo - e.y);
+      need = fabsf(dm) < a.reach;
+    }
+    if (need) {
+      // t[sa] = sum_m conj(U_{k+q}[m][m']) G[sa][m]
+      float2 t[MAXNM];
 #pragma unroll
-    for (int sa = 0; sa < kGenericMaxModes; ++sa) t[sa] = make_float2(0.f, 0.f);
-    const float2* uh = a.UH + (kq * nw + mp) * nw;
-    for (int m = 0; m < nw; ++m) {
-      const float2 u = uh[m];
+      for (int sa = 0; sa < MAXNM; ++sa) t[sa] = make_float2(0.f, 0.f);
+      const float2* uh = a.UH + (kq * nw + mp) * nw;
+      for (int m = 0; m < nw; ++m) {
+        const float2 u = uh[m];
 #pragma unroll
-      for (int sa = 0; sa < kGenericMaxModes; ++sa) {
-        if (sa < nm) {
-          const float gr = gs[2 * (sa * nw + m)], gi = gs[2 * (sa * nw + m) + 1];
-          t[sa].x = fmaf(u.x, gr, fmaf(-u.y, gi, t[sa].x));
-          t[sa].y = fmaf(u.x, gi, fmaf(u.y, gr, t[sa].y));
+        for (int sa = 0; sa < MAXNM; ++sa) {
+          if (sa < nm) {
+            const float gr = gs[2 * (sa * nw + m)], gi = gs[2 * (sa * nw + m) + 1];
+            t[sa].x = fmaf(u.x, gr, fmaf(-u.y, gi, t[sa].x));
+            t[sa].y = fmaf(u.x, gi, fmaf(u.y, gr, t[sa].y));
+          }
         }
       }
-    }
-    const float f = a.f32[kq * nw + mp];
-    for (int v = 0; v < nm; ++v) {
-      float2 g = make_float2(0.f, 0.f);
+      const float f = a.f32[kq * nw + mp];
+      for (int v = 0; v < nm; ++v) {
+        float2 g = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int sa = 0; sa < kGenericMaxModes; ++sa) {
-        if (sa < nm) {
-          const float2 z = zs[sa * nm + v];
-          g.x = fmaf(t[sa].x, z.x, fmaf(-t[sa].y, z.y, g.x));
-          g.y = fmaf(t[sa].x, z.y, fmaf(t[sa].y, z.x, g.y));
+        for (int sa = 0; sa < MAXNM; ++sa) {
+          if (sa < nm) {
+            const float2 z = zs[sa * nm + v];
+            g.x = fmaf(t[sa].x, z.x, fmaf(-t[sa].y, z.y, g.x));
+            g.y = fmaf(t[sa].x, z.y, fmaf(t[sa].y, z.x, g.y));
+          }
         }
+        const float t1 = (dm - oms[v]) * a.inv_sigma;
+        const float t2 = (dm + oms[v]) * a.inv_sigma;
+        float w = 0.f;
+        if (t1 * t1 < a.cut2) w += (nbs[v] + 1.f - f) * expf(-t1 * t1);
+        if (t2 * t2 < a.cut2) w += (nbs[v] + f) * expf(-t2 * t2);
+        part = fmaf(g.x * g.x + g.y * g.y, w, part);
       }
-      const float t1 = (dm - oms[v]) * a.inv_sigma;
-      const float t2 = (dm + oms[v]) * a.inv_sigma;
-      float w = 0.f;
-      if (t1 * t1 < a.cut2) w += (nbs[v] + 1.f - f) * expf(-t1 * t1);
-      if (t2 * t2 < a.cut2) w += (nbs[v] + f) * expf(-t2 * t2);
-      part = fmaf(g.x * g.x + g.y * g.y, w, part);
     }
-  }
-  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-  if (lane == 0 && part != 0.f) {
-    const float sT = generic_pow2_scale(__uint_as_float(*a.tmax));
-    atomicAdd(a.gamma + a.s_base + s, (double)part * (a.scale_base / ((double)sT * (double)sT)));
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0 && part != 0.f) {
+      const float sT = generic_pow2_scale(__uint_as_float(*a.tmax));
+      atomicAdd(a.gamma + a.s_base + s, (double)part * (a.scale_base / ((double)sT * (double)sT)));
+    }
   }
 }
 
@@ -100,13 +106,27 @@ size_t elph_generic_smem(int nw, int nm) {
   return sizeof(float2) * nm * nm + sizeof(float) * (8 * 2 * nw * nm + 2 * nm);
 }
 
-int launch_elph_generic(cudaStream_t s, const ElphGenericArgs& a, int64_t rows) {
+template <int MAXNM>
+static int launch_nm(cudaStream_t s, const ElphGenericArgs& a, int64_t rows) {
   const size_t smem = elph_generic_smem(a.nw, a.nm);
-  if (cudaFuncSetAttribute(k_elph_generic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (cudaFuncSetAttribute(k_elph_generic<MAXNM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
     return -1;
-  dim3 grid((unsigned)rows, (unsigned)((a.S + 7) / 8));
-  k_elph_generic<<<grid, 256, smem, s>>>(a);
+  dim3 grid((unsigned)rows, (unsigned)((a.S + kGenericStatesPerBlock - 1) / kGenericStatesPerBlock));
+  k_elph_generic<MAXNM><<<grid, 256, smem, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_elph_generic(cudaStream_t s, const ElphGenericArgs& a, int64_t rows) {
+  switch (a.nm) {  // 3 modes per atom: exact unrolling for 1..6 atoms
+    case 3: return launch_nm<3>(s, a, rows);
+    case 6: return launch_nm<6>(s, a, rows);
+    case 9: return launch_nm<9>(s, a, rows);
+    case 12: return launch_nm<12>(s, a, rows);
+    case 15: return launch_nm<15>(s, a, rows);
+    case 18: return launch_nm<18>(s, a, rows);
+    default: return launch_nm<kGenericMaxModes>(s, a, rows);
+  }
 }
 
 }  // namespace phx

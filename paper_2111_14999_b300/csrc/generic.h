@@ -18,6 +18,7 @@ __host__ __device__ inline float pow2_scale(float maxabs) {
 __device__ __forceinline__ float generic_pow2_scale(float maxabs) { return pow2_scale(maxabs); }
 
 constexpr int kGenericMaxModes = kMaxModes;
+constexpr int kGenericStatesPerBlock = 128;  // states per block of the generic epilogue
 
 struct ElphGenericArgs {
   const float* G;          // [rows][ldg] stage-2 result of this q chunk, state s at columns s*2*nw*nm

@@ -137,8 +137,10 @@ static int check_params(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, GridM
   if (!(p->degen_tol_eV >= 0.0)) return fail(c, PHOEBE_GPU_ERR_ARG, "degen_tol_eV must be >= 0");
   if (p->precision < PHOEBE_PREC_FP64 || p->precision > PHOEBE_PREC_BF16X3)
     return fail(c, PHOEBE_GPU_ERR_ARG, "unknown precision %d", p->precision);
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 3; ++i)
     if (p->reserved[i] != 0) return fail(c, PHOEBE_GPU_ERR_ARG, "reserved fields must be zero");
+  if (p->sampler_fp32_network != 0 && p->sampler_fp32_network != 1)
+    return fail(c, PHOEBE_GPU_ERR_ARG, "sampler_fp32_network must be 0 or 1");
   if (p->sampler < PHOEBE_SAMPLER_FULL || p->sampler > PHOEBE_SAMPLER_UNIFORM)
     return fail(c, PHOEBE_GPU_ERR_ARG, "unknown sampler %d", p->sampler);
   if (p->sampler != PHOEBE_SAMPLER_FULL) {

@@ -19,6 +19,7 @@
 #include <random>
 #include <vector>
 
+#include "mlp_tc.h"
 #include "sampler.h"
 
 namespace phx {
@@ -788,6 +789,60 @@ static int mlp_backward(phoebe_gpu_ctx* c, const float* Wr, const RowX& X, int64
   return PHOEBE_GPU_OK;
 }
 
+// Scores z[s][q] of S states over every q of a grid: tcgen05 kernel (FP16 operands, FP32
+// accumulation) or the CUDA-core forward pass (FP32 activations) in row chunks.
+static int network_scores(phoebe_gpu_ctx* c, const float* qt, const float* feat, int S, int64_t Nq, bool tensor_cores,
+                          float* z) {
+  int st;
+  float* Wr;
+  TRY(round_params(c, &Wr));
+  if (tensor_cores) {
+    __half* W2h = (__half*)ensure(c, "mlp_w2h", sizeof(__half) * kNh * kNh, &st);
+    if (!W2h) return st;
+    __half* W3h = (__half*)ensure(c, "mlp_w3h", sizeof(__half) * kNh * kNh, &st);
+    if (!W3h) return st;
+    int* err = (int*)ensure(c, "mlp_err", 64, &st);
+    if (!err) return st;
+    CK(c, cudaMemsetAsync(err, 0, 64, c->stream));
+    if (mlp_tc_params(c->stream, Wr, W2h, W3h) != 0) {
+      cudaGetLastError();
+      return fail(c, PHOEBE_GPU_ERR_CUDA, "parameter conversion for the tensor-core network failed");
+    }
+    MlpTcArgs ma;
+    ma.W2h = W2h;
+    ma.W3h = W3h;
+    ma.P = Wr;
+    ma.qt = qt;
+    ma.feat = feat;
+    ma.Nq = Nq;
+    ma.tiles_per_state = (Nq + 127) / 128;
+    ma.ntiles = (int64_t)S * ma.tiles_per_state;
+    ma.z = z;
+    ma.err = err;
+    if (mlp_tc_launch(c->stream, c->num_sms, ma) != 0) {
+      cudaGetLastError();
+      return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the tensor-core network failed");
+    }
+    c->launches += 2;
+    int herr = 0;
+    CK(c, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (herr) return fail(c, PHOEBE_GPU_ERR_TIMEOUT, "a tensor-core network wait ran out; results discarded");
+    return PHOEBE_GPU_OK;
+  }
+  const int64_t spc = std::max<int64_t>(1, kMaxRows / Nq);  // states per network chunk
+  for (int64_t s0 = 0; s0 < S; s0 += spc) {
+    const int64_t ns = std::min<int64_t>(spc, S - s0);
+    RowX X;
+    X.qt = qt;
+    X.feat = feat + s0 * 4;
+    X.Nq = Nq;
+    X.rows = ns * Nq;
+    TRY(mlp_forward(c, Wr, X, X.rows, z + s0 * Nq, false, nullptr));
+  }
+  return PHOEBE_GPU_OK;
+}
+
 // ------------------------------------------------------------------ host: one batch of states
 template <int NW, int NM>
 int is_batch(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& gm, const IsBatch& b,
@@ -880,18 +935,7 @@ int is_batch(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& g
       if (!qt) return st;
       k_wrapped_q<<<(unsigned)((Nq + 255) / 256), 256, 0, c->stream>>>(gm.nq[0], gm.nq[1], gm.nq[2], Nq, qt);
       TRY(launched(c, 1));
-      float* Wr;
-      TRY(round_params(c, &Wr));
-      const int64_t spc = std::max<int64_t>(1, kMaxRows / Nq);  // states per network chunk
-      for (int64_t s0 = 0; s0 < S; s0 += spc) {
-        const int64_t ns = std::min<int64_t>(spc, S - s0);
-        RowX X;
-        X.qt = qt;
-        X.feat = feat + s0 * 4;
-        X.Nq = Nq;
-        X.rows = ns * Nq;
-        TRY(mlp_forward(c, Wr, X, X.rows, z + s0 * Nq, false, nullptr));
-      }
+      TRY(network_scores(c, qt, feat, S, Nq, c->cc >= 100 && !p->sampler_fp32_network, z));
       k_logit_stats<<<S, 256, 0, c->stream>>>(z, Nq, zmax, zsum);
       TRY(launched(c, 1));
       P.z = z;
@@ -1249,6 +1293,32 @@ extern "C" int phoebe_gpu_is_uniforms(phoebe_gpu_ctx* c, uint64_t seed, int32_t 
   c->launches++;
   CK(c, cudaGetLastError());
   CK(c, cudaMemcpyAsync(u, d, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return PHOEBE_GPU_OK;
+}
+
+extern "C" int phoebe_gpu_mlp_scores(phoebe_gpu_ctx* c, int n_states, const float* features, const int32_t nq[3],
+                                     int tensor_cores, float* z) {
+  if (!c) return PHOEBE_GPU_ERR_ARG;
+  c->launches = 0;
+  if (n_states < 1 || !features || !nq || !z) return fail(c, PHOEBE_GPU_ERR_ARG, "mlp_scores: bad arguments");
+  for (int i = 0; i < 3; ++i)
+    if (nq[i] < 1 || nq[i] > 4096) return fail(c, PHOEBE_GPU_ERR_ARG, "mlp_scores: grid sizes must be in 1..4096");
+  if (!c->have_mlp) return fail(c, PHOEBE_GPU_ERR_ORDER, "mlp_scores: no parameters (init, load or train first)");
+  if (tensor_cores && c->cc < 100)
+    return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "tensor-core network scores need an sm_10x GPU");
+  const int64_t Nq = (int64_t)nq[0] * nq[1] * nq[2];
+  int st;
+  void* dfeat;
+  TRY(upload(c, "ms_feat", features, sizeof(float) * 4 * n_states, &dfeat));
+  float* qt = (float*)ensure(c, "ms_qt", sizeof(float) * Nq * 3, &st);
+  if (!qt) return st;
+  float* zd = (float*)ensure(c, "ms_z", sizeof(float) * Nq * n_states, &st);
+  if (!zd) return st;
+  k_wrapped_q<<<(unsigned)((Nq + 255) / 256), 256, 0, c->stream>>>(nq[0], nq[1], nq[2], Nq, qt);
+  TRY(launched(c, 1));
+  TRY(network_scores(c, qt, (const float*)dfeat, n_states, Nq, tensor_cores != 0, zd));
+  CK(c, cudaMemcpyAsync(z, zd, sizeof(float) * Nq * n_states, cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   return PHOEBE_GPU_OK;
 }

@@ -108,7 +108,7 @@ def test_sampled_gamma_equals_oracle_estimate(ctx, uniform):
     ctx.sampler_load(blob)
     frac, alpha, seed = 0.25, 0.1, 12345
     prm2 = prm.with_(k_subset=kk, precision=PREC, sampler=2 if uniform else 1, sample_fraction=frac,
-                     mix_alpha=alpha, seed=seed)
+                     mix_alpha=alpha, seed=seed, sampler_fp32_network=1)
     ki, bd, g = ctx.linewidths_rta(prm2)
     ks, bs, go = S.linewidths_is(mat, prm, blob, frac, alpha, seed, k_indices=kk, uniform=uniform)
     assert np.array_equal(ki, ks) and np.array_equal(bd, bs)
@@ -116,6 +116,26 @@ def test_sampled_gamma_equals_oracle_estimate(ctx, uniform):
     # a draw may differ where a uniform falls within rounding of a CDF step (FP32 vs FP64 network)
     assert np.mean(rel < 1e-4) >= 0.9
     assert np.median(rel) < 1e-5
+
+
+def test_tensor_core_scores_vs_oracle(ctx):
+    # tcgen05 inference (FP16 operands, tanh-based SiLU) and the FP32 CUDA-core forward pass
+    # against the FP64 network on every q of a 12^3 grid (13 tiles of 128 rows plus a tail)
+    blob = _blob(13, scale=2.5)
+    ctx.sampler_load(blob)
+    rng = np.random.default_rng(9)
+    feat = np.column_stack([rng.uniform(-0.5, 0.5, 6), rng.normal(0, 1.5, (6, 3))]).astype(np.float32)
+    nq = (12, 12, 12)
+    z_tc = ctx.mlp_scores(feat, nq, tensor_cores=True)
+    z_fp = ctx.mlp_scores(feat, nq, tensor_cores=False)
+    th = S.bf16_params(blob)
+    qt = S.wrapped_q(nq)
+    for s in range(len(feat)):
+        zo = S.mlp_forward(th, S.rows_for_state(feat[s].astype(np.float64), qt))[0]
+        scale = np.max(np.abs(zo - zo.mean())) + 1e-3
+        assert np.max(np.abs(z_fp[s] - zo)) <= 1e-3 * np.max(np.abs(zo)) + 1e-5
+        assert np.max(np.abs(z_tc[s] - zo)) <= 2e-2 * scale, s
+        assert np.corrcoef(z_tc[s], zo)[0, 1] > 0.999
 
 
 def test_sampled_gamma_is_unbiased(ctx):

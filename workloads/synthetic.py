@@ -82,6 +82,7 @@ class RTAParams:
     sample_fraction: float = 0.05
     mix_alpha: float = 0.1
     seed: int = 0
+    sampler_fp32_network: int = 0
 
     def with_(self, **kw) -> "RTAParams":
         return replace(self, **kw)
