@@ -151,7 +151,7 @@ def learned_leg(pg, W, dev, stream, args) -> dict:
     ctx.set_material(mat20)
     ctx.sampler_init(1)
     t0 = time.perf_counter()
-    loss = ctx.sampler_train(p20.with_(precision=prec))
+    loss = ctx.sampler_train(p20.with_(precision=prec), **({"epochs": args.learned_epochs} if args.learned_epochs else {}))
     train_s = time.perf_counter() - t0
     mat, prm = W.si_like(seed=0, nk=40, nq=80)
     ctx.set_material(mat)
@@ -194,6 +194,70 @@ def learned_leg(pg, W, dev, stream, args) -> dict:
         "learned_ms": {"network_proposal_draws": res["learned"]["sampler_ms"], "sampled_pairs": res["learned"]["pairs_ms"],
                        "total": res["learned"]["total_ms"]},
         "full_ms": {"stage2": full_st["stage2_ms"], "total": full_st["total_ms"]},
+    }
+
+
+def batch_leg(pg, W, dev, args) -> dict:
+    """64 uneven materials (N_w 4-24, 1-6 atoms, |R| 100-1200, grids 16^3-40^3, a seeded subset of k
+    per material, split BF16): one call per material against one batch call whose stage 2 for all
+    materials is a single CUDA graph with autotuned tiles."""
+    import torch
+    t0 = time.perf_counter()
+    mats = [W.batch_material(i, g_budget_bytes=128e6) for i in range(64)]
+    gen_s = time.perf_counter() - t0
+    ctxs, jobs = [], []
+    for i, (mat, prm) in enumerate(mats):
+        c = pg.PhoebeGPU(dev)
+        c.set_material(mat)
+        n = prm.nk[0]
+        kk = np.sort(np.random.default_rng([5, i]).choice(n ** 3, min(args.batch_k, n ** 3), replace=False))
+        ctxs.append(c)
+        jobs.append((c, pg.make_params(prm, precision=1, k_subset=kk)))
+    caps = [c.count_states(p) for c, p in jobs]
+    for (c, p), cap in zip(jobs, caps):          # warm-up
+        c.linewidths_rta(p, capacity=cap)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    eager = [c.linewidths_rta(p, capacity=cap) for (c, p), cap in zip(jobs, caps)]
+    torch.cuda.synchronize()
+    eager_s = time.perf_counter() - t0
+    for c, p in jobs:
+        c.set_profiling(True)
+    agg = {}
+    for (c, p), cap in zip(jobs, caps):          # per-stage breakdown (not timed as a whole)
+        c.linewidths_rta(p, capacity=cap)
+        st = c.stats()
+        for key in ("bands_ms", "phonons_ms", "stage1_ms", "stage2_ms", "delta_ms", "stage2_flops"):
+            agg[key] = agg.get(key, 0.0) + st[key]
+    for c, p in jobs:
+        c.set_profiling(False)
+    pg.binding.linewidths_rta_batch(jobs, capacities=caps)   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res, info = pg.binding.linewidths_rta_batch(jobs, capacities=caps)
+    torch.cuda.synchronize()
+    batch_s = time.perf_counter() - t0
+    states = int(sum(len(g) for _, _, g in eager))
+    diff = 0.0
+    for (_, _, g), (_, _, g1) in zip(res, eager):
+        if len(g) and np.any(g1):
+            diff = max(diff, float(np.max(np.abs(g - g1) / np.maximum(np.abs(g1), 1e-6 * np.median(np.abs(g1))))))
+    for c in ctxs:
+        c.close()
+    tiles = {}
+    for t in info["tiles"]:
+        tiles[f"{t[0]}x{t[1]}"] = tiles.get(f"{t[0]}x{t[1]}", 0) + 1
+    return {
+        "workload": f"64 batch materials (seed 0), {args.batch_k} seeded k each, full q grids, split_bf16",
+        "states": states, "generation_s": gen_s,
+        "one_call_per_material": {"wall_s": eager_s, "linewidths_per_s": states / eager_s},
+        "one_batch_call": {"wall_s": batch_s, "linewidths_per_s": states / batch_s, "plan_ms": info["plan_ms"],
+                           "graph_ms": info["graph_ms"], "graph_nodes": info["graph_nodes"],
+                           "finish_ms": info["finish_ms"]},
+        "per_material_stage_ms_sum": {k: v for k, v in agg.items() if k.endswith("_ms")},
+        "stage2_algorithmic_tflops_in_graph": agg["stage2_flops"] / (info["graph_ms"] / 1e3) / 1e12,
+        "autotuned_tiles_columns_x_kblocks": tiles,
+        "max_rel_diff_batch_vs_per_material": diff,
     }
 
 
@@ -251,6 +315,10 @@ def main():
                     help="profiling case: restrict to this many seeded active k points (0 = whole grid)")
     ap.add_argument("--main-only", action="store_true", help="only the timed device leg (for ncu captures)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the many-materials leg")
+    ap.add_argument("--learned-only", action="store_true", help="only the learned-proposal leg (profiling case)")
+    ap.add_argument("--learned-epochs", type=int, default=0, help="training epochs of the learned leg (0: default)")
+    ap.add_argument("--batch-k", type=int, default=64, help="seeded k points per material in the many-materials leg")
     ap.add_argument("--learned-k", type=int, default=512, help="seeded k points of the learned-proposal evaluation")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -261,6 +329,12 @@ def main():
     from workloads import synthetic as W
 
     world, rank, local = _dist()
+    if args.learned_only:
+        dev = local if torch.cuda.is_available() else 0
+        torch.cuda.set_device(dev)
+        if rank == 0:
+            print(json.dumps({"learned_sampler": learned_leg(pg, W, dev, torch.cuda.current_stream(), args)}), flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as td
@@ -428,6 +502,8 @@ def main():
     }
     if rank == 0 and not args.no_learned:
         line["learned_sampler"] = learned_leg(pg, W, dev, stream, args)
+    if rank == 0 and not args.no_batch:
+        line["batched_materials"] = batch_leg(pg, W, dev, args)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle(args.cpu_k)
     if rank == 0:

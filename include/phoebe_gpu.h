@@ -192,6 +192,18 @@ int phoebe_gpu_get_stats(const phoebe_gpu_ctx* ctx, phoebe_gpu_stats* out);
 /* Cap on the context's device memory (bytes, 0 = none); exceeding it returns ERR_NOMEM. */
 int phoebe_gpu_set_memory_cap(phoebe_gpu_ctx* ctx, int64_t bytes);
 
+/* RTA transport coefficients from the linewidths of linewidths_rta with the same parameters
+ * (Sec. 4.2 fluxes J and Q, Onsager coefficients; Sec. 4.3.2): with tau = hbar / Gamma and hbar v
+ * the k-derivative of Eq. 10 (Sec. 3.3, Cartesian),
+ *     L_n = 1/(N_k V) sum_{active kb, Gamma > 0} tau v v^T (eps - mu)^n (-df/deps),
+ *     sigma = e^2 L_0 (S/m),  seebeck = -(1/(e T)) L_0^{-1} L_1 (V/K, electron charge -e),
+ *     kappa = (1/T)(L_2 - L_1 L_0^{-1} L_1) (W/(m K)),
+ * no spin factor.  lattice: host, primitive vectors as rows (Angstrom), the cell of the R
+ * coordinates of set_hamiltonian.  Outputs: host row-major 3 x 3.  Degenerate bands use
+ * the diagonal velocity elements of the eigenvectors returned by the eigensolver. */
+int phoebe_gpu_transport_rta(phoebe_gpu_ctx* ctx, const phoebe_gpu_rta_params* params, const double lattice[9],
+                             double sigma[9], double seebeck[9], double kappa[9]);
+
 /* ------------------------------------------------------------------------------------------
  * Importance-sampled q sums with a learned proposal.  The paper has no counterpart: Eq. 29
  * sums every q of the grid.  Write c_nk(q) for N_q times the q term of Eq. 29, so that

@@ -417,3 +417,65 @@ def contributions(mat, params, k_indices=None, q_indices=None, table=None):
         w = np.where(alive[qi][:, None, :], w, 0.0)
         out[j] = 2.0 * np.pi * np.sum(g2 * w, axis=(1, 2))
     return ks, bs, out
+
+
+# ------------------------------------------------- RTA transport from the linewidths (Sec. 4.2, 4.3.2)
+
+HBAR_EV_S = 6.582119569e-16     # hbar in eV s
+E_CHARGE = 1.602176634e-19      # elementary charge, C
+
+
+def group_velocities(k: np.ndarray, mat, U: np.ndarray) -> np.ndarray:
+    """hbar v_kb in eV A, Cartesian: the derivative of Eq. 10 with respect to k (Sec. 3.3).
+
+    Diagonal elements of U^dagger dH/dk U with dH/dk_cart = sum_R w_R i R_cart e^{ik.R} H(R)
+    (Hellmann-Feynman; the velocity of non-degenerate bands; U (nk, nw, nw) columns = bands).
+    """
+    k = np.atleast_2d(k)
+    P = phases(k, mat.R_H) * mat.w_H[None, :]
+    Rc = np.asarray(mat.R_H, dtype=np.float64) @ np.asarray(mat.lattice, dtype=np.float64)
+    Hf = mat.H.reshape(len(mat.R_H), -1)
+    out = np.zeros((len(k), mat.nw, 3))
+    for a in range(3):
+        dH = ((P * (1j * Rc[:, a])[None, :]) @ Hf).reshape(len(k), mat.nw, mat.nw)
+        out[:, :, a] = np.real(np.einsum("kmb,kmn,knb->kb", np.conj(U), dH, U))
+    return out
+
+
+def transport_rta(mat, params, gamma: np.ndarray, ks: np.ndarray, bs: np.ndarray, table=None) -> dict:
+    """Electrical conductivity, Seebeck coefficient and electronic thermal conductivity in the
+    relaxation-time approximation (Sec. 4.3.2) from the linewidths of the active states.
+
+    tau = hbar / Gamma; delta f = -tau v.(e E) df/de for a field and -tau v.grad T df/dT for a
+    gradient (Sec. 4.2 with the scattering matrix reduced to its diagonal), inserted in the charge
+    and energy fluxes J, Q of Sec. 4.2:
+        L_n[a][b] = 1/(N_k V) sum_kb tau v_a v_b (eps - mu)^n (-df/deps),
+        sigma = e^2 L_0,  S = -(1/(e T)) L_0^{-1} L_1 (electron charge -e),
+        kappa_el = (1/T) (L_2 - L_1 L_0^{-1} L_1).
+    Readings: no spin factor (as in Eq. 29 and the fluxes of Sec. 4.2); states with Gamma = 0
+    (no scattering partner) are left out; sums over the active states of the window only.
+    Returns SI values: sigma in S/m, seebeck in V/K, kappa in W/(m K) (3x3 each).
+    """
+    F, eps_F, U_F, k_to_F = table if table is not None else electron_table(mat, params)
+    nk = tuple(int(x) for x in params.nk)
+    kpts = grid_points(nk)
+    f_idx = k_to_F[np.asarray(ks)]
+    v = group_velocities(kpts[np.asarray(ks)], mat, U_F[f_idx])[np.arange(len(ks)), np.asarray(bs)]  # eV A
+    eps = eps_F[f_idx, np.asarray(bs)]
+    kT = KB_EV * params.T_K
+    f = fermi_dirac(eps, params.mu_eV, params.T_K)
+    mdf = f * (1.0 - f) / kT                                   # -df/deps, 1/eV
+    keep = np.asarray(gamma) > 0
+    tau = np.where(keep, HBAR_EV_S / np.where(keep, gamma, 1.0), 0.0)   # s
+    vs = v * (E_CHARGE * 1e-10) / (HBAR_EV_S * E_CHARGE)       # m/s: (eV A) / hbar
+    vol = abs(np.linalg.det(np.asarray(mat.lattice, dtype=np.float64))) * 1e-30   # m^3
+    Nk = int(np.prod(nk))
+    de = (eps - params.mu_eV) * E_CHARGE                       # J
+    w = tau * mdf / E_CHARGE                                   # s / J
+    L = [np.einsum("s,sa,sb->ab", w * de ** n, vs, vs) / (Nk * vol) for n in range(3)]
+    T = params.T_K
+    sigma = E_CHARGE ** 2 * L[0]
+    L0i = np.linalg.inv(L[0])
+    seebeck = -(1.0 / (E_CHARGE * T)) * (L0i @ L[1])
+    kappa = (L[2] - L[1] @ L0i @ L[1]) / T
+    return {"sigma": sigma, "seebeck": seebeck, "kappa": kappa, "L": L}

@@ -35,7 +35,7 @@ EXPORTED = (
     "phoebe_gpu_sampler_init", "phoebe_gpu_sampler_load", "phoebe_gpu_sampler_save",
     "phoebe_gpu_train_opts_default", "phoebe_gpu_sampler_train", "phoebe_gpu_q_contributions",
     "phoebe_gpu_mlp_loss_grad", "phoebe_gpu_is_uniforms", "phoebe_gpu_mlp_scores",
-    "phoebe_gpu_batch_opts_default", "phoebe_gpu_linewidths_rta_batch",
+    "phoebe_gpu_batch_opts_default", "phoebe_gpu_linewidths_rta_batch", "phoebe_gpu_transport_rta",
 )
 
 
@@ -133,6 +133,7 @@ def _load() -> C.CDLL:
         "phoebe_gpu_mlp_scores": (I, [P, I, P, P, I, P]),
         "phoebe_gpu_batch_opts_default": (None, [C.POINTER(BatchOpts)]),
         "phoebe_gpu_linewidths_rta_batch": (I, [C.POINTER(BatchItem), I, C.POINTER(BatchOpts)]),
+        "phoebe_gpu_transport_rta": (I, [P, C.POINTER(RTAParams), P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -308,6 +309,15 @@ class PhoebeGPU:
         self._check(lib.phoebe_gpu_linewidths_rta_dev(self._ctx, C.byref(s), C.byref(nn), _ptr(k_index_dev),
                                                       _ptr(band_dev), _ptr(gamma_dev)))
         return nn.value
+
+    def transport_rta(self, params, lattice, **kw):
+        """RTA sigma (S/m), Seebeck (V/K) and electronic kappa (W/(m K)), each 3 x 3."""
+        s = params if isinstance(params, RTAParams) else make_params(params, **kw)
+        lat = np.ascontiguousarray(lattice, dtype=np.float64).reshape(9)
+        out = [np.empty(9) for _ in range(3)]
+        self._check(lib.phoebe_gpu_transport_rta(self._ctx, C.byref(s), _ptr(lat), _ptr(out[0]), _ptr(out[1]),
+                                                 _ptr(out[2])))
+        return {"sigma": out[0].reshape(3, 3), "seebeck": out[1].reshape(3, 3), "kappa": out[2].reshape(3, 3)}
 
     def set_profiling(self, on: bool = True):
         self._check(lib.phoebe_gpu_set_profiling(self._ctx, 1 if on else 0))

@@ -55,9 +55,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(MlpTcArgs a) {
   uint8_t* W2s = smem;
   uint8_t* W3s = smem + kOpBytes;
   uint8_t* Hs = smem + 2 * kOpBytes;  // two operands, one per group
-  float* W1 = reinterpret_cast<float*>(smem + 4 * kOpBytes);  // [128][7]
-  float* b1 = W1 + 128 * 7;
-  float* b2 = b1 + 128;
+  float* b2 = reinterpret_cast<float*>(smem + 4 * kOpBytes);  // 16-byte aligned
   float* b3 = b2 + 128;
   float* w4 = b3 + 128;
   float* b4 = w4 + 128;
@@ -76,9 +74,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(MlpTcArgs a) {
     *reinterpret_cast<uint4*>(W2s + sw_offset(row, chunk)) = v2;
     *reinterpret_cast<uint4*>(W3s + sw_offset(row, chunk)) = v3;
   }
-  for (int i = tid; i < 128 * 7; i += kThreads) W1[i] = a.P[kMlpOffW1 + i];
   for (int i = tid; i < 128; i += kThreads) {
-    b1[i] = a.P[kMlpOffB1 + i];
     b2[i] = a.P[kMlpOffB2 + i];
     b3[i] = a.P[kMlpOffB3 + i];
     w4[i] = a.P[kMlpOffW4 + i];
@@ -156,8 +152,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(MlpTcArgs a) {
       if (valid)
 #pragma unroll
         for (int d = 0; d < 3; ++d) qv[d] = a.qt[q * 3 + d];
-      const float4 f = reinterpret_cast<const float4*>(a.feat)[s];
-      // layer 1 (7 inputs) and SiLU, 8 neurons per 16-byte chunk
+      // layer 1 (7 inputs) and SiLU, 8 neurons per 16-byte chunk; the state's part of the
+      // 7-input layer is folded into w1c[s][j].w
+      const float4* wc = a.w1c + (int64_t)s * 128;
+#pragma unroll 2
       for (int chunk = 0; chunk < 16; ++chunk) {
         uint32_t w[4];
 #pragma unroll
@@ -165,17 +163,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(MlpTcArgs a) {
           float x[2];
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
-            const int j = chunk * 8 + p * 2 + e;
-            const float* wj = W1 + j * 7;
-            float acc = b1[j];
-            acc = fmaf(wj[0], qv[0], acc);
-            acc = fmaf(wj[1], qv[1], acc);
-            acc = fmaf(wj[2], qv[2], acc);
-            acc = fmaf(wj[3], f.x, acc);
-            acc = fmaf(wj[4], f.y, acc);
-            acc = fmaf(wj[5], f.z, acc);
-            acc = fmaf(wj[6], f.w, acc);
-            x[e] = acc;
+            const float4 c4 = __ldg(wc + chunk * 8 + p * 2 + e);
+            x[e] = fmaf(c4.x, qv[0], fmaf(c4.y, qv[1], fmaf(c4.z, qv[2], c4.w)));
           }
           w[p] = silu2(x[0], x[1]);
         }
@@ -204,21 +193,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(MlpTcArgs a) {
           tmem_ld32(taddr + c0, v);
 #pragma unroll
           for (int cc = 0; cc < 4; ++cc) {
+            const int j0 = c0 + cc * 8;
+            const float4 bA = reinterpret_cast<const float4*>(bias + j0)[0];
+            const float4 bB = reinterpret_cast<const float4*>(bias + j0)[1];
+            const float bv[8] = {bA.x, bA.y, bA.z, bA.w, bB.x, bB.y, bB.z, bB.w};
             uint32_t w[4];
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
-              const int j = c0 + cc * 8 + p * 2;
-              w[p] = silu2(v[cc * 8 + p * 2] + bias[j], v[cc * 8 + p * 2 + 1] + bias[j + 1]);
-            }
+            for (int p = 0; p < 4; ++p) w[p] = silu2(v[cc * 8 + p * 2] + bv[p * 2], v[cc * 8 + p * 2 + 1] + bv[p * 2 + 1]);
             if (l == 0) {
               *reinterpret_cast<uint4*>(H + sw_offset(row, (c0 >> 3) + cc)) = make_uint4(w[0], w[1], w[2], w[3]);
             } else {
+              const float4 wA = reinterpret_cast<const float4*>(w4 + j0)[0];
+              const float4 wB = reinterpret_cast<const float4*>(w4 + j0)[1];
+              const float wv[8] = {wA.x, wA.y, wA.z, wA.w, wB.x, wB.y, wB.z, wB.w};
 #pragma unroll
               for (int p = 0; p < 4; ++p) {
                 const float2 hv = __half22float2(*reinterpret_cast<__half2*>(&w[p]));
-                const int j = c0 + cc * 8 + p * 2;
-                z = fmaf(hv.x, w4[j], z);
-                z = fmaf(hv.y, w4[j + 1], z);
+                z = fmaf(hv.x, wv[p * 2], z);
+                z = fmaf(hv.y, wv[p * 2 + 1], z);
               }
             }
           }
@@ -242,6 +234,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(MlpTcArgs a) {
   if (tid == 0 && *abort_flag) atomicOr(a.err, 1);
 }
 
+// w1c[s][j] = (W1[j][0], W1[j][1], W1[j][2], b1[j] + sum_i W1[j][3+i] feat[s][i]): the 7-input layer
+// with the state's features folded in.
+__global__ void k_w1c(const float* __restrict__ P, const float* __restrict__ feat, int S, float4* __restrict__ w1c) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= S * 128) return;
+  const int s = t >> 7, j = t & 127;
+  const float* wj = P + kMlpOffW1 + j * 7;
+  const float* f = feat + (int64_t)s * 4;
+  float c = P[kMlpOffB1 + j];
+  c = fmaf(wj[3], f[0], c);
+  c = fmaf(wj[4], f[1], c);
+  c = fmaf(wj[5], f[2], c);
+  c = fmaf(wj[6], f[3], c);
+  w1c[t] = make_float4(wj[0], wj[1], wj[2], c);
+}
+
+int mlp_tc_w1c(cudaStream_t s, const float* P, const float* feat, int S, float4* w1c) {
+  k_w1c<<<(S * 128 + 255) / 256, 256, 0, s>>>(P, feat, S, w1c);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 __global__ void k_params_half(const float* __restrict__ P, __half* __restrict__ W2h, __half* __restrict__ W3h) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 128 * 128) return;
@@ -250,7 +263,7 @@ __global__ void k_params_half(const float* __restrict__ P, __half* __restrict__ 
 }
 
 size_t mlp_tc_smem_bytes() {
-  return 1024 + 4 * kOpBytes + sizeof(float) * (128 * 7 + 4 * 128 + 4) + 8 * 6 + 16;
+  return 1024 + 4 * kOpBytes + sizeof(float) * (3 * 128 + 4) + 8 * 6 + 16;
 }
 
 int mlp_tc_launch(cudaStream_t s, int num_sms, const MlpTcArgs& a) {
