@@ -342,6 +342,13 @@ int phoebe_gpu_linewidths_rta_batch(phoebe_gpu_batch_item* items, int n, phoebe_
 int phoebe_gpu_bands_noalloc(int nw, int n_R, const int32_t* R, const double* w, const double* H, int n_k,
                              const double* k, double* eps, double* U, void* cuda_stream);
 
+/* Check of the bounded device waits of the pipeline kernels: one block waits on an mbarrier
+ * phase that its producer publishes only when `publish` is non-zero.  Unpublished, the wait
+ * gives up after limit_us microseconds (1..1e7) and the call returns PHOEBE_GPU_ERR_TIMEOUT;
+ * the context stays usable.  Published, it returns PHOEBE_GPU_OK.  The paper has no
+ * counterpart. */
+int phoebe_gpu_selftest_wait(phoebe_gpu_ctx* ctx, int publish, int64_t limit_us);
+
 /* Physical constants compiled into the library: out[0] = k_B (eV/K),
  * out[1] = hbar*sqrt(eV/(A^2 amu)) (eV), out[2] = hbar^2/(amu eV A^2).  Needs no GPU. */
 void phoebe_gpu_constants(double out[3]);

@@ -36,6 +36,7 @@ EXPORTED = (
     "phoebe_gpu_train_opts_default", "phoebe_gpu_sampler_train", "phoebe_gpu_q_contributions",
     "phoebe_gpu_mlp_loss_grad", "phoebe_gpu_is_uniforms", "phoebe_gpu_mlp_scores",
     "phoebe_gpu_batch_opts_default", "phoebe_gpu_linewidths_rta_batch", "phoebe_gpu_transport_rta",
+    "phoebe_gpu_selftest_wait",
 )
 
 
@@ -134,6 +135,7 @@ def _load() -> C.CDLL:
         "phoebe_gpu_batch_opts_default": (None, [C.POINTER(BatchOpts)]),
         "phoebe_gpu_linewidths_rta_batch": (I, [C.POINTER(BatchItem), I, C.POINTER(BatchOpts)]),
         "phoebe_gpu_transport_rta": (I, [P, C.POINTER(RTAParams), P, P, P, P]),
+        "phoebe_gpu_selftest_wait": (I, [P, I, I64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
