@@ -28,8 +28,9 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-PREC_NAMES = {0: "fp64", 1: "split_bf16", 2: "split_tf32", 3: "bf16", 4: "tf32", 5: "split_fp16", 6: "bf16x3"}
-PREC_DTYPE = {0: "f64", 1: "bf16x6+f32acc", 2: "tf32x3+f32acc", 3: "bf16+f32acc", 4: "tf32+f32acc",
+PREC_NAMES = {0: "fp64", 1: "split_bf16", 2: "split_tf32", 3: "bf16", 4: "tf32", 5: "split_fp16", 6: "bf16x3",
+              7: "fp32_grid_dft"}
+PREC_DTYPE = {0: "f64", 1: "bf16x6+f32acc", 2: "tf32x3+f32acc", 3: "bf16+f32acc", 4: "tf32+f32acc", 7: "f32",
               5: "f16x3+f32acc", 6: "bf16x3+f32acc"}
 METRIC = "Gamma_nk linewidths/s (el-ph RTA, Si-like 40^3 k x 40^3 q)"
 WORKLOAD = "si_like_fcc_nw8_na2_R429_k40x40x40_q40x40x40_T300_sigma0.02_window0.5"
@@ -393,9 +394,20 @@ def main():
     s2_launch = sum(s["stage2_launches"] for s in stats)
     s2_flops = sum(s["stage2_flops"] for s in stats)
     achieved = s2_flops / (s2_ms / 1e3) / 1e12 if s2_ms > 0 else None
-    split_factor = {0: 1, 1: 6, 2: 3, 3: 1, 4: 1, 5: 3, 6: 3}[args.precision]
+    split_factor = {0: 1, 1: 6, 2: 3, 3: 1, 4: 1, 5: 3, 6: 3, 7: 1}[args.precision]
     kpad = (-(-2 * 429 // 64) * 64) / (2 * 429)
-    if args.precision == 0:
+    if args.precision == 7:
+        # CUDA-core FP32: 148 SMs x 128 FP32 lanes x 2 flop per FMA x the maximum SM clock
+        fp32_peak = 148 * 128 * 2 * 2.032e9 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak if achieved else None, "traffic": None,
+                "peak_source": "FP32 FMA rate from unit counts and the 2032 MHz maximum clock",
+                "kernel": "k_dft_yz + k_dft_x_elph (stage 2 as a separable grid DFT, epilogue fused)",
+                "algorithmic_flops_per_launch": s2_flops / max(s2_launch, 1),
+                "avg_launch_ms": s2_ms / max(s2_launch, 1),
+                "note": "flops count the DFT's complex MACs (8 flop each); the fused rotation/delta epilogue "
+                        "is not counted"}
+    elif args.precision == 0:
         roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
                 "frac": achieved / 1.25 if achieved else None, "traffic": None,
                 "peak_source": "nominal FP64 1.25 TFLOP/s"}

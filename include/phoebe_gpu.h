@@ -62,7 +62,12 @@ typedef enum {
   PHOEBE_PREC_TF32 = 4,        /* single-pass TF32 contractions (reported, not within 1e-5) */
   PHOEBE_PREC_SPLIT_FP16 = 5,  /* two FP16 parts (hi + lo) of power-of-two scaled operands, three
                                   products: 22 significant bits at the cost of three BF16 passes */
-  PHOEBE_PREC_BF16X3 = 6       /* two BF16 parts, three products (reported, ~1e-5) */
+  PHOEBE_PREC_BF16X3 = 6,      /* two BF16 parts, three products (reported, ~1e-5) */
+  PHOEBE_PREC_FP32_DFT = 7     /* linewidths only: stage 1 as SPLIT_FP16; stage 2 evaluated for every
+                                  q of the grid as a separable DFT over the R_p residues mod the
+                                  q-grid sizes (e^{iq.R} factorises per axis on a grid), FP32 on
+                                  the CUDA cores, rotations and deltas fused; needs q-grid sizes
+                                  Nx, Nz <= 64 and (nw, 3na) in {(8,6), (2,3), (1,3)} */
 } phoebe_gpu_precision;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
@@ -179,7 +184,9 @@ typedef struct {
   int64_t couplings_executed;  /* pairs_executed * nw * 3na */
   int64_t kernel_launches;     /* kernels this library launched in the call */
   int64_t stage2_launches;     /* launches of the dominant (R_p contraction) kernel */
-  double stage2_flops;         /* algorithmic real flops of the R_p contraction (8 per cMAC) */
+  double stage2_flops;         /* real flops of the R_p contraction as evaluated, 8 per complex MAC:
+                                  8 N_Rp nw 3na per pair for the GEMM forms, the DFT's MACs for
+                                  PHOEBE_PREC_FP32_DFT */
   double stage2_ms;            /* event-timed device time of the R_p contraction launches */
   double bands_ms, phonons_ms, window_ms, stage1_ms, rotate_ms, delta_ms, total_ms;
   double sampler_ms;           /* sampled q sums: network scores, proposal and draws */

@@ -21,6 +21,7 @@ STATUS = {
     -6: "ERR_CUDA", -7: "ERR_TIMEOUT", -8: "ERR_NOTCONVERGED", -9: "ERR_UNSUPPORTED",
 }
 PREC_FP64, PREC_SPLIT_BF16, PREC_SPLIT_TF32, PREC_BF16, PREC_TF32, PREC_SPLIT_FP16, PREC_BF16X3 = 0, 1, 2, 3, 4, 5, 6
+PREC_FP32_DFT = 7
 SAMPLER_FULL, SAMPLER_LEARNED, SAMPLER_UNIFORM = 0, 1, 2
 MLP_NPARAM = 34177
 

@@ -1,0 +1,202 @@
+// Stage 2 on grid q points as a separable DFT over the R_p box (Sec. 5.5 Eq. 70 evaluated
+// exactly in another order).  With q = (jx/Nx, jy/Ny, jz/Nz) the phase of Eq. 13 factorises,
+// e^{2 pi i q.R} = e^{2 pi i jx rx/Nx} e^{2 pi i jy ry/Ny} e^{2 pi i jz rz/Nz} with r = R mod N,
+// so for every state
+//   G(q)[c] = sum_rx Ex[jx][rx] sum_ry Ey[jy][ry] sum_rz Ez[jz][rz] T~[rx][ry][rz][c],
+// T~ the stage-1 output T summed over the R_p of equal residue (weights folded in).  The y/z
+// sums run first (k_dft_yz, into Y[s][rx][jy][jz][c]); k_dft_x_elph finishes the x sum for one
+// q per thread and applies U_{k+q}^dagger, Z_q and the delta weights of Eq. 29 (Sec. 4.7 Eq. 61)
+// like the fused tensor-core epilogue.  FP32 on the CUDA cores.
+#include "dft.h"
+
+namespace phx {
+
+// One block per (column chunk of 16, rx residue, state); thread (jz, column).  For each chunk
+// of 16 jy: acc[jy] = sum_ry Ey[jy][ry] (sum_{R in (rx, ry)} Ez[jz][rz(R)] w_R T[s][R][c]).
+__global__ void __launch_bounds__(1024) k_dft_yz(DftYzArgs a) {
+  const int c = blockIdx.x * 16 + (threadIdx.x & 15);
+  const int jz = threadIdx.x >> 4;
+  const int ax = blockIdx.y;
+  const int s = blockIdx.z;
+  if (jz >= a.Nz || c >= a.E) return;
+  const float2* T = a.T + (int64_t)s * a.nR * a.E;
+  const int p0 = a.plane_off[ax], p1 = a.plane_off[ax + 1];
+  float2* Y = a.Y + (((int64_t)s * a.Bx + ax) * a.Ny) * a.Nz * a.E;
+  for (int jy0 = 0; jy0 < a.Ny; jy0 += 16) {
+    float2 acc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) acc[i] = make_float2(0.f, 0.f);
+    int e = p0;
+    while (e < p1) {
+      const int ay = a.ent_ay[e];
+      float2 yz = make_float2(0.f, 0.f);
+      for (; e < p1 && a.ent_ay[e] == ay; ++e) {
+        const float2 ez = a.Ez[jz * a.Bz + a.ent_az[e]];
+        const float2 t = T[(int64_t)a.ent_r[e] * a.E + c];
+        const float w = a.w[a.ent_r[e]];
+        const float tr = t.x * w, ti = t.y * w;
+        yz.x = fmaf(ez.x, tr, fmaf(-ez.y, ti, yz.x));
+        yz.y = fmaf(ez.x, ti, fmaf(ez.y, tr, yz.y));
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        if (jy0 + i < a.Ny) {
+          const float2 ey = a.Ey[(jy0 + i) * a.By + ay];
+          acc[i].x = fmaf(ey.x, yz.x, fmaf(-ey.y, yz.y, acc[i].x));
+          acc[i].y = fmaf(ey.x, yz.y, fmaf(ey.y, yz.x, acc[i].y));
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (jy0 + i < a.Ny) Y[((int64_t)(jy0 + i) * a.Nz + jz) * a.E + c] = acc[i];
+  }
+}
+
+// One block per (group of kDftLines (jy, jz) lines, state); thread (jx, line).  The lines'
+// Y[rx][c] sit in shared memory; each thread sums over rx for its q and runs the epilogue.
+template <int NW, int NM>
+__global__ void __launch_bounds__(kDftMaxThreads) k_dft_x_elph(DftXArgs a) {
+  constexpr int E = NW * NM;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* Ys = reinterpret_cast<float2*>(smem);  // [Bx][kDftLines][E]
+  const int s = blockIdx.y;
+  const int line0 = blockIdx.x * kDftLines;
+  const int nlines = a.Ny * a.Nz;
+  const float2* Yg = a.Y + (int64_t)s * a.Bx * nlines * E;
+  for (int i = threadIdx.x; i < a.Bx * kDftLines * E; i += blockDim.x) {
+    const int ax = i / (kDftLines * E), rem = i % (kDftLines * E);
+    const int l = rem / E, cc = rem % E;
+    Ys[i] = line0 + l < nlines ? Yg[((int64_t)ax * nlines + line0 + l) * E + cc] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int jx = threadIdx.x % a.Nx, l = threadIdx.x / a.Nx;
+  const int line = line0 + l;
+  double acc = 0.0;
+  if (l < kDftLines && line < nlines) {
+    float2 G[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) G[e] = make_float2(0.f, 0.f);
+    for (int ax = 0; ax < a.Bx; ++ax) {
+      const float2 ex = a.Ex[jx * a.Bx + ax];
+      const float2* y = Ys + (ax * kDftLines + l) * E;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const float2 v = y[e];
+        G[e].x = fmaf(ex.x, v.x, fmaf(-ex.y, v.y, G[e].x));
+        G[e].y = fmaf(ex.x, v.y, fmaf(ex.y, v.x, G[e].y));
+      }
+    }
+    const int jy = line / a.Nz, jz = line % a.Nz;
+    const int q = (jx * a.Ny + jy) * a.Nz + jz;
+    const int64_t kf = a.gm.k_to_fine(a.st_k[s]);
+    int kc[3];
+    grid_coords(kf, a.gm.nf, kc);
+    const int qc[3] = {jx, jy, jz};
+    int fc[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) fc[d] = (kc[d] + qc[d] * a.gm.sq[d]) % a.gm.nf[d];
+    const int64_t kq = grid_flat(fc, a.gm.nf);
+    const double e_n = a.epsF[kf * NW + a.st_b[s]];
+    const float en_hi = (float)e_n, en_lo = (float)(e_n - (double)en_hi);
+    float om[NM], nb[NM];
+#pragma unroll
+    for (int v = 0; v < NM; ++v) {
+      om[v] = a.omf[(int64_t)q * NM + v];
+      nb[v] = a.nBf[(int64_t)q * NM + v];
+    }
+    const float2* zq = a.Zf + (int64_t)q * NM * NM;
+    float part = 0.f;
+#pragma unroll 1
+    for (int mp = 0; mp < NW; ++mp) {
+      const float2 ee = a.eps2[kq * NW + mp];
+      const float dm = (en_hi - ee.x) + (en_lo - ee.y);  // eps_n - eps_{m', k+q}
+      if (!(fabsf(dm) < a.reach)) continue;
+      const float2* uh = a.UH + (kq * NW + mp) * NW;
+      float2 u[NW];
+#pragma unroll
+      for (int m = 0; m < NW; ++m) u[m] = uh[m];
+      float2 t[NM];
+#pragma unroll
+      for (int sa = 0; sa < NM; ++sa) {
+        t[sa] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int m = 0; m < NW; ++m) {
+          const float2 gv = G[sa * NW + m];
+          t[sa].x = fmaf(u[m].x, gv.x, fmaf(-u[m].y, gv.y, t[sa].x));
+          t[sa].y = fmaf(u[m].x, gv.y, fmaf(u[m].y, gv.x, t[sa].y));
+        }
+      }
+      const float f = a.f32[kq * NW + mp];
+#pragma unroll
+      for (int v = 0; v < NM; ++v) {
+        float2 g = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int sa = 0; sa < NM; ++sa) {
+          const float2 zz = zq[sa * NM + v];
+          g.x = fmaf(t[sa].x, zz.x, fmaf(-t[sa].y, zz.y, g.x));
+          g.y = fmaf(t[sa].x, zz.y, fmaf(t[sa].y, zz.x, g.y));
+        }
+        const float t1 = (dm - om[v]) * a.inv_sigma;
+        const float t2 = (dm + om[v]) * a.inv_sigma;
+        float w = 0.f;
+        if (t1 * t1 < a.cut2) w += (nb[v] + 1.f - f) * expf(-t1 * t1);
+        if (t2 * t2 < a.cut2) w += (nb[v] + f) * expf(-t2 * t2);
+        part = fmaf(g.x * g.x + g.y * g.y, w, part);
+      }
+    }
+    acc = (double)part * a.scale;
+  }
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) sum += red[i];
+    if (sum != 0.0) atomicAdd(a.gamma + a.s_base + s, sum);
+  }
+}
+
+template <int NW, int NM>
+static int launch_x(cudaStream_t st, const DftXArgs& a, int S) {
+  const size_t smem = sizeof(float2) * (size_t)a.Bx * kDftLines * NW * NM;
+  if (cudaFuncSetAttribute(k_dft_x_elph<NW, NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return -1;
+  const int lines = a.Ny * a.Nz;
+  dim3 grid((unsigned)((lines + kDftLines - 1) / kDftLines), (unsigned)S);
+  const int threads = (a.Nx * kDftLines + 31) / 32 * 32;  // whole warps for the reduction
+  k_dft_x_elph<NW, NM><<<grid, threads, smem, st>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int dft_launch(cudaStream_t st, const DftYzArgs& yz, const DftXArgs& x, int S, int nw, int nm) {
+  dim3 g1((unsigned)((yz.E + 15) / 16), (unsigned)yz.Bx, (unsigned)S);
+  k_dft_yz<<<g1, yz.Nz * 16, 0, st>>>(yz);
+  if (cudaGetLastError() != cudaSuccess) return -1;
+  if (nw == 8 && nm == 6) return launch_x<8, 6>(st, x, S);
+  if (nw == 2 && nm == 3) return launch_x<2, 3>(st, x, S);
+  if (nw == 1 && nm == 3) return launch_x<1, 3>(st, x, S);
+  return -2;
+}
+
+size_t dft_smem_bytes(int Bx, int E) { return sizeof(float2) * (size_t)Bx * kDftLines * E; }
+
+// E[j][a] = e^{2 pi i j r_a / N} for residues r_a (exact integer argument reduction, sincospi).
+__global__ void k_dft_table(const int* __restrict__ res, int B, int N, float2* __restrict__ E) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * B) return;
+  const int j = t / B, a = t % B;
+  const int r = (int)(((int64_t)j * res[a]) % N);
+  double sv, cv;
+  sincospi(2.0 * (double)r / (double)N, &sv, &cv);
+  E[t] = make_float2((float)cv, (float)sv);
+}
+
+int dft_table(cudaStream_t st, const int* res, int B, int N, float2* E) {
+  k_dft_table<<<(N * B + 127) / 128, 128, 0, st>>>(res, B, N, E);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace phx

@@ -34,6 +34,7 @@
 #include "tc.h"
 #include "sampler.h"
 #include "generic.h"
+#include "dft.h"
 #include "tc_ptx.cuh"
 
 struct TcState {
@@ -1778,6 +1779,207 @@ static int run_tc_mode(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const 
 #undef PHX_RUN
 }
 
+// Stage 2 by the separable grid DFT (dft.cu): stage 1 in split FP16 on the tensor cores, then the
+// R_p sum for every q of the grid in FP32 on the CUDA cores, with the fused rotations and deltas.
+static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& gm, int64_t ns,
+                   const std::vector<int>& hk, const int* st_k, const int* st_b, const double* epsF, const cplx* UF,
+                   const double* fF, const double* omega, const double* nB, const cplx* Zq, double* raw) {
+  constexpr int FMT = 0, NSPLIT = 2, NPROD = 3;
+  const int nw = c->nw, nm = 3 * c->na, nRe = c->nRe, nRp = c->nRp;
+  const int E = nw * nm;
+  if (!((nw == 8 && nm == 6) || (nw == 2 && nm == 3) || (nw == 1 && nm == 3)))
+    return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "the grid-DFT stage 2 is built for (nw, 3na) in {(8,6), (2,3), (1,3)}");
+  const int Nx = gm.nq[0], Ny = gm.nq[1], Nz = gm.nq[2];
+  if (Nx * kDftLines > kDftMaxThreads || Nz * 16 > 1024)
+    return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "the grid-DFT stage 2 needs q-grid sizes Nx <= 64 and Nz <= 64");
+  const int esz = 2, KB = 64;
+  const int Kp1 = (2 * nRe + KB - 1) / KB * KB;
+  const int64_t C = (int64_t)nRp * nw * nw * nm;
+  const int64_t NF = (int64_t)gm.nf[0] * gm.nf[1] * gm.nf[2];
+  const int64_t Nq = (int64_t)Nx * Ny * Nz;
+  int st;
+  Timer tm;
+  int* err = (int*)ensure(c, "tc_err", 64, &st);
+  if (!err) return st;
+  CK(c, cudaMemsetAsync(err, 0, 64, c->stream));
+  const float sA1 = host_pow2_scale(c->we_max);
+  TRY((ensure_g_operand<FMT, NSPLIT>(c, C, Kp1, esz)));
+  Parts Pg{{c->tc->g_part[0], c->tc->g_part[1], c->tc->g_part[2]}};
+  tm.begin(c);
+  float2* UH = (float2*)ensure(c, "tc_UH", sizeof(float2) * NF * nw * nw, &st);
+  if (!UH) return st;
+  float* f32 = (float*)ensure(c, "tc_f32", sizeof(float) * NF * nw, &st);
+  if (!f32) return st;
+  float2* eps2 = (float2*)ensure(c, "tc_eps2", sizeof(float2) * NF * nw, &st);
+  if (!eps2) return st;
+  unsigned long long* dmax = (unsigned long long*)ensure(c, "tc_max", 64, &st);
+  if (!dmax) return st;
+  float2* Zf = (float2*)ensure(c, "tcg_Zf", sizeof(float2) * Nq * nm * nm, &st);
+  if (!Zf) return st;
+  float* omf = (float*)ensure(c, "tcg_omf", sizeof(float) * Nq * nm, &st);
+  if (!omf) return st;
+  float* nBf = (float*)ensure(c, "tcg_nBf", sizeof(float) * Nq * nm, &st);
+  if (!nBf) return st;
+  k_tables_el<<<(unsigned)((NF * nw * nw + 255) / 256), 256, 0, c->stream>>>(UF, fF, epsF, NF, nw, UH, f32, eps2);
+  CK(c, cudaMemsetAsync(dmax, 0, 64, c->stream));
+  k_absmax_f64<<<64, 256, 0, c->stream>>>(omega, Nq * nm, dmax);
+  k_tables_ph<<<(unsigned)((Nq * nm * nm + 255) / 256), 256, 0, c->stream>>>(Zq, omega, nB, Nq, nm, Zf, omf, nBf);
+  c->launches += 3;
+  CK(c, cudaGetLastError());
+  unsigned long long ombits = 0;
+  CK(c, cudaMemcpyAsync(&ombits, dmax, sizeof(ombits), cudaMemcpyDeviceToHost, c->stream));
+  // residues of R_p per axis and the entry lists of the y/z sums
+  std::vector<int> Rp((size_t)3 * nRp);
+  std::vector<double> wp(nRp);
+  CK(c, cudaMemcpyAsync(Rp.data(), c->bufs["Rp"].p, sizeof(int) * 3 * nRp, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemcpyAsync(wp.data(), c->bufs["wp"].p, sizeof(double) * nRp, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  const int N3[3] = {Nx, Ny, Nz};
+  std::vector<int> resv[3];
+  std::vector<int> idx((size_t)3 * nRp);
+  for (int d = 0; d < 3; ++d) {
+    std::vector<int> r(nRp);
+    for (int i = 0; i < nRp; ++i) r[i] = ((Rp[3 * i + d] % N3[d]) + N3[d]) % N3[d];
+    resv[d] = r;
+    std::sort(resv[d].begin(), resv[d].end());
+    resv[d].erase(std::unique(resv[d].begin(), resv[d].end()), resv[d].end());
+    for (int i = 0; i < nRp; ++i)
+      idx[3 * i + d] = (int)(std::lower_bound(resv[d].begin(), resv[d].end(), r[i]) - resv[d].begin());
+  }
+  const int Bx = (int)resv[0].size(), By = (int)resv[1].size(), Bz = (int)resv[2].size();
+  std::vector<int> order(nRp);
+  for (int i = 0; i < nRp; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    if (idx[3 * a] != idx[3 * b]) return idx[3 * a] < idx[3 * b];
+    return idx[3 * a + 1] < idx[3 * b + 1];
+  });
+  std::vector<int> plane_off(Bx + 1, 0), ent_ay(nRp), ent_az(nRp), ent_r(nRp);
+  for (int e = 0; e < nRp; ++e) {
+    const int r = order[e];
+    ent_ay[e] = idx[3 * r + 1];
+    ent_az[e] = idx[3 * r + 2];
+    ent_r[e] = r;
+    plane_off[idx[3 * r] + 1] = e + 1;
+  }
+  for (int a = 1; a <= Bx; ++a) plane_off[a] = std::max(plane_off[a], plane_off[a - 1]);
+  std::vector<float> wf(nRp);
+  for (int i = 0; i < nRp; ++i) wf[i] = (float)wp[i];
+  void *d_po, *d_ay, *d_az, *d_r, *d_w, *d_rx, *d_ry, *d_rz;
+  TRY(upload(c, "dft_po", plane_off.data(), sizeof(int) * (Bx + 1), &d_po));
+  TRY(upload(c, "dft_ay", ent_ay.data(), sizeof(int) * nRp, &d_ay));
+  TRY(upload(c, "dft_az", ent_az.data(), sizeof(int) * nRp, &d_az));
+  TRY(upload(c, "dft_r", ent_r.data(), sizeof(int) * nRp, &d_r));
+  TRY(upload(c, "dft_w", wf.data(), sizeof(float) * nRp, &d_w));
+  TRY(upload(c, "dft_rx", resv[0].data(), sizeof(int) * Bx, &d_rx));
+  TRY(upload(c, "dft_ry", resv[1].data(), sizeof(int) * By, &d_ry));
+  TRY(upload(c, "dft_rz", resv[2].data(), sizeof(int) * Bz, &d_rz));
+  float2* Ex = (float2*)ensure(c, "dft_Ex", sizeof(float2) * Nx * Bx, &st);
+  if (!Ex) return st;
+  float2* Ey = (float2*)ensure(c, "dft_Ey", sizeof(float2) * Ny * By, &st);
+  if (!Ey) return st;
+  float2* Ez = (float2*)ensure(c, "dft_Ez", sizeof(float2) * Nz * Bz, &st);
+  if (!Ez) return st;
+  if (dft_table(c->stream, (const int*)d_rx, Bx, Nx, Ex) || dft_table(c->stream, (const int*)d_ry, By, Ny, Ey) ||
+      dft_table(c->stream, (const int*)d_rz, Bz, Nz, Ez)) {
+    cudaGetLastError();
+    return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the DFT phase tables failed");
+  }
+  c->launches += 3;
+  GridPhase gk = make_phase(gm.nk);
+  cplx* cis_k;
+  TRY(cis_table(c, gk, "cis_k", &cis_k));
+  double omega_max;
+  memcpy(&omega_max, &ombits, sizeof(double));
+  tm.end(c, &c->stats.stage1_ms);
+  unsigned* tmaxp = (unsigned*)ensure(c, "tc_tmax", 64, &st);
+  if (!tmaxp) return st;
+  const int64_t per_state = (int64_t)Bx * Ny * Nz * E * (int64_t)sizeof(float2);
+  const int max_states = p->max_batch_states > 0
+                             ? p->max_batch_states
+                             : (int)std::max<int64_t>(1, std::min<int64_t>(4096, ((int64_t)8 << 30) / per_state));
+  std::vector<int> kb_list, st_kb;
+  int64_t i0 = 0;
+  while (i0 < ns) {
+    const int64_t i1 = next_batch(hk, ns, i0, max_states, &kb_list, &st_kb);
+    const int S = (int)(i1 - i0);
+    const int nkb = (int)kb_list.size();
+    void *d_kb, *d_stkb;
+    TRY(upload(c, "tc_batch_k", kb_list.data(), sizeof(int) * nkb, &d_kb));
+    TRY(upload(c, "tc_batch_stkb", st_kb.data(), sizeof(int) * S, &d_stkb));
+    tm.begin(c);
+    float2* Tb;
+    TRY((stage1_batch<FMT, NSPLIT, NPROD>(c, gm, kb_list, st_kb, i0, st_k, st_b, UF, Pg, sA1, cis_k, gk, err, tmaxp,
+                                          (const int*)d_kb, (const int*)d_stkb, &Tb)));
+    tm.end(c, &c->stats.stage1_ms);
+    float2* Y = (float2*)ensure(c, "dft_Y", (size_t)per_state * S, &st);
+    if (!Y) return st;
+    DftYzArgs yz;
+    yz.T = Tb;
+    yz.w = (const float*)d_w;
+    yz.nR = nRp;
+    yz.E = E;
+    yz.Bx = Bx;
+    yz.By = By;
+    yz.Bz = Bz;
+    yz.Ny = Ny;
+    yz.Nz = Nz;
+    yz.plane_off = (const int*)d_po;
+    yz.ent_ay = (const int*)d_ay;
+    yz.ent_az = (const int*)d_az;
+    yz.ent_r = (const int*)d_r;
+    yz.Ey = Ey;
+    yz.Ez = Ez;
+    yz.Y = Y;
+    DftXArgs x;
+    x.Y = Y;
+    x.Bx = Bx;
+    x.Nx = Nx;
+    x.Ny = Ny;
+    x.Nz = Nz;
+    x.Ex = Ex;
+    x.st_k = st_k + i0;
+    x.st_b = st_b + i0;
+    x.epsF = epsF;
+    x.gm = gm;
+    x.eps2 = eps2;
+    x.f32 = f32;
+    x.UH = UH;
+    x.Zf = Zf;
+    x.omf = omf;
+    x.nBf = nBf;
+    x.reach = (float)(omega_max + p->delta_cut_sigmas * p->sigma_eV) * 1.0001f;
+    x.inv_sigma = (float)(1.0 / p->sigma_eV);
+    x.cut2 = (float)(p->delta_cut_sigmas * p->delta_cut_sigmas);
+    x.scale = (2.0 * kPi / (double)Nq) / (kSqrtPi * p->sigma_eV);
+    x.gamma = raw;
+    x.s_base = i0;
+    tm.begin(c);
+    const int r = dft_launch(c->stream, yz, x, S, nw, nm);
+    if (r != 0) {
+      cudaGetLastError();
+      return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the grid-DFT stage 2 failed");
+    }
+    c->launches += 2;
+    c->stats.stage2_launches++;
+    tm.end(c, &c->stats.stage2_ms);
+    i0 = i1;
+  }
+  int herr = 0;
+  CK(c, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (herr) return fail(c, PHOEBE_GPU_ERR_TIMEOUT, "a tensor-core pipeline wait ran out; results discarded");
+  c->stats.pairs_executed = ns * Nq;
+  // complex MACs of the DFT as evaluated: y/z sums per state, x sum per (state, q)
+  double yz_cmac = 0.0;
+  for (int a = 0; a < Bx; ++a) {
+    int groups = 0;
+    for (int e = plane_off[a]; e < plane_off[a + 1]; ++e) groups += (e == plane_off[a] || ent_ay[e] != ent_ay[e - 1]);
+    yz_cmac += (double)((Ny + 15) / 16) * ((plane_off[a + 1] - plane_off[a]) + 16.0 * groups) * Nz * E;
+  }
+  c->stats.stage2_flops = 8.0 * (double)ns * (yz_cmac + (double)Nq * Bx * E);
+  return PHOEBE_GPU_OK;
+}
+
 static int run_tc_generic_mode(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& gm, int64_t ns,
                                const std::vector<int>& hk, const int* st_k, const int* st_b, const double* epsF,
                                const cplx* UF, const double* fF, const double* omega, const double* nB,
@@ -1801,6 +2003,11 @@ int run_tc(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& gm,
            const double* fF, const double* omega, const double* nB, const cplx* Zq, double* raw) {
   if (c->cc < 100) return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "tensor-core precisions need an sm_10x GPU");
   const int nw = c->nw, nm = 3 * c->na;
+  if (p->precision == PHOEBE_PREC_FP32_DFT) {
+    if (c->defer || c->isreq)
+      return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "the grid-DFT stage 2 serves the full q sum of single calls");
+    return run_dft(c, p, gm, ns, hk, st_k, st_b, epsF, UF, fF, omega, nB, Zq, raw);
+  }
   if (c->defer) {  // batched materials: one stage-2 form for every shape, recorded for later issue
     if (c->isreq) return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "batched linewidths use the full q sum");
     return run_tc_generic_mode(c, p, gm, ns, hk, st_k, st_b, epsF, UF, fF, omega, nB, Zq, raw);

@@ -43,7 +43,7 @@ def toy_ctx(pg):
 
 
 @pytest.mark.parametrize("prec,tol", [(1, SPLIT_RTOL), (2, SPLIT_RTOL), (5, SPLIT_RTOL), (3, SINGLE_RTOL),
-                                      (4, SINGLE_RTOL), (6, 1e-4)])
+                                      (4, SINGLE_RTOL), (6, 1e-4), (7, SPLIT_RTOL)])
 def test_toy_full_grid_precisions(pg, toy_ctx, toy_ref, prec, tol):
     ctx, prm = toy_ctx
     ks, bs, gam = ctx.linewidths_rta(prm, precision=prec)
@@ -69,7 +69,7 @@ def test_toy_subset_and_coarse_k(pg, toy_ctx):
     assert rel_err(gam, ref) <= SPLIT_RTOL
 
 
-@pytest.mark.parametrize("prec", [1, 5])
+@pytest.mark.parametrize("prec", [1, 5, 7])
 def test_einstein_closed_form_split(pg, prec):
     mat, prm = W.tb_einstein(eps0=0.05, t=0.25, lam=0.215, n=8, mu=0.1)
     with pg.PhoebeGPU(0) as ctx:
@@ -107,7 +107,7 @@ def test_si_like_full_grid_split_fp16_sampled(pg, si):
     assert err <= SPLIT_RTOL
 
 
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec", [1, 2, 7])
 def test_si_like_subset_split_bf16_tf32(pg, si, prec):
     mat, prm, tab = si
     eg = tab[1][tab[3]]
@@ -121,3 +121,15 @@ def test_si_like_subset_split_bf16_tf32(pg, si, prec):
     err = rel_err(gam, ref)
     print(f"Si-like subset precision {prec}: max rel err {err:.3e}")
     assert err <= SPLIT_RTOL
+
+
+def test_grid_dft_matches_tensor_core_stage2_on_full_grid(pg, si):
+    """Stage 2 as the separable grid DFT (FP32) against the tensor-core GEMM (split FP16) over every
+    active state of the Si-like 40^3 grid: both approximate the same FP64 sum to ~2e-6."""
+    mat, prm, tab = si
+    with pg.PhoebeGPU(0) as ctx:
+        ctx.set_material(mat)
+        k5, b5, g5 = ctx.linewidths_rta(prm, precision=5)
+        k7, b7, g7 = ctx.linewidths_rta(prm, precision=7, max_batch_states=700)   # ragged batches
+    assert np.array_equal(k5, k7) and np.array_equal(b5, b7)
+    assert rel_err(g7, g5) <= 2 * SPLIT_RTOL
