@@ -13,35 +13,61 @@ namespace phx {
 
 // One block per (column chunk of 16, rx residue, state); thread (jz, column).  For each chunk
 // of 16 jy: acc[jy] = sum_ry Ey[jy][ry] (sum_{R in (rx, ry)} Ez[jz][rz(R)] w_R T[s][R][c]).
+// The plane's weighted T columns and the phase tables are staged in shared memory.
 __global__ void __launch_bounds__(1024) k_dft_yz(DftYzArgs a) {
-  const int c = blockIdx.x * 16 + (threadIdx.x & 15);
-  const int jz = threadIdx.x >> 4;
-  const int ax = blockIdx.y;
-  const int s = blockIdx.z;
-  if (jz >= a.Nz || c >= a.E) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int p0 = a.plane_off[blockIdx.y], p1 = a.plane_off[blockIdx.y + 1];
+  const int ne = p1 - p0;
+  float2* Ts = reinterpret_cast<float2*>(smem);  // [ne][16]
+  float2* Eys = Ts + (size_t)ne * 16;            // [Ny][By]
+  float2* Ezs = Eys + (size_t)a.Ny * a.By;       // [Nz][Bz]
+  int* ays = reinterpret_cast<int*>(Ezs + (size_t)a.Nz * a.Bz);  // [ne]
+  int* azs = ays + ne;                                           // [ne]
+  const int s = blockIdx.z, ax = blockIdx.y, c0 = blockIdx.x * 16;
   const float2* T = a.T + (int64_t)s * a.nR * a.E;
-  const int p0 = a.plane_off[ax], p1 = a.plane_off[ax + 1];
+  for (int i = threadIdx.x; i < ne * 16; i += blockDim.x) {
+    const int e = p0 + i / 16, cc = c0 + (i & 15);
+    const int r = a.ent_r[e];
+    float2 t = make_float2(0.f, 0.f);
+    if (cc < a.E) {
+      t = T[(int64_t)r * a.E + cc];
+      const float w = a.w[r];
+      t.x *= w;
+      t.y *= w;
+    }
+    Ts[i] = t;
+  }
+  for (int i = threadIdx.x; i < a.Ny * a.By; i += blockDim.x) Eys[i] = a.Ey[i];
+  for (int i = threadIdx.x; i < a.Nz * a.Bz; i += blockDim.x) Ezs[i] = a.Ez[i];
+  for (int i = threadIdx.x; i < ne; i += blockDim.x) {
+    ays[i] = a.ent_ay[p0 + i];
+    azs[i] = a.ent_az[p0 + i];
+  }
+  __syncthreads();
+  const int cl = threadIdx.x & 15;
+  const int c = c0 + cl;
+  const int jz = threadIdx.x >> 4;
+  if (jz >= a.Nz || c >= a.E) return;
   float2* Y = a.Y + (((int64_t)s * a.Bx + ax) * a.Ny) * a.Nz * a.E;
+  const float2* ez_row = Ezs + jz * a.Bz;
   for (int jy0 = 0; jy0 < a.Ny; jy0 += 16) {
     float2 acc[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) acc[i] = make_float2(0.f, 0.f);
-    int e = p0;
-    while (e < p1) {
-      const int ay = a.ent_ay[e];
+    int e = 0;
+    while (e < ne) {
+      const int ay = ays[e];
       float2 yz = make_float2(0.f, 0.f);
-      for (; e < p1 && a.ent_ay[e] == ay; ++e) {
-        const float2 ez = a.Ez[jz * a.Bz + a.ent_az[e]];
-        const float2 t = T[(int64_t)a.ent_r[e] * a.E + c];
-        const float w = a.w[a.ent_r[e]];
-        const float tr = t.x * w, ti = t.y * w;
-        yz.x = fmaf(ez.x, tr, fmaf(-ez.y, ti, yz.x));
-        yz.y = fmaf(ez.x, ti, fmaf(ez.y, tr, yz.y));
+      for (; e < ne && ays[e] == ay; ++e) {
+        const float2 ez = ez_row[azs[e]];
+        const float2 t = Ts[e * 16 + cl];
+        yz.x = fmaf(ez.x, t.x, fmaf(-ez.y, t.y, yz.x));
+        yz.y = fmaf(ez.x, t.y, fmaf(ez.y, t.x, yz.y));
       }
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         if (jy0 + i < a.Ny) {
-          const float2 ey = a.Ey[(jy0 + i) * a.By + ay];
+          const float2 ey = Eys[(jy0 + i) * a.By + ay];
           acc[i].x = fmaf(ey.x, yz.x, fmaf(-ey.y, yz.y, acc[i].x));
           acc[i].y = fmaf(ey.x, yz.y, fmaf(ey.y, yz.x, acc[i].y));
         }
@@ -53,13 +79,19 @@ __global__ void __launch_bounds__(1024) k_dft_yz(DftYzArgs a) {
   }
 }
 
-// One block per (group of kDftLines (jy, jz) lines, state); thread (jx, line).  The lines'
-// Y[rx][c] sit in shared memory; each thread sums over rx for its q and runs the epilogue.
+// One block per (group of kDftLines (jy, jz) lines, state); thread (jx, line).  Phase 1: each
+// thread sums over rx for its q (G in registers, then its own slot of shared memory) and marks the
+// final bands m' that can reach the delta window.  Phase 2: the warp compacts its (q, m') items
+// and every lane takes items in turn, so a band is rotated only for the q that need it.
 template <int NW, int NM>
 __global__ void __launch_bounds__(kDftMaxThreads) k_dft_x_elph(DftXArgs a) {
   constexpr int E = NW * NM;
   extern __shared__ __align__(16) unsigned char smem[];
-  float2* Ys = reinterpret_cast<float2*>(smem);  // [Bx][kDftLines][E]
+  float2* Ys = reinterpret_cast<float2*>(smem);                       // [Bx][kDftLines][E]
+  float2* Gs = Ys + (size_t)a.Bx * kDftLines * E;                      // [E][threads] (element-major)
+  float2* Exs = Gs + (size_t)blockDim.x * E;                           // [Nx][Bx]
+  int* items = reinterpret_cast<int*>(Exs + (size_t)a.Nx * a.Bx);      // [warps][32 * NW]
+  int* qkq = items + (blockDim.x >> 5) * 32 * NW;                      // [threads][2]: q, k+q
   const int s = blockIdx.y;
   const int line0 = blockIdx.x * kDftLines;
   const int nlines = a.Ny * a.Nz;
@@ -69,87 +101,119 @@ __global__ void __launch_bounds__(kDftMaxThreads) k_dft_x_elph(DftXArgs a) {
     const int l = rem / E, cc = rem % E;
     Ys[i] = line0 + l < nlines ? Yg[((int64_t)ax * nlines + line0 + l) * E + cc] : make_float2(0.f, 0.f);
   }
+  for (int i = threadIdx.x; i < a.Nx * a.Bx; i += blockDim.x) Exs[i] = a.Ex[i];
   __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int jx = threadIdx.x % a.Nx, l = threadIdx.x / a.Nx;
   const int line = line0 + l;
-  double acc = 0.0;
+  const int64_t kf = a.gm.k_to_fine(a.st_k[s]);
+  const double e_n = a.epsF[kf * NW + a.st_b[s]];
+  const float en_hi = (float)e_n, en_lo = (float)(e_n - (double)en_hi);
+  unsigned need = 0;
   if (l < kDftLines && line < nlines) {
     float2 G[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) G[e] = make_float2(0.f, 0.f);
     for (int ax = 0; ax < a.Bx; ++ax) {
-      const float2 ex = a.Ex[jx * a.Bx + ax];
+      const float2 ex = Exs[jx * a.Bx + ax];
       const float2* y = Ys + (ax * kDftLines + l) * E;
+      if constexpr (E % 2 == 0) {  // two complex values per 16-byte load
 #pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const float2 v = y[e];
-        G[e].x = fmaf(ex.x, v.x, fmaf(-ex.y, v.y, G[e].x));
-        G[e].y = fmaf(ex.x, v.y, fmaf(ex.y, v.x, G[e].y));
+        for (int e = 0; e < E; e += 2) {
+          const float4 v = reinterpret_cast<const float4*>(y)[e / 2];
+          G[e].x = fmaf(ex.x, v.x, fmaf(-ex.y, v.y, G[e].x));
+          G[e].y = fmaf(ex.x, v.y, fmaf(ex.y, v.x, G[e].y));
+          G[e + 1].x = fmaf(ex.x, v.z, fmaf(-ex.y, v.w, G[e + 1].x));
+          G[e + 1].y = fmaf(ex.x, v.w, fmaf(ex.y, v.z, G[e + 1].y));
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const float2 v = y[e];
+          G[e].x = fmaf(ex.x, v.x, fmaf(-ex.y, v.y, G[e].x));
+          G[e].y = fmaf(ex.x, v.y, fmaf(ex.y, v.x, G[e].y));
+        }
       }
     }
+#pragma unroll
+    for (int e = 0; e < E; ++e) Gs[(size_t)e * blockDim.x + threadIdx.x] = G[e];
     const int jy = line / a.Nz, jz = line % a.Nz;
     const int q = (jx * a.Ny + jy) * a.Nz + jz;
-    const int64_t kf = a.gm.k_to_fine(a.st_k[s]);
     int kc[3];
     grid_coords(kf, a.gm.nf, kc);
     const int qc[3] = {jx, jy, jz};
     int fc[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) fc[d] = (kc[d] + qc[d] * a.gm.sq[d]) % a.gm.nf[d];
-    const int64_t kq = grid_flat(fc, a.gm.nf);
-    const double e_n = a.epsF[kf * NW + a.st_b[s]];
-    const float en_hi = (float)e_n, en_lo = (float)(e_n - (double)en_hi);
-    float om[NM], nb[NM];
+    const int kq = (int)grid_flat(fc, a.gm.nf);
+    qkq[2 * threadIdx.x] = q;
+    qkq[2 * threadIdx.x + 1] = kq;
 #pragma unroll
-    for (int v = 0; v < NM; ++v) {
-      om[v] = a.omf[(int64_t)q * NM + v];
-      nb[v] = a.nBf[(int64_t)q * NM + v];
+    for (int mp = 0; mp < NW; ++mp) {
+      const float2 ee = a.eps2[(int64_t)kq * NW + mp];
+      const float dm = (en_hi - ee.x) + (en_lo - ee.y);
+      if (fabsf(dm) < a.reach) need |= 1u << mp;
     }
+  }
+  // compact the warp's (thread, m') items
+  const int cnt = __popc(need);
+  int off = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, off, o);
+    if (lane >= o) off += t;
+  }
+  const int total = __shfl_sync(0xffffffffu, off, 31);
+  off -= cnt;
+  int* wl = items + warp * 32 * NW;
+  for (unsigned m = need; m; m &= m - 1) wl[off++] = (threadIdx.x << 4) | (__ffs(m) - 1);
+  __syncwarp();
+  double acc = 0.0;
+  for (int it = lane; it < total; it += 32) {
+    const int src = wl[it] >> 4, mp = wl[it] & 15;
+    const int q = qkq[2 * src], kq = qkq[2 * src + 1];
+    const float2* gs = Gs + src;  // element e at gs[e * blockDim.x]
+    const float2 ee = a.eps2[(int64_t)kq * NW + mp];
+    const float dm = (en_hi - ee.x) + (en_lo - ee.y);
+    const float2* uh = a.UH + ((int64_t)kq * NW + mp) * NW;
+    float2 u[NW];
+#pragma unroll
+    for (int m = 0; m < NW; ++m) u[m] = uh[m];
+    float2 t[NM];
+#pragma unroll
+    for (int sa = 0; sa < NM; ++sa) {
+      t[sa] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int m = 0; m < NW; ++m) {
+        const float2 gv = gs[(size_t)(sa * NW + m) * blockDim.x];
+        t[sa].x = fmaf(u[m].x, gv.x, fmaf(-u[m].y, gv.y, t[sa].x));
+        t[sa].y = fmaf(u[m].x, gv.y, fmaf(u[m].y, gv.x, t[sa].y));
+      }
+    }
+    const float f = a.f32[(int64_t)kq * NW + mp];
     const float2* zq = a.Zf + (int64_t)q * NM * NM;
     float part = 0.f;
-#pragma unroll 1
-    for (int mp = 0; mp < NW; ++mp) {
-      const float2 ee = a.eps2[kq * NW + mp];
-      const float dm = (en_hi - ee.x) + (en_lo - ee.y);  // eps_n - eps_{m', k+q}
-      if (!(fabsf(dm) < a.reach)) continue;
-      const float2* uh = a.UH + (kq * NW + mp) * NW;
-      float2 u[NW];
 #pragma unroll
-      for (int m = 0; m < NW; ++m) u[m] = uh[m];
-      float2 t[NM];
+    for (int v = 0; v < NM; ++v) {
+      float2 g = make_float2(0.f, 0.f);
 #pragma unroll
       for (int sa = 0; sa < NM; ++sa) {
-        t[sa] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int m = 0; m < NW; ++m) {
-          const float2 gv = G[sa * NW + m];
-          t[sa].x = fmaf(u[m].x, gv.x, fmaf(-u[m].y, gv.y, t[sa].x));
-          t[sa].y = fmaf(u[m].x, gv.y, fmaf(u[m].y, gv.x, t[sa].y));
-        }
+        const float2 zz = zq[sa * NM + v];
+        g.x = fmaf(t[sa].x, zz.x, fmaf(-t[sa].y, zz.y, g.x));
+        g.y = fmaf(t[sa].x, zz.y, fmaf(t[sa].y, zz.x, g.y));
       }
-      const float f = a.f32[kq * NW + mp];
-#pragma unroll
-      for (int v = 0; v < NM; ++v) {
-        float2 g = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int sa = 0; sa < NM; ++sa) {
-          const float2 zz = zq[sa * NM + v];
-          g.x = fmaf(t[sa].x, zz.x, fmaf(-t[sa].y, zz.y, g.x));
-          g.y = fmaf(t[sa].x, zz.y, fmaf(t[sa].y, zz.x, g.y));
-        }
-        const float t1 = (dm - om[v]) * a.inv_sigma;
-        const float t2 = (dm + om[v]) * a.inv_sigma;
-        float w = 0.f;
-        if (t1 * t1 < a.cut2) w += (nb[v] + 1.f - f) * expf(-t1 * t1);
-        if (t2 * t2 < a.cut2) w += (nb[v] + f) * expf(-t2 * t2);
-        part = fmaf(g.x * g.x + g.y * g.y, w, part);
-      }
+      const float om = a.omf[(int64_t)q * NM + v], nb = a.nBf[(int64_t)q * NM + v];
+      const float t1 = (dm - om) * a.inv_sigma;
+      const float t2 = (dm + om) * a.inv_sigma;
+      float w = 0.f;
+      if (t1 * t1 < a.cut2) w += (nb + 1.f - f) * expf(-t1 * t1);
+      if (t2 * t2 < a.cut2) w += (nb + f) * expf(-t2 * t2);
+      part = fmaf(g.x * g.x + g.y * g.y, w, part);
     }
-    acc = (double)part * a.scale;
+    acc += (double)part * a.scale;
   }
   __shared__ double red[32];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  if (lane == 0) red[warp] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double sum = 0.0;
@@ -160,20 +224,22 @@ __global__ void __launch_bounds__(kDftMaxThreads) k_dft_x_elph(DftXArgs a) {
 
 template <int NW, int NM>
 static int launch_x(cudaStream_t st, const DftXArgs& a, int S) {
-  const size_t smem = sizeof(float2) * (size_t)a.Bx * kDftLines * NW * NM;
+  const int threads = (a.Nx * kDftLines + 31) / 32 * 32;  // whole warps for the compaction and reduction
+  const size_t smem = dft_smem_bytes(a.Bx, NW * NM, threads, NW, a.Nx);
   if (cudaFuncSetAttribute(k_dft_x_elph<NW, NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return -1;
   const int lines = a.Ny * a.Nz;
   dim3 grid((unsigned)((lines + kDftLines - 1) / kDftLines), (unsigned)S);
-  const int threads = (a.Nx * kDftLines + 31) / 32 * 32;  // whole warps for the reduction
   k_dft_x_elph<NW, NM><<<grid, threads, smem, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int dft_launch(cudaStream_t st, const DftYzArgs& yz, const DftXArgs& x, int S, int nw, int nm) {
   dim3 g1((unsigned)((yz.E + 15) / 16), (unsigned)yz.Bx, (unsigned)S);
-  k_dft_yz<<<g1, yz.Nz * 16, 0, st>>>(yz);
+  const size_t sm1 = dft_yz_smem_bytes(yz.ne_max, yz.Ny, yz.By, yz.Nz, yz.Bz);
+  if (cudaFuncSetAttribute(k_dft_yz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1) != cudaSuccess) return -1;
+  k_dft_yz<<<g1, yz.Nz * 16, sm1, st>>>(yz);
   if (cudaGetLastError() != cudaSuccess) return -1;
   if (nw == 8 && nm == 6) return launch_x<8, 6>(st, x, S);
   if (nw == 2 && nm == 3) return launch_x<2, 3>(st, x, S);
@@ -181,7 +247,14 @@ int dft_launch(cudaStream_t st, const DftYzArgs& yz, const DftXArgs& x, int S, i
   return -2;
 }
 
-size_t dft_smem_bytes(int Bx, int E) { return sizeof(float2) * (size_t)Bx * kDftLines * E; }
+size_t dft_smem_bytes(int Bx, int E, int threads, int nw, int Nx) {
+  return sizeof(float2) * ((size_t)Bx * kDftLines * E + (size_t)threads * E + (size_t)Nx * Bx) +
+         sizeof(int) * ((size_t)(threads / 32) * 32 * nw + 2 * (size_t)threads);
+}
+
+size_t dft_yz_smem_bytes(int ne_max, int Ny, int By, int Nz, int Bz) {
+  return sizeof(float2) * ((size_t)ne_max * 16 + (size_t)Ny * By + (size_t)Nz * Bz) + sizeof(int) * 2 * (size_t)ne_max;
+}
 
 // E[j][a] = e^{2 pi i j r_a / N} for residues r_a (exact integer argument reduction, sincospi).
 __global__ void k_dft_table(const int* __restrict__ res, int B, int N, float2* __restrict__ E) {

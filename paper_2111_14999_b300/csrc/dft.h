@@ -5,7 +5,7 @@
 
 namespace phx {
 
-constexpr int kDftLines = 8;          // (jy, jz) lines per block of the x-sum kernel
+constexpr int kDftLines = 4;          // (jy, jz) lines per block of the x-sum kernel
 constexpr int kDftMaxThreads = 512;   // Nx * kDftLines <= 512 (Nx <= 64)
 
 struct DftYzArgs {
@@ -15,6 +15,7 @@ struct DftYzArgs {
   int Bx, By, Bz;        // residues of R_p mod N per axis
   int Ny, Nz;
   const int* plane_off;  // [Bx+1] entries of each rx residue
+  int ne_max;            // most entries of one rx residue
   const int* ent_ay;     // per entry (sorted by rx residue, then ry residue): ry residue index
   const int* ent_az;     //   rz residue index
   const int* ent_r;      //   R_p index
@@ -45,7 +46,8 @@ struct DftXArgs {
 
 // Launches both kernels for S states; -1 on a launch error, -2 for a (nw, 3na) without a kernel.
 int dft_launch(cudaStream_t st, const DftYzArgs& yz, const DftXArgs& x, int S, int nw, int nm);
-size_t dft_smem_bytes(int Bx, int E);
+size_t dft_smem_bytes(int Bx, int E, int threads, int nw, int Nx);
+size_t dft_yz_smem_bytes(int ne_max, int Ny, int By, int Nz, int Bz);
 int dft_table(cudaStream_t st, const int* res, int B, int N, float2* E);
 
 }  // namespace phx

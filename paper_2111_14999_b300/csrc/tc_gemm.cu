@@ -1924,6 +1924,8 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
     yz.Ny = Ny;
     yz.Nz = Nz;
     yz.plane_off = (const int*)d_po;
+    yz.ne_max = 0;
+    for (int a = 0; a < Bx; ++a) yz.ne_max = std::max(yz.ne_max, plane_off[a + 1] - plane_off[a]);
     yz.ent_ay = (const int*)d_ay;
     yz.ent_az = (const int*)d_az;
     yz.ent_r = (const int*)d_r;
