@@ -8,6 +8,8 @@ T = 300 K, sigma = 0.02 eV, window +-0.5 eV), inputs already resident in HBM.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P] [--impl reference]
 
+The default mode evaluates stage 2 as a separable DFT over the R_p residues (FP32,
+exact on the grid); the tensor-core stage 2 (split FP16) is timed beside it.
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 on a bounded sample of the same workload instead.
 """
@@ -30,7 +32,8 @@ import numpy as np  # noqa: E402
 
 PREC_NAMES = {0: "fp64", 1: "split_bf16", 2: "split_tf32", 3: "bf16", 4: "tf32", 5: "split_fp16", 6: "bf16x3",
               7: "fp32_grid_dft"}
-PREC_DTYPE = {0: "f64", 1: "bf16x6+f32acc", 2: "tf32x3+f32acc", 3: "bf16+f32acc", 4: "tf32+f32acc", 7: "f32",
+PREC_DTYPE = {0: "f64", 1: "bf16x6+f32acc", 2: "tf32x3+f32acc", 3: "bf16+f32acc", 4: "tf32+f32acc",
+              7: "f32 (stage 2); f16x3+f32acc (stage 1)",
               5: "f16x3+f32acc", 6: "bf16x3+f32acc"}
 METRIC = "Gamma_nk linewidths/s (el-ph RTA, Si-like 40^3 k x 40^3 q)"
 WORKLOAD = "si_like_fcc_nw8_na2_R429_k40x40x40_q40x40x40_T300_sigma0.02_window0.5"
@@ -121,6 +124,52 @@ def _blas_threads() -> int:
     return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
 
 
+def roofline(precision: int, stats: list, k_limit: int) -> dict:
+    """Roofline object of the dominant stage-2 kernel from the library's per-launch CUDA-event times."""
+    peaks, peak_src = _peaks()
+    s2_ms = sum(s["stage2_ms"] for s in stats)
+    s2_launch = sum(s["stage2_launches"] for s in stats)
+    s2_flops = sum(s["stage2_flops"] for s in stats)
+    achieved = s2_flops / (s2_ms / 1e3) / 1e12 if s2_ms > 0 else None
+    split_factor = {0: 1, 1: 6, 2: 3, 3: 1, 4: 1, 5: 3, 6: 3, 7: 1}[precision]
+    kpad = (-(-2 * 429 // 64) * 64) / (2 * 429)
+    if precision == 7:
+        # CUDA-core FP32: 148 SMs x 128 FP32 lanes x 2 flop per FMA x the maximum SM clock
+        fp32_peak = 148 * 128 * 2 * 2.032e9 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak if achieved else None, "traffic": None,
+                "peak_source": "FP32 FMA rate from unit counts and the 2032 MHz maximum clock",
+                "kernel": "k_dft_yz + k_dft_x_elph (stage 2 as a separable grid DFT, epilogue fused)",
+                "algorithmic_flops_per_launch": s2_flops / max(s2_launch, 1),
+                "avg_launch_ms": s2_ms / max(s2_launch, 1),
+                "note": "flops count the DFT's complex MACs (8 flop each); the fused rotation/delta epilogue "
+                        "is not counted"}
+    elif precision == 0:
+        roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
+                "frac": achieved / 1.25 if achieved else None, "traffic": None,
+                "peak_source": "nominal FP64 1.25 TFLOP/s"}
+    else:
+        peak = peaks.get("bf16_tflops_sustained", 1400.0)
+        if precision in (2, 4):
+            peak *= 0.5     # TF32 dense rate is half the BF16 rate (nominal ratio)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "peak_source": f"{peak_src} bf16_tflops_sustained" + (" x 0.5 (tf32)" if precision in (2, 4) else ""),
+                "kernel": "k_tc_gemm<ElphEpi<8,6>> (stage 2, R_p contraction + fused epilogue)",
+                "algorithmic_flops_per_launch": s2_flops / max(s2_launch, 1),
+                "avg_launch_ms": s2_ms / max(s2_launch, 1),
+                "issued_tensor_tflops": achieved * split_factor * kpad if achieved else None,
+                "issued_frac": achieved * split_factor * kpad / peak if achieved else None}
+    traffic_path = os.path.join(ROOT, "profiles", "stage2_traffic.txt")
+    key = {5: "dram_bytes_per_launch_full=", 7: "dft_dram_bytes_per_launch_full="}.get(precision)
+    if key and os.path.exists(traffic_path) and k_limit == 0:
+        with open(traffic_path) as f:
+            for ln in f:
+                if ln.startswith(key):
+                    roof["traffic"] = float(ln.split("=", 1)[1])
+    return roof
+
+
 def cpu_baseline_oracle(n_k: int, seed: int = 0) -> dict:
     """The FP64 oracle as it stands, on a bounded sample of the workload (n_k active k points)."""
     from oracle import elph
@@ -145,7 +194,7 @@ def learned_leg(pg, W, dev, stream, args) -> dict:
     40^3 k x 80^3 q (a seeded subset of k) at 5% of q against the full q sum of the same
     precision; the uniform proposal and the FP64 full sum (a smaller sample) beside it."""
     import torch
-    prec = args.precision if args.precision != 0 else 5
+    prec = args.precision if args.precision not in (0, 7) else 5   # sampled q sums run on the tensor-core modes
     ctx = pg.PhoebeGPU(dev, stream=stream)
     ctx.set_profiling(True)
     mat20, p20 = W.si_like(seed=0, nk=20)
@@ -306,7 +355,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", type=int, default=5, help="0 fp64, 1 split bf16, 2 split tf32, 5 split fp16")
+    ap.add_argument("--precision", type=int, default=7,
+                    help="0 fp64, 1 split bf16, 2 split tf32, 5 split fp16 (tensor cores), 7 fp32 grid DFT")
+    ap.add_argument("--no-tc-leg", action="store_true", help="skip the tensor-core stage-2 leg beside the headline")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-k-per-step", type=int, default=2)
     ap.add_argument("--cpu-k", type=int, default=4, help="k points of the CPU-oracle baseline sample")
@@ -388,49 +439,32 @@ def main():
     couplings = world * stats[-1]["couplings_dense"] * args.steps / (ms / 1e3)
     launches = int(sum(s["kernel_launches"] for s in stats))
 
-    # roofline of the dominant kernel: stage-2 tcgen05 GEMM with the fused el-ph epilogue
-    peaks, peak_src = _peaks()
-    s2_ms = sum(s["stage2_ms"] for s in stats)
-    s2_launch = sum(s["stage2_launches"] for s in stats)
-    s2_flops = sum(s["stage2_flops"] for s in stats)
-    achieved = s2_flops / (s2_ms / 1e3) / 1e12 if s2_ms > 0 else None
-    split_factor = {0: 1, 1: 6, 2: 3, 3: 1, 4: 1, 5: 3, 6: 3, 7: 1}[args.precision]
-    kpad = (-(-2 * 429 // 64) * 64) / (2 * 429)
-    if args.precision == 7:
-        # CUDA-core FP32: 148 SMs x 128 FP32 lanes x 2 flop per FMA x the maximum SM clock
-        fp32_peak = 148 * 128 * 2 * 2.032e9 / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak if achieved else None, "traffic": None,
-                "peak_source": "FP32 FMA rate from unit counts and the 2032 MHz maximum clock",
-                "kernel": "k_dft_yz + k_dft_x_elph (stage 2 as a separable grid DFT, epilogue fused)",
-                "algorithmic_flops_per_launch": s2_flops / max(s2_launch, 1),
-                "avg_launch_ms": s2_ms / max(s2_launch, 1),
-                "note": "flops count the DFT's complex MACs (8 flop each); the fused rotation/delta epilogue "
-                        "is not counted"}
-    elif args.precision == 0:
-        roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
-                "frac": achieved / 1.25 if achieved else None, "traffic": None,
-                "peak_source": "nominal FP64 1.25 TFLOP/s"}
-    else:
-        peak = peaks.get("bf16_tflops_sustained", 1400.0)
-        if args.precision in (2, 4):
-            peak *= 0.5     # TF32 dense rate is half the BF16 rate (nominal ratio)
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
-                "peak_source": f"{peak_src} bf16_tflops_sustained" + (" x 0.5 (tf32)" if args.precision in (2, 4) else ""),
-                "kernel": "k_tc_gemm<ElphEpi<8,6>> (stage 2, R_p contraction + fused epilogue)",
-                "algorithmic_flops_per_launch": s2_flops / max(s2_launch, 1),
-                "avg_launch_ms": s2_ms / max(s2_launch, 1),
-                "issued_tensor_tflops": achieved * split_factor * kpad if achieved else None,
-                "issued_frac": achieved * split_factor * kpad / peak if achieved else None}
-    traffic_path = os.path.join(ROOT, "profiles", "stage2_traffic.txt")
-    if os.path.exists(traffic_path) and args.precision == 5 and args.k_limit == 0:
-        with open(traffic_path) as f:
-            for ln in f:
-                if ln.startswith("dram_bytes_per_launch_full="):
-                    roof["traffic"] = float(ln.split("=", 1)[1])
+    roof = roofline(args.precision, stats, args.k_limit)
 
     extra = {}
+    if not args.main_only and not args.no_tc_leg and args.precision != 5:
+        # the tensor-core stage 2 (split FP16) on the same workload, beside the headline mode
+        p5 = pg.make_params(prm, precision=5)
+        g_head = g_out.cpu().numpy().copy()
+        ctx.linewidths_rta_dev(p5, k_out, b_out, g_out, n)
+        torch.cuda.synchronize()
+        s5 = []
+        t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0e.record(stream)
+        for _ in range(args.steps):
+            ctx.linewidths_rta_dev(p5, k_out, b_out, g_out, n)
+            s5.append(ctx.stats())
+        t1e.record(stream)
+        torch.cuda.synchronize()
+        ms5 = t0e.elapsed_time(t1e) / args.steps
+        g5 = g_out.cpu().numpy()
+        fl = 1e-6 * np.median(np.abs(g5))
+        extra["tensor_core_mode"] = {
+            "precision": "split_fp16", "value": n / (ms5 / 1e3), "unit": "linewidths/s", "ms_per_step": ms5,
+            "roofline": roofline(5, s5, args.k_limit),
+            "max_rel_diff_vs_headline": float(np.max(np.abs(g5 - g_head) / np.maximum(np.abs(g5), fl)))}
+        ctx.linewidths_rta_dev(params, k_out, b_out, g_out, n)     # headline outputs back for the checks below
+        torch.cuda.synchronize()
     if args.main_only:
         line = {"metric": METRIC, "value": value, "unit": "linewidths/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "states_per_step": n, "roofline": roof,

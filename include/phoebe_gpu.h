@@ -142,7 +142,11 @@ typedef struct {
   uint64_t seed;             /* sampler LEARNED/UNIFORM: key of the Philox4x32-10 draws */
   int sampler_fp32_network;  /* sampler LEARNED: 1 scores q with the FP32 CUDA-core forward pass,
                                 0 (default) with the tensor-core kernel (FP16 operands) on sm_10x */
-  int reserved[3];           /* must be zero */
+  int reserved0;             /* must be zero */
+  double population_delta;   /* > 0: initial states are those with f(1 - f) > population_delta (the
+                                population window of Sec. 5.2, 0 < delta < 1/4) instead of the energy
+                                window; 0 (default): energy window */
+  int reserved[2];           /* must be zero */
 } phoebe_gpu_rta_params;
 
 typedef enum {

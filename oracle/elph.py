@@ -256,8 +256,10 @@ def couplings_for_pairs(k: np.ndarray, q: np.ndarray, mat, omega_cut: float = 1e
 
 # ------------------------------------------------------- windows (Sec. 5.2) and linewidths (Eq. 29)
 
-def active_states(eps_k: np.ndarray, mu: float, window: float):
-    """Energy window of Sec. 5.2: keep (k, b) with |eps_kb - mu| < window (window <= 0: all).
+def active_states(eps_k: np.ndarray, mu: float, window: float, T: float | None = None,
+                  population_delta: float = 0.0):
+    """Windows of Sec. 5.2 on the initial states: the energy window |eps_kb - mu| < window
+    (window <= 0: all), or with population_delta > 0 the population window f(1-f) > delta.
 
     Reading: the window applies to initial states only; final states at k+q
     range over all bands.  Returns (k_index, band) arrays ordered by k then band.
@@ -266,10 +268,20 @@ def active_states(eps_k: np.ndarray, mu: float, window: float):
     ks, bs = [], []
     for ik in range(nk):
         for b in range(nb):
-            if window <= 0 or abs(eps_k[ik, b] - mu) < window:
+            if population_delta > 0:
+                f = fermi_dirac(eps_k[ik, b], mu, T)
+                keep = f * (1.0 - f) > population_delta
+            else:
+                keep = window <= 0 or abs(eps_k[ik, b] - mu) < window
+            if keep:
                 ks.append(ik)
                 bs.append(b)
     return np.array(ks, dtype=np.int64), np.array(bs, dtype=np.int64)
+
+
+def _active(eps_grid, params):
+    return active_states(eps_grid, params.mu_eV, params.window_eV, params.T_K,
+                         getattr(params, "population_delta", 0.0))
 
 
 def fine_grid(nk, nq):
@@ -322,7 +334,7 @@ def linewidths_rta(mat, params, k_indices=None, direct: bool = False, return_raw
 
     F, eps_F, U_F, k_to_F = table if table is not None else electron_table(mat, params)
     eps_grid = eps_F[k_to_F]
-    ks, bs = active_states(eps_grid, mu, params.window_eV)
+    ks, bs = _active(eps_grid, params)
     if k_indices is not None:
         keep = np.isin(ks, np.asarray(k_indices))
         ks, bs = ks[keep], bs[keep]
@@ -391,7 +403,7 @@ def contributions(mat, params, k_indices=None, q_indices=None, table=None):
     cut = params.delta_cut_sigmas
     F, eps_F, U_F, k_to_F = table if table is not None else electron_table(mat, params)
     eps_grid = eps_F[k_to_F]
-    ks, bs = active_states(eps_grid, mu, params.window_eV)
+    ks, bs = _active(eps_grid, params)
     if k_indices is not None:
         keep = np.isin(ks, np.asarray(k_indices))
         ks, bs = ks[keep], bs[keep]

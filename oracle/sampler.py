@@ -246,7 +246,7 @@ def linewidths_is(mat, params, blob, fraction: float, alpha: float, seed: int, k
     Nq = int(np.prod(nq))
     S = int(np.ceil(fraction * Nq))
     eps_grid = eps_F[k_to_F]
-    ks, bs = elph.active_states(eps_grid, params.mu_eV, params.window_eV)
+    ks, bs = elph._active(eps_grid, params)
     if k_indices is not None:
         keep = np.isin(ks, np.asarray(k_indices))
         ks, bs = ks[keep], bs[keep]

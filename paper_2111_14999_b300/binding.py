@@ -58,8 +58,9 @@ class RTAParams(C.Structure):
         ("max_batch_states", C.c_int),
         ("sampler", C.c_int),
         ("sample_fraction", C.c_double), ("mix_alpha", C.c_double), ("seed", C.c_uint64),
-        ("sampler_fp32_network", C.c_int),
-        ("reserved", C.c_int * 3),
+        ("sampler_fp32_network", C.c_int), ("reserved0", C.c_int),
+        ("population_delta", C.c_double),
+        ("reserved", C.c_int * 2),
     ]
 
 
@@ -204,7 +205,7 @@ def make_params(p=None, **kw) -> RTAParams:
             setattr(s, key, float(val))
         elif key in ("precision", "max_batch_states", "sampler", "seed", "sampler_fp32_network"):
             setattr(s, key, int(val))
-        elif key in ("sample_fraction", "mix_alpha"):
+        elif key in ("sample_fraction", "mix_alpha", "population_delta"):
             setattr(s, key, float(val))
     s._keep = keep  # keep the subset array alive with the struct
     return s

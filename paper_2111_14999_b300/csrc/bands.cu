@@ -219,8 +219,18 @@ __global__ void k_fermi(const double* __restrict__ eps, int64_t N, double mu, do
 // ------------------------------------------------------------------ window (Sec. 5.2)
 // count[c] = number of bands of candidate k point c (k-grid index kidx[c], or c itself)
 // with |eps - mu| < window (all bands if window <= 0).
+// Initial-state windows (Sec. 5.2): the population window f(1-f) > delta when delta > 0, else
+// the energy window |eps - mu| < window (window <= 0: every state).
+__device__ __forceinline__ bool in_window(double e, double mu, double window, double kT, double delta) {
+  if (delta > 0.0) {
+    const double f = 1.0 / (exp((e - mu) / kT) + 1.0);
+    return f * (1.0 - f) > delta;
+  }
+  return window <= 0.0 || fabs(e - mu) < window;
+}
+
 __global__ void k_window_count(const double* __restrict__ epsF, const int* __restrict__ kidx, int64_t NC, int nw, GridMap gm,
-                               double mu, double window, int* __restrict__ count) {
+                               double mu, double window, double kT, double delta, int* __restrict__ count) {
   int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= NC) return;
   int64_t k = kidx ? kidx[c] : c;
@@ -228,7 +238,7 @@ __global__ void k_window_count(const double* __restrict__ epsF, const int* __res
   int cnt = 0;
   for (int b = 0; b < nw; ++b) {
     double e = epsF[f * nw + b];
-    if (window <= 0.0 || fabs(e - mu) < window) ++cnt;
+    if (in_window(e, mu, window, kT, delta)) ++cnt;
   }
   count[c] = cnt;
 }
@@ -259,7 +269,7 @@ __global__ void k_scan_single_block(const int* __restrict__ count, int64_t N, in
 
 // Write the active states (k grid index, band) in k-then-band order.
 __global__ void k_window_write(const double* __restrict__ epsF, const int* __restrict__ kidx, int64_t NC,
-                               int nw, GridMap gm, double mu, double window,
+                               int nw, GridMap gm, double mu, double window, double kT, double delta,
                                const int64_t* __restrict__ offset, int* __restrict__ st_k,
                                int* __restrict__ st_b) {
   int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -269,7 +279,7 @@ __global__ void k_window_write(const double* __restrict__ epsF, const int* __res
   int64_t o = offset[c];
   for (int b = 0; b < nw; ++b) {
     double e = epsF[f * nw + b];
-    if (window <= 0.0 || fabs(e - mu) < window) {
+    if (in_window(e, mu, window, kT, delta)) {
       st_k[o] = (int)k;
       st_b[o] = b;
       ++o;

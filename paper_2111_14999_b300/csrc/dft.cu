@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(1024) k_dft_yz(DftYzArgs a) {
 // final bands m' that can reach the delta window.  Phase 2: the warp compacts its (q, m') items
 // and every lane takes items in turn, so a band is rotated only for the q that need it.
 template <int NW, int NM>
-__global__ void __launch_bounds__(kDftMaxThreads) k_dft_x_elph(DftXArgs a) {
+__global__ void __launch_bounds__(kDftMaxThreads / PHX_DFT_MINB, PHX_DFT_MINB) k_dft_x_elph(DftXArgs a) {
   constexpr int E = NW * NM;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* Ys = reinterpret_cast<float2*>(smem);                       // [Bx][kDftLines][E]

@@ -5,7 +5,13 @@
 
 namespace phx {
 
-constexpr int kDftLines = 4;          // (jy, jz) lines per block of the x-sum kernel
+#ifndef PHX_DFT_LINES
+#define PHX_DFT_LINES 4
+#endif
+#ifndef PHX_DFT_MINB
+#define PHX_DFT_MINB 1
+#endif
+constexpr int kDftLines = PHX_DFT_LINES;  // (jy, jz) lines per block of the x-sum kernel
 constexpr int kDftMaxThreads = 512;   // Nx * kDftLines <= 512 (Nx <= 64)
 
 struct DftYzArgs {

@@ -48,10 +48,11 @@ __global__ void k_phonon_factors(const double* lam, const cplx* z, int nm, int64
                                  double* nB, cplx* Z);
 __global__ void k_fermi(const double* eps, int64_t N, double mu, double T, double* f);
 __global__ void k_window_count(const double* epsF, const int* kidx, int64_t NC, int nw, GridMap gm,
-                               double mu, double window, int* count);
+                               double mu, double window, double kT, double delta, int* count);
 __global__ void k_scan_single_block(const int* count, int64_t N, int64_t* offset);
 __global__ void k_window_write(const double* epsF, const int* kidx, int64_t NC, int nw, GridMap gm,
-                               double mu, double window, const int64_t* offset, int* st_k, int* st_b);
+                               double mu, double window, double kT, double delta, const int64_t* offset, int* st_k,
+                               int* st_b);
 
 // ---------------------------------------------------------------- couple_fp64.cu
 __global__ void k_phase_table_grid(cplx* P, const int* pts, int64_t npts, const int* R, const double* w,

@@ -137,8 +137,11 @@ static int check_params(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, GridM
   if (!(p->degen_tol_eV >= 0.0)) return fail(c, PHOEBE_GPU_ERR_ARG, "degen_tol_eV must be >= 0");
   if (p->precision < PHOEBE_PREC_FP64 || p->precision > PHOEBE_PREC_FP32_DFT)
     return fail(c, PHOEBE_GPU_ERR_ARG, "unknown precision %d", p->precision);
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 2; ++i)
     if (p->reserved[i] != 0) return fail(c, PHOEBE_GPU_ERR_ARG, "reserved fields must be zero");
+  if (p->reserved0 != 0) return fail(c, PHOEBE_GPU_ERR_ARG, "reserved fields must be zero");
+  if (!(p->population_delta >= 0.0 && p->population_delta < 0.25))
+    return fail(c, PHOEBE_GPU_ERR_ARG, "population_delta must be in [0, 0.25)");
   if (p->sampler_fp32_network != 0 && p->sampler_fp32_network != 1)
     return fail(c, PHOEBE_GPU_ERR_ARG, "sampler_fp32_network must be 0 or 1");
   if (p->sampler < PHOEBE_SAMPLER_FULL || p->sampler > PHOEBE_SAMPLER_UNIFORM)
@@ -356,8 +359,9 @@ int linewidths(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, int* n_states,
   int64_t* offset = (int64_t*)ensure(c, "win_off", sizeof(int64_t) * (NC + 1), &st);
   if (!offset) return st;
   double window = p->window_eV;
-  k_window_count<<<(unsigned)((NC + 255) / 256), 256, 0, c->stream>>>(epsF, kidx, NC, nw, gm, p->mu_eV, window,
-                                                                       count);
+  const double kT = kBoltzmannEV * p->T_K;
+  k_window_count<<<(unsigned)((NC + 255) / 256), 256, 0, c->stream>>>(epsF, kidx, NC, nw, gm, p->mu_eV, window, kT,
+                                                                       p->population_delta, count);
   k_scan_single_block<<<1, 1024, 0, c->stream>>>(count, NC, offset);
   TRY(launch_check(c, 2));
   int64_t ns = 0;
@@ -375,8 +379,8 @@ int linewidths(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, int* n_states,
   if (!st_k) return st;
   int* st_b = (int*)ensure(c, "st_b", sizeof(int) * (ns + 1), &st);
   if (!st_b) return st;
-  k_window_write<<<(unsigned)((NC + 255) / 256), 256, 0, c->stream>>>(epsF, kidx, NC, nw, gm, p->mu_eV, window,
-                                                                       offset, st_k, st_b);
+  k_window_write<<<(unsigned)((NC + 255) / 256), 256, 0, c->stream>>>(epsF, kidx, NC, nw, gm, p->mu_eV, window, kT,
+                                                                       p->population_delta, offset, st_k, st_b);
   TRY(launch_check(c, 1));
   t.end(c, &c->stats.window_ms);
   c->stats.n_states = ns;

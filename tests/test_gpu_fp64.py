@@ -190,3 +190,22 @@ def test_si_like_fp64_sampled_k(pg, si):
     k2, b2, ref = elph.linewidths_rta(mat, prm, k_indices=pick, table=tab)
     assert np.array_equal(ks, k2) and np.array_equal(bs, b2)
     np.testing.assert_allclose(gam, ref, rtol=RTOL_FP64)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (5, 1e-5)])
+def test_population_window_vs_oracle(prec, tol):
+    import paper_2111_14999_b300 as pg
+    mat, prm = W.si_like(seed=0, nk=8)
+    prm = prm.with_(population_delta=1e-4)
+    tab = elph.electron_table(mat, prm)
+    k_all, _ = elph.active_states(tab[1][tab[3]], prm.mu_eV, 0.0, prm.T_K, prm.population_delta)
+    assert 0 < len(k_all) < 512 * 8
+    pick = np.unique(k_all)[::max(1, len(np.unique(k_all)) // 6)][:6]
+    prm = prm.with_(k_subset=pick)
+    ks, bs, ref = elph.linewidths_rta(mat, prm, k_indices=pick, table=tab)
+    assert len(ks) > 0
+    with pg.PhoebeGPU(0) as ctx:
+        ctx.set_material(mat)
+        k2, b2, g = ctx.linewidths_rta(prm, precision=prec)
+    assert np.array_equal(k2, ks) and np.array_equal(b2, bs)
+    assert np.max(np.abs(g - ref) / np.maximum(np.abs(ref), 1e-6 * np.median(np.abs(ref)))) <= tol

@@ -326,3 +326,18 @@ def test_oracle_reproduces_stored_toy_values(toy):
     ks, bs, gam = elph.linewidths_rta(mat, prm)
     assert np.array_equal(ref[:, 0].astype(int), ks) and np.array_equal(ref[:, 1].astype(int), bs)
     assert np.allclose(gam, ref[:, 2], rtol=1e-12, atol=0)
+
+
+def test_population_window_is_an_energy_window():
+    # Sec. 5.2 population window f(1-f) > delta: with f(1-f) = 1/(4 cosh^2(x/2)), x = (e - mu)/kT, it keeps
+    # exactly |e - mu| < 2 kT acosh(1/(2 sqrt(delta)))
+    rng = np.random.default_rng(12)
+    eps = rng.uniform(-0.6, 0.6, (300, 4))
+    T, mu, delta = 300.0, 0.05, 1e-3
+    W = 2 * elph.KB_EV * T * np.arccosh(1 / (2 * np.sqrt(delta)))
+    far = np.abs(np.abs(eps - mu) - W) > 1e-9
+    eps = np.where(far, eps, mu + 2 * W)
+    k1, b1 = elph.active_states(eps, mu, 0.0, T, delta)
+    k2, b2 = elph.active_states(eps, mu, W)
+    assert np.array_equal(k1, k2) and np.array_equal(b1, b2)
+    assert 0 < len(k1) < eps.size

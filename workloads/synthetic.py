@@ -83,6 +83,7 @@ class RTAParams:
     mix_alpha: float = 0.1
     seed: int = 0
     sampler_fp32_network: int = 0
+    population_delta: float = 0.0   # > 0: population window f(1-f) > delta on initial states
 
     def with_(self, **kw) -> "RTAParams":
         return replace(self, **kw)
