@@ -2,216 +2,510 @@
 // exactly in another order).  With q = (jx/Nx, jy/Ny, jz/Nz) the phase of Eq. 13 factorises,
 // e^{2 pi i q.R} = e^{2 pi i jx rx/Nx} e^{2 pi i jy ry/Ny} e^{2 pi i jz rz/Nz} with r = R mod N,
 // so for every state
-//   G(q)[c] = sum_rx Ex[jx][rx] sum_ry Ey[jy][ry] sum_rz Ez[jz][rz] T~[rx][ry][rz][c],
-// T~ the stage-1 output T summed over the R_p of equal residue (weights folded in).  The y/z
-// sums run first (k_dft_yz, into Y[s][rx][jy][jz][c]); k_dft_x_elph finishes the x sum for one
-// q per thread and applies U_{k+q}^dagger, Z_q and the delta weights of Eq. 29 (Sec. 4.7 Eq. 61)
-// like the fused tensor-core epilogue.  FP32 on the CUDA cores.
+//   G(q)[c] = sum_rx Ex[jx][rx] sum_ry Ey[jy][ry] sum_rz Ez[jz][rz] w_R T[R][c],
+// T the stage-1 output.  k_dft_z sums over rz for every (rx, ry) pair present in the R_p set
+// (Zs[jz][pair][c], in HBM); k_dft_yx_elph then, for one jz and a run of jy, sums over ry into
+// shared memory, finishes the x sum for the q whose final bands can reach the delta window and
+// applies U_{k+q}^dagger, Z_q and the delta weights of Eq. 29 (Sec. 4.7 Eq. 61) like the fused
+// tensor-core epilogue.  FP32 on the CUDA cores.
+#include <algorithm>
+
 #include "dft.h"
 
 namespace phx {
 
-// One block per (column chunk of 16, rx residue, state); thread (jz, column).  For each chunk
-// of 16 jy: acc[jy] = sum_ry Ey[jy][ry] (sum_{R in (rx, ry)} Ez[jz][rz(R)] w_R T[s][R][c]).
-// The plane's weighted T columns and the phase tables are staged in shared memory.
-__global__ void __launch_bounds__(1024) k_dft_yz(DftYzArgs a) {
+// Sum over rz: one block per (rx plane, state); work unit = (pair of the plane, 4 jz, column
+// vector).  The plane's weighted T rows and the Ez table are staged in shared memory.
+__global__ void __launch_bounds__(256) k_dft_z(DftZArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int p0 = a.plane_off[blockIdx.y], p1 = a.plane_off[blockIdx.y + 1];
-  const int ne = p1 - p0;
-  float2* Ts = reinterpret_cast<float2*>(smem);  // [ne][16]
-  float2* Eys = Ts + (size_t)ne * 16;            // [Ny][By]
-  float2* Ezs = Eys + (size_t)a.Ny * a.By;       // [Nz][Bz]
-  int* ays = reinterpret_cast<int*>(Ezs + (size_t)a.Nz * a.Bz);  // [ne]
-  int* azs = ays + ne;                                           // [ne]
-  const int s = blockIdx.z, ax = blockIdx.y, c0 = blockIdx.x * 16;
-  const float2* T = a.T + (int64_t)s * a.nR * a.E;
-  for (int i = threadIdx.x; i < ne * 16; i += blockDim.x) {
-    const int e = p0 + i / 16, cc = c0 + (i & 15);
-    const int r = a.ent_r[e];
-    float2 t = make_float2(0.f, 0.f);
-    if (cc < a.E) {
-      t = T[(int64_t)r * a.E + cc];
-      const float w = a.w[r];
-      t.x *= w;
-      t.y *= w;
-    }
+  const int rx = blockIdx.x, s = blockIdx.y;
+  const int p0 = a.plane_pair_off[rx], p1 = a.plane_pair_off[rx + 1];
+  const int e0 = a.pair_ent_off[p0], ne = a.pair_ent_off[p1] - e0;
+  const int E = a.E;
+  float2* Ts = reinterpret_cast<float2*>(smem);            // [ne][E]
+  float2* Ezs = Ts + (size_t)ne * E;                       // [Nz][Bz]
+  int* azs = reinterpret_cast<int*>(Ezs + (size_t)a.Nz * a.Bz);  // [ne]
+  const float2* T = a.T + (int64_t)s * a.nR * E;
+  for (int i = threadIdx.x; i < ne * E; i += blockDim.x) {
+    const int e = i / E, cc = i % E;
+    const int r = a.ent_r[e0 + e];
+    float2 t = T[(int64_t)r * E + cc];
+    const float w = a.w[r];
+    t.x *= w;
+    t.y *= w;
     Ts[i] = t;
   }
-  for (int i = threadIdx.x; i < a.Ny * a.By; i += blockDim.x) Eys[i] = a.Ey[i];
   for (int i = threadIdx.x; i < a.Nz * a.Bz; i += blockDim.x) Ezs[i] = a.Ez[i];
-  for (int i = threadIdx.x; i < ne; i += blockDim.x) {
-    ays[i] = a.ent_ay[p0 + i];
-    azs[i] = a.ent_az[p0 + i];
-  }
+  for (int i = threadIdx.x; i < ne; i += blockDim.x) azs[i] = a.ent_az[e0 + i];
   __syncthreads();
-  const int cl = threadIdx.x & 15;
-  const int c = c0 + cl;
-  const int jz = threadIdx.x >> 4;
-  if (jz >= a.Nz || c >= a.E) return;
-  float2* Y = a.Y + (((int64_t)s * a.Bx + ax) * a.Ny) * a.Nz * a.E;
-  const float2* ez_row = Ezs + jz * a.Bz;
-  for (int jy0 = 0; jy0 < a.Ny; jy0 += 16) {
-    float2 acc[16];
+  constexpr int JZ = 4;
+  const int nzq = (a.Nz + JZ - 1) / JZ;
+  float2* Zs = a.Zs + (int64_t)s * a.Nz * a.P * E;
+  if (E % 2 == 0) {
+    const int EV = E / 2;
+    const int units = (p1 - p0) * nzq * EV;
+    for (int u = threadIdx.x; u < units; u += blockDim.x) {
+      const int cv = u % EV, rest = u / EV;
+      const int jq = rest % nzq, p = p0 + rest / nzq;
+      float4 acc[JZ];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) acc[i] = make_float2(0.f, 0.f);
-    int e = 0;
-    while (e < ne) {
-      const int ay = ays[e];
-      float2 yz = make_float2(0.f, 0.f);
-      for (; e < ne && ays[e] == ay; ++e) {
-        const float2 ez = ez_row[azs[e]];
-        const float2 t = Ts[e * 16 + cl];
-        yz.x = fmaf(ez.x, t.x, fmaf(-ez.y, t.y, yz.x));
-        yz.y = fmaf(ez.x, t.y, fmaf(ez.y, t.x, yz.y));
-      }
+      for (int i = 0; i < JZ; ++i) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int e = a.pair_ent_off[p] - e0; e < a.pair_ent_off[p + 1] - e0; ++e) {
+        const float4 t = reinterpret_cast<const float4*>(Ts + (size_t)e * E)[cv];
+        const int az = azs[e];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        if (jy0 + i < a.Ny) {
-          const float2 ey = Eys[(jy0 + i) * a.By + ay];
-          acc[i].x = fmaf(ey.x, yz.x, fmaf(-ey.y, yz.y, acc[i].x));
-          acc[i].y = fmaf(ey.x, yz.y, fmaf(ey.y, yz.x, acc[i].y));
+        for (int i = 0; i < JZ; ++i) {
+          const int jz = jq * JZ + i;
+          if (jz < a.Nz) {
+            const float2 ez = Ezs[jz * a.Bz + az];
+            acc[i].x = fmaf(ez.x, t.x, fmaf(-ez.y, t.y, acc[i].x));
+            acc[i].y = fmaf(ez.x, t.y, fmaf(ez.y, t.x, acc[i].y));
+            acc[i].z = fmaf(ez.x, t.z, fmaf(-ez.y, t.w, acc[i].z));
+            acc[i].w = fmaf(ez.x, t.w, fmaf(ez.y, t.z, acc[i].w));
+          }
         }
       }
-    }
 #pragma unroll
-    for (int i = 0; i < 16; ++i)
-      if (jy0 + i < a.Ny) Y[((int64_t)(jy0 + i) * a.Nz + jz) * a.E + c] = acc[i];
+      for (int i = 0; i < JZ; ++i) {
+        const int jz = jq * JZ + i;
+        if (jz < a.Nz) reinterpret_cast<float4*>(Zs + ((int64_t)jz * a.P + p) * E)[cv] = acc[i];
+      }
+    }
+  } else {
+    const int units = (p1 - p0) * nzq * E;
+    for (int u = threadIdx.x; u < units; u += blockDim.x) {
+      const int cv = u % E, rest = u / E;
+      const int jq = rest % nzq, p = p0 + rest / nzq;
+      float2 acc[JZ];
+#pragma unroll
+      for (int i = 0; i < JZ; ++i) acc[i] = make_float2(0.f, 0.f);
+      for (int e = a.pair_ent_off[p] - e0; e < a.pair_ent_off[p + 1] - e0; ++e) {
+        const float2 t = Ts[(size_t)e * E + cv];
+        const int az = azs[e];
+#pragma unroll
+        for (int i = 0; i < JZ; ++i) {
+          const int jz = jq * JZ + i;
+          if (jz < a.Nz) {
+            const float2 ez = Ezs[jz * a.Bz + az];
+            acc[i].x = fmaf(ez.x, t.x, fmaf(-ez.y, t.y, acc[i].x));
+            acc[i].y = fmaf(ez.x, t.y, fmaf(ez.y, t.x, acc[i].y));
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < JZ; ++i) {
+        const int jz = jq * JZ + i;
+        if (jz < a.Nz) Zs[((int64_t)jz * a.P + p) * E + cv] = acc[i];
+      }
+    }
   }
 }
 
-// One block per (group of kDftLines (jy, jz) lines, state); thread (jx, line).  Phase 1: each
-// thread sums over rx for its q (G in registers, then its own slot of shared memory) and marks the
-// final bands m' that can reach the delta window.  Phase 2: the warp compacts its (q, m') items
-// and every lane takes items in turn, so a band is rotated only for the q that need it.
-template <int NW, int NM>
-__global__ void __launch_bounds__(kDftMaxThreads / PHX_DFT_MINB, PHX_DFT_MINB) k_dft_x_elph(DftXArgs a) {
-  constexpr int E = NW * NM;
-  extern __shared__ __align__(16) unsigned char smem[];
-  float2* Ys = reinterpret_cast<float2*>(smem);                       // [Bx][kDftLines][E]
-  float2* Gs = Ys + (size_t)a.Bx * kDftLines * E;                      // [E][threads] (element-major)
-  float2* Exs = Gs + (size_t)blockDim.x * E;                           // [Nx][Bx]
-  int* items = reinterpret_cast<int*>(Exs + (size_t)a.Nx * a.Bx);      // [warps][32 * NW]
-  int* qkq = items + (blockDim.x >> 5) * 32 * NW;                      // [threads][2]: q, k+q
-  const int s = blockIdx.y;
-  const int line0 = blockIdx.x * kDftLines;
-  const int nlines = a.Ny * a.Nz;
-  const float2* Yg = a.Y + (int64_t)s * a.Bx * nlines * E;
-  for (int i = threadIdx.x; i < a.Bx * kDftLines * E; i += blockDim.x) {
-    const int ax = i / (kDftLines * E), rem = i % (kDftLines * E);
-    const int l = rem / E, cc = rem % E;
-    Ys[i] = line0 + l < nlines ? Yg[((int64_t)ax * nlines + line0 + l) * E + cc] : make_float2(0.f, 0.f);
+// 16-byte (or 8-byte) asynchronous global -> shared copies (cp.async).
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// N consecutive floats / complex values of a table row with the widest aligned vector loads (rows
+// start on multiples of N elements, so N % 4 == 0 floats or N % 2 == 0 complex values are 16-byte aligned).
+template <int N>
+__device__ __forceinline__ void load_row(const float* __restrict__ p, float (&e)[N]) {
+  if constexpr (N % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(p) + i);
+      e[4 * i] = v.x;
+      e[4 * i + 1] = v.y;
+      e[4 * i + 2] = v.z;
+      e[4 * i + 3] = v.w;
+    }
+  } else if constexpr (N % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+      const float2 v = __ldg(reinterpret_cast<const float2*>(p) + i);
+      e[2 * i] = v.x;
+      e[2 * i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) e[i] = __ldg(p + i);
   }
-  for (int i = threadIdx.x; i < a.Nx * a.Bx; i += blockDim.x) Exs[i] = a.Ex[i];
-  __syncthreads();
+}
+template <int N>
+__device__ __forceinline__ void load_cplx(const float2* __restrict__ p, float2 (&z)[N]) {
+  if constexpr (N % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(p) + i);
+      z[2 * i] = make_float2(v.x, v.y);
+      z[2 * i + 1] = make_float2(v.z, v.w);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) z[i] = __ldg(p + i);
+  }
+}
+
+// Shared-memory row stride of Y (complex elements): at least E, congruent to NW modulo 16 so that
+// the rows of consecutive lines start half a bank cycle apart (a lane group reads NW consecutive
+// complex values of a row), even whenever E is (16-byte loads stay aligned).
+__host__ __device__ constexpr int dft_row_stride(int E, int NW) { return E + ((NW - E) % 16 + 16) % 16; }
+
+// One block per (jz, run of kDftLines jy, state), kDftXThreads threads.
+// Loads: the state's Zs[jz] slice (every (rx, ry) pair) by cp.async, the phase tables.
+// Phase 0 (while the slice arrives): every q = (jx, jy, jz) of the block tests which final bands m'
+// at k+q lie within the Gaussian's reach of eps_nk; the q with at least one such band are listed
+// (warp ballots, in (line, jx) order).  Phase Y: Y[rx][line][c] = sum_ry Ey[jy][ry] Zs[(rx,ry)][c]
+// into shared memory; unit = (rx, kDftUnitLines lines, column vector).  Phase X: SPLIT consecutive
+// lanes take one listed q: lane j sums over rx the elements c = sa*NW + m of its m range, then the
+// group applies U_{k+q}^dagger (partial sums over m, combined by shuffles), Z_q and the delta
+// weights for each listed m'.  q whose bands all miss the window contribute nothing to Eq. 29 and
+// are not evaluated.
+template <int NW, int NM, int SPLIT>
+__global__ void __launch_bounds__(kDftXThreads) k_dft_yx_elph(DftXArgs a) {
+  constexpr int E = NW * NM, MW = NW / SPLIT, ES = dft_row_stride(E, NW);
+  constexpr int L = kDftLines, UL = kDftUnitLines;
+  constexpr int SLOT = dft_slot(NW, NM);
+  constexpr bool A16 = NW % 2 == 0 && NM % 2 == 0;  // every prefetched segment 16-byte aligned
+  static_assert(NW % SPLIT == 0 && 32 % SPLIT == 0 && NW <= 16, "lane split must divide NW and the warp");
+  static_assert(SPLIT == dft_split(NW), "lane split must match the host's shared-memory sizing");
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int P = a.P;
+  const int zsl_len = max(P * E, (kDftXThreads / SPLIT) * SLOT);
+  float2* Zsl = reinterpret_cast<float2*>(smem);          // [P][E]; after phase Y the groups' prefetch slots
+  float2* Ys = Zsl + (size_t)zsl_len;                     // [Bx][L][ES]
+  float2* Exs = Ys + (size_t)a.Bx * L * ES;               // [Nx][K]
+  float2* Eys = Exs + (size_t)a.Nx * a.K;                 // [L][By]
+  int* ppo = reinterpret_cast<int*>(Eys + (size_t)L * a.By);  // [Bx+1]
+  int* xS = ppo + a.Bx + 1;                               // [K]
+  int* xD = xS + a.K;                                     // [K]
+  int* pay = xD + a.K;                                    // [P]
+  int* list = pay + P;                                    // [L * Nx]
+  __shared__ int cnt;
+  __shared__ double red[kDftXThreads / 32];
+  const int s = blockIdx.y;
+  const int nch = (a.Ny + L - 1) / L;
+  const int jz = blockIdx.x / nch, jy0 = (blockIdx.x % nch) * L;
+  const int nl = min(L, a.Ny - jy0);
+  if (threadIdx.x == 0) cnt = 0;
+  {  // the Zs[jz] slice of this state: P * E contiguous complex values
+    const float2* zg = a.Zs + ((int64_t)s * a.Nz + jz) * P * E;
+    if ((P * E) % 2 == 0) {
+      for (int i = threadIdx.x; i < P * E / 2; i += blockDim.x) cp_async16(Zsl + 2 * i, zg + 2 * i);
+    } else {
+      for (int i = threadIdx.x; i < P * E; i += blockDim.x) cp_async8(Zsl + i, zg + i);
+    }
+  }
+  for (int i = threadIdx.x; i < a.Nx * a.K; i += blockDim.x) Exs[i] = a.Ex[i];
+  for (int i = threadIdx.x; i < a.K; i += blockDim.x) {
+    xS[i] = a.xS[i];
+    xD[i] = a.xD[i];
+  }
+  for (int i = threadIdx.x; i < L * a.By; i += blockDim.x) {
+    const int l = i / a.By;
+    Eys[i] = l < nl ? a.Ey[(jy0 + l) * a.By + i % a.By] : make_float2(0.f, 0.f);
+  }
+  for (int i = threadIdx.x; i <= a.Bx; i += blockDim.x) ppo[i] = a.plane_pair_off[i];
+  for (int i = threadIdx.x; i < P; i += blockDim.x) pay[i] = a.pair_ay[i];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int jx = threadIdx.x % a.Nx, l = threadIdx.x / a.Nx;
-  const int line = line0 + l;
   const int64_t kf = a.gm.k_to_fine(a.st_k[s]);
   const double e_n = a.epsF[kf * NW + a.st_b[s]];
   const float en_hi = (float)e_n, en_lo = (float)(e_n - (double)en_hi);
-  unsigned need = 0;
-  if (l < kDftLines && line < nlines) {
-    float2 G[E];
+  int kc[3];
+  grid_coords(kf, a.gm.nf, kc);
+  __syncthreads();  // cnt initialised
+  // fine-grid coordinates of k+q: k_d + j_d * s_d with k_d < nf_d and j_d * s_d < nf_d, so one
+  // conditional subtraction reduces them modulo nf_d
+  const int sx = a.gm.sq[0], sy = a.gm.sq[1];
+  const int nfx = a.gm.nf[0], nfy = a.gm.nf[1], nfz = a.gm.nf[2];
+  int fz = kc[2] + jz * a.gm.sq[2];
+  fz -= fz >= nfz ? nfz : 0;
+  const float en_f = en_hi;
+  // phase 0: list the q of the block that can reach the delta window (two q per thread and round,
+  // their energy rows loaded before either is tested)
+  const int nq_blk = nl * a.Nx;
+  for (int q0 = 0; q0 < nq_blk; q0 += 2 * blockDim.x) {
+    float ev[2][NW];
+    int qis[2];
 #pragma unroll
-    for (int e = 0; e < E; ++e) G[e] = make_float2(0.f, 0.f);
-    for (int ax = 0; ax < a.Bx; ++ax) {
-      const float2 ex = Exs[jx * a.Bx + ax];
-      const float2* y = Ys + (ax * kDftLines + l) * E;
-      if constexpr (E % 2 == 0) {  // two complex values per 16-byte load
-#pragma unroll
-        for (int e = 0; e < E; e += 2) {
-          const float4 v = reinterpret_cast<const float4*>(y)[e / 2];
-          G[e].x = fmaf(ex.x, v.x, fmaf(-ex.y, v.y, G[e].x));
-          G[e].y = fmaf(ex.x, v.y, fmaf(ex.y, v.x, G[e].y));
-          G[e + 1].x = fmaf(ex.x, v.z, fmaf(-ex.y, v.w, G[e + 1].x));
-          G[e + 1].y = fmaf(ex.x, v.w, fmaf(ex.y, v.z, G[e + 1].y));
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const float2 v = y[e];
-          G[e].x = fmaf(ex.x, v.x, fmaf(-ex.y, v.y, G[e].x));
-          G[e].y = fmaf(ex.x, v.y, fmaf(ex.y, v.x, G[e].y));
-        }
+    for (int u = 0; u < 2; ++u) {
+      const int qi = q0 + u * blockDim.x + threadIdx.x;
+      qis[u] = qi;
+      if (qi < nq_blk) {
+        const int l = qi / a.Nx, jx = qi - l * a.Nx;
+        int fx = kc[0] + jx * sx, fy = kc[1] + (jy0 + l) * sy;
+        fx -= fx >= nfx ? nfx : 0;
+        fy -= fy >= nfy ? nfy : 0;
+        load_row<NW>(a.epsf + ((int64_t)(fx * nfy + fy) * nfz + fz) * NW, ev[u]);
       }
     }
 #pragma unroll
-    for (int e = 0; e < E; ++e) Gs[(size_t)e * blockDim.x + threadIdx.x] = G[e];
-    const int jy = line / a.Nz, jz = line % a.Nz;
-    const int q = (jx * a.Ny + jy) * a.Nz + jz;
-    int kc[3];
-    grid_coords(kf, a.gm.nf, kc);
-    const int qc[3] = {jx, jy, jz};
-    int fc[3];
+    for (int u = 0; u < 2; ++u) {
+      unsigned need = 0;
+      if (qis[u] < nq_blk) {
 #pragma unroll
-    for (int d = 0; d < 3; ++d) fc[d] = (kc[d] + qc[d] * a.gm.sq[d]) % a.gm.nf[d];
-    const int kq = (int)grid_flat(fc, a.gm.nf);
-    qkq[2 * threadIdx.x] = q;
-    qkq[2 * threadIdx.x + 1] = kq;
-#pragma unroll
-    for (int mp = 0; mp < NW; ++mp) {
-      const float2 ee = a.eps2[(int64_t)kq * NW + mp];
-      const float dm = (en_hi - ee.x) + (en_lo - ee.y);
-      if (fabsf(dm) < a.reach) need |= 1u << mp;
+        for (int mp = 0; mp < NW; ++mp)
+          if (fabsf(en_f - ev[u][mp]) < a.reach) need |= 1u << mp;
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, need != 0);
+      int base = 0;
+      if (lane == 0 && bal) base = atomicAdd(&cnt, __popc(bal));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (need) list[base + __popc(bal & ((1u << lane) - 1))] = (int)(need << 16) | qis[u];
     }
   }
-  // compact the warp's (thread, m') items
-  const int cnt = __popc(need);
-  int off = cnt;
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, off, o);
-    if (lane >= o) off += t;
+  cp_async_wait_all();
+  __syncthreads();
+  // phase Y: sum over ry of the slice into Y rows (lines past the grid edge get Ey = 0)
+  if constexpr (E % 2 == 0) {
+    constexpr int EV = E / 2;
+    const int units = a.Bx * (L / UL) * EV;
+    for (int u = threadIdx.x; u < units; u += blockDim.x) {
+      const int cv = u % EV, rest = u / EV;
+      const int lh = rest % (L / UL), rx = rest / (L / UL);
+      float4 acc[UL];
+#pragma unroll
+      for (int l = 0; l < UL; ++l) acc[l] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int p = ppo[rx]; p < ppo[rx + 1]; ++p) {
+        const float4 z = reinterpret_cast<const float4*>(Zsl + (size_t)p * E)[cv];
+        const int ay = pay[p];
+#pragma unroll
+        for (int l = 0; l < UL; ++l) {
+          const float2 ey = Eys[(lh * UL + l) * a.By + ay];
+          acc[l].x = fmaf(ey.x, z.x, fmaf(-ey.y, z.y, acc[l].x));
+          acc[l].y = fmaf(ey.x, z.y, fmaf(ey.y, z.x, acc[l].y));
+          acc[l].z = fmaf(ey.x, z.z, fmaf(-ey.y, z.w, acc[l].z));
+          acc[l].w = fmaf(ey.x, z.w, fmaf(ey.y, z.z, acc[l].w));
+        }
+      }
+#pragma unroll
+      for (int l = 0; l < UL; ++l)
+        reinterpret_cast<float4*>(Ys + (size_t)(rx * L + lh * UL + l) * ES)[cv] = acc[l];
+    }
+  } else {
+    const int units = a.Bx * (L / UL) * E;
+    for (int u = threadIdx.x; u < units; u += blockDim.x) {
+      const int cv = u % E, rest = u / E;
+      const int lh = rest % (L / UL), rx = rest / (L / UL);
+      float2 acc[UL];
+#pragma unroll
+      for (int l = 0; l < UL; ++l) acc[l] = make_float2(0.f, 0.f);
+      for (int p = ppo[rx]; p < ppo[rx + 1]; ++p) {
+        const float2 z = Zsl[(size_t)p * E + cv];
+        const int ay = pay[p];
+#pragma unroll
+        for (int l = 0; l < UL; ++l) {
+          const float2 ey = Eys[(lh * UL + l) * a.By + ay];
+          acc[l].x = fmaf(ey.x, z.x, fmaf(-ey.y, z.y, acc[l].x));
+          acc[l].y = fmaf(ey.x, z.y, fmaf(ey.y, z.x, acc[l].y));
+        }
+      }
+#pragma unroll
+      for (int l = 0; l < UL; ++l) Ys[(size_t)(rx * L + lh * UL + l) * ES + cv] = acc[l];
+    }
   }
-  const int total = __shfl_sync(0xffffffffu, off, 31);
-  off -= cnt;
-  int* wl = items + warp * 32 * NW;
-  for (unsigned m = need; m; m &= m - 1) wl[off++] = (threadIdx.x << 4) | (__ffs(m) - 1);
-  __syncwarp();
+  __syncthreads();
+  // rows of residue pairs (r, -r) -> S = Y_r + Y_-r, D = Y_r - Y_-r (in place)
+  if (a.KP > 0) {
+    if constexpr (ES % 2 == 0) {
+      constexpr int RV = L * ES / 2;  // float4 per plane's rows
+      for (int i = threadIdx.x; i < a.KP * RV; i += blockDim.x) {
+        const int k = a.K0 + i / RV, o = i % RV;
+        float4* ya = reinterpret_cast<float4*>(Ys + (size_t)xS[k] * L * ES) + o;
+        float4* yb = reinterpret_cast<float4*>(Ys + (size_t)xD[k] * L * ES) + o;
+        const float4 u = *ya, v = *yb;
+        *ya = make_float4(u.x + v.x, u.y + v.y, u.z + v.z, u.w + v.w);
+        *yb = make_float4(u.x - v.x, u.y - v.y, u.z - v.z, u.w - v.w);
+      }
+    } else {
+      constexpr int RV = L * ES;
+      for (int i = threadIdx.x; i < a.KP * RV; i += blockDim.x) {
+        const int k = a.K0 + i / RV, o = i % RV;
+        float2* ya = Ys + (size_t)xS[k] * L * ES + o;
+        float2* yb = Ys + (size_t)xD[k] * L * ES + o;
+        const float2 u = *ya, v = *yb;
+        *ya = make_float2(u.x + v.x, u.y + v.y);
+        *yb = make_float2(u.x - v.x, u.y - v.y);
+      }
+    }
+    __syncthreads();
+  }
+  const int total = cnt;
+  // phase 1: SPLIT lanes per listed q
+  const int j = threadIdx.x % SPLIT;
+  const unsigned gmask = (SPLIT == 32 ? 0xffffffffu : ((1u << SPLIT) - 1)) << (lane & ~(SPLIT - 1));
   double acc = 0.0;
-  for (int it = lane; it < total; it += 32) {
-    const int src = wl[it] >> 4, mp = wl[it] & 15;
-    const int q = qkq[2 * src], kq = qkq[2 * src + 1];
-    const float2* gs = Gs + src;  // element e at gs[e * blockDim.x]
-    const float2 ee = a.eps2[(int64_t)kq * NW + mp];
-    const float dm = (en_hi - ee.x) + (en_lo - ee.y);
-    const float2* uh = a.UH + ((int64_t)kq * NW + mp) * NW;
-    float2 u[NW];
-#pragma unroll
-    for (int m = 0; m < NW; ++m) u[m] = uh[m];
-    float2 t[NM];
-#pragma unroll
-    for (int sa = 0; sa < NM; ++sa) {
-      t[sa] = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int m = 0; m < NW; ++m) {
-        const float2 gv = gs[(size_t)(sa * NW + m) * blockDim.x];
-        t[sa].x = fmaf(u[m].x, gv.x, fmaf(-u[m].y, gv.y, t[sa].x));
-        t[sa].y = fmaf(u[m].x, gv.y, fmaf(u[m].y, gv.x, t[sa].y));
+  // this group's prefetch slot: [0,2) el row of the first listed band, [2, 2+NW) its U row,
+  // then Z_q transposed [v][sa], then (omega, n_B)[v]
+  float2* pf = Zsl + (size_t)(threadIdx.x / SPLIT) * SLOT;
+  constexpr int O_UH = 2, O_ZT = 2 + NW, O_ON = 2 + NW + NM * NM, NPF = 2 + NW + NM * NM + NM;
+  for (int it = threadIdx.x / SPLIT; it < total; it += blockDim.x / SPLIT) {
+    const int w = list[it];
+    const int qi = w & 0xffff;
+    const unsigned need = (unsigned)w >> 16;
+    const int l = qi / a.Nx, jx = qi - l * a.Nx;
+    const int jy = jy0 + l;
+    const int q = (jx * a.Ny + jy) * a.Nz + jz;
+    int fx = kc[0] + jx * sx, fy = kc[1] + jy * sy;
+    fx -= fx >= nfx ? nfx : 0;
+    fy -= fy >= nfy ? nfy : 0;
+    const int64_t kq = (int64_t)(fx * nfy + fy) * nfz + fz;
+    const int mp0 = __ffs(need) - 1;
+    {  // issue the epilogue's loads now; they land while the x sum runs
+      const float2* s_el = reinterpret_cast<const float2*>(a.el4 + kq * NW + mp0);
+      const float2* s_uh = a.UH + (kq * NW + mp0) * NW;
+      const float2* s_zt = a.ZT + (int64_t)q * NM * NM;
+      const float2* s_on = a.omnb + (int64_t)q * NM;
+      constexpr int STEP = A16 ? 2 : 1;
+      for (int o = j * STEP; o < NPF; o += SPLIT * STEP) {
+        const float2* src = o < O_UH ? s_el + o : o < O_ZT ? s_uh + (o - O_UH) : o < O_ON ? s_zt + (o - O_ZT) : s_on + (o - O_ON);
+        if constexpr (A16) cp_async16(pf + o, src);
+        else cp_async8(pf + o, src);
       }
     }
-    const float f = a.f32[(int64_t)kq * NW + mp];
-    const float2* zq = a.Zf + (int64_t)q * NM * NM;
-    float part = 0.f;
+    float2 G[NM][MW];
 #pragma unroll
-    for (int v = 0; v < NM; ++v) {
-      float2 g = make_float2(0.f, 0.f);
+    for (int sa = 0; sa < NM; ++sa)
+#pragma unroll
+      for (int mm = 0; mm < MW; ++mm) G[sa][mm] = make_float2(0.f, 0.f);
+    // real-factor rows, then residue pairs (cos S + i sin D), then residues without a partner
+    for (int k = 0; k < a.K0; ++k) {
+      const float c = Exs[jx * a.K + k].x;
+      const float2* ys = Ys + (xS[k] * L + l) * ES + j * MW;
 #pragma unroll
       for (int sa = 0; sa < NM; ++sa) {
-        const float2 zz = zq[sa * NM + v];
-        g.x = fmaf(t[sa].x, zz.x, fmaf(-t[sa].y, zz.y, g.x));
-        g.y = fmaf(t[sa].x, zz.y, fmaf(t[sa].y, zz.x, g.y));
+        if constexpr (MW % 2 == 0) {
+#pragma unroll
+          for (int mm = 0; mm < MW; mm += 2) {
+            const float4 v = *reinterpret_cast<const float4*>(ys + sa * NW + mm);
+            G[sa][mm].x = fmaf(c, v.x, G[sa][mm].x);
+            G[sa][mm].y = fmaf(c, v.y, G[sa][mm].y);
+            G[sa][mm + 1].x = fmaf(c, v.z, G[sa][mm + 1].x);
+            G[sa][mm + 1].y = fmaf(c, v.w, G[sa][mm + 1].y);
+          }
+        } else {
+#pragma unroll
+          for (int mm = 0; mm < MW; ++mm) {
+            const float2 v = ys[sa * NW + mm];
+            G[sa][mm].x = fmaf(c, v.x, G[sa][mm].x);
+            G[sa][mm].y = fmaf(c, v.y, G[sa][mm].y);
+          }
+        }
       }
-      const float om = a.omf[(int64_t)q * NM + v], nb = a.nBf[(int64_t)q * NM + v];
-      const float t1 = (dm - om) * a.inv_sigma;
-      const float t2 = (dm + om) * a.inv_sigma;
-      float w = 0.f;
-      if (t1 * t1 < a.cut2) w += (nb + 1.f - f) * expf(-t1 * t1);
-      if (t2 * t2 < a.cut2) w += (nb + f) * expf(-t2 * t2);
-      part = fmaf(g.x * g.x + g.y * g.y, w, part);
     }
-    acc += (double)part * a.scale;
+#pragma unroll 2
+    for (int k = a.K0; k < a.K0 + a.KP; ++k) {
+      const float2 cs = Exs[jx * a.K + k];
+      const float2* ys = Ys + (xS[k] * L + l) * ES + j * MW;
+      const float2* yd = Ys + (xD[k] * L + l) * ES + j * MW;
+#pragma unroll
+      for (int sa = 0; sa < NM; ++sa) {
+        if constexpr (MW % 2 == 0) {
+#pragma unroll
+          for (int mm = 0; mm < MW; mm += 2) {
+            const float4 v = *reinterpret_cast<const float4*>(ys + sa * NW + mm);
+            const float4 d = *reinterpret_cast<const float4*>(yd + sa * NW + mm);
+            G[sa][mm].x = fmaf(cs.x, v.x, fmaf(-cs.y, d.y, G[sa][mm].x));
+            G[sa][mm].y = fmaf(cs.x, v.y, fmaf(cs.y, d.x, G[sa][mm].y));
+            G[sa][mm + 1].x = fmaf(cs.x, v.z, fmaf(-cs.y, d.w, G[sa][mm + 1].x));
+            G[sa][mm + 1].y = fmaf(cs.x, v.w, fmaf(cs.y, d.z, G[sa][mm + 1].y));
+          }
+        } else {
+#pragma unroll
+          for (int mm = 0; mm < MW; ++mm) {
+            const float2 v = ys[sa * NW + mm], d = yd[sa * NW + mm];
+            G[sa][mm].x = fmaf(cs.x, v.x, fmaf(-cs.y, d.y, G[sa][mm].x));
+            G[sa][mm].y = fmaf(cs.x, v.y, fmaf(cs.y, d.x, G[sa][mm].y));
+          }
+        }
+      }
+    }
+    for (int k = a.K0 + a.KP; k < a.K; ++k) {
+      const float2 ex = Exs[jx * a.K + k];
+      const float2* y = Ys + (xS[k] * L + l) * ES + j * MW;
+#pragma unroll
+      for (int sa = 0; sa < NM; ++sa) {
+        if constexpr (MW % 2 == 0) {
+#pragma unroll
+          for (int mm = 0; mm < MW; mm += 2) {
+            const float4 v = *reinterpret_cast<const float4*>(y + sa * NW + mm);
+            G[sa][mm].x = fmaf(ex.x, v.x, fmaf(-ex.y, v.y, G[sa][mm].x));
+            G[sa][mm].y = fmaf(ex.x, v.y, fmaf(ex.y, v.x, G[sa][mm].y));
+            G[sa][mm + 1].x = fmaf(ex.x, v.z, fmaf(-ex.y, v.w, G[sa][mm + 1].x));
+            G[sa][mm + 1].y = fmaf(ex.x, v.w, fmaf(ex.y, v.z, G[sa][mm + 1].y));
+          }
+        } else {
+#pragma unroll
+          for (int mm = 0; mm < MW; ++mm) {
+            const float2 v = y[sa * NW + mm];
+            G[sa][mm].x = fmaf(ex.x, v.x, fmaf(-ex.y, v.y, G[sa][mm].x));
+            G[sa][mm].y = fmaf(ex.x, v.y, fmaf(ex.y, v.x, G[sa][mm].y));
+          }
+        }
+      }
+    }
+    cp_async_wait_all();
+    __syncwarp(gmask);
+    for (unsigned m = need; m; m &= m - 1) {
+      const int mp = __ffs(m) - 1;
+      float4 el;
+      float2 u[MW];
+      if (mp == mp0) {
+        el = *reinterpret_cast<const float4*>(pf);
+#pragma unroll
+        for (int mm = 0; mm < MW; ++mm) u[mm] = pf[O_UH + j * MW + mm];
+      } else {
+        el = a.el4[kq * NW + mp];
+        load_cplx<MW>(a.UH + (kq * NW + mp) * NW + j * MW, u);
+      }
+      const float dm = (en_hi - el.x) + (en_lo - el.y);
+      const float f = el.z;
+      float2 t[NM];
+#pragma unroll
+      for (int sa = 0; sa < NM; ++sa) {
+        t[sa] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int mm = 0; mm < MW; ++mm) {
+          t[sa].x = fmaf(u[mm].x, G[sa][mm].x, fmaf(-u[mm].y, G[sa][mm].y, t[sa].x));
+          t[sa].y = fmaf(u[mm].x, G[sa][mm].y, fmaf(u[mm].y, G[sa][mm].x, t[sa].y));
+        }
+      }
+#pragma unroll
+      for (int o = 1; o < SPLIT; o <<= 1) {
+#pragma unroll
+        for (int sa = 0; sa < NM; ++sa) {
+          t[sa].x += __shfl_xor_sync(gmask, t[sa].x, o);
+          t[sa].y += __shfl_xor_sync(gmask, t[sa].y, o);
+        }
+      }
+      float part = 0.f;
+      for (int v = j; v < NM; v += SPLIT) {
+        const float2* z = pf + O_ZT + v * NM;
+        float2 g = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int sa = 0; sa < NM; ++sa) {
+          const float2 zz = z[sa];
+          g.x = fmaf(t[sa].x, zz.x, fmaf(-t[sa].y, zz.y, g.x));
+          g.y = fmaf(t[sa].x, zz.y, fmaf(t[sa].y, zz.x, g.y));
+        }
+        const float2 on = pf[O_ON + v];
+        const float t1 = (dm - on.x) * a.inv_sigma;
+        const float t2 = (dm + on.x) * a.inv_sigma;
+        float wgt = 0.f;
+        if (t1 * t1 < a.cut2) wgt += (on.y + 1.f - f) * expf(-t1 * t1);
+        if (t2 * t2 < a.cut2) wgt += (on.y + f) * expf(-t2 * t2);
+        part = fmaf(g.x * g.x + g.y * g.y, wgt, part);
+      }
+      acc += (double)part * a.scale;
+    }
+    __syncwarp(gmask);  // the slot is refilled by the group's next q
   }
-  __shared__ double red[32];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) red[warp] = acc;
   __syncthreads();
@@ -219,41 +513,73 @@ __global__ void __launch_bounds__(kDftMaxThreads / PHX_DFT_MINB, PHX_DFT_MINB) k
     double sum = 0.0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) sum += red[i];
     if (sum != 0.0) atomicAdd(a.gamma + a.s_base + s, sum);
+    if (total) atomicAdd(a.nq_evaluated, (unsigned long long)total);
   }
 }
 
-template <int NW, int NM>
-static int launch_x(cudaStream_t st, const DftXArgs& a, int S) {
-  const int threads = (a.Nx * kDftLines + 31) / 32 * 32;  // whole warps for the compaction and reduction
-  const size_t smem = dft_smem_bytes(a.Bx, NW * NM, threads, NW, a.Nx);
-  if (cudaFuncSetAttribute(k_dft_x_elph<NW, NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+template <int NW, int NM, int SPLIT>
+static int launch_yx(cudaStream_t st, const DftXArgs& a, int S) {
+  const size_t smem = dft_smem_bytes(a.P, a.Bx, a.By, NW, NM, a.Nx, a.K);
+  if (cudaFuncSetAttribute(k_dft_yx_elph<NW, NM, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return -1;
-  const int lines = a.Ny * a.Nz;
-  dim3 grid((unsigned)((lines + kDftLines - 1) / kDftLines), (unsigned)S);
-  k_dft_x_elph<NW, NM><<<grid, threads, smem, st>>>(a);
+  dim3 grid((unsigned)(a.Nz * ((a.Ny + kDftLines - 1) / kDftLines)), (unsigned)S);
+  k_dft_yx_elph<NW, NM, SPLIT><<<grid, kDftXThreads, smem, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int dft_launch(cudaStream_t st, const DftYzArgs& yz, const DftXArgs& x, int S, int nw, int nm) {
-  dim3 g1((unsigned)((yz.E + 15) / 16), (unsigned)yz.Bx, (unsigned)S);
-  const size_t sm1 = dft_yz_smem_bytes(yz.ne_max, yz.Ny, yz.By, yz.Nz, yz.Bz);
-  if (cudaFuncSetAttribute(k_dft_yz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1) != cudaSuccess) return -1;
-  k_dft_yz<<<g1, yz.Nz * 16, sm1, st>>>(yz);
+int dft_launch(cudaStream_t st, const DftZArgs& z, const DftXArgs& x, int S, int nw, int nm, int ne_plane_max) {
+  const size_t sm1 = dft_z_smem_bytes(ne_plane_max, z.E, z.Nz, z.Bz);
+  if (cudaFuncSetAttribute(k_dft_z, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1) != cudaSuccess) return -1;
+  k_dft_z<<<dim3((unsigned)x.Bx, (unsigned)S), 256, sm1, st>>>(z);
   if (cudaGetLastError() != cudaSuccess) return -1;
-  if (nw == 8 && nm == 6) return launch_x<8, 6>(st, x, S);
-  if (nw == 2 && nm == 3) return launch_x<2, 3>(st, x, S);
-  if (nw == 1 && nm == 3) return launch_x<1, 3>(st, x, S);
+  if (nw == 8 && nm == 6) return launch_yx<8, 6, dft_split(8)>(st, x, S);
+  if (nw == 2 && nm == 3) return launch_yx<2, 3, dft_split(2)>(st, x, S);
+  if (nw == 1 && nm == 3) return launch_yx<1, 3, dft_split(1)>(st, x, S);
   return -2;
 }
 
-size_t dft_smem_bytes(int Bx, int E, int threads, int nw, int Nx) {
-  return sizeof(float2) * ((size_t)Bx * kDftLines * E + (size_t)threads * E + (size_t)Nx * Bx) +
-         sizeof(int) * ((size_t)(threads / 32) * 32 * nw + 2 * (size_t)threads);
+size_t dft_smem_bytes(int P, int Bx, int By, int nw, int nm, int Nx, int K) {
+  const int E = nw * nm;
+  const size_t zsl = std::max((size_t)P * E, (size_t)(kDftXThreads / dft_split(nw)) * dft_slot(nw, nm));
+  return sizeof(float2) * (zsl + (size_t)Bx * kDftLines * dft_row_stride(E, nw) + (size_t)Nx * K +
+                           (size_t)kDftLines * By) +
+         sizeof(int) * ((size_t)Bx + 1 + 2 * (size_t)K + P + (size_t)kDftLines * Nx);
 }
 
-size_t dft_yz_smem_bytes(int ne_max, int Ny, int By, int Nz, int Bz) {
-  return sizeof(float2) * ((size_t)ne_max * 16 + (size_t)Ny * By + (size_t)Nz * Bz) + sizeof(int) * 2 * (size_t)ne_max;
+size_t dft_z_smem_bytes(int ne_plane_max, int E, int Nz, int Bz) {
+  return sizeof(float2) * ((size_t)ne_plane_max * E + (size_t)Nz * Bz) + sizeof(int) * (size_t)ne_plane_max;
+}
+
+// FP32 tables of the fused kernel: per fine-grid point and band the energy (window test) and
+// (eps hi, eps lo, f); per q the mode factors Z[sa][v] transposed to [v][sa] and (omega, n_B).
+__global__ void k_dft_tables(const double* __restrict__ epsF, const double* __restrict__ fF, int64_t NF, int nw,
+                             const cplx* __restrict__ Z, const double* __restrict__ om, const double* __restrict__ nB,
+                             int64_t Nq, int nm, float* __restrict__ epsf, float4* __restrict__ el4,
+                             float2* __restrict__ ZT, float2* __restrict__ omnb) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < NF * nw) {
+    const double e = epsF[t];
+    const float hi = (float)e;
+    epsf[t] = hi;
+    el4[t] = make_float4(hi, (float)(e - (double)hi), (float)fF[t], 0.f);
+  }
+  if (t < Nq * nm * nm) {
+    const int64_t q = t / (nm * nm);
+    const int r = (int)(t % (nm * nm));
+    const int v = r / nm, sa = r % nm;
+    const cplx z = Z[q * nm * nm + sa * nm + v];
+    ZT[t] = make_float2((float)z.re, (float)z.im);
+  }
+  if (t < Nq * nm) omnb[t] = make_float2((float)om[t], (float)nB[t]);
+}
+
+int dft_tables(cudaStream_t st, const double* epsF, const double* fF, int64_t NF, int nw, const cplx* Z,
+               const double* om, const double* nB, int64_t Nq, int nm, float* epsf, float4* el4, float2* ZT,
+               float2* omnb) {
+  const int64_t n = NF * nw > Nq * nm * nm ? NF * nw : Nq * nm * nm;
+  k_dft_tables<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(epsF, fF, NF, nw, Z, om, nB, Nq, nm, epsf, el4, ZT, omnb);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 // E[j][a] = e^{2 pi i j r_a / N} for residues r_a (exact integer argument reduction, sincospi).

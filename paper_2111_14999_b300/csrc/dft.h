@@ -6,54 +6,77 @@
 namespace phx {
 
 #ifndef PHX_DFT_LINES
-#define PHX_DFT_LINES 4
+#define PHX_DFT_LINES 8
 #endif
-#ifndef PHX_DFT_MINB
-#define PHX_DFT_MINB 1
+#ifndef PHX_DFT_SPLIT8
+#define PHX_DFT_SPLIT8 4
 #endif
-constexpr int kDftLines = PHX_DFT_LINES;  // (jy, jz) lines per block of the x-sum kernel
-constexpr int kDftMaxThreads = 512;   // Nx * kDftLines <= 512 (Nx <= 64)
+#ifndef PHX_DFT_THREADS
+#define PHX_DFT_THREADS 256
+#endif
+constexpr int kDftLines = PHX_DFT_LINES;      // jy lines (at one jz) per block of the fused kernel
+constexpr int kDftXThreads = PHX_DFT_THREADS;  // threads per block of the fused kernel
+constexpr int kDftSplit8 = PHX_DFT_SPLIT8;     // lanes per q of the x sum at nw = 8
+constexpr int kDftUnitLines = kDftLines < 4 ? kDftLines : 4;  // lines per work unit of the y sum
+static_assert(kDftLines % kDftUnitLines == 0, "lines per block must be a multiple of the y-sum unit");
 
-struct DftYzArgs {
-  const float2* T;       // [S][nR][E] stage-1 output (E = 3na * nw, column c = sa*nw + m)
-  const float* w;        // [nR] R_p weights
-  int nR, E;
-  int Bx, By, Bz;        // residues of R_p mod N per axis
-  int Ny, Nz;
-  const int* plane_off;  // [Bx+1] entries of each rx residue
-  int ne_max;            // most entries of one rx residue
-  const int* ent_ay;     // per entry (sorted by rx residue, then ry residue): ry residue index
-  const int* ent_az;     //   rz residue index
-  const int* ent_r;      //   R_p index
-  const float2* Ey;      // [Ny][By] e^{2 pi i jy ry / Ny}
-  const float2* Ez;      // [Nz][Bz]
-  float2* Y;             // [S][Bx][Ny][Nz][E]
+// The R_p set grouped by residues r = R mod N: entries sorted by (rx, ry, rz) residue index,
+// "pairs" = distinct (rx, ry), "planes" = distinct rx.
+struct DftZArgs {
+  const float2* T;           // [S][nR][E] stage-1 output (E = 3na * nw, column c = sa*nw + m)
+  const float* w;            // [nR] R_p weights
+  int nR, E, P, Nz, Bz;
+  const int* plane_pair_off;  // [Bx+1] first pair of each plane
+  const int* pair_ent_off;    // [P+1] first entry of each pair
+  const int* ent_az;          // per entry: rz residue index
+  const int* ent_r;           // per entry: R_p index
+  const float2* Ez;           // [Nz][Bz] e^{2 pi i jz rz / Nz}
+  float2* Zs;                 // [S][Nz][P][E] sum_rz Ez[jz][rz] w_R T[R] over the entries of each pair
 };
 
 struct DftXArgs {
-  const float2* Y;
-  int Bx, Nx, Ny, Nz;
-  const float2* Ex;      // [Nx][Bx]
-  const int* st_k;       // [S]
-  const int* st_b;       // [S]
-  const double* epsF;    // [NF][nw]
+  const float2* Zs;           // [S][Nz][P][E]
+  int P, Bx, By, Nx, Ny, Nz;
+  const int* plane_pair_off;  // [Bx+1]
+  const int* pair_ay;         // [P] ry residue index of each pair
+  // x rows: the rx residues grouped by r -> -r (mod Nx).  Row k reads Y row xS[k]; a residue
+  // with a partner r' = -r (xD[k] >= 0, != xS[k]) has its rows replaced by S = Y_r + Y_r' and
+  // D = Y_r - Y_r' and contributes cos(t r) S + i sin(t r) D, t = 2 pi jx / Nx; a residue equal
+  // to its negative (r = 0, Nx/2; xD[k] = -1) contributes cos(t r) Y_r; one without a partner
+  // (xD[k] == xS[k]) contributes e^{i t r} Y_r in the same form with S = D = Y_r.
+  int K, K0, KP;              // rows [0, K0) real-factor, [K0, K0+KP) pairs, the rest without a partner
+  const int* xS;              // [K]
+  const int* xD;              // [K]
+  const float2* Ex;           // [Nx][K] (cos, sin)(2 pi jx r_k / Nx)
+  const float2* Ey;           // [Ny][By]
+  const int* st_k;            // [S]
+  const int* st_b;            // [S]
+  const double* epsF;         // [NF][nw]
   GridMap gm;
-  const float2* eps2;    // [NF][nw] (hi, lo)
-  const float* f32;      // [NF][nw]
-  const float2* UH;      // [NF][nw][nw] conj(U[m][m'])
-  const float2* Zf;      // [Nq][nm][nm]
-  const float* omf;      // [Nq][nm]
-  const float* nBf;      // [Nq][nm]
+  const float* epsf;          // [NF][nw] FP32 energies (window test)
+  const float4* el4;          // [NF][nw] (eps hi, eps lo, f, 0)
+  const float2* UH;           // [NF][nw][nw] conj(U[m][m'])
+  const float2* ZT;           // [Nq][nm (v)][nm (sa)] mode factors, transposed
+  const float2* omnb;         // [Nq][nm] (omega, n_B)
   float reach, inv_sigma, cut2;
-  double scale;          // (2 pi / N_q) / (sqrt(pi) sigma)
+  double scale;               // (2 pi / N_q) / (sqrt(pi) sigma)
   double* gamma;
   int64_t s_base;
+  unsigned long long* nq_evaluated;  // += the (state, q) pairs whose x sum was evaluated
 };
 
 // Launches both kernels for S states; -1 on a launch error, -2 for a (nw, 3na) without a kernel.
-int dft_launch(cudaStream_t st, const DftYzArgs& yz, const DftXArgs& x, int S, int nw, int nm);
-size_t dft_smem_bytes(int Bx, int E, int threads, int nw, int Nx);
-size_t dft_yz_smem_bytes(int ne_max, int Ny, int By, int Nz, int Bz);
+int dft_launch(cudaStream_t st, const DftZArgs& z, const DftXArgs& x, int S, int nw, int nm, int ne_plane_max);
+// Lanes per q of the x sum for nw Wannier functions.
+__host__ __device__ constexpr int dft_split(int nw) { return nw == 8 ? kDftSplit8 : (nw % 2 == 0 ? 2 : 1); }
+// Per lane group of the x sum: complex slots prefetched for one q (el row, U row, Z_q, (omega, n_B)).
+__host__ __device__ constexpr int dft_slot(int nw, int nm) { return (2 + nw + nm * nm + nm + 1) / 2 * 2; }
+size_t dft_smem_bytes(int P, int Bx, int By, int nw, int nm, int Nx, int K);
+size_t dft_z_smem_bytes(int ne_plane_max, int E, int Nz, int Bz);
 int dft_table(cudaStream_t st, const int* res, int B, int N, float2* E);
+// FP32 tables of the fused kernel from the FP64 band and phonon arrays.
+int dft_tables(cudaStream_t st, const double* epsF, const double* fF, int64_t NF, int nw, const cplx* Z,
+               const double* om, const double* nB, int64_t Nq, int nm, float* epsf, float4* el4, float2* ZT,
+               float2* omnb);
 
 }  // namespace phx

@@ -1790,8 +1790,8 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
   if (!((nw == 8 && nm == 6) || (nw == 2 && nm == 3) || (nw == 1 && nm == 3)))
     return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "the grid-DFT stage 2 is built for (nw, 3na) in {(8,6), (2,3), (1,3)}");
   const int Nx = gm.nq[0], Ny = gm.nq[1], Nz = gm.nq[2];
-  if (Nx * kDftLines > kDftMaxThreads || Nz * 16 > 1024)
-    return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "the grid-DFT stage 2 needs q-grid sizes Nx <= 64 and Nz <= 64");
+  if (Nz * 16 > 1024 || Nx > 256)
+    return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "the grid-DFT stage 2 needs q-grid sizes Nx <= 256 and Nz <= 64");
   const int esz = 2, KB = 64;
   const int Kp1 = (2 * nRe + KB - 1) / KB * KB;
   const int64_t C = (int64_t)nRp * nw * nw * nm;
@@ -1802,6 +1802,9 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
   int* err = (int*)ensure(c, "tc_err", 64, &st);
   if (!err) return st;
   CK(c, cudaMemsetAsync(err, 0, 64, c->stream));
+  unsigned long long* nq_eval = (unsigned long long*)ensure(c, "dft_nq_eval", 64, &st);
+  if (!nq_eval) return st;
+  CK(c, cudaMemsetAsync(nq_eval, 0, 64, c->stream));
   const float sA1 = host_pow2_scale(c->we_max);
   TRY((ensure_g_operand<FMT, NSPLIT>(c, C, Kp1, esz)));
   Parts Pg{{c->tc->g_part[0], c->tc->g_part[1], c->tc->g_part[2]}};
@@ -1814,17 +1817,24 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
   if (!eps2) return st;
   unsigned long long* dmax = (unsigned long long*)ensure(c, "tc_max", 64, &st);
   if (!dmax) return st;
-  float2* Zf = (float2*)ensure(c, "tcg_Zf", sizeof(float2) * Nq * nm * nm, &st);
-  if (!Zf) return st;
-  float* omf = (float*)ensure(c, "tcg_omf", sizeof(float) * Nq * nm, &st);
-  if (!omf) return st;
-  float* nBf = (float*)ensure(c, "tcg_nBf", sizeof(float) * Nq * nm, &st);
-  if (!nBf) return st;
+  float* epsf = (float*)ensure(c, "dft_epsf", sizeof(float) * NF * nw, &st);
+  if (!epsf) return st;
+  float4* el4 = (float4*)ensure(c, "dft_el4", sizeof(float4) * NF * nw, &st);
+  if (!el4) return st;
+  float2* ZT = (float2*)ensure(c, "dft_ZT", sizeof(float2) * Nq * nm * nm, &st);
+  if (!ZT) return st;
+  float2* omnb = (float2*)ensure(c, "dft_omnb", sizeof(float2) * Nq * nm, &st);
+  if (!omnb) return st;
   k_tables_el<<<(unsigned)((NF * nw * nw + 255) / 256), 256, 0, c->stream>>>(UF, fF, epsF, NF, nw, UH, f32, eps2);
   CK(c, cudaMemsetAsync(dmax, 0, 64, c->stream));
   k_absmax_f64<<<64, 256, 0, c->stream>>>(omega, Nq * nm, dmax);
-  k_tables_ph<<<(unsigned)((Nq * nm * nm + 255) / 256), 256, 0, c->stream>>>(Zq, omega, nB, Nq, nm, Zf, omf, nBf);
-  c->launches += 3;
+  c->launches += 2;
+  CK(c, cudaGetLastError());
+  if (dft_tables(c->stream, epsF, fF, NF, nw, Zq, omega, nB, Nq, nm, epsf, el4, ZT, omnb)) {
+    cudaGetLastError();
+    return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the grid-DFT tables failed");
+  }
+  c->launches += 1;
   CK(c, cudaGetLastError());
   unsigned long long ombits = 0;
   CK(c, cudaMemcpyAsync(&ombits, dmax, sizeof(ombits), cudaMemcpyDeviceToHost, c->stream));
@@ -1847,39 +1857,75 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
       idx[3 * i + d] = (int)(std::lower_bound(resv[d].begin(), resv[d].end(), r[i]) - resv[d].begin());
   }
   const int Bx = (int)resv[0].size(), By = (int)resv[1].size(), Bz = (int)resv[2].size();
+  // entries sorted by (rx, ry, rz) residue index; pairs = distinct (rx, ry); planes = distinct rx
   std::vector<int> order(nRp);
   for (int i = 0; i < nRp; ++i) order[i] = i;
   std::sort(order.begin(), order.end(), [&](int a, int b) {
-    if (idx[3 * a] != idx[3 * b]) return idx[3 * a] < idx[3 * b];
-    return idx[3 * a + 1] < idx[3 * b + 1];
+    for (int d = 0; d < 3; ++d)
+      if (idx[3 * a + d] != idx[3 * b + d]) return idx[3 * a + d] < idx[3 * b + d];
+    return a < b;
   });
-  std::vector<int> plane_off(Bx + 1, 0), ent_ay(nRp), ent_az(nRp), ent_r(nRp);
+  std::vector<int> plane_pair_off(Bx + 1, 0), pair_ent_off, pair_ay, ent_az(nRp), ent_r(nRp);
   for (int e = 0; e < nRp; ++e) {
     const int r = order[e];
-    ent_ay[e] = idx[3 * r + 1];
     ent_az[e] = idx[3 * r + 2];
     ent_r[e] = r;
-    plane_off[idx[3 * r] + 1] = e + 1;
+    const bool new_pair = e == 0 || idx[3 * r] != idx[3 * order[e - 1]] || idx[3 * r + 1] != idx[3 * order[e - 1] + 1];
+    if (new_pair) {
+      pair_ent_off.push_back(e);
+      pair_ay.push_back(idx[3 * r + 1]);
+    }
+    plane_pair_off[idx[3 * r] + 1] = (int)pair_ent_off.size();
   }
-  for (int a = 1; a <= Bx; ++a) plane_off[a] = std::max(plane_off[a], plane_off[a - 1]);
+  const int P = (int)pair_ay.size();
+  pair_ent_off.push_back(nRp);
+  for (int a = 1; a <= Bx; ++a) plane_pair_off[a] = std::max(plane_pair_off[a], plane_pair_off[a - 1]);
+  int ne_plane_max = 0;
+  for (int a = 0; a < Bx; ++a)
+    ne_plane_max = std::max(ne_plane_max, pair_ent_off[plane_pair_off[a + 1]] - pair_ent_off[plane_pair_off[a]]);
+  // x rows: pair each rx residue with its negative modulo Nx (Wigner-Seitz sets are inversion symmetric)
+  std::vector<int> xS, xD, xres;
+  int K0 = 0, KP = 0;
+  for (int pass = 0; pass < 3; ++pass) {  // real-factor rows, then pairs, then unpaired residues
+    for (int a = 0; a < Bx; ++a) {
+      const int r = resv[0][a], rn = (Nx - r) % Nx;
+      const int b = (int)(std::lower_bound(resv[0].begin(), resv[0].end(), rn) - resv[0].begin());
+      const bool has = b < Bx && resv[0][b] == rn;
+      const int type = has && b == a ? 0 : has && b > a ? 1 : !has ? 2 : -1;
+      if (type != pass) continue;
+      xS.push_back(a);
+      xD.push_back(type == 0 ? -1 : type == 1 ? b : a);
+      xres.push_back(r);
+      K0 += type == 0;
+      KP += type == 1;
+    }
+  }
+  const int K = (int)xS.size();
+  if (dft_smem_bytes(P, Bx, By, nw, nm, Nx, K) > 227 * 1024 || dft_z_smem_bytes(ne_plane_max, E, Nz, Bz) > 227 * 1024)
+    return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED,
+                "the grid-DFT tiles (%d (rx, ry) residue pairs, Nx = %d) exceed shared memory", P, Nx);
   std::vector<float> wf(nRp);
   for (int i = 0; i < nRp; ++i) wf[i] = (float)wp[i];
-  void *d_po, *d_ay, *d_az, *d_r, *d_w, *d_rx, *d_ry, *d_rz;
-  TRY(upload(c, "dft_po", plane_off.data(), sizeof(int) * (Bx + 1), &d_po));
-  TRY(upload(c, "dft_ay", ent_ay.data(), sizeof(int) * nRp, &d_ay));
+  void *d_ppo, *d_peo, *d_pay, *d_az, *d_r, *d_w, *d_rx, *d_ry, *d_rz;
+  TRY(upload(c, "dft_ppo", plane_pair_off.data(), sizeof(int) * (Bx + 1), &d_ppo));
+  TRY(upload(c, "dft_peo", pair_ent_off.data(), sizeof(int) * (P + 1), &d_peo));
+  TRY(upload(c, "dft_pay", pair_ay.data(), sizeof(int) * P, &d_pay));
   TRY(upload(c, "dft_az", ent_az.data(), sizeof(int) * nRp, &d_az));
   TRY(upload(c, "dft_r", ent_r.data(), sizeof(int) * nRp, &d_r));
   TRY(upload(c, "dft_w", wf.data(), sizeof(float) * nRp, &d_w));
-  TRY(upload(c, "dft_rx", resv[0].data(), sizeof(int) * Bx, &d_rx));
+  void *d_xS, *d_xD;
+  TRY(upload(c, "dft_rx", xres.data(), sizeof(int) * K, &d_rx));
+  TRY(upload(c, "dft_xS", xS.data(), sizeof(int) * K, &d_xS));
+  TRY(upload(c, "dft_xD", xD.data(), sizeof(int) * K, &d_xD));
   TRY(upload(c, "dft_ry", resv[1].data(), sizeof(int) * By, &d_ry));
   TRY(upload(c, "dft_rz", resv[2].data(), sizeof(int) * Bz, &d_rz));
-  float2* Ex = (float2*)ensure(c, "dft_Ex", sizeof(float2) * Nx * Bx, &st);
+  float2* Ex = (float2*)ensure(c, "dft_Ex", sizeof(float2) * Nx * K, &st);
   if (!Ex) return st;
   float2* Ey = (float2*)ensure(c, "dft_Ey", sizeof(float2) * Ny * By, &st);
   if (!Ey) return st;
   float2* Ez = (float2*)ensure(c, "dft_Ez", sizeof(float2) * Nz * Bz, &st);
   if (!Ez) return st;
-  if (dft_table(c->stream, (const int*)d_rx, Bx, Nx, Ex) || dft_table(c->stream, (const int*)d_ry, By, Ny, Ey) ||
+  if (dft_table(c->stream, (const int*)d_rx, K, Nx, Ex) || dft_table(c->stream, (const int*)d_ry, By, Ny, Ey) ||
       dft_table(c->stream, (const int*)d_rz, Bz, Nz, Ez)) {
     cudaGetLastError();
     return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the DFT phase tables failed");
@@ -1893,9 +1939,9 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
   tm.end(c, &c->stats.stage1_ms);
   unsigned* tmaxp = (unsigned*)ensure(c, "tc_tmax", 64, &st);
   if (!tmaxp) return st;
-  const int64_t per_state = (int64_t)Bx * Ny * Nz * E * (int64_t)sizeof(float2);
+  const int64_t per_state = (int64_t)P * Nz * E * (int64_t)sizeof(float2);
   const int max_states = p->max_batch_states > 0
-                             ? p->max_batch_states
+                             ? std::min(p->max_batch_states, 65535)  // states run along gridDim.y
                              : (int)std::max<int64_t>(1, std::min<int64_t>(4096, ((int64_t)8 << 30) / per_state));
   std::vector<int> kb_list, st_kb;
   int64_t i0 = 0;
@@ -1911,52 +1957,57 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
     TRY((stage1_batch<FMT, NSPLIT, NPROD>(c, gm, kb_list, st_kb, i0, st_k, st_b, UF, Pg, sA1, cis_k, gk, err, tmaxp,
                                           (const int*)d_kb, (const int*)d_stkb, &Tb)));
     tm.end(c, &c->stats.stage1_ms);
-    float2* Y = (float2*)ensure(c, "dft_Y", (size_t)per_state * S, &st);
-    if (!Y) return st;
-    DftYzArgs yz;
-    yz.T = Tb;
-    yz.w = (const float*)d_w;
-    yz.nR = nRp;
-    yz.E = E;
-    yz.Bx = Bx;
-    yz.By = By;
-    yz.Bz = Bz;
-    yz.Ny = Ny;
-    yz.Nz = Nz;
-    yz.plane_off = (const int*)d_po;
-    yz.ne_max = 0;
-    for (int a = 0; a < Bx; ++a) yz.ne_max = std::max(yz.ne_max, plane_off[a + 1] - plane_off[a]);
-    yz.ent_ay = (const int*)d_ay;
-    yz.ent_az = (const int*)d_az;
-    yz.ent_r = (const int*)d_r;
-    yz.Ey = Ey;
-    yz.Ez = Ez;
-    yz.Y = Y;
+    float2* Zs = (float2*)ensure(c, "dft_Zs", (size_t)per_state * S, &st);
+    if (!Zs) return st;
+    DftZArgs zz;
+    zz.T = Tb;
+    zz.w = (const float*)d_w;
+    zz.nR = nRp;
+    zz.E = E;
+    zz.P = P;
+    zz.Nz = Nz;
+    zz.Bz = Bz;
+    zz.plane_pair_off = (const int*)d_ppo;
+    zz.pair_ent_off = (const int*)d_peo;
+    zz.ent_az = (const int*)d_az;
+    zz.ent_r = (const int*)d_r;
+    zz.Ez = Ez;
+    zz.Zs = Zs;
     DftXArgs x;
-    x.Y = Y;
+    x.Zs = Zs;
+    x.P = P;
     x.Bx = Bx;
+    x.By = By;
     x.Nx = Nx;
     x.Ny = Ny;
     x.Nz = Nz;
+    x.plane_pair_off = (const int*)d_ppo;
+    x.pair_ay = (const int*)d_pay;
+    x.K = K;
+    x.K0 = K0;
+    x.KP = KP;
+    x.xS = (const int*)d_xS;
+    x.xD = (const int*)d_xD;
     x.Ex = Ex;
+    x.Ey = Ey;
     x.st_k = st_k + i0;
     x.st_b = st_b + i0;
     x.epsF = epsF;
     x.gm = gm;
-    x.eps2 = eps2;
-    x.f32 = f32;
+    x.epsf = epsf;
+    x.el4 = el4;
     x.UH = UH;
-    x.Zf = Zf;
-    x.omf = omf;
-    x.nBf = nBf;
+    x.ZT = ZT;
+    x.omnb = omnb;
     x.reach = (float)(omega_max + p->delta_cut_sigmas * p->sigma_eV) * 1.0001f;
     x.inv_sigma = (float)(1.0 / p->sigma_eV);
     x.cut2 = (float)(p->delta_cut_sigmas * p->delta_cut_sigmas);
     x.scale = (2.0 * kPi / (double)Nq) / (kSqrtPi * p->sigma_eV);
     x.gamma = raw;
     x.s_base = i0;
+    x.nq_evaluated = nq_eval;
     tm.begin(c);
-    const int r = dft_launch(c->stream, yz, x, S, nw, nm);
+    const int r = dft_launch(c->stream, zz, x, S, nw, nm, ne_plane_max);
     if (r != 0) {
       cudaGetLastError();
       return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the grid-DFT stage 2 failed");
@@ -1967,18 +2018,20 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
     i0 = i1;
   }
   int herr = 0;
+  unsigned long long n_x = 0;
   CK(c, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemcpyAsync(&n_x, nq_eval, sizeof(n_x), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   if (herr) return fail(c, PHOEBE_GPU_ERR_TIMEOUT, "a tensor-core pipeline wait ran out; results discarded");
-  c->stats.pairs_executed = ns * Nq;
-  // complex MACs of the DFT as evaluated: y/z sums per state, x sum per (state, q)
-  double yz_cmac = 0.0;
-  for (int a = 0; a < Bx; ++a) {
-    int groups = 0;
-    for (int e = plane_off[a]; e < plane_off[a + 1]; ++e) groups += (e == plane_off[a] || ent_ay[e] != ent_ay[e - 1]);
-    yz_cmac += (double)((Ny + 15) / 16) * ((plane_off[a + 1] - plane_off[a]) + 16.0 * groups) * Nz * E;
-  }
-  c->stats.stage2_flops = 8.0 * (double)ns * (yz_cmac + (double)Nq * Bx * E);
+  c->stats.pairs_executed = (int64_t)n_x;
+  // complex MACs of the DFT as evaluated: z sum over the entries, y sum over the pairs for every
+  // line the fused kernel covers (runs of kDftLines jy), x sum per evaluated (state, q)
+  const double ny_cov = (double)((Ny + kDftLines - 1) / kDftLines) * kDftLines;
+  const double zy_cmac = ((double)nRp * Nz + (double)P * ny_cov * Nz) * E;
+  // x sum: 4 FMA per complex value per residue pair or unpaired residue, 2 per real-factor residue
+  double x_rows = 0.0;
+  for (int k = 0; k < K; ++k) x_rows += xD[k] < 0 ? 0.5 : 1.0;
+  c->stats.stage2_flops = 8.0 * ((double)ns * zy_cmac + (double)n_x * x_rows * E);
   return PHOEBE_GPU_OK;
 }
 

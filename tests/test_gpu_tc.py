@@ -133,3 +133,30 @@ def test_grid_dft_matches_tensor_core_stage2_on_full_grid(pg, si):
         k7, b7, g7 = ctx.linewidths_rta(prm, precision=7, max_batch_states=700)   # ragged batches
     assert np.array_equal(k5, k7) and np.array_equal(b5, b7)
     assert rel_err(g7, g5) <= 2 * SPLIT_RTOL
+
+
+def test_grid_dft_unpaired_and_half_grid_residues(pg):
+    """R_p set without inversion symmetry and with R_x = +-Nx/2: the grid-DFT x sum's rows for a
+    residue without its negative, for r = 0 and for r = Nx/2 (real phase factors), against the oracle."""
+    import dataclasses
+    mat, prm = W.toy(seed=0)
+    keep = mat.Rp[:, 0] != 1                      # residue 1 (mod 8) gone, 7 keeps no partner
+    extra = np.array([[4, 0, 0], [-4, 1, 0]], dtype=np.int32)   # residue 4 = Nx / 2
+    rng = np.random.default_rng(7)
+    shape = (mat.g.shape[0], len(extra)) + mat.g.shape[2:]
+    g_extra = 0.05 * (rng.standard_normal(shape) + 1j * rng.standard_normal(shape))
+    Rp = np.concatenate([mat.Rp[keep], extra]).astype(np.int32)
+    mat2 = dataclasses.replace(mat, Rp=Rp, wp=np.ones(len(Rp)),
+                               g=np.concatenate([mat.g[:, keep], g_extra], axis=1))
+    ks = [0, 5, 17, 63, 200, 511]
+    p2 = prm.with_(k_subset=ks)
+    k_ref, b_ref, ref = elph.linewidths_rta(mat2, p2, k_indices=ks)
+    with pg.PhoebeGPU(0) as ctx:
+        ctx.set_material(mat2)
+        k7, b7, g7 = ctx.linewidths_rta(p2, precision=7)
+        k5, b5, g5 = ctx.linewidths_rta(p2, precision=5)
+    assert np.array_equal(k7, k_ref) and np.array_equal(b7, b_ref)
+    assert rel_err(g5, ref) <= SPLIT_RTOL
+    err = rel_err(g7, ref)
+    print(f"asymmetric R_p set, grid DFT: max rel err {err:.3e}")
+    assert err <= SPLIT_RTOL
