@@ -131,13 +131,84 @@ int phx::cis_table(phoebe_gpu_ctx* c, const GridPhase& gp, const char* name, cpl
 }
 
 // ------------------------------------------------------------------ band structures
+// out[e][p] = sum_R w_R e^{2 pi i k_p.R} in[R][e] on the grid n, evaluated separably over the
+// residue box of the R set (k_sep_* in bands.cu).
+static int fourier_grid_sep(phoebe_gpu_ctx* c, const cplx* in, const int* R_dev, const double* w_dev, int nR, int E,
+                            const int n[3], cplx* out) {
+  std::vector<int> R((size_t)3 * nR);
+  CK(c, cudaMemcpyAsync(R.data(), R_dev, sizeof(int) * 3 * nR, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  std::vector<int> res[3], idx((size_t)3 * nR);
+  for (int d = 0; d < 3; ++d) {
+    std::vector<int> r(nR);
+    for (int i = 0; i < nR; ++i) r[i] = ((R[3 * i + d] % n[d]) + n[d]) % n[d];
+    res[d] = r;
+    std::sort(res[d].begin(), res[d].end());
+    res[d].erase(std::unique(res[d].begin(), res[d].end()), res[d].end());
+    for (int i = 0; i < nR; ++i)
+      idx[3 * i + d] = (int)(std::lower_bound(res[d].begin(), res[d].end(), r[i]) - res[d].begin());
+  }
+  const int B0 = (int)res[0].size(), B1 = (int)res[1].size(), B2 = (int)res[2].size();
+  std::vector<int> order(nR);
+  for (int i = 0; i < nR; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    for (int d = 0; d < 3; ++d)
+      if (idx[3 * a + d] != idx[3 * b + d]) return idx[3 * a + d] < idx[3 * b + d];
+    return a < b;
+  });
+  std::vector<int> plane_off(B0 + 1, 0), pair_off, pair_b, ent_c(nR), ent_r(nR);
+  for (int e = 0; e < nR; ++e) {
+    const int r = order[e];
+    ent_c[e] = idx[3 * r + 2];
+    ent_r[e] = r;
+    if (e == 0 || idx[3 * r] != idx[3 * order[e - 1]] || idx[3 * r + 1] != idx[3 * order[e - 1] + 1]) {
+      pair_off.push_back(e);
+      pair_b.push_back(idx[3 * r + 1]);
+    }
+    plane_off[idx[3 * r] + 1] = (int)pair_off.size();
+  }
+  const int npair = (int)pair_b.size();
+  pair_off.push_back(nR);
+  for (int a = 1; a <= B0; ++a) plane_off[a] = std::max(plane_off[a], plane_off[a - 1]);
+  int st;
+  void *d_res0, *d_res1, *d_res2, *d_po, *d_pb, *d_plo, *d_ec, *d_er;
+  TRY(upload(c, "sep_res0", res[0].data(), sizeof(int) * B0, &d_res0));
+  TRY(upload(c, "sep_res1", res[1].data(), sizeof(int) * B1, &d_res1));
+  TRY(upload(c, "sep_res2", res[2].data(), sizeof(int) * B2, &d_res2));
+  TRY(upload(c, "sep_pair_off", pair_off.data(), sizeof(int) * (npair + 1), &d_po));
+  TRY(upload(c, "sep_pair_b", pair_b.data(), sizeof(int) * npair, &d_pb));
+  TRY(upload(c, "sep_plane_off", plane_off.data(), sizeof(int) * (B0 + 1), &d_plo));
+  TRY(upload(c, "sep_ent_c", ent_c.data(), sizeof(int) * nR, &d_ec));
+  TRY(upload(c, "sep_ent_r", ent_r.data(), sizeof(int) * nR, &d_er));
+  cplx* E0 = (cplx*)ensure(c, "sep_E0", sizeof(cplx) * n[0] * B0, &st);
+  if (!E0) return st;
+  cplx* E1 = (cplx*)ensure(c, "sep_E1", sizeof(cplx) * n[1] * B1, &st);
+  if (!E1) return st;
+  cplx* E2 = (cplx*)ensure(c, "sep_E2", sizeof(cplx) * n[2] * B2, &st);
+  if (!E2) return st;
+  const int64_t nz = (int64_t)npair * E * n[2], ny = (int64_t)B0 * E * n[1] * n[2];
+  const int64_t nx = (int64_t)E * n[0] * n[1] * n[2];
+  cplx* Zs = (cplx*)ensure(c, "sep_Zs", sizeof(cplx) * nz, &st);
+  if (!Zs) return st;
+  cplx* Y = (cplx*)ensure(c, "sep_Y", sizeof(cplx) * ny, &st);
+  if (!Y) return st;
+  k_sep_table<<<(n[0] * B0 + 127) / 128, 128, 0, c->stream>>>((const int*)d_res0, B0, n[0], E0);
+  k_sep_table<<<(n[1] * B1 + 127) / 128, 128, 0, c->stream>>>((const int*)d_res1, B1, n[1], E1);
+  k_sep_table<<<(n[2] * B2 + 127) / 128, 128, 0, c->stream>>>((const int*)d_res2, B2, n[2], E2);
+  k_sep_z<<<(unsigned)((nz + 255) / 256), 256, 0, c->stream>>>(in, w_dev, E, npair, (const int*)d_po,
+                                                                (const int*)d_ec, (const int*)d_er, E2, n[2], B2, Zs);
+  k_sep_y<<<(unsigned)((ny + 255) / 256), 256, 0, c->stream>>>(Zs, E, B0, (const int*)d_plo, (const int*)d_pb, E1,
+                                                                n[1], B1, n[2], Y);
+  k_sep_x<<<(unsigned)((nx + 255) / 256), 256, 0, c->stream>>>(Y, E, B0, E0, n[0], n[1], n[2], out);
+  c->launches += 6;
+  CK(c, cudaGetLastError());
+  return PHOEBE_GPU_OK;
+}
+
 // eps[P][nw], U[P][nw][nw] (columns = eigenvectors) on the grid n.
 int phx::electron_grid(phoebe_gpu_ctx* c, const int n[3], double** eps, cplx** U) {
-  GridPhase gp = make_phase(n);
   int64_t P = (int64_t)n[0] * n[1] * n[2];
   int nw = c->nw, E = nw * nw, st;
-  cplx* cis;
-  if ((st = cis_table(c, gp, "cis_el", &cis))) return st;
   cplx* A = (cplx*)ensure(c, "jac_A", sizeof(cplx) * P * E, &st);
   if (!A) return st;
   cplx* V = (cplx*)ensure(c, "jac_V", sizeof(cplx) * P * E, &st);
@@ -149,11 +220,10 @@ int phx::electron_grid(phoebe_gpu_ctx* c, const int n[3], double** eps, cplx** U
   int* status = (int*)ensure(c, "status", 64, &st);
   if (!status) return st;
   CK(c, cudaMemsetAsync(status, 0, 64, c->stream));
-  dim3 g((unsigned)((P + 127) / 128), (unsigned)E);
-  k_fourier_grid_c<<<g, 128, 0, c->stream>>>((const cplx*)c->bufs["H"].p, (const int*)c->bufs["RH"].p,
-                                               (const double*)c->bufs["wH"].p, c->nRH, E, gp, cis, P, A);
+  TRY(fourier_grid_sep(c, (const cplx*)c->bufs["H"].p, (const int*)c->bufs["RH"].p,
+                       (const double*)c->bufs["wH"].p, c->nRH, E, n, A));
   k_jacobi_herm<<<(unsigned)((P + 127) / 128), 128, 0, c->stream>>>(A, V, nw, P, kJacobiSweeps, e, u, status);
-  c->launches += 2;
+  c->launches += 1;
   CK(c, cudaGetLastError());
   int hs = 0;
   CK(c, cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));

@@ -19,25 +19,72 @@ __global__ void k_cis_table(cplx* cis, int L) {
   cis[r] = {c, s};
 }
 
-// Grid Fourier sum, complex input: out[e][p] = sum_R w_R e^{2 pi i k_p.R} in[R][e]
-// (SoA output).  One thread per (point p, entry e = blockIdx.y).
-__global__ void k_fourier_grid_c(const cplx* __restrict__ in, const int* __restrict__ R,
-                                 const double* __restrict__ w, int nR, int E, GridPhase gp,
-                                 const cplx* __restrict__ cis, int64_t P, cplx* __restrict__ out) {
-  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int e = blockIdx.y;
-  if (p >= P) return;
-  int j[3];
-  grid_coords(p, gp.n, j);
+// Grid Fourier sum, complex input: out[e][p] = sum_R w_R e^{2 pi i k_p.R} in[R][e] (SoA output),
+// evaluated separably over the residue box of R (FP64): on a grid k = (j0/N0, j1/N1, j2/N2) the
+// phase factorises per axis, e^{2 pi i k.R} = prod_d e^{2 pi i j_d r_d/N_d}
+// with r_d = R_d mod N_d, so out[e][p] = sum_a E0[j0][a] sum_b E1[j1][b] sum_c E2[j2][c] w_R in[R][e]
+// over the R of residues (a, b, c).  Three passes: over c for every (a, b) pair present, over b
+// into Y[a][e][j1][j2], over a into out.  Equal to the direct sum over R up to rounding.
+
+// e^{2 pi i j r / N} for the residue list res[0..B): E[j][a] (exact integer argument reduction).
+__global__ void k_sep_table(const int* __restrict__ res, int B, int N, cplx* __restrict__ E) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * B) return;
+  const int j = t / B, a = t % B;
+  const int r = (int)(((int64_t)j * res[a]) % N);
+  double sv, cv;
+  sincospi(2.0 * (double)r / (double)N, &sv, &cv);
+  E[t] = {cv, sv};
+}
+
+// Zs[pair][e][j2] = sum over the entries of the pair of E2[j2][c] w_R in[R][e]; thread (pair, e, j2).
+__global__ void k_sep_z(const cplx* __restrict__ in, const double* __restrict__ w, int E, int npair,
+                        const int* __restrict__ pair_off, const int* __restrict__ ent_c, const int* __restrict__ ent_r,
+                        const cplx* __restrict__ E2, int N2, int B2, cplx* __restrict__ Zs) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)npair * E * N2) return;
+  const int j2 = (int)(t % N2);
+  const int e = (int)((t / N2) % E);
+  const int pr = (int)(t / ((int64_t)N2 * E));
   cplx acc = {0.0, 0.0};
-  for (int r = 0; r < nR; ++r) {
-    int Rv[3] = {__ldg(R + 3 * r), __ldg(R + 3 * r + 1), __ldg(R + 3 * r + 2)};
-    cplx ph = ldc(cis + phase_index(j, Rv, gp.mult, gp.L));
-    cplx h = ldc(in + (int64_t)r * E + e);
-    double wr = __ldg(w + r);
-    cfma(acc, {ph.re * wr, ph.im * wr}, h);
+  for (int i = pair_off[pr]; i < pair_off[pr + 1]; ++i) {
+    const int r = ent_r[i];
+    const cplx h = ldc(in + (int64_t)r * E + e);
+    const double wr = w[r];
+    cfma(acc, ldc(E2 + (int64_t)j2 * B2 + ent_c[i]), {h.re * wr, h.im * wr});
   }
-  out[(int64_t)e * P + p] = acc;
+  Zs[t] = acc;
+}
+
+// Y[a][e][j1][j2] = sum over the pairs (a, b) of E1[j1][b] Zs[pair][e][j2]; thread (a, e, j1, j2).
+__global__ void k_sep_y(const cplx* __restrict__ Zs, int E, int B0, const int* __restrict__ plane_off,
+                        const int* __restrict__ pair_b, const cplx* __restrict__ E1, int N1, int B1, int N2,
+                        cplx* __restrict__ Y) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)B0 * E * N1 * N2) return;
+  const int j2 = (int)(t % N2);
+  const int j1 = (int)((t / N2) % N1);
+  const int e = (int)((t / ((int64_t)N2 * N1)) % E);
+  const int a = (int)(t / ((int64_t)N2 * N1 * E));
+  cplx acc = {0.0, 0.0};
+  for (int pr = plane_off[a]; pr < plane_off[a + 1]; ++pr)
+    cfma(acc, ldc(E1 + (int64_t)j1 * B1 + pair_b[pr]), ldc(Zs + ((int64_t)pr * E + e) * N2 + j2));
+  Y[t] = acc;
+}
+
+// out[e][p] = sum_a E0[j0][a] Y[a][e][j1][j2], p = (j0 * N1 + j1) * N2 + j2; thread (e, p).
+__global__ void k_sep_x(const cplx* __restrict__ Y, int E, int B0, const cplx* __restrict__ E0, int N0, int N1,
+                        int N2, cplx* __restrict__ out) {
+  const int64_t P = (int64_t)N0 * N1 * N2;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)E * P) return;
+  const int64_t p = t % P;
+  const int e = (int)(t / P);
+  const int j0 = (int)(p / ((int64_t)N1 * N2));
+  const int64_t l = p % ((int64_t)N1 * N2);
+  cplx acc = {0.0, 0.0};
+  for (int a = 0; a < B0; ++a) cfma(acc, ldc(E0 + (int64_t)j0 * B0 + a), ldc(Y + ((int64_t)a * E + e) * N1 * N2 + l));
+  out[t] = acc;
 }
 
 // Point-list Fourier sum (off-grid k): phases from sincospi(2 frac(k.R)).

@@ -3,7 +3,7 @@
 // e^{2 pi i q.R} = e^{2 pi i jx rx/Nx} e^{2 pi i jy ry/Ny} e^{2 pi i jz rz/Nz} with r = R mod N,
 // so for every state
 //   G(q)[c] = sum_rx Ex[jx][rx] sum_ry Ey[jy][ry] sum_rz Ez[jz][rz] w_R T[R][c],
-// T the stage-1 output.  k_dft_z sums over rz for every (rx, ry) pair present in the R_p set
+// T the stage-1 output rotated to the initial band.  k_dft_z forms T and sums over rz for every (rx, ry) pair present in the R_p set
 // (Zs[jz][pair][c], in HBM); k_dft_yx_elph then, for one jz and a run of jy, sums over ry into
 // shared memory, finishes the x sum for the q whose final bands can reach the delta window and
 // applies U_{k+q}^dagger, Z_q and the delta weights of Eq. 29 (Sec. 4.7 Eq. 61) like the fused
@@ -15,25 +15,39 @@
 namespace phx {
 
 // Sum over rz: one block per (rx plane, state); work unit = (pair of the plane, 4 jz, column
-// vector).  The plane's weighted T rows and the Ez table are staged in shared memory.
+// vector).  The plane's T rows, T[R][sa][m] = w_R sum_n X[R][m][n][sa] U_k[n][b] (the rotation to the
+// initial band, Eq. 71), are formed in shared memory from the stage-1 rows, read in their memory
+// order; the Ez table is staged beside them.
 __global__ void __launch_bounds__(256) k_dft_z(DftZArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ float2 us[16];
   const int rx = blockIdx.x, s = blockIdx.y;
   const int p0 = a.plane_pair_off[rx], p1 = a.plane_pair_off[rx + 1];
   const int e0 = a.pair_ent_off[p0], ne = a.pair_ent_off[p1] - e0;
-  const int E = a.E;
+  const int E = a.E, nw = a.nw, nm = E / nw;
   float2* Ts = reinterpret_cast<float2*>(smem);            // [ne][E]
   float2* Ezs = Ts + (size_t)ne * E;                       // [Nz][Bz]
   int* azs = reinterpret_cast<int*>(Ezs + (size_t)a.Nz * a.Bz);  // [ne]
-  const float2* T = a.T + (int64_t)s * a.nR * E;
-  for (int i = threadIdx.x; i < ne * E; i += blockDim.x) {
-    const int e = i / E, cc = i % E;
+  if (threadIdx.x < nw) {
+    const cplx u = a.UF[(a.gm.k_to_fine(a.st_k[s]) * nw + threadIdx.x) * nw + a.st_b[s]];
+    us[threadIdx.x] = make_float2((float)u.re, (float)u.im);
+  }
+  __syncthreads();
+  const float2* X = reinterpret_cast<const float2*>(a.X + (int64_t)a.st_kb[s] * a.ldx);
+  for (int i = threadIdx.x; i < ne * E; i += blockDim.x) {  // i = (e, m, sa), sa fastest
+    const int e = i / E, rem = i % E;
+    const int m = rem / nm, sa = rem % nm;
     const int r = a.ent_r[e0 + e];
-    float2 t = T[(int64_t)r * E + cc];
-    const float w = a.w[r];
-    t.x *= w;
-    t.y *= w;
-    Ts[i] = t;
+    const float2* x = X + ((int64_t)r * nw + m) * nw * nm + sa;
+    float re = 0.f, im = 0.f;
+    for (int n = 0; n < nw; ++n) {
+      const float2 v = __ldg(x + n * nm);
+      const float2 u = us[n];
+      re = fmaf(v.x, u.x, fmaf(-v.y, u.y, re));
+      im = fmaf(v.x, u.y, fmaf(v.y, u.x, im));
+    }
+    const float sc = a.w[r] * a.unscale;
+    Ts[e * E + sa * nw + m] = make_float2(re * sc, im * sc);
   }
   for (int i = threadIdx.x; i < a.Nz * a.Bz; i += blockDim.x) Ezs[i] = a.Ez[i];
   for (int i = threadIdx.x; i < ne; i += blockDim.x) azs[i] = a.ent_az[e0 + i];

@@ -23,7 +23,17 @@ static_assert(kDftLines % kDftUnitLines == 0, "lines per block must be a multipl
 // The R_p set grouped by residues r = R mod N: entries sorted by (rx, ry, rz) residue index,
 // "pairs" = distinct (rx, ry), "planes" = distinct rx.
 struct DftZArgs {
-  const float2* T;           // [S][nR][E] stage-1 output (E = 3na * nw, column c = sa*nw + m)
+  // stage-1 GEMM output: row st_kb[s] holds sum_Re w e^{ik.Re} g(Re, Rp)[m][n][sa] (re, im) at
+  // column 2 * (((Rp * nw + m) * nw + n) * nm + sa), scaled by 1 / unscale
+  const float* X;
+  int64_t ldx;
+  float unscale;
+  const int* st_kb;          // [S] row of X of each state
+  const int* st_k;           // [S] k (coarse grid) of each state
+  const int* st_b;           // [S] band of each state
+  GridMap gm;
+  const cplx* UF;            // [NF][nw][nw] eigenvectors U_k[n][b]
+  int nw;
   const float* w;            // [nR] R_p weights
   int nR, E, P, Nz, Bz;
   const int* plane_pair_off;  // [Bx+1] first pair of each plane

@@ -34,8 +34,12 @@ struct GridMap {
 
 // ---------------------------------------------------------------- bands.cu
 __global__ void k_cis_table(cplx* cis, int L);
-__global__ void k_fourier_grid_c(const cplx* in, const int* R, const double* w, int nR, int E, GridPhase gp,
-                                 const cplx* cis, int64_t P, cplx* out);
+__global__ void k_sep_table(const int* res, int B, int N, cplx* E);
+__global__ void k_sep_z(const cplx* in, const double* w, int E, int npair, const int* pair_off, const int* ent_c,
+                        const int* ent_r, const cplx* E2, int N2, int B2, cplx* Zs);
+__global__ void k_sep_y(const cplx* Zs, int E, int B0, const int* plane_off, const int* pair_b, const cplx* E1,
+                        int N1, int B1, int N2, cplx* Y);
+__global__ void k_sep_x(const cplx* Y, int E, int B0, const cplx* E0, int N0, int N1, int N2, cplx* out);
 __global__ void k_fourier_points_c(const cplx* in, const int* R, const double* w, int nR, int E,
                                    const double* kpts, int64_t P, cplx* out);
 __global__ void k_dynmat_grid(const double* Phi, const int* R, const double* w, int nR, int nm,

@@ -1087,12 +1087,14 @@ static int64_t next_batch(const std::vector<int>& hk, int64_t ns, int64_t i0, in
 
 // Stage 1 of one batch of whole k points on the tensor cores (Sec. 5.5 Eq. 71):
 // X[kb] = sum_Re w e^{ik.Re} g(Re, .) by a GEMM, then T[s][Rp][sa][m] = sum_n X[kb(s)] U_k[n][b(s)]
-// (FP32, physical scale) with the batch's max |T| in *tmaxp.
+// (FP32, physical scale) with the batch's max |T| in *tmaxp.  With Tb_out == nullptr the rotation
+// is left to the caller: *X_out, *ldx_out receive the GEMM output (scaled by 1 / unscale).
 template <int FMT, int NSPLIT, int NPROD>
 static int stage1_batch(phoebe_gpu_ctx* c, const GridMap& gm, const std::vector<int>& kb_list,
                         const std::vector<int>& st_kb, int64_t i0, const int* st_k, const int* st_b, const cplx* UF,
                         const Parts& Pg, float sA1, const cplx* cis_k, const GridPhase& gk, int* err, unsigned* tmaxp,
-                        const int* d_kb, const int* d_stkb, float2** Tb_out) {
+                        const int* d_kb, const int* d_stkb, float2** Tb_out, const float** X_out = nullptr,
+                        int64_t* ldx_out = nullptr) {
   const int nw = c->nw, nm = 3 * c->na, nRe = c->nRe, nRp = c->nRp;
   const int esz = FMT == 2 ? 4 : 2;
   const int KB = 128 / esz;
@@ -1130,6 +1132,11 @@ static int stage1_batch(phoebe_gpu_ctx* c, const GridMap& gm, const std::vector<
     a.err = err;
     StoreEpi::Params ep{X, ldx, nkb, (int)(2 * C)};
     TRY(launch_gemm<StoreEpi, FMT, NSPLIT, NPROD>(c, tAk, tG, a, ep));
+  }
+  if (!Tb_out) {
+    *X_out = X;
+    *ldx_out = ldx;
+    return PHOEBE_GPU_OK;
   }
   float2* Tb = (float2*)ensure(c, "tc_T", sizeof(float2) * (size_t)S * nRp * nm * nw, &st);
   if (!Tb) return st;
@@ -1953,14 +1960,23 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
     TRY(upload(c, "tc_batch_k", kb_list.data(), sizeof(int) * nkb, &d_kb));
     TRY(upload(c, "tc_batch_stkb", st_kb.data(), sizeof(int) * S, &d_stkb));
     tm.begin(c);
-    float2* Tb;
+    const float* X1;
+    int64_t ldx1;
     TRY((stage1_batch<FMT, NSPLIT, NPROD>(c, gm, kb_list, st_kb, i0, st_k, st_b, UF, Pg, sA1, cis_k, gk, err, tmaxp,
-                                          (const int*)d_kb, (const int*)d_stkb, &Tb)));
+                                          (const int*)d_kb, (const int*)d_stkb, nullptr, &X1, &ldx1)));
     tm.end(c, &c->stats.stage1_ms);
     float2* Zs = (float2*)ensure(c, "dft_Zs", (size_t)per_state * S, &st);
     if (!Zs) return st;
     DftZArgs zz;
-    zz.T = Tb;
+    zz.X = X1;
+    zz.ldx = ldx1;
+    zz.unscale = 1.0f / (sA1 * c->tc->g_scale);
+    zz.st_kb = (const int*)d_stkb;
+    zz.st_k = st_k + i0;
+    zz.st_b = st_b + i0;
+    zz.gm = gm;
+    zz.UF = UF;
+    zz.nw = nw;
     zz.w = (const float*)d_w;
     zz.nR = nRp;
     zz.E = E;
