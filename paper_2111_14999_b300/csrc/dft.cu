@@ -171,43 +171,132 @@ __device__ __forceinline__ void load_cplx(const float2* __restrict__ p, float2 (
 // complex values of a row), even whenever E is (16-byte loads stay aligned).
 __host__ __device__ constexpr int dft_row_stride(int E, int NW) { return E + ((NW - E) % 16 + 16) % 16; }
 
-// One block per (jz, run of kDftLines jy, state), kDftXThreads threads.
-// Loads: the state's Zs[jz] slice (every (rx, ry) pair) by cp.async, the phase tables.
-// Phase 0 (while the slice arrives): every q = (jx, jy, jz) of the block tests which final bands m'
-// at k+q lie within the Gaussian's reach of eps_nk; the q with at least one such band are listed
-// (warp ballots, in (line, jx) order).  Phase Y: Y[rx][line][c] = sum_ry Ey[jy][ry] Zs[(rx,ry)][c]
-// into shared memory; unit = (rx, kDftUnitLines lines, column vector).  Phase X: SPLIT consecutive
-// lanes take one listed q: lane j sums over rx the elements c = sa*NW + m of its m range, then the
-// group applies U_{k+q}^dagger (partial sums over m, combined by shuffles), Z_q and the delta
-// weights for each listed m'.  q whose bands all miss the window contribute nothing to Eq. 29 and
-// are not evaluated.
+// x sum of one q over the rows of one line: real-factor rows, residue pairs (cos S + i sin D),
+// residues without a partner (e^{i t r} Y).  Lane j of the group owns elements c = sa*NW + j*MW + mm.
+template <int NW, int NM, int MW, int ES, int L>
+__device__ __forceinline__ void dft_x_line(const float2* __restrict__ Ys, const float2* __restrict__ Exs,
+                                           const int* __restrict__ xS, const int* __restrict__ xD, int K, int K0,
+                                           int KP, int jx, int l, int j, float2 (&G)[NM][MW]) {
+#pragma unroll
+  for (int sa = 0; sa < NM; ++sa)
+#pragma unroll
+    for (int mm = 0; mm < MW; ++mm) G[sa][mm] = make_float2(0.f, 0.f);
+  for (int k = 0; k < K0; ++k) {
+    const float c = Exs[jx * K + k].x;
+    const float2* ys = Ys + (xS[k] * L + l) * ES + j * MW;
+#pragma unroll
+    for (int sa = 0; sa < NM; ++sa) {
+      if constexpr (MW % 2 == 0) {
+#pragma unroll
+        for (int mm = 0; mm < MW; mm += 2) {
+          const float4 v = *reinterpret_cast<const float4*>(ys + sa * NW + mm);
+          G[sa][mm].x = fmaf(c, v.x, G[sa][mm].x);
+          G[sa][mm].y = fmaf(c, v.y, G[sa][mm].y);
+          G[sa][mm + 1].x = fmaf(c, v.z, G[sa][mm + 1].x);
+          G[sa][mm + 1].y = fmaf(c, v.w, G[sa][mm + 1].y);
+        }
+      } else {
+#pragma unroll
+        for (int mm = 0; mm < MW; ++mm) {
+          const float2 v = ys[sa * NW + mm];
+          G[sa][mm].x = fmaf(c, v.x, G[sa][mm].x);
+          G[sa][mm].y = fmaf(c, v.y, G[sa][mm].y);
+        }
+      }
+    }
+  }
+#pragma unroll 2
+  for (int k = K0; k < K0 + KP; ++k) {
+    const float2 cs = Exs[jx * K + k];
+    const float2* ys = Ys + (xS[k] * L + l) * ES + j * MW;
+    const float2* yd = Ys + (xD[k] * L + l) * ES + j * MW;
+#pragma unroll
+    for (int sa = 0; sa < NM; ++sa) {
+      if constexpr (MW % 2 == 0) {
+#pragma unroll
+        for (int mm = 0; mm < MW; mm += 2) {
+          const float4 v = *reinterpret_cast<const float4*>(ys + sa * NW + mm);
+          const float4 d = *reinterpret_cast<const float4*>(yd + sa * NW + mm);
+          G[sa][mm].x = fmaf(cs.x, v.x, fmaf(-cs.y, d.y, G[sa][mm].x));
+          G[sa][mm].y = fmaf(cs.x, v.y, fmaf(cs.y, d.x, G[sa][mm].y));
+          G[sa][mm + 1].x = fmaf(cs.x, v.z, fmaf(-cs.y, d.w, G[sa][mm + 1].x));
+          G[sa][mm + 1].y = fmaf(cs.x, v.w, fmaf(cs.y, d.z, G[sa][mm + 1].y));
+        }
+      } else {
+#pragma unroll
+        for (int mm = 0; mm < MW; ++mm) {
+          const float2 v = ys[sa * NW + mm], d = yd[sa * NW + mm];
+          G[sa][mm].x = fmaf(cs.x, v.x, fmaf(-cs.y, d.y, G[sa][mm].x));
+          G[sa][mm].y = fmaf(cs.x, v.y, fmaf(cs.y, d.x, G[sa][mm].y));
+        }
+      }
+    }
+  }
+  for (int k = K0 + KP; k < K; ++k) {
+    const float2 ex = Exs[jx * K + k];
+    const float2* y = Ys + (xS[k] * L + l) * ES + j * MW;
+#pragma unroll
+    for (int sa = 0; sa < NM; ++sa) {
+      if constexpr (MW % 2 == 0) {
+#pragma unroll
+        for (int mm = 0; mm < MW; mm += 2) {
+          const float4 v = *reinterpret_cast<const float4*>(y + sa * NW + mm);
+          G[sa][mm].x = fmaf(ex.x, v.x, fmaf(-ex.y, v.y, G[sa][mm].x));
+          G[sa][mm].y = fmaf(ex.x, v.y, fmaf(ex.y, v.x, G[sa][mm].y));
+          G[sa][mm + 1].x = fmaf(ex.x, v.z, fmaf(-ex.y, v.w, G[sa][mm + 1].x));
+          G[sa][mm + 1].y = fmaf(ex.x, v.w, fmaf(ex.y, v.z, G[sa][mm + 1].y));
+        }
+      } else {
+#pragma unroll
+        for (int mm = 0; mm < MW; ++mm) {
+          const float2 v = y[sa * NW + mm];
+          G[sa][mm].x = fmaf(ex.x, v.x, fmaf(-ex.y, v.y, G[sa][mm].x));
+          G[sa][mm].y = fmaf(ex.x, v.y, fmaf(ex.y, v.x, G[sa][mm].y));
+        }
+      }
+    }
+  }
+}
+
+// One block per (jz, state), kDftXThreads threads; the block walks the jy lines in runs of
+// kDftLines.  Loaded once: the state's Zs[jz] slice (every (rx, ry) pair) by cp.async, the phase
+// tables.  Per run: phase 0 (in the previous run's last phase) lists the q = (jx, jy, jz) of the
+// run whose final bands m' at k+q can reach the delta window around eps_nk (warp ballots, in
+// (line, jx) order, two lists used alternately); phase Y forms Y[rx][line][c] =
+// sum_ry Ey[jy][ry] Zs[(rx,ry)][c] in shared memory (unit = (rx, kDftUnitLines lines, column
+// vector)) and turns the rows of residue pairs into S and D; phase X: SPLIT consecutive lanes
+// take one listed q, sum over the rows (dft_x_line), apply U_{k+q}^dagger (partial sums over m
+// combined by shuffles), Z_q and the delta weights of every listed m'.  q whose bands all miss
+// the window contribute nothing to Eq. 29 and are not evaluated.
 template <int NW, int NM, int SPLIT>
-__global__ void __launch_bounds__(kDftXThreads) k_dft_yx_elph(DftXArgs a) {
+__global__ void __launch_bounds__(kDftXThreads, PHX_DFT_MINB) k_dft_yx_elph(DftXArgs a) {
   constexpr int E = NW * NM, MW = NW / SPLIT, ES = dft_row_stride(E, NW);
   constexpr int L = kDftLines, UL = kDftUnitLines;
-  constexpr int SLOT = dft_slot(NW, NM);
-  constexpr bool A16 = NW % 2 == 0 && NM % 2 == 0;  // every prefetched segment 16-byte aligned
   static_assert(NW % SPLIT == 0 && 32 % SPLIT == 0 && NW <= 16, "lane split must divide NW and the warp");
   static_assert(SPLIT == dft_split(NW), "lane split must match the host's shared-memory sizing");
   extern __shared__ __align__(16) unsigned char smem[];
   const int P = a.P;
-  const int zsl_len = max(P * E, (kDftXThreads / SPLIT) * SLOT);
-  float2* Zsl = reinterpret_cast<float2*>(smem);          // [P][E]; after phase Y the groups' prefetch slots
-  float2* Ys = Zsl + (size_t)zsl_len;                     // [Bx][L][ES]
+  float2* Zsl = reinterpret_cast<float2*>(smem);          // [P][E]
+  float2* Ys = Zsl + (size_t)P * E + (P * E) % 2;         // [Bx][L][ES]
   float2* Exs = Ys + (size_t)a.Bx * L * ES;               // [Nx][K]
-  float2* Eys = Exs + (size_t)a.Nx * a.K;                 // [L][By]
-  int* ppo = reinterpret_cast<int*>(Eys + (size_t)L * a.By);  // [Bx+1]
+  float2* Eys = Exs + (size_t)a.Nx * a.K;                 // [2][L][By] Ey rows of a run, used alternately
+  int* ppo = reinterpret_cast<int*>(Eys + (size_t)2 * L * a.By);  // [Bx+1]
   int* xS = ppo + a.Bx + 1;                               // [K]
   int* xD = xS + a.K;                                     // [K]
   int* pay = xD + a.K;                                    // [P]
-  int* list = pay + P;                                    // [L * Nx]
-  __shared__ int cnt;
+  int* lists = pay + P;                                   // [2][L * Nx]
+  __shared__ int cnt[2];
+  __shared__ float en_s[2];
   __shared__ double red[kDftXThreads / 32];
-  const int s = blockIdx.y;
-  const int nch = (a.Ny + L - 1) / L;
-  const int jz = blockIdx.x / nch, jy0 = (blockIdx.x % nch) * L;
-  const int nl = min(L, a.Ny - jy0);
-  if (threadIdx.x == 0) cnt = 0;
+  const int s = blockIdx.y, jz = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    cnt[0] = 0;
+    cnt[1] = 0;
+    const double e_n = a.epsF[a.gm.k_to_fine(a.st_k[s]) * NW + a.st_b[s]];
+    en_s[0] = (float)e_n;
+    en_s[1] = (float)(e_n - (double)en_s[0]);
+  }
   {  // the Zs[jz] slice of this state: P * E contiguous complex values
     const float2* zg = a.Zs + ((int64_t)s * a.Nz + jz) * P * E;
     if ((P * E) % 2 == 0) {
@@ -221,323 +310,227 @@ __global__ void __launch_bounds__(kDftXThreads) k_dft_yx_elph(DftXArgs a) {
     xS[i] = a.xS[i];
     xD[i] = a.xD[i];
   }
-  for (int i = threadIdx.x; i < L * a.By; i += blockDim.x) {
-    const int l = i / a.By;
-    Eys[i] = l < nl ? a.Ey[(jy0 + l) * a.By + i % a.By] : make_float2(0.f, 0.f);
-  }
   for (int i = threadIdx.x; i <= a.Bx; i += blockDim.x) ppo[i] = a.plane_pair_off[i];
   for (int i = threadIdx.x; i < P; i += blockDim.x) pay[i] = a.pair_ay[i];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t kf = a.gm.k_to_fine(a.st_k[s]);
-  const double e_n = a.epsF[kf * NW + a.st_b[s]];
-  const float en_hi = (float)e_n, en_lo = (float)(e_n - (double)en_hi);
   int kc[3];
-  grid_coords(kf, a.gm.nf, kc);
-  __syncthreads();  // cnt initialised
+  grid_coords(a.gm.k_to_fine(a.st_k[s]), a.gm.nf, kc);
   // fine-grid coordinates of k+q: k_d + j_d * s_d with k_d < nf_d and j_d * s_d < nf_d, so one
   // conditional subtraction reduces them modulo nf_d
   const int sx = a.gm.sq[0], sy = a.gm.sq[1];
   const int nfx = a.gm.nf[0], nfy = a.gm.nf[1], nfz = a.gm.nf[2];
   int fz = kc[2] + jz * a.gm.sq[2];
   fz -= fz >= nfz ? nfz : 0;
-  const float en_f = en_hi;
-  // phase 0: list the q of the block that can reach the delta window (two q per thread and round,
-  // their energy rows loaded before either is tested)
-  const int nq_blk = nl * a.Nx;
-  for (int q0 = 0; q0 < nq_blk; q0 += 2 * blockDim.x) {
-    float ev[2][NW];
-    int qis[2];
+  const float inv_nx = 1.f / (float)a.Nx;  // qi < 2^16, Nx <= 256: (qi + 0.5) / Nx truncates exactly
+  __syncthreads();  // counters and en_s
+  const float en_hi = en_s[0], en_lo = en_s[1];
+  // phase 0 for the run starting at jy0, into list b: two q per thread and round, their energy
+  // rows loaded before either is tested
+  auto phase0 = [&](int jy0, int b) {
+    const int nq_blk = min(L, a.Ny - jy0) * a.Nx;
+    int* list = lists + b * L * a.Nx;
+    for (int i = threadIdx.x; i < L * a.By; i += blockDim.x) {  // Ey rows of the run (0 past the grid edge)
+      const int jy = jy0 + i / a.By;
+      Eys[b * L * a.By + i] = jy < a.Ny ? a.Ey[jy * a.By + i % a.By] : make_float2(0.f, 0.f);
+    }
+    for (int q0 = 0; q0 < nq_blk; q0 += 2 * blockDim.x) {
+      float ev[2][NW];
+      int qis[2];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int qi = q0 + u * blockDim.x + threadIdx.x;
-      qis[u] = qi;
-      if (qi < nq_blk) {
-        const int l = qi / a.Nx, jx = qi - l * a.Nx;
-        int fx = kc[0] + jx * sx, fy = kc[1] + (jy0 + l) * sy;
-        fx -= fx >= nfx ? nfx : 0;
-        fy -= fy >= nfy ? nfy : 0;
-        load_row<NW>(a.epsf + ((int64_t)(fx * nfy + fy) * nfz + fz) * NW, ev[u]);
+      for (int u = 0; u < 2; ++u) {
+        const int qi = q0 + u * blockDim.x + threadIdx.x;
+        const int l = (int)(((float)qi + 0.5f) * inv_nx);
+        const int jx = qi - l * a.Nx;
+        qis[u] = (l << 8) | jx;  // (line, jx)
+        if (qi < nq_blk) {
+          int fx = kc[0] + jx * sx, fy = kc[1] + (jy0 + l) * sy;
+          fx -= fx >= nfx ? nfx : 0;
+          fy -= fy >= nfy ? nfy : 0;
+          load_row<NW>(a.epsf + ((int64_t)(fx * nfy + fy) * nfz + fz) * NW, ev[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        unsigned need = 0;
+        if (q0 + u * (int)blockDim.x + (int)threadIdx.x < nq_blk) {
+#pragma unroll
+          for (int mp = 0; mp < NW; ++mp)
+            if (fabsf(en_hi - ev[u][mp]) < a.reach) need |= 1u << mp;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, need != 0);
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&cnt[b], __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (need) list[base + __popc(bal & ((1u << lane) - 1))] = (int)(need << 16) | qis[u];
       }
     }
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      unsigned need = 0;
-      if (qis[u] < nq_blk) {
-#pragma unroll
-        for (int mp = 0; mp < NW; ++mp)
-          if (fabsf(en_f - ev[u][mp]) < a.reach) need |= 1u << mp;
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, need != 0);
-      int base = 0;
-      if (lane == 0 && bal) base = atomicAdd(&cnt, __popc(bal));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (need) list[base + __popc(bal & ((1u << lane) - 1))] = (int)(need << 16) | qis[u];
-    }
-  }
+  };
+  phase0(0, 0);
   cp_async_wait_all();
-  __syncthreads();
-  // phase Y: sum over ry of the slice into Y rows (lines past the grid edge get Ey = 0)
-  if constexpr (E % 2 == 0) {
-    constexpr int EV = E / 2;
-    const int units = a.Bx * (L / UL) * EV;
-    for (int u = threadIdx.x; u < units; u += blockDim.x) {
-      const int cv = u % EV, rest = u / EV;
-      const int lh = rest % (L / UL), rx = rest / (L / UL);
-      float4 acc[UL];
+  const int j = threadIdx.x % SPLIT;
+  const unsigned gmask = (SPLIT == 32 ? 0xffffffffu : ((1u << SPLIT) - 1)) << (lane & ~(SPLIT - 1));
+  float acc = 0.f;  // every term of Eq. 29 is non-negative: FP32 partial sums lose nothing to cancellation
+  for (int jy0 = 0, run = 0; jy0 < a.Ny; jy0 += L, ++run) {
+    const int b = run & 1;
+    __syncthreads();  // phase 0 of this run done (and, on the first run, the slice landed)
+    const int total = cnt[b];
+    // phase Y: sum over ry of the slice into Y rows (lines past the grid edge get Ey = 0)
+    if constexpr (E % 2 == 0) {
+      constexpr int EV = E / 2;
+      const int units = a.Bx * (L / UL) * EV;
+      for (int u = threadIdx.x; u < units; u += blockDim.x) {
+        const int cv = u % EV, rest = u / EV;
+        const int lh = rest % (L / UL), rx = rest / (L / UL);
+        const float2* eyb = Eys + (size_t)(b * L + lh * UL) * a.By;
+        float4 acc4[UL];
 #pragma unroll
-      for (int l = 0; l < UL; ++l) acc[l] = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int p = ppo[rx]; p < ppo[rx + 1]; ++p) {
-        const float4 z = reinterpret_cast<const float4*>(Zsl + (size_t)p * E)[cv];
-        const int ay = pay[p];
+        for (int l = 0; l < UL; ++l) acc4[l] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int p = ppo[rx]; p < ppo[rx + 1]; ++p) {
+          const float4 z = reinterpret_cast<const float4*>(Zsl + (size_t)p * E)[cv];
+          const int ay = pay[p];
 #pragma unroll
-        for (int l = 0; l < UL; ++l) {
-          const float2 ey = Eys[(lh * UL + l) * a.By + ay];
-          acc[l].x = fmaf(ey.x, z.x, fmaf(-ey.y, z.y, acc[l].x));
-          acc[l].y = fmaf(ey.x, z.y, fmaf(ey.y, z.x, acc[l].y));
-          acc[l].z = fmaf(ey.x, z.z, fmaf(-ey.y, z.w, acc[l].z));
-          acc[l].w = fmaf(ey.x, z.w, fmaf(ey.y, z.z, acc[l].w));
+          for (int l = 0; l < UL; ++l) {
+            const float2 ey = eyb[l * a.By + ay];
+            acc4[l].x = fmaf(ey.x, z.x, fmaf(-ey.y, z.y, acc4[l].x));
+            acc4[l].y = fmaf(ey.x, z.y, fmaf(ey.y, z.x, acc4[l].y));
+            acc4[l].z = fmaf(ey.x, z.z, fmaf(-ey.y, z.w, acc4[l].z));
+            acc4[l].w = fmaf(ey.x, z.w, fmaf(ey.y, z.z, acc4[l].w));
+          }
         }
-      }
 #pragma unroll
-      for (int l = 0; l < UL; ++l)
-        reinterpret_cast<float4*>(Ys + (size_t)(rx * L + lh * UL + l) * ES)[cv] = acc[l];
-    }
-  } else {
-    const int units = a.Bx * (L / UL) * E;
-    for (int u = threadIdx.x; u < units; u += blockDim.x) {
-      const int cv = u % E, rest = u / E;
-      const int lh = rest % (L / UL), rx = rest / (L / UL);
-      float2 acc[UL];
-#pragma unroll
-      for (int l = 0; l < UL; ++l) acc[l] = make_float2(0.f, 0.f);
-      for (int p = ppo[rx]; p < ppo[rx + 1]; ++p) {
-        const float2 z = Zsl[(size_t)p * E + cv];
-        const int ay = pay[p];
-#pragma unroll
-        for (int l = 0; l < UL; ++l) {
-          const float2 ey = Eys[(lh * UL + l) * a.By + ay];
-          acc[l].x = fmaf(ey.x, z.x, fmaf(-ey.y, z.y, acc[l].x));
-          acc[l].y = fmaf(ey.x, z.y, fmaf(ey.y, z.x, acc[l].y));
-        }
-      }
-#pragma unroll
-      for (int l = 0; l < UL; ++l) Ys[(size_t)(rx * L + lh * UL + l) * ES + cv] = acc[l];
-    }
-  }
-  __syncthreads();
-  // rows of residue pairs (r, -r) -> S = Y_r + Y_-r, D = Y_r - Y_-r (in place)
-  if (a.KP > 0) {
-    if constexpr (ES % 2 == 0) {
-      constexpr int RV = L * ES / 2;  // float4 per plane's rows
-      for (int i = threadIdx.x; i < a.KP * RV; i += blockDim.x) {
-        const int k = a.K0 + i / RV, o = i % RV;
-        float4* ya = reinterpret_cast<float4*>(Ys + (size_t)xS[k] * L * ES) + o;
-        float4* yb = reinterpret_cast<float4*>(Ys + (size_t)xD[k] * L * ES) + o;
-        const float4 u = *ya, v = *yb;
-        *ya = make_float4(u.x + v.x, u.y + v.y, u.z + v.z, u.w + v.w);
-        *yb = make_float4(u.x - v.x, u.y - v.y, u.z - v.z, u.w - v.w);
+        for (int l = 0; l < UL; ++l)
+          reinterpret_cast<float4*>(Ys + (size_t)(rx * L + lh * UL + l) * ES)[cv] = acc4[l];
       }
     } else {
-      constexpr int RV = L * ES;
-      for (int i = threadIdx.x; i < a.KP * RV; i += blockDim.x) {
-        const int k = a.K0 + i / RV, o = i % RV;
-        float2* ya = Ys + (size_t)xS[k] * L * ES + o;
-        float2* yb = Ys + (size_t)xD[k] * L * ES + o;
-        const float2 u = *ya, v = *yb;
-        *ya = make_float2(u.x + v.x, u.y + v.y);
-        *yb = make_float2(u.x - v.x, u.y - v.y);
+      const int units = a.Bx * (L / UL) * E;
+      for (int u = threadIdx.x; u < units; u += blockDim.x) {
+        const int cv = u % E, rest = u / E;
+        const int lh = rest % (L / UL), rx = rest / (L / UL);
+        float2 acc2[UL];
+#pragma unroll
+        for (int l = 0; l < UL; ++l) acc2[l] = make_float2(0.f, 0.f);
+        const float2* eyb = Eys + (size_t)(b * L + lh * UL) * a.By;
+        for (int p = ppo[rx]; p < ppo[rx + 1]; ++p) {
+          const float2 z = Zsl[(size_t)p * E + cv];
+          const int ay = pay[p];
+#pragma unroll
+          for (int l = 0; l < UL; ++l) {
+            const float2 ey = eyb[l * a.By + ay];
+            acc2[l].x = fmaf(ey.x, z.x, fmaf(-ey.y, z.y, acc2[l].x));
+            acc2[l].y = fmaf(ey.x, z.y, fmaf(ey.y, z.x, acc2[l].y));
+          }
+        }
+#pragma unroll
+        for (int l = 0; l < UL; ++l) Ys[(size_t)(rx * L + lh * UL + l) * ES + cv] = acc2[l];
       }
     }
     __syncthreads();
-  }
-  const int total = cnt;
-  // phase 1: SPLIT lanes per listed q
-  const int j = threadIdx.x % SPLIT;
-  const unsigned gmask = (SPLIT == 32 ? 0xffffffffu : ((1u << SPLIT) - 1)) << (lane & ~(SPLIT - 1));
-  double acc = 0.0;
-  // this group's prefetch slot: [0,2) el row of the first listed band, [2, 2+NW) its U row,
-  // then Z_q transposed [v][sa], then (omega, n_B)[v]
-  float2* pf = Zsl + (size_t)(threadIdx.x / SPLIT) * SLOT;
-  constexpr int O_UH = 2, O_ZT = 2 + NW, O_ON = 2 + NW + NM * NM, NPF = 2 + NW + NM * NM + NM;
-  for (int it = threadIdx.x / SPLIT; it < total; it += blockDim.x / SPLIT) {
-    const int w = list[it];
-    const int qi = w & 0xffff;
-    const unsigned need = (unsigned)w >> 16;
-    const int l = qi / a.Nx, jx = qi - l * a.Nx;
-    const int jy = jy0 + l;
-    const int q = (jx * a.Ny + jy) * a.Nz + jz;
-    int fx = kc[0] + jx * sx, fy = kc[1] + jy * sy;
-    fx -= fx >= nfx ? nfx : 0;
-    fy -= fy >= nfy ? nfy : 0;
-    const int64_t kq = (int64_t)(fx * nfy + fy) * nfz + fz;
-    const int mp0 = __ffs(need) - 1;
-    {  // issue the epilogue's loads now; they land while the x sum runs
-      const float2* s_el = reinterpret_cast<const float2*>(a.el4 + kq * NW + mp0);
-      const float2* s_uh = a.UH + (kq * NW + mp0) * NW;
-      const float2* s_zt = a.ZT + (int64_t)q * NM * NM;
-      const float2* s_on = a.omnb + (int64_t)q * NM;
-      constexpr int STEP = A16 ? 2 : 1;
-      for (int o = j * STEP; o < NPF; o += SPLIT * STEP) {
-        const float2* src = o < O_UH ? s_el + o : o < O_ZT ? s_uh + (o - O_UH) : o < O_ON ? s_zt + (o - O_ZT) : s_on + (o - O_ON);
-        if constexpr (A16) cp_async16(pf + o, src);
-        else cp_async8(pf + o, src);
-      }
-    }
-    float2 G[NM][MW];
-#pragma unroll
-    for (int sa = 0; sa < NM; ++sa)
-#pragma unroll
-      for (int mm = 0; mm < MW; ++mm) G[sa][mm] = make_float2(0.f, 0.f);
-    // real-factor rows, then residue pairs (cos S + i sin D), then residues without a partner
-    for (int k = 0; k < a.K0; ++k) {
-      const float c = Exs[jx * a.K + k].x;
-      const float2* ys = Ys + (xS[k] * L + l) * ES + j * MW;
-#pragma unroll
-      for (int sa = 0; sa < NM; ++sa) {
-        if constexpr (MW % 2 == 0) {
-#pragma unroll
-          for (int mm = 0; mm < MW; mm += 2) {
-            const float4 v = *reinterpret_cast<const float4*>(ys + sa * NW + mm);
-            G[sa][mm].x = fmaf(c, v.x, G[sa][mm].x);
-            G[sa][mm].y = fmaf(c, v.y, G[sa][mm].y);
-            G[sa][mm + 1].x = fmaf(c, v.z, G[sa][mm + 1].x);
-            G[sa][mm + 1].y = fmaf(c, v.w, G[sa][mm + 1].y);
-          }
-        } else {
-#pragma unroll
-          for (int mm = 0; mm < MW; ++mm) {
-            const float2 v = ys[sa * NW + mm];
-            G[sa][mm].x = fmaf(c, v.x, G[sa][mm].x);
-            G[sa][mm].y = fmaf(c, v.y, G[sa][mm].y);
-          }
+    if (threadIdx.x == 0) cnt[b] = 0;  // every thread read this run's count before the barrier above
+    // rows of residue pairs (r, -r) -> S = Y_r + Y_-r, D = Y_r - Y_-r (in place)
+    if (a.KP > 0) {
+      if constexpr (ES % 2 == 0) {
+        constexpr int RV = L * ES / 2;  // float4 per plane's rows
+        for (int i = threadIdx.x; i < a.KP * RV; i += blockDim.x) {
+          const int k = a.K0 + i / RV, o = i % RV;
+          float4* ya = reinterpret_cast<float4*>(Ys + (size_t)xS[k] * L * ES) + o;
+          float4* yb = reinterpret_cast<float4*>(Ys + (size_t)xD[k] * L * ES) + o;
+          const float4 u = *ya, v = *yb;
+          *ya = make_float4(u.x + v.x, u.y + v.y, u.z + v.z, u.w + v.w);
+          *yb = make_float4(u.x - v.x, u.y - v.y, u.z - v.z, u.w - v.w);
         }
-      }
-    }
-#pragma unroll 2
-    for (int k = a.K0; k < a.K0 + a.KP; ++k) {
-      const float2 cs = Exs[jx * a.K + k];
-      const float2* ys = Ys + (xS[k] * L + l) * ES + j * MW;
-      const float2* yd = Ys + (xD[k] * L + l) * ES + j * MW;
-#pragma unroll
-      for (int sa = 0; sa < NM; ++sa) {
-        if constexpr (MW % 2 == 0) {
-#pragma unroll
-          for (int mm = 0; mm < MW; mm += 2) {
-            const float4 v = *reinterpret_cast<const float4*>(ys + sa * NW + mm);
-            const float4 d = *reinterpret_cast<const float4*>(yd + sa * NW + mm);
-            G[sa][mm].x = fmaf(cs.x, v.x, fmaf(-cs.y, d.y, G[sa][mm].x));
-            G[sa][mm].y = fmaf(cs.x, v.y, fmaf(cs.y, d.x, G[sa][mm].y));
-            G[sa][mm + 1].x = fmaf(cs.x, v.z, fmaf(-cs.y, d.w, G[sa][mm + 1].x));
-            G[sa][mm + 1].y = fmaf(cs.x, v.w, fmaf(cs.y, d.z, G[sa][mm + 1].y));
-          }
-        } else {
-#pragma unroll
-          for (int mm = 0; mm < MW; ++mm) {
-            const float2 v = ys[sa * NW + mm], d = yd[sa * NW + mm];
-            G[sa][mm].x = fmaf(cs.x, v.x, fmaf(-cs.y, d.y, G[sa][mm].x));
-            G[sa][mm].y = fmaf(cs.x, v.y, fmaf(cs.y, d.x, G[sa][mm].y));
-          }
-        }
-      }
-    }
-    for (int k = a.K0 + a.KP; k < a.K; ++k) {
-      const float2 ex = Exs[jx * a.K + k];
-      const float2* y = Ys + (xS[k] * L + l) * ES + j * MW;
-#pragma unroll
-      for (int sa = 0; sa < NM; ++sa) {
-        if constexpr (MW % 2 == 0) {
-#pragma unroll
-          for (int mm = 0; mm < MW; mm += 2) {
-            const float4 v = *reinterpret_cast<const float4*>(y + sa * NW + mm);
-            G[sa][mm].x = fmaf(ex.x, v.x, fmaf(-ex.y, v.y, G[sa][mm].x));
-            G[sa][mm].y = fmaf(ex.x, v.y, fmaf(ex.y, v.x, G[sa][mm].y));
-            G[sa][mm + 1].x = fmaf(ex.x, v.z, fmaf(-ex.y, v.w, G[sa][mm + 1].x));
-            G[sa][mm + 1].y = fmaf(ex.x, v.w, fmaf(ex.y, v.z, G[sa][mm + 1].y));
-          }
-        } else {
-#pragma unroll
-          for (int mm = 0; mm < MW; ++mm) {
-            const float2 v = y[sa * NW + mm];
-            G[sa][mm].x = fmaf(ex.x, v.x, fmaf(-ex.y, v.y, G[sa][mm].x));
-            G[sa][mm].y = fmaf(ex.x, v.y, fmaf(ex.y, v.x, G[sa][mm].y));
-          }
-        }
-      }
-    }
-    cp_async_wait_all();
-    __syncwarp(gmask);
-    for (unsigned m = need; m; m &= m - 1) {
-      const int mp = __ffs(m) - 1;
-      float4 el;
-      float2 u[MW];
-      if (mp == mp0) {
-        el = *reinterpret_cast<const float4*>(pf);
-#pragma unroll
-        for (int mm = 0; mm < MW; ++mm) u[mm] = pf[O_UH + j * MW + mm];
       } else {
-        el = a.el4[kq * NW + mp];
-        load_cplx<MW>(a.UH + (kq * NW + mp) * NW + j * MW, u);
-      }
-      const float dm = (en_hi - el.x) + (en_lo - el.y);
-      const float f = el.z;
-      float2 t[NM];
-#pragma unroll
-      for (int sa = 0; sa < NM; ++sa) {
-        t[sa] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int mm = 0; mm < MW; ++mm) {
-          t[sa].x = fmaf(u[mm].x, G[sa][mm].x, fmaf(-u[mm].y, G[sa][mm].y, t[sa].x));
-          t[sa].y = fmaf(u[mm].x, G[sa][mm].y, fmaf(u[mm].y, G[sa][mm].x, t[sa].y));
+        constexpr int RV = L * ES;
+        for (int i = threadIdx.x; i < a.KP * RV; i += blockDim.x) {
+          const int k = a.K0 + i / RV, o = i % RV;
+          float2* ya = Ys + (size_t)xS[k] * L * ES + o;
+          float2* yb = Ys + (size_t)xD[k] * L * ES + o;
+          const float2 u = *ya, v = *yb;
+          *ya = make_float2(u.x + v.x, u.y + v.y);
+          *yb = make_float2(u.x - v.x, u.y - v.y);
         }
       }
-#pragma unroll
-      for (int o = 1; o < SPLIT; o <<= 1) {
-#pragma unroll
-        for (int sa = 0; sa < NM; ++sa) {
-          t[sa].x += __shfl_xor_sync(gmask, t[sa].x, o);
-          t[sa].y += __shfl_xor_sync(gmask, t[sa].y, o);
-        }
-      }
-      float part = 0.f;
-      for (int v = j; v < NM; v += SPLIT) {
-        const float2* z = pf + O_ZT + v * NM;
-        float2 g = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int sa = 0; sa < NM; ++sa) {
-          const float2 zz = z[sa];
-          g.x = fmaf(t[sa].x, zz.x, fmaf(-t[sa].y, zz.y, g.x));
-          g.y = fmaf(t[sa].x, zz.y, fmaf(t[sa].y, zz.x, g.y));
-        }
-        const float2 on = pf[O_ON + v];
-        const float t1 = (dm - on.x) * a.inv_sigma;
-        const float t2 = (dm + on.x) * a.inv_sigma;
-        float wgt = 0.f;
-        if (t1 * t1 < a.cut2) wgt += (on.y + 1.f - f) * expf(-t1 * t1);
-        if (t2 * t2 < a.cut2) wgt += (on.y + f) * expf(-t2 * t2);
-        part = fmaf(g.x * g.x + g.y * g.y, wgt, part);
-      }
-      acc += (double)part * a.scale;
+      __syncthreads();
     }
-    __syncwarp(gmask);  // the slot is refilled by the group's next q
+    // phase X: SPLIT lanes per listed q
+    const int* list = lists + b * L * a.Nx;
+    for (int it = threadIdx.x / SPLIT; it < total; it += blockDim.x / SPLIT) {
+      const int w = list[it];
+      const unsigned need = (unsigned)w >> 16;
+      const int l = (w >> 8) & 0xff, jx = w & 0xff;
+      const int jy = jy0 + l;
+      float2 G[NM][MW];
+      dft_x_line<NW, NM, MW, ES, L>(Ys, Exs, xS, xD, a.K, a.K0, a.KP, jx, l, j, G);
+      const int q = (jx * a.Ny + jy) * a.Nz + jz;
+      int fx = kc[0] + jx * sx, fy = kc[1] + jy * sy;
+      fx -= fx >= nfx ? nfx : 0;
+      fy -= fy >= nfy ? nfy : 0;
+      const int64_t kq = (int64_t)(fx * nfy + fy) * nfz + fz;
+      const float2* zt = a.ZT + (int64_t)q * NM * NM;
+      const float2* onb = a.omnb + (int64_t)q * NM;
+      for (unsigned m = need; m; m &= m - 1) {
+        const int mp = __ffs(m) - 1;
+        const float4 el = __ldg(a.el4 + kq * NW + mp);
+        const float dm = (en_hi - el.x) + (en_lo - el.y);
+        const float f = el.z;
+        float2 u[MW];
+        load_cplx<MW>(a.UH + (kq * NW + mp) * NW + j * MW, u);
+        float2 t[NM];
+#pragma unroll
+        for (int sa = 0; sa < NM; ++sa) {
+          t[sa] = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int mm = 0; mm < MW; ++mm) {
+            t[sa].x = fmaf(u[mm].x, G[sa][mm].x, fmaf(-u[mm].y, G[sa][mm].y, t[sa].x));
+            t[sa].y = fmaf(u[mm].x, G[sa][mm].y, fmaf(u[mm].y, G[sa][mm].x, t[sa].y));
+          }
+        }
+#pragma unroll
+        for (int o = 1; o < SPLIT; o <<= 1) {
+#pragma unroll
+          for (int sa = 0; sa < NM; ++sa) {
+            t[sa].x += __shfl_xor_sync(gmask, t[sa].x, o);
+            t[sa].y += __shfl_xor_sync(gmask, t[sa].y, o);
+          }
+        }
+        for (int v = j; v < NM; v += SPLIT) {
+          float2 z[NM];
+          load_cplx<NM>(zt + v * NM, z);
+          float2 g = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int sa = 0; sa < NM; ++sa) {
+            g.x = fmaf(t[sa].x, z[sa].x, fmaf(-t[sa].y, z[sa].y, g.x));
+            g.y = fmaf(t[sa].x, z[sa].y, fmaf(t[sa].y, z[sa].x, g.y));
+          }
+          const float2 on = __ldg(onb + v);
+          const float t1 = (dm - on.x) * a.inv_sigma;
+          const float t2 = (dm + on.x) * a.inv_sigma;
+          float wgt = 0.f;
+          if (t1 * t1 < a.cut2) wgt += (on.y + 1.f - f) * expf(-t1 * t1);
+          if (t2 * t2 < a.cut2) wgt += (on.y + f) * expf(-t2 * t2);
+          acc = fmaf(g.x * g.x + g.y * g.y, wgt, acc);
+        }
+      }
+    }
+    if (threadIdx.x == 0) atomicAdd(a.nq_evaluated, (unsigned long long)total);
+    // phase 0 of the next run (into the other list) while other warps finish this run's q
+    if (jy0 + L < a.Ny) phase0(jy0 + L, b ^ 1);
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) red[warp] = acc;
+  if (lane == 0) red[warp] = (double)acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double sum = 0.0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) sum += red[i];
-    if (sum != 0.0) atomicAdd(a.gamma + a.s_base + s, sum);
-    if (total) atomicAdd(a.nq_evaluated, (unsigned long long)total);
+    if (sum != 0.0) atomicAdd(a.gamma + a.s_base + s, sum * a.scale);
   }
 }
 
 template <int NW, int NM, int SPLIT>
 static int launch_yx(cudaStream_t st, const DftXArgs& a, int S) {
-  const size_t smem = dft_smem_bytes(a.P, a.Bx, a.By, NW, NM, a.Nx, a.K);
+  const size_t smem = dft_smem_bytes(a.P, a.Bx, a.By, NW, NM, a.Nx, a.Ny, a.K);
   if (cudaFuncSetAttribute(k_dft_yx_elph<NW, NM, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return -1;
-  dim3 grid((unsigned)(a.Nz * ((a.Ny + kDftLines - 1) / kDftLines)), (unsigned)S);
+  dim3 grid((unsigned)a.Nz, (unsigned)S);
   k_dft_yx_elph<NW, NM, SPLIT><<<grid, kDftXThreads, smem, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -553,12 +546,11 @@ int dft_launch(cudaStream_t st, const DftZArgs& z, const DftXArgs& x, int S, int
   return -2;
 }
 
-size_t dft_smem_bytes(int P, int Bx, int By, int nw, int nm, int Nx, int K) {
+size_t dft_smem_bytes(int P, int Bx, int By, int nw, int nm, int Nx, int Ny, int K) {
   const int E = nw * nm;
-  const size_t zsl = std::max((size_t)P * E, (size_t)(kDftXThreads / dft_split(nw)) * dft_slot(nw, nm));
-  return sizeof(float2) * (zsl + (size_t)Bx * kDftLines * dft_row_stride(E, nw) + (size_t)Nx * K +
-                           (size_t)kDftLines * By) +
-         sizeof(int) * ((size_t)Bx + 1 + 2 * (size_t)K + P + (size_t)kDftLines * Nx);
+  return sizeof(float2) * ((size_t)P * E + (size_t)(P * E) % 2 + (size_t)Bx * kDftLines * dft_row_stride(E, nw) +
+                           (size_t)Nx * K + 2 * (size_t)kDftLines * By) +
+         sizeof(int) * ((size_t)Bx + 1 + 2 * (size_t)K + P + 2 * (size_t)kDftLines * Nx);
 }
 
 size_t dft_z_smem_bytes(int ne_plane_max, int E, int Nz, int Bz) {

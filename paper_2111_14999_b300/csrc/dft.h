@@ -14,11 +14,14 @@ namespace phx {
 #ifndef PHX_DFT_THREADS
 #define PHX_DFT_THREADS 256
 #endif
-constexpr int kDftLines = PHX_DFT_LINES;      // jy lines (at one jz) per block of the fused kernel
+#ifndef PHX_DFT_MINB
+#define PHX_DFT_MINB 3
+#endif
+constexpr int kDftLines = PHX_DFT_LINES;      // jy lines (at one jz) per run of the fused kernel
 constexpr int kDftXThreads = PHX_DFT_THREADS;  // threads per block of the fused kernel
 constexpr int kDftSplit8 = PHX_DFT_SPLIT8;     // lanes per q of the x sum at nw = 8
 constexpr int kDftUnitLines = kDftLines < 4 ? kDftLines : 4;  // lines per work unit of the y sum
-static_assert(kDftLines % kDftUnitLines == 0, "lines per block must be a multiple of the y-sum unit");
+static_assert(kDftLines % kDftUnitLines == 0 && kDftLines <= 256, "lines per block: a multiple of the y-sum unit, at most 256");
 
 // The R_p set grouped by residues r = R mod N: entries sorted by (rx, ry, rz) residue index,
 // "pairs" = distinct (rx, ry), "planes" = distinct rx.
@@ -79,9 +82,7 @@ struct DftXArgs {
 int dft_launch(cudaStream_t st, const DftZArgs& z, const DftXArgs& x, int S, int nw, int nm, int ne_plane_max);
 // Lanes per q of the x sum for nw Wannier functions.
 __host__ __device__ constexpr int dft_split(int nw) { return nw == 8 ? kDftSplit8 : (nw % 2 == 0 ? 2 : 1); }
-// Per lane group of the x sum: complex slots prefetched for one q (el row, U row, Z_q, (omega, n_B)).
-__host__ __device__ constexpr int dft_slot(int nw, int nm) { return (2 + nw + nm * nm + nm + 1) / 2 * 2; }
-size_t dft_smem_bytes(int P, int Bx, int By, int nw, int nm, int Nx, int K);
+size_t dft_smem_bytes(int P, int Bx, int By, int nw, int nm, int Nx, int Ny, int K);
 size_t dft_z_smem_bytes(int ne_plane_max, int E, int Nz, int Bz);
 int dft_table(cudaStream_t st, const int* res, int B, int N, float2* E);
 // FP32 tables of the fused kernel from the FP64 band and phonon arrays.

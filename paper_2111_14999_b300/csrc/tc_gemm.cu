@@ -1908,7 +1908,7 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
     }
   }
   const int K = (int)xS.size();
-  if (dft_smem_bytes(P, Bx, By, nw, nm, Nx, K) > 227 * 1024 || dft_z_smem_bytes(ne_plane_max, E, Nz, Bz) > 227 * 1024)
+  if (dft_smem_bytes(P, Bx, By, nw, nm, Nx, Ny, K) > 227 * 1024 || dft_z_smem_bytes(ne_plane_max, E, Nz, Bz) > 227 * 1024)
     return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED,
                 "the grid-DFT tiles (%d (rx, ry) residue pairs, Nx = %d) exceed shared memory", P, Nx);
   std::vector<float> wf(nRp);
