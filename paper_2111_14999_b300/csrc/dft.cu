@@ -263,8 +263,8 @@ __device__ __forceinline__ void dft_x_line(const float2* __restrict__ Ys, const 
 // tables.  Per run: phase 0 (in the previous run's last phase) lists the q = (jx, jy, jz) of the
 // run whose final bands m' at k+q can reach the delta window around eps_nk (warp ballots, in
 // (line, jx) order, two lists used alternately); phase Y forms Y[rx][line][c] =
-// sum_ry Ey[jy][ry] Zs[(rx,ry)][c] in shared memory (unit = (rx, kDftUnitLines lines, column
-// vector)) and turns the rows of residue pairs into S and D; phase X: SPLIT consecutive lanes
+// sum_ry Ey[jy][ry] Zs[(rx,ry)][c] in shared memory, the rows of residue pairs directly as S and D;
+// phase X: SPLIT consecutive lanes
 // take one listed q, sum over the rows (dft_x_line), apply U_{k+q}^dagger (partial sums over m
 // combined by shuffles), Z_q and the delta weights of every listed m'.  q whose bands all miss
 // the window contribute nothing to Eq. 29 and are not evaluated.
@@ -284,7 +284,8 @@ __global__ void __launch_bounds__(kDftXThreads, PHX_DFT_MINB) k_dft_yx_elph(DftX
   int* xS = ppo + a.Bx + 1;                               // [K]
   int* xD = xS + a.K;                                     // [K]
   int* pay = xD + a.K;                                    // [P]
-  int* lists = pay + P;                                   // [2][L * Nx]
+  int* mate = pay + P;                                    // [P]
+  int* lists = mate + P;                                  // [2][L * Nx]
   __shared__ int cnt[2];
   __shared__ float en_s[2];
   __shared__ double red[kDftXThreads / 32];
@@ -311,7 +312,10 @@ __global__ void __launch_bounds__(kDftXThreads, PHX_DFT_MINB) k_dft_yx_elph(DftX
     xD[i] = a.xD[i];
   }
   for (int i = threadIdx.x; i <= a.Bx; i += blockDim.x) ppo[i] = a.plane_pair_off[i];
-  for (int i = threadIdx.x; i < P; i += blockDim.x) pay[i] = a.pair_ay[i];
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    pay[i] = a.pair_ay[i];
+    mate[i] = a.pair_mate[i];
+  }
   int kc[3];
   grid_coords(a.gm.k_to_fine(a.st_k[s]), a.gm.nf, kc);
   // fine-grid coordinates of k+q: k_d + j_d * s_d with k_d < nf_d and j_d * s_d < nf_d, so one
@@ -373,83 +377,113 @@ __global__ void __launch_bounds__(kDftXThreads, PHX_DFT_MINB) k_dft_yx_elph(DftX
     const int b = run & 1;
     __syncthreads();  // phase 0 of this run done (and, on the first run, the slice landed)
     const int total = cnt[b];
-    // phase Y: sum over ry of the slice into Y rows (lines past the grid edge get Ey = 0)
+    // phase Y: sum over ry of the slice into Y rows (lines past the grid edge get Ey = 0).  For a
+    // residue pair row k (planes a = xS[k], b = xD[k], the pairs of b mirroring those of a) the
+    // rows are formed directly as S = Y_a + Y_b and D = Y_a - Y_b: with Z1 = Zs[(a, ry)],
+    // Z2 = Zs[(b, -ry)] and Ey[jy][ry] = c + i s,
+    //   S = sum_ry c (Z1 + Z2) + i s (Z1 - Z2),   D = sum_ry c (Z1 - Z2) + i s (Z1 + Z2).
+    // Other rows: Y_a = sum_ry Ey Z1.  Unit = (row, kDftUnitLines lines, column vector).
     if constexpr (E % 2 == 0) {
       constexpr int EV = E / 2;
-      const int units = a.Bx * (L / UL) * EV;
+      const int npu = a.KP * (L / UL) * EV;
+      const int units = a.Bx * (L / UL) * EV - npu;  // each pair unit covers two planes
       for (int u = threadIdx.x; u < units; u += blockDim.x) {
-        const int cv = u % EV, rest = u / EV;
-        const int lh = rest % (L / UL), rx = rest / (L / UL);
+        const bool pr = u < npu;
+        const int uu = pr ? u : u - npu;
+        const int cv = uu % EV, rest = uu / EV;
+        const int lh = rest % (L / UL), kk = rest / (L / UL);
+        const int k = pr ? a.K0 + kk : (kk < a.K0 ? kk : kk + a.KP);
+        const int ra = xS[k];
         const float2* eyb = Eys + (size_t)(b * L + lh * UL) * a.By;
-        float4 acc4[UL];
+        float4 s4[UL], d4[UL];
 #pragma unroll
-        for (int l = 0; l < UL; ++l) acc4[l] = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int p = ppo[rx]; p < ppo[rx + 1]; ++p) {
-          const float4 z = reinterpret_cast<const float4*>(Zsl + (size_t)p * E)[cv];
-          const int ay = pay[p];
+        for (int l = 0; l < UL; ++l) {
+          s4[l] = make_float4(0.f, 0.f, 0.f, 0.f);
+          d4[l] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (pr) {
+          for (int p = ppo[ra]; p < ppo[ra + 1]; ++p) {
+            const float4 z1 = reinterpret_cast<const float4*>(Zsl + (size_t)p * E)[cv];
+            const float4 z2 = reinterpret_cast<const float4*>(Zsl + (size_t)mate[p] * E)[cv];
+            const float4 pp = make_float4(z1.x + z2.x, z1.y + z2.y, z1.z + z2.z, z1.w + z2.w);
+            const float4 mm = make_float4(z1.x - z2.x, z1.y - z2.y, z1.z - z2.z, z1.w - z2.w);
+            const int ay = pay[p];
+#pragma unroll
+            for (int l = 0; l < UL; ++l) {
+              const float2 ey = eyb[l * a.By + ay];
+              s4[l].x = fmaf(ey.x, pp.x, fmaf(-ey.y, mm.y, s4[l].x));
+              s4[l].y = fmaf(ey.x, pp.y, fmaf(ey.y, mm.x, s4[l].y));
+              s4[l].z = fmaf(ey.x, pp.z, fmaf(-ey.y, mm.w, s4[l].z));
+              s4[l].w = fmaf(ey.x, pp.w, fmaf(ey.y, mm.z, s4[l].w));
+              d4[l].x = fmaf(ey.x, mm.x, fmaf(-ey.y, pp.y, d4[l].x));
+              d4[l].y = fmaf(ey.x, mm.y, fmaf(ey.y, pp.x, d4[l].y));
+              d4[l].z = fmaf(ey.x, mm.z, fmaf(-ey.y, pp.w, d4[l].z));
+              d4[l].w = fmaf(ey.x, mm.w, fmaf(ey.y, pp.z, d4[l].w));
+            }
+          }
+          const int rb = xD[k];
 #pragma unroll
           for (int l = 0; l < UL; ++l) {
-            const float2 ey = eyb[l * a.By + ay];
-            acc4[l].x = fmaf(ey.x, z.x, fmaf(-ey.y, z.y, acc4[l].x));
-            acc4[l].y = fmaf(ey.x, z.y, fmaf(ey.y, z.x, acc4[l].y));
-            acc4[l].z = fmaf(ey.x, z.z, fmaf(-ey.y, z.w, acc4[l].z));
-            acc4[l].w = fmaf(ey.x, z.w, fmaf(ey.y, z.z, acc4[l].w));
+            reinterpret_cast<float4*>(Ys + (size_t)(ra * L + lh * UL + l) * ES)[cv] = s4[l];
+            reinterpret_cast<float4*>(Ys + (size_t)(rb * L + lh * UL + l) * ES)[cv] = d4[l];
           }
-        }
+        } else {
+          for (int p = ppo[ra]; p < ppo[ra + 1]; ++p) {
+            const float4 z = reinterpret_cast<const float4*>(Zsl + (size_t)p * E)[cv];
+            const int ay = pay[p];
 #pragma unroll
-        for (int l = 0; l < UL; ++l)
-          reinterpret_cast<float4*>(Ys + (size_t)(rx * L + lh * UL + l) * ES)[cv] = acc4[l];
+            for (int l = 0; l < UL; ++l) {
+              const float2 ey = eyb[l * a.By + ay];
+              s4[l].x = fmaf(ey.x, z.x, fmaf(-ey.y, z.y, s4[l].x));
+              s4[l].y = fmaf(ey.x, z.y, fmaf(ey.y, z.x, s4[l].y));
+              s4[l].z = fmaf(ey.x, z.z, fmaf(-ey.y, z.w, s4[l].z));
+              s4[l].w = fmaf(ey.x, z.w, fmaf(ey.y, z.z, s4[l].w));
+            }
+          }
+#pragma unroll
+          for (int l = 0; l < UL; ++l) reinterpret_cast<float4*>(Ys + (size_t)(ra * L + lh * UL + l) * ES)[cv] = s4[l];
+        }
       }
     } else {
-      const int units = a.Bx * (L / UL) * E;
+      const int npu = a.KP * (L / UL) * E;
+      const int units = a.Bx * (L / UL) * E - npu;
       for (int u = threadIdx.x; u < units; u += blockDim.x) {
-        const int cv = u % E, rest = u / E;
-        const int lh = rest % (L / UL), rx = rest / (L / UL);
-        float2 acc2[UL];
-#pragma unroll
-        for (int l = 0; l < UL; ++l) acc2[l] = make_float2(0.f, 0.f);
+        const bool pr = u < npu;
+        const int uu = pr ? u : u - npu;
+        const int cv = uu % E, rest = uu / E;
+        const int lh = rest % (L / UL), kk = rest / (L / UL);
+        const int k = pr ? a.K0 + kk : (kk < a.K0 ? kk : kk + a.KP);
+        const int ra = xS[k];
         const float2* eyb = Eys + (size_t)(b * L + lh * UL) * a.By;
-        for (int p = ppo[rx]; p < ppo[rx + 1]; ++p) {
-          const float2 z = Zsl[(size_t)p * E + cv];
+        float2 s2[UL], d2[UL];
+#pragma unroll
+        for (int l = 0; l < UL; ++l) {
+          s2[l] = make_float2(0.f, 0.f);
+          d2[l] = make_float2(0.f, 0.f);
+        }
+        for (int p = ppo[ra]; p < ppo[ra + 1]; ++p) {
+          const float2 z1 = Zsl[(size_t)p * E + cv];
+          const float2 z2 = pr ? Zsl[(size_t)mate[p] * E + cv] : make_float2(0.f, 0.f);
+          const float2 pp = make_float2(z1.x + z2.x, z1.y + z2.y), mm = make_float2(z1.x - z2.x, z1.y - z2.y);
           const int ay = pay[p];
 #pragma unroll
           for (int l = 0; l < UL; ++l) {
             const float2 ey = eyb[l * a.By + ay];
-            acc2[l].x = fmaf(ey.x, z.x, fmaf(-ey.y, z.y, acc2[l].x));
-            acc2[l].y = fmaf(ey.x, z.y, fmaf(ey.y, z.x, acc2[l].y));
+            s2[l].x = fmaf(ey.x, pp.x, fmaf(-ey.y, mm.y, s2[l].x));
+            s2[l].y = fmaf(ey.x, pp.y, fmaf(ey.y, mm.x, s2[l].y));
+            d2[l].x = fmaf(ey.x, mm.x, fmaf(-ey.y, pp.y, d2[l].x));
+            d2[l].y = fmaf(ey.x, mm.y, fmaf(ey.y, pp.x, d2[l].y));
           }
         }
 #pragma unroll
-        for (int l = 0; l < UL; ++l) Ys[(size_t)(rx * L + lh * UL + l) * ES + cv] = acc2[l];
+        for (int l = 0; l < UL; ++l) {
+          Ys[(size_t)(ra * L + lh * UL + l) * ES + cv] = s2[l];
+          if (pr) Ys[(size_t)(xD[k] * L + lh * UL + l) * ES + cv] = d2[l];
+        }
       }
     }
     __syncthreads();
     if (threadIdx.x == 0) cnt[b] = 0;  // every thread read this run's count before the barrier above
-    // rows of residue pairs (r, -r) -> S = Y_r + Y_-r, D = Y_r - Y_-r (in place)
-    if (a.KP > 0) {
-      if constexpr (ES % 2 == 0) {
-        constexpr int RV = L * ES / 2;  // float4 per plane's rows
-        for (int i = threadIdx.x; i < a.KP * RV; i += blockDim.x) {
-          const int k = a.K0 + i / RV, o = i % RV;
-          float4* ya = reinterpret_cast<float4*>(Ys + (size_t)xS[k] * L * ES) + o;
-          float4* yb = reinterpret_cast<float4*>(Ys + (size_t)xD[k] * L * ES) + o;
-          const float4 u = *ya, v = *yb;
-          *ya = make_float4(u.x + v.x, u.y + v.y, u.z + v.z, u.w + v.w);
-          *yb = make_float4(u.x - v.x, u.y - v.y, u.z - v.z, u.w - v.w);
-        }
-      } else {
-        constexpr int RV = L * ES;
-        for (int i = threadIdx.x; i < a.KP * RV; i += blockDim.x) {
-          const int k = a.K0 + i / RV, o = i % RV;
-          float2* ya = Ys + (size_t)xS[k] * L * ES + o;
-          float2* yb = Ys + (size_t)xD[k] * L * ES + o;
-          const float2 u = *ya, v = *yb;
-          *ya = make_float2(u.x + v.x, u.y + v.y);
-          *yb = make_float2(u.x - v.x, u.y - v.y);
-        }
-      }
-      __syncthreads();
-    }
     // phase X: SPLIT lanes per listed q
     const int* list = lists + b * L * a.Nx;
     for (int it = threadIdx.x / SPLIT; it < total; it += blockDim.x / SPLIT) {
@@ -550,7 +584,7 @@ size_t dft_smem_bytes(int P, int Bx, int By, int nw, int nm, int Nx, int Ny, int
   const int E = nw * nm;
   return sizeof(float2) * ((size_t)P * E + (size_t)(P * E) % 2 + (size_t)Bx * kDftLines * dft_row_stride(E, nw) +
                            (size_t)Nx * K + 2 * (size_t)kDftLines * By) +
-         sizeof(int) * ((size_t)Bx + 1 + 2 * (size_t)K + P + 2 * (size_t)kDftLines * Nx);
+         sizeof(int) * ((size_t)Bx + 1 + 2 * (size_t)K + 2 * (size_t)P + 2 * (size_t)kDftLines * Nx);
 }
 
 size_t dft_z_smem_bytes(int ne_plane_max, int E, int Nz, int Bz) {

@@ -52,6 +52,7 @@ struct DftXArgs {
   int P, Bx, By, Nx, Ny, Nz;
   const int* plane_pair_off;  // [Bx+1]
   const int* pair_ay;         // [P] ry residue index of each pair
+  const int* pair_mate;       // [P] for the pairs of plane xS[k] of a pair row k: the pair (xD[k], -ry)
   // x rows: the rx residues grouped by r -> -r (mod Nx).  Row k reads Y row xS[k]; a residue
   // with a partner r' = -r (xD[k] >= 0, != xS[k]) has its rows replaced by S = Y_r + Y_r' and
   // D = Y_r - Y_r' and contributes cos(t r) S + i sin(t r) D, t = 2 pi jx / Nx; a residue equal

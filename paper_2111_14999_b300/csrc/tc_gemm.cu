@@ -1890,15 +1890,36 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
   int ne_plane_max = 0;
   for (int a = 0; a < Bx; ++a)
     ne_plane_max = std::max(ne_plane_max, pair_ent_off[plane_pair_off[a + 1]] - pair_ent_off[plane_pair_off[a]]);
-  // x rows: pair each rx residue with its negative modulo Nx (Wigner-Seitz sets are inversion symmetric)
+  // x rows: pair each rx residue with its negative modulo Nx.  A pair (a, b) is taken when the
+  // (rx, ry) pairs of plane b are those of plane a with ry negated (true of inversion-symmetric R
+  // sets such as Wigner-Seitz sets); pair_mate then maps each pair of plane a to its mirror in b.
+  std::vector<int> pair_mate(P, -1);
+  auto planes_mirror = [&](int a, int b) {
+    if (plane_pair_off[a + 1] - plane_pair_off[a] != plane_pair_off[b + 1] - plane_pair_off[b]) return false;
+    for (int p = plane_pair_off[a]; p < plane_pair_off[a + 1]; ++p) {
+      const int ryn = (Ny - resv[1][pair_ay[p]]) % Ny;
+      int mate = -1;
+      for (int q = plane_pair_off[b]; q < plane_pair_off[b + 1]; ++q)
+        if (resv[1][pair_ay[q]] == ryn) mate = q;
+      if (mate < 0) return false;
+    }
+    return true;
+  };
   std::vector<int> xS, xD, xres;
   int K0 = 0, KP = 0;
   for (int pass = 0; pass < 3; ++pass) {  // real-factor rows, then pairs, then unpaired residues
     for (int a = 0; a < Bx; ++a) {
       const int r = resv[0][a], rn = (Nx - r) % Nx;
-      const int b = (int)(std::lower_bound(resv[0].begin(), resv[0].end(), rn) - resv[0].begin());
-      const bool has = b < Bx && resv[0][b] == rn;
+      int b = (int)(std::lower_bound(resv[0].begin(), resv[0].end(), rn) - resv[0].begin());
+      bool has = b < Bx && resv[0][b] == rn;
+      if (has && b != a && !planes_mirror(std::min(a, b), std::max(a, b))) has = false;
       const int type = has && b == a ? 0 : has && b > a ? 1 : !has ? 2 : -1;
+      if (type == 1)
+        for (int p = plane_pair_off[a]; p < plane_pair_off[a + 1]; ++p) {
+          const int ryn = (Ny - resv[1][pair_ay[p]]) % Ny;
+          for (int q = plane_pair_off[b]; q < plane_pair_off[b + 1]; ++q)
+            if (resv[1][pair_ay[q]] == ryn) pair_mate[p] = q;
+        }
       if (type != pass) continue;
       xS.push_back(a);
       xD.push_back(type == 0 ? -1 : type == 1 ? b : a);
@@ -1917,6 +1938,8 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
   TRY(upload(c, "dft_ppo", plane_pair_off.data(), sizeof(int) * (Bx + 1), &d_ppo));
   TRY(upload(c, "dft_peo", pair_ent_off.data(), sizeof(int) * (P + 1), &d_peo));
   TRY(upload(c, "dft_pay", pair_ay.data(), sizeof(int) * P, &d_pay));
+  void* d_mate;
+  TRY(upload(c, "dft_mate", pair_mate.data(), sizeof(int) * P, &d_mate));
   TRY(upload(c, "dft_az", ent_az.data(), sizeof(int) * nRp, &d_az));
   TRY(upload(c, "dft_r", ent_r.data(), sizeof(int) * nRp, &d_r));
   TRY(upload(c, "dft_w", wf.data(), sizeof(float) * nRp, &d_w));
@@ -1999,6 +2022,7 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
     x.Nz = Nz;
     x.plane_pair_off = (const int*)d_ppo;
     x.pair_ay = (const int*)d_pay;
+    x.pair_mate = (const int*)d_mate;
     x.K = K;
     x.K0 = K0;
     x.KP = KP;
