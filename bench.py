@@ -139,11 +139,12 @@ def roofline(precision: int, stats: list, k_limit: int) -> dict:
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak if achieved else None, "traffic": None,
                 "peak_source": "FP32 FMA rate from unit counts and the 2032 MHz maximum clock",
-                "kernel": "k_dft_yz + k_dft_x_elph (stage 2 as a separable grid DFT, epilogue fused)",
+                "kernel": "k_dft_z + k_dft_yx_elph (stage 2 as a separable grid DFT: z sum, then the fused "
+                          "y sum / windowed x sum / rotation and delta epilogue)",
                 "algorithmic_flops_per_launch": s2_flops / max(s2_launch, 1),
                 "avg_launch_ms": s2_ms / max(s2_launch, 1),
-                "note": "flops count the DFT's complex MACs (8 flop each); the fused rotation/delta epilogue "
-                        "is not counted"}
+                "note": "flops count the DFT's complex MACs as evaluated (8 flop each; x sum only for the q "
+                        "whose final bands reach the delta window); the rotation/delta epilogue is not counted"}
     elif precision == 0:
         roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
                 "frac": achieved / 1.25 if achieved else None, "traffic": None,
