@@ -36,6 +36,7 @@ __all__ = [
     "coupling_wannier_direct", "coupling_stage1", "coupling_stage2",
     "rotate_final", "bloch_coupling", "couplings_for_pairs",
     "active_states", "fine_grid", "electron_table", "linewidths_rta", "contributions",
+    "phonon_rates_elph",
 ]
 
 
@@ -429,6 +430,62 @@ def contributions(mat, params, k_indices=None, q_indices=None, table=None):
         w = np.where(alive[qi][:, None, :], w, 0.0)
         out[j] = 2.0 * np.pi * np.sum(g2 * w, axis=(1, 2))
     return ks, bs, out
+
+
+def phonon_rates_elph(mat, params, table=None):
+    """Phonon-electron scattering rates P^{el-ph}_{q nu} on the q grid (Sec. 4.3, the diagonal
+    phonon-electron term of the phonon scattering matrix):
+
+    P_{q nu} = -(2 pi / N_k) n_{q nu} (n_{q nu} + 1)
+               sum_{k b b'} |g_{b' b nu}(k,q)|^2 (f_{k b} - f_{k+q b'}) delta(eps_{k b} - eps_{k+q b'} - hbar w_{q nu})
+
+    with the paper's replacement f_{kb} - f_{k+q b'} -> (df/d eps)(eps_{kb}) hbar w_{q nu}, so that
+    P_{q nu} = (2 pi / N_k) n (n + 1) hbar w sum_{k b b'} |g|^2 [f (1 - f) / k_B T]_{k b} delta(...).
+
+    Readings: hbar = 1 energy units (P in eV, like Gamma); b runs over the active initial
+    states of the window (the states the linewidth path sums over; outside the window
+    f(1-f)/k_B T is negligible), b' over all bands at k+q; delta is the truncated Gaussian of
+    Eq. 61; dead modes (hbar w < omega_cut) give 0; P is averaged over modes degenerate within
+    degen_tol at the same q (the mode basis inside a degenerate subspace is arbitrary).
+    Returns P with shape (N_q, 3 N_at), q in grid order.
+    """
+    nk = tuple(int(x) for x in params.nk)
+    nq = tuple(int(x) for x in params.nq)
+    qpts = grid_points(nq)
+    kpts = grid_points(nk)
+    Nk = len(kpts)
+    T, mu, sigma = params.T_K, params.mu_eV, params.sigma_eV
+    cut = params.delta_cut_sigmas
+    kT = KB_EV * T
+    F, eps_F, U_F, k_to_F = table if table is not None else electron_table(mat, params)
+    eps_grid = eps_F[k_to_F]
+    ks, bs = _active(eps_grid, params)
+    omega, z = phonon_modes(qpts, mat)
+    Zq = mode_factors(omega, z, mat.mass_amu, params.omega_cut_eV)
+    nB = bose_einstein(omega, T)
+    alive = omega >= params.omega_cut_eV
+    acc = np.zeros(omega.shape)
+    for ik in np.unique(ks):
+        sel = np.nonzero(ks == ik)[0]
+        bands = bs[sel]
+        k = kpts[ik]
+        U_k = U_F[k_to_F[ik]]
+        kq = grid_index(k[None, :] + qpts, F)
+        eps_kq, U_kq = eps_F[kq], U_F[kq]
+        G = coupling_stage2(coupling_stage1(k, mat, U_k[:, bands]), qpts, mat)  # (Nq, m, b, s)
+        g2 = np.abs(rotate_final(G, U_kq, Zq)) ** 2                              # (Nq, m', b, nu)
+        for jb, b in enumerate(bands):
+            e = eps_grid[ik, b]
+            f = fermi_dirac(np.array([e]), mu, T)[0]
+            d = gaussian_delta(e - eps_kq[:, :, None] - omega[:, None, :], sigma, cut)  # (Nq, m', nu)
+            acc += f * (1.0 - f) / kT * np.sum(g2[:, :, jb, :] * d, axis=1)
+    P = np.where(alive, 2.0 * np.pi / Nk * nB * (nB + 1.0) * omega * acc, 0.0)
+    out = P.copy()
+    for iq in range(len(qpts)):
+        for nu in range(omega.shape[1]):
+            grp = np.abs(omega[iq] - omega[iq, nu]) < params.degen_tol_eV
+            out[iq, nu] = P[iq, grp].mean()
+    return out
 
 
 # ------------------------------------------------- RTA transport from the linewidths (Sec. 4.2, 4.3.2)

@@ -341,3 +341,42 @@ def test_population_window_is_an_energy_window():
     k2, b2 = elph.active_states(eps, mu, W)
     assert np.array_equal(k1, k2) and np.array_equal(b1, b2)
     assert 0 < len(k1) < eps.size
+
+
+def test_closed_form_einstein_phonon_rate():
+    # Sec. 4.3 phonon-electron rate for one tight-binding band, an Einstein mode (three
+    # degenerate modes, averaged) and constant g: with sum_nu |g_nu|^2 = g0^2,
+    # P_q = (1/3)(2 pi/N) n0 (n0+1) hbar w0 g0^2 sum_k [f(1-f)/kT]_k d(e_k - e_{k+q} - hbar w0),
+    # computed here from eps(k) on the integer grid alone.
+    lam, M, cvec, n = 0.215, 28.0, np.array([0.3, -0.2, 0.1]), 8
+    mat, prm = W.tb_einstein(eps0=0.05, t=0.25, lam=lam, c=cvec, mass=M, n=n, mu=0.1)
+    P = elph.phonon_rates_elph(mat, prm)
+    hw0 = HBAR * np.sqrt(EV / (ANG ** 2 * AMU)) / EV * np.sqrt(lam)
+    g0sq = np.sum(cvec ** 2) * (HBAR ** 2 / (AMU * EV * ANG ** 2)) / (2 * M * hw0)
+    kT = 8.617333262e-5 * prm.T_K
+    n0 = 1.0 / np.expm1(hw0 / kT)
+    i = np.indices((n, n, n)).reshape(3, -1).T
+    eps = 0.05 - 2 * 0.25 * np.sum(np.cos(2 * np.pi * i / n), axis=1)
+    f = 1.0 / (np.exp((eps - 0.1) / kT) + 1.0)
+    s, cut = prm.sigma_eV, prm.delta_cut_sigmas
+    want = np.zeros(n ** 3)
+    for iq, j in enumerate(i):
+        kq = (i + j) % n
+        e_kq = eps[(kq[:, 0] * n + kq[:, 1]) * n + kq[:, 2]]
+        x = eps - e_kq - hw0
+        d = np.where(np.abs(x) < cut * s, np.exp(-(x / s) ** 2) / (np.sqrt(np.pi) * s), 0.0)
+        want[iq] = 2 * np.pi / n ** 3 * n0 * (n0 + 1) * hw0 * g0sq / 3.0 * np.sum(f * (1 - f) / kT * d)
+    assert P.shape == (n ** 3, 3)
+    assert np.allclose(P, want[:, None], rtol=1e-11, atol=1e-16)
+    assert np.max(P) > 1e-5
+
+
+def test_phonon_rate_nonnegative_and_quadratic_in_g(toy):
+    mat, prm = toy
+    p1 = elph.phonon_rates_elph(mat, prm)
+    mat2 = W.Material(**{**mat.__dict__, "g": 1.3 * mat.g})
+    p2 = elph.phonon_rates_elph(mat2, prm)
+    assert np.all(p1 >= 0) and np.max(p1) > 0
+    assert np.allclose(p2, 1.3 ** 2 * p1, rtol=1e-12)
+    # the three acoustic modes at Gamma are dead (omega < omega_cut): no rate
+    assert np.all(p1[0] == 0.0)
