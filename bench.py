@@ -248,6 +248,27 @@ def learned_leg(pg, W, dev, stream, args) -> dict:
     }
 
 
+def prate_leg(pg, ctx, prm, mat, ms_linewidths: float) -> dict:
+    """Phonon-electron rates P_{q nu} (Sec. 4.3) of the same Si-like workload: one call runs the whole
+    linewidth pipeline with the rate accumulated in the grid-DFT epilogue; timed against the
+    linewidth step alone."""
+    import torch
+    p7 = pg.make_params(prm, precision=7)
+    nm = 3 * mat.na
+    P = ctx.phonon_rates_elph(p7, nm)                   # warm-up
+    torch.cuda.synchronize()
+    reps = 3
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        P = ctx.phonon_rates_elph(p7, nm)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / reps
+    return {"workload": "si_like 40^3 k x 40^3 q, every (q, nu) of the q grid", "values": int(P.size),
+            "ms_per_call": ms, "ms_linewidths_only": ms_linewidths,
+            "overhead_vs_linewidths": ms / ms_linewidths - 1.0, "unit": "host-timed call incl. download of P",
+            "max_P_eV": float(np.max(P)), "nonzero_fraction": float(np.mean(P > 0))}
+
+
 def batch_leg(pg, W, dev, args) -> dict:
     """64 uneven materials (N_w 4-24, 1-6 atoms, |R| 100-1200, grids 16^3-40^3, a seeded subset of k
     per material, split BF16): one call per material against one batch call whose stage 2 for all
@@ -369,6 +390,7 @@ def main():
     ap.add_argument("--main-only", action="store_true", help="only the timed device leg (for ncu captures)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the many-materials leg")
+    ap.add_argument("--no-prate", action="store_true", help="skip the phonon-electron rate leg")
     ap.add_argument("--learned-only", action="store_true", help="only the learned-proposal leg (profiling case)")
     ap.add_argument("--learned-epochs", type=int, default=0, help="training epochs of the learned leg (0: default)")
     ap.add_argument("--batch-k", type=int, default=64, help="seeded k points per material in the many-materials leg")
@@ -547,6 +569,8 @@ def main():
         "e2e": {"value": e2e_value, "unit": "linewidths/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         **extra,
     }
+    if rank == 0 and args.precision == 7 and not args.no_prate:
+        line["phonon_rates"] = prate_leg(pg, ctx, prm, mat, ms_per_step)
     if rank == 0 and not args.no_learned:
         line["learned_sampler"] = learned_leg(pg, W, dev, stream, args)
     if rank == 0 and not args.no_batch:

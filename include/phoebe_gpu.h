@@ -177,6 +177,20 @@ int phoebe_gpu_linewidths_rta(phoebe_gpu_ctx* ctx, const phoebe_gpu_rta_params* 
 int phoebe_gpu_linewidths_rta_dev(phoebe_gpu_ctx* ctx, const phoebe_gpu_rta_params* params, int* n_states,
                                   int32_t* k_index_dev, int32_t* band_dev, double* gamma_dev);
 
+/* Phonon-electron scattering rates on the q grid (Sec. 4.3, the phonon-electron term on the
+ * diagonal of the phonon scattering matrix), with the paper's replacement
+ * f_kb - f_{k+q b'} -> (df/deps)(eps_kb) hbar w_{q nu}:
+ *   P_{q nu} = (2 pi / N_k) n_{q nu} (n_{q nu} + 1) hbar w_{q nu}
+ *              sum_{k b b'} |g_{b' b nu}(k,q)|^2 [f (1 - f) / k_B T]_{kb} delta(eps_kb - eps_{k+q b'} - hbar w_{q nu})
+ * in eV, b over the active initial states of the window (as linewidths_rta), b' over all bands,
+ * delta the truncated Gaussian, 0 for dead modes, averaged over modes degenerate within
+ * degen_tol at the same q.  Runs the whole linewidth pipeline once (Gamma is computed along the
+ * way and discarded); params->precision must be PHOEBE_PREC_FP32_DFT and the sampler FULL
+ * (ERR_UNSUPPORTED otherwise).  P_eV: host, caller-owned, n_values = N_q * 3 n_at doubles in
+ * q-grid order, [q][nu] (ERR_ARG on another count). */
+int phoebe_gpu_phonon_rates_elph(phoebe_gpu_ctx* ctx, const phoebe_gpu_rta_params* params, int64_t n_values,
+                                 double* P_eV);
+
 /* Work and timing record of the last linewidths_rta call. */
 typedef struct {
   int64_t n_states;            /* active states computed */

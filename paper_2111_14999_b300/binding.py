@@ -37,7 +37,7 @@ EXPORTED = (
     "phoebe_gpu_train_opts_default", "phoebe_gpu_sampler_train", "phoebe_gpu_q_contributions",
     "phoebe_gpu_mlp_loss_grad", "phoebe_gpu_is_uniforms", "phoebe_gpu_mlp_scores",
     "phoebe_gpu_batch_opts_default", "phoebe_gpu_linewidths_rta_batch", "phoebe_gpu_transport_rta",
-    "phoebe_gpu_selftest_wait",
+    "phoebe_gpu_selftest_wait", "phoebe_gpu_phonon_rates_elph",
 )
 
 
@@ -137,6 +137,7 @@ def _load() -> C.CDLL:
         "phoebe_gpu_batch_opts_default": (None, [C.POINTER(BatchOpts)]),
         "phoebe_gpu_linewidths_rta_batch": (I, [C.POINTER(BatchItem), I, C.POINTER(BatchOpts)]),
         "phoebe_gpu_transport_rta": (I, [P, C.POINTER(RTAParams), P, P, P, P]),
+        "phoebe_gpu_phonon_rates_elph": (I, [P, C.POINTER(RTAParams), C.c_int64, P]),
         "phoebe_gpu_selftest_wait": (I, [P, I, I64]),
     }
     for name, (res, args) in sig.items():
@@ -313,6 +314,14 @@ class PhoebeGPU:
         self._check(lib.phoebe_gpu_linewidths_rta_dev(self._ctx, C.byref(s), C.byref(nn), _ptr(k_index_dev),
                                                       _ptr(band_dev), _ptr(gamma_dev)))
         return nn.value
+
+    def phonon_rates_elph(self, params, n_modes: int, **kw):
+        """Phonon-electron rates P[q, nu] (eV) on the q grid of `params` (precision 7)."""
+        s = params if isinstance(params, RTAParams) else make_params(params, **kw)
+        nq = int(s.nq[0]) * int(s.nq[1]) * int(s.nq[2])
+        out = np.empty((nq, int(n_modes)), dtype=np.float64)
+        self._check(lib.phoebe_gpu_phonon_rates_elph(self._ctx, C.byref(s), C.c_int64(out.size), _ptr(out)))
+        return out
 
     def transport_rta(self, params, lattice, **kw):
         """RTA sigma (S/m), Seebeck (V/K) and electronic kappa (W/(m K)), each 3 x 3."""

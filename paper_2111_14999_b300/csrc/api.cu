@@ -509,4 +509,49 @@ int phoebe_gpu_linewidths_rta_dev(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params
   return linewidths(c, p, n_states, k_index_dev, band_dev, gamma_dev, true);
 }
 
+int phoebe_gpu_phonon_rates_elph(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, int64_t n_values,
+                                 double* P_eV) {
+  if (!c) return PHOEBE_GPU_ERR_ARG;
+  cudaSetDevice(c->device);
+  if (!p || !P_eV) return fail(c, PHOEBE_GPU_ERR_ARG, "params or P_eV is NULL");
+  if (p->precision != PHOEBE_PREC_FP32_DFT)
+    return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "phonon-electron rates are evaluated by the grid-DFT stage 2 (precision 7)");
+  if (p->sampler != PHOEBE_SAMPLER_FULL)
+    return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "phonon-electron rates need the full q sum");
+  if (p->nq[0] <= 0 || p->nq[1] <= 0 || p->nq[2] <= 0 || p->nk[0] <= 0 || p->nk[1] <= 0 || p->nk[2] <= 0)
+    return fail(c, PHOEBE_GPU_ERR_ARG, "grid sizes must be positive");
+  if (!c->have_H || !c->have_Phi || !c->have_g)
+    return fail(c, PHOEBE_GPU_ERR_ORDER, "phonon_rates_elph needs all three set_* calls first");
+  const int64_t Nq = (int64_t)p->nq[0] * p->nq[1] * p->nq[2];
+  const int nm = 3 * c->na;
+  if (n_values != Nq * nm)
+    return fail(c, PHOEBE_GPU_ERR_ARG, "P needs N_q * 3 n_at = %lld values, got %lld", (long long)(Nq * nm),
+                (long long)n_values);
+  int st;
+  double* acc = (double*)ensure(c, "prate_acc", sizeof(double) * Nq * nm, &st);
+  if (!acc) return st;
+  double* out = (double*)ensure(c, "prate_out", sizeof(double) * Nq * nm, &st);
+  if (!out) return st;
+  const int64_t cap = (int64_t)p->nk[0] * p->nk[1] * p->nk[2] * c->nw;  // every (k, band) at most
+  if (cap > INT32_MAX) return fail(c, PHOEBE_GPU_ERR_ARG, "k grid too large");
+  int32_t* kd = (int32_t*)ensure(c, "prate_k", sizeof(int32_t) * cap, &st);
+  if (!kd) return st;
+  int32_t* bd = (int32_t*)ensure(c, "prate_b", sizeof(int32_t) * cap, &st);
+  if (!bd) return st;
+  double* gd = (double*)ensure(c, "prate_g", sizeof(double) * cap, &st);
+  if (!gd) return st;
+  CK(c, cudaMemsetAsync(acc, 0, sizeof(double) * Nq * nm, c->stream));
+  CK(c, cudaMemsetAsync(out, 0, sizeof(double) * Nq * nm, c->stream));
+  c->prate_acc = acc;
+  c->prate_out = out;
+  int n = (int)cap;
+  st = linewidths(c, p, &n, kd, bd, gd, true);
+  c->prate_acc = nullptr;
+  c->prate_out = nullptr;
+  if (st) return st;
+  CK(c, cudaMemcpyAsync(P_eV, out, sizeof(double) * Nq * nm, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return PHOEBE_GPU_OK;
+}
+
 }  // extern "C"

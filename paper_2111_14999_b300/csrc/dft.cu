@@ -268,7 +268,7 @@ __device__ __forceinline__ void dft_x_line(const float2* __restrict__ Ys, const 
 // take one listed q, sum over the rows (dft_x_line), apply U_{k+q}^dagger (partial sums over m
 // combined by shuffles), Z_q and the delta weights of every listed m'.  q whose bands all miss
 // the window contribute nothing to Eq. 29 and are not evaluated.
-template <int NW, int NM, int SPLIT>
+template <int NW, int NM, int SPLIT, bool PR>
 __global__ void __launch_bounds__(kDftXThreads, PHX_DFT_MINB) k_dft_yx_elph(DftXArgs a) {
   constexpr int E = NW * NM, MW = NW / SPLIT, ES = dft_row_stride(E, NW);
   constexpr int L = kDftLines, UL = kDftUnitLines;
@@ -288,6 +288,7 @@ __global__ void __launch_bounds__(kDftXThreads, PHX_DFT_MINB) k_dft_yx_elph(DftX
   int* lists = mate + P;                                  // [2][L * Nx]
   __shared__ int cnt[2];
   __shared__ float en_s[2];
+  __shared__ double pw_s;
   __shared__ double red[kDftXThreads / 32];
   const int s = blockIdx.y, jz = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -297,6 +298,10 @@ __global__ void __launch_bounds__(kDftXThreads, PHX_DFT_MINB) k_dft_yx_elph(DftX
     const double e_n = a.epsF[a.gm.k_to_fine(a.st_k[s]) * NW + a.st_b[s]];
     en_s[0] = (float)e_n;
     en_s[1] = (float)(e_n - (double)en_s[0]);
+    if (PR) {  // f (1 - f) / kT of the initial state (the df/de replacement of the rate)
+      const double fn = 1.0 / (exp((e_n - a.mu) * a.inv_kT) + 1.0);
+      pw_s = fn * (1.0 - fn) * a.inv_kT;
+    }
   }
   {  // the Zs[jz] slice of this state: P * E contiguous complex values
     const float2* zg = a.Zs + ((int64_t)s * a.Nz + jz) * P * E;
@@ -327,6 +332,7 @@ __global__ void __launch_bounds__(kDftXThreads, PHX_DFT_MINB) k_dft_yx_elph(DftX
   const float inv_nx = 1.f / (float)a.Nx;  // qi < 2^16, Nx <= 256: (qi + 0.5) / Nx truncates exactly
   __syncthreads();  // counters and en_s
   const float en_hi = en_s[0], en_lo = en_s[1];
+  const double pw = PR ? pw_s : 0.0;
   // phase 0 for the run starting at jy0, into list b: two q per thread and round, their energy
   // rows loaded before either is tested
   auto phase0 = [&](int jy0, int b) {
@@ -537,10 +543,16 @@ __global__ void __launch_bounds__(kDftXThreads, PHX_DFT_MINB) k_dft_yx_elph(DftX
           const float2 on = __ldg(onb + v);
           const float t1 = (dm - on.x) * a.inv_sigma;
           const float t2 = (dm + on.x) * a.inv_sigma;
+          const float g2 = g.x * g.x + g.y * g.y;
           float wgt = 0.f;
-          if (t1 * t1 < a.cut2) wgt += (on.y + 1.f - f) * expf(-t1 * t1);
+          if (t1 * t1 < a.cut2) {
+            const float e1 = expf(-t1 * t1);
+            wgt += (on.y + 1.f - f) * e1;
+            if constexpr (PR)  // this state's share of P_{q nu}: |g|^2 e^{-t1^2} f(1-f)/kT (emission delta)
+              atomicAdd(a.pacc + (int64_t)q * NM + v, (double)(g2 * e1) * pw);
+          }
           if (t2 * t2 < a.cut2) wgt += (on.y + f) * expf(-t2 * t2);
-          acc = fmaf(g.x * g.x + g.y * g.y, wgt, acc);
+          acc = fmaf(g2, wgt, acc);
         }
       }
     }
@@ -558,15 +570,20 @@ __global__ void __launch_bounds__(kDftXThreads, PHX_DFT_MINB) k_dft_yx_elph(DftX
   }
 }
 
-template <int NW, int NM, int SPLIT>
-static int launch_yx(cudaStream_t st, const DftXArgs& a, int S) {
+template <int NW, int NM, int SPLIT, bool PR>
+static int launch_yx_t(cudaStream_t st, const DftXArgs& a, int S) {
   const size_t smem = dft_smem_bytes(a.P, a.Bx, a.By, NW, NM, a.Nx, a.Ny, a.K);
-  if (cudaFuncSetAttribute(k_dft_yx_elph<NW, NM, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
+  if (cudaFuncSetAttribute(k_dft_yx_elph<NW, NM, SPLIT, PR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
     return -1;
   dim3 grid((unsigned)a.Nz, (unsigned)S);
-  k_dft_yx_elph<NW, NM, SPLIT><<<grid, kDftXThreads, smem, st>>>(a);
+  k_dft_yx_elph<NW, NM, SPLIT, PR><<<grid, kDftXThreads, smem, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <int NW, int NM, int SPLIT>
+static int launch_yx(cudaStream_t st, const DftXArgs& a, int S) {
+  return a.pacc ? launch_yx_t<NW, NM, SPLIT, true>(st, a, S) : launch_yx_t<NW, NM, SPLIT, false>(st, a, S);
 }
 
 int dft_launch(cudaStream_t st, const DftZArgs& z, const DftXArgs& x, int S, int nw, int nm, int ne_plane_max) {
@@ -589,6 +606,38 @@ size_t dft_smem_bytes(int P, int Bx, int By, int nw, int nm, int Nx, int Ny, int
 
 size_t dft_z_smem_bytes(int ne_plane_max, int E, int Nz, int Bz) {
   return sizeof(float2) * ((size_t)ne_plane_max * E + (size_t)Nz * Bz) + sizeof(int) * (size_t)ne_plane_max;
+}
+
+// Phonon-electron rates from the accumulated sums (Sec. 4.3): P_{q nu} = (2 pi / N_k) n (n + 1)
+// hbar w acc_{q nu} / (sqrt(pi) sigma) for live modes (0 for dead ones), then averaged over the
+// modes degenerate within degen_tol at the same q.  One thread per q.
+__global__ void k_prate_finish(const double* __restrict__ acc, const double* __restrict__ omega,
+                               const double* __restrict__ nB, int64_t Q, int nm, double pref, double omega_cut,
+                               double degen_tol, double* __restrict__ P) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  double raw[32];
+  for (int v = 0; v < nm; ++v) {
+    const double w = omega[q * nm + v], n = nB[q * nm + v];
+    raw[v] = w >= omega_cut ? pref * n * (n + 1.0) * w * acc[q * nm + v] : 0.0;
+  }
+  for (int v = 0; v < nm; ++v) {
+    double s = 0.0;
+    int c = 0;
+    for (int u = 0; u < nm; ++u)
+      if (fabs(omega[q * nm + u] - omega[q * nm + v]) < degen_tol) {
+        s += raw[u];
+        ++c;
+      }
+    P[q * nm + v] = s / c;
+  }
+}
+
+int prate_finish(cudaStream_t st, const double* acc, const double* omega, const double* nB, int64_t Q, int nm,
+                 double pref, double omega_cut, double degen_tol, double* P) {
+  if (nm > 32) return -2;
+  k_prate_finish<<<(unsigned)((Q + 127) / 128), 128, 0, st>>>(acc, omega, nB, Q, nm, pref, omega_cut, degen_tol, P);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 // FP32 tables of the fused kernel: per fine-grid point and band the energy (window test) and

@@ -77,6 +77,10 @@ struct DftXArgs {
   double* gamma;
   int64_t s_base;
   unsigned long long* nq_evaluated;  // += the (state, q) pairs whose x sum was evaluated
+  // phonon-electron rates (optional, nullptr = off): pacc[q][nu] += f(1-f)/kT of the state times
+  // sum_m' |g_{m' n nu}(k,q)|^2 e^{-((eps_nk - eps_m'k+q - w_q nu)/sigma)^2}
+  double* pacc;
+  double mu, inv_kT;
 };
 
 // Launches both kernels for S states; -1 on a launch error, -2 for a (nw, 3na) without a kernel.
@@ -86,6 +90,9 @@ __host__ __device__ constexpr int dft_split(int nw) { return nw == 8 ? kDftSplit
 size_t dft_smem_bytes(int P, int Bx, int By, int nw, int nm, int Nx, int Ny, int K);
 size_t dft_z_smem_bytes(int ne_plane_max, int E, int Nz, int Bz);
 int dft_table(cudaStream_t st, const int* res, int B, int N, float2* E);
+// P[q][nu] from pacc (see DftXArgs::pacc); pref = 2 pi / (N_k sqrt(pi) sigma).  -2 if nm > 32.
+int prate_finish(cudaStream_t st, const double* acc, const double* omega, const double* nB, int64_t Q, int nm,
+                 double pref, double omega_cut, double degen_tol, double* P);
 // FP32 tables of the fused kernel from the FP64 band and phonon arrays.
 int dft_tables(cudaStream_t st, const double* epsF, const double* fF, int64_t NF, int nw, const cplx* Z,
                const double* om, const double* nB, int64_t Nq, int nm, float* epsf, float4* el4, float2* ZT,

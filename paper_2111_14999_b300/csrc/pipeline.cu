@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "pipeline.h"
+#include "dft.h"
 #include "tc.h"
 
 namespace phx {
@@ -409,6 +410,16 @@ int linewidths(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, int* n_states,
     TRY(run_tc(c, p, gm, ns, hk, st_k, st_b, epsF, UF, fF, omega, nB, Zq, raw));
   }
   c->stats.couplings_executed = c->stats.pairs_executed * nw * nm;
+  if (c->prate_acc) {  // phonon-electron rates accumulated by the grid-DFT stage 2
+    const double Nk = (double)gm.nk[0] * gm.nk[1] * gm.nk[2];
+    const double pref = 2.0 * kPi / (Nk * kSqrtPi * p->sigma_eV);
+    if (prate_finish(c->stream, c->prate_acc, omega, nB, Nq, nm, pref, p->omega_cut_eV, p->degen_tol_eV,
+                     c->prate_out)) {
+      cudaGetLastError();
+      return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the phonon-rate finish failed");
+    }
+    c->launches++;
+  }
   if (c->defer) {  // stage 2 recorded, not run: finish later
     c->defer->ns = ns;
     c->defer->gm = gm;

@@ -43,6 +43,10 @@ struct phoebe_gpu_ctx {
   struct IsRequest* isreq = nullptr;
   // set by the batch entry point: stage 2 is recorded instead of launched
   struct Deferred* defer = nullptr;
+  // phonon-electron rates requested by phoebe_gpu_phonon_rates_elph: accumulation [Nq][3na] and
+  // the finished rates (device), nullptr otherwise
+  double* prate_acc = nullptr;
+  double* prate_out = nullptr;
 };
 
 // Stage-2 work of one material recorded for later issue (batch.cu): each op launches

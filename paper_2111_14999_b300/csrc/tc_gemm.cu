@@ -2046,6 +2046,9 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
     x.gamma = raw;
     x.s_base = i0;
     x.nq_evaluated = nq_eval;
+    x.pacc = c->prate_acc;
+    x.mu = p->mu_eV;
+    x.inv_kT = 1.0 / (kBoltzmannEV * p->T_K);
     tm.begin(c);
     const int r = dft_launch(c->stream, zz, x, S, nw, nm, ne_plane_max);
     if (r != 0) {
