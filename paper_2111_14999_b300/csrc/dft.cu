@@ -171,18 +171,23 @@ __device__ __forceinline__ void load_cplx(const float2* __restrict__ p, float2 (
 // complex values of a row), even whenever E is (16-byte loads stay aligned).
 __host__ __device__ constexpr int dft_row_stride(int E, int NW) { return E + ((NW - E) % 16 + 16) % 16; }
 
-// x sum of one q over the rows of one line: real-factor rows, residue pairs (cos S + i sin D),
-// residues without a partner (e^{i t r} Y).  Lane j of the group owns elements c = sa*NW + j*MW + mm.
-template <int NW, int NM, int MW, int ES, int L>
+// x sum of NQ q (same line l, columns jx[]) over the rows of that line: real-factor rows, residue
+// pairs (cos S + i sin D), residues without a partner (e^{i t r} Y).  Lane j of the group owns
+// elements c = sa*NW + j*MW + mm; each row value loaded serves all NQ q.
+template <int NW, int NM, int MW, int ES, int L, int NQ>
 __device__ __forceinline__ void dft_x_line(const float2* __restrict__ Ys, const float2* __restrict__ Exs,
                                            const int* __restrict__ xS, const int* __restrict__ xD, int K, int K0,
-                                           int KP, int jx, int l, int j, float2 (&G)[NM][MW]) {
+                                           int KP, const int (&jx)[NQ], int l, int j, float2 (&G)[NQ][NM][MW]) {
 #pragma unroll
-  for (int sa = 0; sa < NM; ++sa)
+  for (int u = 0; u < NQ; ++u)
 #pragma unroll
-    for (int mm = 0; mm < MW; ++mm) G[sa][mm] = make_float2(0.f, 0.f);
+    for (int sa = 0; sa < NM; ++sa)
+#pragma unroll
+      for (int mm = 0; mm < MW; ++mm) G[u][sa][mm] = make_float2(0.f, 0.f);
   for (int k = 0; k < K0; ++k) {
-    const float c = Exs[jx * K + k].x;
+    float c[NQ];
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) c[u] = Exs[jx[u] * K + k].x;
     const float2* ys = Ys + (xS[k] * L + l) * ES + j * MW;
 #pragma unroll
     for (int sa = 0; sa < NM; ++sa) {
@@ -190,24 +195,32 @@ __device__ __forceinline__ void dft_x_line(const float2* __restrict__ Ys, const 
 #pragma unroll
         for (int mm = 0; mm < MW; mm += 2) {
           const float4 v = *reinterpret_cast<const float4*>(ys + sa * NW + mm);
-          G[sa][mm].x = fmaf(c, v.x, G[sa][mm].x);
-          G[sa][mm].y = fmaf(c, v.y, G[sa][mm].y);
-          G[sa][mm + 1].x = fmaf(c, v.z, G[sa][mm + 1].x);
-          G[sa][mm + 1].y = fmaf(c, v.w, G[sa][mm + 1].y);
+#pragma unroll
+          for (int u = 0; u < NQ; ++u) {
+            G[u][sa][mm].x = fmaf(c[u], v.x, G[u][sa][mm].x);
+            G[u][sa][mm].y = fmaf(c[u], v.y, G[u][sa][mm].y);
+            G[u][sa][mm + 1].x = fmaf(c[u], v.z, G[u][sa][mm + 1].x);
+            G[u][sa][mm + 1].y = fmaf(c[u], v.w, G[u][sa][mm + 1].y);
+          }
         }
       } else {
 #pragma unroll
         for (int mm = 0; mm < MW; ++mm) {
           const float2 v = ys[sa * NW + mm];
-          G[sa][mm].x = fmaf(c, v.x, G[sa][mm].x);
-          G[sa][mm].y = fmaf(c, v.y, G[sa][mm].y);
+#pragma unroll
+          for (int u = 0; u < NQ; ++u) {
+            G[u][sa][mm].x = fmaf(c[u], v.x, G[u][sa][mm].x);
+            G[u][sa][mm].y = fmaf(c[u], v.y, G[u][sa][mm].y);
+          }
         }
       }
     }
   }
 #pragma unroll 2
   for (int k = K0; k < K0 + KP; ++k) {
-    const float2 cs = Exs[jx * K + k];
+    float2 cs[NQ];
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) cs[u] = Exs[jx[u] * K + k];
     const float2* ys = Ys + (xS[k] * L + l) * ES + j * MW;
     const float2* yd = Ys + (xD[k] * L + l) * ES + j * MW;
 #pragma unroll
@@ -217,23 +230,31 @@ __device__ __forceinline__ void dft_x_line(const float2* __restrict__ Ys, const 
         for (int mm = 0; mm < MW; mm += 2) {
           const float4 v = *reinterpret_cast<const float4*>(ys + sa * NW + mm);
           const float4 d = *reinterpret_cast<const float4*>(yd + sa * NW + mm);
-          G[sa][mm].x = fmaf(cs.x, v.x, fmaf(-cs.y, d.y, G[sa][mm].x));
-          G[sa][mm].y = fmaf(cs.x, v.y, fmaf(cs.y, d.x, G[sa][mm].y));
-          G[sa][mm + 1].x = fmaf(cs.x, v.z, fmaf(-cs.y, d.w, G[sa][mm + 1].x));
-          G[sa][mm + 1].y = fmaf(cs.x, v.w, fmaf(cs.y, d.z, G[sa][mm + 1].y));
+#pragma unroll
+          for (int u = 0; u < NQ; ++u) {
+            G[u][sa][mm].x = fmaf(cs[u].x, v.x, fmaf(-cs[u].y, d.y, G[u][sa][mm].x));
+            G[u][sa][mm].y = fmaf(cs[u].x, v.y, fmaf(cs[u].y, d.x, G[u][sa][mm].y));
+            G[u][sa][mm + 1].x = fmaf(cs[u].x, v.z, fmaf(-cs[u].y, d.w, G[u][sa][mm + 1].x));
+            G[u][sa][mm + 1].y = fmaf(cs[u].x, v.w, fmaf(cs[u].y, d.z, G[u][sa][mm + 1].y));
+          }
         }
       } else {
 #pragma unroll
         for (int mm = 0; mm < MW; ++mm) {
           const float2 v = ys[sa * NW + mm], d = yd[sa * NW + mm];
-          G[sa][mm].x = fmaf(cs.x, v.x, fmaf(-cs.y, d.y, G[sa][mm].x));
-          G[sa][mm].y = fmaf(cs.x, v.y, fmaf(cs.y, d.x, G[sa][mm].y));
+#pragma unroll
+          for (int u = 0; u < NQ; ++u) {
+            G[u][sa][mm].x = fmaf(cs[u].x, v.x, fmaf(-cs[u].y, d.y, G[u][sa][mm].x));
+            G[u][sa][mm].y = fmaf(cs[u].x, v.y, fmaf(cs[u].y, d.x, G[u][sa][mm].y));
+          }
         }
       }
     }
   }
   for (int k = K0 + KP; k < K; ++k) {
-    const float2 ex = Exs[jx * K + k];
+    float2 ex[NQ];
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) ex[u] = Exs[jx[u] * K + k];
     const float2* y = Ys + (xS[k] * L + l) * ES + j * MW;
 #pragma unroll
     for (int sa = 0; sa < NM; ++sa) {
@@ -241,17 +262,23 @@ __device__ __forceinline__ void dft_x_line(const float2* __restrict__ Ys, const 
 #pragma unroll
         for (int mm = 0; mm < MW; mm += 2) {
           const float4 v = *reinterpret_cast<const float4*>(y + sa * NW + mm);
-          G[sa][mm].x = fmaf(ex.x, v.x, fmaf(-ex.y, v.y, G[sa][mm].x));
-          G[sa][mm].y = fmaf(ex.x, v.y, fmaf(ex.y, v.x, G[sa][mm].y));
-          G[sa][mm + 1].x = fmaf(ex.x, v.z, fmaf(-ex.y, v.w, G[sa][mm + 1].x));
-          G[sa][mm + 1].y = fmaf(ex.x, v.w, fmaf(ex.y, v.z, G[sa][mm + 1].y));
+#pragma unroll
+          for (int u = 0; u < NQ; ++u) {
+            G[u][sa][mm].x = fmaf(ex[u].x, v.x, fmaf(-ex[u].y, v.y, G[u][sa][mm].x));
+            G[u][sa][mm].y = fmaf(ex[u].x, v.y, fmaf(ex[u].y, v.x, G[u][sa][mm].y));
+            G[u][sa][mm + 1].x = fmaf(ex[u].x, v.z, fmaf(-ex[u].y, v.w, G[u][sa][mm + 1].x));
+            G[u][sa][mm + 1].y = fmaf(ex[u].x, v.w, fmaf(ex[u].y, v.z, G[u][sa][mm + 1].y));
+          }
         }
       } else {
 #pragma unroll
         for (int mm = 0; mm < MW; ++mm) {
           const float2 v = y[sa * NW + mm];
-          G[sa][mm].x = fmaf(ex.x, v.x, fmaf(-ex.y, v.y, G[sa][mm].x));
-          G[sa][mm].y = fmaf(ex.x, v.y, fmaf(ex.y, v.x, G[sa][mm].y));
+#pragma unroll
+          for (int u = 0; u < NQ; ++u) {
+            G[u][sa][mm].x = fmaf(ex[u].x, v.x, fmaf(-ex[u].y, v.y, G[u][sa][mm].x));
+            G[u][sa][mm].y = fmaf(ex[u].x, v.y, fmaf(ex[u].y, v.x, G[u][sa][mm].y));
+          }
         }
       }
     }
@@ -268,8 +295,8 @@ __device__ __forceinline__ void dft_x_line(const float2* __restrict__ Ys, const 
 // take one listed q, sum over the rows (dft_x_line), apply U_{k+q}^dagger (partial sums over m
 // combined by shuffles), Z_q and the delta weights of every listed m'.  q whose bands all miss
 // the window contribute nothing to Eq. 29 and are not evaluated.
-template <int NW, int NM, int SPLIT, bool PR>
-__global__ void __launch_bounds__(kDftXThreads, PHX_DFT_MINB) k_dft_yx_elph(DftXArgs a) {
+template <int NW, int NM, int SPLIT, bool PR, int NQ>
+__global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT_MINB2) k_dft_yx_elph(DftXArgs a) {
   constexpr int E = NW * NM, MW = NW / SPLIT, ES = dft_row_stride(E, NW);
   constexpr int L = kDftLines, UL = kDftUnitLines;
   static_assert(NW % SPLIT == 0 && 32 % SPLIT == 0 && NW <= 16, "lane split must divide NW and the warp");
@@ -285,7 +312,8 @@ __global__ void __launch_bounds__(kDftXThreads, PHX_DFT_MINB) k_dft_yx_elph(DftX
   int* xD = xS + a.K;                                     // [K]
   int* pay = xD + a.K;                                    // [P]
   int* mate = pay + P;                                    // [P]
-  int* lists = mate + P;                                  // [2][L * Nx]
+  int* lists = mate + P;                                  // [2][lcap]
+  const int lcap = dft_list_cap(L, a.Nx);
   __shared__ int cnt[2];
   __shared__ float en_s[2];
   __shared__ double pw_s;
@@ -337,7 +365,7 @@ __global__ void __launch_bounds__(kDftXThreads, PHX_DFT_MINB) k_dft_yx_elph(DftX
   // rows loaded before either is tested
   auto phase0 = [&](int jy0, int b) {
     const int nq_blk = min(L, a.Ny - jy0) * a.Nx;
-    int* list = lists + b * L * a.Nx;
+    int* list = lists + b * lcap;
     for (int i = threadIdx.x; i < L * a.By; i += blockDim.x) {  // Ey rows of the run (0 past the grid edge)
       const int jy = jy0 + i / a.By;
       Eys[b * L * a.By + i] = jy < a.Ny ? a.Ey[jy * a.By + i % a.By] : make_float2(0.f, 0.f);
@@ -367,10 +395,28 @@ __global__ void __launch_bounds__(kDftXThreads, PHX_DFT_MINB) k_dft_yx_elph(DftX
             if (fabsf(en_hi - ev[u][mp]) < a.reach) need |= 1u << mp;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, need != 0);
-        int base = 0;
-        if (lane == 0 && bal) base = atomicAdd(&cnt[b], __popc(bal));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (need) list[base + __popc(bal & ((1u << lane) - 1))] = (int)(need << 16) | qis[u];
+        if constexpr (NQ == 1) {
+          int base = 0;
+          if (lane == 0 && bal) base = atomicAdd(&cnt[b], __popc(bal));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (need) list[base + __popc(bal & ((1u << lane) - 1))] = (int)(need << 16) | qis[u];
+        } else {
+          // entries are consumed in pairs: each line's run of listed q in this warp is padded to an
+          // even length with an entry of the same line and no band (its x sum runs, nothing else)
+          const unsigned same = __match_any_sync(0xffffffffu, qis[u] >> 8);  // lanes of my line
+          const unsigned bl = bal & same;
+          const int first = __ffs(same) - 1;
+          const bool odd_lead = lane == first && (__popc(bl) & 1);
+          const unsigned oddm = __ballot_sync(0xffffffffu, odd_lead);
+          const int tot = __popc(bal) + __popc(oddm);
+          int base = 0;
+          if (lane == 0 && tot) base = atomicAdd(&cnt[b], tot);
+          base = __shfl_sync(0xffffffffu, base, 0);
+          const unsigned before = (1u << first) - 1;  // lanes of the earlier lines (lines grow with lane)
+          const int seg = base + __popc(bal & before) + __popc(oddm & before);
+          if (need) list[seg + __popc(bl & ((1u << lane) - 1))] = (int)(need << 16) | qis[u];
+          if (odd_lead) list[seg + __popc(bl)] = qis[u] & 0xffff;
+        }
       }
     }
   };
@@ -490,69 +536,80 @@ __global__ void __launch_bounds__(kDftXThreads, PHX_DFT_MINB) k_dft_yx_elph(DftX
     }
     __syncthreads();
     if (threadIdx.x == 0) cnt[b] = 0;  // every thread read this run's count before the barrier above
-    // phase X: SPLIT lanes per listed q
-    const int* list = lists + b * L * a.Nx;
-    for (int it = threadIdx.x / SPLIT; it < total; it += blockDim.x / SPLIT) {
-      const int w = list[it];
-      const unsigned need = (unsigned)w >> 16;
-      const int l = (w >> 8) & 0xff, jx = w & 0xff;
+    // phase X: SPLIT lanes per NQ consecutive list entries (same line when NQ = 2)
+    const int* list = lists + b * lcap;
+    for (int it = (threadIdx.x / SPLIT) * NQ; it < total; it += (blockDim.x / SPLIT) * NQ) {
+      int jxs[NQ];
+      unsigned needs[NQ];
+#pragma unroll
+      for (int u = 0; u < NQ; ++u) {
+        const int w = list[it + u];
+        needs[u] = (unsigned)w >> 16;
+        jxs[u] = w & 0xff;
+      }
+      const int l = (list[it] >> 8) & 0xff;
       const int jy = jy0 + l;
-      float2 G[NM][MW];
-      dft_x_line<NW, NM, MW, ES, L>(Ys, Exs, xS, xD, a.K, a.K0, a.KP, jx, l, j, G);
-      const int q = (jx * a.Ny + jy) * a.Nz + jz;
-      int fx = kc[0] + jx * sx, fy = kc[1] + jy * sy;
-      fx -= fx >= nfx ? nfx : 0;
+      float2 G[NQ][NM][MW];
+      dft_x_line<NW, NM, MW, ES, L, NQ>(Ys, Exs, xS, xD, a.K, a.K0, a.KP, jxs, l, j, G);
+      int fy = kc[1] + jy * sy;
       fy -= fy >= nfy ? nfy : 0;
-      const int64_t kq = (int64_t)(fx * nfy + fy) * nfz + fz;
-      const float2* zt = a.ZT + (int64_t)q * NM * NM;
-      const float2* onb = a.omnb + (int64_t)q * NM;
-      for (unsigned m = need; m; m &= m - 1) {
-        const int mp = __ffs(m) - 1;
-        const float4 el = __ldg(a.el4 + kq * NW + mp);
-        const float dm = (en_hi - el.x) + (en_lo - el.y);
-        const float f = el.z;
-        float2 u[MW];
-        load_cplx<MW>(a.UH + (kq * NW + mp) * NW + j * MW, u);
-        float2 t[NM];
 #pragma unroll
-        for (int sa = 0; sa < NM; ++sa) {
-          t[sa] = make_float2(0.f, 0.f);
-#pragma unroll
-          for (int mm = 0; mm < MW; ++mm) {
-            t[sa].x = fmaf(u[mm].x, G[sa][mm].x, fmaf(-u[mm].y, G[sa][mm].y, t[sa].x));
-            t[sa].y = fmaf(u[mm].x, G[sa][mm].y, fmaf(u[mm].y, G[sa][mm].x, t[sa].y));
-          }
-        }
-#pragma unroll
-        for (int o = 1; o < SPLIT; o <<= 1) {
+      for (int u = 0; u < NQ; ++u) {
+        const int jx = jxs[u];
+        const int q = (jx * a.Ny + jy) * a.Nz + jz;
+        int fx = kc[0] + jx * sx;
+        fx -= fx >= nfx ? nfx : 0;
+        const int64_t kq = (int64_t)(fx * nfy + fy) * nfz + fz;
+        const float2* zt = a.ZT + (int64_t)q * NM * NM;
+        const float2* onb = a.omnb + (int64_t)q * NM;
+        for (unsigned m = needs[u]; m; m &= m - 1) {
+          const int mp = __ffs(m) - 1;
+          const float4 el = __ldg(a.el4 + kq * NW + mp);
+          const float dm = (en_hi - el.x) + (en_lo - el.y);
+          const float f = el.z;
+          float2 uu[MW];
+          load_cplx<MW>(a.UH + (kq * NW + mp) * NW + j * MW, uu);
+          float2 t[NM];
 #pragma unroll
           for (int sa = 0; sa < NM; ++sa) {
-            t[sa].x += __shfl_xor_sync(gmask, t[sa].x, o);
-            t[sa].y += __shfl_xor_sync(gmask, t[sa].y, o);
-          }
-        }
-        for (int v = j; v < NM; v += SPLIT) {
-          float2 z[NM];
-          load_cplx<NM>(zt + v * NM, z);
-          float2 g = make_float2(0.f, 0.f);
+            t[sa] = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int sa = 0; sa < NM; ++sa) {
-            g.x = fmaf(t[sa].x, z[sa].x, fmaf(-t[sa].y, z[sa].y, g.x));
-            g.y = fmaf(t[sa].x, z[sa].y, fmaf(t[sa].y, z[sa].x, g.y));
+            for (int mm = 0; mm < MW; ++mm) {
+              t[sa].x = fmaf(uu[mm].x, G[u][sa][mm].x, fmaf(-uu[mm].y, G[u][sa][mm].y, t[sa].x));
+              t[sa].y = fmaf(uu[mm].x, G[u][sa][mm].y, fmaf(uu[mm].y, G[u][sa][mm].x, t[sa].y));
+            }
           }
-          const float2 on = __ldg(onb + v);
-          const float t1 = (dm - on.x) * a.inv_sigma;
-          const float t2 = (dm + on.x) * a.inv_sigma;
-          const float g2 = g.x * g.x + g.y * g.y;
-          float wgt = 0.f;
-          if (t1 * t1 < a.cut2) {
-            const float e1 = expf(-t1 * t1);
-            wgt += (on.y + 1.f - f) * e1;
-            if constexpr (PR)  // this state's share of P_{q nu}: |g|^2 e^{-t1^2} f(1-f)/kT (emission delta)
-              atomicAdd(a.pacc + (int64_t)q * NM + v, (double)(g2 * e1) * pw);
+#pragma unroll
+          for (int o = 1; o < SPLIT; o <<= 1) {
+#pragma unroll
+            for (int sa = 0; sa < NM; ++sa) {
+              t[sa].x += __shfl_xor_sync(gmask, t[sa].x, o);
+              t[sa].y += __shfl_xor_sync(gmask, t[sa].y, o);
+            }
           }
-          if (t2 * t2 < a.cut2) wgt += (on.y + f) * expf(-t2 * t2);
-          acc = fmaf(g2, wgt, acc);
+          for (int v = j; v < NM; v += SPLIT) {
+            float2 z[NM];
+            load_cplx<NM>(zt + v * NM, z);
+            float2 g = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int sa = 0; sa < NM; ++sa) {
+              g.x = fmaf(t[sa].x, z[sa].x, fmaf(-t[sa].y, z[sa].y, g.x));
+              g.y = fmaf(t[sa].x, z[sa].y, fmaf(t[sa].y, z[sa].x, g.y));
+            }
+            const float2 on = __ldg(onb + v);
+            const float t1 = (dm - on.x) * a.inv_sigma;
+            const float t2 = (dm + on.x) * a.inv_sigma;
+            const float g2 = g.x * g.x + g.y * g.y;
+            float wgt = 0.f;
+            if (t1 * t1 < a.cut2) {
+              const float e1 = expf(-t1 * t1);
+              wgt += (on.y + 1.f - f) * e1;
+              if constexpr (PR)  // this state's share of P_{q nu}: |g|^2 e^{-t1^2} f(1-f)/kT (emission delta)
+                atomicAdd(a.pacc + (int64_t)q * NM + v, (double)(g2 * e1) * pw);
+            }
+            if (t2 * t2 < a.cut2) wgt += (on.y + f) * expf(-t2 * t2);
+            acc = fmaf(g2, wgt, acc);
+          }
         }
       }
     }
@@ -570,20 +627,24 @@ __global__ void __launch_bounds__(kDftXThreads, PHX_DFT_MINB) k_dft_yx_elph(DftX
   }
 }
 
-template <int NW, int NM, int SPLIT, bool PR>
+template <int NW, int NM, int SPLIT, bool PR, int NQ>
 static int launch_yx_t(cudaStream_t st, const DftXArgs& a, int S) {
   const size_t smem = dft_smem_bytes(a.P, a.Bx, a.By, NW, NM, a.Nx, a.Ny, a.K);
-  if (cudaFuncSetAttribute(k_dft_yx_elph<NW, NM, SPLIT, PR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(k_dft_yx_elph<NW, NM, SPLIT, PR, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return -1;
   dim3 grid((unsigned)a.Nz, (unsigned)S);
-  k_dft_yx_elph<NW, NM, SPLIT, PR><<<grid, kDftXThreads, smem, st>>>(a);
+  k_dft_yx_elph<NW, NM, SPLIT, PR, NQ><<<grid, kDftXThreads, smem, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+// Two q per lane group when a warp's 32 consecutive q span at most two lines (Nx >= 32).
 template <int NW, int NM, int SPLIT>
 static int launch_yx(cudaStream_t st, const DftXArgs& a, int S) {
-  return a.pacc ? launch_yx_t<NW, NM, SPLIT, true>(st, a, S) : launch_yx_t<NW, NM, SPLIT, false>(st, a, S);
+  const bool pair = kDftQPair && a.Nx >= 32;
+  if (a.pacc)
+    return pair ? launch_yx_t<NW, NM, SPLIT, true, 2>(st, a, S) : launch_yx_t<NW, NM, SPLIT, true, 1>(st, a, S);
+  return pair ? launch_yx_t<NW, NM, SPLIT, false, 2>(st, a, S) : launch_yx_t<NW, NM, SPLIT, false, 1>(st, a, S);
 }
 
 int dft_launch(cudaStream_t st, const DftZArgs& z, const DftXArgs& x, int S, int nw, int nm, int ne_plane_max) {
@@ -601,7 +662,7 @@ size_t dft_smem_bytes(int P, int Bx, int By, int nw, int nm, int Nx, int Ny, int
   const int E = nw * nm;
   return sizeof(float2) * ((size_t)P * E + (size_t)(P * E) % 2 + (size_t)Bx * kDftLines * dft_row_stride(E, nw) +
                            (size_t)Nx * K + 2 * (size_t)kDftLines * By) +
-         sizeof(int) * ((size_t)Bx + 1 + 2 * (size_t)K + 2 * (size_t)P + 2 * (size_t)kDftLines * Nx);
+         sizeof(int) * ((size_t)Bx + 1 + 2 * (size_t)K + 2 * (size_t)P + 2 * (size_t)dft_list_cap(kDftLines, Nx));
 }
 
 size_t dft_z_smem_bytes(int ne_plane_max, int E, int Nz, int Bz) {

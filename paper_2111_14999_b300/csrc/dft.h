@@ -17,6 +17,9 @@ namespace phx {
 #ifndef PHX_DFT_MINB
 #define PHX_DFT_MINB 3
 #endif
+#ifndef PHX_DFT_MINB2
+#define PHX_DFT_MINB2 2  // blocks per SM the register budget of the two-q kernel is sized for
+#endif
 constexpr int kDftLines = PHX_DFT_LINES;      // jy lines (at one jz) per run of the fused kernel
 constexpr int kDftXThreads = PHX_DFT_THREADS;  // threads per block of the fused kernel
 constexpr int kDftSplit8 = PHX_DFT_SPLIT8;     // lanes per q of the x sum at nw = 8
@@ -85,6 +88,13 @@ struct DftXArgs {
 
 // Launches both kernels for S states; -1 on a launch error, -2 for a (nw, 3na) without a kernel.
 int dft_launch(cudaStream_t st, const DftZArgs& z, const DftXArgs& x, int S, int nw, int nm, int ne_plane_max);
+#ifndef PHX_DFT_QPAIR
+#define PHX_DFT_QPAIR 1
+#endif
+constexpr bool kDftQPair = PHX_DFT_QPAIR != 0;  // two listed q per lane group (lines of Nx >= 32)
+// Entries of one run's q list: every q of the run plus, with pairing, one padding entry per
+// (warp round, line) at most -- two lines per round of 32 consecutive q when Nx >= 32.
+__host__ __device__ constexpr int dft_list_cap(int L, int Nx) { return L * Nx + 2 * ((L * Nx + 31) / 32) + 2; }
 // Lanes per q of the x sum for nw Wannier functions.
 __host__ __device__ constexpr int dft_split(int nw) { return nw == 8 ? kDftSplit8 : (nw % 2 == 0 ? 2 : 1); }
 size_t dft_smem_bytes(int P, int Bx, int By, int nw, int nm, int Nx, int Ny, int K);
