@@ -36,7 +36,7 @@ __all__ = [
     "coupling_wannier_direct", "coupling_stage1", "coupling_stage2",
     "rotate_final", "bloch_coupling", "couplings_for_pairs",
     "active_states", "fine_grid", "electron_table", "linewidths_rta", "contributions",
-    "phonon_rates_elph",
+    "phonon_rates_elph", "adaptive_sigma",
 ]
 
 
@@ -305,6 +305,23 @@ def electron_table(mat, params):
     return F, eps_F, U_F, k_to_F
 
 
+def adaptive_sigma(v_a: np.ndarray, v_b: np.ndarray, lattice: np.ndarray, n, sigma_min: float) -> np.ndarray:
+    """Adaptive Gaussian width for a pair of states (Sec. 4.7):
+    sigma = (A / sqrt 12) sqrt( sum_beta ( sum_alpha (v^alpha_a - v^alpha_b) C_alpha,beta / N_beta )^2 ),  A = 1.
+
+    Readings: the square inside the beta sum (the printed formula has none; a signed sum
+    under the root is not a width); hbar v in eV A (Cartesian); C_alpha,beta = component alpha
+    of the reciprocal lattice vector b_beta = 2 pi (A^-1)^T, so sum_alpha dv_alpha C_alpha,beta
+    / N_beta is the energy change across one mesh cell along b_beta; N_beta the mesh the sum
+    runs over (the q grid); a floor sigma_min keeps the width positive where the velocities
+    coincide.  v_a, v_b broadcast, last axis Cartesian.
+    """
+    B = 2.0 * np.pi * np.linalg.inv(np.asarray(lattice, dtype=np.float64)).T     # rows b_beta
+    C = B.T / np.asarray(n, dtype=np.float64)[None, :]                             # C[alpha, beta] / N_beta
+    d = (np.asarray(v_a) - np.asarray(v_b)) @ C
+    return np.maximum(np.sqrt(np.sum(d * d, axis=-1) / 12.0), sigma_min)
+
+
 def linewidths_rta(mat, params, k_indices=None, direct: bool = False, return_raw: bool = False,
                    table=None):
     """RTA linewidths Gamma_nk = hbar/tau_nk of the active states   (Sec. 4.2 Eq. 29, Sec. 4.3.2).
@@ -344,6 +361,9 @@ def linewidths_rta(mat, params, k_indices=None, direct: bool = False, return_raw
     Zq = mode_factors(omega, z, mat.mass_amu, params.omega_cut_eV)
     nB = bose_einstein(omega, T)
     alive = omega >= params.omega_cut_eV
+    adaptive = getattr(params, "smearing", 0) == 1
+    if adaptive:   # hbar v of every band at every fine-grid point (k and k+q)
+        v_F = group_velocities(grid_points(F), mat, U_F)
 
     raw = np.zeros(len(ks))
     for ik in np.unique(ks):
@@ -365,8 +385,14 @@ def linewidths_rta(mat, params, k_indices=None, direct: bool = False, return_raw
             e = eps_grid[ik, b]
             x_em = e - omega[:, None, :] - eps_kq[:, :, None]            # (Nq, m', nu)
             x_ab = e + omega[:, None, :] - eps_kq[:, :, None]
-            w = ((nB[:, None, :] + 1.0 - f_kq[:, :, None]) * gaussian_delta(x_em, sigma, cut)
-                 + (nB[:, None, :] + f_kq[:, :, None]) * gaussian_delta(x_ab, sigma, cut))
+            if adaptive:   # one width per (k b, k+q m') pair, the same for every mode
+                sg = adaptive_sigma(v_F[k_to_F[ik], b][None, None, :], v_F[kq], mat.lattice, nq,
+                                    params.sigma_min_eV)[:, :, None]
+                w = ((nB[:, None, :] + 1.0 - f_kq[:, :, None]) * gaussian_delta(x_em, sg, cut)
+                     + (nB[:, None, :] + f_kq[:, :, None]) * gaussian_delta(x_ab, sg, cut))
+            else:
+                w = ((nB[:, None, :] + 1.0 - f_kq[:, :, None]) * gaussian_delta(x_em, sigma, cut)
+                     + (nB[:, None, :] + f_kq[:, :, None]) * gaussian_delta(x_ab, sigma, cut))
             w = np.where(alive[:, None, :], w, 0.0)
             raw[j] = 2.0 * np.pi / Nq * np.sum(g2[:, :, jb, :] * w)
 

@@ -380,3 +380,49 @@ def test_phonon_rate_nonnegative_and_quadratic_in_g(toy):
     assert np.allclose(p2, 1.3 ** 2 * p1, rtol=1e-12)
     # the three acoustic modes at Gamma are dead (omega < omega_cut): no rate
     assert np.all(p1[0] == 0.0)
+
+
+def test_closed_form_einstein_linewidth_adaptive_smearing():
+    # Sec. 4.7 adaptive Gaussian smearing on the Einstein model: with a = 1 A (simple cubic) the
+    # band velocity is hbar v_a = 2t sin(2 pi k_a + phi), b_beta = 2 pi e_beta, so each pair (k, k')
+    # has sigma = max((1/sqrt 12)(2 pi/N)|v(k) - v(k')|, sigma_min), and Gamma_k is the smeared DOS
+    # sum of the fixed-width closed form with that width per pair, all from eps(k) and v(k) alone.
+    lam, M, cvec, n, t, phi = 0.215, 28.0, np.array([0.3, -0.2, 0.1]), 8, 0.25, 0.3
+    mat, prm = W.tb_einstein(eps0=0.05, t=t, lam=lam, c=cvec, mass=M, n=n, mu=0.1, hop_phase=phi)
+    prm = prm.with_(smearing=1, sigma_min_eV=2e-3)
+    ks, bs, gam = elph.linewidths_rta(mat, prm)
+    hw0 = HBAR * np.sqrt(EV / (ANG ** 2 * AMU)) / EV * np.sqrt(lam)
+    g0sq = np.sum(cvec ** 2) * (HBAR ** 2 / (AMU * EV * ANG ** 2)) / (2 * M * hw0)
+    kT = 8.617333262e-5 * prm.T_K
+    n0 = 1.0 / np.expm1(hw0 / kT)
+    x = np.indices((n, n, n)).reshape(3, -1).T / n
+    eps = 0.05 - 2 * t * np.sum(np.cos(2 * np.pi * x + phi), axis=1)
+    vel = 2 * t * np.sin(2 * np.pi * x + phi)
+    f = 1.0 / (np.exp((eps - 0.1) / kT) + 1.0)
+    cut = prm.delta_cut_sigmas
+    want = np.zeros(n ** 3)
+    for i in range(n ** 3):
+        sg = np.maximum(2 * np.pi / n * np.linalg.norm(vel[i] - vel, axis=1) / np.sqrt(12.0), 2e-3)
+
+        def dlt(y):
+            return np.where(np.abs(y) < cut * sg, np.exp(-(y / sg) ** 2) / (np.sqrt(np.pi) * sg), 0.0)
+        s = (n0 + 1 - f) * dlt(eps[i] - hw0 - eps) + (n0 + f) * dlt(eps[i] + hw0 - eps)
+        want[i] = 2 * np.pi * g0sq * s.mean()
+    assert np.array_equal(ks, np.arange(n ** 3))
+    assert np.allclose(gam, want, rtol=1e-10, atol=1e-14)
+    fixed = elph.linewidths_rta(mat, prm.with_(smearing=0))[2]
+    assert not np.allclose(gam, fixed, rtol=1e-3)          # the width really varies per pair
+
+
+def test_adaptive_sigma_scaling():
+    # the width is the energy change across one mesh cell: it halves when the mesh doubles and
+    # is symmetric in the two states; a rotated lattice leaves it unchanged with rotated velocities
+    rng = np.random.default_rng(9)
+    lat = rng.normal(size=(3, 3)) + 3 * np.eye(3)
+    va, vb = rng.normal(size=(5, 3)), rng.normal(size=(5, 3))
+    s8 = elph.adaptive_sigma(va, vb, lat, (8, 8, 8), 0.0)
+    assert np.allclose(elph.adaptive_sigma(va, vb, lat, (16, 16, 16), 0.0), s8 / 2, rtol=1e-13)
+    assert np.allclose(elph.adaptive_sigma(vb, va, lat, (8, 8, 8), 0.0), s8, rtol=1e-13)
+    Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    assert np.allclose(elph.adaptive_sigma(va @ Q, vb @ Q, lat @ Q, (8, 8, 8), 0.0), s8, rtol=1e-12)
+    assert np.all(elph.adaptive_sigma(va, va, lat, (8, 8, 8), 1e-3) == 1e-3)
