@@ -98,6 +98,11 @@ int phoebe_gpu_set_hamiltonian(phoebe_gpu_ctx* ctx, int nw, int n_R, const int32
 int phoebe_gpu_set_force_constants(phoebe_gpu_ctx* ctx, int na, const double* mass_amu, int n_R,
                                    const int32_t* R, const double* w, const double* Phi);
 
+/* Primitive lattice vectors (rows, Cartesian, Angstrom; lattice[3*i + a] = a-th component of
+ * vector i), needed by the adaptive smearing (band velocities in Cartesian coordinates and the
+ * reciprocal vectors).  ERR_ARG for a singular lattice. */
+int phoebe_gpu_set_lattice(phoebe_gpu_ctx* ctx, const double* lattice);
+
 /* Electron-phonon coupling in the Wannier representation (Sec. 3.2, Eq. 13).
  *   Re, we  n_Re electron lattice vectors and weights (NULL = 1)
  *   Rp, wp  n_Rp phonon lattice vectors and weights (NULL = 1)
@@ -142,10 +147,15 @@ typedef struct {
   uint64_t seed;             /* sampler LEARNED/UNIFORM: key of the Philox4x32-10 draws */
   int sampler_fp32_network;  /* sampler LEARNED: 1 scores q with the FP32 CUDA-core forward pass,
                                 0 (default) with the tensor-core kernel (FP16 operands) on sm_10x */
-  int reserved0;             /* must be zero */
+  int smearing;              /* 0 (default): Gaussian of fixed width sigma_eV; 1: adaptive width per pair
+                                of states (Sec. 4.7), sigma = max(sigma_min_eV, (1/sqrt 12) sqrt(sum_b
+                                ((hbar v_nk - hbar v_m'k+q) . b_b / N_b)^2)), b_b the reciprocal vectors,
+                                N_b the q grid; needs phoebe_gpu_set_lattice and precision
+                                PHOEBE_PREC_FP32_DFT */
   double population_delta;   /* > 0: initial states are those with f(1 - f) > population_delta (the
                                 population window of Sec. 5.2, 0 < delta < 1/4) instead of the energy
                                 window; 0 (default): energy window */
+  double sigma_min_eV;       /* adaptive smearing: floor of the width (> 0, default 1e-3) */
   int reserved[2];           /* must be zero */
 } phoebe_gpu_rta_params;
 
@@ -156,7 +166,7 @@ typedef enum {
 } phoebe_gpu_sampler;
 
 /* Fill *p with the defaults (cut 6 sigma, omega_cut 1e-4, degen 1e-6, FP64, T=300, full q sum,
- * sample fraction 0.05, alpha 0.1, seed 0). */
+ * sample fraction 0.05, alpha 0.1, seed 0, fixed smearing, sigma_min 1e-3). */
 void phoebe_gpu_rta_params_default(phoebe_gpu_rta_params* p);
 
 /* RTA linewidths of all active (k, n) states on the k grid (Sec. 4.2 Eq. 29):

@@ -37,7 +37,7 @@ EXPORTED = (
     "phoebe_gpu_train_opts_default", "phoebe_gpu_sampler_train", "phoebe_gpu_q_contributions",
     "phoebe_gpu_mlp_loss_grad", "phoebe_gpu_is_uniforms", "phoebe_gpu_mlp_scores",
     "phoebe_gpu_batch_opts_default", "phoebe_gpu_linewidths_rta_batch", "phoebe_gpu_transport_rta",
-    "phoebe_gpu_selftest_wait", "phoebe_gpu_phonon_rates_elph",
+    "phoebe_gpu_selftest_wait", "phoebe_gpu_phonon_rates_elph", "phoebe_gpu_set_lattice",
 )
 
 
@@ -58,8 +58,8 @@ class RTAParams(C.Structure):
         ("max_batch_states", C.c_int),
         ("sampler", C.c_int),
         ("sample_fraction", C.c_double), ("mix_alpha", C.c_double), ("seed", C.c_uint64),
-        ("sampler_fp32_network", C.c_int), ("reserved0", C.c_int),
-        ("population_delta", C.c_double),
+        ("sampler_fp32_network", C.c_int), ("smearing", C.c_int),
+        ("population_delta", C.c_double), ("sigma_min_eV", C.c_double),
         ("reserved", C.c_int * 2),
     ]
 
@@ -138,6 +138,7 @@ def _load() -> C.CDLL:
         "phoebe_gpu_linewidths_rta_batch": (I, [C.POINTER(BatchItem), I, C.POINTER(BatchOpts)]),
         "phoebe_gpu_transport_rta": (I, [P, C.POINTER(RTAParams), P, P, P, P]),
         "phoebe_gpu_phonon_rates_elph": (I, [P, C.POINTER(RTAParams), C.c_int64, P]),
+        "phoebe_gpu_set_lattice": (I, [P, P]),
         "phoebe_gpu_selftest_wait": (I, [P, I, I64]),
     }
     for name, (res, args) in sig.items():
@@ -204,9 +205,9 @@ def make_params(p=None, **kw) -> RTAParams:
             s.k_subset = arr.ctypes.data_as(C.POINTER(C.c_int32))
         elif key in ("T_K", "mu_eV", "sigma_eV", "window_eV", "delta_cut_sigmas", "omega_cut_eV", "degen_tol_eV"):
             setattr(s, key, float(val))
-        elif key in ("precision", "max_batch_states", "sampler", "seed", "sampler_fp32_network"):
+        elif key in ("precision", "max_batch_states", "sampler", "seed", "sampler_fp32_network", "smearing"):
             setattr(s, key, int(val))
-        elif key in ("sample_fraction", "mix_alpha", "population_delta"):
+        elif key in ("sample_fraction", "mix_alpha", "population_delta", "sigma_min_eV"):
             setattr(s, key, float(val))
     s._keep = keep  # keep the subset array alive with the struct
     return s
@@ -271,7 +272,14 @@ class PhoebeGPU:
         self.set_hamiltonian(mat.nw, mat.R_H, mat.w_H, mat.H)
         self.set_force_constants(mat.na, mat.mass_amu, mat.R_fc, mat.w_fc, mat.Phi)
         self.set_elph_wannier(mat.Re, mat.we, mat.Rp, mat.wp, mat.g)
+        if getattr(mat, "lattice", None) is not None:
+            self.set_lattice(mat.lattice)
         self.nw, self.na = int(mat.nw), int(mat.na)
+
+    def set_lattice(self, lattice):
+        """Primitive lattice vectors (rows, Cartesian, Angstrom)."""
+        lat = np.ascontiguousarray(lattice, dtype=np.float64).reshape(9)
+        self._check(lib.phoebe_gpu_set_lattice(self._ctx, _ptr(lat)))
 
     # -------------------------------------------------------------- compute
     def interpolate_couplings(self, k, q, precision: int = PREC_FP64, nw: int | None = None,

@@ -205,6 +205,33 @@ static int fourier_grid_sep(phoebe_gpu_ctx* c, const cplx* in, const int* R_dev,
   return PHOEBE_GPU_OK;
 }
 
+// hbar v [P][nw] (eV A, Cartesian, FP32 (vx, vy, vz, 0)) on the grid n from its eigenvectors U.
+int phx::velocity_grid(phoebe_gpu_ctx* c, const int n[3], const cplx* U, float4** vel_out) {
+  if (!c->have_lattice) return fail(c, PHOEBE_GPU_ERR_ORDER, "band velocities need set_lattice first");
+  const int64_t P = (int64_t)n[0] * n[1] * n[2];
+  const int nw = c->nw, E = nw * nw, nR = c->nRH;
+  int st;
+  cplx* in = (cplx*)ensure(c, "vel_in", sizeof(cplx) * (size_t)nR * 3 * E, &st);
+  if (!in) return st;
+  cplx* dH = (cplx*)ensure(c, "vel_dH", sizeof(cplx) * (size_t)3 * E * P, &st);
+  if (!dH) return st;
+  float4* vel = (float4*)ensure(c, "vel_grid", sizeof(float4) * (size_t)P * nw, &st);
+  if (!vel) return st;
+  Lat9 lat;
+  for (int i = 0; i < 9; ++i) lat.a[i] = c->lattice[i];
+  const int64_t ni = (int64_t)nR * 3 * E;
+  k_vel_input<<<(unsigned)((ni + 255) / 256), 256, 0, c->stream>>>((const cplx*)c->bufs["H"].p,
+                                                                     (const int*)c->bufs["RH"].p, lat, nR, E, in);
+  c->launches++;
+  CK(c, cudaGetLastError());
+  TRY(fourier_grid_sep(c, in, (const int*)c->bufs["RH"].p, (const double*)c->bufs["wH"].p, nR, 3 * E, n, dH));
+  k_band_velocity<<<(unsigned)((P * nw + 127) / 128), 128, 0, c->stream>>>(dH, U, P, nw, vel);
+  c->launches++;
+  CK(c, cudaGetLastError());
+  *vel_out = vel;
+  return PHOEBE_GPU_OK;
+}
+
 // eps[P][nw], U[P][nw][nw] (columns = eigenvectors) on the grid n.
 int phx::electron_grid(phoebe_gpu_ctx* c, const int n[3], double** eps, cplx** U) {
   int64_t P = (int64_t)n[0] * n[1] * n[2];
@@ -306,6 +333,19 @@ void phoebe_gpu_rta_params_default(phoebe_gpu_rta_params* p) {
   p->sampler = PHOEBE_SAMPLER_FULL;
   p->sample_fraction = 0.05;
   p->mix_alpha = 0.1;
+  p->sigma_min_eV = 1e-3;
+}
+
+int phoebe_gpu_set_lattice(phoebe_gpu_ctx* c, const double* lattice) {
+  if (!c) return PHOEBE_GPU_ERR_ARG;
+  if (!lattice) return fail(c, PHOEBE_GPU_ERR_ARG, "lattice is NULL");
+  const double* A = lattice;
+  const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                     A[2] * (A[3] * A[7] - A[4] * A[6]);
+  if (!(fabs(det) > 1e-12)) return fail(c, PHOEBE_GPU_ERR_ARG, "lattice vectors are singular");
+  for (int i = 0; i < 9; ++i) c->lattice[i] = A[i];
+  c->have_lattice = true;
+  return PHOEBE_GPU_OK;
 }
 
 int phoebe_gpu_create(phoebe_gpu_ctx** out, int device, void* cuda_stream) {

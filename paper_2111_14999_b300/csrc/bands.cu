@@ -87,6 +87,45 @@ __global__ void k_sep_x(const cplx* __restrict__ Y, int E, int B0, const cplx* _
   out[t] = acc;
 }
 
+// Inputs of the band-velocity Fourier sums: out[r][a][e] = i R_cart,a H(R)[e] with
+// R_cart = sum_i R_i A_i (lattice rows), so that sum_R w_R e^{ik.R} out[R][a] = dH/dk_a.
+__global__ void k_vel_input(const cplx* __restrict__ H, const int* __restrict__ R, Lat9 lat, int nR, int E,
+                            cplx* __restrict__ out) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nR * 3 * E) return;
+  const int e = (int)(t % E);
+  const int a = (int)((t / E) % 3);
+  const int r = (int)(t / (3 * (int64_t)E));
+  const double x = R[3 * r] * lat.a[a] + R[3 * r + 1] * lat.a[3 + a] + R[3 * r + 2] * lat.a[6 + a];
+  const cplx h = H[(int64_t)r * E + e];
+  out[t] = {-x * h.im, x * h.re};
+}
+
+// hbar v_pb (eV A, Cartesian) = Re (U^dagger dH/dk_a U)_bb (Hellmann-Feynman, Sec. 3.3) from
+// dH [a*nw*nw + e][p] (SoA) and U [p][m][b]; thread (p, b); FP32 output (vx, vy, vz, 0).
+__global__ void k_band_velocity(const cplx* __restrict__ dH, const cplx* __restrict__ U, int64_t P, int nw,
+                                float4* __restrict__ vel) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= P * nw) return;
+  const int64_t p = t / nw;
+  const int b = (int)(t % nw);
+  const int E = nw * nw;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int m = 0; m < nw; ++m) {
+    const cplx um = U[(p * nw + m) * nw + b];
+    for (int n = 0; n < nw; ++n) {
+      const cplx un = U[(p * nw + n) * nw + b];
+      // conj(um) * un
+      const double cr = um.re * un.re + um.im * un.im, ci = um.re * un.im - um.im * un.re;
+      for (int a = 0; a < 3; ++a) {
+        const cplx d = dH[((int64_t)a * E + m * nw + n) * P + p];
+        v[a] += d.re * cr - d.im * ci;
+      }
+    }
+  }
+  vel[t] = make_float4((float)v[0], (float)v[1], (float)v[2], 0.f);
+}
+
 // Point-list Fourier sum (off-grid k): phases from sincospi(2 frac(k.R)).
 __global__ void k_fourier_points_c(const cplx* __restrict__ in, const int* __restrict__ R,
                                    const double* __restrict__ w, int nR, int E,

@@ -285,6 +285,20 @@ __device__ __forceinline__ void dft_x_line(const float2* __restrict__ Ys, const 
   }
 }
 
+// Adaptive Gaussian width of a pair of states (Sec. 4.7): the energy change across one mesh
+// cell along each reciprocal vector, summed in quadrature over the three, over sqrt 12.
+__device__ __forceinline__ float adaptive_width(const float4 va, const float4 vb, const float* __restrict__ cB,
+                                                float smin) {
+  const float dx = va.x - vb.x, dy = va.y - vb.y, dz = va.z - vb.z;
+  float s2 = 0.f;
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const float d = fmaf(dx, cB[b], fmaf(dy, cB[3 + b], dz * cB[6 + b]));
+    s2 = fmaf(d, d, s2);
+  }
+  return fmaxf(sqrtf(s2 * (1.f / 12.f)), smin);
+}
+
 // One block per (jz, state), kDftXThreads threads; the block walks the jy lines in runs of
 // kDftLines.  Loaded once: the state's Zs[jz] slice (every (rx, ry) pair) by cp.async, the phase
 // tables.  Per run: phase 0 (in the previous run's last phase) lists the q = (jx, jy, jz) of the
@@ -295,7 +309,7 @@ __device__ __forceinline__ void dft_x_line(const float2* __restrict__ Ys, const 
 // take one listed q, sum over the rows (dft_x_line), apply U_{k+q}^dagger (partial sums over m
 // combined by shuffles), Z_q and the delta weights of every listed m'.  q whose bands all miss
 // the window contribute nothing to Eq. 29 and are not evaluated.
-template <int NW, int NM, int SPLIT, bool PR, int NQ>
+template <int NW, int NM, int SPLIT, bool PR, int NQ, bool AD>
 __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT_MINB2) k_dft_yx_elph(DftXArgs a) {
   constexpr int E = NW * NM, MW = NW / SPLIT, ES = dft_row_stride(E, NW);
   constexpr int L = kDftLines, UL = kDftUnitLines;
@@ -317,6 +331,7 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
   __shared__ int cnt[2];
   __shared__ float en_s[2];
   __shared__ double pw_s;
+  __shared__ float4 vn_s;  // adaptive smearing: hbar v of the initial state
   __shared__ double red[kDftXThreads / 32];
   const int s = blockIdx.y, jz = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -326,6 +341,7 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
     const double e_n = a.epsF[a.gm.k_to_fine(a.st_k[s]) * NW + a.st_b[s]];
     en_s[0] = (float)e_n;
     en_s[1] = (float)(e_n - (double)en_s[0]);
+    if (AD) vn_s = a.vel[a.gm.k_to_fine(a.st_k[s]) * NW + a.st_b[s]];
     if (PR) {  // f (1 - f) / kT of the initial state (the df/de replacement of the rate)
       const double fn = 1.0 / (exp((e_n - a.mu) * a.inv_kT) + 1.0);
       pw_s = fn * (1.0 - fn) * a.inv_kT;
@@ -361,6 +377,7 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
   __syncthreads();  // counters and en_s
   const float en_hi = en_s[0], en_lo = en_s[1];
   const double pw = PR ? pw_s : 0.0;
+  const float4 vn = AD ? vn_s : make_float4(0.f, 0.f, 0.f, 0.f);
   // phase 0 for the run starting at jy0, into list b: two q per thread and round, their energy
   // rows loaded before either is tested
   auto phase0 = [&](int jy0, int b) {
@@ -370,11 +387,13 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
       const int jy = jy0 + i / a.By;
       Eys[b * L * a.By + i] = jy < a.Ny ? a.Ey[jy * a.By + i % a.By] : make_float2(0.f, 0.f);
     }
-    for (int q0 = 0; q0 < nq_blk; q0 += 2 * blockDim.x) {
-      float ev[2][NW];
-      int qis[2];
+    constexpr int QR = AD ? 1 : 2;  // q per thread and round (the adaptive test also reads velocities)
+    for (int q0 = 0; q0 < nq_blk; q0 += QR * blockDim.x) {
+      float ev[QR][NW];
+      int64_t kqs[QR];
+      int qis[QR];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < QR; ++u) {
         const int qi = q0 + u * blockDim.x + threadIdx.x;
         const int l = (int)(((float)qi + 0.5f) * inv_nx);
         const int jx = qi - l * a.Nx;
@@ -383,16 +402,22 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
           int fx = kc[0] + jx * sx, fy = kc[1] + (jy0 + l) * sy;
           fx -= fx >= nfx ? nfx : 0;
           fy -= fy >= nfy ? nfy : 0;
-          load_row<NW>(a.epsf + ((int64_t)(fx * nfy + fy) * nfz + fz) * NW, ev[u]);
+          kqs[u] = (int64_t)(fx * nfy + fy) * nfz + fz;
+          load_row<NW>(a.epsf + kqs[u] * NW, ev[u]);
         }
       }
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < QR; ++u) {
         unsigned need = 0;
         if (q0 + u * (int)blockDim.x + (int)threadIdx.x < nq_blk) {
 #pragma unroll
-          for (int mp = 0; mp < NW; ++mp)
-            if (fabsf(en_hi - ev[u][mp]) < a.reach) need |= 1u << mp;
+          for (int mp = 0; mp < NW; ++mp) {
+            float reach = a.reach;
+            if constexpr (AD)
+              reach = (a.omega_max + a.cut * adaptive_width(vn, __ldg(a.vel + kqs[u] * NW + mp), a.cB, a.sigma_min)) *
+                      1.0001f;
+            if (fabsf(en_hi - ev[u][mp]) < reach) need |= 1u << mp;
+          }
         }
         const unsigned bal = __ballot_sync(0xffffffffu, need != 0);
         if constexpr (NQ == 1) {
@@ -567,6 +592,11 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
           const float4 el = __ldg(a.el4 + kq * NW + mp);
           const float dm = (en_hi - el.x) + (en_lo - el.y);
           const float f = el.z;
+          float inv_s = a.inv_sigma, norm = 1.f;  // adaptive: 1/sigma of the pair, inside the sum
+          if constexpr (AD) {
+            inv_s = 1.f / adaptive_width(vn, __ldg(a.vel + kq * NW + mp), a.cB, a.sigma_min);
+            norm = inv_s;
+          }
           float2 uu[MW];
           load_cplx<MW>(a.UH + (kq * NW + mp) * NW + j * MW, uu);
           float2 t[NM];
@@ -597,8 +627,8 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
               g.y = fmaf(t[sa].x, z[sa].y, fmaf(t[sa].y, z[sa].x, g.y));
             }
             const float2 on = __ldg(onb + v);
-            const float t1 = (dm - on.x) * a.inv_sigma;
-            const float t2 = (dm + on.x) * a.inv_sigma;
+            const float t1 = (dm - on.x) * inv_s;
+            const float t2 = (dm + on.x) * inv_s;
             const float g2 = g.x * g.x + g.y * g.y;
             float wgt = 0.f;
             if (t1 * t1 < a.cut2) {
@@ -608,7 +638,7 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
                 atomicAdd(a.pacc + (int64_t)q * NM + v, (double)(g2 * e1) * pw);
             }
             if (t2 * t2 < a.cut2) wgt += (on.y + f) * expf(-t2 * t2);
-            acc = fmaf(g2, wgt, acc);
+            acc = fmaf(g2, wgt * norm, acc);
           }
         }
       }
@@ -627,24 +657,30 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
   }
 }
 
-template <int NW, int NM, int SPLIT, bool PR, int NQ>
+template <int NW, int NM, int SPLIT, bool PR, int NQ, bool AD>
 static int launch_yx_t(cudaStream_t st, const DftXArgs& a, int S) {
   const size_t smem = dft_smem_bytes(a.P, a.Bx, a.By, NW, NM, a.Nx, a.Ny, a.K);
-  if (cudaFuncSetAttribute(k_dft_yx_elph<NW, NM, SPLIT, PR, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(k_dft_yx_elph<NW, NM, SPLIT, PR, NQ, AD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return -1;
   dim3 grid((unsigned)a.Nz, (unsigned)S);
-  k_dft_yx_elph<NW, NM, SPLIT, PR, NQ><<<grid, kDftXThreads, smem, st>>>(a);
+  k_dft_yx_elph<NW, NM, SPLIT, PR, NQ, AD><<<grid, kDftXThreads, smem, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-// Two q per lane group when a warp's 32 consecutive q span at most two lines (Nx >= 32).
+// Two q per lane group when a warp's 32 consecutive q span at most two lines (Nx >= 32).  The
+// phonon-electron rates and the adaptive width are not combined (the host rejects it).
 template <int NW, int NM, int SPLIT>
 static int launch_yx(cudaStream_t st, const DftXArgs& a, int S) {
   const bool pair = kDftQPair && a.Nx >= 32;
+  if (a.vel)
+    return pair ? launch_yx_t<NW, NM, SPLIT, false, 2, true>(st, a, S)
+                : launch_yx_t<NW, NM, SPLIT, false, 1, true>(st, a, S);
   if (a.pacc)
-    return pair ? launch_yx_t<NW, NM, SPLIT, true, 2>(st, a, S) : launch_yx_t<NW, NM, SPLIT, true, 1>(st, a, S);
-  return pair ? launch_yx_t<NW, NM, SPLIT, false, 2>(st, a, S) : launch_yx_t<NW, NM, SPLIT, false, 1>(st, a, S);
+    return pair ? launch_yx_t<NW, NM, SPLIT, true, 2, false>(st, a, S)
+                : launch_yx_t<NW, NM, SPLIT, true, 1, false>(st, a, S);
+  return pair ? launch_yx_t<NW, NM, SPLIT, false, 2, false>(st, a, S)
+              : launch_yx_t<NW, NM, SPLIT, false, 1, false>(st, a, S);
 }
 
 int dft_launch(cudaStream_t st, const DftZArgs& z, const DftXArgs& x, int S, int nw, int nm, int ne_plane_max) {

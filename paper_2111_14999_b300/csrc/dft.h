@@ -84,6 +84,12 @@ struct DftXArgs {
   // sum_m' |g_{m' n nu}(k,q)|^2 e^{-((eps_nk - eps_m'k+q - w_q nu)/sigma)^2}
   double* pacc;
   double mu, inv_kT;
+  // adaptive smearing (optional, vel == nullptr = fixed width): hbar v [NF][nw] (vx, vy, vz, 0) in
+  // eV A; width = max(sigma_min, sqrt(sum_b (sum_a dv_a cB[a][b])^2 / 12)), cB[a][b] = (b_b)_a / N_b;
+  // a state can reach the window when |eps_nk - eps_m'k+q| < omega_max + cut * width
+  const float4* vel;
+  float cB[9];
+  float sigma_min, omega_max, cut;
 };
 
 // Launches both kernels for S states; -1 on a launch error, -2 for a (nw, 3na) without a kernel.

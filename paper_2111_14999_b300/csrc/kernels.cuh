@@ -34,6 +34,11 @@ struct GridMap {
 
 // ---------------------------------------------------------------- bands.cu
 __global__ void k_cis_table(cplx* cis, int L);
+struct Lat9 {
+  double a[9];  // lattice rows, Cartesian, A
+};
+__global__ void k_vel_input(const cplx* H, const int* R, Lat9 lat, int nR, int E, cplx* out);
+__global__ void k_band_velocity(const cplx* dH, const cplx* U, int64_t P, int nw, float4* vel);
 __global__ void k_sep_table(const int* res, int B, int N, cplx* E);
 __global__ void k_sep_z(const cplx* in, const double* w, int E, int npair, const int* pair_off, const int* ent_c,
                         const int* ent_r, const cplx* E2, int N2, int B2, cplx* Zs);

@@ -140,7 +140,16 @@ static int check_params(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, GridM
     return fail(c, PHOEBE_GPU_ERR_ARG, "unknown precision %d", p->precision);
   for (int i = 0; i < 2; ++i)
     if (p->reserved[i] != 0) return fail(c, PHOEBE_GPU_ERR_ARG, "reserved fields must be zero");
-  if (p->reserved0 != 0) return fail(c, PHOEBE_GPU_ERR_ARG, "reserved fields must be zero");
+  if (p->smearing != 0 && p->smearing != 1) return fail(c, PHOEBE_GPU_ERR_ARG, "smearing must be 0 or 1");
+  if (p->smearing == 1) {
+    if (!(p->sigma_min_eV > 0.0)) return fail(c, PHOEBE_GPU_ERR_ARG, "sigma_min_eV must be > 0");
+    if (p->precision != PHOEBE_PREC_FP32_DFT || p->sampler != PHOEBE_SAMPLER_FULL)
+      return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED,
+                  "adaptive smearing is evaluated by the grid-DFT stage 2 (precision 7, full q sum)");
+    if (!c->have_lattice) return fail(c, PHOEBE_GPU_ERR_ORDER, "adaptive smearing needs set_lattice first");
+    if (c->prate_acc)
+      return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "phonon-electron rates use the fixed Gaussian width");
+  }
   if (!(p->population_delta >= 0.0 && p->population_delta < 0.25))
     return fail(c, PHOEBE_GPU_ERR_ARG, "population_delta must be in [0, 0.25)");
   if (p->sampler_fp32_network != 0 && p->sampler_fp32_network != 1)

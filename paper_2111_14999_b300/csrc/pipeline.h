@@ -47,6 +47,9 @@ struct phoebe_gpu_ctx {
   // the finished rates (device), nullptr otherwise
   double* prate_acc = nullptr;
   double* prate_out = nullptr;
+  // primitive lattice vectors (rows, Cartesian, A), set by phoebe_gpu_set_lattice
+  bool have_lattice = false;
+  double lattice[9] = {0};
 };
 
 // Stage-2 work of one material recorded for later issue (batch.cu): each op launches
@@ -106,6 +109,7 @@ struct Timer {
 GridPhase make_phase(const int n[3]);
 int cis_table(phoebe_gpu_ctx* c, const GridPhase& gp, const char* name, cplx** out);
 int electron_grid(phoebe_gpu_ctx* c, const int n[3], double** eps, cplx** U);
+int velocity_grid(phoebe_gpu_ctx* c, const int n[3], const cplx* U, float4** vel);
 int phonon_modes(phoebe_gpu_ctx* c, const int n[3], const double* qpts_dev, int64_t Q, double T,
                  double omega_cut, double** omega, double** nB, cplx** Z, const char* tag);
 

@@ -1842,6 +1842,8 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
     return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the grid-DFT tables failed");
   }
   c->launches += 1;
+  float4* vel = nullptr;  // adaptive smearing: band velocities on the fine grid
+  if (p->smearing == 1) TRY(velocity_grid(c, gm.nf, UF, &vel));
   CK(c, cudaGetLastError());
   unsigned long long ombits = 0;
   CK(c, cudaMemcpyAsync(&ombits, dmax, sizeof(ombits), cudaMemcpyDeviceToHost, c->stream));
@@ -2049,6 +2051,25 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
     x.pacc = c->prate_acc;
     x.mu = p->mu_eV;
     x.inv_kT = 1.0 / (kBoltzmannEV * p->T_K);
+    x.vel = vel;
+    x.sigma_min = (float)p->sigma_min_eV;
+    x.omega_max = (float)omega_max;
+    x.cut = (float)p->delta_cut_sigmas;
+    for (int i = 0; i < 9; ++i) x.cB[i] = 0.f;
+    if (vel) {  // cB[a][b] = (b_b)_a / N_b with b = 2 pi (A^-1)^T; the 1/sigma of each pair is in the sum
+      const double* A = c->lattice;
+      const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                         A[2] * (A[3] * A[7] - A[4] * A[6]);
+      const double inv[9] = {(A[4] * A[8] - A[5] * A[7]) / det, (A[2] * A[7] - A[1] * A[8]) / det,
+                             (A[1] * A[5] - A[2] * A[4]) / det, (A[5] * A[6] - A[3] * A[8]) / det,
+                             (A[0] * A[8] - A[2] * A[6]) / det, (A[2] * A[3] - A[0] * A[5]) / det,
+                             (A[3] * A[7] - A[4] * A[6]) / det, (A[1] * A[6] - A[0] * A[7]) / det,
+                             (A[0] * A[4] - A[1] * A[3]) / det};  // inv[a][b] = (A^-1)_{ab}
+      const int Nb[3] = {Nx, Ny, Nz};
+      for (int a2 = 0; a2 < 3; ++a2)
+        for (int b2 = 0; b2 < 3; ++b2) x.cB[a2 * 3 + b2] = (float)(2.0 * kPi * inv[a2 * 3 + b2] / Nb[b2]);
+      x.scale = (2.0 * kPi / (double)Nq) / kSqrtPi;
+    }
     tm.begin(c);
     const int r = dft_launch(c->stream, zz, x, S, nw, nm, ne_plane_max);
     if (r != 0) {

@@ -78,3 +78,24 @@ def test_create_without_gpu_fails_cleanly():
     with pytest.raises(pg.PhoebeGPUError):
         pg.PhoebeGPU(0)
     assert pg.version().startswith("phoebe_gpu")
+
+
+def test_make_params_carries_every_workload_field():
+    # every field of the workloads parameter record reaches the C struct (no silent drop)
+    import dataclasses
+    from workloads import synthetic as W
+    pg = pytest.importorskip("paper_2111_14999_b300")
+    prm = W.RTAParams(nk=(4, 4, 4), nq=(8, 8, 8), T_K=250.0, mu_eV=0.3, sigma_eV=0.02, window_eV=0.4,
+                      delta_cut_sigmas=5.0, omega_cut_eV=2e-4, degen_tol_eV=1e-7, precision=7,
+                      sampler=2, sample_fraction=0.1, mix_alpha=0.2, seed=7, sampler_fp32_network=1,
+                      population_delta=0.01, smearing=1, sigma_min_eV=3e-3)
+    s = pg.make_params(prm)
+    for f in dataclasses.fields(prm):
+        v = getattr(prm, f.name)
+        if f.name == "k_subset" or v is None:
+            continue
+        got = getattr(s, f.name)
+        if f.name in ("nk", "nq"):
+            assert list(got) == list(v), f.name
+        else:
+            assert got == pytest.approx(v), f.name
