@@ -156,7 +156,10 @@ typedef struct {
                                 population window of Sec. 5.2, 0 < delta < 1/4) instead of the energy
                                 window; 0 (default): energy window */
   double sigma_min_eV;       /* adaptive smearing: floor of the width (> 0, default 1e-3) */
-  int reserved[2];           /* must be zero */
+  int window_final;          /* 1: final states (k+q, m') must also pass the window (energy or
+                                population, as the initial states); 0 (default): every band at k+q.
+                                1 needs precision PHOEBE_PREC_FP32_DFT */
+  int reserved1;             /* must be zero */
 } phoebe_gpu_rta_params;
 
 typedef enum {

@@ -36,7 +36,7 @@ __all__ = [
     "coupling_wannier_direct", "coupling_stage1", "coupling_stage2",
     "rotate_final", "bloch_coupling", "couplings_for_pairs",
     "active_states", "fine_grid", "electron_table", "linewidths_rta", "contributions",
-    "phonon_rates_elph", "adaptive_sigma",
+    "phonon_rates_elph", "adaptive_sigma", "in_window",
 ]
 
 
@@ -280,6 +280,28 @@ def active_states(eps_k: np.ndarray, mu: float, window: float, T: float | None =
     return np.array(ks, dtype=np.int64), np.array(bs, dtype=np.int64)
 
 
+def in_window(eps: np.ndarray, params) -> np.ndarray:
+    """Membership of states of energies eps in the window of Sec. 5.2 (the energy window
+    |eps - mu| < window, window <= 0: all; or with population_delta > 0 the population window
+    f(1-f) > delta), elementwise."""
+    eps = np.asarray(eps, dtype=np.float64)
+    delta = getattr(params, "population_delta", 0.0)
+    if delta > 0:
+        f = fermi_dirac(eps, params.mu_eV, params.T_K)
+        return f * (1.0 - f) > delta
+    if params.window_eV <= 0:
+        return np.ones(eps.shape, dtype=bool)
+    return np.abs(eps - params.mu_eV) < params.window_eV
+
+
+def _final_ok(eps_kq, params):
+    """Final states allowed: every band (the default reading), or with window_final = 1 only those
+    inside the window (Phoebe's active band structure for both states of a transition)."""
+    if getattr(params, "window_final", 0) == 1:
+        return in_window(eps_kq, params)
+    return np.ones(np.shape(eps_kq), dtype=bool)
+
+
 def _active(eps_grid, params):
     return active_states(eps_grid, params.mu_eV, params.window_eV, params.T_K,
                          getattr(params, "population_delta", 0.0))
@@ -393,7 +415,7 @@ def linewidths_rta(mat, params, k_indices=None, direct: bool = False, return_raw
             else:
                 w = ((nB[:, None, :] + 1.0 - f_kq[:, :, None]) * gaussian_delta(x_em, sigma, cut)
                      + (nB[:, None, :] + f_kq[:, :, None]) * gaussian_delta(x_ab, sigma, cut))
-            w = np.where(alive[:, None, :], w, 0.0)
+            w = np.where(alive[:, None, :] & _final_ok(eps_kq, params)[:, :, None], w, 0.0)
             raw[j] = 2.0 * np.pi / Nq * np.sum(g2[:, :, jb, :] * w)
 
     out = raw.copy()
@@ -453,7 +475,7 @@ def contributions(mat, params, k_indices=None, q_indices=None, table=None):
         om, nb_ = omega[qi][:, None, :], nB[qi][:, None, :]
         w = ((nb_ + 1.0 - f_kq[:, :, None]) * gaussian_delta(e - om - eps_kq[:, :, None], sigma, cut)
              + (nb_ + f_kq[:, :, None]) * gaussian_delta(e + om - eps_kq[:, :, None], sigma, cut))
-        w = np.where(alive[qi][:, None, :], w, 0.0)
+        w = np.where(alive[qi][:, None, :] & _final_ok(eps_kq, params)[:, :, None], w, 0.0)
         out[j] = 2.0 * np.pi * np.sum(g2 * w, axis=(1, 2))
     return ks, bs, out
 
@@ -504,6 +526,7 @@ def phonon_rates_elph(mat, params, table=None):
             e = eps_grid[ik, b]
             f = fermi_dirac(np.array([e]), mu, T)[0]
             d = gaussian_delta(e - eps_kq[:, :, None] - omega[:, None, :], sigma, cut)  # (Nq, m', nu)
+            d = np.where(_final_ok(eps_kq, params)[:, :, None], d, 0.0)
             acc += f * (1.0 - f) / kT * np.sum(g2[:, :, jb, :] * d, axis=1)
     P = np.where(alive, 2.0 * np.pi / Nk * nB * (nB + 1.0) * omega * acc, 0.0)
     out = P.copy()

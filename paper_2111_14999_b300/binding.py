@@ -60,7 +60,7 @@ class RTAParams(C.Structure):
         ("sample_fraction", C.c_double), ("mix_alpha", C.c_double), ("seed", C.c_uint64),
         ("sampler_fp32_network", C.c_int), ("smearing", C.c_int),
         ("population_delta", C.c_double), ("sigma_min_eV", C.c_double),
-        ("reserved", C.c_int * 2),
+        ("window_final", C.c_int), ("reserved1", C.c_int),
     ]
 
 
@@ -205,7 +205,8 @@ def make_params(p=None, **kw) -> RTAParams:
             s.k_subset = arr.ctypes.data_as(C.POINTER(C.c_int32))
         elif key in ("T_K", "mu_eV", "sigma_eV", "window_eV", "delta_cut_sigmas", "omega_cut_eV", "degen_tol_eV"):
             setattr(s, key, float(val))
-        elif key in ("precision", "max_batch_states", "sampler", "seed", "sampler_fp32_network", "smearing"):
+        elif key in ("precision", "max_batch_states", "sampler", "seed", "sampler_fp32_network", "smearing",
+                     "window_final"):
             setattr(s, key, int(val))
         elif key in ("sample_fraction", "mix_alpha", "population_delta", "sigma_min_eV"):
             setattr(s, key, float(val))

@@ -329,6 +329,16 @@ __global__ void k_window_count(const double* __restrict__ epsF, const int* __res
   count[c] = cnt;
 }
 
+// Final-state window (Sec. 5.2 applied to both states of a transition): the FP32 energy of every
+// band that fails the initial states' window (FP64 test) is replaced by 3e38, so that no state can
+// reach it in the window listing of the grid-DFT stage 2.
+__global__ void k_final_window(const double* __restrict__ epsF, int64_t n, double mu, double window, double kT,
+                               double delta, float* __restrict__ epsf) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  if (!in_window(epsF[t], mu, window, kT, delta)) epsf[t] = 3.0e38f;
+}
+
 // Single-block exclusive scan of count[0..N) into offset[0..N], offset[N] = total.
 __global__ void k_scan_single_block(const int* __restrict__ count, int64_t N, int64_t* __restrict__ offset) {
   __shared__ int64_t part[1024];

@@ -70,7 +70,8 @@ struct DftXArgs {
   const int* st_b;            // [S]
   const double* epsF;         // [NF][nw]
   GridMap gm;
-  const float* epsf;          // [NF][nw] FP32 energies (window test)
+  const float* epsf;          // [NF][nw] FP32 energies (window test); bands excluded as final states
+                              // (final-state window) hold 3e38, out of every reach
   const float4* el4;          // [NF][nw] (eps hi, eps lo, f, 0)
   const float2* UH;           // [NF][nw][nw] conj(U[m][m'])
   const float2* ZT;           // [Nq][nm (v)][nm (sa)] mode factors, transposed
@@ -89,8 +90,7 @@ struct DftXArgs {
   // a state can reach the window when |eps_nk - eps_m'k+q| < omega_max + cut * width
   const float4* vel;
   float cB[9];
-  float sigma_min, omega_max, cut;
-};
+  float sigma_min, omega_max, cut;};
 
 // Launches both kernels for S states; -1 on a launch error, -2 for a (nw, 3na) without a kernel.
 int dft_launch(cudaStream_t st, const DftZArgs& z, const DftXArgs& x, int S, int nw, int nm, int ne_plane_max);

@@ -38,6 +38,8 @@ struct Lat9 {
   double a[9];  // lattice rows, Cartesian, A
 };
 __global__ void k_vel_input(const cplx* H, const int* R, Lat9 lat, int nR, int E, cplx* out);
+__global__ void k_final_window(const double* epsF, int64_t n, double mu, double window, double kT, double delta,
+                               float* epsf);
 __global__ void k_band_velocity(const cplx* dH, const cplx* U, int64_t P, int nw, float4* vel);
 __global__ void k_sep_table(const int* res, int B, int N, cplx* E);
 __global__ void k_sep_z(const cplx* in, const double* w, int E, int npair, const int* pair_off, const int* ent_c,

@@ -138,8 +138,11 @@ static int check_params(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, GridM
   if (!(p->degen_tol_eV >= 0.0)) return fail(c, PHOEBE_GPU_ERR_ARG, "degen_tol_eV must be >= 0");
   if (p->precision < PHOEBE_PREC_FP64 || p->precision > PHOEBE_PREC_FP32_DFT)
     return fail(c, PHOEBE_GPU_ERR_ARG, "unknown precision %d", p->precision);
-  for (int i = 0; i < 2; ++i)
-    if (p->reserved[i] != 0) return fail(c, PHOEBE_GPU_ERR_ARG, "reserved fields must be zero");
+  if (p->reserved1 != 0) return fail(c, PHOEBE_GPU_ERR_ARG, "reserved fields must be zero");
+  if (p->window_final != 0 && p->window_final != 1) return fail(c, PHOEBE_GPU_ERR_ARG, "window_final must be 0 or 1");
+  if (p->window_final == 1 && (p->precision != PHOEBE_PREC_FP32_DFT || p->sampler != PHOEBE_SAMPLER_FULL))
+    return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED,
+                "final-state windows are evaluated by the grid-DFT stage 2 (precision 7, full q sum)");
   if (p->smearing != 0 && p->smearing != 1) return fail(c, PHOEBE_GPU_ERR_ARG, "smearing must be 0 or 1");
   if (p->smearing == 1) {
     if (!(p->sigma_min_eV > 0.0)) return fail(c, PHOEBE_GPU_ERR_ARG, "sigma_min_eV must be > 0");

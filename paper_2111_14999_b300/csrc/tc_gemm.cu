@@ -1844,6 +1844,12 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
   c->launches += 1;
   float4* vel = nullptr;  // adaptive smearing: band velocities on the fine grid
   if (p->smearing == 1) TRY(velocity_grid(c, gm.nf, UF, &vel));
+  if (p->window_final == 1) {  // final-state window: excluded bands out of every reach
+    k_final_window<<<(unsigned)((NF * nw + 255) / 256), 256, 0, c->stream>>>(
+        epsF, NF * nw, p->mu_eV, p->window_eV, kBoltzmannEV * p->T_K, p->population_delta, epsf);
+    c->launches++;
+    CK(c, cudaGetLastError());
+  }
   CK(c, cudaGetLastError());
   unsigned long long ombits = 0;
   CK(c, cudaMemcpyAsync(&ombits, dmax, sizeof(ombits), cudaMemcpyDeviceToHost, c->stream));

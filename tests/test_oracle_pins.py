@@ -426,3 +426,32 @@ def test_adaptive_sigma_scaling():
     Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
     assert np.allclose(elph.adaptive_sigma(va @ Q, vb @ Q, lat @ Q, (8, 8, 8), 0.0), s8, rtol=1e-12)
     assert np.all(elph.adaptive_sigma(va, va, lat, (8, 8, 8), 1e-3) == 1e-3)
+
+
+def test_closed_form_einstein_linewidth_final_state_window():
+    # Sec. 5.2 windows on both states of a transition (window_final = 1): the Einstein closed form
+    # with the sum over k' restricted to |e_k' - mu| < window; initial states are those in the window.
+    lam, M, cvec, n, win = 0.215, 28.0, np.array([0.3, -0.2, 0.1]), 8, 0.43   # no energy on the edge
+    mat, prm = W.tb_einstein(eps0=0.05, t=0.25, lam=lam, c=cvec, mass=M, n=n, mu=0.1)
+    prm = prm.with_(window_eV=win, window_final=1)
+    ks, bs, gam = elph.linewidths_rta(mat, prm)
+    hw0 = HBAR * np.sqrt(EV / (ANG ** 2 * AMU)) / EV * np.sqrt(lam)
+    g0sq = np.sum(cvec ** 2) * (HBAR ** 2 / (AMU * EV * ANG ** 2)) / (2 * M * hw0)
+    idx = np.indices((n, n, n)).reshape(3, -1).T / n
+    eps_all = 0.05 - 2 * 0.25 * np.sum(np.cos(2 * np.pi * idx), axis=1)
+    inside = np.abs(eps_all - 0.1) < win
+    assert np.array_equal(ks, np.nonzero(inside)[0]) and 0 < inside.sum() < n ** 3
+    kT = 8.617333262e-5 * prm.T_K
+    n0 = 1.0 / np.expm1(hw0 / kT)
+    f = 1.0 / (np.exp((eps_all - 0.1) / kT) + 1.0)
+    s, cut = prm.sigma_eV, prm.delta_cut_sigmas
+
+    def dlt(x):
+        return np.where(np.abs(x) < cut * s, np.exp(-(x / s) ** 2) / (np.sqrt(np.pi) * s), 0.0)
+    want = []
+    for e in eps_all[inside]:
+        t = ((n0 + 1 - f) * dlt(e - hw0 - eps_all) + (n0 + f) * dlt(e + hw0 - eps_all)) * inside
+        want.append(2 * np.pi * g0sq * t.mean())
+    assert np.allclose(gam, want, rtol=1e-11, atol=1e-14)
+    wide = elph.linewidths_rta(mat, prm.with_(window_final=0))[2]
+    assert np.all(gam <= wide + 1e-15) and np.any(gam < wide - 1e-6)   # edge states lose transitions

@@ -86,6 +86,7 @@ class RTAParams:
     population_delta: float = 0.0   # > 0: population window f(1-f) > delta on initial states
     smearing: int = 0               # 0 fixed Gaussian width sigma_eV, 1 adaptive width per pair of states
     sigma_min_eV: float = 1e-3      # adaptive smearing: floor of the width
+    window_final: int = 0           # 1: final states (k+q, m') also pass the window
 
     def with_(self, **kw) -> "RTAParams":
         return replace(self, **kw)
