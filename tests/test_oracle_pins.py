@@ -455,3 +455,69 @@ def test_closed_form_einstein_linewidth_final_state_window():
     assert np.allclose(gam, want, rtol=1e-11, atol=1e-14)
     wide = elph.linewidths_rta(mat, prm.with_(window_final=0))[2]
     assert np.all(gam <= wide + 1e-15) and np.any(gam < wide - 1e-6)   # edge states lose transitions
+
+
+def _polar_si(alpha=1.0):
+    mat, prm = W.si_like(seed=0, nk=4)
+    zs = np.diag([2.0, 2.2, 1.8])
+    return mat, prm, {"Zstar": np.stack([zs, -zs]), "eps_inf": np.array([[9.0, 0.5, 0.0], [0.5, 10.0, 0.2],
+                                                                        [0.0, 0.2, 11.0]]), "alpha": alpha}
+
+
+def test_coulomb_constant():
+    e, eps0 = 1.602176634e-19, 8.8541878128e-12          # CODATA 2018
+    assert elph.E2_4PI_EPS0_EV_A == pytest.approx(e / (4 * np.pi * eps0) * 1e10, rel=1e-12)
+
+
+def test_polar_long_range_small_q_limit():
+    # Sec. 3.2 Eq. polarlong: as q -> 0 only the G = 0 term diverges, so for the optical modes
+    # |q| L_q -> i (4 pi/V) e^2/(4 pi eps0) sum_s (qhat . Z*_s . Zq_s) / (qhat . eps . qhat)
+    mat, prm, pol = _polar_si()
+    A = mat.lattice
+    B = 2 * np.pi * np.linalg.inv(A).T
+    V = abs(np.linalg.det(A))
+    direction = np.array([0.3, -0.2, 0.5])
+    errs = []
+    for d in (1e-3, 1e-4):
+        q = d * direction[None, :]
+        om, z = elph.phonon_modes(q, mat)
+        Zq = elph.mode_factors(om, z, mat.mass_amu, prm.omega_cut_eV)
+        L = elph.polar_long_range(q, mat, pol, Zq)[0]
+        qc = q[0] @ B
+        qh = qc / np.linalg.norm(qc)
+        want = np.zeros(6, dtype=complex)
+        for s in range(2):
+            want += (qh @ pol["Zstar"][s]) @ Zq[0, 3 * s:3 * s + 3, :]
+        want *= 1j * 4 * np.pi / V * elph.E2_4PI_EPS0_EV_A / (qh @ pol["eps_inf"] @ qh)
+        got = np.linalg.norm(qc) * L
+        errs.append(np.max(np.abs(got[3:] - want[3:])) / np.max(np.abs(want[3:])))
+    assert errs[1] < 1e-3 and errs[1] < errs[0] / 5          # converges linearly in |q|
+
+
+def test_polar_long_range_scalings():
+    # linear in Z*; unchanged under eps -> c eps with alpha -> c alpha up to 1/c; a dead mode gives 0
+    mat, prm, pol = _polar_si()
+    q = np.array([[0.25, 0.0, 0.5], [0.1, 0.2, 0.3]])
+    om, z = elph.phonon_modes(q, mat)
+    Zq = elph.mode_factors(om, z, mat.mass_amu, prm.omega_cut_eV)
+    L = elph.polar_long_range(q, mat, pol, Zq)
+    L2 = elph.polar_long_range(q, mat, {**pol, "Zstar": 1.5 * pol["Zstar"]}, Zq)
+    assert np.allclose(L2, 1.5 * L, rtol=1e-12)
+    L3 = elph.polar_long_range(q, mat, {**pol, "eps_inf": 2 * pol["eps_inf"], "alpha": 2.0}, Zq)
+    assert np.allclose(L3, L / 2, rtol=1e-10)
+    Zd = Zq.copy()
+    Zd[:, :, 4] = 0.0
+    assert np.all(elph.polar_long_range(q, mat, pol, Zd)[:, 4] == 0)
+    assert np.max(np.abs(L)) > 1e-3
+
+
+def test_polar_coupling_adds_coherently():
+    # g = g^S + L_q [U_{k+q}^dagger U_k]: doubling L (Z* -> 2 Z*) with g^S = 0 quadruples Gamma
+    mat, prm, pol = _polar_si()
+    mat0 = W.Material(**{**mat.__dict__, "g": 0.0 * mat.g})
+    ks, bs, g1 = elph.linewidths_rta(mat0, prm, k_indices=[0, 5], polar=pol)
+    _, _, g2 = elph.linewidths_rta(mat0, prm, k_indices=[0, 5], polar={**pol, "Zstar": 2 * pol["Zstar"]})
+    assert np.all(g1 > 0) and np.allclose(g2, 4 * g1, rtol=1e-10)
+    _, _, gs = elph.linewidths_rta(mat, prm, k_indices=[0, 5])
+    _, _, gt = elph.linewidths_rta(mat, prm, k_indices=[0, 5], polar=pol)
+    assert not np.allclose(gt, gs + g1, rtol=1e-3)           # interference between g^S and g^L
