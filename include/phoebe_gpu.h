@@ -103,6 +103,19 @@ int phoebe_gpu_set_force_constants(phoebe_gpu_ctx* ctx, int na, const double* ma
  * reciprocal vectors).  ERR_ARG for a singular lattice. */
 int phoebe_gpu_set_lattice(phoebe_gpu_ctx* ctx, const double* lattice);
 
+/* Polar long-range coupling (Sec. 3.2, Eq. polarlong), added to the interpolated g before |g|^2:
+ *   g^L_{m'n nu}(k,q) = L_{q nu} [U_{k+q}^dagger U_k]_{m'n},
+ *   L_{q nu} = i (4 pi/V) e^2/(4 pi eps0) sum_s sum_{G, q+G != 0} [(q+G).Z*_s.Z_q[s.][nu]] /
+ *              [(q+G).eps_inf.(q+G)] exp(-(q+G).eps_inf.(q+G) / (4 alpha)),
+ * Z_q the mode factors of Eq. 7 (A), V the cell volume, terms with exponent >= 25 dropped.
+ *   Zstar    na x 3 x 3 Born effective charges (Zstar[s][a][b], row a contracted with q+G)
+ *   eps_inf  3 x 3 high-frequency dielectric tensor (symmetric positive definite)
+ *   alpha    Gaussian filter, 1/A^2 (> 0); Zstar == NULL switches the term off.
+ * Needs set_force_constants (na) and set_lattice; used by linewidths_rta with precision
+ * PHOEBE_PREC_FP32_DFT (ERR_UNSUPPORTED for other precisions, sampled q sums, adaptive smearing
+ * and phonon_rates_elph while it is on). */
+int phoebe_gpu_set_polar(phoebe_gpu_ctx* ctx, const double* Zstar, const double* eps_inf, double alpha);
+
 /* Electron-phonon coupling in the Wannier representation (Sec. 3.2, Eq. 13).
  *   Re, we  n_Re electron lattice vectors and weights (NULL = 1)
  *   Rp, wp  n_Rp phonon lattice vectors and weights (NULL = 1)

@@ -38,6 +38,7 @@ EXPORTED = (
     "phoebe_gpu_mlp_loss_grad", "phoebe_gpu_is_uniforms", "phoebe_gpu_mlp_scores",
     "phoebe_gpu_batch_opts_default", "phoebe_gpu_linewidths_rta_batch", "phoebe_gpu_transport_rta",
     "phoebe_gpu_selftest_wait", "phoebe_gpu_phonon_rates_elph", "phoebe_gpu_set_lattice",
+    "phoebe_gpu_set_polar",
 )
 
 
@@ -139,6 +140,7 @@ def _load() -> C.CDLL:
         "phoebe_gpu_transport_rta": (I, [P, C.POINTER(RTAParams), P, P, P, P]),
         "phoebe_gpu_phonon_rates_elph": (I, [P, C.POINTER(RTAParams), C.c_int64, P]),
         "phoebe_gpu_set_lattice": (I, [P, P]),
+        "phoebe_gpu_set_polar": (I, [P, P, P, C.c_double]),
         "phoebe_gpu_selftest_wait": (I, [P, I, I64]),
     }
     for name, (res, args) in sig.items():
@@ -276,6 +278,16 @@ class PhoebeGPU:
         if getattr(mat, "lattice", None) is not None:
             self.set_lattice(mat.lattice)
         self.nw, self.na = int(mat.nw), int(mat.na)
+
+    def set_polar(self, Zstar=None, eps_inf=None, alpha: float = 1.0):
+        """Born charges (na, 3, 3), eps_inf (3, 3) and the Gaussian filter alpha (1/A^2) of the polar
+        long-range coupling; Zstar=None switches it off."""
+        if Zstar is None:
+            self._check(lib.phoebe_gpu_set_polar(self._ctx, None, None, C.c_double(0.0)))
+            return
+        zs = np.ascontiguousarray(Zstar, dtype=np.float64).reshape(-1)
+        ep = np.ascontiguousarray(eps_inf, dtype=np.float64).reshape(9)
+        self._check(lib.phoebe_gpu_set_polar(self._ctx, _ptr(zs), _ptr(ep), C.c_double(alpha)))
 
     def set_lattice(self, lattice):
         """Primitive lattice vectors (rows, Cartesian, Angstrom)."""

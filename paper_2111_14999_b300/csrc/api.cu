@@ -336,6 +336,28 @@ void phoebe_gpu_rta_params_default(phoebe_gpu_rta_params* p) {
   p->sigma_min_eV = 1e-3;
 }
 
+int phoebe_gpu_set_polar(phoebe_gpu_ctx* c, const double* Zstar, const double* eps_inf, double alpha) {
+  if (!c) return PHOEBE_GPU_ERR_ARG;
+  if (!Zstar) {
+    c->have_polar = false;
+    return PHOEBE_GPU_OK;
+  }
+  if (!c->have_Phi) return fail(c, PHOEBE_GPU_ERR_ORDER, "set_polar needs set_force_constants first");
+  if (!eps_inf || !(alpha > 0.0)) return fail(c, PHOEBE_GPU_ERR_ARG, "eps_inf must be given and alpha > 0");
+  const double* e = eps_inf;
+  const double det = e[0] * (e[4] * e[8] - e[5] * e[7]) - e[1] * (e[3] * e[8] - e[5] * e[6]) +
+                     e[2] * (e[3] * e[7] - e[4] * e[6]);
+  const double m2 = e[0] * e[4] - e[1] * e[3];
+  if (!(e[0] > 0.0 && m2 > 0.0 && det > 0.0) || fabs(e[1] - e[3]) > 1e-12 || fabs(e[2] - e[6]) > 1e-12 ||
+      fabs(e[5] - e[7]) > 1e-12)
+    return fail(c, PHOEBE_GPU_ERR_ARG, "eps_inf must be symmetric positive definite");
+  c->zstar.assign(Zstar, Zstar + 9 * c->na);
+  for (int i = 0; i < 9; ++i) c->eps_inf[i] = e[i];
+  c->polar_alpha = alpha;
+  c->have_polar = true;
+  return PHOEBE_GPU_OK;
+}
+
 int phoebe_gpu_set_lattice(phoebe_gpu_ctx* c, const double* lattice) {
   if (!c) return PHOEBE_GPU_ERR_ARG;
   if (!lattice) return fail(c, PHOEBE_GPU_ERR_ARG, "lattice is NULL");

@@ -15,6 +15,7 @@ constexpr double kHbarOmegaEV = 0.06465415130134121;       // hbar*sqrt(eV/(A^2 
 constexpr double kHbar2AmuEvA2 = 0.004180159280496722;     // hbar^2/(amu eV A^2)
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kSqrtPi = 1.77245385090551602730;
+constexpr double kCoulombEVA = 14.399645478425668;  // e^2 / (4 pi eps0), eV A
 
 constexpr int kMaxNw = 32;      // Wannier functions
 constexpr int kMaxModes = 30;   // 3 * atoms (10 atoms)

@@ -309,7 +309,7 @@ __device__ __forceinline__ float adaptive_width(const float4 va, const float4 vb
 // take one listed q, sum over the rows (dft_x_line), apply U_{k+q}^dagger (partial sums over m
 // combined by shuffles), Z_q and the delta weights of every listed m'.  q whose bands all miss
 // the window contribute nothing to Eq. 29 and are not evaluated.
-template <int NW, int NM, int SPLIT, bool PR, int NQ, bool AD>
+template <int NW, int NM, int SPLIT, bool PR, int NQ, bool AD, bool PL>
 __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT_MINB2) k_dft_yx_elph(DftXArgs a) {
   constexpr int E = NW * NM, MW = NW / SPLIT, ES = dft_row_stride(E, NW);
   constexpr int L = kDftLines, UL = kDftUnitLines;
@@ -332,6 +332,7 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
   __shared__ float en_s[2];
   __shared__ double pw_s;
   __shared__ float4 vn_s;  // adaptive smearing: hbar v of the initial state
+  __shared__ float2 uk_s[NW];  // polar term: U_k[m][n] of the initial state
   __shared__ double red[kDftXThreads / 32];
   const int s = blockIdx.y, jz = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -342,6 +343,11 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
     en_s[0] = (float)e_n;
     en_s[1] = (float)(e_n - (double)en_s[0]);
     if (AD) vn_s = a.vel[a.gm.k_to_fine(a.st_k[s]) * NW + a.st_b[s]];
+    if (PL)
+      for (int m = 0; m < NW; ++m) {
+        const cplx u = a.UF[(a.gm.k_to_fine(a.st_k[s]) * NW + m) * NW + a.st_b[s]];
+        uk_s[m] = make_float2((float)u.re, (float)u.im);
+      }
     if (PR) {  // f (1 - f) / kT of the initial state (the df/de replacement of the rate)
       const double fn = 1.0 / (exp((e_n - a.mu) * a.inv_kT) + 1.0);
       pw_s = fn * (1.0 - fn) * a.inv_kT;
@@ -609,12 +615,25 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
               t[sa].y = fmaf(uu[mm].x, G[u][sa][mm].y, fmaf(uu[mm].y, G[u][sa][mm].x, t[sa].y));
             }
           }
+          float2 ov = make_float2(0.f, 0.f);  // polar term: [U_{k+q}^dagger U_k]_{m'n}, lane's m range
+          if constexpr (PL) {
+#pragma unroll
+            for (int mm = 0; mm < MW; ++mm) {
+              const float2 w = uk_s[j * MW + mm];
+              ov.x = fmaf(uu[mm].x, w.x, fmaf(-uu[mm].y, w.y, ov.x));
+              ov.y = fmaf(uu[mm].x, w.y, fmaf(uu[mm].y, w.x, ov.y));
+            }
+          }
 #pragma unroll
           for (int o = 1; o < SPLIT; o <<= 1) {
 #pragma unroll
             for (int sa = 0; sa < NM; ++sa) {
               t[sa].x += __shfl_xor_sync(gmask, t[sa].x, o);
               t[sa].y += __shfl_xor_sync(gmask, t[sa].y, o);
+            }
+            if constexpr (PL) {
+              ov.x += __shfl_xor_sync(gmask, ov.x, o);
+              ov.y += __shfl_xor_sync(gmask, ov.y, o);
             }
           }
           for (int v = j; v < NM; v += SPLIT) {
@@ -625,6 +644,11 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
             for (int sa = 0; sa < NM; ++sa) {
               g.x = fmaf(t[sa].x, z[sa].x, fmaf(-t[sa].y, z[sa].y, g.x));
               g.y = fmaf(t[sa].x, z[sa].y, fmaf(t[sa].y, z[sa].x, g.y));
+            }
+            if constexpr (PL) {  // + g^L = L_{q nu} [U_{k+q}^dagger U_k]_{m'n}
+              const float2 l = __ldg(a.gL + (int64_t)q * NM + v);
+              g.x = fmaf(l.x, ov.x, fmaf(-l.y, ov.y, g.x));
+              g.y = fmaf(l.x, ov.y, fmaf(l.y, ov.x, g.y));
             }
             const float2 on = __ldg(onb + v);
             const float t1 = (dm - on.x) * inv_s;
@@ -657,22 +681,26 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
   }
 }
 
-template <int NW, int NM, int SPLIT, bool PR, int NQ, bool AD>
+template <int NW, int NM, int SPLIT, bool PR, int NQ, bool AD, bool PL = false>
 static int launch_yx_t(cudaStream_t st, const DftXArgs& a, int S) {
   const size_t smem = dft_smem_bytes(a.P, a.Bx, a.By, NW, NM, a.Nx, a.Ny, a.K);
-  if (cudaFuncSetAttribute(k_dft_yx_elph<NW, NM, SPLIT, PR, NQ, AD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(k_dft_yx_elph<NW, NM, SPLIT, PR, NQ, AD, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return -1;
   dim3 grid((unsigned)a.Nz, (unsigned)S);
-  k_dft_yx_elph<NW, NM, SPLIT, PR, NQ, AD><<<grid, kDftXThreads, smem, st>>>(a);
+  k_dft_yx_elph<NW, NM, SPLIT, PR, NQ, AD, PL><<<grid, kDftXThreads, smem, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 // Two q per lane group when a warp's 32 consecutive q span at most two lines (Nx >= 32).  The
-// phonon-electron rates and the adaptive width are not combined (the host rejects it).
+// phonon-electron rates, the adaptive width and the polar term are not combined (the host
+// rejects it).
 template <int NW, int NM, int SPLIT>
 static int launch_yx(cudaStream_t st, const DftXArgs& a, int S) {
   const bool pair = kDftQPair && a.Nx >= 32;
+  if (a.gL)
+    return pair ? launch_yx_t<NW, NM, SPLIT, false, 2, false, true>(st, a, S)
+                : launch_yx_t<NW, NM, SPLIT, false, 1, false, true>(st, a, S);
   if (a.vel)
     return pair ? launch_yx_t<NW, NM, SPLIT, false, 2, true>(st, a, S)
                 : launch_yx_t<NW, NM, SPLIT, false, 1, true>(st, a, S);
@@ -703,6 +731,44 @@ size_t dft_smem_bytes(int P, int Bx, int By, int nw, int nm, int Nx, int Ny, int
 
 size_t dft_z_smem_bytes(int ne_plane_max, int E, int Nz, int Bz) {
   return sizeof(float2) * ((size_t)ne_plane_max * E + (size_t)Nz * Bz) + sizeof(int) * (size_t)ne_plane_max;
+}
+
+// L_{q nu} of the polar long-range coupling (Sec. 3.2, Eq. polarlong), one thread per (q, nu):
+// i pref sum_G sum_s [(q+G).Z*_s.Zq[s.][nu]] e^{-x/(4 alpha)} / x, x = (q+G).eps.(q+G), over the G box
+// with q+G != 0 and x / (4 alpha) < cut; FP64 sums, FP32 result.
+__global__ void k_polar_q(PolarArgs a) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= a.Q * a.nm) return;
+  const int64_t q = t / a.nm;
+  const int nu = (int)(t % a.nm);
+  const int j2 = (int)(q % a.N[2]), j1 = (int)((q / a.N[2]) % a.N[1]), j0 = (int)(q / ((int64_t)a.N[2] * a.N[1]));
+  const double qf[3] = {(double)j0 / a.N[0], (double)j1 / a.N[1], (double)j2 / a.N[2]};
+  double re = 0.0, im = 0.0;
+  for (int g0 = -a.nmax[0]; g0 <= a.nmax[0]; ++g0)
+    for (int g1 = -a.nmax[1]; g1 <= a.nmax[1]; ++g1)
+      for (int g2 = -a.nmax[2]; g2 <= a.nmax[2]; ++g2) {
+        const double f0 = qf[0] + g0, f1 = qf[1] + g1, f2 = qf[2] + g2;
+        double K[3];
+        for (int c = 0; c < 3; ++c) K[c] = f0 * a.B[c] + f1 * a.B[3 + c] + f2 * a.B[6 + c];
+        double x = 0.0;
+        for (int r = 0; r < 3; ++r)
+          for (int c = 0; c < 3; ++c) x += K[r] * a.eps[3 * r + c] * K[c];
+        if (!(x > 1e-14) || x / (4.0 * a.alpha) >= a.cut) continue;
+        const double fac = exp(-x / (4.0 * a.alpha)) / x;
+        for (int s = 0; s < a.na; ++s)
+          for (int b = 0; b < 3; ++b) {
+            const double kz = K[0] * a.zstar[9 * s + b] + K[1] * a.zstar[9 * s + 3 + b] + K[2] * a.zstar[9 * s + 6 + b];
+            const cplx z = a.Zq[(q * a.nm + 3 * s + b) * a.nm + nu];
+            re += fac * kz * z.re;
+            im += fac * kz * z.im;
+          }
+      }
+  a.out[t] = make_float2((float)(-a.pref * im), (float)(a.pref * re));  // i * pref * sum
+}
+
+int polar_table(cudaStream_t st, const PolarArgs& a) {
+  k_polar_q<<<(unsigned)((a.Q * a.nm + 127) / 128), 128, 0, st>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 // Phonon-electron rates from the accumulated sums (Sec. 4.3): P_{q nu} = (2 pi / N_k) n (n + 1)

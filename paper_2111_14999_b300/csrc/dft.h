@@ -90,7 +90,23 @@ struct DftXArgs {
   // a state can reach the window when |eps_nk - eps_m'k+q| < omega_max + cut * width
   const float4* vel;
   float cB[9];
-  float sigma_min, omega_max, cut;};
+  float sigma_min, omega_max, cut;
+  // polar long-range term (optional, gL == nullptr = off): g += gL[q][nu] [U_{k+q}^dagger U_k]_{m'n}
+  const float2* gL;           // [Nq][nm]
+  const cplx* UF;             // [NF][nw][nw] eigenvectors (the initial state's column is staged)
+};
+
+// q-only factor of the polar long-range coupling on the q grid (see phoebe_gpu_set_polar).
+struct PolarArgs {
+  const double* zstar;        // [na][3][3]
+  const cplx* Zq;             // [Q][nm][nm] mode factors of Eq. 7
+  float2* out;                // [Q][nm]
+  int64_t Q;
+  int na, nm, N[3], nmax[3];
+  double B[9];                // reciprocal rows b_i (1/A), B[3 i + c]
+  double eps[9];
+  double alpha, cut, pref;    // pref = (4 pi / V) e^2 / (4 pi eps0)
+};
 
 // Launches both kernels for S states; -1 on a launch error, -2 for a (nw, 3na) without a kernel.
 int dft_launch(cudaStream_t st, const DftZArgs& z, const DftXArgs& x, int S, int nw, int nm, int ne_plane_max);
@@ -106,6 +122,7 @@ __host__ __device__ constexpr int dft_split(int nw) { return nw == 8 ? kDftSplit
 size_t dft_smem_bytes(int P, int Bx, int By, int nw, int nm, int Nx, int Ny, int K);
 size_t dft_z_smem_bytes(int ne_plane_max, int E, int Nz, int Bz);
 int dft_table(cudaStream_t st, const int* res, int B, int N, float2* E);
+int polar_table(cudaStream_t st, const PolarArgs& a);
 // P[q][nu] from pacc (see DftXArgs::pacc); pref = 2 pi / (N_k sqrt(pi) sigma).  -2 if nm > 32.
 int prate_finish(cudaStream_t st, const double* acc, const double* omega, const double* nB, int64_t Q, int nm,
                  double pref, double omega_cut, double degen_tol, double* P);

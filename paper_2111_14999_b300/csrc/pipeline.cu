@@ -139,6 +139,16 @@ static int check_params(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, GridM
   if (p->precision < PHOEBE_PREC_FP64 || p->precision > PHOEBE_PREC_FP32_DFT)
     return fail(c, PHOEBE_GPU_ERR_ARG, "unknown precision %d", p->precision);
   if (p->reserved1 != 0) return fail(c, PHOEBE_GPU_ERR_ARG, "reserved fields must be zero");
+  if (c->have_polar) {
+    if (p->precision != PHOEBE_PREC_FP32_DFT || p->sampler != PHOEBE_SAMPLER_FULL || p->smearing != 0 ||
+        c->prate_acc)
+      return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED,
+                  "the polar long-range term is evaluated by the grid-DFT linewidths (precision 7, full q sum, "
+                  "fixed smearing)");
+    if (!c->have_lattice) return fail(c, PHOEBE_GPU_ERR_ORDER, "the polar term needs set_lattice first");
+    if ((int)c->zstar.size() != 9 * c->na)
+      return fail(c, PHOEBE_GPU_ERR_SHAPE, "Born charges were set for another atom count");
+  }
   if (p->window_final != 0 && p->window_final != 1) return fail(c, PHOEBE_GPU_ERR_ARG, "window_final must be 0 or 1");
   if (p->window_final == 1 && (p->precision != PHOEBE_PREC_FP32_DFT || p->sampler != PHOEBE_SAMPLER_FULL))
     return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED,

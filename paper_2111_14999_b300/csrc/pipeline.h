@@ -50,6 +50,11 @@ struct phoebe_gpu_ctx {
   // primitive lattice vectors (rows, Cartesian, A), set by phoebe_gpu_set_lattice
   bool have_lattice = false;
   double lattice[9] = {0};
+  // polar long-range coupling, set by phoebe_gpu_set_polar
+  bool have_polar = false;
+  std::vector<double> zstar;  // [na][3][3]
+  double eps_inf[9] = {0};
+  double polar_alpha = 0.0;
 };
 
 // Stage-2 work of one material recorded for later issue (batch.cu): each op launches

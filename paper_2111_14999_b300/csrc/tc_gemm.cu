@@ -1844,6 +1844,67 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
   c->launches += 1;
   float4* vel = nullptr;  // adaptive smearing: band velocities on the fine grid
   if (p->smearing == 1) TRY(velocity_grid(c, gm.nf, UF, &vel));
+  float2* gL = nullptr;  // polar long-range term: L_{q nu} on the q grid
+  if (c->have_polar) {
+    gL = (float2*)ensure(c, "dft_gL", sizeof(float2) * Nq * nm, &st);
+    if (!gL) return st;
+    void* d_zs;
+    TRY(upload(c, "polar_zstar", c->zstar.data(), sizeof(double) * 9 * c->na, &d_zs));
+    PolarArgs pa;
+    pa.zstar = (const double*)d_zs;
+    pa.Zq = Zq;
+    pa.out = gL;
+    pa.Q = Nq;
+    pa.na = c->na;
+    pa.nm = nm;
+    for (int d = 0; d < 3; ++d) pa.N[d] = gm.nq[d];
+    const double* A = c->lattice;
+    const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                       A[2] * (A[3] * A[7] - A[4] * A[6]);
+    const double inv[9] = {(A[4] * A[8] - A[5] * A[7]) / det, (A[2] * A[7] - A[1] * A[8]) / det,
+                           (A[1] * A[5] - A[2] * A[4]) / det, (A[5] * A[6] - A[3] * A[8]) / det,
+                           (A[0] * A[8] - A[2] * A[6]) / det, (A[2] * A[3] - A[0] * A[5]) / det,
+                           (A[3] * A[7] - A[4] * A[6]) / det, (A[1] * A[6] - A[0] * A[7]) / det,
+                           (A[0] * A[4] - A[1] * A[3]) / det};
+    for (int i = 0; i < 3; ++i)  // b_i = 2 pi (row i of (A^-1)^T) = 2 pi (column i of A^-1)
+      for (int cc = 0; cc < 3; ++cc) pa.B[3 * i + cc] = 2.0 * kPi * inv[3 * cc + i];
+    for (int i = 0; i < 9; ++i) pa.eps[i] = c->eps_inf[i];
+    pa.alpha = c->polar_alpha;
+    pa.cut = 25.0;
+    pa.pref = 4.0 * kPi / fabs(det) * kCoulombEVA;
+    // G box: |q+G|^2 <= 4 alpha cut / lambda_min(eps) for every q of the first cell
+    // smallest eigenvalue of the symmetric eps (trigonometric solution of the characteristic cubic)
+    const double* ep = c->eps_inf;
+    double lmin;
+    {
+      const double p1 = ep[1] * ep[1] + ep[2] * ep[2] + ep[5] * ep[5];
+      if (p1 == 0.0) {
+        lmin = std::min(ep[0], std::min(ep[4], ep[8]));
+      } else {
+        const double qm = (ep[0] + ep[4] + ep[8]) / 3.0;
+        const double p2 = (ep[0] - qm) * (ep[0] - qm) + (ep[4] - qm) * (ep[4] - qm) + (ep[8] - qm) * (ep[8] - qm) +
+                          2.0 * p1;
+        const double pp = sqrt(p2 / 6.0);
+        double Bm[9];
+        for (int i = 0; i < 9; ++i) Bm[i] = (ep[i] - (i % 4 == 0 ? qm : 0.0)) / pp;
+        const double r = 0.5 * (Bm[0] * (Bm[4] * Bm[8] - Bm[5] * Bm[7]) - Bm[1] * (Bm[3] * Bm[8] - Bm[5] * Bm[6]) +
+                                Bm[2] * (Bm[3] * Bm[7] - Bm[4] * Bm[6]));
+        const double phi = acos(std::max(-1.0, std::min(1.0, r))) / 3.0;
+        lmin = qm + 2.0 * pp * cos(phi + 2.0 * kPi / 3.0);
+      }
+    }
+    lmin *= 0.999;  // a bound: a slightly larger box is harmless
+    const double kmax = sqrt(4.0 * pa.alpha * pa.cut / lmin);
+    for (int i = 0; i < 3; ++i) {
+      const double len = sqrt(A[3 * i] * A[3 * i] + A[3 * i + 1] * A[3 * i + 1] + A[3 * i + 2] * A[3 * i + 2]);
+      pa.nmax[i] = (int)ceil(kmax / (2.0 * kPi) * len) + 1;
+    }
+    if (polar_table(c->stream, pa)) {
+      cudaGetLastError();
+      return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the polar long-range table failed");
+    }
+    c->launches++;
+  }
   if (p->window_final == 1) {  // final-state window: excluded bands out of every reach
     k_final_window<<<(unsigned)((NF * nw + 255) / 256), 256, 0, c->stream>>>(
         epsF, NF * nw, p->mu_eV, p->window_eV, kBoltzmannEV * p->T_K, p->population_delta, epsf);
@@ -2058,6 +2119,8 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
     x.mu = p->mu_eV;
     x.inv_kT = 1.0 / (kBoltzmannEV * p->T_K);
     x.vel = vel;
+    x.gL = gL;
+    x.UF = UF;
     x.sigma_min = (float)p->sigma_min_eV;
     x.omega_max = (float)omega_max;
     x.cut = (float)p->delta_cut_sigmas;
