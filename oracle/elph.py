@@ -38,6 +38,7 @@ __all__ = [
     "rotate_final", "bloch_coupling", "couplings_for_pairs",
     "active_states", "fine_grid", "electron_table", "linewidths_rta", "contributions",
     "phonon_rates_elph", "adaptive_sigma", "in_window", "polar_long_range", "E2_4PI_EPS0_EV_A",
+    "v3_coupling", "three_phonon_diag",
 ]
 
 
@@ -585,6 +586,91 @@ def phonon_rates_elph(mat, params, table=None):
             grp = np.abs(omega[iq] - omega[iq, nu]) < params.degen_tol_eV
             out[iq, nu] = P[iq, grp].mean()
     return out
+
+
+# ---------------------------------------------------- three-phonon coupling (Sec. 3.1, Sec. 4.3)
+
+def v3_coupling(q, qp, qpp, mat, anh, omega_cut: float = 1e-4) -> np.ndarray:
+    """V3(q nu, q' nu', q'' nu'') for explicit triples (Sec. 3.1, Eq. 3PhCouplingInterpolation):
+
+    V3 = sum_{R R'} sum_{a b c} sum_{s s' s''} w e^{-i (q.R + q'.R')} V3(s a R, s' b R', s'' c 0)
+         conj(Z_q[s a, nu]) conj(Z_q'[s' b, nu']) conj(Z_q''[s'' c, nu'']),
+
+    Z the mode factors of Eq. 7 (eigenvector times sqrt(hbar^2 / (2 M_s hbar w))).  Readings: the
+    printed sqrt(m m m / (w w w)) with (2/hbar)^{3/2} is read as these mode factors (masses in
+    the denominator, as Eq. 7 has them; the printed form would make V3 grow with the masses);
+    1/N0^3 is folded into the input; dead modes give 0.  q, qp, qpp: (n, 3) crystal coordinates.
+    Returns (n, 3na, 3na, 3na) complex, eV.
+    """
+    q, qp, qpp = (np.atleast_2d(x) for x in (q, qp, qpp))
+    Zs = []
+    for x in (q, qp, qpp):
+        om, z = phonon_modes(x, mat)
+        Zs.append(mode_factors(om, z, mat.mass_amu, omega_cut))
+    ph = np.exp(-2j * np.pi * (q @ anh.R.T.astype(np.float64) + qp @ anh.Rp.T.astype(np.float64)))  # (n, pairs)
+    T = np.einsum("np,p,pabc->nabc", ph, anh.w, anh.Phi3)
+    return np.einsum("nabc,nai,nbj,nck->nijk", T, np.conj(Zs[0]), np.conj(Zs[1]), np.conj(Zs[2]))
+
+
+def three_phonon_diag(mat, anh, params, q_indices=None) -> np.ndarray:
+    """Three-phonon part of the diagonal of the phonon scattering matrix A (Sec. 4.3):
+
+    A_{q nu} = sum_{q' nu' nu''} [ P^{q'' nu''}_{q nu, q' nu'} + P^{q' nu', q'' nu''}_{q nu} / 2 ]
+             = (2 pi / N_q) sum_{q~ nu' nu''} |W|^2 [ n n' (n''+1) d(w + w' - w'')
+                                                   + (1/2) n (n'+1)(n''+1) d(w - w' - w'') ],
+
+    W = V3(q nu, q~ nu', -q'' nu'') with q'' = q + q~ on the grid (the Kronecker delta of the
+    sum over G): the coalescence partner is q' = q~, the decay partner q' = -q~, and both use
+    |V3(q, q~, -(q + q~))|^2 (w', n' are even in q').  Readings: hbar = 1 energy units (A in
+    eV); delta the truncated Gaussian of Eq. 61 with the fixed sigma; modes dead at any of
+    the three wavevectors contribute nothing; A averaged over modes degenerate within
+    degen_tol at the same q.  Returns (len(q_indices) or N_q, 3na).
+    """
+    nq = tuple(int(x) for x in params.nq)
+    qpts = grid_points(nq)
+    Nq = len(qpts)
+    omega, z = phonon_modes(qpts, mat)
+    Zq = mode_factors(omega, z, mat.mass_amu, params.omega_cut_eV)
+    nB = bose_einstein(omega, params.T_K)
+    alive = omega >= params.omega_cut_eV
+    sigma, cut = params.sigma_eV, params.delta_cut_sigmas
+    Rps = sorted({tuple(r) for r in anh.Rp})
+    rp_index = {r: i for i, r in enumerate(Rps)}
+    rp_of_pair = np.array([rp_index[tuple(r)] for r in anh.Rp])
+    Rp_arr = np.array(Rps, dtype=np.float64)
+    ph2 = np.exp(-2j * np.pi * (qpts @ Rp_arr.T))                   # (N_q~, R') = e^{-i q~.R'}
+    grid = np.indices(nq).reshape(3, -1).T
+    qi_list = np.arange(Nq) if q_indices is None else np.asarray(q_indices)
+    out = np.zeros((len(qi_list), omega.shape[1]))
+    for row, iq in enumerate(qi_list):
+        # stage 1 at fixed q: A[R'][nu][s'b][s''c] = sum_{R} w e^{-i q.R} sum_{s a} Phi3 conj(Z_q[s a, nu])
+        ph1 = anh.w * np.exp(-2j * np.pi * (anh.R.astype(np.float64) @ qpts[iq]))
+        A = np.zeros((len(Rps),) + (omega.shape[1],) * 3, dtype=np.complex128)
+        np.add.at(A, rp_of_pair, np.einsum("p,pabc,an->pnbc", ph1, anh.Phi3, np.conj(Zq[iq])))
+        # stage 2 over q~: B[q~][nu][s'b][s''c] = sum_R' e^{-i q~.R'} A[R']
+        B = np.einsum("tr,rnbc->tnbc", ph2, A)
+        j = grid[iq]
+        jq2 = (j[None, :] + grid) % np.array(nq)                       # q'' = q + q~
+        i2 = (jq2[:, 0] * nq[1] + jq2[:, 1]) * nq[2] + jq2[:, 2]
+        jm = (-jq2) % np.array(nq)                                     # -q''
+        im = (jm[:, 0] * nq[1] + jm[:, 1]) * nq[2] + jm[:, 2]
+        W = np.einsum("tnbc,tbi,tck->tnik", B, np.conj(Zq), np.conj(Zq[im]))
+        w0 = omega[iq][None, :, None, None]
+        w1 = omega[:, None, :, None]
+        w2 = omega[i2][:, None, None, :]
+        n0, n1, n2 = nB[iq][None, :, None, None], nB[:, None, :, None], nB[i2][:, None, None, :]
+        ok = alive[iq][None, :, None, None] & alive[:, None, :, None] & alive[i2][:, None, None, :] & alive[im][:, None, None, :]
+        n1s, n2s = np.where(ok, n1, 0.0), np.where(ok, n2, 0.0)
+        wt = (n0 * n1s * (n2s + 1.0) * gaussian_delta(w0 + w1 - w2, sigma, cut)
+              + 0.5 * n0 * (n1s + 1.0) * (n2s + 1.0) * gaussian_delta(w0 - w1 - w2, sigma, cut))
+        wt = np.where(ok, wt, 0.0)
+        out[row] = 2.0 * np.pi / Nq * np.sum(np.abs(W) ** 2 * wt, axis=(0, 2, 3))
+    res = out.copy()
+    for row, iq in enumerate(qi_list):
+        for nu in range(omega.shape[1]):
+            grp = np.abs(omega[iq] - omega[iq, nu]) < params.degen_tol_eV
+            res[row, nu] = out[row, grp].mean()
+    return res
 
 
 # ------------------------------------------------- RTA transport from the linewidths (Sec. 4.2, 4.3.2)

@@ -521,3 +521,72 @@ def test_polar_coupling_adds_coherently():
     _, _, gs = elph.linewidths_rta(mat, prm, k_indices=[0, 5])
     _, _, gt = elph.linewidths_rta(mat, prm, k_indices=[0, 5], polar=pol)
     assert not np.allclose(gt, gs + g1, rtol=1e-3)           # interference between g^S and g^L
+
+
+def test_three_phonon_einstein_closed_form():
+    # Sec. 4.3 with two Einstein atoms (hbar w2 = 2 hbar w1) and on-site third-order constants:
+    # every q contributes alike.  Modes at w1 coalesce with a w1 mode into a w2 mode, modes at w2
+    # decay into two w1 modes; averaged over the degenerate modes,
+    #   A(w1) = 2 pi (1/3) sum |Phi3[0a,0b,1c]|^2 c1^2 c2 n1 n1 (n2+1) / (sqrt(pi) sigma)
+    #   A(w2) = 2 pi (1/3) sum |Phi3[1a,0b,0c]|^2 c2 c1^2 (1/2) n2 (n1+1)^2 / (sqrt(pi) sigma)
+    # with c = hbar^2 / (2 M hbar w) from Eq. 7's mode factor.
+    mat, anh, prm = W.einstein3(lam1=0.1, mass1=28.0, mass2=20.0, n=4)
+    A = elph.three_phonon_diag(mat, anh, prm)
+    hw1 = HBAR * np.sqrt(EV / (ANG ** 2 * AMU)) / EV * np.sqrt(0.1)
+    hw2 = 2 * hw1
+    h2 = HBAR ** 2 / (AMU * EV * ANG ** 2)
+    c1, c2 = h2 / (2 * 28.0 * hw1), h2 / (2 * 20.0 * hw2)
+    kT = 8.617333262e-5 * prm.T_K
+    n1, n2 = 1 / np.expm1(hw1 / kT), 1 / np.expm1(hw2 / kT)
+    d0 = 1 / (np.sqrt(np.pi) * prm.sigma_eV)
+    P = anh.Phi3[0]
+    a1 = 2 * np.pi / 3 * np.sum(P[:3, :3, 3:] ** 2) * c1 ** 2 * c2 * n1 * n1 * (n2 + 1) * d0
+    a2 = 2 * np.pi / 3 * np.sum(P[3:, :3, :3] ** 2) * c2 * c1 ** 2 * 0.5 * n2 * (n1 + 1) ** 2 * d0
+    assert np.allclose(A[:, :3], a1, rtol=1e-11) and np.allclose(A[:, 3:], a2, rtol=1e-11)
+
+
+def test_three_phonon_phase_convention():
+    # one off-site pair (R0, R0'): with q-independent Einstein modes V3 = e^{-i 2 pi (q.R0 + q'.R0')} C
+    R0, R0p = (1, 0, 0), (0, 1, 0)
+    mat, anh, prm = W.einstein3(offsite=(R0, R0p))
+    rng = np.random.default_rng(11)
+    q, qp, qpp = rng.uniform(0, 1, (3, 5, 3))
+    V = elph.v3_coupling(q, qp, qpp, mat, anh)
+    V0 = elph.v3_coupling(np.zeros((1, 3)), np.zeros((1, 3)), np.zeros((1, 3)), mat, anh)[0]
+    ph = np.exp(-2j * np.pi * (q @ np.array(R0, float) + qp @ np.array(R0p, float)))
+    assert np.allclose(V, ph[:, None, None, None] * V0[None], rtol=1e-12, atol=1e-15)
+    wrong = np.exp(+2j * np.pi * (q @ np.array(R0, float) + qp @ np.array(R0p, float)))
+    assert not np.allclose(V, wrong[:, None, None, None] * V0[None], rtol=1e-3)
+
+
+def test_three_phonon_factorised_equals_brute_force():
+    # the grid form (R sum at fixed q, then R' over all q~) equals the direct definition on a 3^3 grid
+    mat, anh, prm = W.three_phonon_si_like(seed=1, nq=3)
+    prm = prm.with_(sigma_eV=0.02)
+    A = elph.three_phonon_diag(mat, anh, prm, q_indices=[1, 5])
+    qs = elph.grid_points((3, 3, 3))
+    om, z = elph.phonon_modes(qs, mat)
+    nB = elph.bose_einstein(om, prm.T_K)
+    alive = om >= prm.omega_cut_eV
+    for row, iq in enumerate([1, 5]):
+        acc = np.zeros(6)
+        for it in range(27):
+            qpp = qs[iq] + qs[it]
+            i2 = elph.grid_index(qpp[None, :], (3, 3, 3))[0]
+            V = elph.v3_coupling(qs[iq][None], qs[it][None], -qpp[None], mat, anh)[0]
+            for nu in range(6):
+                for a in range(6):
+                    for b in range(6):
+                        if not (alive[iq, nu] and alive[it, a] and alive[i2, b]):
+                            continue
+                        d1 = elph.gaussian_delta(np.array(om[iq, nu] + om[it, a] - om[i2, b]), 0.02, 6.0)
+                        d2 = elph.gaussian_delta(np.array(om[iq, nu] - om[it, a] - om[i2, b]), 0.02, 6.0)
+                        acc[nu] += abs(V[nu, a, b]) ** 2 * (nB[iq, nu] * nB[it, a] * (nB[i2, b] + 1) * d1
+                                                            + 0.5 * nB[iq, nu] * (nB[it, a] + 1) * (nB[i2, b] + 1) * d2)
+        acc *= 2 * np.pi / 27
+        want = acc.copy()
+        for nu in range(6):
+            grp = np.abs(om[iq] - om[iq, nu]) < prm.degen_tol_eV
+            want[nu] = acc[grp].mean()
+        assert np.allclose(A[row], want, rtol=1e-9, atol=1e-18)
+    assert np.max(A) > 0

@@ -33,6 +33,9 @@ __all__ = [
     "wigner_seitz_set",
     "batch_material",
     "grid_fractions",
+    "Anharmonic",
+    "three_phonon_si_like",
+    "einstein3",
 ]
 
 
@@ -387,3 +390,67 @@ def batch_material(index: int, seed: int = 0, g_budget_bytes: float = 256e6) -> 
     nw, na, nR_target, n = (int(rng.integers(4, 25)), int(rng.integers(1, 7)), int(rng.integers(100, 1201)),
                             int(rng.integers(16, 41)))
     return material_of_shape(f"batch{index}", nw, na, nR_target, n, rng, g_budget_bytes)
+
+
+# ------------------------------------------------------------ third-order force constants
+
+@dataclass
+class Anharmonic:
+    """Third-order force constants V3(s a R, s' b R', s'' c 0) on a list of (R, R') pairs
+    (the arrays the C ABI ``set_force_constants3`` takes); any 1/N0^3 is folded in."""
+
+    R: np.ndarray                # (n,3) int32
+    Rp: np.ndarray               # (n,3) int32
+    w: np.ndarray                # (n,) weights
+    Phi3: np.ndarray             # (n, 3na, 3na, 3na) float64, eV/A^3, [s a][s' b][s'' c]
+
+
+def _phonon_only_material(name, lat, pos, masses, Rf, wf, Phi):
+    """A material with phonons only: one Wannier function with H = 0 and a zero coupling
+    (the three-phonon path needs the harmonic and third-order force constants alone)."""
+    Z0 = np.zeros((1, 3), dtype=np.int32)
+    na = len(masses)
+    return Material(name, 1, na, np.asarray(masses, dtype=np.float64), lat, pos, Z0, np.ones(1),
+                    np.zeros((1, 1, 1), dtype=np.complex128), Rf, wf, Phi, Z0.copy(), np.ones(1), Z0.copy(),
+                    np.ones(1), np.zeros((1, 1, 1, 1, 3 * na), dtype=np.complex128))
+
+
+def three_phonon_si_like(seed: int = 0, nq: int = 16, shell: float = 0.75) -> tuple[Material, Anharmonic, RTAParams]:
+    """fcc Si-like crystal (two atoms, the spring model of ``si_like``) with random third-order
+    force constants on the (R, R') pairs of the lattice vectors with |R| <= shell * a, decaying as
+    exp(-(|R| + |R'|) / (0.4 a)), 2 eV/A^3 at R = R' = 0.  Draw order: one (n, 6, 6, 6) normal
+    array.  q grid nq^3, T = 300 K, sigma = 2 meV.  Not symmetrised (the interpolation of
+    Eq. 3PhCouplingInterpolation needs none)."""
+    a = SI_A
+    lat = 0.5 * a * np.array([[0, 1, 1], [1, 0, 1], [1, 1, 0]], dtype=np.float64)
+    pos = np.array([[0, 0, 0], [0.25 * a, 0.25 * a, 0.25 * a]])
+    Rf, wf, Phi = _central_springs(lat, pos, [(np.sqrt(3.0) * a / 4.0, 10.0), (a / np.sqrt(2.0), 2.0)], search=2)
+    mat = _phonon_only_material("si_like_3ph", lat, pos, [28.0855, 28.0855], Rf, wf, Phi)
+    S = np.array([r for r in itertools.product(range(-2, 3), repeat=3)
+                  if np.linalg.norm(np.array(r) @ lat) <= shell * a + 1e-9], dtype=np.int32)
+    R = np.repeat(S, len(S), axis=0)
+    Rp = np.tile(S, (len(S), 1))
+    L = np.linalg.norm(R @ lat, axis=1) + np.linalg.norm(Rp @ lat, axis=1)
+    rng = np.random.default_rng(seed)
+    Phi3 = rng.normal(size=(len(R), 6, 6, 6)) * (2.0 * np.exp(-L / (0.4 * a)))[:, None, None, None]
+    anh = Anharmonic(R.astype(np.int32), Rp.astype(np.int32), np.ones(len(R)), Phi3)
+    return mat, anh, RTAParams(nk=(nq, nq, nq), nq=(nq, nq, nq), T_K=300.0, sigma_eV=0.002, window_eV=0.0)
+
+
+def einstein3(lam1: float = 0.1, mass1: float = 28.0, mass2: float = 20.0, n: int = 6, T_K: float = 300.0,
+              sigma: float = 0.002, offsite=None, seed: int = 4) -> tuple[Material, Anharmonic, RTAParams]:
+    """Closed-form case of the three-phonon path: simple cubic (a = 1 A), two atoms at the origin
+    with Einstein springs, D = diag(lam1 I, 4 lam1 I) (hbar w2 = 2 hbar w1, exactly resonant for
+    w2 -> w1 + w1), and third-order constants on one (R, R') pair: (0, 0), or ``offsite`` =
+    (R0, R0').  Phi3 = the (6, 6, 6) normal draw of ``seed``."""
+    lat = np.eye(3)
+    pos = np.zeros((2, 3))
+    Phi = np.zeros((1, 6, 6))
+    Phi[0, :3, :3] = mass1 * lam1 * np.eye(3)
+    Phi[0, 3:, 3:] = mass2 * 4.0 * lam1 * np.eye(3)
+    mat = _phonon_only_material("einstein3", lat, pos, [mass1, mass2], np.zeros((1, 3), dtype=np.int32),
+                                np.ones(1), Phi)
+    R0, R0p = ((0, 0, 0), (0, 0, 0)) if offsite is None else offsite
+    Phi3 = np.random.default_rng(seed).normal(size=(1, 6, 6, 6))
+    anh = Anharmonic(np.array([R0], dtype=np.int32), np.array([R0p], dtype=np.int32), np.ones(1), Phi3)
+    return mat, anh, RTAParams(nk=(n, n, n), nq=(n, n, n), T_K=T_K, sigma_eV=sigma, window_eV=0.0)
