@@ -289,6 +289,33 @@ def adaptive_leg(pg, ctx, prm, ms_linewidths: float, n_states: int) -> dict:
             "unit": "host-timed call incl. download of Gamma", "median_gamma_eV": float(np.median(g))}
 
 
+def three_phonon_leg(pg, W, dev) -> dict:
+    """Three-phonon diagonal of the phonon scattering matrix (Sec. 3.1 V3 interpolation, Sec. 4.3)
+    for every (q, nu) of a 16^3 grid of the Si-like two-atom crystal (169 (R, R') pairs, 13 R');
+    host-timed calls, the stage-2 kernel timed by CUDA events inside the library."""
+    import torch
+    mat, anh, prm = W.three_phonon_si_like(seed=0, nq=16)
+    with pg.PhoebeGPU(dev) as c:
+        c.set_material(mat)
+        c.set_force_constants3(anh)
+        c.set_profiling(True)
+        p3 = pg.make_params(prm)
+        A = c.three_phonon_rates(p3, 6)                  # warm-up
+        torch.cuda.synchronize()
+        reps = 3
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            A = c.three_phonon_rates(p3, 6)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3 / reps
+        st = c.stats()
+    q = int(np.prod(prm.nq))
+    return {"workload": "si_like two-atom 16^3 q grid, 169 (R, R') pairs, every (q, nu)", "q_points": q,
+            "ms_per_call": ms, "mode_rates_per_s": q * 6 / (ms / 1e3),
+            "stage2_ms": st["stage2_ms"], "stage2_tflops": st["stage2_flops"] / (st["stage2_ms"] / 1e3) / 1e12,
+            "unit": "host-timed call incl. phonons and download", "max_A_eV": float(np.max(A))}
+
+
 def batch_leg(pg, W, dev, args) -> dict:
     """64 uneven materials (N_w 4-24, 1-6 atoms, |R| 100-1200, grids 16^3-40^3, a seeded subset of k
     per material, split BF16): one call per material against one batch call whose stage 2 for all
@@ -593,6 +620,8 @@ def main():
         line["phonon_rates"] = prate_leg(pg, ctx, prm, mat, ms_per_step)
     if rank == 0 and args.precision == 7 and not args.no_prate:
         line["adaptive_smearing"] = adaptive_leg(pg, ctx, prm, ms_per_step, n)
+    if rank == 0 and not args.no_prate:
+        line["three_phonon"] = three_phonon_leg(pg, W, dev)
     if rank == 0 and not args.no_learned:
         line["learned_sampler"] = learned_leg(pg, W, dev, stream, args)
     if rank == 0 and not args.no_batch:

@@ -217,6 +217,24 @@ int phoebe_gpu_linewidths_rta_dev(phoebe_gpu_ctx* ctx, const phoebe_gpu_rta_para
 int phoebe_gpu_phonon_rates_elph(phoebe_gpu_ctx* ctx, const phoebe_gpu_rta_params* params, int64_t n_values,
                                  double* P_eV);
 
+/* Third-order force constants V3(s a R, s' b R', s'' c 0) (Sec. 3.1) on n (R, R') pairs:
+ *   R, Rp  n x 3 lattice vectors (crystal coordinates), w  n weights (NULL = 1),
+ *   Phi3   n x (3na) x (3na) x (3na) real, eV/A^3, [s a][s' b][s'' c]; any 1/N0^3 folded in.
+ * Requires set_force_constants (na) first. */
+int phoebe_gpu_set_force_constants3(phoebe_gpu_ctx* ctx, int n, const int32_t* R, const int32_t* Rp, const double* w,
+                                    const double* Phi3);
+
+/* Three-phonon part of the diagonal of the phonon scattering matrix on the q grid params->nq
+ * (Sec. 4.3, with the coupling V3 of Sec. 3.1 interpolated on the grid):
+ *   A_{q nu} = (2 pi / N_q) sum_{q~ nu' nu''} |V3(q nu, q~ nu', -(q+q~) nu'')|^2
+ *              [n n' (n''+1) delta(w + w' - w'') + (1/2) n (n'+1)(n''+1) delta(w - w' - w'')]
+ * (coalescence with q' = q~ plus half the decay with q' = -q~, q'' = q + q~), in eV, with the
+ * mode factors of Eq. 7, the Gaussian of fixed width sigma_eV, dead modes excluded, averaged
+ * over degenerate modes.  Uses nq, T_K, sigma_eV, delta_cut_sigmas, omega_cut_eV, degen_tol_eV
+ * of params.  One or two atoms, N_q <= 65535.  A_eV: host, n_values = N_q * 3na doubles, [q][nu]. */
+int phoebe_gpu_three_phonon_rates(phoebe_gpu_ctx* ctx, const phoebe_gpu_rta_params* params, int64_t n_values,
+                                  double* A_eV);
+
 /* Work and timing record of the last linewidths_rta call. */
 typedef struct {
   int64_t n_states;            /* active states computed */

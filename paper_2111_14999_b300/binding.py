@@ -38,7 +38,7 @@ EXPORTED = (
     "phoebe_gpu_mlp_loss_grad", "phoebe_gpu_is_uniforms", "phoebe_gpu_mlp_scores",
     "phoebe_gpu_batch_opts_default", "phoebe_gpu_linewidths_rta_batch", "phoebe_gpu_transport_rta",
     "phoebe_gpu_selftest_wait", "phoebe_gpu_phonon_rates_elph", "phoebe_gpu_set_lattice",
-    "phoebe_gpu_set_polar",
+    "phoebe_gpu_set_polar", "phoebe_gpu_set_force_constants3", "phoebe_gpu_three_phonon_rates",
 )
 
 
@@ -141,6 +141,8 @@ def _load() -> C.CDLL:
         "phoebe_gpu_phonon_rates_elph": (I, [P, C.POINTER(RTAParams), C.c_int64, P]),
         "phoebe_gpu_set_lattice": (I, [P, P]),
         "phoebe_gpu_set_polar": (I, [P, P, P, C.c_double]),
+        "phoebe_gpu_set_force_constants3": (I, [P, C.c_int, P, P, P, P]),
+        "phoebe_gpu_three_phonon_rates": (I, [P, C.POINTER(RTAParams), C.c_int64, P]),
         "phoebe_gpu_selftest_wait": (I, [P, I, I64]),
     }
     for name, (res, args) in sig.items():
@@ -278,6 +280,21 @@ class PhoebeGPU:
         if getattr(mat, "lattice", None) is not None:
             self.set_lattice(mat.lattice)
         self.nw, self.na = int(mat.nw), int(mat.na)
+
+    def set_force_constants3(self, anh):
+        """Third-order force constants from an object with the workloads.Anharmonic fields."""
+        R, Rp = _i32(anh.R).reshape(-1, 3), _i32(anh.Rp).reshape(-1, 3)
+        w = _f64(anh.w)
+        phi = _f64(anh.Phi3)
+        self._check(lib.phoebe_gpu_set_force_constants3(self._ctx, len(R), _ptr(R), _ptr(Rp), _ptr(w), _ptr(phi)))
+
+    def three_phonon_rates(self, params, n_modes: int, **kw):
+        """Three-phonon diagonal of the phonon scattering matrix A[q, nu] (eV) on the q grid."""
+        s = params if isinstance(params, RTAParams) else make_params(params, **kw)
+        nq = int(s.nq[0]) * int(s.nq[1]) * int(s.nq[2])
+        out = np.empty((nq, int(n_modes)), dtype=np.float64)
+        self._check(lib.phoebe_gpu_three_phonon_rates(self._ctx, C.byref(s), C.c_int64(out.size), _ptr(out)))
+        return out
 
     def set_polar(self, Zstar=None, eps_inf=None, alpha: float = 1.0):
         """Born charges (na, 3, 3), eps_inf (3, 3) and the Gaussian filter alpha (1/A^2) of the polar

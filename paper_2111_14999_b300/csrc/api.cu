@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <map>
 #include <numeric>
 #include <set>
@@ -334,6 +335,67 @@ void phoebe_gpu_rta_params_default(phoebe_gpu_rta_params* p) {
   p->sample_fraction = 0.05;
   p->mix_alpha = 0.1;
   p->sigma_min_eV = 1e-3;
+}
+
+int phoebe_gpu_set_force_constants3(phoebe_gpu_ctx* c, int n, const int32_t* R, const int32_t* Rp, const double* w,
+                                    const double* Phi3) {
+  if (!c) return PHOEBE_GPU_ERR_ARG;
+  cudaSetDevice(c->device);
+  if (!c->have_Phi) return fail(c, PHOEBE_GPU_ERR_ORDER, "set_force_constants3 needs set_force_constants first");
+  if (n <= 0 || !R || !Rp || !Phi3) return fail(c, PHOEBE_GPU_ERR_ARG, "n, R, Rp and Phi3 are required");
+  const int nm = 3 * c->na;
+  const int64_t blk = (int64_t)nm * nm * nm;
+  std::map<std::array<int, 3>, int> rp_index;  // distinct R', sorted
+  for (int i = 0; i < n; ++i) rp_index[{Rp[3 * i], Rp[3 * i + 1], Rp[3 * i + 2]}] = 0;
+  int k = 0;
+  std::vector<int> rpd;
+  for (auto& kv : rp_index) {
+    kv.second = k++;
+    rpd.insert(rpd.end(), kv.first.begin(), kv.first.end());
+  }
+  const int NRp = k;
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  auto rpi = [&](int i) { return rp_index[{Rp[3 * i], Rp[3 * i + 1], Rp[3 * i + 2]}]; };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return rpi(a) < rpi(b); });
+  std::vector<int> Rs((size_t)3 * n), off(NRp + 1, 0);
+  std::vector<double> ws(n), phs((size_t)n * blk);
+  for (int i = 0; i < n; ++i) {
+    const int o = order[i];
+    for (int d = 0; d < 3; ++d) Rs[3 * i + d] = R[3 * o + d];
+    ws[i] = w ? w[o] : 1.0;
+    for (int64_t e = 0; e < blk; ++e) phs[(size_t)i * blk + e] = Phi3[(size_t)o * blk + e];
+    off[rpi(o) + 1] = i + 1;
+  }
+  for (int r = 1; r <= NRp; ++r) off[r] = std::max(off[r], off[r - 1]);
+  void* d;
+  int st;
+  if ((st = upload(c, "ph3_R", Rs.data(), sizeof(int) * 3 * n, &d))) return st;
+  if ((st = upload(c, "ph3_w", ws.data(), sizeof(double) * n, &d))) return st;
+  if ((st = upload(c, "ph3_phi", phs.data(), sizeof(double) * n * blk, &d))) return st;
+  if ((st = upload(c, "ph3_off", off.data(), sizeof(int) * (NRp + 1), &d))) return st;
+  if ((st = upload(c, "ph3_Rpd", rpd.data(), sizeof(int) * 3 * NRp, &d))) return st;
+  c->ph3_nrp = NRp;
+  c->ph3_na = c->na;
+  c->have_phi3 = true;
+  return PHOEBE_GPU_OK;
+}
+
+int phoebe_gpu_three_phonon_rates(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, int64_t n_values, double* A_eV) {
+  if (!c) return PHOEBE_GPU_ERR_ARG;
+  cudaSetDevice(c->device);
+  if (!p || !A_eV) return fail(c, PHOEBE_GPU_ERR_ARG, "params or A_eV is NULL");
+  if (!c->have_phi3 || c->ph3_na != c->na)
+    return fail(c, PHOEBE_GPU_ERR_ORDER, "three_phonon_rates needs set_force_constants3 for the current atoms");
+  for (int i = 0; i < 3; ++i)
+    if (p->nq[i] < 1 || p->nq[i] > 4096) return fail(c, PHOEBE_GPU_ERR_ARG, "grid sizes must be in 1..4096");
+  if (!(p->T_K > 0.0) || !(p->sigma_eV > 0.0) || !(p->delta_cut_sigmas > 0.0) || !(p->omega_cut_eV >= 0.0) ||
+      !(p->degen_tol_eV >= 0.0))
+    return fail(c, PHOEBE_GPU_ERR_ARG, "T_K, sigma_eV, delta_cut_sigmas must be > 0, omega_cut and degen_tol >= 0");
+  const int64_t Q = (int64_t)p->nq[0] * p->nq[1] * p->nq[2];
+  if (n_values != Q * 3 * c->na)
+    return fail(c, PHOEBE_GPU_ERR_ARG, "A needs N_q * 3 n_at = %lld values", (long long)(Q * 3 * c->na));
+  return three_phonon(c, p, A_eV);
 }
 
 int phoebe_gpu_set_polar(phoebe_gpu_ctx* c, const double* Zstar, const double* eps_inf, double alpha) {

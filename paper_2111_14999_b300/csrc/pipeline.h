@@ -51,6 +51,9 @@ struct phoebe_gpu_ctx {
   bool have_lattice = false;
   double lattice[9] = {0};
   // polar long-range coupling, set by phoebe_gpu_set_polar
+  // third-order force constants, set by phoebe_gpu_set_force_constants3 (device buffers ph3_*)
+  bool have_phi3 = false;
+  int ph3_na = 0, ph3_nrp = 0;
   bool have_polar = false;
   std::vector<double> zstar;  // [na][3][3]
   double eps_inf[9] = {0};
@@ -115,6 +118,7 @@ GridPhase make_phase(const int n[3]);
 int cis_table(phoebe_gpu_ctx* c, const GridPhase& gp, const char* name, cplx** out);
 int electron_grid(phoebe_gpu_ctx* c, const int n[3], double** eps, cplx** U);
 int velocity_grid(phoebe_gpu_ctx* c, const int n[3], const cplx* U, float4** vel);
+int three_phonon(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, double* out_host);
 int phonon_modes(phoebe_gpu_ctx* c, const int n[3], const double* qpts_dev, int64_t Q, double T,
                  double omega_cut, double** omega, double** nB, cplx** Z, const char* tag);
 
