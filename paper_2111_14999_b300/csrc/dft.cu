@@ -166,10 +166,12 @@ __device__ __forceinline__ void load_cplx(const float2* __restrict__ p, float2 (
   }
 }
 
-// Shared-memory row stride of Y (complex elements): at least E, congruent to NW modulo 16 so that
-// the rows of consecutive lines start half a bank cycle apart (a lane group reads NW consecutive
-// complex values of a row), even whenever E is (16-byte loads stay aligned).
-__host__ __device__ constexpr int dft_row_stride(int E, int NW) { return E + ((NW - E) % 16 + 16) % 16; }
+// Shared-memory row stride of Y (complex elements): at least E and even whenever E is (16-byte
+// accesses stay aligned); for even NW congruent to NW modulo 16, so that the rows of consecutive
+// lines start half a bank cycle apart (a lane group reads NW consecutive complex values of a row).
+__host__ __device__ constexpr int dft_row_stride(int E, int NW) {
+  return NW % 2 == 0 ? E + ((NW - E) % 16 + 16) % 16 : E + (E % 2 == 0 ? 2 : 1);
+}
 
 // x sum of NQ q (same line l, columns jx[]) over the rows of that line: real-factor rows, residue
 // pairs (cos S + i sin D), residues without a partner (e^{i t r} Y).  Lane j of the group owns
@@ -717,7 +719,12 @@ int dft_launch(cudaStream_t st, const DftZArgs& z, const DftXArgs& x, int S, int
   k_dft_z<<<dim3((unsigned)x.Bx, (unsigned)S), 256, sm1, st>>>(z);
   if (cudaGetLastError() != cudaSuccess) return -1;
   if (nw == 8 && nm == 6) return launch_yx<8, 6, dft_split(8)>(st, x, S);
+  if (nw == 8 && nm == 3) return launch_yx<8, 3, dft_split(8)>(st, x, S);
+  if (nw == 4 && nm == 6) return launch_yx<4, 6, dft_split(4)>(st, x, S);
+  if (nw == 4 && nm == 3) return launch_yx<4, 3, dft_split(4)>(st, x, S);
+  if (nw == 2 && nm == 6) return launch_yx<2, 6, dft_split(2)>(st, x, S);
   if (nw == 2 && nm == 3) return launch_yx<2, 3, dft_split(2)>(st, x, S);
+  if (nw == 1 && nm == 6) return launch_yx<1, 6, dft_split(1)>(st, x, S);
   if (nw == 1 && nm == 3) return launch_yx<1, 3, dft_split(1)>(st, x, S);
   return -2;
 }

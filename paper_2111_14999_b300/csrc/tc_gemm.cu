@@ -1794,8 +1794,8 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
   constexpr int FMT = 0, NSPLIT = 2, NPROD = 3;
   const int nw = c->nw, nm = 3 * c->na, nRe = c->nRe, nRp = c->nRp;
   const int E = nw * nm;
-  if (!((nw == 8 && nm == 6) || (nw == 2 && nm == 3) || (nw == 1 && nm == 3)))
-    return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "the grid-DFT stage 2 is built for (nw, 3na) in {(8,6), (2,3), (1,3)}");
+  if (!((nw == 1 || nw == 2 || nw == 4 || nw == 8) && (nm == 3 || nm == 6)))
+    return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "the grid-DFT stage 2 is built for nw in {1, 2, 4, 8} and 3na in {3, 6}");
   const int Nx = gm.nq[0], Ny = gm.nq[1], Nz = gm.nq[2];
   if (Nz * 16 > 1024 || Nx > 256)
     return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "the grid-DFT stage 2 needs q-grid sizes Nx <= 256 and Nz <= 64");
