@@ -166,20 +166,22 @@ __device__ __forceinline__ void load_cplx(const float2* __restrict__ p, float2 (
   }
 }
 
-// Shared-memory row stride of Y (complex elements): at least E and even whenever E is (16-byte
-// accesses stay aligned); for even NW congruent to NW modulo 16, so that the rows of consecutive
-// lines start half a bank cycle apart (a lane group reads NW consecutive complex values of a row).
-__host__ __device__ constexpr int dft_row_stride(int E, int NW) {
-  return NW % 2 == 0 ? E + ((NW - E) % 16 + 16) % 16 : E + (E % 2 == 0 ? 2 : 1);
+// Shared-memory layout of a Y buffer: line-major, Y[line][row][c].  A row holds EP = E rounded up
+// to even complex values (16-byte accesses stay aligned).  The line stride is Bx EP padded so that,
+// for even NW, it is congruent to NW modulo 16: lane groups reading the same row of two consecutive
+// lines (NW consecutive complex values each) then start half a bank cycle apart.
+__host__ __device__ constexpr int dft_elem_stride(int E) { return E + E % 2; }
+__host__ __device__ constexpr int dft_line_stride(int Bx, int E, int NW) {
+  return Bx * dft_elem_stride(E) + (NW % 2 == 0 ? ((NW - Bx * dft_elem_stride(E)) % 16 + 16) % 16 : 0);
 }
 
 // x sum of NQ q (same line l, columns jx[]) over the rows of that line: real-factor rows, residue
 // pairs (cos S + i sin D), residues without a partner (e^{i t r} Y).  Lane j of the group owns
 // elements c = sa*NW + j*MW + mm; each row value loaded serves all NQ q.
-template <int NW, int NM, int MW, int ES, int L, int NQ>
-__device__ __forceinline__ void dft_x_line(const float2* __restrict__ Ys, const float2* __restrict__ Exs,
+template <int NW, int NM, int MW, int EP, int NQ>
+__device__ __forceinline__ void dft_x_line(const float2* __restrict__ Yl, const float2* __restrict__ Exs,
                                            const int* __restrict__ xS, const int* __restrict__ xD, int K, int K0,
-                                           int KP, const int (&jx)[NQ], int l, int j, float2 (&G)[NQ][NM][MW]) {
+                                           int KP, const int (&jx)[NQ], int j, float2 (&G)[NQ][NM][MW]) {
 #pragma unroll
   for (int u = 0; u < NQ; ++u)
 #pragma unroll
@@ -190,7 +192,7 @@ __device__ __forceinline__ void dft_x_line(const float2* __restrict__ Ys, const 
     float c[NQ];
 #pragma unroll
     for (int u = 0; u < NQ; ++u) c[u] = Exs[jx[u] * K + k].x;
-    const float2* ys = Ys + (xS[k] * L + l) * ES + j * MW;
+    const float2* ys = Yl + xS[k] * EP + j * MW;
 #pragma unroll
     for (int sa = 0; sa < NM; ++sa) {
       if constexpr (MW % 2 == 0) {
@@ -223,8 +225,8 @@ __device__ __forceinline__ void dft_x_line(const float2* __restrict__ Ys, const 
     float2 cs[NQ];
 #pragma unroll
     for (int u = 0; u < NQ; ++u) cs[u] = Exs[jx[u] * K + k];
-    const float2* ys = Ys + (xS[k] * L + l) * ES + j * MW;
-    const float2* yd = Ys + (xD[k] * L + l) * ES + j * MW;
+    const float2* ys = Yl + xS[k] * EP + j * MW;
+    const float2* yd = Yl + xD[k] * EP + j * MW;
 #pragma unroll
     for (int sa = 0; sa < NM; ++sa) {
       if constexpr (MW % 2 == 0) {
@@ -257,7 +259,7 @@ __device__ __forceinline__ void dft_x_line(const float2* __restrict__ Ys, const 
     float2 ex[NQ];
 #pragma unroll
     for (int u = 0; u < NQ; ++u) ex[u] = Exs[jx[u] * K + k];
-    const float2* y = Ys + (xS[k] * L + l) * ES + j * MW;
+    const float2* y = Yl + xS[k] * EP + j * MW;
 #pragma unroll
     for (int sa = 0; sa < NM; ++sa) {
       if constexpr (MW % 2 == 0) {
@@ -302,45 +304,56 @@ __device__ __forceinline__ float adaptive_width(const float4 va, const float4 vb
 }
 
 // One block per (jz, state), kDftXThreads threads; the block walks the jy lines in runs of
-// kDftLines.  Loaded once: the state's Zs[jz] slice (every (rx, ry) pair) by cp.async, the phase
-// tables.  Per run: phase 0 (in the previous run's last phase) lists the q = (jx, jy, jz) of the
-// run whose final bands m' at k+q can reach the delta window around eps_nk (warp ballots, in
-// (line, jx) order, two lists used alternately); phase Y forms Y[rx][line][c] =
-// sum_ry Ey[jy][ry] Zs[(rx,ry)][c] in shared memory, the rows of residue pairs directly as S and D;
-// phase X: SPLIT consecutive lanes
-// take one listed q, sum over the rows (dft_x_line), apply U_{k+q}^dagger (partial sums over m
-// combined by shuffles), Z_q and the delta weights of every listed m'.  q whose bands all miss
-// the window contribute nothing to Eq. 29 and are not evaluated.
+// kDftLines.  Loaded once: the state's Zs[jz] slice (every (rx, ry) pair) by cp.async and the
+// phase tables.  Three kinds of warp task:
+//  - listing (run r, 32 QR consecutive q of the run): which final bands m' at k+q can reach the
+//    delta window around eps_nk; the q with at least one are appended to the run's list (warp
+//    ballots, in (line, jx) order);
+//  - y (run r, 32 column vectors): Y[rx][line][c] = sum_ry Ey[jy][ry] Zs[(rx,ry)][c] into one of two
+//    Y buffers, the rows of residue pairs directly as S and D;
+//  - x (run r, 32 / SPLIT groups of SPLIT lanes, NQ listed q of one line each): sum over the rows
+//    (dft_x_line), apply U_{k+q}^dagger (partial sums over m combined by shuffles), Z_q and the delta
+//    weights of every listed m'.
+// Iteration r, closed by one block barrier, hands out from a shared counter the x tasks of run r,
+// the y tasks of run r+1 and the listing tasks of run r+2 (three lists), so that warps without x
+// work prepare the next runs instead of waiting.  q whose bands all miss the window contribute
+// nothing to Eq. 29 and are not evaluated.
 template <int NW, int NM, int SPLIT, bool PR, int NQ, bool AD, bool PL>
 __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT_MINB2) k_dft_yx_elph(DftXArgs a) {
-  constexpr int E = NW * NM, MW = NW / SPLIT, ES = dft_row_stride(E, NW);
-  constexpr int L = kDftLines, UL = kDftUnitLines;
+  constexpr int E = NW * NM, MW = NW / SPLIT, EP = dft_elem_stride(E);
+  constexpr int L = kDftLines, UL = kDftUnitLines, NWARP = kDftXThreads / 32;
+  constexpr int QR = AD ? 1 : 2;         // q per lane of a listing task (the adaptive test also reads velocities)
+  constexpr int XT = (32 / SPLIT) * NQ;  // list entries per x task
   static_assert(NW % SPLIT == 0 && 32 % SPLIT == 0 && NW <= 16, "lane split must divide NW and the warp");
   static_assert(SPLIT == dft_split(NW), "lane split must match the host's shared-memory sizing");
   extern __shared__ __align__(16) unsigned char smem[];
-  const int P = a.P;
-  float2* Zsl = reinterpret_cast<float2*>(smem);          // [P][E]
-  float2* Ys = Zsl + (size_t)P * E + (P * E) % 2;         // [Bx][L][ES]
-  float2* Exs = Ys + (size_t)a.Bx * L * ES;               // [Nx][K]
-  float2* Eys = Exs + (size_t)a.Nx * a.K;                 // [2][L][By] Ey rows of a run, used alternately
-  int* ppo = reinterpret_cast<int*>(Eys + (size_t)2 * L * a.By);  // [Bx+1]
-  int* xS = ppo + a.Bx + 1;                               // [K]
-  int* xD = xS + a.K;                                     // [K]
-  int* pay = xD + a.K;                                    // [P]
-  int* mate = pay + P;                                    // [P]
-  int* lists = mate + P;                                  // [2][lcap]
-  const int lcap = dft_list_cap(L, a.Nx);
-  __shared__ int cnt[2];
+  const int P = a.P, Bx = a.Bx, By = a.By, Nx = a.Nx, Ny = a.Ny;
+  const int LS = dft_line_stride(Bx, E, NW);                 // complex values per line of a Y buffer
+  const int YB = L * LS;                                     // complex values per Y buffer
+  float2* Zsl = reinterpret_cast<float2*>(smem);             // [P][E]
+  float2* Ys = Zsl + (size_t)P * E + (P * E) % 2;            // [2][L][LS]
+  float2* Exs = Ys + (size_t)2 * YB;                         // [Nx][K]
+  float2* Eys = Exs + (size_t)Nx * a.K;                      // [Ny][By]
+  int* ppo = reinterpret_cast<int*>(Eys + (size_t)Ny * By);  // [Bx+1]
+  int* xS = ppo + Bx + 1;                                    // [K]
+  int* xD = xS + a.K;                                        // [K]
+  int* pay = xD + a.K;                                       // [P]
+  int* mate = pay + P;                                       // [P]
+  int* lists = mate + P;                                     // [3][lcap], run r in list r % 3
+  const int lcap = dft_list_cap(L, Nx);
+  __shared__ int cnt[4];  // list length of run r in cnt[r % 4]
+  __shared__ int wq[2];   // task counter of iteration r in wq[r % 2]
   __shared__ float en_s[2];
   __shared__ double pw_s;
-  __shared__ float4 vn_s;  // adaptive smearing: hbar v of the initial state
+  __shared__ float4 vn_s;      // adaptive smearing: hbar v of the initial state
   __shared__ float2 uk_s[NW];  // polar term: U_k[m][n] of the initial state
-  __shared__ double red[kDftXThreads / 32];
+  __shared__ double red[NWARP];
   const int s = blockIdx.y, jz = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
-    cnt[0] = 0;
-    cnt[1] = 0;
+    for (int i = 0; i < 4; ++i) cnt[i] = 0;
+    wq[0] = 0;
+    wq[1] = 0;
     const double e_n = a.epsF[a.gm.k_to_fine(a.st_k[s]) * NW + a.st_b[s]];
     en_s[0] = (float)e_n;
     en_s[1] = (float)(e_n - (double)en_s[0]);
@@ -363,12 +376,13 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
       for (int i = threadIdx.x; i < P * E; i += blockDim.x) cp_async8(Zsl + i, zg + i);
     }
   }
-  for (int i = threadIdx.x; i < a.Nx * a.K; i += blockDim.x) Exs[i] = a.Ex[i];
+  for (int i = threadIdx.x; i < Nx * a.K; i += blockDim.x) Exs[i] = a.Ex[i];
+  for (int i = threadIdx.x; i < Ny * By; i += blockDim.x) Eys[i] = a.Ey[i];
   for (int i = threadIdx.x; i < a.K; i += blockDim.x) {
     xS[i] = a.xS[i];
     xD[i] = a.xD[i];
   }
-  for (int i = threadIdx.x; i <= a.Bx; i += blockDim.x) ppo[i] = a.plane_pair_off[i];
+  for (int i = threadIdx.x; i <= Bx; i += blockDim.x) ppo[i] = a.plane_pair_off[i];
   for (int i = threadIdx.x; i < P; i += blockDim.x) {
     pay[i] = a.pair_ay[i];
     mate[i] = a.pair_mate[i];
@@ -381,304 +395,342 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
   const int nfx = a.gm.nf[0], nfy = a.gm.nf[1], nfz = a.gm.nf[2];
   int fz = kc[2] + jz * a.gm.sq[2];
   fz -= fz >= nfz ? nfz : 0;
-  const float inv_nx = 1.f / (float)a.Nx;  // qi < 2^16, Nx <= 256: (qi + 0.5) / Nx truncates exactly
-  __syncthreads();  // counters and en_s
+  const float inv_nx = 1.f / (float)Nx;  // qi < 2^16, Nx <= 256: (qi + 0.5) / Nx truncates exactly
+  __syncthreads();  // counters, en_s, tables
   const float en_hi = en_s[0], en_lo = en_s[1];
   const double pw = PR ? pw_s : 0.0;
   const float4 vn = AD ? vn_s : make_float4(0.f, 0.f, 0.f, 0.f);
-  // phase 0 for the run starting at jy0, into list b: two q per thread and round, their energy
-  // rows loaded before either is tested
-  auto phase0 = [&](int jy0, int b) {
-    const int nq_blk = min(L, a.Ny - jy0) * a.Nx;
-    int* list = lists + b * lcap;
-    for (int i = threadIdx.x; i < L * a.By; i += blockDim.x) {  // Ey rows of the run (0 past the grid edge)
-      const int jy = jy0 + i / a.By;
-      Eys[b * L * a.By + i] = jy < a.Ny ? a.Ey[jy * a.By + i % a.By] : make_float2(0.f, 0.f);
-    }
-    constexpr int QR = AD ? 1 : 2;  // q per thread and round (the adaptive test also reads velocities)
-    for (int q0 = 0; q0 < nq_blk; q0 += QR * blockDim.x) {
-      float ev[QR][NW];
-      int64_t kqs[QR];
-      int qis[QR];
+  const int R = (Ny + L - 1) / L;
+  auto list_tasks = [&](int rr) { return (min(L, Ny - rr * L) * Nx + 32 * QR - 1) / (32 * QR); };
+
+  // listing task t of run rr: q = 32 QR t + 32 u + lane of the run (u < QR), energy rows loaded
+  // before any is tested
+  auto list_task = [&](int rr, int t) {
+    const int jy0 = rr * L;
+    const int nq_run = min(L, Ny - jy0) * Nx;
+    int* list = lists + (rr % 3) * lcap;
+    int* cn = cnt + (rr & 3);
+    const int q0 = t * 32 * QR;
+    float ev[QR][NW];
+    int64_t kqs[QR];
+    int qis[QR];
 #pragma unroll
-      for (int u = 0; u < QR; ++u) {
-        const int qi = q0 + u * blockDim.x + threadIdx.x;
-        const int l = (int)(((float)qi + 0.5f) * inv_nx);
-        const int jx = qi - l * a.Nx;
-        qis[u] = (l << 8) | jx;  // (line, jx)
-        if (qi < nq_blk) {
-          int fx = kc[0] + jx * sx, fy = kc[1] + (jy0 + l) * sy;
-          fx -= fx >= nfx ? nfx : 0;
-          fy -= fy >= nfy ? nfy : 0;
-          kqs[u] = (int64_t)(fx * nfy + fy) * nfz + fz;
-          load_row<NW>(a.epsf + kqs[u] * NW, ev[u]);
+    for (int u = 0; u < QR; ++u) {
+      const int qi = q0 + u * 32 + lane;
+      const int l = (int)(((float)qi + 0.5f) * inv_nx);
+      const int jx = qi - l * Nx;
+      qis[u] = (l << 8) | jx;  // (line, jx)
+      if (qi < nq_run) {
+        int fx = kc[0] + jx * sx, fy = kc[1] + (jy0 + l) * sy;
+        fx -= fx >= nfx ? nfx : 0;
+        fy -= fy >= nfy ? nfy : 0;
+        kqs[u] = (int64_t)(fx * nfy + fy) * nfz + fz;
+        load_row<NW>(a.epsf + kqs[u] * NW, ev[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < QR; ++u) {
+      unsigned need = 0;
+      if (q0 + u * 32 + lane < nq_run) {
+#pragma unroll
+        for (int mp = 0; mp < NW; ++mp) {
+          float reach = a.reach;
+          if constexpr (AD)
+            reach = (a.omega_max + a.cut * adaptive_width(vn, __ldg(a.vel + kqs[u] * NW + mp), a.cB, a.sigma_min)) *
+                    1.0001f;
+          if (fabsf(en_hi - ev[u][mp]) < reach) need |= 1u << mp;
         }
       }
-#pragma unroll
-      for (int u = 0; u < QR; ++u) {
-        unsigned need = 0;
-        if (q0 + u * (int)blockDim.x + (int)threadIdx.x < nq_blk) {
-#pragma unroll
-          for (int mp = 0; mp < NW; ++mp) {
-            float reach = a.reach;
-            if constexpr (AD)
-              reach = (a.omega_max + a.cut * adaptive_width(vn, __ldg(a.vel + kqs[u] * NW + mp), a.cB, a.sigma_min)) *
-                      1.0001f;
-            if (fabsf(en_hi - ev[u][mp]) < reach) need |= 1u << mp;
-          }
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, need != 0);
-        if constexpr (NQ == 1) {
-          int base = 0;
-          if (lane == 0 && bal) base = atomicAdd(&cnt[b], __popc(bal));
-          base = __shfl_sync(0xffffffffu, base, 0);
-          if (need) list[base + __popc(bal & ((1u << lane) - 1))] = (int)(need << 16) | qis[u];
-        } else {
-          // entries are consumed in pairs: each line's run of listed q in this warp is padded to an
-          // even length with an entry of the same line and no band (its x sum runs, nothing else)
-          const unsigned same = __match_any_sync(0xffffffffu, qis[u] >> 8);  // lanes of my line
-          const unsigned bl = bal & same;
-          const int first = __ffs(same) - 1;
-          const bool odd_lead = lane == first && (__popc(bl) & 1);
-          const unsigned oddm = __ballot_sync(0xffffffffu, odd_lead);
-          const int tot = __popc(bal) + __popc(oddm);
-          int base = 0;
-          if (lane == 0 && tot) base = atomicAdd(&cnt[b], tot);
-          base = __shfl_sync(0xffffffffu, base, 0);
-          const unsigned before = (1u << first) - 1;  // lanes of the earlier lines (lines grow with lane)
-          const int seg = base + __popc(bal & before) + __popc(oddm & before);
-          if (need) list[seg + __popc(bl & ((1u << lane) - 1))] = (int)(need << 16) | qis[u];
-          if (odd_lead) list[seg + __popc(bl)] = qis[u] & 0xffff;
-        }
+      const unsigned bal = __ballot_sync(0xffffffffu, need != 0);
+      if constexpr (NQ == 1) {
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(cn, __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (need) list[base + __popc(bal & ((1u << lane) - 1))] = (int)(need << 16) | qis[u];
+      } else {
+        // entries are consumed in pairs: each line's run of listed q in this warp is padded to an
+        // even length with an entry of the same line and no band (its x sum runs, nothing else)
+        const unsigned same = __match_any_sync(0xffffffffu, qis[u] >> 8);  // lanes of my line
+        const unsigned bl = bal & same;
+        const int first = __ffs(same) - 1;
+        const bool odd_lead = lane == first && (__popc(bl) & 1);
+        const unsigned oddm = __ballot_sync(0xffffffffu, odd_lead);
+        const int tot = __popc(bal) + __popc(oddm);
+        int base = 0;
+        if (lane == 0 && tot) base = atomicAdd(cn, tot);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const unsigned before = (1u << first) - 1;  // lanes of the earlier lines (lines grow with lane)
+        const int seg = base + __popc(bal & before) + __popc(oddm & before);
+        if (need) list[seg + __popc(bl & ((1u << lane) - 1))] = (int)(need << 16) | qis[u];
+        if (odd_lead) list[seg + __popc(bl)] = qis[u] & 0xffff;
       }
     }
   };
-  phase0(0, 0);
-  cp_async_wait_all();
-  const int j = threadIdx.x % SPLIT;
-  const unsigned gmask = (SPLIT == 32 ? 0xffffffffu : ((1u << SPLIT) - 1)) << (lane & ~(SPLIT - 1));
-  float acc = 0.f;  // every term of Eq. 29 is non-negative: FP32 partial sums lose nothing to cancellation
-  for (int jy0 = 0, run = 0; jy0 < a.Ny; jy0 += L, ++run) {
-    const int b = run & 1;
-    __syncthreads();  // phase 0 of this run done (and, on the first run, the slice landed)
-    const int total = cnt[b];
-    // phase Y: sum over ry of the slice into Y rows (lines past the grid edge get Ey = 0).  For a
-    // residue pair row k (planes a = xS[k], b = xD[k], the pairs of b mirroring those of a) the
-    // rows are formed directly as S = Y_a + Y_b and D = Y_a - Y_b: with Z1 = Zs[(a, ry)],
-    // Z2 = Zs[(b, -ry)] and Ey[jy][ry] = c + i s,
-    //   S = sum_ry c (Z1 + Z2) + i s (Z1 - Z2),   D = sum_ry c (Z1 - Z2) + i s (Z1 + Z2).
-    // Other rows: Y_a = sum_ry Ey Z1.  Unit = (row, kDftUnitLines lines, column vector).
+
+  // y task t of run rr into Y buffer rr % 2, one unit per lane.  For a residue pair row k
+  // (planes a = xS[k], b = xD[k], the pairs of b mirroring those of a) the rows are formed
+  // directly as S = Y_a + Y_b and D = Y_a - Y_b: with Z1 = Zs[(a, ry)], Z2 = Zs[(b, -ry)] and
+  // Ey[jy][ry] = c + i s,
+  //   S = sum_ry c (Z1 + Z2) + i s (Z1 - Z2),   D = sum_ry c (Z1 - Z2) + i s (Z1 + Z2).
+  // Other rows: Y_a = sum_ry Ey Z1.  Unit = (row, kDftUnitLines lines, column vector); lines past
+  // the grid edge read the last Ey row (never listed, never read).
+  constexpr int CV = E % 2 == 0 ? E / 2 : E;  // column vectors per row (float4 when E is even)
+  const int npu = a.KP * (L / UL) * CV;
+  const int units = Bx * (L / UL) * CV - npu;  // each pair unit covers two planes
+  const int y_tasks = (units + 31) / 32;
+  auto y_task = [&](int rr, int t) {
+    const int u = t * 32 + lane;
+    if (u >= units) return;
+    float2* Yb = Ys + (size_t)(rr & 1) * YB;
+    const bool pr = u < npu;
+    const int uu = pr ? u : u - npu;
+    const int cv = uu % CV, rest = uu / CV;
+    const int lh = rest % (L / UL), kk = rest / (L / UL);
+    const int k = pr ? a.K0 + kk : (kk < a.K0 ? kk : kk + a.KP);
+    const int ra = xS[k];
+    int eo[UL];
+#pragma unroll
+    for (int l = 0; l < UL; ++l) eo[l] = min(rr * L + lh * UL + l, Ny - 1) * By;
     if constexpr (E % 2 == 0) {
-      constexpr int EV = E / 2;
-      const int npu = a.KP * (L / UL) * EV;
-      const int units = a.Bx * (L / UL) * EV - npu;  // each pair unit covers two planes
-      for (int u = threadIdx.x; u < units; u += blockDim.x) {
-        const bool pr = u < npu;
-        const int uu = pr ? u : u - npu;
-        const int cv = uu % EV, rest = uu / EV;
-        const int lh = rest % (L / UL), kk = rest / (L / UL);
-        const int k = pr ? a.K0 + kk : (kk < a.K0 ? kk : kk + a.KP);
-        const int ra = xS[k];
-        const float2* eyb = Eys + (size_t)(b * L + lh * UL) * a.By;
-        float4 s4[UL], d4[UL];
+      float4 s4[UL], d4[UL];
 #pragma unroll
-        for (int l = 0; l < UL; ++l) {
-          s4[l] = make_float4(0.f, 0.f, 0.f, 0.f);
-          d4[l] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        if (pr) {
-          for (int p = ppo[ra]; p < ppo[ra + 1]; ++p) {
-            const float4 z1 = reinterpret_cast<const float4*>(Zsl + (size_t)p * E)[cv];
-            const float4 z2 = reinterpret_cast<const float4*>(Zsl + (size_t)mate[p] * E)[cv];
-            const float4 pp = make_float4(z1.x + z2.x, z1.y + z2.y, z1.z + z2.z, z1.w + z2.w);
-            const float4 mm = make_float4(z1.x - z2.x, z1.y - z2.y, z1.z - z2.z, z1.w - z2.w);
-            const int ay = pay[p];
-#pragma unroll
-            for (int l = 0; l < UL; ++l) {
-              const float2 ey = eyb[l * a.By + ay];
-              s4[l].x = fmaf(ey.x, pp.x, fmaf(-ey.y, mm.y, s4[l].x));
-              s4[l].y = fmaf(ey.x, pp.y, fmaf(ey.y, mm.x, s4[l].y));
-              s4[l].z = fmaf(ey.x, pp.z, fmaf(-ey.y, mm.w, s4[l].z));
-              s4[l].w = fmaf(ey.x, pp.w, fmaf(ey.y, mm.z, s4[l].w));
-              d4[l].x = fmaf(ey.x, mm.x, fmaf(-ey.y, pp.y, d4[l].x));
-              d4[l].y = fmaf(ey.x, mm.y, fmaf(ey.y, pp.x, d4[l].y));
-              d4[l].z = fmaf(ey.x, mm.z, fmaf(-ey.y, pp.w, d4[l].z));
-              d4[l].w = fmaf(ey.x, mm.w, fmaf(ey.y, pp.z, d4[l].w));
-            }
-          }
-          const int rb = xD[k];
-#pragma unroll
-          for (int l = 0; l < UL; ++l) {
-            reinterpret_cast<float4*>(Ys + (size_t)(ra * L + lh * UL + l) * ES)[cv] = s4[l];
-            reinterpret_cast<float4*>(Ys + (size_t)(rb * L + lh * UL + l) * ES)[cv] = d4[l];
-          }
-        } else {
-          for (int p = ppo[ra]; p < ppo[ra + 1]; ++p) {
-            const float4 z = reinterpret_cast<const float4*>(Zsl + (size_t)p * E)[cv];
-            const int ay = pay[p];
-#pragma unroll
-            for (int l = 0; l < UL; ++l) {
-              const float2 ey = eyb[l * a.By + ay];
-              s4[l].x = fmaf(ey.x, z.x, fmaf(-ey.y, z.y, s4[l].x));
-              s4[l].y = fmaf(ey.x, z.y, fmaf(ey.y, z.x, s4[l].y));
-              s4[l].z = fmaf(ey.x, z.z, fmaf(-ey.y, z.w, s4[l].z));
-              s4[l].w = fmaf(ey.x, z.w, fmaf(ey.y, z.z, s4[l].w));
-            }
-          }
-#pragma unroll
-          for (int l = 0; l < UL; ++l) reinterpret_cast<float4*>(Ys + (size_t)(ra * L + lh * UL + l) * ES)[cv] = s4[l];
-        }
+      for (int l = 0; l < UL; ++l) {
+        s4[l] = make_float4(0.f, 0.f, 0.f, 0.f);
+        d4[l] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
-    } else {
-      const int npu = a.KP * (L / UL) * E;
-      const int units = a.Bx * (L / UL) * E - npu;
-      for (int u = threadIdx.x; u < units; u += blockDim.x) {
-        const bool pr = u < npu;
-        const int uu = pr ? u : u - npu;
-        const int cv = uu % E, rest = uu / E;
-        const int lh = rest % (L / UL), kk = rest / (L / UL);
-        const int k = pr ? a.K0 + kk : (kk < a.K0 ? kk : kk + a.KP);
-        const int ra = xS[k];
-        const float2* eyb = Eys + (size_t)(b * L + lh * UL) * a.By;
-        float2 s2[UL], d2[UL];
-#pragma unroll
-        for (int l = 0; l < UL; ++l) {
-          s2[l] = make_float2(0.f, 0.f);
-          d2[l] = make_float2(0.f, 0.f);
-        }
+      if (pr) {
         for (int p = ppo[ra]; p < ppo[ra + 1]; ++p) {
-          const float2 z1 = Zsl[(size_t)p * E + cv];
-          const float2 z2 = pr ? Zsl[(size_t)mate[p] * E + cv] : make_float2(0.f, 0.f);
-          const float2 pp = make_float2(z1.x + z2.x, z1.y + z2.y), mm = make_float2(z1.x - z2.x, z1.y - z2.y);
+          const float4 z1 = reinterpret_cast<const float4*>(Zsl + (size_t)p * E)[cv];
+          const float4 z2 = reinterpret_cast<const float4*>(Zsl + (size_t)mate[p] * E)[cv];
+          const float4 pp = make_float4(z1.x + z2.x, z1.y + z2.y, z1.z + z2.z, z1.w + z2.w);
+          const float4 mm = make_float4(z1.x - z2.x, z1.y - z2.y, z1.z - z2.z, z1.w - z2.w);
           const int ay = pay[p];
 #pragma unroll
           for (int l = 0; l < UL; ++l) {
-            const float2 ey = eyb[l * a.By + ay];
-            s2[l].x = fmaf(ey.x, pp.x, fmaf(-ey.y, mm.y, s2[l].x));
-            s2[l].y = fmaf(ey.x, pp.y, fmaf(ey.y, mm.x, s2[l].y));
-            d2[l].x = fmaf(ey.x, mm.x, fmaf(-ey.y, pp.y, d2[l].x));
-            d2[l].y = fmaf(ey.x, mm.y, fmaf(ey.y, pp.x, d2[l].y));
+            const float2 ey = Eys[eo[l] + ay];
+            s4[l].x = fmaf(ey.x, pp.x, fmaf(-ey.y, mm.y, s4[l].x));
+            s4[l].y = fmaf(ey.x, pp.y, fmaf(ey.y, mm.x, s4[l].y));
+            s4[l].z = fmaf(ey.x, pp.z, fmaf(-ey.y, mm.w, s4[l].z));
+            s4[l].w = fmaf(ey.x, pp.w, fmaf(ey.y, mm.z, s4[l].w));
+            d4[l].x = fmaf(ey.x, mm.x, fmaf(-ey.y, pp.y, d4[l].x));
+            d4[l].y = fmaf(ey.x, mm.y, fmaf(ey.y, pp.x, d4[l].y));
+            d4[l].z = fmaf(ey.x, mm.z, fmaf(-ey.y, pp.w, d4[l].z));
+            d4[l].w = fmaf(ey.x, mm.w, fmaf(ey.y, pp.z, d4[l].w));
           }
         }
+        const int rb = xD[k];
 #pragma unroll
         for (int l = 0; l < UL; ++l) {
-          Ys[(size_t)(ra * L + lh * UL + l) * ES + cv] = s2[l];
-          if (pr) Ys[(size_t)(xD[k] * L + lh * UL + l) * ES + cv] = d2[l];
+          reinterpret_cast<float4*>(Yb + (size_t)(lh * UL + l) * LS + ra * EP)[cv] = s4[l];
+          reinterpret_cast<float4*>(Yb + (size_t)(lh * UL + l) * LS + rb * EP)[cv] = d4[l];
+        }
+      } else {
+        for (int p = ppo[ra]; p < ppo[ra + 1]; ++p) {
+          const float4 z = reinterpret_cast<const float4*>(Zsl + (size_t)p * E)[cv];
+          const int ay = pay[p];
+#pragma unroll
+          for (int l = 0; l < UL; ++l) {
+            const float2 ey = Eys[eo[l] + ay];
+            s4[l].x = fmaf(ey.x, z.x, fmaf(-ey.y, z.y, s4[l].x));
+            s4[l].y = fmaf(ey.x, z.y, fmaf(ey.y, z.x, s4[l].y));
+            s4[l].z = fmaf(ey.x, z.z, fmaf(-ey.y, z.w, s4[l].z));
+            s4[l].w = fmaf(ey.x, z.w, fmaf(ey.y, z.z, s4[l].w));
+          }
+        }
+#pragma unroll
+        for (int l = 0; l < UL; ++l) reinterpret_cast<float4*>(Yb + (size_t)(lh * UL + l) * LS + ra * EP)[cv] = s4[l];
+      }
+    } else {
+      float2 s2[UL], d2[UL];
+#pragma unroll
+      for (int l = 0; l < UL; ++l) {
+        s2[l] = make_float2(0.f, 0.f);
+        d2[l] = make_float2(0.f, 0.f);
+      }
+      for (int p = ppo[ra]; p < ppo[ra + 1]; ++p) {
+        const float2 z1 = Zsl[(size_t)p * E + cv];
+        const float2 z2 = pr ? Zsl[(size_t)mate[p] * E + cv] : make_float2(0.f, 0.f);
+        const float2 pp = make_float2(z1.x + z2.x, z1.y + z2.y), mm = make_float2(z1.x - z2.x, z1.y - z2.y);
+        const int ay = pay[p];
+#pragma unroll
+        for (int l = 0; l < UL; ++l) {
+          const float2 ey = Eys[eo[l] + ay];
+          s2[l].x = fmaf(ey.x, pp.x, fmaf(-ey.y, mm.y, s2[l].x));
+          s2[l].y = fmaf(ey.x, pp.y, fmaf(ey.y, mm.x, s2[l].y));
+          d2[l].x = fmaf(ey.x, mm.x, fmaf(-ey.y, pp.y, d2[l].x));
+          d2[l].y = fmaf(ey.x, mm.y, fmaf(ey.y, pp.x, d2[l].y));
         }
       }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) cnt[b] = 0;  // every thread read this run's count before the barrier above
-    // phase X: SPLIT lanes per NQ consecutive list entries (same line when NQ = 2)
-    const int* list = lists + b * lcap;
-    for (int it = (threadIdx.x / SPLIT) * NQ; it < total; it += (blockDim.x / SPLIT) * NQ) {
-      int jxs[NQ];
-      unsigned needs[NQ];
 #pragma unroll
-      for (int u = 0; u < NQ; ++u) {
-        const int w = list[it + u];
-        needs[u] = (unsigned)w >> 16;
-        jxs[u] = w & 0xff;
+      for (int l = 0; l < UL; ++l) {
+        Yb[(size_t)(lh * UL + l) * LS + ra * EP + cv] = s2[l];
+        if (pr) Yb[(size_t)(lh * UL + l) * LS + xD[k] * EP + cv] = d2[l];
       }
-      const int l = (list[it] >> 8) & 0xff;
-      const int jy = jy0 + l;
-      float2 G[NQ][NM][MW];
-      dft_x_line<NW, NM, MW, ES, L, NQ>(Ys, Exs, xS, xD, a.K, a.K0, a.KP, jxs, l, j, G);
-      int fy = kc[1] + jy * sy;
-      fy -= fy >= nfy ? nfy : 0;
+    }
+  };
+
+  const int j = threadIdx.x % SPLIT;
+  const unsigned gmask = (SPLIT == 32 ? 0xffffffffu : ((1u << SPLIT) - 1)) << (lane & ~(SPLIT - 1));
+  // x task t of run r: group g of the warp takes list entries XT t + NQ g .. + NQ - 1 (one line);
+  // returns the lane's share of the task's Eq. 29 sum.  Every term is non-negative, so FP32 partial
+  // sums lose nothing to cancellation.
+  auto x_task = [&](int r, int t, int total) -> float {
+    float acc = 0.f;
+    const int it = t * XT + (lane / SPLIT) * NQ;
+    if (it >= total) return acc;
+    const float2* Yb = Ys + (size_t)(r & 1) * YB;
+    const int* list = lists + (r % 3) * lcap;
+    int jxs[NQ];
+    unsigned needs[NQ];
 #pragma unroll
-      for (int u = 0; u < NQ; ++u) {
-        const int jx = jxs[u];
-        const int q = (jx * a.Ny + jy) * a.Nz + jz;
-        int fx = kc[0] + jx * sx;
-        fx -= fx >= nfx ? nfx : 0;
-        const int64_t kq = (int64_t)(fx * nfy + fy) * nfz + fz;
-        const float2* zt = a.ZT + (int64_t)q * NM * NM;
-        const float2* onb = a.omnb + (int64_t)q * NM;
-        for (unsigned m = needs[u]; m; m &= m - 1) {
-          const int mp = __ffs(m) - 1;
-          const float4 el = __ldg(a.el4 + kq * NW + mp);
-          const float dm = (en_hi - el.x) + (en_lo - el.y);
-          const float f = el.z;
-          float inv_s = a.inv_sigma, norm = 1.f;  // adaptive: 1/sigma of the pair, inside the sum
-          if constexpr (AD) {
-            inv_s = 1.f / adaptive_width(vn, __ldg(a.vel + kq * NW + mp), a.cB, a.sigma_min);
-            norm = inv_s;
+    for (int u = 0; u < NQ; ++u) {
+      const int w = list[it + u];
+      needs[u] = (unsigned)w >> 16;
+      jxs[u] = w & 0xff;
+    }
+    const int l = (list[it] >> 8) & 0xff;
+    const int jy = r * L + l;
+    float2 G[NQ][NM][MW];
+    dft_x_line<NW, NM, MW, EP, NQ>(Yb + (size_t)l * LS, Exs, xS, xD, a.K, a.K0, a.KP, jxs, j, G);
+    int fy = kc[1] + jy * sy;
+    fy -= fy >= nfy ? nfy : 0;
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) {
+      const int jx = jxs[u];
+      const int q = (jx * Ny + jy) * a.Nz + jz;
+      int fx = kc[0] + jx * sx;
+      fx -= fx >= nfx ? nfx : 0;
+      const int64_t kq = (int64_t)(fx * nfy + fy) * nfz + fz;
+      const float2* zt = a.ZT + (int64_t)q * NM * NM;
+      const float2* onb = a.omnb + (int64_t)q * NM;
+      for (unsigned m = needs[u]; m; m &= m - 1) {
+        const int mp = __ffs(m) - 1;
+        const float4 el = __ldg(a.el4 + kq * NW + mp);
+        const float dm = (en_hi - el.x) + (en_lo - el.y);
+        const float f = el.z;
+        float inv_s = a.inv_sigma, norm = 1.f;  // adaptive: 1/sigma of the pair, inside the sum
+        if constexpr (AD) {
+          inv_s = 1.f / adaptive_width(vn, __ldg(a.vel + kq * NW + mp), a.cB, a.sigma_min);
+          norm = inv_s;
+        }
+        float2 uu[MW];
+        load_cplx<MW>(a.UH + (kq * NW + mp) * NW + j * MW, uu);
+        float2 t[NM];
+#pragma unroll
+        for (int sa = 0; sa < NM; ++sa) {
+          t[sa] = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int mm = 0; mm < MW; ++mm) {
+            t[sa].x = fmaf(uu[mm].x, G[u][sa][mm].x, fmaf(-uu[mm].y, G[u][sa][mm].y, t[sa].x));
+            t[sa].y = fmaf(uu[mm].x, G[u][sa][mm].y, fmaf(uu[mm].y, G[u][sa][mm].x, t[sa].y));
           }
-          float2 uu[MW];
-          load_cplx<MW>(a.UH + (kq * NW + mp) * NW + j * MW, uu);
-          float2 t[NM];
+        }
+        float2 ov = make_float2(0.f, 0.f);  // polar term: [U_{k+q}^dagger U_k]_{m'n}, lane's m range
+        if constexpr (PL) {
+#pragma unroll
+          for (int mm = 0; mm < MW; ++mm) {
+            const float2 w = uk_s[j * MW + mm];
+            ov.x = fmaf(uu[mm].x, w.x, fmaf(-uu[mm].y, w.y, ov.x));
+            ov.y = fmaf(uu[mm].x, w.y, fmaf(uu[mm].y, w.x, ov.y));
+          }
+        }
+#pragma unroll
+        for (int o = 1; o < SPLIT; o <<= 1) {
 #pragma unroll
           for (int sa = 0; sa < NM; ++sa) {
-            t[sa] = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int mm = 0; mm < MW; ++mm) {
-              t[sa].x = fmaf(uu[mm].x, G[u][sa][mm].x, fmaf(-uu[mm].y, G[u][sa][mm].y, t[sa].x));
-              t[sa].y = fmaf(uu[mm].x, G[u][sa][mm].y, fmaf(uu[mm].y, G[u][sa][mm].x, t[sa].y));
-            }
+            t[sa].x += __shfl_xor_sync(gmask, t[sa].x, o);
+            t[sa].y += __shfl_xor_sync(gmask, t[sa].y, o);
           }
-          float2 ov = make_float2(0.f, 0.f);  // polar term: [U_{k+q}^dagger U_k]_{m'n}, lane's m range
           if constexpr (PL) {
-#pragma unroll
-            for (int mm = 0; mm < MW; ++mm) {
-              const float2 w = uk_s[j * MW + mm];
-              ov.x = fmaf(uu[mm].x, w.x, fmaf(-uu[mm].y, w.y, ov.x));
-              ov.y = fmaf(uu[mm].x, w.y, fmaf(uu[mm].y, w.x, ov.y));
-            }
+            ov.x += __shfl_xor_sync(gmask, ov.x, o);
+            ov.y += __shfl_xor_sync(gmask, ov.y, o);
           }
+        }
+        for (int v = j; v < NM; v += SPLIT) {
+          float2 z[NM];
+          load_cplx<NM>(zt + v * NM, z);
+          float2 g = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int o = 1; o < SPLIT; o <<= 1) {
-#pragma unroll
-            for (int sa = 0; sa < NM; ++sa) {
-              t[sa].x += __shfl_xor_sync(gmask, t[sa].x, o);
-              t[sa].y += __shfl_xor_sync(gmask, t[sa].y, o);
-            }
-            if constexpr (PL) {
-              ov.x += __shfl_xor_sync(gmask, ov.x, o);
-              ov.y += __shfl_xor_sync(gmask, ov.y, o);
-            }
+          for (int sa = 0; sa < NM; ++sa) {
+            g.x = fmaf(t[sa].x, z[sa].x, fmaf(-t[sa].y, z[sa].y, g.x));
+            g.y = fmaf(t[sa].x, z[sa].y, fmaf(t[sa].y, z[sa].x, g.y));
           }
-          for (int v = j; v < NM; v += SPLIT) {
-            float2 z[NM];
-            load_cplx<NM>(zt + v * NM, z);
-            float2 g = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int sa = 0; sa < NM; ++sa) {
-              g.x = fmaf(t[sa].x, z[sa].x, fmaf(-t[sa].y, z[sa].y, g.x));
-              g.y = fmaf(t[sa].x, z[sa].y, fmaf(t[sa].y, z[sa].x, g.y));
-            }
-            if constexpr (PL) {  // + g^L = L_{q nu} [U_{k+q}^dagger U_k]_{m'n}
-              const float2 l = __ldg(a.gL + (int64_t)q * NM + v);
-              g.x = fmaf(l.x, ov.x, fmaf(-l.y, ov.y, g.x));
-              g.y = fmaf(l.x, ov.y, fmaf(l.y, ov.x, g.y));
-            }
-            const float2 on = __ldg(onb + v);
-            const float t1 = (dm - on.x) * inv_s;
-            const float t2 = (dm + on.x) * inv_s;
-            const float g2 = g.x * g.x + g.y * g.y;
-            float wgt = 0.f;
-            if (t1 * t1 < a.cut2) {
-              const float e1 = expf(-t1 * t1);
-              wgt += (on.y + 1.f - f) * e1;
-              if constexpr (PR)  // this state's share of P_{q nu}: |g|^2 e^{-t1^2} f(1-f)/kT (emission delta)
-                atomicAdd(a.pacc + (int64_t)q * NM + v, (double)(g2 * e1) * pw);
-            }
-            if (t2 * t2 < a.cut2) wgt += (on.y + f) * expf(-t2 * t2);
-            acc = fmaf(g2, wgt * norm, acc);
+          if constexpr (PL) {  // + g^L = L_{q nu} [U_{k+q}^dagger U_k]_{m'n}
+            const float2 lq = __ldg(a.gL + (int64_t)q * NM + v);
+            g.x = fmaf(lq.x, ov.x, fmaf(-lq.y, ov.y, g.x));
+            g.y = fmaf(lq.x, ov.y, fmaf(lq.y, ov.x, g.y));
           }
+          const float2 on = __ldg(onb + v);
+          const float t1 = (dm - on.x) * inv_s;
+          const float t2 = (dm + on.x) * inv_s;
+          const float g2 = g.x * g.x + g.y * g.y;
+          float wgt = 0.f;
+          if (t1 * t1 < a.cut2) {
+            const float e1 = expf(-t1 * t1);
+            wgt += (on.y + 1.f - f) * e1;
+            if constexpr (PR)  // this state's share of P_{q nu}: |g|^2 e^{-t1^2} f(1-f)/kT (emission delta)
+              atomicAdd(a.pacc + (int64_t)q * NM + v, (double)(g2 * e1) * pw);
+          }
+          if (t2 * t2 < a.cut2) wgt += (on.y + f) * expf(-t2 * t2);
+          acc = fmaf(g2, wgt * norm, acc);
         }
       }
     }
-    if (threadIdx.x == 0) atomicAdd(a.nq_evaluated, (unsigned long long)total);
-    // phase 0 of the next run (into the other list) while other warps finish this run's q
-    if (jy0 + L < a.Ny) phase0(jy0 + L, b ^ 1);
+    return acc;
+  };
+
+  double accd = 0.0;  // this warp's x tasks (every lane holds the same value)
+
+  // prologue: the lists of runs 0 and 1, then (slice landed) the Y rows of run 0
+  {
+    const int n0 = list_tasks(0), n1 = R > 1 ? list_tasks(1) : 0;
+    for (int t = warp; t < n0 + n1; t += NWARP) {
+      if (t < n0)
+        list_task(0, t);
+      else
+        list_task(1, t - n0);
+    }
   }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) red[warp] = (double)acc;
+  cp_async_wait_all();
+  __syncthreads();
+  for (int t = warp; t < y_tasks; t += NWARP) y_task(0, t);
+  __syncthreads();
+  for (int r = 0; r < R; ++r) {
+    const int total = cnt[r & 3];
+    if (threadIdx.x == 0) {
+      // cnt[(r - 1) % 4] was read in iteration r - 1 and is next written by the listing of run
+      // r + 3 in iteration r + 1; wq[(r + 1) % 2] was last used in iteration r - 1
+      cnt[(r + 3) & 3] = 0;
+      wq[(r + 1) & 1] = 0;
+      atomicAdd(a.nq_evaluated, (unsigned long long)total);
+    }
+    const int nx = (total + XT - 1) / XT;
+    const int ny = r + 1 < R ? y_tasks : 0;
+    const int np = r + 2 < R ? list_tasks(r + 2) : 0;
+    const int ntask = nx + ny + np;
+    for (;;) {
+      int t = 0;
+      if (lane == 0) t = atomicAdd(wq + (r & 1), 1);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      if (t >= ntask) break;
+      if (t < nx) {
+        // the task's sum in a fixed order, then FP64: which warp takes which task does not change
+        // the result beyond FP64 rounding
+        float part = x_task(r, t, total);
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        accd += (double)part;
+      } else if (t < nx + ny)
+        y_task(r + 1, t - nx);
+      else
+        list_task(r + 2, t - nx - ny);
+    }
+    __syncthreads();
+  }
+  if (lane == 0) red[warp] = accd;
   __syncthreads();
   if (threadIdx.x == 0) {
     double sum = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) sum += red[i];
+    for (int i = 0; i < NWARP; ++i) sum += red[i];
     if (sum != 0.0) atomicAdd(a.gamma + a.s_base + s, sum * a.scale);
   }
 }
@@ -731,9 +783,9 @@ int dft_launch(cudaStream_t st, const DftZArgs& z, const DftXArgs& x, int S, int
 
 size_t dft_smem_bytes(int P, int Bx, int By, int nw, int nm, int Nx, int Ny, int K) {
   const int E = nw * nm;
-  return sizeof(float2) * ((size_t)P * E + (size_t)(P * E) % 2 + (size_t)Bx * kDftLines * dft_row_stride(E, nw) +
-                           (size_t)Nx * K + 2 * (size_t)kDftLines * By) +
-         sizeof(int) * ((size_t)Bx + 1 + 2 * (size_t)K + 2 * (size_t)P + 2 * (size_t)dft_list_cap(kDftLines, Nx));
+  return sizeof(float2) * ((size_t)P * E + (size_t)(P * E) % 2 + 2 * (size_t)kDftLines * dft_line_stride(Bx, E, nw) +
+                           (size_t)Nx * K + (size_t)Ny * By) +
+         sizeof(int) * ((size_t)Bx + 1 + 2 * (size_t)K + 2 * (size_t)P + 3 * (size_t)dft_list_cap(kDftLines, Nx));
 }
 
 size_t dft_z_smem_bytes(int ne_plane_max, int E, int Nz, int Bz) {

@@ -8,6 +8,9 @@ namespace phx {
 #ifndef PHX_DFT_LINES
 #define PHX_DFT_LINES 8
 #endif
+#ifndef PHX_DFT_UNIT
+#define PHX_DFT_UNIT (PHX_DFT_LINES % 4 == 0 ? 4 : PHX_DFT_LINES % 3 == 0 ? 3 : PHX_DFT_LINES <= 8 ? PHX_DFT_LINES : 1)
+#endif
 #ifndef PHX_DFT_SPLIT8
 #define PHX_DFT_SPLIT8 4
 #endif
@@ -15,7 +18,8 @@ namespace phx {
 #define PHX_DFT_THREADS 256
 #endif
 #ifndef PHX_DFT_MINB
-#define PHX_DFT_MINB 3
+#define PHX_DFT_MINB 2  // blocks per SM the register budget of the one-q kernel is sized for (two Y buffers
+                        // keep shared memory at two blocks per SM)
 #endif
 #ifndef PHX_DFT_MINB2
 #define PHX_DFT_MINB2 2  // blocks per SM the register budget of the two-q kernel is sized for
@@ -23,7 +27,7 @@ namespace phx {
 constexpr int kDftLines = PHX_DFT_LINES;      // jy lines (at one jz) per run of the fused kernel
 constexpr int kDftXThreads = PHX_DFT_THREADS;  // threads per block of the fused kernel
 constexpr int kDftSplit8 = PHX_DFT_SPLIT8;     // lanes per q of the x sum at nw = 8
-constexpr int kDftUnitLines = kDftLines < 4 ? kDftLines : 4;  // lines per work unit of the y sum
+constexpr int kDftUnitLines = PHX_DFT_UNIT;   // lines per work unit of the y sum
 static_assert(kDftLines % kDftUnitLines == 0 && kDftLines <= 256, "lines per block: a multiple of the y-sum unit, at most 256");
 
 // The R_p set grouped by residues r = R mod N: entries sorted by (rx, ry, rz) residue index,

@@ -2157,10 +2157,10 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
   CK(c, cudaStreamSynchronize(c->stream));
   if (herr) return fail(c, PHOEBE_GPU_ERR_TIMEOUT, "a tensor-core pipeline wait ran out; results discarded");
   c->stats.pairs_executed = (int64_t)n_x;
-  // complex MACs of the DFT as evaluated: z sum over the entries, y sum over the pairs for every
-  // line the fused kernel covers (runs of kDftLines jy), x sum per evaluated (state, q)
-  const double ny_cov = (double)((Ny + kDftLines - 1) / kDftLines) * kDftLines;
-  const double zy_cmac = ((double)nRp * Nz + (double)P * ny_cov * Nz) * E;
+  // complex MACs of the DFT: z sum over the entries, y sum over the pairs for every (jy, jz) line
+  // (the lines a last, partial run of the fused kernel pads with are not counted), x sum per
+  // evaluated (state, q)
+  const double zy_cmac = ((double)nRp * Nz + (double)P * Ny * Nz) * E;
   // x sum: 4 FMA per complex value per residue pair or unpaired residue, 2 per real-factor residue
   double x_rows = 0.0;
   for (int k = 0; k < K; ++k) x_rows += xD[k] < 0 ? 0.5 : 1.0;
