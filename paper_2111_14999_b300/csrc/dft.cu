@@ -10,6 +10,8 @@
 // tensor-core epilogue.  FP32 on the CUDA cores.
 #include <algorithm>
 
+#include <type_traits>
+
 #include "dft.h"
 
 namespace phx {
@@ -115,7 +117,7 @@ __global__ void __launch_bounds__(256) k_dft_z(DftZArgs a) {
   }
 }
 
-// 16-byte (or 8-byte) asynchronous global -> shared copies (cp.async).
+// 16-, 8- or 4-byte asynchronous global -> shared copies (cp.async).
 __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
@@ -123,6 +125,10 @@ __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
 __device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
@@ -289,6 +295,26 @@ __device__ __forceinline__ void dft_x_line(const float2* __restrict__ Yl, const 
   }
 }
 
+// Complex-vector helpers of the y sum: float2 = one complex value, float4 = two.
+template <class V> __device__ __forceinline__ V vzero();
+template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ float4 vzero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float4 vadd(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+__device__ __forceinline__ float4 vsub(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+// acc += c p + i s m for e = (c, s), per complex value
+__device__ __forceinline__ void vcis_acc(float2& acc, float2 e, float2 p, float2 m) {
+  acc.x = fmaf(e.x, p.x, fmaf(-e.y, m.y, acc.x));
+  acc.y = fmaf(e.x, p.y, fmaf(e.y, m.x, acc.y));
+}
+__device__ __forceinline__ void vcis_acc(float4& acc, float2 e, float4 p, float4 m) {
+  acc.x = fmaf(e.x, p.x, fmaf(-e.y, m.y, acc.x));
+  acc.y = fmaf(e.x, p.y, fmaf(e.y, m.x, acc.y));
+  acc.z = fmaf(e.x, p.z, fmaf(-e.y, m.w, acc.z));
+  acc.w = fmaf(e.x, p.w, fmaf(e.y, m.z, acc.w));
+}
+
 // Adaptive Gaussian width of a pair of states (Sec. 4.7): the energy change across one mesh
 // cell along each reciprocal vector, summed in quadrature over the three, over sqrt 12.
 __device__ __forceinline__ float adaptive_width(const float4 va, const float4 vb, const float* __restrict__ cB,
@@ -330,16 +356,16 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
   const int P = a.P, Bx = a.Bx, By = a.By, Nx = a.Nx, Ny = a.Ny;
   const int LS = dft_line_stride(Bx, E, NW);                 // complex values per line of a Y buffer
   const int YB = L * LS;                                     // complex values per Y buffer
-  float2* Zsl = reinterpret_cast<float2*>(smem);             // [P][E]
-  float2* Ys = Zsl + (size_t)P * E + (P * E) % 2;            // [2][L][LS]
-  float2* Exs = Ys + (size_t)2 * YB;                         // [Nx][K]
-  float2* Eys = Exs + (size_t)Nx * a.K;                      // [Ny][By]
-  int* ppo = reinterpret_cast<int*>(Eys + (size_t)Ny * By);  // [Bx+1]
-  int* xS = ppo + Bx + 1;                                    // [K]
-  int* xD = xS + a.K;                                        // [K]
-  int* pay = xD + a.K;                                       // [P]
-  int* mate = pay + P;                                       // [P]
-  int* lists = mate + P;                                     // [3][lcap], run r in list r % 3
+  float2* Zsl = reinterpret_cast<float2*>(smem);                   // [P+1][E], row P = 0
+  float2* Ys = Zsl + (size_t)(P + 1) * E + ((P + 1) * E) % 2;      // [2][L][LS]
+  float2* Exs = Ys + (size_t)2 * YB;                               // [Nx][K]
+  float2* Eys = Exs + (size_t)Nx * a.K;                            // [Ny][By]
+  int4* gidx = reinterpret_cast<int4*>(Eys + (size_t)Ny * By + (Nx * a.K + Ny * By) % 2);  // [G]
+  int* gro = reinterpret_cast<int*>(gidx + a.G);                   // [K+1]
+  int* gay = gro + a.K + 1;                                        // [G]
+  int* xS = gay + a.G;                                             // [K]
+  int* xD = xS + a.K;                                              // [K]
+  int* lists = xD + a.K;                                           // [3][lcap], run r in list r % 3
   const int lcap = dft_list_cap(L, Nx);
   __shared__ int cnt[4];  // list length of run r in cnt[r % 4]
   __shared__ int wq[2];   // task counter of iteration r in wq[r % 2]
@@ -376,17 +402,19 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
       for (int i = threadIdx.x; i < P * E; i += blockDim.x) cp_async8(Zsl + i, zg + i);
     }
   }
-  for (int i = threadIdx.x; i < Nx * a.K; i += blockDim.x) Exs[i] = a.Ex[i];
-  for (int i = threadIdx.x; i < Ny * By; i += blockDim.x) Eys[i] = a.Ey[i];
+  // the tables, all in flight at once beside the slice
+  for (int i = threadIdx.x; i < Nx * a.K; i += blockDim.x) cp_async8(Exs + i, a.Ex + i);
+  for (int i = threadIdx.x; i < Ny * By; i += blockDim.x) cp_async8(Eys + i, a.Ey + i);
+  for (int i = threadIdx.x; i < a.G; i += blockDim.x) {
+    cp_async16(gidx + i, a.grp_idx + i);
+    cp_async4(gay + i, a.grp_ay + i);
+  }
+  for (int i = threadIdx.x; i <= a.K; i += blockDim.x) cp_async4(gro + i, a.row_grp_off + i);
   for (int i = threadIdx.x; i < a.K; i += blockDim.x) {
-    xS[i] = a.xS[i];
-    xD[i] = a.xD[i];
+    cp_async4(xS + i, a.xS + i);
+    cp_async4(xD + i, a.xD + i);
   }
-  for (int i = threadIdx.x; i <= Bx; i += blockDim.x) ppo[i] = a.plane_pair_off[i];
-  for (int i = threadIdx.x; i < P; i += blockDim.x) {
-    pay[i] = a.pair_ay[i];
-    mate[i] = a.pair_mate[i];
-  }
+  for (int i = threadIdx.x; i < E; i += blockDim.x) Zsl[(size_t)P * E + i] = make_float2(0.f, 0.f);
   int kc[3];
   grid_coords(a.gm.k_to_fine(a.st_k[s]), a.gm.nf, kc);
   // fine-grid coordinates of k+q: k_d + j_d * s_d with k_d < nf_d and j_d * s_d < nf_d, so one
@@ -396,7 +424,8 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
   int fz = kc[2] + jz * a.gm.sq[2];
   fz -= fz >= nfz ? nfz : 0;
   const float inv_nx = 1.f / (float)Nx;  // qi < 2^16, Nx <= 256: (qi + 0.5) / Nx truncates exactly
-  __syncthreads();  // counters, en_s, tables
+  cp_async_wait_all();
+  __syncthreads();  // counters, en_s, tables, the slice
   const float en_hi = en_s[0], en_lo = en_s[1];
   const double pw = PR ? pw_s : 0.0;
   const float4 vn = AD ? vn_s : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -467,105 +496,75 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
     }
   };
 
-  // y task t of run rr into Y buffer rr % 2, one unit per lane.  For a residue pair row k
-  // (planes a = xS[k], b = xD[k], the pairs of b mirroring those of a) the rows are formed
-  // directly as S = Y_a + Y_b and D = Y_a - Y_b: with Z1 = Zs[(a, ry)], Z2 = Zs[(b, -ry)] and
-  // Ey[jy][ry] = c + i s,
-  //   S = sum_ry c (Z1 + Z2) + i s (Z1 - Z2),   D = sum_ry c (Z1 - Z2) + i s (Z1 + Z2).
-  // Other rows: Y_a = sum_ry Ey Z1.  Unit = (row, kDftUnitLines lines, column vector); lines past
-  // the grid edge read the last Ey row (never listed, never read).
+  // y task t of run rr into Y buffer rr % 2, one unit per lane; unit = (x row, kDftUnitLines lines,
+  // column vector).  With Ey[jy][r] = c + i s and Ey[jy][-r] = c - i s, a y group {r, -r} adds
+  // c Z+ + i s Z- to Y_a, where Z+- = Z(a, r) +- Z(a, -r).  A residue pair row k (planes a = xS[k],
+  // b = xD[k]) is formed directly as S = Y_a + Y_b and D = Y_a - Y_b:
+  //   S += c (Za+ + Zb+) + i s (Za- + Zb-),   D += c (Za+ - Zb+) + i s (Za- - Zb-);
+  // other rows: Y_a += c Za+ + i s Za-.  Absent combinations read the zero row.  Lines past the
+  // grid edge read the last Ey row (never listed, never read).
   constexpr int CV = E % 2 == 0 ? E / 2 : E;  // column vectors per row (float4 when E is even)
+  using VT = typename std::conditional<E % 2 == 0, float4, float2>::type;
   const int npu = a.KP * (L / UL) * CV;
-  const int units = Bx * (L / UL) * CV - npu;  // each pair unit covers two planes
+  const int units = a.K * (L / UL) * CV;
   const int y_tasks = (units + 31) / 32;
   auto y_task = [&](int rr, int t) {
     const int u = t * 32 + lane;
     if (u >= units) return;
-    float2* Yb = Ys + (size_t)(rr & 1) * YB;
-    const bool pr = u < npu;
+    VT* Yb = reinterpret_cast<VT*>(Ys + (size_t)(rr & 1) * YB);
+    const VT* Zv = reinterpret_cast<const VT*>(Zsl);
+    constexpr int RV = E / (int)(sizeof(VT) / sizeof(float2));  // vectors per Zs / Y row
+    const bool pr = u < npu;  // pair-row units first: they cost about twice as much
     const int uu = pr ? u : u - npu;
     const int cv = uu % CV, rest = uu / CV;
     const int lh = rest % (L / UL), kk = rest / (L / UL);
     const int k = pr ? a.K0 + kk : (kk < a.K0 ? kk : kk + a.KP);
-    const int ra = xS[k];
     int eo[UL];
 #pragma unroll
     for (int l = 0; l < UL; ++l) eo[l] = min(rr * L + lh * UL + l, Ny - 1) * By;
-    if constexpr (E % 2 == 0) {
-      float4 s4[UL], d4[UL];
+    VT sv[UL], dv[UL];
 #pragma unroll
-      for (int l = 0; l < UL; ++l) {
-        s4[l] = make_float4(0.f, 0.f, 0.f, 0.f);
-        d4[l] = make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-      if (pr) {
-        for (int p = ppo[ra]; p < ppo[ra + 1]; ++p) {
-          const float4 z1 = reinterpret_cast<const float4*>(Zsl + (size_t)p * E)[cv];
-          const float4 z2 = reinterpret_cast<const float4*>(Zsl + (size_t)mate[p] * E)[cv];
-          const float4 pp = make_float4(z1.x + z2.x, z1.y + z2.y, z1.z + z2.z, z1.w + z2.w);
-          const float4 mm = make_float4(z1.x - z2.x, z1.y - z2.y, z1.z - z2.z, z1.w - z2.w);
-          const int ay = pay[p];
-#pragma unroll
-          for (int l = 0; l < UL; ++l) {
-            const float2 ey = Eys[eo[l] + ay];
-            s4[l].x = fmaf(ey.x, pp.x, fmaf(-ey.y, mm.y, s4[l].x));
-            s4[l].y = fmaf(ey.x, pp.y, fmaf(ey.y, mm.x, s4[l].y));
-            s4[l].z = fmaf(ey.x, pp.z, fmaf(-ey.y, mm.w, s4[l].z));
-            s4[l].w = fmaf(ey.x, pp.w, fmaf(ey.y, mm.z, s4[l].w));
-            d4[l].x = fmaf(ey.x, mm.x, fmaf(-ey.y, pp.y, d4[l].x));
-            d4[l].y = fmaf(ey.x, mm.y, fmaf(ey.y, pp.x, d4[l].y));
-            d4[l].z = fmaf(ey.x, mm.z, fmaf(-ey.y, pp.w, d4[l].z));
-            d4[l].w = fmaf(ey.x, mm.w, fmaf(ey.y, pp.z, d4[l].w));
-          }
-        }
-        const int rb = xD[k];
-#pragma unroll
-        for (int l = 0; l < UL; ++l) {
-          reinterpret_cast<float4*>(Yb + (size_t)(lh * UL + l) * LS + ra * EP)[cv] = s4[l];
-          reinterpret_cast<float4*>(Yb + (size_t)(lh * UL + l) * LS + rb * EP)[cv] = d4[l];
-        }
-      } else {
-        for (int p = ppo[ra]; p < ppo[ra + 1]; ++p) {
-          const float4 z = reinterpret_cast<const float4*>(Zsl + (size_t)p * E)[cv];
-          const int ay = pay[p];
-#pragma unroll
-          for (int l = 0; l < UL; ++l) {
-            const float2 ey = Eys[eo[l] + ay];
-            s4[l].x = fmaf(ey.x, z.x, fmaf(-ey.y, z.y, s4[l].x));
-            s4[l].y = fmaf(ey.x, z.y, fmaf(ey.y, z.x, s4[l].y));
-            s4[l].z = fmaf(ey.x, z.z, fmaf(-ey.y, z.w, s4[l].z));
-            s4[l].w = fmaf(ey.x, z.w, fmaf(ey.y, z.z, s4[l].w));
-          }
-        }
-#pragma unroll
-        for (int l = 0; l < UL; ++l) reinterpret_cast<float4*>(Yb + (size_t)(lh * UL + l) * LS + ra * EP)[cv] = s4[l];
-      }
-    } else {
-      float2 s2[UL], d2[UL];
-#pragma unroll
-      for (int l = 0; l < UL; ++l) {
-        s2[l] = make_float2(0.f, 0.f);
-        d2[l] = make_float2(0.f, 0.f);
-      }
-      for (int p = ppo[ra]; p < ppo[ra + 1]; ++p) {
-        const float2 z1 = Zsl[(size_t)p * E + cv];
-        const float2 z2 = pr ? Zsl[(size_t)mate[p] * E + cv] : make_float2(0.f, 0.f);
-        const float2 pp = make_float2(z1.x + z2.x, z1.y + z2.y), mm = make_float2(z1.x - z2.x, z1.y - z2.y);
-        const int ay = pay[p];
+    for (int l = 0; l < UL; ++l) {
+      sv[l] = vzero<VT>();
+      dv[l] = vzero<VT>();
+    }
+    const int g0 = gro[k], g1 = gro[k + 1];
+    if (pr) {
+      for (int g = g0; g < g1; ++g) {
+        const int4 gi = gidx[g];
+        const VT z1 = Zv[gi.x * RV + cv], z2 = Zv[gi.y * RV + cv];
+        const VT z3 = Zv[gi.z * RV + cv], z4 = Zv[gi.w * RV + cv];
+        const VT ap = vadd(z1, z2), am = vsub(z1, z2), bp = vadd(z3, z4), bm = vsub(z3, z4);
+        const VT ps = vadd(ap, bp), ms = vadd(am, bm), pd = vsub(ap, bp), md = vsub(am, bm);
+        const int ay = gay[g];
 #pragma unroll
         for (int l = 0; l < UL; ++l) {
           const float2 ey = Eys[eo[l] + ay];
-          s2[l].x = fmaf(ey.x, pp.x, fmaf(-ey.y, mm.y, s2[l].x));
-          s2[l].y = fmaf(ey.x, pp.y, fmaf(ey.y, mm.x, s2[l].y));
-          d2[l].x = fmaf(ey.x, mm.x, fmaf(-ey.y, pp.y, d2[l].x));
-          d2[l].y = fmaf(ey.x, mm.y, fmaf(ey.y, pp.x, d2[l].y));
+          vcis_acc(sv[l], ey, ps, ms);
+          vcis_acc(dv[l], ey, pd, md);
         }
       }
+      const int ra = xS[k] * EP, rb = xD[k] * EP;
+      constexpr int VW = (int)(sizeof(VT) / sizeof(float2));
 #pragma unroll
       for (int l = 0; l < UL; ++l) {
-        Yb[(size_t)(lh * UL + l) * LS + ra * EP + cv] = s2[l];
-        if (pr) Yb[(size_t)(lh * UL + l) * LS + xD[k] * EP + cv] = d2[l];
+        const size_t lo = (size_t)(lh * UL + l) * LS;
+        Yb[(lo + ra) / VW + cv] = sv[l];
+        Yb[(lo + rb) / VW + cv] = dv[l];
       }
+    } else {
+      for (int g = g0; g < g1; ++g) {
+        const int4 gi = gidx[g];
+        const VT z1 = Zv[gi.x * RV + cv], z2 = Zv[gi.y * RV + cv];
+        const VT ap = vadd(z1, z2), am = vsub(z1, z2);
+        const int ay = gay[g];
+#pragma unroll
+        for (int l = 0; l < UL; ++l) vcis_acc(sv[l], Eys[eo[l] + ay], ap, am);
+      }
+      const int ra = xS[k] * EP;
+      constexpr int VW = (int)(sizeof(VT) / sizeof(float2));
+#pragma unroll
+      for (int l = 0; l < UL; ++l) Yb[((size_t)(lh * UL + l) * LS + ra) / VW + cv] = sv[l];
     }
   };
 
@@ -681,37 +680,30 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
 
   double accd = 0.0;  // this warp's x tasks (every lane holds the same value)
 
-  // prologue: the lists of runs 0 and 1, then (slice landed) the Y rows of run 0
-  {
-    const int n0 = list_tasks(0), n1 = R > 1 ? list_tasks(1) : 0;
-    for (int t = warp; t < n0 + n1; t += NWARP) {
-      if (t < n0)
-        list_task(0, t);
-      else
-        list_task(1, t - n0);
-    }
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  for (int t = warp; t < y_tasks; t += NWARP) y_task(0, t);
-  __syncthreads();
-  for (int r = 0; r < R; ++r) {
-    const int total = cnt[r & 3];
+  // Iteration r = -1 .. R-1: the x tasks of run r, the y tasks of run r+1, the listing tasks of run
+  // r+2 (and, at r = -1, of run 0).  A warp's first task of an iteration is its warp index, further
+  // ones come from the counter.
+  for (int r = -1; r < R; ++r) {
+    const int total = r >= 0 ? cnt[r & 3] : 0;
     if (threadIdx.x == 0) {
       // cnt[(r - 1) % 4] was read in iteration r - 1 and is next written by the listing of run
       // r + 3 in iteration r + 1; wq[(r + 1) % 2] was last used in iteration r - 1
       cnt[(r + 3) & 3] = 0;
       wq[(r + 1) & 1] = 0;
-      atomicAdd(a.nq_evaluated, (unsigned long long)total);
+      if (r >= 0) atomicAdd(a.nq_evaluated, (unsigned long long)total);
     }
     const int nx = (total + XT - 1) / XT;
     const int ny = r + 1 < R ? y_tasks : 0;
     const int np = r + 2 < R ? list_tasks(r + 2) : 0;
-    const int ntask = nx + ny + np;
-    for (;;) {
-      int t = 0;
-      if (lane == 0) t = atomicAdd(wq + (r & 1), 1);
-      t = __shfl_sync(0xffffffffu, t, 0);
+    const int n0 = r < 0 ? list_tasks(0) : 0;
+    const int ntask = nx + ny + np + n0;
+    for (bool first = true;; first = false) {
+      int t = warp;
+      if (!first) {
+        int tn = 0;
+        if (lane == 0) tn = atomicAdd(wq + (r & 1), 1);
+        t = NWARP + __shfl_sync(0xffffffffu, tn, 0);
+      }
       if (t >= ntask) break;
       if (t < nx) {
         // the task's sum in a fixed order, then FP64: which warp takes which task does not change
@@ -719,10 +711,12 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
         float part = x_task(r, t, total);
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
         accd += (double)part;
-      } else if (t < nx + ny)
+      } else if (t < nx + ny) {
         y_task(r + 1, t - nx);
-      else
-        list_task(r + 2, t - nx - ny);
+      } else {
+        const bool run0 = t >= nx + ny + np;  // the listing of run 0 (iteration -1)
+        list_task(run0 ? 0 : r + 2, t - nx - ny - (run0 ? np : 0));
+      }
     }
     __syncthreads();
   }
@@ -737,7 +731,7 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
 
 template <int NW, int NM, int SPLIT, bool PR, int NQ, bool AD, bool PL = false>
 static int launch_yx_t(cudaStream_t st, const DftXArgs& a, int S) {
-  const size_t smem = dft_smem_bytes(a.P, a.Bx, a.By, NW, NM, a.Nx, a.Ny, a.K);
+  const size_t smem = dft_smem_bytes(a.P, a.Bx, a.By, NW, NM, a.Nx, a.Ny, a.K, a.G);
   if (cudaFuncSetAttribute(k_dft_yx_elph<NW, NM, SPLIT, PR, NQ, AD, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return -1;
@@ -781,11 +775,12 @@ int dft_launch(cudaStream_t st, const DftZArgs& z, const DftXArgs& x, int S, int
   return -2;
 }
 
-size_t dft_smem_bytes(int P, int Bx, int By, int nw, int nm, int Nx, int Ny, int K) {
-  const int E = nw * nm;
-  return sizeof(float2) * ((size_t)P * E + (size_t)(P * E) % 2 + 2 * (size_t)kDftLines * dft_line_stride(Bx, E, nw) +
-                           (size_t)Nx * K + (size_t)Ny * By) +
-         sizeof(int) * ((size_t)Bx + 1 + 2 * (size_t)K + 2 * (size_t)P + 3 * (size_t)dft_list_cap(kDftLines, Nx));
+size_t dft_smem_bytes(int P, int Bx, int By, int nw, int nm, int Nx, int Ny, int K, int G) {
+  const size_t E = (size_t)nw * nm;
+  const size_t c2 = (P + 1) * E + ((P + 1) * E) % 2 + 2 * (size_t)kDftLines * dft_line_stride(Bx, (int)E, nw) +
+                    (size_t)Nx * K + (size_t)Ny * By + ((size_t)Nx * K + (size_t)Ny * By) % 2;
+  return sizeof(float2) * c2 + sizeof(int4) * (size_t)G +
+         sizeof(int) * ((size_t)K + 1 + (size_t)G + 2 * (size_t)K + 3 * (size_t)dft_list_cap(kDftLines, Nx));
 }
 
 size_t dft_z_smem_bytes(int ne_plane_max, int E, int Nz, int Bz) {

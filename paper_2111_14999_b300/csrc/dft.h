@@ -57,9 +57,13 @@ struct DftZArgs {
 struct DftXArgs {
   const float2* Zs;           // [S][Nz][P][E]
   int P, Bx, By, Nx, Ny, Nz;
-  const int* plane_pair_off;  // [Bx+1]
-  const int* pair_ay;         // [P] ry residue index of each pair
-  const int* pair_mate;       // [P] for the pairs of plane xS[k] of a pair row k: the pair (xD[k], -ry)
+  // y groups: the ry residues of x row k (of plane xS[k], and of plane xD[k] for a pair row) grouped
+  // as {r, -r mod Ny}.  Group g holds the pair indices (xS[k], r), (xS[k], -r), (xD[k], r), (xD[k], -r),
+  // P where a combination is absent (a zero row), and grp_ay[g] = the residue index of r.
+  int G;
+  const int* row_grp_off;     // [K+1] first group of each x row
+  const int4* grp_idx;        // [G]
+  const int* grp_ay;          // [G]
   // x rows: the rx residues grouped by r -> -r (mod Nx).  Row k reads Y row xS[k]; a residue
   // with a partner r' = -r (xD[k] >= 0, != xS[k]) has its rows replaced by S = Y_r + Y_r' and
   // D = Y_r - Y_r' and contributes cos(t r) S + i sin(t r) D, t = 2 pi jx / Nx; a residue equal
@@ -123,7 +127,7 @@ constexpr bool kDftQPair = PHX_DFT_QPAIR != 0;  // two listed q per lane group (
 __host__ __device__ constexpr int dft_list_cap(int L, int Nx) { return L * Nx + 2 * ((L * Nx + 31) / 32) + 2; }
 // Lanes per q of the x sum for nw Wannier functions.
 __host__ __device__ constexpr int dft_split(int nw) { return nw == 8 ? kDftSplit8 : (nw % 2 == 0 ? 2 : 1); }
-size_t dft_smem_bytes(int P, int Bx, int By, int nw, int nm, int Nx, int Ny, int K);
+size_t dft_smem_bytes(int P, int Bx, int By, int nw, int nm, int Nx, int Ny, int K, int G);
 size_t dft_z_smem_bytes(int ne_plane_max, int E, int Nz, int Bz);
 int dft_table(cudaStream_t st, const int* res, int B, int N, float2* E);
 int polar_table(cudaStream_t st, const PolarArgs& a);

@@ -1959,36 +1959,17 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
   int ne_plane_max = 0;
   for (int a = 0; a < Bx; ++a)
     ne_plane_max = std::max(ne_plane_max, pair_ent_off[plane_pair_off[a + 1]] - pair_ent_off[plane_pair_off[a]]);
-  // x rows: pair each rx residue with its negative modulo Nx.  A pair (a, b) is taken when the
-  // (rx, ry) pairs of plane b are those of plane a with ry negated (true of inversion-symmetric R
-  // sets such as Wigner-Seitz sets); pair_mate then maps each pair of plane a to its mirror in b.
-  std::vector<int> pair_mate(P, -1);
-  auto planes_mirror = [&](int a, int b) {
-    if (plane_pair_off[a + 1] - plane_pair_off[a] != plane_pair_off[b + 1] - plane_pair_off[b]) return false;
-    for (int p = plane_pair_off[a]; p < plane_pair_off[a + 1]; ++p) {
-      const int ryn = (Ny - resv[1][pair_ay[p]]) % Ny;
-      int mate = -1;
-      for (int q = plane_pair_off[b]; q < plane_pair_off[b + 1]; ++q)
-        if (resv[1][pair_ay[q]] == ryn) mate = q;
-      if (mate < 0) return false;
-    }
-    return true;
-  };
+  // x rows: each rx residue paired with its negative modulo Nx; a pair row carries S = Y_r + Y_-r and
+  // D = Y_r - Y_-r.  Then the y groups of every x row: the ry residues present in its plane(s),
+  // grouped as {r, -r mod Ny}, with the pair indices of the four combinations (P if absent).
   std::vector<int> xS, xD, xres;
   int K0 = 0, KP = 0;
   for (int pass = 0; pass < 3; ++pass) {  // real-factor rows, then pairs, then unpaired residues
     for (int a = 0; a < Bx; ++a) {
       const int r = resv[0][a], rn = (Nx - r) % Nx;
-      int b = (int)(std::lower_bound(resv[0].begin(), resv[0].end(), rn) - resv[0].begin());
-      bool has = b < Bx && resv[0][b] == rn;
-      if (has && b != a && !planes_mirror(std::min(a, b), std::max(a, b))) has = false;
+      const int b = (int)(std::lower_bound(resv[0].begin(), resv[0].end(), rn) - resv[0].begin());
+      const bool has = b < Bx && resv[0][b] == rn;
       const int type = has && b == a ? 0 : has && b > a ? 1 : !has ? 2 : -1;
-      if (type == 1)
-        for (int p = plane_pair_off[a]; p < plane_pair_off[a + 1]; ++p) {
-          const int ryn = (Ny - resv[1][pair_ay[p]]) % Ny;
-          for (int q = plane_pair_off[b]; q < plane_pair_off[b + 1]; ++q)
-            if (resv[1][pair_ay[q]] == ryn) pair_mate[p] = q;
-        }
       if (type != pass) continue;
       xS.push_back(a);
       xD.push_back(type == 0 ? -1 : type == 1 ? b : a);
@@ -1998,17 +1979,47 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
     }
   }
   const int K = (int)xS.size();
-  if (dft_smem_bytes(P, Bx, By, nw, nm, Nx, Ny, K) > 227 * 1024 || dft_z_smem_bytes(ne_plane_max, E, Nz, Bz) > 227 * 1024)
+  std::vector<int> row_grp_off(1, 0), grp_idx, grp_ay;
+  auto pair_of = [&](int plane, int ay) {
+    for (int p = plane_pair_off[plane]; p < plane_pair_off[plane + 1]; ++p)
+      if (pair_ay[p] == ay) return p;
+    return P;
+  };
+  for (int k = 0; k < K; ++k) {
+    const int a = xS[k], b = xD[k] >= 0 && xD[k] != xS[k] ? xD[k] : -1;
+    std::vector<char> present(By, 0), done(By, 0);
+    for (int pl : {a, b})
+      if (pl >= 0)
+        for (int p = plane_pair_off[pl]; p < plane_pair_off[pl + 1]; ++p) present[pair_ay[p]] = 1;
+    for (int ay = 0; ay < By; ++ay) {
+      if (!present[ay] || done[ay]) continue;
+      const int rn = (Ny - resv[1][ay]) % Ny;
+      const int an = (int)(std::lower_bound(resv[1].begin(), resv[1].end(), rn) - resv[1].begin());
+      const bool partner = an < By && an != ay && resv[1][an] == rn && present[an];
+      done[ay] = 1;
+      if (partner) done[an] = 1;
+      grp_idx.push_back(pair_of(a, ay));
+      grp_idx.push_back(partner ? pair_of(a, an) : P);
+      grp_idx.push_back(b >= 0 ? pair_of(b, ay) : P);
+      grp_idx.push_back(b >= 0 && partner ? pair_of(b, an) : P);
+      grp_ay.push_back(ay);
+    }
+    row_grp_off.push_back((int)grp_ay.size());
+  }
+  const int G = (int)grp_ay.size();
+  if (dft_smem_bytes(P, Bx, By, nw, nm, Nx, Ny, K, G) > 227 * 1024 ||
+      dft_z_smem_bytes(ne_plane_max, E, Nz, Bz) > 227 * 1024)
     return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED,
                 "the grid-DFT tiles (%d (rx, ry) residue pairs, Nx = %d) exceed shared memory", P, Nx);
   std::vector<float> wf(nRp);
   for (int i = 0; i < nRp; ++i) wf[i] = (float)wp[i];
-  void *d_ppo, *d_peo, *d_pay, *d_az, *d_r, *d_w, *d_rx, *d_ry, *d_rz;
+  void *d_ppo, *d_peo, *d_az, *d_r, *d_w, *d_rx, *d_ry, *d_rz;
   TRY(upload(c, "dft_ppo", plane_pair_off.data(), sizeof(int) * (Bx + 1), &d_ppo));
   TRY(upload(c, "dft_peo", pair_ent_off.data(), sizeof(int) * (P + 1), &d_peo));
-  TRY(upload(c, "dft_pay", pair_ay.data(), sizeof(int) * P, &d_pay));
-  void* d_mate;
-  TRY(upload(c, "dft_mate", pair_mate.data(), sizeof(int) * P, &d_mate));
+  void *d_gro, *d_gidx, *d_gay;
+  TRY(upload(c, "dft_gro", row_grp_off.data(), sizeof(int) * (K + 1), &d_gro));
+  TRY(upload(c, "dft_gidx", grp_idx.data(), sizeof(int) * 4 * std::max(G, 1), &d_gidx));
+  TRY(upload(c, "dft_gay", grp_ay.data(), sizeof(int) * std::max(G, 1), &d_gay));
   TRY(upload(c, "dft_az", ent_az.data(), sizeof(int) * nRp, &d_az));
   TRY(upload(c, "dft_r", ent_r.data(), sizeof(int) * nRp, &d_r));
   TRY(upload(c, "dft_w", wf.data(), sizeof(float) * nRp, &d_w));
@@ -2089,9 +2100,10 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
     x.Nx = Nx;
     x.Ny = Ny;
     x.Nz = Nz;
-    x.plane_pair_off = (const int*)d_ppo;
-    x.pair_ay = (const int*)d_pay;
-    x.pair_mate = (const int*)d_mate;
+    x.G = G;
+    x.row_grp_off = (const int*)d_gro;
+    x.grp_idx = (const int4*)d_gidx;
+    x.grp_ay = (const int*)d_gay;
     x.K = K;
     x.K0 = K0;
     x.KP = KP;
