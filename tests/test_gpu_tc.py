@@ -137,12 +137,12 @@ def test_grid_dft_matches_tensor_core_stage2_on_full_grid(pg, si):
 
 def test_grid_dft_unpaired_and_half_grid_residues(pg):
     """R_p set without inversion symmetry and with R_x = +-Nx/2: the grid-DFT rows for a residue
-    without its negative, for a residue pair whose planes do not mirror each other, for r = 0 and
-    for r = Nx/2 (real phase factors), against the oracle."""
+    without its negative, for a residue pair whose planes hold different ry sets (y groups with
+    absent combinations), for r = 0 and for r = Nx/2 (real phase factors), against the oracle."""
     import dataclasses
     mat, prm = W.toy(seed=0)
     keep = mat.Rp[:, 0] != 1                      # residue 1 (mod 8) gone, 7 keeps no partner
-    # residue 4 = Nx / 2; residues 2 and 6 = -2 whose (rx, ry) planes do not mirror each other
+    # residue 4 = Nx / 2; residues 2 and 6 = -2 whose planes hold different ry residues
     extra = np.array([[4, 0, 0], [-4, 1, 0], [2, 1, 0], [-2, 0, 0]], dtype=np.int32)
     rng = np.random.default_rng(7)
     shape = (mat.g.shape[0], len(extra)) + mat.g.shape[2:]
