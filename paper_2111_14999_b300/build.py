@@ -9,7 +9,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libphoebe_gpu.so")
-SOURCES = ["api.cu", "pipeline.cu", "bands.cu", "couple_fp64.cu", "tc_gemm.cu", "noalloc.cu", "sampler.cu", "generic.cu", "batch.cu", "mlp_tc.cu", "transport.cu", "selftest.cu", "dft.cu", "threeph.cu"]
+SOURCES = ["api.cu", "pipeline.cu", "bands.cu", "couple_fp64.cu", "tc_gemm.cu", "noalloc.cu", "sampler.cu", "generic.cu", "batch.cu", "mlp_tc.cu", "transport.cu", "selftest.cu", "dft.cu", "dft_s1.cu", "threeph.cu"]
 HEADERS = ["common.cuh", "kernels.cuh", "pipeline.h", "tc.h", "tc_ptx.cuh", "sampler.h", "generic.h", "mlp_tc.h", "dft.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

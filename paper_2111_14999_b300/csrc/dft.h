@@ -116,6 +116,38 @@ struct PolarArgs {
   double alpha, cut, pref;    // pref = (4 pi / V) e^2 / (4 pi eps0)
 };
 
+// Stage 1 on grid k points as a separable DFT over the R_e box (dft_s1.cu): for the batch's k in
+// kx planes, X[row(k)][c] = sum_Re w_e e^{2 pi i k.R_e} g(R_e)[c] with the phase factorised per axis.
+// Entries = R_e sorted by (rz, ry) residue pair; pairs sorted by rz residue; z groups {rz, -rz}.
+constexpr int kS1Cols = 64;     // element columns per block
+struct S1Args {
+  const float2* g;            // [nRe][C] g(R_e)[c] in FP32
+  int64_t C;                  // element columns (nRp nw nw 3na)
+  float* X;                   // out: row r at X + r ldx, complex values interleaved
+  int64_t ldx;                // floats
+  int nRe, Pe, Bx, By, Bz, Gz, nkx, nky, nkz;
+  const int* ent_row;         // [nRe] R_e index of each entry
+  const int* ent_ax;          // [nRe] rx residue index of each entry
+  const float* ent_w;         // [nRe] w of each entry
+  const int* pair_ent_off;    // [Pe+1]
+  const int* pair_ay;         // [Pe] ry residue index of each pair
+  const int* rz_pair_off;     // [Bz+1] pairs of each rz residue index
+  const int2* zgrp;           // [Gz] (rz index of r, rz index of -r or -1)
+  const float2* Ex;           // [nkx][Bx] e^{2 pi i kx rx / nkx}
+  const float2* Ey;           // [nky][By]
+  const float2* Ezg;          // [nkz][Gz] e^{2 pi i kz r / nkz} of each group's r
+  const int* plane_kx;        // [planes] kx of each plane of the batch
+  const int* plane_line_off;  // [planes+1] lines (ky) of each plane
+  const int* line_ky;         // [lines]
+  const int* line_k_off;      // [lines+1] the batch's k on each line
+  const int2* kent;           // [k] (kz, X row)
+};
+size_t s1_smem_bytes(int nRe, int Pe, int Bz, int Gz, int nky, int By, int nkz);
+// Launches the stage-1 DFT for `planes` kx planes; -1 on a launch error, -2 if Gz > 16.
+int s1_launch(cudaStream_t st, const S1Args& a, int planes);
+// g(R_e)[c] (complex128, [nRe][C]) -> FP32 [nRe][C]
+int s1_convert_g(cudaStream_t st, const cplx* g, int64_t n, float2* out);
+
 // Launches both kernels for S states; -1 on a launch error, -2 for a (nw, 3na) without a kernel.
 int dft_launch(cudaStream_t st, const DftZArgs& z, const DftXArgs& x, int S, int nw, int nm, int ne_plane_max);
 #ifndef PHX_DFT_QPAIR

@@ -1,0 +1,137 @@
+// Stage 1 on grid k points as a separable DFT over the R_e box (Sec. 5.5 Eq. 71, its R_e sum
+// evaluated exactly in another order).  With k = (kx/Nx, ky/Ny, kz/Nz) on the k grid,
+//   X_k[c] = sum_Re w_e e^{2 pi i k.R_e} g(R_e)[c]
+//          = sum_rz Ez[kz][rz] sum_ry Ey[ky][ry] sum_rx Ex[kx][rx] w g(rx, ry, rz)[c],
+// r = R_e mod N per axis.  One block per (kx plane of the batch, chunk of element columns): the
+// rx sum into W1[(ry, rz) pair] (g streamed once per plane), then per ky line of the plane the
+// ry sum into the z groups {r, -r} (P = W2(r) + W2(-r), M = W2(r) - W2(-r), so one cos/sin pair
+// per group: Ez(r) W2(r) + Ez(-r) W2(-r) = c P + i s M), then the rz sum for every k of the batch
+// on that line, written as its X row in the layout the tensor-core GEMM writes (unscaled).
+// FP32 on the CUDA cores.
+#include "dft.h"
+
+namespace phx {
+
+template <int GZ>
+__global__ void __launch_bounds__(256) k_s1_dft(S1Args a) {
+  constexpr int CW = kS1Cols, TPC = 256 / CW;  // threads per column
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int Pe = a.Pe, nRe = a.nRe, G = a.Gz, By = a.By;
+  float2* W1 = reinterpret_cast<float2*>(smem);          // [Pe][CW]
+  float2* PM = W1 + (size_t)Pe * CW;                     // [2][G][CW]
+  float2* exw = PM + (size_t)2 * G * CW;                 // [nRe] w Ex[kx][rx] per entry
+  float2* Eyk = exw + nRe;                               // [nky][By]
+  float2* Ezg = Eyk + (size_t)a.nky * By;                // [nkz][G]
+  int2* zg = reinterpret_cast<int2*>(Ezg + (size_t)a.nkz * G);  // [G]
+  int* peo = reinterpret_cast<int*>(zg + G);             // [Pe+1]
+  int* erow = peo + Pe + 1;                              // [nRe]
+  int* pay = erow + nRe;                                 // [Pe]
+  int* rzo = pay + Pe;                                   // [Bz+1]
+  const int pl = blockIdx.y, kx = a.plane_kx[pl];
+  const int64_t c0 = (int64_t)blockIdx.x * CW;
+  const int col = threadIdx.x % CW, t4 = threadIdx.x / CW;
+  const bool live = c0 + col < a.C;
+  for (int i = threadIdx.x; i < nRe; i += blockDim.x) {
+    const float2 e = a.Ex[kx * a.Bx + a.ent_ax[i]];
+    const float w = a.ent_w[i];
+    exw[i] = make_float2(w * e.x, w * e.y);
+    erow[i] = a.ent_row[i];
+  }
+  for (int i = threadIdx.x; i < a.nky * By; i += blockDim.x) Eyk[i] = a.Ey[i];
+  for (int i = threadIdx.x; i < a.nkz * G; i += blockDim.x) Ezg[i] = a.Ezg[i];
+  for (int i = threadIdx.x; i < G; i += blockDim.x) zg[i] = a.zgrp[i];
+  for (int i = threadIdx.x; i <= Pe; i += blockDim.x) peo[i] = a.pair_ent_off[i];
+  for (int i = threadIdx.x; i < Pe; i += blockDim.x) pay[i] = a.pair_ay[i];
+  for (int i = threadIdx.x; i <= a.Bz; i += blockDim.x) rzo[i] = a.rz_pair_off[i];
+  __syncthreads();
+  // rx sum: W1[p][col] = sum over the entries of pair p of w Ex g
+  for (int p = t4; p < Pe; p += TPC) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 4
+    for (int e = peo[p]; e < peo[p + 1]; ++e) {
+      const float2 gv = live ? __ldg(a.g + (int64_t)erow[e] * a.C + c0 + col) : make_float2(0.f, 0.f);
+      const float2 x = exw[e];
+      acc.x = fmaf(x.x, gv.x, fmaf(-x.y, gv.y, acc.x));
+      acc.y = fmaf(x.x, gv.y, fmaf(x.y, gv.x, acc.y));
+    }
+    W1[p * CW + col] = acc;
+  }
+  __syncthreads();
+  for (int li = a.plane_line_off[pl]; li < a.plane_line_off[pl + 1]; ++li) {
+    const float2* ey = Eyk + (size_t)a.line_ky[li] * By;
+    // ry sum into the z groups: W2(r) = sum over the pairs with rz = r of Ey[ky][ry] W1[pair]
+    for (int g = t4; g < G; g += TPC) {
+      const int2 z = zg[g];
+      float2 w[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = h == 0 ? z.x : z.y;
+        if (r < 0) continue;
+        for (int p = rzo[r]; p < rzo[r + 1]; ++p) {
+          const float2 e = ey[pay[p]], v = W1[p * CW + col];
+          w[h].x = fmaf(e.x, v.x, fmaf(-e.y, v.y, w[h].x));
+          w[h].y = fmaf(e.x, v.y, fmaf(e.y, v.x, w[h].y));
+        }
+      }
+      PM[g * CW + col] = make_float2(w[0].x + w[1].x, w[0].y + w[1].y);
+      PM[(G + g) * CW + col] = make_float2(w[0].x - w[1].x, w[0].y - w[1].y);
+    }
+    __syncthreads();
+    // rz sum for the batch's k on this line: X = sum_groups c P + i s M
+    float2 P[GZ], M[GZ];
+#pragma unroll
+    for (int g = 0; g < GZ; ++g) {
+      P[g] = g < G ? PM[g * CW + col] : make_float2(0.f, 0.f);
+      M[g] = g < G ? PM[(G + g) * CW + col] : make_float2(0.f, 0.f);
+    }
+    for (int i = a.line_k_off[li] + t4; i < a.line_k_off[li + 1]; i += TPC) {
+      const int2 kr = a.kent[i];
+      const float2* ez = Ezg + (size_t)kr.x * G;
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int g = 0; g < GZ; ++g) {
+        if (g >= G) break;
+        const float2 e = ez[g];
+        acc.x = fmaf(e.x, P[g].x, fmaf(-e.y, M[g].y, acc.x));
+        acc.y = fmaf(e.x, P[g].y, fmaf(e.y, M[g].x, acc.y));
+      }
+      if (live) *reinterpret_cast<float2*>(a.X + (int64_t)kr.y * a.ldx + 2 * (c0 + col)) = acc;
+    }
+    __syncthreads();  // PM is rewritten for the next line
+  }
+}
+
+size_t s1_smem_bytes(int nRe, int Pe, int Bz, int Gz, int nky, int By, int nkz) {
+  return sizeof(float2) * ((size_t)Pe * kS1Cols + 2 * (size_t)Gz * kS1Cols + nRe + (size_t)nky * By + (size_t)nkz * Gz) +
+         sizeof(int2) * (size_t)Gz + sizeof(int) * ((size_t)Pe + 1 + nRe + Pe + (size_t)Bz + 1);
+}
+
+template <int GZ>
+static int s1_launch_t(cudaStream_t st, const S1Args& a, int planes) {
+  const size_t smem = s1_smem_bytes(a.nRe, a.Pe, a.Bz, a.Gz, a.nky, a.By, a.nkz);
+  if (cudaFuncSetAttribute(k_s1_dft<GZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return -1;
+  dim3 grid((unsigned)((a.C + kS1Cols - 1) / kS1Cols), (unsigned)planes);
+  k_s1_dft<GZ><<<grid, 256, smem, st>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int s1_launch(cudaStream_t st, const S1Args& a, int planes) {
+  if (planes <= 0) return 0;
+  if (a.Gz <= 4) return s1_launch_t<4>(st, a, planes);
+  if (a.Gz <= 8) return s1_launch_t<8>(st, a, planes);
+  if (a.Gz <= 16) return s1_launch_t<16>(st, a, planes);
+  return -2;
+}
+
+__global__ void k_s1_g32(const cplx* __restrict__ g, int64_t n, float2* __restrict__ out) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < n) out[t] = make_float2((float)g[t].re, (float)g[t].im);
+}
+
+int s1_convert_g(cudaStream_t st, const cplx* g, int64_t n, float2* out) {
+  k_s1_g32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, n, out);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace phx

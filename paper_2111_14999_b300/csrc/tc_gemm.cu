@@ -1788,6 +1788,178 @@ static int run_tc_mode(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const 
 
 // Stage 2 by the separable grid DFT (dft.cu): stage 1 in split FP16 on the tensor cores, then the
 // R_p sum for every q of the grid in FP32 on the CUDA cores, with the fused rotations and deltas.
+// Separable stage 1 of the grid-DFT mode (csrc/dft_s1.cu): residue tables of R_e on the k grid,
+// the FP32 copy of g, phase tables.  *ok = false (and PHOEBE_GPU_OK) when the R_e set does not fit
+// the kernel (more than 16 z groups or too much shared memory): the caller then takes the GEMM.
+static int s1_setup(phoebe_gpu_ctx* c, const GridMap& gm, S1Args* a, bool* ok) {
+  *ok = false;
+  const int nRe = c->nRe, nw = c->nw, nm = 3 * c->na;
+  const int64_t C = (int64_t)c->nRp * nw * nw * nm;
+  const int N3[3] = {gm.nk[0], gm.nk[1], gm.nk[2]};
+  std::vector<int> Re((size_t)3 * nRe);
+  std::vector<double> we(nRe);
+  CK(c, cudaMemcpyAsync(Re.data(), c->bufs["Re"].p, sizeof(int) * 3 * nRe, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemcpyAsync(we.data(), c->bufs["we"].p, sizeof(double) * nRe, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  std::vector<int> res[3], idx((size_t)3 * nRe);
+  for (int d = 0; d < 3; ++d) {
+    std::vector<int> r(nRe);
+    for (int i = 0; i < nRe; ++i) r[i] = ((Re[3 * i + d] % N3[d]) + N3[d]) % N3[d];
+    res[d] = r;
+    std::sort(res[d].begin(), res[d].end());
+    res[d].erase(std::unique(res[d].begin(), res[d].end()), res[d].end());
+    for (int i = 0; i < nRe; ++i)
+      idx[3 * i + d] = (int)(std::lower_bound(res[d].begin(), res[d].end(), r[i]) - res[d].begin());
+  }
+  const int Bx = (int)res[0].size(), By = (int)res[1].size(), Bz = (int)res[2].size();
+  // entries sorted by (rz, ry, rx) residue index; pairs = distinct (rz, ry)
+  std::vector<int> order(nRe);
+  for (int i = 0; i < nRe; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int p, int q) {
+    for (int d = 2; d >= 0; --d)
+      if (idx[3 * p + d] != idx[3 * q + d]) return idx[3 * p + d] < idx[3 * q + d];
+    return p < q;
+  });
+  std::vector<int> ent_row(nRe), ent_ax(nRe), peo, pay, rzo(Bz + 1, 0);
+  std::vector<float> ent_w(nRe);
+  for (int e = 0; e < nRe; ++e) {
+    const int r = order[e];
+    ent_row[e] = r;
+    ent_ax[e] = idx[3 * r];
+    ent_w[e] = (float)we[r];
+    if (e == 0 || idx[3 * r + 1] != idx[3 * order[e - 1] + 1] || idx[3 * r + 2] != idx[3 * order[e - 1] + 2]) {
+      peo.push_back(e);
+      pay.push_back(idx[3 * r + 1]);
+    }
+    rzo[idx[3 * r + 2] + 1] = (int)peo.size();
+  }
+  const int Pe = (int)pay.size();
+  peo.push_back(nRe);
+  for (int z = 1; z <= Bz; ++z) rzo[z] = std::max(rzo[z], rzo[z - 1]);
+  // z groups {r, -r mod Nz}
+  std::vector<int> zgrp, zres;
+  std::vector<char> done(Bz, 0);
+  for (int z = 0; z < Bz; ++z) {
+    if (done[z]) continue;
+    const int rn = (N3[2] - res[2][z]) % N3[2];
+    const int zn = (int)(std::lower_bound(res[2].begin(), res[2].end(), rn) - res[2].begin());
+    const bool partner = zn < Bz && zn != z && res[2][zn] == rn;
+    done[z] = 1;
+    if (partner) done[zn] = 1;
+    zgrp.push_back(z);
+    zgrp.push_back(partner ? zn : -1);
+    zres.push_back(res[2][z]);
+  }
+  const int Gz = (int)zres.size();
+  if (Gz > 16 || s1_smem_bytes(nRe, Pe, Bz, Gz, N3[1], By, N3[2]) > 200 * 1024) return PHOEBE_GPU_OK;
+  int st;
+  float2* g32 = (float2*)ensure(c, "s1_g32", sizeof(float2) * (size_t)nRe * C, &st);
+  if (!g32) return st;
+  if (s1_convert_g(c->stream, (const cplx*)c->bufs["g"].p, (int64_t)nRe * C, g32)) {
+    cudaGetLastError();
+    return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the stage-1 operand conversion failed");
+  }
+  void *d_row, *d_ax, *d_w, *d_peo, *d_pay, *d_rzo, *d_zg, *d_rx, *d_ry, *d_rz;
+  TRY(upload(c, "s1_row", ent_row.data(), sizeof(int) * nRe, &d_row));
+  TRY(upload(c, "s1_ax", ent_ax.data(), sizeof(int) * nRe, &d_ax));
+  TRY(upload(c, "s1_w", ent_w.data(), sizeof(float) * nRe, &d_w));
+  TRY(upload(c, "s1_peo", peo.data(), sizeof(int) * (Pe + 1), &d_peo));
+  TRY(upload(c, "s1_pay", pay.data(), sizeof(int) * Pe, &d_pay));
+  TRY(upload(c, "s1_rzo", rzo.data(), sizeof(int) * (Bz + 1), &d_rzo));
+  TRY(upload(c, "s1_zg", zgrp.data(), sizeof(int) * 2 * Gz, &d_zg));
+  TRY(upload(c, "s1_rx", res[0].data(), sizeof(int) * Bx, &d_rx));
+  TRY(upload(c, "s1_ry", res[1].data(), sizeof(int) * By, &d_ry));
+  TRY(upload(c, "s1_rz", zres.data(), sizeof(int) * Gz, &d_rz));
+  float2* Ex = (float2*)ensure(c, "s1_Ex", sizeof(float2) * N3[0] * Bx, &st);
+  float2* Ey = Ex ? (float2*)ensure(c, "s1_Ey", sizeof(float2) * N3[1] * By, &st) : nullptr;
+  float2* Ezg = Ey ? (float2*)ensure(c, "s1_Ezg", sizeof(float2) * N3[2] * Gz, &st) : nullptr;
+  if (!Ezg) return st;
+  if (dft_table(c->stream, (const int*)d_rx, Bx, N3[0], Ex) || dft_table(c->stream, (const int*)d_ry, By, N3[1], Ey) ||
+      dft_table(c->stream, (const int*)d_rz, Gz, N3[2], Ezg)) {
+    cudaGetLastError();
+    return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the stage-1 phase tables failed");
+  }
+  c->launches += 4;
+  a->g = g32;
+  a->C = C;
+  a->nRe = nRe;
+  a->Pe = Pe;
+  a->Bx = Bx;
+  a->By = By;
+  a->Bz = Bz;
+  a->Gz = Gz;
+  a->nkx = N3[0];
+  a->nky = N3[1];
+  a->nkz = N3[2];
+  a->ent_row = (const int*)d_row;
+  a->ent_ax = (const int*)d_ax;
+  a->ent_w = (const float*)d_w;
+  a->pair_ent_off = (const int*)d_peo;
+  a->pair_ay = (const int*)d_pay;
+  a->rz_pair_off = (const int*)d_rzo;
+  a->zgrp = (const int2*)d_zg;
+  a->Ex = Ex;
+  a->Ey = Ey;
+  a->Ezg = Ezg;
+  *ok = true;
+  return PHOEBE_GPU_OK;
+}
+
+// X rows of one batch by the separable stage 1: the batch's k (kb_list, ascending grid indices;
+// row = position in the list) grouped into kx planes and ky lines.
+static int s1_batch(phoebe_gpu_ctx* c, const GridMap& gm, S1Args a, const std::vector<int>& kb_list, float* X,
+                    int64_t ldx) {
+  std::vector<int> pkx, ploff, lky, lkoff, kent;
+  int last_kx = -1, last_ky = -1;
+  for (int i = 0; i < (int)kb_list.size(); ++i) {
+    int kc[3];
+    grid_coords(kb_list[i], gm.nk, kc);
+    if (kc[0] != last_kx) {
+      pkx.push_back(kc[0]);
+      ploff.push_back((int)lky.size());
+      last_kx = kc[0];
+      last_ky = -1;
+    }
+    if (kc[1] != last_ky) {
+      lky.push_back(kc[1]);
+      lkoff.push_back((int)kent.size() / 2);
+      last_ky = kc[1];
+    }
+    kent.push_back(kc[2]);
+    kent.push_back(i);
+  }
+  const int planes = (int)pkx.size(), lines = (int)lky.size();
+  ploff.push_back(lines);
+  lkoff.push_back((int)kent.size() / 2);
+  // one upload: kent (int2, first: 8-byte aligned), plane kx, plane line offsets, line ky, line k offsets
+  std::vector<int> buf(kent);
+  const size_t o1 = buf.size();
+  buf.insert(buf.end(), pkx.begin(), pkx.end());
+  const size_t o2 = buf.size();
+  buf.insert(buf.end(), ploff.begin(), ploff.end());
+  const size_t o3 = buf.size();
+  buf.insert(buf.end(), lky.begin(), lky.end());
+  const size_t o4 = buf.size();
+  buf.insert(buf.end(), lkoff.begin(), lkoff.end());
+  void* d;
+  TRY(upload(c, "s1_batch", buf.data(), sizeof(int) * buf.size(), &d));
+  const int* di = (const int*)d;
+  a.X = X;
+  a.ldx = ldx;
+  a.kent = (const int2*)di;
+  a.plane_kx = di + o1;
+  a.plane_line_off = di + o2;
+  a.line_ky = di + o3;
+  a.line_k_off = di + o4;
+  const int r = s1_launch(c->stream, a, planes);
+  if (r) {
+    cudaGetLastError();
+    return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the separable stage 1 failed");
+  }
+  c->launches++;
+  return PHOEBE_GPU_OK;
+}
+
 static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& gm, int64_t ns,
                    const std::vector<int>& hk, const int* st_k, const int* st_b, const double* epsF, const cplx* UF,
                    const double* fF, const double* omega, const double* nB, const cplx* Zq, double* raw) {
@@ -1813,8 +1985,15 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
   if (!nq_eval) return st;
   CK(c, cudaMemsetAsync(nq_eval, 0, 64, c->stream));
   const float sA1 = host_pow2_scale(c->we_max);
-  TRY((ensure_g_operand<FMT, NSPLIT>(c, C, Kp1, esz)));
-  Parts Pg{{c->tc->g_part[0], c->tc->g_part[1], c->tc->g_part[2]}};
+  // stage 1 as a separable DFT over the R_e box when its tables fit, else the tensor-core GEMM
+  S1Args s1a;
+  bool s1_ok = false;
+#ifndef PHX_S1_GEMM
+  TRY(s1_setup(c, gm, &s1a, &s1_ok));
+#endif
+  if (!s1_ok) TRY((ensure_g_operand<FMT, NSPLIT>(c, C, Kp1, esz)));
+  Parts Pg{{nullptr, nullptr, nullptr}};  // the GEMM's operand parts (c->tc exists once they are built)
+  if (!s1_ok) Pg = Parts{{c->tc->g_part[0], c->tc->g_part[1], c->tc->g_part[2]}};
   tm.begin(c);
   float2* UH = (float2*)ensure(c, "tc_UH", sizeof(float2) * NF * nw * nw, &st);
   if (!UH) return st;
@@ -2065,15 +2244,23 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
     tm.begin(c);
     const float* X1;
     int64_t ldx1;
-    TRY((stage1_batch<FMT, NSPLIT, NPROD>(c, gm, kb_list, st_kb, i0, st_k, st_b, UF, Pg, sA1, cis_k, gk, err, tmaxp,
-                                          (const int*)d_kb, (const int*)d_stkb, nullptr, &X1, &ldx1)));
+    if (s1_ok) {
+      ldx1 = (2 * C + 3) / 4 * 4;
+      float* X = (float*)ensure(c, "tc_X", sizeof(float) * (size_t)nkb * ldx1, &st);
+      if (!X) return st;
+      TRY(s1_batch(c, gm, s1a, kb_list, X, ldx1));
+      X1 = X;
+    } else {
+      TRY((stage1_batch<FMT, NSPLIT, NPROD>(c, gm, kb_list, st_kb, i0, st_k, st_b, UF, Pg, sA1, cis_k, gk, err, tmaxp,
+                                            (const int*)d_kb, (const int*)d_stkb, nullptr, &X1, &ldx1)));
+    }
     tm.end(c, &c->stats.stage1_ms);
     float2* Zs = (float2*)ensure(c, "dft_Zs", (size_t)per_state * S, &st);
     if (!Zs) return st;
     DftZArgs zz;
     zz.X = X1;
     zz.ldx = ldx1;
-    zz.unscale = 1.0f / (sA1 * c->tc->g_scale);
+    zz.unscale = s1_ok ? 1.0f : 1.0f / (sA1 * c->tc->g_scale);
     zz.st_kb = (const int*)d_stkb;
     zz.st_k = st_k + i0;
     zz.st_b = st_b + i0;
