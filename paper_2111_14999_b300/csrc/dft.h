@@ -140,7 +140,8 @@ struct S1Args {
   const int* plane_line_off;  // [planes+1] lines (ky) of each plane
   const int* line_ky;         // [lines]
   const int* line_k_off;      // [lines+1] the batch's k on each line
-  const int2* kent;           // [k] (kz, X row)
+  const int4* kent;           // [entries] (kz, X row, X row of (kx, ky, -kz) or -1, 0); a k whose -kz
+                              // partner is in the batch appears only in its partner's entry
 };
 size_t s1_smem_bytes(int nRe, int Pe, int Bz, int Gz, int nky, int By, int nkz);
 // Launches the stage-1 DFT for `planes` kx planes; -1 on a launch error, -2 if Gz > 16.

@@ -4,9 +4,10 @@
 //          = sum_rz Ez[kz][rz] sum_ry Ey[ky][ry] sum_rx Ex[kx][rx] w g(rx, ry, rz)[c],
 // r = R_e mod N per axis.  One block per (kx plane of the batch, chunk of element columns): the
 // rx sum into W1[(ry, rz) pair] (g streamed once per plane), then per ky line of the plane the
-// ry sum into the z groups {r, -r} (P = W2(r) + W2(-r), M = W2(r) - W2(-r), so one cos/sin pair
-// per group: Ez(r) W2(r) + Ez(-r) W2(-r) = c P + i s M), then the rz sum for every k of the batch
-// on that line, written as its X row in the layout the tensor-core GEMM writes (unscaled).
+// ry sum into W2(rz), then the rz sum for every k of the batch on that line by the z groups {r, -r}:
+// with P = W2(r) + W2(-r), M = W2(r) - W2(-r) and Ez = c + i s, Ez(r) W2(r) + Ez(-r) W2(-r) =
+// c P + i s M; the k (kz) and (-kz) of one line share A = sum c P and B = sum i s M, X = A +- B.
+// X rows are written in the layout the tensor-core GEMM writes (unscaled).
 // FP32 on the CUDA cores.
 #include "dft.h"
 
@@ -18,8 +19,8 @@ __global__ void __launch_bounds__(256) k_s1_dft(S1Args a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int Pe = a.Pe, nRe = a.nRe, G = a.Gz, By = a.By;
   float2* W1 = reinterpret_cast<float2*>(smem);          // [Pe][CW]
-  float2* PM = W1 + (size_t)Pe * CW;                     // [2][G][CW]
-  float2* exw = PM + (size_t)2 * G * CW;                 // [nRe] w Ex[kx][rx] per entry
+  float2* W2 = W1 + (size_t)Pe * CW;                     // [Bz][CW]
+  float2* exw = W2 + (size_t)a.Bz * CW;                  // [nRe] w Ex[kx][rx] per entry
   float2* Eyk = exw + nRe;                               // [nky][By]
   float2* Ezg = Eyk + (size_t)a.nky * By;                // [nkz][G]
   int2* zg = reinterpret_cast<int2*>(Ezg + (size_t)a.nkz * G);  // [G]
@@ -59,50 +60,54 @@ __global__ void __launch_bounds__(256) k_s1_dft(S1Args a) {
   __syncthreads();
   for (int li = a.plane_line_off[pl]; li < a.plane_line_off[pl + 1]; ++li) {
     const float2* ey = Eyk + (size_t)a.line_ky[li] * By;
-    // ry sum into the z groups: W2(r) = sum over the pairs with rz = r of Ey[ky][ry] W1[pair]
-    for (int g = t4; g < G; g += TPC) {
-      const int2 z = zg[g];
-      float2 w[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int r = h == 0 ? z.x : z.y;
-        if (r < 0) continue;
-        for (int p = rzo[r]; p < rzo[r + 1]; ++p) {
-          const float2 e = ey[pay[p]], v = W1[p * CW + col];
-          w[h].x = fmaf(e.x, v.x, fmaf(-e.y, v.y, w[h].x));
-          w[h].y = fmaf(e.x, v.y, fmaf(e.y, v.x, w[h].y));
-        }
+    // ry sum: W2(r) = sum over the pairs with rz = r of Ey[ky][ry] W1[pair], one rz per item
+    for (int r = t4; r < a.Bz; r += TPC) {
+      float2 w = make_float2(0.f, 0.f);
+      for (int p = rzo[r]; p < rzo[r + 1]; ++p) {
+        const float2 e = ey[pay[p]], v = W1[p * CW + col];
+        w.x = fmaf(e.x, v.x, fmaf(-e.y, v.y, w.x));
+        w.y = fmaf(e.x, v.y, fmaf(e.y, v.x, w.y));
       }
-      PM[g * CW + col] = make_float2(w[0].x + w[1].x, w[0].y + w[1].y);
-      PM[(G + g) * CW + col] = make_float2(w[0].x - w[1].x, w[0].y - w[1].y);
+      W2[r * CW + col] = w;
     }
     __syncthreads();
-    // rz sum for the batch's k on this line: X = sum_groups c P + i s M
+    // rz sum for the batch's k on this line
     float2 P[GZ], M[GZ];
 #pragma unroll
     for (int g = 0; g < GZ; ++g) {
-      P[g] = g < G ? PM[g * CW + col] : make_float2(0.f, 0.f);
-      M[g] = g < G ? PM[(G + g) * CW + col] : make_float2(0.f, 0.f);
+      P[g] = M[g] = make_float2(0.f, 0.f);
+      if (g < G) {
+        const int2 z = zg[g];
+        const float2 u = W2[z.x * CW + col], v = z.y >= 0 ? W2[z.y * CW + col] : make_float2(0.f, 0.f);
+        P[g] = make_float2(u.x + v.x, u.y + v.y);
+        M[g] = make_float2(u.x - v.x, u.y - v.y);
+      }
     }
     for (int i = a.line_k_off[li] + t4; i < a.line_k_off[li + 1]; i += TPC) {
-      const int2 kr = a.kent[i];
+      const int4 kr = a.kent[i];  // (kz, X row of kz, X row of -kz or -1)
       const float2* ez = Ezg + (size_t)kr.x * G;
-      float2 acc = make_float2(0.f, 0.f);
+      float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
 #pragma unroll
       for (int g = 0; g < GZ; ++g) {
         if (g >= G) break;
         const float2 e = ez[g];
-        acc.x = fmaf(e.x, P[g].x, fmaf(-e.y, M[g].y, acc.x));
-        acc.y = fmaf(e.x, P[g].y, fmaf(e.y, M[g].x, acc.y));
+        A.x = fmaf(e.x, P[g].x, A.x);
+        A.y = fmaf(e.x, P[g].y, A.y);
+        B.x = fmaf(-e.y, M[g].y, B.x);
+        B.y = fmaf(e.y, M[g].x, B.y);
       }
-      if (live) *reinterpret_cast<float2*>(a.X + (int64_t)kr.y * a.ldx + 2 * (c0 + col)) = acc;
+      if (live) {
+        *reinterpret_cast<float2*>(a.X + (int64_t)kr.y * a.ldx + 2 * (c0 + col)) = make_float2(A.x + B.x, A.y + B.y);
+        if (kr.z >= 0)
+          *reinterpret_cast<float2*>(a.X + (int64_t)kr.z * a.ldx + 2 * (c0 + col)) = make_float2(A.x - B.x, A.y - B.y);
+      }
     }
-    __syncthreads();  // PM is rewritten for the next line
+    __syncthreads();  // W2 is rewritten for the next line
   }
 }
 
 size_t s1_smem_bytes(int nRe, int Pe, int Bz, int Gz, int nky, int By, int nkz) {
-  return sizeof(float2) * ((size_t)Pe * kS1Cols + 2 * (size_t)Gz * kS1Cols + nRe + (size_t)nky * By + (size_t)nkz * Gz) +
+  return sizeof(float2) * ((size_t)Pe * kS1Cols + (size_t)Bz * kS1Cols + nRe + (size_t)nky * By + (size_t)nkz * Gz) +
          sizeof(int2) * (size_t)Gz + sizeof(int) * ((size_t)Pe + 1 + nRe + Pe + (size_t)Bz + 1);
 }
 

@@ -1910,28 +1910,43 @@ static int s1_setup(phoebe_gpu_ctx* c, const GridMap& gm, S1Args* a, bool* ok) {
 static int s1_batch(phoebe_gpu_ctx* c, const GridMap& gm, S1Args a, const std::vector<int>& kb_list, float* X,
                     int64_t ldx) {
   std::vector<int> pkx, ploff, lky, lkoff, kent;
+  std::vector<std::pair<int, int>> line;  // (kz, row) of the current line
+  const int nkz = gm.nk[2];
+  auto flush = [&]() {  // entries of a line: k with its (-kz) partner when both are in the batch
+    std::vector<int> row_of(nkz, -1);
+    for (auto& e : line) row_of[e.first] = e.second;
+    for (auto& e : line) {
+      const int kz = e.first, kn = (nkz - kz) % nkz;
+      if (kn != kz && row_of[kn] >= 0 && kn < kz) continue;  // taken with its partner
+      kent.push_back(kz);
+      kent.push_back(e.second);
+      kent.push_back(kn != kz ? row_of[kn] : -1);
+      kent.push_back(0);
+    }
+    line.clear();
+  };
   int last_kx = -1, last_ky = -1;
   for (int i = 0; i < (int)kb_list.size(); ++i) {
     int kc[3];
     grid_coords(kb_list[i], gm.nk, kc);
-    if (kc[0] != last_kx) {
-      pkx.push_back(kc[0]);
-      ploff.push_back((int)lky.size());
-      last_kx = kc[0];
-      last_ky = -1;
-    }
-    if (kc[1] != last_ky) {
+    if (kc[0] != last_kx || kc[1] != last_ky) {
+      flush();
+      if (kc[0] != last_kx) {
+        pkx.push_back(kc[0]);
+        ploff.push_back((int)lky.size());
+        last_kx = kc[0];
+      }
       lky.push_back(kc[1]);
-      lkoff.push_back((int)kent.size() / 2);
+      lkoff.push_back((int)kent.size() / 4);
       last_ky = kc[1];
     }
-    kent.push_back(kc[2]);
-    kent.push_back(i);
+    line.push_back({kc[2], i});
   }
+  flush();
   const int planes = (int)pkx.size(), lines = (int)lky.size();
   ploff.push_back(lines);
-  lkoff.push_back((int)kent.size() / 2);
-  // one upload: kent (int2, first: 8-byte aligned), plane kx, plane line offsets, line ky, line k offsets
+  lkoff.push_back((int)kent.size() / 4);
+  // one upload: kent (int4, first: 16-byte aligned), plane kx, plane line offsets, line ky, line k offsets
   std::vector<int> buf(kent);
   const size_t o1 = buf.size();
   buf.insert(buf.end(), pkx.begin(), pkx.end());
@@ -1946,7 +1961,7 @@ static int s1_batch(phoebe_gpu_ctx* c, const GridMap& gm, S1Args a, const std::v
   const int* di = (const int*)d;
   a.X = X;
   a.ldx = ldx;
-  a.kent = (const int2*)di;
+  a.kent = (const int4*)di;
   a.plane_kx = di + o1;
   a.plane_line_off = di + o2;
   a.line_ky = di + o3;
