@@ -1085,6 +1085,26 @@ static int64_t next_batch(const std::vector<int>& hk, int64_t ns, int64_t i0, in
   return i1;
 }
 
+// Like next_batch, but the batch ends on a kx-plane boundary of the k grid when it holds more than
+// one plane (the separable stage 1 then reads each plane's R_e terms once per step).
+static int64_t next_batch_planes(const std::vector<int>& hk, int64_t ns, int64_t i0, int max_states, const int nk[3],
+                                 std::vector<int>* kb_list, std::vector<int>* st_kb) {
+  int64_t i1 = next_batch(hk, ns, i0, max_states, kb_list, st_kb);
+  if (i1 >= ns) return i1;
+  const int plane_len = nk[1] * nk[2];
+  const int last_plane = hk[i1 - 1] / plane_len;
+  if (hk[i1] / plane_len != last_plane || hk[i0] / plane_len == last_plane) return i1;  // already on a boundary
+  int64_t cut = i1;
+  while (cut > i0 && hk[cut - 1] / plane_len == last_plane) --cut;
+  kb_list->clear();
+  st_kb->clear();
+  for (int64_t i = i0; i < cut; ++i) {
+    if (kb_list->empty() || kb_list->back() != hk[i]) kb_list->push_back(hk[i]);
+    st_kb->push_back((int)kb_list->size() - 1);
+  }
+  return cut;
+}
+
 // Stage 1 of one batch of whole k points on the tensor cores (Sec. 5.5 Eq. 71):
 // X[kb] = sum_Re w e^{ik.Re} g(Re, .) by a GEMM, then T[s][Rp][sa][m] = sum_n X[kb(s)] U_k[n][b(s)]
 // (FP32, physical scale) with the batch's max |T| in *tmaxp.  With Tb_out == nullptr the rotation
@@ -2250,7 +2270,8 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
   std::vector<int> kb_list, st_kb;
   int64_t i0 = 0;
   while (i0 < ns) {
-    const int64_t i1 = next_batch(hk, ns, i0, max_states, &kb_list, &st_kb);
+    const int64_t i1 = s1_ok ? next_batch_planes(hk, ns, i0, max_states, gm.nk, &kb_list, &st_kb)
+                             : next_batch(hk, ns, i0, max_states, &kb_list, &st_kb);
     const int S = (int)(i1 - i0);
     const int nkb = (int)kb_list.size();
     void *d_kb, *d_stkb;
