@@ -161,13 +161,19 @@ def roofline(precision: int, stats: list, k_limit: int) -> dict:
                 "avg_launch_ms": s2_ms / max(s2_launch, 1),
                 "issued_tensor_tflops": achieved * split_factor * kpad if achieved else None,
                 "issued_frac": achieved * split_factor * kpad / peak if achieved else None}
+    # DRAM bytes of one captured launch, scaled by algorithmic flop (the units processed) to this
+    # run's average launch
     traffic_path = os.path.join(ROOT, "profiles", "stage2_traffic.txt")
-    key = {5: "dram_bytes_per_launch_full=", 7: "dft_dram_bytes_per_launch_full="}.get(precision)
-    if key and os.path.exists(traffic_path) and k_limit == 0:
+    prefix = {5: "tc_capture_", 7: "dft_capture_"}.get(precision)
+    if prefix and os.path.exists(traffic_path) and k_limit == 0 and s2_launch:
+        vals = {}
         with open(traffic_path) as f:
             for ln in f:
-                if ln.startswith(key):
-                    roof["traffic"] = float(ln.split("=", 1)[1])
+                if ln.startswith(prefix) and "=" in ln:
+                    k, v = ln.strip().split("=", 1)
+                    vals[k[len(prefix):]] = float(v)
+        if "bytes" in vals and vals.get("flops"):
+            roof["traffic"] = vals["bytes"] * (s2_flops / s2_launch) / vals["flops"]
     return roof
 
 
@@ -612,7 +618,9 @@ def main():
         "vs_baseline": None, "dtype": PREC_DTYPE[args.precision], "data": "synthetic",
         "config": {"workload": WORKLOAD, "states_per_step": n, "q_points": 64000,
                    "precision": PREC_NAMES[args.precision],
-                   "l2": "inputs larger than L2 (stage-1 operand from g: 1.2 GB, q-phase operand 0.23 GB)",
+                   "l2": ("inputs larger than L2 (g in FP32: 0.57 GB read per kx plane; X rows and Zs of a "
+                          "batch: several GB)") if args.precision == 7 else
+                         "inputs larger than L2 (stage-1 operand from g: 1.2 GB, q-phase operand 0.23 GB)",
                    "parallelism": f"{world} independent instance(s), one per GPU"},
         "couplings_per_s": couplings,
         "gpu_launches": launches,
