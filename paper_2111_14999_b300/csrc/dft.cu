@@ -54,8 +54,12 @@ __global__ void __launch_bounds__(256) k_dft_z(DftZArgs a) {
   for (int i = threadIdx.x; i < a.Nz * a.Bz; i += blockDim.x) Ezs[i] = a.Ez[i];
   for (int i = threadIdx.x; i < ne; i += blockDim.x) azs[i] = a.ent_az[e0 + i];
   __syncthreads();
+  // jz and Nz - jz share the sums: with Ez[jz][rz] = c + i s, Z(jz) = A + B and Z(-jz) = A - B for
+  // A = sum c T, B = sum i s T; units run over jz = 0 .. Nz/2 (0 and Nz/2 are their own partners,
+  // s = 0 there)
   constexpr int JZ = 4;
-  const int nzq = (a.Nz + JZ - 1) / JZ;
+  const int NJ = a.Nz / 2 + 1;
+  const int nzq = (NJ + JZ - 1) / JZ;
   float2* Zs = a.Zs + (int64_t)s * a.Nz * a.P * E;
   if (E % 2 == 0) {
     const int EV = E / 2;
@@ -63,28 +67,38 @@ __global__ void __launch_bounds__(256) k_dft_z(DftZArgs a) {
     for (int u = threadIdx.x; u < units; u += blockDim.x) {
       const int cv = u % EV, rest = u / EV;
       const int jq = rest % nzq, p = p0 + rest / nzq;
-      float4 acc[JZ];
+      float4 A[JZ], B[JZ];
 #pragma unroll
-      for (int i = 0; i < JZ; ++i) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int i = 0; i < JZ; ++i) A[i] = B[i] = make_float4(0.f, 0.f, 0.f, 0.f);
       for (int e = a.pair_ent_off[p] - e0; e < a.pair_ent_off[p + 1] - e0; ++e) {
         const float4 t = reinterpret_cast<const float4*>(Ts + (size_t)e * E)[cv];
         const int az = azs[e];
 #pragma unroll
         for (int i = 0; i < JZ; ++i) {
           const int jz = jq * JZ + i;
-          if (jz < a.Nz) {
+          if (jz < NJ) {
             const float2 ez = Ezs[jz * a.Bz + az];
-            acc[i].x = fmaf(ez.x, t.x, fmaf(-ez.y, t.y, acc[i].x));
-            acc[i].y = fmaf(ez.x, t.y, fmaf(ez.y, t.x, acc[i].y));
-            acc[i].z = fmaf(ez.x, t.z, fmaf(-ez.y, t.w, acc[i].z));
-            acc[i].w = fmaf(ez.x, t.w, fmaf(ez.y, t.z, acc[i].w));
+            A[i].x = fmaf(ez.x, t.x, A[i].x);
+            A[i].y = fmaf(ez.x, t.y, A[i].y);
+            A[i].z = fmaf(ez.x, t.z, A[i].z);
+            A[i].w = fmaf(ez.x, t.w, A[i].w);
+            B[i].x = fmaf(-ez.y, t.y, B[i].x);
+            B[i].y = fmaf(ez.y, t.x, B[i].y);
+            B[i].z = fmaf(-ez.y, t.w, B[i].z);
+            B[i].w = fmaf(ez.y, t.z, B[i].w);
           }
         }
       }
 #pragma unroll
       for (int i = 0; i < JZ; ++i) {
         const int jz = jq * JZ + i;
-        if (jz < a.Nz) reinterpret_cast<float4*>(Zs + ((int64_t)jz * a.P + p) * E)[cv] = acc[i];
+        if (jz < NJ) {
+          reinterpret_cast<float4*>(Zs + ((int64_t)jz * a.P + p) * E)[cv] =
+              make_float4(A[i].x + B[i].x, A[i].y + B[i].y, A[i].z + B[i].z, A[i].w + B[i].w);
+          if (jz != 0 && 2 * jz != a.Nz)
+            reinterpret_cast<float4*>(Zs + ((int64_t)(a.Nz - jz) * a.P + p) * E)[cv] =
+                make_float4(A[i].x - B[i].x, A[i].y - B[i].y, A[i].z - B[i].z, A[i].w - B[i].w);
+        }
       }
     }
   } else {
@@ -92,26 +106,32 @@ __global__ void __launch_bounds__(256) k_dft_z(DftZArgs a) {
     for (int u = threadIdx.x; u < units; u += blockDim.x) {
       const int cv = u % E, rest = u / E;
       const int jq = rest % nzq, p = p0 + rest / nzq;
-      float2 acc[JZ];
+      float2 A[JZ], B[JZ];
 #pragma unroll
-      for (int i = 0; i < JZ; ++i) acc[i] = make_float2(0.f, 0.f);
+      for (int i = 0; i < JZ; ++i) A[i] = B[i] = make_float2(0.f, 0.f);
       for (int e = a.pair_ent_off[p] - e0; e < a.pair_ent_off[p + 1] - e0; ++e) {
         const float2 t = Ts[(size_t)e * E + cv];
         const int az = azs[e];
 #pragma unroll
         for (int i = 0; i < JZ; ++i) {
           const int jz = jq * JZ + i;
-          if (jz < a.Nz) {
+          if (jz < NJ) {
             const float2 ez = Ezs[jz * a.Bz + az];
-            acc[i].x = fmaf(ez.x, t.x, fmaf(-ez.y, t.y, acc[i].x));
-            acc[i].y = fmaf(ez.x, t.y, fmaf(ez.y, t.x, acc[i].y));
+            A[i].x = fmaf(ez.x, t.x, A[i].x);
+            A[i].y = fmaf(ez.x, t.y, A[i].y);
+            B[i].x = fmaf(-ez.y, t.y, B[i].x);
+            B[i].y = fmaf(ez.y, t.x, B[i].y);
           }
         }
       }
 #pragma unroll
       for (int i = 0; i < JZ; ++i) {
         const int jz = jq * JZ + i;
-        if (jz < a.Nz) Zs[((int64_t)jz * a.P + p) * E + cv] = acc[i];
+        if (jz < NJ) {
+          Zs[((int64_t)jz * a.P + p) * E + cv] = make_float2(A[i].x + B[i].x, A[i].y + B[i].y);
+          if (jz != 0 && 2 * jz != a.Nz)
+            Zs[((int64_t)(a.Nz - jz) * a.P + p) * E + cv] = make_float2(A[i].x - B[i].x, A[i].y - B[i].y);
+        }
       }
     }
   }
