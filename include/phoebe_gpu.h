@@ -63,11 +63,13 @@ typedef enum {
   PHOEBE_PREC_SPLIT_FP16 = 5,  /* two FP16 parts (hi + lo) of power-of-two scaled operands, three
                                   products: 22 significant bits at the cost of three BF16 passes */
   PHOEBE_PREC_BF16X3 = 6,      /* two BF16 parts, three products (reported, ~1e-5) */
-  PHOEBE_PREC_FP32_DFT = 7     /* linewidths only: stage 1 as SPLIT_FP16; stage 2 evaluated for every
-                                  q of the grid as a separable DFT over the R_p residues mod the
-                                  q-grid sizes (e^{iq.R} factorises per axis on a grid), FP32 on
-                                  the CUDA cores, rotations and deltas fused; needs q-grid sizes
-                                  Nx, Nz <= 64 and (nw, 3na) in {(8,6), (2,3), (1,3)} */
+  PHOEBE_PREC_FP32_DFT = 7     /* linewidths only: both phase sums on the grids as separable DFTs
+                                  over the R residues mod the grid sizes (e^{ik.R} factorises per
+                                  axis on a grid): stage 1 over the k grid (the SPLIT_FP16 GEMM when
+                                  the R_e residue tables do not fit), stage 2 for the q whose final
+                                  bands can reach the delta window, FP32 on the CUDA cores,
+                                  rotations and deltas fused; needs q-grid sizes Nx <= 256,
+                                  Nz <= 64, nw in {1, 2, 4, 8} and 3na in {3, 6} */
 } phoebe_gpu_precision;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
