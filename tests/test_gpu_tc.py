@@ -86,13 +86,15 @@ def si():
     return mat, prm, tab
 
 
-def test_si_like_full_grid_split_fp16_sampled(pg, si):
+@pytest.mark.parametrize("prec", [5, 7])
+def test_si_like_full_grid_sampled(pg, si, prec):
     """The benchmark configuration: every active state of the 40^3 x 40^3 Si-like grid in split
-    FP16, compared on a seeded sample of k points with the FP64 oracle."""
+    FP16 (precision 5) or as grid DFTs (precision 7, the benchmarked mode, default batches),
+    compared on a seeded sample of k points with the FP64 oracle."""
     mat, prm, tab = si
     with pg.PhoebeGPU(0) as ctx:
         ctx.set_material(mat)
-        ks, bs, gam = ctx.linewidths_rta(prm, precision=5)
+        ks, bs, gam = ctx.linewidths_rta(prm, precision=prec)
         st = ctx.stats()
     eg = tab[1][tab[3]]
     k_all, b_all = elph.active_states(eg, prm.mu_eV, prm.window_eV)
@@ -103,7 +105,7 @@ def test_si_like_full_grid_split_fp16_sampled(pg, si):
     k2, b2, ref = elph.linewidths_rta(mat, prm, k_indices=pick, table=tab)
     sel = np.isin(ks, pick)
     err = rel_err(gam[sel], ref)
-    print(f"Si-like full grid split-FP16: {len(gam)} states, sampled max rel err {err:.3e}, stats {st}")
+    print(f"Si-like full grid precision {prec}: {len(gam)} states, sampled max rel err {err:.3e}, stats {st}")
     assert err <= SPLIT_RTOL
 
 
