@@ -48,7 +48,7 @@ typedef enum {
   PHOEBE_GPU_ERR_CUDA = -6,           /* a CUDA runtime call failed (text in last_error) */
   PHOEBE_GPU_ERR_TIMEOUT = -7,        /* a bounded device-side wait ran out */
   PHOEBE_GPU_ERR_NOTCONVERGED = -8,   /* a Jacobi eigensolve hit its sweep cap */
-  PHOEBE_GPU_ERR_UNSUPPORTED = -9     /* valid request this build does not implement */
+  PHOEBE_GPU_ERR_UNSUPPORTED = -9     /* valid request the library does not implement */
 } phoebe_gpu_status;
 
 typedef enum {
@@ -130,7 +130,7 @@ int phoebe_gpu_set_elph_wannier(phoebe_gpu_ctx* ctx, int n_Re, const int32_t* Re
 
 /* Couplings at explicit (k, q) pairs (need not lie on a grid).
  *   k, q     n_pairs x 3 crystal coordinates
- *   precision  PHOEBE_PREC_FP64 only in this build (others return ERR_UNSUPPORTED)
+ *   precision  PHOEBE_PREC_FP64 only (others return ERR_UNSUPPORTED)
  *   g2       n_pairs x nw(m') x nw(n) x 3na |g_{m' n nu}(k,q)|^2 in eV^2 (or NULL)
  *   eps_k, eps_kq  n_pairs x nw band energies at k and k+q, ascending (or NULL)
  *   omega_q  n_pairs x 3na phonon energies hbar w in eV, ascending (or NULL)
