@@ -685,12 +685,12 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
           const float g2 = g.x * g.x + g.y * g.y;
           float wgt = 0.f;
           if (t1 * t1 < a.cut2) {
-            const float e1 = expf(-t1 * t1);
+            const float e1 = __expf(-t1 * t1);
             wgt += (on.y + 1.f - f) * e1;
             if constexpr (PR)  // this state's share of P_{q nu}: |g|^2 e^{-t1^2} f(1-f)/kT (emission delta)
               atomicAdd(a.pacc + (int64_t)q * NM + v, (double)(g2 * e1) * pw);
           }
-          if (t2 * t2 < a.cut2) wgt += (on.y + f) * expf(-t2 * t2);
+          if (t2 * t2 < a.cut2) wgt += (on.y + f) * __expf(-t2 * t2);
           acc = fmaf(g2, wgt * norm, acc);
         }
       }
