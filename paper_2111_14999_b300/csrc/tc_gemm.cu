@@ -279,11 +279,9 @@ __device__ constexpr int kProdA[6] = {0, 0, 1, 0, 2, 1};
 __device__ constexpr int kProdB[6] = {0, 1, 0, 2, 0, 1};
 
 // FMT: 0 = FP16, 1 = BF16 (tcgen05 kind::f16), 2 = TF32 (kind::tf32).  NSPLIT parts per
-// operand, NPROD leading products of the parts (1, 3 or 6).  CN > 1: the CN CTAs of a
-// cluster work on the same 128-row A tile and CN consecutive n tiles; each CTA loads
-// 128/CN rows of every A K-block and multicasts them to the whole cluster, so L2 delivers
-// each A tile once per cluster instead of once per CTA.
-template <class Epi, int FMT, int NSPLIT, int NPROD, int CN>
+// operand, NPROD leading products of the parts (1, 3 or 6).  Every CTA loads its own A and
+// B tiles; CTAs that share an A tile find it in L2.
+template <class Epi, int FMT, int NSPLIT, int NPROD>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
               const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB0,
@@ -311,14 +309,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nchunk = (a.kblocks + a.kb_per_chunk - 1) / a.kb_per_chunk;
   if (a.tile_list) a.ntiles = (int)*a.ntiles_dev;  // same value in every thread
-  const int rank = CN > 1 ? (int)cluster_ctarank() : 0;
-  const int cid = blockIdx.x / CN, nclu = gridDim.x / CN;  // cluster id / count
-  constexpr uint16_t kMask = (uint16_t)((1u << CN) - 1u);
-  constexpr int kArows = 128 / CN;                          // A rows this CTA loads per K block
+  const int cid = blockIdx.x, nclu = gridDim.x;  // persistent: tiles cid, cid + nclu, ...
   if (threadIdx.x == 0) {
     for (int i = 0; i < a.stages; ++i) {
       mbar_init(full + i, 1);
-      mbar_init(empty + i, CN);  // released by the MMA of every CTA that reads the slot
+      mbar_init(empty + i, 1);  // released by the MMA commit of the slot's last K block
     }
     for (int i = 0; i < NPART; ++i) {
       mbar_init(pfull + i, 1);
@@ -345,10 +340,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tmem_relinquish();
   }
   tc_fence_before();
-  if (CN > 1)
-    cluster_sync();  // peers multicast into this CTA's smem and arrive on its barriers
-  else
-    __syncthreads();
+  __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
@@ -363,7 +355,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int t = cid; t < a.ntiles && ok; t += nclu) {
         int m, n;
         tile_coords(a, t, m, n);
-        n = n * CN + rank;
         for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
           const int s = (int)(it % (uint32_t)a.stages);
           const uint32_t ph = (it / (uint32_t)a.stages) & 1u;
@@ -375,17 +366,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           mbar_arrive_expect_tx(full + s, STAGE);
           const int kx = kb * (KIND == 0 ? 64 : 32);
           uint8_t* bbase = base + NSPLIT * kTileABytes;
-          uint8_t* aslice = base + rank * kArows * 128;
-          const int ay = m * 128 + rank * kArows;
-          if (CN > 1) {
-            tma_load_2d_mc(aslice, &tmA0, full + s, kx, ay, kMask);
-            if (NSPLIT > 1) tma_load_2d_mc(aslice + kTileABytes, &tmA1, full + s, kx, ay, kMask);
-            if (NSPLIT > 2) tma_load_2d_mc(aslice + 2 * kTileABytes, &tmA2, full + s, kx, ay, kMask);
-          } else {
-            tma_load_2d(aslice, &tmA0, full + s, kx, ay);
-            if (NSPLIT > 1) tma_load_2d(aslice + kTileABytes, &tmA1, full + s, kx, ay);
-            if (NSPLIT > 2) tma_load_2d(aslice + 2 * kTileABytes, &tmA2, full + s, kx, ay);
-          }
+          const int ay = m * 128;
+          tma_load_2d(base, &tmA0, full + s, kx, ay);
+          if (NSPLIT > 1) tma_load_2d(base + kTileABytes, &tmA1, full + s, kx, ay);
+          if (NSPLIT > 2) tma_load_2d(base + 2 * kTileABytes, &tmA2, full + s, kx, ay);
           tma_load_2d(bbase, &tmB0, full + s, kx, n * a.b_row_step);
           if (NSPLIT > 1) tma_load_2d(bbase + B_BYTES, &tmB1, full + s, kx, n * a.b_row_step);
           if (NSPLIT > 2) tma_load_2d(bbase + 2 * B_BYTES, &tmB2, full + s, kx, n * a.b_row_step);
@@ -450,10 +434,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
               }
             }
-            if (CN > 1)
-              mma_commit_mc(empty + s, kMask);
-            else
-              mma_commit(empty + s);
+            mma_commit(empty + s);
           }
           if (!ok) break;
           mma_commit(pf);
@@ -490,7 +471,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int t = cid; t < a.ntiles && ok; t += nclu, ++zcount) {
       int m, n;
       tile_coords(a, t, m, n);
-      n = n * CN + rank;
       typename Epi::Pre pre;
       Epi::prefetch(ep, m, n, wg, row, pre);
       float acc[BNW];
@@ -573,7 +553,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tmem_dealloc(tmem_base, 512);
   }
   if (threadIdx.x == 0 && *abort_flag) atomicOr(a.err, 1);
-  if (CN > 1) cluster_sync();  // no CTA leaves while a peer may still write into its smem
 }
 
 // ------------------------------------------------------------------ operand packing
@@ -949,40 +928,24 @@ static int pick_stages(int BN, int nsplit, int extra) {
   return std::max(1, std::min(st, 8));
 }
 
-constexpr int kClusterN = 1;  // CTAs sharing each A tile through TMA multicast (1: off)
-
-// a.n_tiles on entry: n tiles of the problem; padded to whole clusters here.
+// Persistent launch: one CTA per SM (or fewer when there are fewer tiles).
 template <class Epi, int FMT, int NSPLIT, int NPROD>
 static int launch_gemm(phoebe_gpu_ctx* c, const CUtensorMap* A, const CUtensorMap* B, TcGemmArgs a,
                        const typename Epi::Params& ep) {
-  constexpr int CN = kClusterN;
-  auto kern = k_tc_gemm<Epi, FMT, NSPLIT, NPROD, CN>;
+  auto kern = k_tc_gemm<Epi, FMT, NSPLIT, NPROD>;
   a.stages = pick_stages(Epi::BN, NSPLIT, (int)((Epi::SMEM_BYTES + 1023u) & ~1023u));
   a.kb_per_chunk = std::max(1, std::min(a.kb_per_chunk, a.stages));  // a chunk must fit in the smem ring
-  a.n_tiles = (a.n_tiles + CN - 1) / CN;                              // cluster-level n groups
   a.group_m = std::min(a.group_m, a.m_tiles);
   a.ntiles = a.m_tiles * a.n_tiles;
   int sm = a.stages * stage_bytes(Epi::BN, NSPLIT) + (int)((Epi::SMEM_BYTES + 1023u) & ~1023u) + 1024 + 512;
   CK(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CN;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(kTcThreads, 1, 1);
-  cfg.dynamicSmemBytes = sm;
-  cfg.stream = c->stream;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cfg.gridDim = dim3((unsigned)((c->num_sms > 0 ? c->num_sms : 148) / CN * CN), 1, 1);
-  int max_clusters = 0;
-  CK(c, cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg));
-  if (max_clusters <= 0) return fail(c, PHOEBE_GPU_ERR_CUDA, "no %d-CTA cluster of this kernel fits on the GPU", CN);
-  int clusters = std::min(max_clusters, a.ntiles);
-  if (clusters <= 0) return PHOEBE_GPU_OK;
-  cfg.gridDim = dim3((unsigned)(clusters * CN), 1, 1);
-  CK(c, cudaLaunchKernelEx(&cfg, kern, A[0], A[1], A[2], B[0], B[1], B[2], a, ep));
+  int per_sm = 0;
+  CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTcThreads, sm));
+  if (per_sm <= 0) return fail(c, PHOEBE_GPU_ERR_CUDA, "the tensor-core GEMM (%d B smem) does not fit on an SM", sm);
+  const int sms = c->num_sms > 0 ? c->num_sms : 148;
+  const int grid = std::min(sms, a.ntiles);
+  if (grid <= 0) return PHOEBE_GPU_OK;
+  kern<<<grid, kTcThreads, sm, c->stream>>>(A[0], A[1], A[2], B[0], B[1], B[2], a, ep);
   c->launches++;
   CK(c, cudaGetLastError());
   return PHOEBE_GPU_OK;
@@ -1136,7 +1099,7 @@ static int stage1_batch(phoebe_gpu_ctx* c, const GridMap& gm, const std::vector<
     CK(c, cudaGetLastError());
   }
   CUtensorMap tAk[3], tG[3];
-  TRY(part_maps(c, tAk, PAk, NSPLIT, FMT, Kp1, nkb, 128 / kClusterN));
+  TRY(part_maps(c, tAk, PAk, NSPLIT, FMT, Kp1, nkb, 128));
   TRY(part_maps(c, tG, Pg, NSPLIT, FMT, Kp1, 2 * C, BN1));
   {
     TcGemmArgs a;
@@ -1357,7 +1320,7 @@ static int run_tc_generic(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, con
       Parts PAc;
       for (int i = 0; i < 3; ++i)
         PAc.p[i] = PAq.p[i] ? static_cast<uint8_t*>(PAq.p[i]) + (size_t)q0 * Kp2 * esz : nullptr;
-      TRY(part_maps(c, tA, PAc, NSPLIT, FMT, Kp2, rows, 128 / kClusterN));
+      TRY(part_maps(c, tA, PAc, NSPLIT, FMT, Kp2, rows, 128));
       TRY(part_maps(c, tB, PB, NSPLIT, FMT, Kp2, ncols, (uint32_t)bn));
       a->m_tiles = (int)(rows / 128);
       a->n_tiles = (int)((ncols + bn - 1) / bn);
@@ -1615,7 +1578,7 @@ static int run_tc_typed(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const
   const double reach = omega_max + p->delta_cut_sigmas * p->sigma_eV;
   tm.end(c, &c->stats.stage1_ms);
   CUtensorMap tAq[3];
-  TRY(part_maps(c, tAq, PAq, NSPLIT, FMT, Kp2, Mrows, 128 / kClusterN));
+  TRY(part_maps(c, tAq, PAq, NSPLIT, FMT, Kp2, Mrows, 128));
 
   // stage-2 tiling: whole states per n tile
   using EE = ElphEpi<NW, NM>;
@@ -1665,7 +1628,7 @@ static int run_tc_typed(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const
       CK(c, cudaGetLastError());
     }
     CUtensorMap tAk[3], tG[3];
-    TRY(part_maps(c, tAk, PAk, NSPLIT, FMT, Kp1, nkb, 128 / kClusterN));
+    TRY(part_maps(c, tAk, PAk, NSPLIT, FMT, Kp1, nkb, 128));
     TRY(part_maps(c, tG, Pg, NSPLIT, FMT, Kp1, 2 * C, BN1));
     {
       TcGemmArgs a;
