@@ -69,7 +69,12 @@ typedef enum {
                                   the R_e residue tables do not fit), stage 2 for the q whose final
                                   bands can reach the delta window, FP32 on the CUDA cores,
                                   rotations and deltas fused; needs q-grid sizes Nx <= 256,
-                                  Nz <= 64, nw in {1, 2, 4, 8} and 3na in {3, 6} */
+                                  Nz <= 64, nw in {1, 2, 4, 8} and 3na in {3, 6} */,
+  PHOEBE_PREC_FP64_DFT = 8     /* linewidths only: the separable grid DFTs of PHOEBE_PREC_FP32_DFT in
+                                  FP64 throughout (phase tables, both stages, rotations, Gaussians),
+                                  the plain FP64 counterpart of the same algorithm; fixed smearing,
+                                  full q sum, no polar term or phonon-electron rates; needs the
+                                  stage-1 residue tables in shared memory, nw <= 16, 3na <= 30 */
 } phoebe_gpu_precision;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
@@ -392,9 +397,11 @@ int phoebe_gpu_linewidths_rta_batch(phoebe_gpu_batch_item* items, int n, phoebe_
  * programs sharing the GPU with a framework that has already reserved nearly all of
  * it for its own pool (cudaMalloc would fail), and latency-sensitive callers that
  * cannot accept the device-wide synchronisation cudaMalloc/cudaFree may imply.
- * It computes H^W_k = sum_R w_R e^{ik.R} H(R) and eps_k, U_k of Eq. 11 like the
- * grid path, needs no context, and allocates nothing: its only scratch is a static
- * 16 MiB device array that every GPU loading the library holds until exit.
+ * It forms the Wannier sum H_k = sum_R w_R e^{ik.R} H(R) at each point and solves the
+ * Hermitian eigenproblem of H_k (energies ascending, eigenvectors as columns) with the
+ * same kernels as the grid path; it needs no context and allocates nothing: its only
+ * scratch is a static 16 MiB device array that every GPU loading the library holds
+ * until exit.
  *   nw, n_R      as for set_hamiltonian (nw <= 32)
  *   R, w, H      DEVICE arrays: n_R x 3 int32, n_R weights (not NULL), n_R x nw x nw
  *                complex (interleaved doubles), caller-owned
@@ -407,9 +414,11 @@ int phoebe_gpu_linewidths_rta_batch(phoebe_gpu_batch_item* items, int n, phoebe_
  * bytes exceed the 16 MiB scratch, PHOEBE_GPU_ERR_ARG for bad sizes or NULL
  * pointers, PHOEBE_GPU_ERR_NOTCONVERGED if an eigensolve hit its sweep cap.
  * The first call on each device looks up the scratch address on the current device
- * (one-time set-up); make that first call before any stream capture begins.  All
- * calls on a device share the one scratch array: calls that overlap on the GPU
- * (other streams, other host threads) race on it. */
+ * (one-time set-up); make that first call before any stream capture begins.  Every
+ * call reads its convergence word back and synchronises the stream, so a call on a
+ * stream that is being captured returns PHOEBE_GPU_ERR_ARG before enqueuing anything
+ * (the capture is left intact).  All calls on a device share the one scratch array:
+ * calls that overlap on the GPU (other streams, other host threads) race on it. */
 int phoebe_gpu_bands_noalloc(int nw, int n_R, const int32_t* R, const double* w, const double* H, int n_k,
                              const double* k, double* eps, double* U, void* cuda_stream);
 

@@ -37,6 +37,15 @@ extern "C" int phoebe_gpu_bands_noalloc(int nw, int n_R, const int32_t* R, const
     return PHOEBE_GPU_ERR_CUDA;
   }
   if (dev < 0 || dev >= kMaxDevices) return PHOEBE_GPU_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // every call ends with a read-back and a stream synchronisation, which a stream capture
+  // does not allow: refuse before anything is enqueued, so the caller's capture stays valid
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return PHOEBE_GPU_ERR_CUDA;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return PHOEBE_GPU_ERR_ARG;
   void* base = nullptr;
   {
     // one-time set-up per device, with that device current: device address of the scratch array
@@ -52,7 +61,6 @@ extern "C" int phoebe_gpu_bands_noalloc(int nw, int n_R, const int32_t* R, const
     }
     base = g_noalloc_addr[dev];
   }
-  cudaStream_t s = (cudaStream_t)cuda_stream;
   cplx* A = reinterpret_cast<cplx*>(base);
   cplx* V = A + per;
   int* status = reinterpret_cast<int*>(static_cast<unsigned char*>(base) + kNoallocScratchBytes);
