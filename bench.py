@@ -31,9 +31,9 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 PREC_NAMES = {0: "fp64", 1: "split_bf16", 2: "split_tf32", 3: "bf16", 4: "tf32", 5: "split_fp16", 6: "bf16x3",
-              7: "fp32_grid_dft"}
+              7: "fp32_grid_dft", 8: "fp64_grid_dft"}
 PREC_DTYPE = {0: "f64", 1: "bf16x6+f32acc", 2: "tf32x3+f32acc", 3: "bf16+f32acc", 4: "tf32+f32acc",
-              7: "f32",
+              7: "f32", 8: "f64",
               5: "f16x3+f32acc", 6: "bf16x3+f32acc"}
 METRIC = "Gamma_nk linewidths/s (el-ph RTA, Si-like 40^3 k x 40^3 q)"
 WORKLOAD = "si_like_fcc_nw8_na2_R429_k40x40x40_q40x40x40_T300_sigma0.02_window0.5"
@@ -131,7 +131,7 @@ def roofline(precision: int, stats: list, k_limit: int) -> dict:
     s2_launch = sum(s["stage2_launches"] for s in stats)
     s2_flops = sum(s["stage2_flops"] for s in stats)
     achieved = s2_flops / (s2_ms / 1e3) / 1e12 if s2_ms > 0 else None
-    split_factor = {0: 1, 1: 6, 2: 3, 3: 1, 4: 1, 5: 3, 6: 3, 7: 1}[precision]
+    split_factor = {0: 1, 1: 6, 2: 3, 3: 1, 4: 1, 5: 3, 6: 3, 7: 1, 8: 1}[precision]
     kpad = (-(-2 * 429 // 64) * 64) / (2 * 429)
     if precision == 7:
         # CUDA-core FP32: 148 SMs x 128 FP32 lanes x 2 flop per FMA x the maximum SM clock
@@ -145,10 +145,14 @@ def roofline(precision: int, stats: list, k_limit: int) -> dict:
                 "avg_launch_ms": s2_ms / max(s2_launch, 1),
                 "note": "flops count the DFT's complex MACs as evaluated (8 flop each; x sum only for the q "
                         "whose final bands reach the delta window); the rotation/delta epilogue is not counted"}
-    elif precision == 0:
+    elif precision in (0, 8):
         roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
                 "frac": achieved / 1.25 if achieved else None, "traffic": None,
-                "peak_source": "nominal FP64 1.25 TFLOP/s"}
+                "peak_source": "nominal FP64 1.25 TFLOP/s",
+                "kernel": "k_zgemm (dense R_p sum)" if precision == 0 else
+                          "k_dft_z64 + k_dft_yx64 (FP64 separable grid DFT)",
+                "algorithmic_flops_per_launch": s2_flops / max(s2_launch, 1),
+                "avg_launch_ms": s2_ms / max(s2_launch, 1)}
     else:
         peak = peaks.get("bf16_tflops_sustained", 1400.0)
         if precision in (2, 4):
@@ -431,8 +435,9 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--precision", type=int, default=7,
-                    help="0 fp64, 1 split bf16, 2 split tf32, 5 split fp16 (tensor cores), 7 fp32 grid DFT")
-    ap.add_argument("--no-tc-leg", action="store_true", help="skip the tensor-core stage-2 leg beside the headline")
+                    help="0 fp64, 1 split bf16, 2 split tf32, 5 split fp16 (tensor cores), 7 fp32 grid DFT, 8 fp64 grid DFT")
+    ap.add_argument("--no-tc-leg", action="store_true", help="skip the tensor-core stage-2 legs beside the headline")
+    ap.add_argument("--no-fp64-dft", action="store_true", help="skip the FP64 grid-DFT leg")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-k-per-step", type=int, default=2)
     ap.add_argument("--cpu-k", type=int, default=4, help="k points of the CPU-oracle baseline sample")
@@ -517,33 +522,45 @@ def main():
         ms = float(t.item())
     ms_per_step = ms / args.steps
     value = world * n * args.steps / (ms / 1e3)
-    couplings = world * stats[-1]["couplings_dense"] * args.steps / (ms / 1e3)
+    couplings = world * stats[-1]["couplings_executed"] * args.steps / (ms / 1e3)
+    couplings_dense = world * stats[-1]["couplings_dense"] * args.steps / (ms / 1e3)
     launches = int(sum(s["kernel_launches"] for s in stats))
 
     roof = roofline(args.precision, stats, args.k_limit or args.k_planes)
 
     extra = {}
-    if not args.main_only and not args.no_tc_leg and args.precision != 5:
-        # the tensor-core stage 2 (split FP16) on the same workload, beside the headline mode
-        p5 = pg.make_params(prm, precision=5)
-        g_head = g_out.cpu().numpy().copy()
-        ctx.linewidths_rta_dev(p5, k_out, b_out, g_out, n)
+    g_head = g_out.cpu().numpy().copy()
+    ks_head = k_out.cpu().numpy().copy()
+
+    def device_leg(prec, steps):
+        """The same full step in another precision: one untimed call, then `steps` timed calls."""
+        pp = pg.make_params(prm, precision=prec)
+        ctx.linewidths_rta_dev(pp, k_out, b_out, g_out, n)
         torch.cuda.synchronize()
-        s5 = []
+        sx = []
         t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0e.record(stream)
-        for _ in range(args.steps):
-            ctx.linewidths_rta_dev(p5, k_out, b_out, g_out, n)
-            s5.append(ctx.stats())
+        for _ in range(steps):
+            ctx.linewidths_rta_dev(pp, k_out, b_out, g_out, n)
+            sx.append(ctx.stats())
         t1e.record(stream)
         torch.cuda.synchronize()
-        ms5 = t0e.elapsed_time(t1e) / args.steps
-        g5 = g_out.cpu().numpy()
-        fl = 1e-6 * np.median(np.abs(g5))
-        extra["tensor_core_mode"] = {
-            "precision": "split_fp16", "value": n / (ms5 / 1e3), "unit": "linewidths/s", "ms_per_step": ms5,
-            "roofline": roofline(5, s5, args.k_limit or args.k_planes),
-            "max_rel_diff_vs_headline": float(np.max(np.abs(g5 - g_head) / np.maximum(np.abs(g5), fl)))}
+        msx = t0e.elapsed_time(t1e) / steps
+        return msx, sx, g_out.cpu().numpy().copy()
+
+    legs = {}
+    if not args.main_only and not args.no_tc_leg:
+        # the tensor-core stage 2 in each split precision on the same workload
+        for prec in (5, 1, 2):
+            if prec == args.precision:
+                continue
+            msx, sx, gx = device_leg(prec, min(args.steps, 3))
+            fl = 1e-6 * np.median(np.abs(gx))
+            legs[prec] = {
+                "precision": PREC_NAMES[prec], "value": n / (msx / 1e3), "unit": "linewidths/s", "ms_per_step": msx,
+                "roofline": roofline(prec, sx, args.k_limit or args.k_planes),
+                "max_rel_diff_vs_headline": float(np.max(np.abs(gx - g_head) / np.maximum(np.abs(gx), fl))),
+                "_g": gx}
         ctx.linewidths_rta_dev(params, k_out, b_out, g_out, n)     # headline outputs back for the checks below
         torch.cuda.synchronize()
     if args.main_only:
@@ -554,11 +571,10 @@ def main():
             print(json.dumps(line), flush=True)
         ctx.close()
         return
-    # FP64 GPU comparison on a sample + error of this precision against it
+    # FP64 on the GPU: the dense R_p sum (every q, k_zgemm) on a sample of k, and the FP64 separable grid
+    # DFT (the headline's algorithm in FP64) on the whole step; errors of every precision against FP64
     if rank == 0 and args.fp64_k > 0:
-        ks_all = k_out.cpu().numpy()
-        g_all = g_out.cpu().numpy()
-        uk = np.unique(ks_all)
+        uk = np.unique(ks_head)
         pick = np.sort(np.random.default_rng(5).choice(uk, min(args.fp64_k, len(uk)), replace=False))
         ctx.set_profiling(True)
         t0 = torch.cuda.Event(enable_timing=True)
@@ -569,15 +585,37 @@ def main():
         torch.cuda.synchronize()
         fp64_ms = t0.elapsed_time(t1)
         st64 = ctx.stats()
-        sel = np.isin(ks_all, pick)
+        sel = np.isin(ks_head, pick)
         floor = 1e-6 * np.median(np.abs(g64))
-        err = float(np.max(np.abs(g_all[sel] - g64) / np.maximum(np.abs(g64), floor)))
+
+        def err_vs_fp64(g_all):
+            return float(np.max(np.abs(g_all[sel] - g64) / np.maximum(np.abs(g64), floor)))
         fp64_rate = len(g64) / (fp64_ms / 1e3)
-        extra["fp64_gpu"] = {"value": fp64_rate, "unit": "linewidths/s",
+        extra["fp64_gpu"] = {"value": fp64_rate, "unit": "linewidths/s", "algorithm": "dense R_p sum over every q",
                              "sample": f"{len(g64)} states on {len(pick)} seeded k points",
                              "stage2_tflops": st64["stage2_flops"] / st64["stage2_ms"] / 1e9 if st64["stage2_ms"] else None}
         extra["speedup_vs_fp64_gpu"] = (value / world) / fp64_rate
-        extra["max_rel_err_vs_fp64"] = err
+        extra["max_rel_err_vs_fp64"] = err_vs_fp64(g_head)
+        if args.precision != 8 and not args.no_fp64_dft:
+            ms8, s8, g8 = device_leg(8, 1)
+            extra["fp64_grid_dft"] = {
+                "value": n / (ms8 / 1e3), "unit": "linewidths/s", "ms_per_step": ms8,
+                "algorithm": "the headline's separable grid DFT in FP64 (precision 8), whole step",
+                "roofline": roofline(8, s8, args.k_limit or args.k_planes),
+                "max_rel_err_vs_fp64_dense": err_vs_fp64(g8)}
+            fl8 = 1e-6 * np.median(np.abs(g8))
+            extra["speedup_vs_fp64_grid_dft"] = (value / world) / (n / (ms8 / 1e3))
+            extra["max_rel_err_vs_fp64_grid_dft"] = float(np.max(np.abs(g_head - g8) / np.maximum(np.abs(g8), fl8)))
+            ctx.linewidths_rta_dev(params, k_out, b_out, g_out, n)
+            torch.cuda.synchronize()
+        for prec, leg in legs.items():
+            leg["max_rel_err_vs_fp64"] = err_vs_fp64(leg["_g"])
+    for prec, leg in legs.items():
+        leg.pop("_g")
+    if 5 in legs:
+        extra["tensor_core_mode"] = legs.pop(5)
+    if legs:
+        extra["split_precision_legs"] = list(legs.values())
 
     # end to end through the public host-buffer API, inputs from pinned host memory every step
     def pinned(a):
@@ -623,6 +661,9 @@ def main():
                          "inputs larger than L2 (stage-1 operand from g: 1.2 GB, q-phase operand 0.23 GB)",
                    "parallelism": f"{world} independent instance(s), one per GPU"},
         "couplings_per_s": couplings,
+        "couplings_per_s_note": ("complex g_{m'n nu}(k,q) elements computed per second: (state, q) pairs whose "
+                                 "contraction ran (the q whose final bands reach the delta window) x N_w x 3N_at"),
+        "couplings_dense_equivalent_per_s": couplings_dense,
         "gpu_launches": launches,
         "roofline": roof,
         "clocks": clocks,

@@ -22,6 +22,7 @@ STATUS = {
 }
 PREC_FP64, PREC_SPLIT_BF16, PREC_SPLIT_TF32, PREC_BF16, PREC_TF32, PREC_SPLIT_FP16, PREC_BF16X3 = 0, 1, 2, 3, 4, 5, 6
 PREC_FP32_DFT = 7
+PREC_FP64_DFT = 8
 SAMPLER_FULL, SAMPLER_LEARNED, SAMPLER_UNIFORM = 0, 1, 2
 MLP_NPARAM = 34177
 

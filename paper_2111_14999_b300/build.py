@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(os.path.dirname(HERE), "_build")
 LIB = os.path.join(HERE, "libphoebe_gpu.so")
 SOURCES = ["api.cu", "pipeline.cu", "bands.cu", "couple_fp64.cu", "tc_gemm.cu", "noalloc.cu", "sampler.cu", "generic.cu",
-           "batch.cu", "mlp_tc.cu", "transport.cu", "selftest.cu", "dft.cu", "dft_s1.cu", "threeph.cu"]
+           "batch.cu", "mlp_tc.cu", "transport.cu", "selftest.cu", "dft.cu", "dft_s1.cu", "dft64.cu", "threeph.cu"]
 HEADERS = ["common.cuh", "kernels.cuh", "pipeline.h", "tc.h", "tc_ptx.cuh", "sampler.h", "generic.h", "mlp_tc.h", "dft.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]

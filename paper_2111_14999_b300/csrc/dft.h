@@ -149,6 +149,75 @@ int s1_launch(cudaStream_t st, const S1Args& a, int planes);
 // g(R_e)[c] (complex128, [nRe][C]) -> FP32 [nRe][C]
 int s1_convert_g(cudaStream_t st, const cplx* g, int64_t n, float2* out);
 
+// ---------------------------------------------------------------- FP64 grid DFT (dft64.cu)
+// The same separable evaluation of Eqs. 70-71 as the FP32 kernels, in FP64 throughout: the phase
+// tables from sincospi in FP64, g read in complex128, every sum and the Gaussians of Eq. 61 in FP64.
+// The index tables (entries, pairs, groups, x rows, batch lines) are the FP32 path's.
+constexpr int kS64Cols = 32;    // element columns per block of the FP64 stage 1
+constexpr int kDft64Lines = 4;  // jy lines per run of the FP64 y/x kernel
+struct S64Args {
+  S1Args i;                   // index tables and sizes (its float pointers are unused)
+  const double2* g;           // [nRe][C] complex128
+  double2* X;                 // out: row r at X + r C
+  const double* ent_w;        // [nRe] w of each entry
+  const double2* Ex;          // [nkx][Bx]
+  const double2* Ey;          // [nky][By]
+  const double2* Ezg;         // [nkz][Gz]
+};
+struct DftZ64Args {
+  const double2* X;           // stage-1 rows, row st_kb[s], column ((Rp nw + m) nw + n) 3na + sa
+  int64_t ldx;                // complex values per row
+  const int* st_kb;
+  const int* st_k;
+  const int* st_b;
+  GridMap gm;
+  const cplx* UF;
+  int nw;
+  const double* w;            // [nR] R_p weights
+  int nR, E, P, Nz, Bz;
+  const int* plane_pair_off;
+  const int* pair_ent_off;
+  const int* ent_az;
+  const int* ent_r;
+  const double2* Ez;          // [Nz][Bz]
+  double2* Zs;                // [S][Nz][P][E]
+};
+struct DftX64Args {
+  const double2* Zs;          // [S][Nz][P][E]
+  int P, Bx, By, Nx, Ny, Nz;
+  int G;
+  const int* row_grp_off;
+  const int4* grp_idx;
+  const int* grp_ay;
+  int K, K0, KP;
+  const int* xS;
+  const int* xD;
+  const double2* Ex;          // [Nx][K]
+  const double2* Ey;          // [Ny][By]
+  const int* st_k;
+  const int* st_b;
+  GridMap gm;
+  int nw, nm;
+  const double* epsF;         // [NF][nw]
+  const double* fF;           // [NF][nw]
+  const cplx* UF;             // [NF][nw][nw]
+  const cplx* Zq;             // [Nq][nm (sa)][nm (nu)] mode factors of Eq. 7 (0 for dead modes)
+  const double* omega;        // [Nq][nm]
+  const double* nB;           // [Nq][nm]
+  double reach;               // a final band m' can contribute only if |eps_nk - eps_m'k+q| < reach
+  double inv_sigma, xcut;     // 1 / sigma; the Gaussian is 0 for |x| >= xcut = cut sigma
+  double scale;               // (2 pi / N_q) / (sqrt(pi) sigma)
+  double* gamma;
+  int64_t s_base;
+  unsigned long long* nq_evaluated;
+};
+size_t s64_smem_bytes(int nRe, int Pe, int Bz, int Gz, int nky, int By, int nkz);
+size_t dft64_z_smem_bytes(int ne_plane_max, int E, int Nz, int Bz);
+size_t dft64_smem_bytes(int P, int Bx, int By, int E, int Nx, int Ny, int K, int G);
+int s64_launch(cudaStream_t st, const S64Args& a, int planes);  // -1 launch error, -2 Gz > 16
+int dft64_launch(cudaStream_t st, const DftZ64Args& z, const DftX64Args& x, int S, int ne_plane_max);
+int dft_table64(cudaStream_t st, const int* res, int B, int N, double2* E);
+
 // Launches both kernels for S states; -1 on a launch error, -2 for a (nw, 3na) without a kernel.
 int dft_launch(cudaStream_t st, const DftZArgs& z, const DftXArgs& x, int S, int nw, int nm, int ne_plane_max);
 #ifndef PHX_DFT_QPAIR

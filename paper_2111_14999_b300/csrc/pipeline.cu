@@ -136,7 +136,7 @@ static int check_params(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, GridM
   if (!(p->delta_cut_sigmas > 0.0)) return fail(c, PHOEBE_GPU_ERR_ARG, "delta_cut_sigmas must be > 0");
   if (!(p->omega_cut_eV >= 0.0)) return fail(c, PHOEBE_GPU_ERR_ARG, "omega_cut_eV must be >= 0");
   if (!(p->degen_tol_eV >= 0.0)) return fail(c, PHOEBE_GPU_ERR_ARG, "degen_tol_eV must be >= 0");
-  if (p->precision < PHOEBE_PREC_FP64 || p->precision > PHOEBE_PREC_FP32_DFT)
+  if (p->precision < PHOEBE_PREC_FP64 || p->precision > PHOEBE_PREC_FP64_DFT)
     return fail(c, PHOEBE_GPU_ERR_ARG, "unknown precision %d", p->precision);
   if (p->reserved1 != 0) return fail(c, PHOEBE_GPU_ERR_ARG, "reserved fields must be zero");
   if (c->have_polar) {

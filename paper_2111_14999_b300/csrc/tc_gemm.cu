@@ -1774,7 +1774,8 @@ static int run_tc_mode(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const 
 // Separable stage 1 of the grid-DFT mode (csrc/dft_s1.cu): residue tables of R_e on the k grid,
 // the FP32 copy of g, phase tables.  *ok = false (and PHOEBE_GPU_OK) when the R_e set does not fit
 // the kernel (more than 16 z groups or too much shared memory): the caller then takes the GEMM.
-static int s1_setup(phoebe_gpu_ctx* c, const GridMap& gm, S1Args* a, bool* ok) {
+// With a64 != nullptr the FP64 form: g read in complex128, FP64 weights and phase tables in *a64.
+static int s1_setup(phoebe_gpu_ctx* c, const GridMap& gm, S1Args* a, bool* ok, S64Args* a64 = nullptr) {
   *ok = false;
   const int nRe = c->nRe, nw = c->nw, nm = 3 * c->na;
   const int64_t C = (int64_t)c->nRp * nw * nw * nm;
@@ -1834,13 +1835,18 @@ static int s1_setup(phoebe_gpu_ctx* c, const GridMap& gm, S1Args* a, bool* ok) {
     zres.push_back(res[2][z]);
   }
   const int Gz = (int)zres.size();
-  if (Gz > 16 || s1_smem_bytes(nRe, Pe, Bz, Gz, N3[1], By, N3[2]) > 200 * 1024) return PHOEBE_GPU_OK;
+  const size_t s1_smem = a64 ? s64_smem_bytes(nRe, Pe, Bz, Gz, N3[1], By, N3[2])
+                             : s1_smem_bytes(nRe, Pe, Bz, Gz, N3[1], By, N3[2]);
+  if (Gz > 16 || s1_smem > 200 * 1024) return PHOEBE_GPU_OK;
   int st;
-  float2* g32 = (float2*)ensure(c, "s1_g32", sizeof(float2) * (size_t)nRe * C, &st);
-  if (!g32) return st;
-  if (s1_convert_g(c->stream, (const cplx*)c->bufs["g"].p, (int64_t)nRe * C, g32)) {
-    cudaGetLastError();
-    return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the stage-1 operand conversion failed");
+  float2* g32 = nullptr;
+  if (!a64) {
+    g32 = (float2*)ensure(c, "s1_g32", sizeof(float2) * (size_t)nRe * C, &st);
+    if (!g32) return st;
+    if (s1_convert_g(c->stream, (const cplx*)c->bufs["g"].p, (int64_t)nRe * C, g32)) {
+      cudaGetLastError();
+      return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the stage-1 operand conversion failed");
+    }
   }
   void *d_row, *d_ax, *d_w, *d_peo, *d_pay, *d_rzo, *d_zg, *d_rx, *d_ry, *d_rz;
   TRY(upload(c, "s1_row", ent_row.data(), sizeof(int) * nRe, &d_row));
@@ -1853,16 +1859,41 @@ static int s1_setup(phoebe_gpu_ctx* c, const GridMap& gm, S1Args* a, bool* ok) {
   TRY(upload(c, "s1_rx", res[0].data(), sizeof(int) * Bx, &d_rx));
   TRY(upload(c, "s1_ry", res[1].data(), sizeof(int) * By, &d_ry));
   TRY(upload(c, "s1_rz", zres.data(), sizeof(int) * Gz, &d_rz));
-  float2* Ex = (float2*)ensure(c, "s1_Ex", sizeof(float2) * N3[0] * Bx, &st);
-  float2* Ey = Ex ? (float2*)ensure(c, "s1_Ey", sizeof(float2) * N3[1] * By, &st) : nullptr;
-  float2* Ezg = Ey ? (float2*)ensure(c, "s1_Ezg", sizeof(float2) * N3[2] * Gz, &st) : nullptr;
-  if (!Ezg) return st;
-  if (dft_table(c->stream, (const int*)d_rx, Bx, N3[0], Ex) || dft_table(c->stream, (const int*)d_ry, By, N3[1], Ey) ||
-      dft_table(c->stream, (const int*)d_rz, Gz, N3[2], Ezg)) {
-    cudaGetLastError();
-    return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the stage-1 phase tables failed");
+  float2 *Ex = nullptr, *Ey = nullptr, *Ezg = nullptr;
+  if (a64) {
+    std::vector<double> wd(we.begin(), we.end());
+    for (int e = 0; e < nRe; ++e) wd[e] = we[ent_row[e]];
+    void* d_w64;
+    TRY(upload(c, "s1_w64", wd.data(), sizeof(double) * nRe, &d_w64));
+    double2* Ex64 = (double2*)ensure(c, "s1_Ex64", sizeof(double2) * N3[0] * Bx, &st);
+    double2* Ey64 = Ex64 ? (double2*)ensure(c, "s1_Ey64", sizeof(double2) * N3[1] * By, &st) : nullptr;
+    double2* Ez64 = Ey64 ? (double2*)ensure(c, "s1_Ezg64", sizeof(double2) * N3[2] * Gz, &st) : nullptr;
+    if (!Ez64) return st;
+    if (dft_table64(c->stream, (const int*)d_rx, Bx, N3[0], Ex64) ||
+        dft_table64(c->stream, (const int*)d_ry, By, N3[1], Ey64) ||
+        dft_table64(c->stream, (const int*)d_rz, Gz, N3[2], Ez64)) {
+      cudaGetLastError();
+      return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the FP64 stage-1 phase tables failed");
+    }
+    c->launches += 3;
+    a64->g = (const double2*)c->bufs["g"].p;
+    a64->ent_w = (const double*)d_w64;
+    a64->Ex = Ex64;
+    a64->Ey = Ey64;
+    a64->Ezg = Ez64;
+  } else {
+    Ex = (float2*)ensure(c, "s1_Ex", sizeof(float2) * N3[0] * Bx, &st);
+    Ey = Ex ? (float2*)ensure(c, "s1_Ey", sizeof(float2) * N3[1] * By, &st) : nullptr;
+    Ezg = Ey ? (float2*)ensure(c, "s1_Ezg", sizeof(float2) * N3[2] * Gz, &st) : nullptr;
+    if (!Ezg) return st;
+    if (dft_table(c->stream, (const int*)d_rx, Bx, N3[0], Ex) ||
+        dft_table(c->stream, (const int*)d_ry, By, N3[1], Ey) ||
+        dft_table(c->stream, (const int*)d_rz, Gz, N3[2], Ezg)) {
+      cudaGetLastError();
+      return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the stage-1 phase tables failed");
+    }
+    c->launches += 4;
   }
-  c->launches += 4;
   a->g = g32;
   a->C = C;
   a->nRe = nRe;
@@ -1884,14 +1915,16 @@ static int s1_setup(phoebe_gpu_ctx* c, const GridMap& gm, S1Args* a, bool* ok) {
   a->Ex = Ex;
   a->Ey = Ey;
   a->Ezg = Ezg;
+  if (a64) a64->i = *a;
   *ok = true;
   return PHOEBE_GPU_OK;
 }
 
 // X rows of one batch by the separable stage 1: the batch's k (kb_list, ascending grid indices;
-// row = position in the list) grouped into kx planes and ky lines.
+// row = position in the list) grouped into kx planes and ky lines.  With a64 != nullptr the FP64
+// form writes complex128 rows of C values to X64 (X and ldx unused).
 static int s1_batch(phoebe_gpu_ctx* c, const GridMap& gm, S1Args a, const std::vector<int>& kb_list, float* X,
-                    int64_t ldx) {
+                    int64_t ldx, const S64Args* a64 = nullptr, double2* X64 = nullptr) {
   std::vector<int> pkx, ploff, lky, lkoff, kent;
   std::vector<std::pair<int, int>> line;  // (kz, row) of the current line
   const int nkz = gm.nk[2];
@@ -1949,7 +1982,15 @@ static int s1_batch(phoebe_gpu_ctx* c, const GridMap& gm, S1Args a, const std::v
   a.plane_line_off = di + o2;
   a.line_ky = di + o3;
   a.line_k_off = di + o4;
-  const int r = s1_launch(c->stream, a, planes);
+  int r;
+  if (a64) {
+    S64Args b = *a64;
+    b.i = a;
+    b.X = X64;
+    r = s64_launch(c->stream, b, planes);
+  } else {
+    r = s1_launch(c->stream, a, planes);
+  }
   if (r) {
     cudaGetLastError();
     return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the separable stage 1 failed");
@@ -1958,13 +1999,18 @@ static int s1_batch(phoebe_gpu_ctx* c, const GridMap& gm, S1Args a, const std::v
   return PHOEBE_GPU_OK;
 }
 
+// fp64: the FP64 grid DFT (dft64.cu) with the same residue tables; every sum, table and Gaussian in
+// FP64, the band and phonon arrays read as they are.
 static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& gm, int64_t ns,
                    const std::vector<int>& hk, const int* st_k, const int* st_b, const double* epsF, const cplx* UF,
-                   const double* fF, const double* omega, const double* nB, const cplx* Zq, double* raw) {
+                   const double* fF, const double* omega, const double* nB, const cplx* Zq, double* raw,
+                   bool fp64 = false) {
   constexpr int FMT = 0, NSPLIT = 2, NPROD = 3;
   const int nw = c->nw, nm = 3 * c->na, nRe = c->nRe, nRp = c->nRp;
   const int E = nw * nm;
-  if (!((nw == 1 || nw == 2 || nw == 4 || nw == 8) && (nm == 3 || nm == 6)))
+  if (fp64 && (nw > 16 || nm > 30))
+    return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "the FP64 grid DFT is built for nw <= 16 and 3na <= 30");
+  if (!fp64 && !((nw == 1 || nw == 2 || nw == 4 || nw == 8) && (nm == 3 || nm == 6)))
     return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "the grid-DFT stage 2 is built for nw in {1, 2, 4, 8} and 3na in {3, 6}");
   const int Nx = gm.nq[0], Ny = gm.nq[1], Nz = gm.nq[2];
   if (Nz * 16 > 1024 || Nx > 256)
@@ -1985,40 +2031,50 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
   const float sA1 = host_pow2_scale(c->we_max);
   // stage 1 as a separable DFT over the R_e box when its tables fit, else the tensor-core GEMM
   S1Args s1a;
+  S64Args s64a;
   bool s1_ok = false;
 #ifndef PHX_S1_GEMM
-  TRY(s1_setup(c, gm, &s1a, &s1_ok));
+  TRY(s1_setup(c, gm, &s1a, &s1_ok, fp64 ? &s64a : nullptr));
 #endif
+  if (fp64 && !s1_ok)
+    return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "the FP64 grid DFT needs the R_e residue tables in shared memory");
   if (!s1_ok) TRY((ensure_g_operand<FMT, NSPLIT>(c, C, Kp1, esz)));
   Parts Pg{{nullptr, nullptr, nullptr}};  // the GEMM's operand parts (c->tc exists once they are built)
   if (!s1_ok) Pg = Parts{{c->tc->g_part[0], c->tc->g_part[1], c->tc->g_part[2]}};
   tm.begin(c);
-  float2* UH = (float2*)ensure(c, "tc_UH", sizeof(float2) * NF * nw * nw, &st);
-  if (!UH) return st;
-  float* f32 = (float*)ensure(c, "tc_f32", sizeof(float) * NF * nw, &st);
-  if (!f32) return st;
-  float2* eps2 = (float2*)ensure(c, "tc_eps2", sizeof(float2) * NF * nw, &st);
-  if (!eps2) return st;
   unsigned long long* dmax = (unsigned long long*)ensure(c, "tc_max", 64, &st);
   if (!dmax) return st;
-  float* epsf = (float*)ensure(c, "dft_epsf", sizeof(float) * NF * nw, &st);
-  if (!epsf) return st;
-  float4* el4 = (float4*)ensure(c, "dft_el4", sizeof(float4) * NF * nw, &st);
-  if (!el4) return st;
-  float2* ZT = (float2*)ensure(c, "dft_ZT", sizeof(float2) * Nq * nm * nm, &st);
-  if (!ZT) return st;
-  float2* omnb = (float2*)ensure(c, "dft_omnb", sizeof(float2) * Nq * nm, &st);
-  if (!omnb) return st;
-  k_tables_el<<<(unsigned)((NF * nw * nw + 255) / 256), 256, 0, c->stream>>>(UF, fF, epsF, NF, nw, UH, f32, eps2);
   CK(c, cudaMemsetAsync(dmax, 0, 64, c->stream));
   k_absmax_f64<<<64, 256, 0, c->stream>>>(omega, Nq * nm, dmax);
-  c->launches += 2;
-  CK(c, cudaGetLastError());
-  if (dft_tables(c->stream, epsF, fF, NF, nw, Zq, omega, nB, Nq, nm, epsf, el4, ZT, omnb)) {
-    cudaGetLastError();
-    return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the grid-DFT tables failed");
-  }
   c->launches += 1;
+  CK(c, cudaGetLastError());
+  float2 *UH = nullptr, *ZT = nullptr, *omnb = nullptr;
+  float* epsf = nullptr;
+  float4* el4 = nullptr;
+  if (!fp64) {  // FP32 tables of the FP32 kernels
+    UH = (float2*)ensure(c, "tc_UH", sizeof(float2) * NF * nw * nw, &st);
+    if (!UH) return st;
+    float* f32 = (float*)ensure(c, "tc_f32", sizeof(float) * NF * nw, &st);
+    if (!f32) return st;
+    float2* eps2 = (float2*)ensure(c, "tc_eps2", sizeof(float2) * NF * nw, &st);
+    if (!eps2) return st;
+    epsf = (float*)ensure(c, "dft_epsf", sizeof(float) * NF * nw, &st);
+    if (!epsf) return st;
+    el4 = (float4*)ensure(c, "dft_el4", sizeof(float4) * NF * nw, &st);
+    if (!el4) return st;
+    ZT = (float2*)ensure(c, "dft_ZT", sizeof(float2) * Nq * nm * nm, &st);
+    if (!ZT) return st;
+    omnb = (float2*)ensure(c, "dft_omnb", sizeof(float2) * Nq * nm, &st);
+    if (!omnb) return st;
+    k_tables_el<<<(unsigned)((NF * nw * nw + 255) / 256), 256, 0, c->stream>>>(UF, fF, epsF, NF, nw, UH, f32, eps2);
+    c->launches += 1;
+    CK(c, cudaGetLastError());
+    if (dft_tables(c->stream, epsF, fF, NF, nw, Zq, omega, nB, Nq, nm, epsf, el4, ZT, omnb)) {
+      cudaGetLastError();
+      return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the grid-DFT tables failed");
+    }
+    c->launches += 1;
+  }
   float4* vel = nullptr;  // adaptive smearing: band velocities on the fine grid
   if (p->smearing == 1) TRY(velocity_grid(c, gm.nf, UF, &vel));
   float2* gL = nullptr;  // polar long-range term: L_{q nu} on the q grid
@@ -2184,13 +2240,15 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
     row_grp_off.push_back((int)grp_ay.size());
   }
   const int G = (int)grp_ay.size();
-  if (dft_smem_bytes(P, Bx, By, nw, nm, Nx, Ny, K, G) > 227 * 1024 ||
-      dft_z_smem_bytes(ne_plane_max, E, Nz, Bz) > 227 * 1024)
+  const size_t smem_yx = fp64 ? dft64_smem_bytes(P, Bx, By, E, Nx, Ny, K, G) : dft_smem_bytes(P, Bx, By, nw, nm, Nx, Ny, K, G);
+  const size_t smem_z = fp64 ? dft64_z_smem_bytes(ne_plane_max, E, Nz, Bz) : dft_z_smem_bytes(ne_plane_max, E, Nz, Bz);
+  if (smem_yx > 227 * 1024 || smem_z > 227 * 1024)
     return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED,
                 "the grid-DFT tiles (%d (rx, ry) residue pairs, Nx = %d) exceed shared memory", P, Nx);
   std::vector<float> wf(nRp);
   for (int i = 0; i < nRp; ++i) wf[i] = (float)wp[i];
-  void *d_ppo, *d_peo, *d_az, *d_r, *d_w, *d_rx, *d_ry, *d_rz;
+  void *d_ppo, *d_peo, *d_az, *d_r, *d_w, *d_rx, *d_ry, *d_rz, *d_w64 = nullptr;
+  if (fp64) TRY(upload(c, "dft_w64", wp.data(), sizeof(double) * nRp, &d_w64));
   TRY(upload(c, "dft_ppo", plane_pair_off.data(), sizeof(int) * (Bx + 1), &d_ppo));
   TRY(upload(c, "dft_peo", pair_ent_off.data(), sizeof(int) * (P + 1), &d_peo));
   void *d_gro, *d_gidx, *d_gay;
@@ -2206,16 +2264,32 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
   TRY(upload(c, "dft_xD", xD.data(), sizeof(int) * K, &d_xD));
   TRY(upload(c, "dft_ry", resv[1].data(), sizeof(int) * By, &d_ry));
   TRY(upload(c, "dft_rz", resv[2].data(), sizeof(int) * Bz, &d_rz));
-  float2* Ex = (float2*)ensure(c, "dft_Ex", sizeof(float2) * Nx * K, &st);
-  if (!Ex) return st;
-  float2* Ey = (float2*)ensure(c, "dft_Ey", sizeof(float2) * Ny * By, &st);
-  if (!Ey) return st;
-  float2* Ez = (float2*)ensure(c, "dft_Ez", sizeof(float2) * Nz * Bz, &st);
-  if (!Ez) return st;
-  if (dft_table(c->stream, (const int*)d_rx, K, Nx, Ex) || dft_table(c->stream, (const int*)d_ry, By, Ny, Ey) ||
-      dft_table(c->stream, (const int*)d_rz, Bz, Nz, Ez)) {
-    cudaGetLastError();
-    return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the DFT phase tables failed");
+  float2 *Ex = nullptr, *Ey = nullptr, *Ez = nullptr;
+  double2 *Ex64 = nullptr, *Ey64 = nullptr, *Ez64 = nullptr;
+  if (fp64) {
+    Ex64 = (double2*)ensure(c, "dft_Ex64", sizeof(double2) * Nx * K, &st);
+    if (!Ex64) return st;
+    Ey64 = (double2*)ensure(c, "dft_Ey64", sizeof(double2) * Ny * By, &st);
+    if (!Ey64) return st;
+    Ez64 = (double2*)ensure(c, "dft_Ez64", sizeof(double2) * Nz * Bz, &st);
+    if (!Ez64) return st;
+    if (dft_table64(c->stream, (const int*)d_rx, K, Nx, Ex64) || dft_table64(c->stream, (const int*)d_ry, By, Ny, Ey64) ||
+        dft_table64(c->stream, (const int*)d_rz, Bz, Nz, Ez64)) {
+      cudaGetLastError();
+      return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the FP64 DFT phase tables failed");
+    }
+  } else {
+    Ex = (float2*)ensure(c, "dft_Ex", sizeof(float2) * Nx * K, &st);
+    if (!Ex) return st;
+    Ey = (float2*)ensure(c, "dft_Ey", sizeof(float2) * Ny * By, &st);
+    if (!Ey) return st;
+    Ez = (float2*)ensure(c, "dft_Ez", sizeof(float2) * Nz * Bz, &st);
+    if (!Ez) return st;
+    if (dft_table(c->stream, (const int*)d_rx, K, Nx, Ex) || dft_table(c->stream, (const int*)d_ry, By, Ny, Ey) ||
+        dft_table(c->stream, (const int*)d_rz, Bz, Nz, Ez)) {
+      cudaGetLastError();
+      return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the DFT phase tables failed");
+    }
   }
   c->launches += 3;
   GridPhase gk = make_phase(gm.nk);
@@ -2226,7 +2300,7 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
   tm.end(c, &c->stats.stage1_ms);
   unsigned* tmaxp = (unsigned*)ensure(c, "tc_tmax", 64, &st);
   if (!tmaxp) return st;
-  const int64_t per_state = (int64_t)P * Nz * E * (int64_t)sizeof(float2);
+  const int64_t per_state = (int64_t)P * Nz * E * (int64_t)(fp64 ? sizeof(double2) : sizeof(float2));
   const int max_states = p->max_batch_states > 0
                              ? std::min(p->max_batch_states, 65535)  // states run along gridDim.y
                              : (int)std::max<int64_t>(1, std::min<int64_t>(4096, ((int64_t)8 << 30) / per_state));
@@ -2241,9 +2315,14 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
     TRY(upload(c, "tc_batch_k", kb_list.data(), sizeof(int) * nkb, &d_kb));
     TRY(upload(c, "tc_batch_stkb", st_kb.data(), sizeof(int) * S, &d_stkb));
     tm.begin(c);
-    const float* X1;
-    int64_t ldx1;
-    if (s1_ok) {
+    const float* X1 = nullptr;
+    int64_t ldx1 = 0;
+    double2* X64 = nullptr;
+    if (fp64) {
+      X64 = (double2*)ensure(c, "tc_X64", sizeof(double2) * (size_t)nkb * C, &st);
+      if (!X64) return st;
+      TRY(s1_batch(c, gm, s1a, kb_list, nullptr, 0, &s64a, X64));
+    } else if (s1_ok) {
       ldx1 = (2 * C + 3) / 4 * 4;
       float* X = (float*)ensure(c, "tc_X", sizeof(float) * (size_t)nkb * ldx1, &st);
       if (!X) return st;
@@ -2254,6 +2333,78 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
                                             (const int*)d_kb, (const int*)d_stkb, nullptr, &X1, &ldx1)));
     }
     tm.end(c, &c->stats.stage1_ms);
+    if (fp64) {
+      double2* Zs64 = (double2*)ensure(c, "dft_Zs64", (size_t)per_state * S, &st);
+      if (!Zs64) return st;
+      DftZ64Args z;
+      z.X = X64;
+      z.ldx = C;
+      z.st_kb = (const int*)d_stkb;
+      z.st_k = st_k + i0;
+      z.st_b = st_b + i0;
+      z.gm = gm;
+      z.UF = UF;
+      z.nw = nw;
+      z.w = (const double*)d_w64;
+      z.nR = nRp;
+      z.E = E;
+      z.P = P;
+      z.Nz = Nz;
+      z.Bz = Bz;
+      z.plane_pair_off = (const int*)d_ppo;
+      z.pair_ent_off = (const int*)d_peo;
+      z.ent_az = (const int*)d_az;
+      z.ent_r = (const int*)d_r;
+      z.Ez = Ez64;
+      z.Zs = Zs64;
+      DftX64Args x;
+      x.Zs = Zs64;
+      x.P = P;
+      x.Bx = Bx;
+      x.By = By;
+      x.Nx = Nx;
+      x.Ny = Ny;
+      x.Nz = Nz;
+      x.G = G;
+      x.row_grp_off = (const int*)d_gro;
+      x.grp_idx = (const int4*)d_gidx;
+      x.grp_ay = (const int*)d_gay;
+      x.K = K;
+      x.K0 = K0;
+      x.KP = KP;
+      x.xS = (const int*)d_xS;
+      x.xD = (const int*)d_xD;
+      x.Ex = Ex64;
+      x.Ey = Ey64;
+      x.st_k = st_k + i0;
+      x.st_b = st_b + i0;
+      x.gm = gm;
+      x.nw = nw;
+      x.nm = nm;
+      x.epsF = epsF;
+      x.fF = fF;
+      x.UF = UF;
+      x.Zq = Zq;
+      x.omega = omega;
+      x.nB = nB;
+      x.reach = (omega_max + p->delta_cut_sigmas * p->sigma_eV) * (1.0 + 1e-9);
+      x.inv_sigma = 1.0 / p->sigma_eV;
+      x.xcut = p->delta_cut_sigmas * p->sigma_eV;
+      x.scale = (2.0 * kPi / (double)Nq) / (kSqrtPi * p->sigma_eV);
+      x.gamma = raw;
+      x.s_base = i0;
+      x.nq_evaluated = nq_eval;
+      tm.begin(c);
+      if (dft64_launch(c->stream, z, x, S, ne_plane_max) != 0) {
+        cudaGetLastError();
+        return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the FP64 grid-DFT stage 2 failed");
+      }
+      c->launches += 2;
+      c->stats.stage2_launches++;
+      tm.end(c, &c->stats.stage2_ms);
+      i0 = i1;
+      continue;
+    }
     float2* Zs = (float2*)ensure(c, "dft_Zs", (size_t)per_state * S, &st);
     if (!Zs) return st;
     DftZArgs zz;
@@ -2389,10 +2540,11 @@ int run_tc(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& gm,
            const double* fF, const double* omega, const double* nB, const cplx* Zq, double* raw) {
   if (c->cc < 100) return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "tensor-core precisions need an sm_10x GPU");
   const int nw = c->nw, nm = 3 * c->na;
-  if (p->precision == PHOEBE_PREC_FP32_DFT) {
+  if (p->precision == PHOEBE_PREC_FP32_DFT || p->precision == PHOEBE_PREC_FP64_DFT) {
     if (c->defer || c->isreq)
       return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "the grid-DFT stage 2 serves the full q sum of single calls");
-    return run_dft(c, p, gm, ns, hk, st_k, st_b, epsF, UF, fF, omega, nB, Zq, raw);
+    return run_dft(c, p, gm, ns, hk, st_k, st_b, epsF, UF, fF, omega, nB, Zq, raw,
+                   p->precision == PHOEBE_PREC_FP64_DFT);
   }
   if (c->defer) {  // batched materials: one stage-2 form for every shape, recorded for later issue
     if (c->isreq) return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "batched linewidths use the full q sum");
