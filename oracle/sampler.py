@@ -13,13 +13,21 @@ module states the sampled alternative the library adds on top of it:
     (q~: q wrapped into [-1/2, 1/2) per axis; v_nk = <n| dH/dk |n> / 2 pi with
     the Fourier derivative of Eq. 10), 7 -> 128 -> 128 -> 128 -> 1 with SiLU,
     whose parameters are rounded to BF16;
-  * per k the defensive mixture p_k(q) = (1 - a) mean_{n active at k}
-    softmax_q z_nk(q) + a / N_q;
+  * per state the shell factor phi_nk(q): the bracket of Eq. 29 with |g|^2
+    replaced by 1/(hbar w_q nu), summed over final bands and live modes (zero
+    exactly where every Gaussian of the q term is cut, so zero wherever
+    c_nk(q) is);
+  * per k the defensive mixture p_k(q) = (1 - a) mean_n softmax_q (z_nk(q) +
+    log phi_nk(q)) + a mean_n phi_nk(q) / sum_q phi_nk, over the active bands n
+    with some phi > 0 (uniform when there is none: then every c is 0);
   * S i.i.d. draws q_j from p_k (inverse CDF in q-index order, FP64, driven by
     Philox4x32-10 uniforms) and the unbiased estimate
     Gamma^_nk = (1/S) sum_j c_nk(q_j) / (N_q p_k(q_j));
   * the training loss: per state the cross entropy between the target
-    distribution t(q) = c(q) / sum_q c and softmax_q z(q), averaged over states.
+    distribution t(q) = c(q) / sum_q c and softmax_q (z(q) + log phi(q)),
+    averaged over states;
+  * the network-free alternatives: the shell proposal mean_n phi_nk / sum phi_nk
+    and the uniform proposal 1/N_q.
 
 Parameter blob (float32, the library's layout): W1[128][7], b1[128], W2[128][128],
 b2[128], W3[128][128], b3[128], w4[128], b4 -- 34177 numbers.
@@ -144,27 +152,31 @@ def mlp_backward(theta: dict, cache, dz: np.ndarray) -> dict:
     return g
 
 
-def softmax_ce(z: np.ndarray, group_off: np.ndarray, target: np.ndarray):
-    """Loss (1/G) sum_groups -sum_{r in group} t_r log softmax(z)_r with t normalised per group,
-    and its gradient dL/dz = (softmax(z) - t) / G."""
+def softmax_ce(z: np.ndarray, group_off: np.ndarray, target: np.ndarray, prior: np.ndarray | None = None):
+    """Loss (1/G) sum_groups -sum_{r in group} t_r log softmax(z + prior)_r with t normalised per group,
+    and its gradient dL/dz = (softmax(z + prior) - t) / G.  ``prior``: per-row additive log-weights
+    (-inf allowed where the target is 0), default 0."""
     G = len(group_off) - 1
     loss, dz = 0.0, np.zeros_like(z)
     for g in range(G):
         a, b = int(group_off[g]), int(group_off[g + 1])
-        zz = z[a:b]
+        zz = z[a:b] + (prior[a:b] if prior is not None else 0.0)
         m = zz.max()
         lse = m + np.log(np.sum(np.exp(zz - m)))
         t = target[a:b] / np.sum(target[a:b])
-        loss += -np.sum(t * (zz - lse))
+        pos = t > 0
+        loss += -np.sum(t[pos] * (zz[pos] - lse))
         dz[a:b] = (np.exp(zz - lse) - t) / G
     return loss / G, dz
 
 
-def loss_and_grad(blob: np.ndarray, X: np.ndarray, group_off: np.ndarray, target: np.ndarray):
+def loss_and_grad(blob: np.ndarray, X: np.ndarray, group_off: np.ndarray, target: np.ndarray,
+                  prior: np.ndarray | None = None):
     """Training loss and its gradient (as a blob) at the BF16-rounded parameters of ``blob``."""
     theta = bf16_params(blob)
     z, cache = mlp_forward(theta, X)
-    loss, dz = softmax_ce(z, np.asarray(group_off), np.asarray(target, dtype=np.float64))
+    loss, dz = softmax_ce(z, np.asarray(group_off), np.asarray(target, dtype=np.float64),
+                          None if prior is None else np.asarray(prior, dtype=np.float64))
     return loss, pack(mlp_backward(theta, cache, dz)), z
 
 
@@ -209,16 +221,80 @@ def rows_for_state(feat: np.ndarray, qt: np.ndarray) -> np.ndarray:
     return X
 
 
+# ------------------------------------------------------------------ shell factor
+
+def shell_factor(mat, params, ks, bs, table=None, q_indices=None) -> np.ndarray:
+    """phi_nk(q) = sum_{m'} sum_{nu: hbar w_q nu >= omega_cut} [ (n_q nu + 1 - f_m'k+q) D(eps_nk - hbar w_q nu - eps_m'k+q)
+                  + (n_q nu + f_m'k+q) D(eps_nk + hbar w_q nu - eps_m'k+q) ] / (hbar w_q nu),
+    D(x) = exp(-x^2 / sigma^2) for |x| < cut sigma and 0 beyond: the bracket of Eq. 29 (Sec. 4.2,
+    Gaussian of Eq. 61 without its normalisation) with |g_m'n nu|^2 replaced by 1/(hbar w_q nu).
+    Every term of c_nk(q) carries one of these weights, so phi_nk(q) = 0 implies c_nk(q) = 0.
+    Returns (n_states, N_q) for every q of the grid (or (n_states, len(q_indices[s])))."""
+    F, eps_F, U_F, k_to_F = table if table is not None else elph.electron_table(mat, params)
+    nq = tuple(int(x) for x in params.nq)
+    qpts = elph.grid_points(nq)
+    kpts = elph.grid_points(tuple(int(x) for x in params.nk))
+    omega, _ = elph.phonon_modes(qpts, mat)
+    nB = elph.bose_einstein(omega, params.T_K)
+    alive = omega >= params.omega_cut_eV
+    inv_w = np.where(alive, 1.0 / np.where(alive, omega, 1.0), 0.0)
+    sig, xcut = params.sigma_eV, params.delta_cut_sigmas * params.sigma_eV
+    ks, bs = np.asarray(ks), np.asarray(bs)
+    out = []
+    for j, (k, b) in enumerate(zip(ks, bs)):
+        qi = np.arange(len(qpts)) if q_indices is None else np.asarray(q_indices[j])
+        e = eps_F[k_to_F[k], b]
+        kq = elph.grid_index(kpts[k][None, :] + qpts[qi], F)
+        ekq = eps_F[kq]                                              # (nq, m')
+        f = elph.fermi_dirac(ekq, params.mu_eV, params.T_K)
+        x1 = e - omega[qi][:, None, :] - ekq[:, :, None]             # (nq, m', nu)
+        x2 = e + omega[qi][:, None, :] - ekq[:, :, None]
+        d1 = np.where(np.abs(x1) < xcut, np.exp(-(x1 / sig) ** 2), 0.0)
+        d2 = np.where(np.abs(x2) < xcut, np.exp(-(x2 / sig) ** 2), 0.0)
+        w = (nB[qi][:, None, :] + 1.0 - f[:, :, None]) * d1 + (nB[qi][:, None, :] + f[:, :, None]) * d2
+        out.append(np.sum(w * inv_w[qi][:, None, :], axis=(1, 2)))
+    return np.array(out).reshape(len(ks), -1)
+
+
+def log_shell(phi: np.ndarray) -> np.ndarray:
+    """log phi with -inf where phi = 0."""
+    phi = np.asarray(phi, dtype=np.float64)
+    with np.errstate(divide="ignore"):
+        return np.where(phi > 0, np.log(np.where(phi > 0, phi, 1.0)), -np.inf)
+
+
 # ------------------------------------------------------------------ importance sampling
 
-def proposal(logits: np.ndarray, alpha: float) -> np.ndarray:
-    """p(q) = (1 - alpha) mean_rows softmax(logits[row]) + alpha / N_q for one k (rows = its active bands)."""
+def _softmax_rows(x: np.ndarray) -> np.ndarray:
+    m = x.max(axis=1, keepdims=True)
+    e = np.exp(x - m)
+    return e / e.sum(axis=1, keepdims=True)
+
+
+def proposal(logits: np.ndarray, alpha: float, log_phi: np.ndarray | None = None) -> np.ndarray:
+    """Proposal of one k (rows = its active bands).  Without ``log_phi``:
+    p(q) = (1 - alpha) mean_rows softmax(logits[row]) + alpha / N_q.  With it (the shell factor):
+    p(q) = (1 - alpha) mean_live softmax(logits + log_phi) + alpha mean_live softmax(log_phi) over the
+    rows with some phi > 0; the uniform 1/N_q when there is none (every c of the k is then 0)."""
     logits = np.atleast_2d(logits)
-    m = logits.max(axis=1, keepdims=True)
-    e = np.exp(logits - m)
-    sm = e / e.sum(axis=1, keepdims=True)
     Nq = logits.shape[1]
-    return (1.0 - alpha) * sm.mean(axis=0) + alpha / Nq
+    if log_phi is None:
+        return (1.0 - alpha) * _softmax_rows(logits).mean(axis=0) + alpha / Nq
+    lp = np.atleast_2d(log_phi)
+    live = np.isfinite(lp).any(axis=1)
+    if not live.any():
+        return np.full(Nq, 1.0 / Nq)
+    return ((1.0 - alpha) * _softmax_rows(logits[live] + lp[live]).mean(axis=0)
+            + alpha * _softmax_rows(lp[live]).mean(axis=0))
+
+
+def shell_proposal(log_phi: np.ndarray) -> np.ndarray:
+    """p(q) = mean_live phi_row(q) / sum_q phi_row over the rows with some phi > 0 (uniform if none)."""
+    lp = np.atleast_2d(log_phi)
+    live = np.isfinite(lp).any(axis=1)
+    if not live.any():
+        return np.full(lp.shape[1], 1.0 / lp.shape[1])
+    return _softmax_rows(lp[live]).mean(axis=0)
 
 
 def draw(p: np.ndarray, u: np.ndarray) -> np.ndarray:
@@ -236,10 +312,12 @@ def is_estimate(c_sampled: np.ndarray, p: np.ndarray, q_drawn: np.ndarray) -> np
 
 
 def linewidths_is(mat, params, blob, fraction: float, alpha: float, seed: int, k_indices=None,
-                  uniform: bool = False, table=None):
+                  uniform: bool = False, table=None, mode: str | None = None):
     """Importance-sampled Gamma of the active states (before degenerate averaging is applied, then
-    averaged like ``elph.linewidths_rta``).  ``uniform``: p_k = 1/N_q (the method without the network).
+    averaged like ``elph.linewidths_rta``).  ``mode``: "learned" (network times shell factor, the
+    default), "shell" (the shell factor alone) or "uniform" (p_k = 1/N_q; also ``uniform=True``).
     Returns (k_index, band, gamma)."""
+    mode = "uniform" if uniform else (mode or "learned")
     table = table if table is not None else elph.electron_table(mat, params)
     F, eps_F, U_F, k_to_F = table
     nq = tuple(int(x) for x in params.nq)
@@ -250,17 +328,21 @@ def linewidths_is(mat, params, blob, fraction: float, alpha: float, seed: int, k
     if k_indices is not None:
         keep = np.isin(ks, np.asarray(k_indices))
         ks, bs = ks[keep], bs[keep]
-    theta = None if uniform else bf16_params(blob)
+    theta = bf16_params(blob) if mode == "learned" else None
     qt = wrapped_q(nq)
-    feats = state_features(mat, params, ks, bs, table=table) if not uniform else None
+    feats = state_features(mat, params, ks, bs, table=table) if mode == "learned" else None
     raw = np.zeros(len(ks))
     for ik in np.unique(ks):
         sel = np.nonzero(ks == ik)[0]
-        if uniform:
+        if mode == "uniform":
             p = np.full(Nq, 1.0 / Nq)
         else:
-            logits = np.stack([mlp_forward(theta, rows_for_state(feats[j], qt))[0] for j in sel])
-            p = proposal(logits, alpha)
+            lp = log_shell(shell_factor(mat, params, ks[sel], bs[sel], table=table))
+            if mode == "shell":
+                p = shell_proposal(lp)
+            else:
+                logits = np.stack([mlp_forward(theta, rows_for_state(feats[j], qt))[0] for j in sel])
+                p = proposal(logits, alpha, lp)
         q = draw(p, is_uniforms(seed, int(ik), S))
         qi = np.repeat(q[None, :], len(sel), axis=0)
         _, _, c = elph.contributions(mat, params, k_indices=[ik], q_indices=qi, table=table)

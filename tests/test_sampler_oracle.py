@@ -215,3 +215,127 @@ def test_importance_sampled_linewidth_is_unbiased():
         mean, se = runs.mean(0), runs.std(0, ddof=1) / np.sqrt(len(runs))
         assert np.all(np.abs(mean - exact) <= 4 * se + 1e-12 * exact)
         assert np.max(se) > 0
+
+
+# ------------------------------------------------------------------ shell factor of the proposal
+
+def _two_einstein(equal_ratio: bool):
+    """Two Einstein frequencies (hbar w_s = 0.0647 sqrt(lam_s)); with |c|^2/M1 = |d|^2/M2 every mode's
+    sum over its three degenerate partners of |g|^2 is K / (hbar w_s) with one K for both atoms."""
+    c = np.array([0.3, -0.2, 0.1])
+    M = (28.0, 12.0)
+    d = c * np.sqrt(M[1] / M[0]) * (1.0 if equal_ratio else 1.7)
+    return W.tb_einstein2(c=tuple(c), d=tuple(d), mass=M, lam=(0.215, 0.6), n=6)
+
+
+def test_shell_factor_zero_variance_on_einstein_models():
+    # one band, constant coupling: c_k(q) = 2 pi / (sqrt(pi) sigma) sum_nu |g_nu|^2 W_nu(q) with W the
+    # bracket of Eq. 29.  With |g_nu|^2 proportional to 1/(hbar w_nu) for every mode, c / phi is the same
+    # for every q, so the shell proposal p ~ phi gives the exact q sum for any draws.  The one-frequency
+    # model fixes the occupation and Gaussian weights; the two-frequency model fixes the 1/(hbar w) factor.
+    for mat, prm in (W.tb_einstein(eps0=0.05, t=0.25, lam=0.215, n=6, mu=0.1), _two_einstein(True)):
+        tab = elph.electron_table(mat, prm)
+        kk = [0, 7, 100, 215]
+        ks, bs, c = elph.contributions(mat, prm, k_indices=kk, table=tab)
+        phi = S.shell_factor(mat, prm, ks, bs, table=tab)
+        pos = c > 0
+        assert np.all(phi[pos] > 0) and np.any(pos)
+        ratio = c[pos] / phi[pos]
+        assert np.max(ratio) - np.min(ratio) <= 1e-10 * np.max(ratio)
+        _, _, exact = elph.linewidths_rta(mat, prm, k_indices=kk, table=tab)
+        for seed in (1, 2):
+            _, _, est = S.linewidths_is(mat, prm, None, 0.05, 0.1, seed, k_indices=kk, table=tab, mode="shell")
+            assert np.allclose(est, exact, rtol=1e-10, atol=0)
+    # unequal |c|^2 / M: the two frequencies' terms no longer share one ratio (the estimate is noisy)
+    mat, prm = _two_einstein(False)
+    tab = elph.electron_table(mat, prm)
+    ks, bs, c = elph.contributions(mat, prm, k_indices=[7, 100], table=tab)
+    phi = S.shell_factor(mat, prm, ks, bs, table=tab)
+    r = c[c > 0] / phi[c > 0]
+    assert np.max(r) - np.min(r) > 1e-3 * np.max(r)
+
+
+def test_shell_factor_vanishes_only_where_every_term_is_cut():
+    # phi > 0 wherever c > 0 (the proposal then covers every non-zero term, so the estimate is unbiased);
+    # phi = 0 at some q (the delta shell excludes them), and phi is unchanged by the coupling's size
+    mat, prm = W.toy(seed=0)
+    tab = elph.electron_table(mat, prm)
+    kk = [3, 77, 300]
+    ks, bs, c = elph.contributions(mat, prm, k_indices=kk, table=tab)
+    phi = S.shell_factor(mat, prm, ks, bs, table=tab)
+    assert phi.shape == c.shape
+    assert np.all(phi[c > 0] > 0)
+    prm2 = prm.with_(sigma_eV=0.01)
+    ks2, bs2, c2 = elph.contributions(mat, prm2, k_indices=kk, table=tab)
+    phi2 = S.shell_factor(mat, prm2, ks2, bs2, table=tab)
+    assert np.all(phi2[c2 > 0] > 0) and np.any(phi2 == 0)
+    mat3 = W.Material(**{**mat.__dict__, "g": mat.g * 3.0})
+    assert np.array_equal(S.shell_factor(mat3, prm2, ks2, bs2, table=tab), phi2)
+    qi = np.array([[0, 5, 511], [2, 2, 100], [7, 8, 9]])
+    sub = S.shell_factor(mat, prm, ks[:3], bs[:3], table=tab, q_indices=qi)
+    assert np.array_equal(sub, np.take_along_axis(phi[:3], qi, axis=1))
+
+
+def test_shell_proposal_is_normalised_and_defensive():
+    rng = np.random.default_rng(8)
+    logits = rng.standard_normal((3, 64)) * 4
+    phi = rng.uniform(0, 1, (3, 64)) ** 3
+    phi[:, :10] = 0.0                                   # outside every row's shell
+    phi[2] = 0.0                                        # a row without any shell: left out
+    lp = S.log_shell(phi)
+    p = S.proposal(logits, 0.1, lp)
+    assert p.sum() == pytest.approx(1.0, rel=1e-14)
+    assert np.all(p[:10] == 0.0)
+    sh = S.shell_proposal(lp)
+    assert sh.sum() == pytest.approx(1.0, rel=1e-14)
+    assert np.allclose(sh, 0.5 * (phi[0] / phi[0].sum() + phi[1] / phi[1].sum()), rtol=1e-13)
+    assert np.all(p >= 0.1 * sh * (1 - 1e-14))
+    assert np.all(S.proposal(logits, 0.1, np.full((3, 64), -np.inf)) == 1.0 / 64)
+
+
+def test_loss_gradient_with_prior_matches_finite_differences():
+    rng = np.random.default_rng(12)
+    X = rng.uniform(-1, 1, (50, S.NIN))
+    off = np.array([0, 20, 50])
+    t = rng.uniform(0, 1, 50) ** 4
+    prior = rng.normal(0, 2, 50)
+    t[[3, 30]] = 0.0
+    prior[[3, 30]] = -np.inf                             # zero prior weight where the target is 0
+    theta = S.bf16_params(_random_blob(4, scale=2.0))
+
+    def loss_of(th):
+        return S.softmax_ce(S.mlp_forward(th, X)[0], off, t, prior)[0]
+
+    z, cache = S.mlp_forward(theta, X)
+    loss, dz = S.softmax_ce(z, off, t, prior)
+    assert np.isfinite(loss) and dz[3] == 0.0 and dz[30] == 0.0
+    g = S.mlp_backward(theta, cache, dz)
+    h = 1e-6
+    for name, shape in S.SHAPES:
+        flat = theta[name].ravel()
+        for idx in rng.choice(flat.size, size=min(5, flat.size), replace=False):
+            tp = {k: v.copy() for k, v in theta.items()}
+            tm = {k: v.copy() for k, v in theta.items()}
+            tp[name].ravel()[idx] += h
+            tm[name].ravel()[idx] -= h
+            fd = (loss_of(tp) - loss_of(tm)) / (2 * h)
+            assert abs(fd - g[name].ravel()[idx]) <= 1e-6 * max(1e-3, abs(fd)), (name, idx)
+    # the minimum is at softmax(z + prior) = t
+    zmin = np.where(t > 0, np.log(np.where(t > 0, t, 1.0)), 0.0) - np.where(np.isfinite(prior), prior, 0.0)
+    _, dzmin = S.softmax_ce(zmin, off, t, prior)
+    assert np.max(np.abs(dzmin)) < 1e-15
+
+
+def test_shell_and_learned_proposals_are_unbiased():
+    # E[Gamma^] = Gamma over 32 seeds for the shell proposal and the network-times-shell proposal
+    mat, prm = W.toy(seed=0)
+    prm = prm.with_(nk=(4, 4, 4), nq=(4, 4, 4), sigma_eV=0.1)
+    tab = elph.electron_table(mat, prm)
+    kk = [1, 22, 43]
+    ks, bs, exact = elph.linewidths_rta(mat, prm, k_indices=kk, table=tab)
+    blob = _random_blob(13, scale=3.0)
+    for mode in ("shell", "learned"):
+        runs = np.array([S.linewidths_is(mat, prm, blob, 0.25, 0.1, seed, k_indices=kk, table=tab,
+                                         mode=mode)[2] for seed in range(32)])
+        mean, se = runs.mean(0), runs.std(0, ddof=1) / np.sqrt(len(runs))
+        assert np.all(np.abs(mean - exact) <= 4 * se + 1e-12 * exact)

@@ -307,6 +307,29 @@ def tb_einstein(eps0: float = 0.0, t: float = 0.25, lam: float = 0.215,
                           sigma_eV=sigma, window_eV=0.0)
 
 
+def tb_einstein2(eps0: float = 0.05, t: float = 0.25, lam=(0.215, 0.6), mass=(28.0, 12.0),
+                 c=(0.3, -0.2, 0.1), d=(0.1, 0.25, -0.15), n: int = 6, sigma: float = 0.05,
+                 T_K: float = 300.0, mu: float = 0.1) -> tuple[Material, RTAParams]:
+    """One band, two atoms with independent Einstein springs (two frequencies), constant coupling.
+
+    The band is that of ``tb_einstein``; Phi(0) = diag(M1 lam1 I, M2 lam2 I), so the modes are
+    hbar w_s = 0.06465 sqrt(lam_s), three per atom, their eigenvectors on one atom each;
+    g(Re=0,Rp=0)[0][0][3s + a] = c_a (s = 0) or d_a (s = 1).  No randomness.
+    """
+    mat1, prm = tb_einstein(eps0=eps0, t=t, lam=lam[0], c=c, mass=mass[0], n=n, sigma=sigma, T_K=T_K, mu=mu)
+    Phi = np.zeros((1, 6, 6))
+    Phi[0, :3, :3] = mass[0] * lam[0] * np.eye(3)
+    Phi[0, 3:, 3:] = mass[1] * lam[1] * np.eye(3)
+    g = np.zeros((1, 1, 1, 1, 6), dtype=np.complex128)
+    g[0, 0, 0, 0, :3] = np.asarray(c, dtype=np.complex128)
+    g[0, 0, 0, 0, 3:] = np.asarray(d, dtype=np.complex128)
+    Z0 = np.zeros((1, 3), dtype=np.int32)
+    mat = Material("tb_einstein2", 1, 2, np.array(mass, dtype=np.float64), np.eye(3),
+                   np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.5]]), mat1.R_H, mat1.w_H, mat1.H,
+                   np.zeros((1, 3), dtype=np.int32), np.ones(1), Phi, Z0, np.ones(1), Z0.copy(), np.ones(1), g)
+    return mat, prm
+
+
 def material_of_shape(name: str, nw: int, na: int, nR_target: int, n: int, rng: np.random.Generator,
                       g_budget_bytes: float = 256e6) -> tuple[Material, RTAParams]:
     """A crystal of a given shape built by the Si-like rules (fcc lattice, decaying seeded H and g).
