@@ -144,7 +144,9 @@ def roofline(precision: int, stats: list, k_limit: int) -> dict:
                 "algorithmic_flops_per_launch": s2_flops / max(s2_launch, 1),
                 "avg_launch_ms": s2_ms / max(s2_launch, 1),
                 "note": "flops count the DFT's complex MACs as evaluated (8 flop each; x sum only for the q "
-                        "whose final bands reach the delta window); the rotation/delta epilogue is not counted"}
+                        "whose final bands reach the delta window) and the epilogue's two rotations per listed "
+                        "(state, q, band) (U_{k+q}^dagger: N_w 3N_at, Z_q: (3N_at)^2 complex MACs); the Gaussian "
+                        "and occupation arithmetic is not counted"}
     elif precision in (0, 8):
         roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
                 "frac": achieved / 1.25 if achieved else None, "traffic": None,
@@ -228,7 +230,7 @@ def learned_leg(pg, W, dev, stream, args) -> dict:
     timed(pe)                                     # warm-up (allocations, 80^3 tables)
     (_, _, full), full_s, full_st = timed(pe)
     res = {}
-    for name, smp in (("learned", 1), ("uniform", 2)):
+    for name, smp in (("learned", 1), ("shell", 3), ("uniform", 2)):
         errs, walls, st = [], [], None
         for seed in range(4):
             (_, _, g), w, st = timed(pe.with_(sampler=smp, sample_fraction=0.05, seed=seed))
@@ -245,10 +247,16 @@ def learned_leg(pg, W, dev, stream, args) -> dict:
         "workload": "si_like 40^3 k x 80^3 q, seeded subset of k; trained on the si_like 20^3 x 20^3 q terms",
         "states": int(n), "sample_fraction": 0.05, "mix_alpha": 0.1, "precision": PREC_NAMES[prec],
         "train_s": train_s, "train_loss_first_last": [float(loss[0]), float(loss[-1])],
-        "l2_rel_err_learned": res["learned"]["l2_rel_err"], "l2_rel_err_uniform": res["uniform"]["l2_rel_err"],
+        "proposal": "(1 - alpha) softmax(z + log phi) + alpha phi / sum phi, phi the shell factor (the bracket of "
+                    "Eq. 29 with |g|^2 replaced by 1/(hbar w))",
+        "l2_rel_err_learned": res["learned"]["l2_rel_err"], "l2_rel_err_shell_only": res["shell"]["l2_rel_err"],
+        "l2_rel_err_uniform": res["uniform"]["l2_rel_err"],
         "variance_ratio_uniform_over_learned": float(np.mean(np.square(res["uniform"]["l2_rel_err"])) /
                                                      np.mean(np.square(res["learned"]["l2_rel_err"]))),
+        "variance_ratio_shell_only_over_learned": float(np.mean(np.square(res["shell"]["l2_rel_err"])) /
+                                                        np.mean(np.square(res["learned"]["l2_rel_err"]))),
         "gate_l2_1pct_met": bool(np.mean(res["learned"]["l2_rel_err"]) <= 0.01),
+        "linewidths_per_s_shell_only": n / res["shell"]["wall_s"],
         "linewidths_per_s_learned": lw, "linewidths_per_s_full_same_precision": n / full_s,
         "linewidths_per_s_fp64_gpu_full": len(g64) / w64,
         "speedup_learned_vs_fp64_gpu": lw / (len(g64) / w64),

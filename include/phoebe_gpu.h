@@ -160,11 +160,11 @@ typedef struct {
   const int32_t* k_subset;   /*       k-grid indices (i1*N2+i2)*N3+i3 */
   int max_batch_states;      /* states per stage-1/stage-2 batch, 0 = automatic */
   int sampler;               /* phoebe_gpu_sampler: how the q sum of Eq. 29 is evaluated (default full) */
-  double sample_fraction;    /* sampler LEARNED/UNIFORM: draws per initial k = ceil(fraction * N_q),
+  double sample_fraction;    /* sampler LEARNED/UNIFORM/SHELL: draws per initial k = ceil(fraction * N_q),
                                 0 < fraction <= 1 (default 0.05) */
-  double mix_alpha;          /* sampler LEARNED: weight of the uniform part of the proposal,
+  double mix_alpha;          /* sampler LEARNED: weight of the shell-only part of the proposal,
                                 0 < alpha <= 1 (default 0.1) */
-  uint64_t seed;             /* sampler LEARNED/UNIFORM: key of the Philox4x32-10 draws */
+  uint64_t seed;             /* sampler LEARNED/UNIFORM/SHELL: key of the Philox4x32-10 draws */
   int sampler_fp32_network;  /* sampler LEARNED: 1 scores q with the FP32 CUDA-core forward pass,
                                 0 (default) with the tensor-core kernel (FP16 operands) on sm_10x */
   int smearing;              /* 0 (default): Gaussian of fixed width sigma_eV; 1: adaptive width per pair
@@ -185,7 +185,8 @@ typedef struct {
 typedef enum {
   PHOEBE_SAMPLER_FULL = 0,     /* every q of the grid (the paper's sum) */
   PHOEBE_SAMPLER_LEARNED = 1,  /* importance sampling from the learned proposal (see below) */
-  PHOEBE_SAMPLER_UNIFORM = 2   /* importance sampling from the uniform proposal */
+  PHOEBE_SAMPLER_UNIFORM = 2,  /* importance sampling from the uniform proposal */
+  PHOEBE_SAMPLER_SHELL = 3     /* importance sampling from the shell factor alone (no network) */
 } phoebe_gpu_sampler;
 
 /* Fill *p with the defaults (cut 6 sigma, omega_cut 1e-4, degen 1e-6, FP64, T=300, full q sum,
@@ -283,15 +284,22 @@ int phoebe_gpu_transport_rta(phoebe_gpu_ctx* ctx, const phoebe_gpu_rta_params* p
 /* ------------------------------------------------------------------------------------------
  * Importance-sampled q sums with a learned proposal.  The paper has no counterpart: Eq. 29
  * sums every q of the grid.  Write c_nk(q) for N_q times the q term of Eq. 29, so that
- * Gamma_nk = (1/N_q) sum_q c_nk(q).  With params->sampler = PHOEBE_SAMPLER_LEARNED,
- * linewidths_rta draws, per initial k, S = ceil(sample_fraction * N_q) q points i.i.d. from
- *     p_k(q) = (1 - alpha) mean_{n active at k} softmax_q z_nk(q) + alpha / N_q
+ * Gamma_nk = (1/N_q) sum_q c_nk(q).  The shell factor of a state is the bracket of Eq. 29 with
+ * |g|^2 replaced by 1/(hbar w_q nu), summed over final bands and live modes (delta = the
+ * truncated Gaussian of Eq. 61 without its normalisation):
+ *     phi_nk(q) = sum_{m' nu} [(n + 1 - f_m'k+q) D(eps_nk - w - eps_m'k+q) + (n + f) D(eps_nk + w - ...)] / w;
+ * it is zero exactly where every term of c_nk(q) is cut, so it vanishes wherever c does.
+ * With params->sampler = PHOEBE_SAMPLER_LEARNED, linewidths_rta draws, per initial k,
+ * S = ceil(sample_fraction * N_q) q points i.i.d. from
+ *     p_k(q) = (1 - alpha) mean_n softmax_q (z_nk(q) + log phi_nk(q)) + alpha mean_n phi_nk(q) / sum_q phi_nk,
+ * the means over the active bands n of k with some phi > 0 (1/N_q when there is none)
  * (inverse CDF in q-index order, FP64, Philox4x32-10 uniforms: draw j of k-grid index k uses
  * counter (j, k, 0x4953, 0), key (seed low word, seed high word), u = ((x1 << 32 | x0) >> 11) 2^-53)
  * and returns the unbiased estimate
  *     Gamma^_nk = (1/S) sum_j c_nk(q_j) / (N_q p_k(q_j)),
- * then averages degenerate bands as the full sum does.  PHOEBE_SAMPLER_UNIFORM uses
- * p_k = 1/N_q (no network).  Both need a tensor-core precision (1..6) and (nw, 3na) in
+ * then averages degenerate bands as the full sum does.  PHOEBE_SAMPLER_SHELL uses
+ * p_k = mean_n phi_nk / sum_q phi_nk, PHOEBE_SAMPLER_UNIFORM p_k = 1/N_q (neither needs the network).
+ * All three need a tensor-core precision (1..6) and (nw, 3na) in
  * {(8,6), (2,3), (1,3)} with N_Rp * 3na * nw * 8 bytes <= 200 KB.
  * The network z = MLP(x), x = (q~, eps_nk - mu, v_nk): q~ is q wrapped into [-1/2, 1/2) per
  * axis, v_nk = <n| sum_R w_R i R e^{ik.R} H(R) |n> = (1/2 pi) d eps_nk / dk (eV, crystal axes);
@@ -320,27 +328,30 @@ void phoebe_gpu_train_opts_default(phoebe_gpu_train_opts* o);
 /* Train the network on one full-grid run: computes c_nk(q) for every active state of `grid`
  * (its sampler field is ignored; its precision must be 1..6) and minimises, with Adam, the
  * mean over states of the cross entropy between t(q) = c_nk(q) / sum_q c_nk(q) and
- * softmax_q z_nk(q).  States with sum_q c = 0 are skipped.  loss_per_epoch (host, `epochs`
+ * softmax_q (z_nk(q) + log phi_nk(q)).  States with sum_q c = 0 are skipped.  loss_per_epoch (host, `epochs`
  * doubles, may be NULL) receives the mean loss of each epoch.  Needs init or load first. */
 int phoebe_gpu_sampler_train(phoebe_gpu_ctx* ctx, const phoebe_gpu_rta_params* grid,
                              const phoebe_gpu_train_opts* opts, double* loss_per_epoch);
 
-/* c_nk(q) for every active state and every q (host float [n_states][N_q], q in grid-index order)
- * and the state features (host float [n_states][4]: eps - mu, v[3]; may be NULL).  Two-call
- * pattern as linewidths_rta; precision must be 1..6. */
+/* c_nk(q) for every active state and every q (host float [n_states][N_q], q in grid-index order),
+ * the state features (host float [n_states][4]: eps - mu, v[3]; may be NULL) and log phi_nk(q)
+ * (host float [n_states][N_q], -inf where phi = 0; may be NULL).  Two-call pattern as
+ * linewidths_rta; precision must be 1..6. */
 int phoebe_gpu_q_contributions(phoebe_gpu_ctx* ctx, const phoebe_gpu_rta_params* params, int* n_states,
-                               int32_t* k_index, int32_t* band, float* c, float* features);
+                               int32_t* k_index, int32_t* band, float* c, float* features, float* log_shell);
 
 /* The network and its training loss on explicit rows, for checking the kernels.
  *   x       host float [n_rows][7]
  *   group_off  host int64 [n_groups + 1] row offsets of the softmax groups (0 = first, n_rows = last)
  *   target  host float [n_rows] non-negative, or NULL (then only logits are computed)
- *   logits  host float [n_rows] or NULL
- *   loss    mean over groups of -sum t log softmax(z), t = target / its group sum (or NULL)
+ *   log_prior  host float [n_rows] additive log weights of the softmax (-inf allowed where the
+ *              target is 0), or NULL (0)
+ *   logits  host float [n_rows] or NULL (the network's z, without the prior)
+ *   loss    mean over groups of -sum t log softmax(z + prior), t = target / its group sum (or NULL)
  *   grad    host float [PHOEBE_GPU_MLP_NPARAM] dloss/dparameters at the BF16-rounded values (or NULL) */
 int phoebe_gpu_mlp_loss_grad(phoebe_gpu_ctx* ctx, int64_t n_rows, const float* x, int n_groups,
-                             const int64_t* group_off, const float* target, float* logits, double* loss,
-                             float* grad);
+                             const int64_t* group_off, const float* target, const float* log_prior, float* logits,
+                             double* loss, float* grad);
 
 /* Network scores z for n_states feature rows (host float [n_states][4]: eps - mu, v[3]) over
  * every q of the grid nq (host float output [n_states][N_q], q in grid-index order).
@@ -356,9 +367,10 @@ int phoebe_gpu_is_uniforms(phoebe_gpu_ctx* ctx, uint64_t seed, int32_t k, int64_
 /* ------------------------------------------------------------------------------------------
  * Many materials in one call.  The paper has no counterpart (it treats one crystal per run).
  * Each item names a context holding one material (set_* done; all contexts on one device)
- * and its parameters (precision 1..6, sampler FULL).  Phase 1 runs, per material on its own
- * context and stream, the grid band structure, phonons, window, stage 1 and the stage-2
- * operands, and records the material's stage-2 launches; with autotune on, the tile width
+ * and its parameters (precision 1..6, sampler FULL; distinct contexts).  Phase 1 runs, per
+ * material on its own context and stream, the grid band structure, phonons, window, stage 1
+ * and the stage-2 operands, and records the material's stage-2 launches, several materials at
+ * once on plan_threads host threads; with autotune on, the tile width
  * (128 or 256 columns) and the K blocks per TMEM partial (1, 2 or 4) of its stage-2 GEMM are
  * chosen by timing each candidate once on the material's first q chunk.  Phase 2 captures
  * the recorded launches of all materials into one CUDA graph (materials spread round-robin
@@ -386,7 +398,10 @@ typedef struct {
   double finish_ms;          /* out: phase 3 wall time */
   int64_t graph_nodes;       /* out: nodes of the captured graph */
   int64_t recorded_launches; /* out: recorded stage-2 chunks (each a GEMM and an epilogue launch) */
-  int reserved[4];           /* must be zero */
+  int plan_threads;          /* host threads of phase 1, each planning one material at a time on the
+                                material's own stream, so that materials overlap on the GPU
+                                (0 = default 8, at most 64; 1 = one material after the other) */
+  int reserved[3];           /* must be zero */
 } phoebe_gpu_batch_opts;
 
 void phoebe_gpu_batch_opts_default(phoebe_gpu_batch_opts* o);

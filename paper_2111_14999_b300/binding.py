@@ -23,7 +23,7 @@ STATUS = {
 PREC_FP64, PREC_SPLIT_BF16, PREC_SPLIT_TF32, PREC_BF16, PREC_TF32, PREC_SPLIT_FP16, PREC_BF16X3 = 0, 1, 2, 3, 4, 5, 6
 PREC_FP32_DFT = 7
 PREC_FP64_DFT = 8
-SAMPLER_FULL, SAMPLER_LEARNED, SAMPLER_UNIFORM = 0, 1, 2
+SAMPLER_FULL, SAMPLER_LEARNED, SAMPLER_UNIFORM, SAMPLER_SHELL = 0, 1, 2, 3
 MLP_NPARAM = 34177
 
 # symbols declared in include/phoebe_gpu.h
@@ -88,7 +88,7 @@ class BatchOpts(C.Structure):
         ("autotune", C.c_int), ("n_streams", C.c_int), ("g_chunk_bytes", C.c_int64),
         ("plan_ms", C.c_double), ("graph_ms", C.c_double), ("finish_ms", C.c_double),
         ("graph_nodes", C.c_int64), ("recorded_launches", C.c_int64),
-        ("reserved", C.c_int * 4),
+        ("plan_threads", C.c_int), ("reserved", C.c_int * 3),
     ]
 
 
@@ -132,8 +132,8 @@ def _load() -> C.CDLL:
         "phoebe_gpu_sampler_save": (I, [P, P, I64]),
         "phoebe_gpu_train_opts_default": (None, [C.POINTER(TrainOpts)]),
         "phoebe_gpu_sampler_train": (I, [P, C.POINTER(RTAParams), C.POINTER(TrainOpts), P]),
-        "phoebe_gpu_q_contributions": (I, [P, C.POINTER(RTAParams), C.POINTER(I), P, P, P, P]),
-        "phoebe_gpu_mlp_loss_grad": (I, [P, I64, P, I, P, P, P, P, P]),
+        "phoebe_gpu_q_contributions": (I, [P, C.POINTER(RTAParams), C.POINTER(I), P, P, P, P, P]),
+        "phoebe_gpu_mlp_loss_grad": (I, [P, I64, P, I, P, P, P, P, P, P]),
         "phoebe_gpu_is_uniforms": (I, [P, C.c_uint64, C.c_int32, I64, P]),
         "phoebe_gpu_mlp_scores": (I, [P, I, P, P, I, P]),
         "phoebe_gpu_batch_opts_default": (None, [C.POINTER(BatchOpts)]),
@@ -406,37 +406,45 @@ class PhoebeGPU:
         self._check(lib.phoebe_gpu_sampler_train(self._ctx, C.byref(s), C.byref(o), _ptr(loss)))
         return loss
 
-    def q_contributions(self, params, nq_total: int | None = None, **kw):
-        """c_nk(q) for every active state and q: returns (k_index, band, c [n][N_q] float32, features [n][4])."""
+    def q_contributions(self, params, nq_total: int | None = None, log_shell: bool = False, **kw):
+        """c_nk(q) for every active state and q: returns (k_index, band, c [n][N_q] float32, features [n][4]),
+        plus log phi [n][N_q] (the shell factor) with ``log_shell``."""
         s = params if isinstance(params, RTAParams) else make_params(params, **kw)
         n = C.c_int(0)
-        self._check(lib.phoebe_gpu_q_contributions(self._ctx, C.byref(s), C.byref(n), None, None, None, None))
+        self._check(lib.phoebe_gpu_q_contributions(self._ctx, C.byref(s), C.byref(n), None, None, None, None, None))
         Nq = int(s.nq[0]) * int(s.nq[1]) * int(s.nq[2])
         m = max(n.value, 1)
         ki = np.empty(m, dtype=np.int32)
         bd = np.empty(m, dtype=np.int32)
         cq = np.empty((m, Nq), dtype=np.float32)
         ft = np.empty((m, 4), dtype=np.float32)
+        lp = np.empty((m, Nq), dtype=np.float32) if log_shell else None
         nn = C.c_int(m)
         self._check(lib.phoebe_gpu_q_contributions(self._ctx, C.byref(s), C.byref(nn), _ptr(ki), _ptr(bd), _ptr(cq),
-                                                   _ptr(ft)))
+                                                   _ptr(ft), _ptr(lp) if log_shell else None))
         k = nn.value
+        if log_shell:
+            return ki[:k], bd[:k], cq[:k], ft[:k], lp[:k]
         return ki[:k], bd[:k], cq[:k], ft[:k]
 
-    def mlp_loss_grad(self, x, group_off=None, target=None):
-        """Network logits, and with targets the loss and gradient, on explicit rows x [n][7]."""
+    def mlp_loss_grad(self, x, group_off=None, target=None, log_prior=None):
+        """Network logits, and with targets the loss and gradient (softmax of z + log_prior), on explicit
+        rows x [n][7]."""
         x = np.ascontiguousarray(x, dtype=np.float32)
         n = len(x)
         logits = np.empty(n, dtype=np.float32)
         if target is None:
-            self._check(lib.phoebe_gpu_mlp_loss_grad(self._ctx, n, _ptr(x), 0, None, None, _ptr(logits), None, None))
+            self._check(lib.phoebe_gpu_mlp_loss_grad(self._ctx, n, _ptr(x), 0, None, None, None, _ptr(logits), None,
+                                                     None))
             return logits
         off = np.ascontiguousarray(group_off, dtype=np.int64)
         t = np.ascontiguousarray(target, dtype=np.float32)
+        lp = None if log_prior is None else np.ascontiguousarray(log_prior, dtype=np.float32)
         loss = C.c_double(0.0)
         grad = np.empty(MLP_NPARAM, dtype=np.float32)
         self._check(lib.phoebe_gpu_mlp_loss_grad(self._ctx, n, _ptr(x), len(off) - 1, _ptr(off), _ptr(t),
-                                                 _ptr(logits), C.byref(loss), _ptr(grad)))
+                                                 None if lp is None else _ptr(lp), _ptr(logits), C.byref(loss),
+                                                 _ptr(grad)))
         return logits, loss.value, grad
 
     def mlp_scores(self, features, nq, tensor_cores: bool = True) -> np.ndarray:

@@ -1,12 +1,17 @@
 // Linewidths of many materials in one call.  Phase 1 runs, per material on its own
 // context, everything up to the stage-2 operands (grid bands, phonons, window, stage 1,
 // packing, epilogue tables) and records the material's stage-2 launches with tile shapes
-// chosen by timing the candidates (autotuner).  Phase 2 captures every recorded launch of
-// every material into one CUDA graph, materials spread over parallel branches, and launches
-// it once.  Phase 3 averages degenerate bands and copies each material's outputs.
+// chosen by timing the candidates (autotuner); a pool of host threads plans several
+// materials at once, each on its material's stream, so that small materials, host-side
+// planning and synchronisations of one material overlap the kernels of others.  Phase 2
+// captures every recorded launch of every material into one CUDA graph, materials spread over
+// parallel branches, and launches it once.  Phase 3 averages degenerate bands and copies each material's outputs.
 #include <string.h>
 #include <time.h>
 
+#include <algorithm>
+#include <atomic>
+#include <thread>
 #include <vector>
 
 #include "pipeline.h"
@@ -40,6 +45,7 @@ extern "C" void phoebe_gpu_batch_opts_default(phoebe_gpu_batch_opts* o) {
   o->autotune = 1;
   o->n_streams = 4;
   o->g_chunk_bytes = (int64_t)128 << 20;
+  o->plan_threads = 8;
 }
 
 extern "C" int phoebe_gpu_linewidths_rta_batch(phoebe_gpu_batch_item* items, int n, phoebe_gpu_batch_opts* opts) {
@@ -48,11 +54,15 @@ extern "C" int phoebe_gpu_linewidths_rta_batch(phoebe_gpu_batch_item* items, int
   phoebe_gpu_batch_opts_default(&dflt);
   phoebe_gpu_batch_opts* o = opts ? opts : &dflt;
   if (o->n_streams < 1 || o->n_streams > 64 || o->g_chunk_bytes < ((int64_t)1 << 20)) return PHOEBE_GPU_ERR_ARG;
-  for (int i = 0; i < 4; ++i)
+  if (o->plan_threads < 0 || o->plan_threads > 64) return PHOEBE_GPU_ERR_ARG;
+  for (int i = 0; i < 3; ++i)
     if (o->reserved[i]) return PHOEBE_GPU_ERR_ARG;
   bool count_only = false;
   for (int i = 0; i < n; ++i) {
     if (!items[i].ctx || !items[i].params) return PHOEBE_GPU_ERR_ARG;
+    for (int j = 0; j < i; ++j)  // phase 1 plans materials concurrently: one context per item
+      if (items[j].ctx == items[i].ctx)
+        return fail(items[i].ctx, PHOEBE_GPU_ERR_ARG, "batch items %d and %d share a context", j, i);
     if (items[i].ctx->device != items[0].ctx->device) {
       return fail(items[i].ctx, PHOEBE_GPU_ERR_ARG, "batch item %d is on device %d, item 0 on device %d", i,
                   items[i].ctx->device, items[0].ctx->device);
@@ -78,20 +88,47 @@ extern "C" int phoebe_gpu_linewidths_rta_batch(phoebe_gpu_batch_item* items, int
   };
   double t0 = wall();
   std::vector<Deferred> D(n);
-  for (int i = 0; i < n; ++i) {
-    phoebe_gpu_ctx* c = items[i].ctx;
+  for (int i = 0; i < n; ++i)
     if (items[i].params->sampler != PHOEBE_SAMPLER_FULL)
-      return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "batched linewidths use the full q sum");
-    D[i].autotune = o->autotune != 0;
-    D[i].g_budget = o->g_chunk_bytes;
-    c->defer = &D[i];
-    int cap = items[i].n_states;
-    const int r = linewidths(c, items[i].params, &cap, nullptr, nullptr, items[i].gamma_eV, false);
-    c->defer = nullptr;
-    if (r != PHOEBE_GPU_OK) return r;
-    items[i].n_states = cap;
-    CK(c, cudaStreamSynchronize(c->stream));
+      return fail(items[i].ctx, PHOEBE_GPU_ERR_UNSUPPORTED, "batched linewidths use the full q sum");
+  std::atomic<int> next(0), first_err(PHOEBE_GPU_OK);
+  const int device = items[0].ctx->device;
+  auto plan = [&]() {
+    if (cudaSetDevice(device) != cudaSuccess) {
+      int ok = PHOEBE_GPU_OK;
+      first_err.compare_exchange_strong(ok, PHOEBE_GPU_ERR_CUDA);
+      return;
+    }
+    for (int i = next++; i < n && first_err.load() == PHOEBE_GPU_OK; i = next++) {
+      phoebe_gpu_ctx* c = items[i].ctx;
+      D[i].autotune = o->autotune != 0;
+      D[i].g_budget = o->g_chunk_bytes;
+      c->defer = &D[i];
+      int cap = items[i].n_states;
+      int r = linewidths(c, items[i].params, &cap, nullptr, nullptr, items[i].gamma_eV, false);
+      c->defer = nullptr;
+      if (r == PHOEBE_GPU_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        r = fail(c, PHOEBE_GPU_ERR_CUDA, "phase 1 of material %d failed on the device", i);
+      }
+      if (r != PHOEBE_GPU_OK) {
+        int ok = PHOEBE_GPU_OK;
+        first_err.compare_exchange_strong(ok, r);
+        return;
+      }
+      items[i].n_states = cap;
+    }
+  };
+  const int nthreads = std::max(1, std::min(o->plan_threads > 0 ? o->plan_threads : 8, n));
+  if (nthreads == 1) {
+    plan();
+  } else {
+    std::vector<std::thread> pool;
+    for (int w = 0; w < nthreads; ++w) pool.emplace_back(plan);
+    for (auto& th : pool) th.join();
   }
+  if (first_err.load() != PHOEBE_GPU_OK) return first_err.load();
+  if (cudaSetDevice(device) != cudaSuccess) return PHOEBE_GPU_ERR_CUDA;
   o->plan_ms = wall() - t0;
   // ---- phase 2: one graph holding every material's stage 2
   phoebe_gpu_ctx* c0 = items[0].ctx;

@@ -491,6 +491,10 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
         }
       }
       const unsigned bal = __ballot_sync(0xffffffffu, need != 0);
+      {  // listed (state, q, band) triples, for the flop count of the epilogue's rotations
+        const unsigned nb = __reduce_add_sync(0xffffffffu, (unsigned)__popc(need));
+        if (lane == 0 && nb) atomicAdd(a.nq_evaluated + 1, (unsigned long long)nb);
+      }
       if constexpr (NQ == 1) {
         int base = 0;
         if (lane == 0 && bal) base = atomicAdd(cn, __popc(bal));

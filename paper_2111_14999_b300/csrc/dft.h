@@ -88,7 +88,8 @@ struct DftXArgs {
   double scale;               // (2 pi / N_q) / (sqrt(pi) sigma)
   double* gamma;
   int64_t s_base;
-  unsigned long long* nq_evaluated;  // += the (state, q) pairs whose x sum was evaluated
+  unsigned long long* nq_evaluated;  // [0] += the (state, q) pairs whose x sum was evaluated,
+                                     // [1] += the listed (state, q, band) triples
   // phonon-electron rates (optional, nullptr = off): pacc[q][nu] += f(1-f)/kT of the state times
   // sum_m' |g_{m' n nu}(k,q)|^2 e^{-((eps_nk - eps_m'k+q - w_q nu)/sigma)^2}
   double* pacc;

@@ -264,6 +264,7 @@ __global__ void __launch_bounds__(256) k_dft_yx64(DftX64Args a) {
   __syncthreads();
   const double en = en_s;
   double acc = 0.0;  // lanes < nm: this lane's share of the Eq. 29 sum
+  unsigned nbands = 0;  // listed (q, band) pairs of this thread's listing
   const int R = (Ny + L - 1) / L;
   for (int r = 0; r < R; ++r) {
     const int jy0 = r * L, nl = min(L, Ny - jy0);
@@ -309,6 +310,7 @@ __global__ void __launch_bounds__(256) k_dft_yx64(DftX64Args a) {
       for (int mp = 0; mp < nw; ++mp)
         if (fabs(en - a.epsF[kq * nw + mp]) < a.reach) need |= 1u << mp;
       if (need) list[atomicAdd(cnt + (r & 1), 1)] = (int)(need << 16) | (l << 8) | jx;
+      nbands += __popc(need);
     }
     __syncthreads();
     const int total = cnt[r & 1];
@@ -373,6 +375,8 @@ __global__ void __launch_bounds__(256) k_dft_yx64(DftX64Args a) {
     __syncthreads();  // Y and the list are rewritten by the next run
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  nbands = __reduce_add_sync(0xffffffffu, nbands);
+  if (lane == 0 && nbands) atomicAdd(a.nq_evaluated + 1, (unsigned long long)nbands);
   if (lane == 0) red[warp] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {

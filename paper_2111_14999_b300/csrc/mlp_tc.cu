@@ -98,7 +98,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(MlpTcArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tslot;
-  const int64_t n_local = a.ntiles > blockIdx.x ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t nrows = a.rows ? (int64_t)*a.nrows : 0;  // row-list mode: the listed rows only
+  const int64_t ntiles = a.rows ? (nrows + 127) / 128 : a.ntiles;
+  const int64_t n_local = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
   if (warp == 8) {
     if (lane == 0) {
@@ -145,9 +147,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(MlpTcArgs a) {
     uint32_t dph = 0;
     for (int64_t i = g; i < n_local; i += 2) {
       const int64_t t = blockIdx.x + i * gridDim.x;
-      const int s = (int)(t / a.tiles_per_state);
-      const int64_t q = (t % a.tiles_per_state) * 128 + row;
-      const bool valid = q < a.Nq;
+      int s;
+      int64_t q;
+      bool valid;
+      if (a.rows) {
+        const int64_t r = t * 128 + row;
+        valid = r < nrows;
+        const int2 sq = valid ? a.rows[r] : make_int2(0, 0);
+        s = sq.x;
+        q = sq.y;
+      } else {
+        s = (int)(t / a.tiles_per_state);
+        q = (t % a.tiles_per_state) * 128 + row;
+        valid = q < a.Nq;
+      }
       float qv[3] = {0.f, 0.f, 0.f};
       if (valid)
 #pragma unroll

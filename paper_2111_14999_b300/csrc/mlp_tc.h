@@ -29,6 +29,11 @@ struct MlpTcArgs {
   int64_t ntiles;          // S * tiles_per_state
   float* z;                // [S][Nq] scores
   int* err;                // set to 1 if a bounded wait ran out
+  // optional row list: rows[r] = (state, q) for r < *nrows (device count); the kernel then walks
+  // ceil(*nrows / 128) tiles (ntiles is only the grid's upper bound) and writes z[state][q] of
+  // those rows alone
+  const int2* rows = nullptr;
+  const unsigned long long* nrows = nullptr;
 };
 
 size_t mlp_tc_smem_bytes();

@@ -167,7 +167,7 @@ static int check_params(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, GridM
     return fail(c, PHOEBE_GPU_ERR_ARG, "population_delta must be in [0, 0.25)");
   if (p->sampler_fp32_network != 0 && p->sampler_fp32_network != 1)
     return fail(c, PHOEBE_GPU_ERR_ARG, "sampler_fp32_network must be 0 or 1");
-  if (p->sampler < PHOEBE_SAMPLER_FULL || p->sampler > PHOEBE_SAMPLER_UNIFORM)
+  if (p->sampler < PHOEBE_SAMPLER_FULL || p->sampler > PHOEBE_SAMPLER_SHELL)
     return fail(c, PHOEBE_GPU_ERR_ARG, "unknown sampler %d", p->sampler);
   if (p->sampler != PHOEBE_SAMPLER_FULL) {
     if (!(p->sample_fraction > 0.0 && p->sample_fraction <= 1.0))

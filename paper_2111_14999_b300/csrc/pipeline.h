@@ -79,6 +79,7 @@ struct IsRequest {
   int mode = 0;             // 1: importance-sampled Gamma into the raw accumulator; 2: c_nk(q) of every q
   float* c_out = nullptr;   // mode 2: device [n_states][N_q]
   float* feat_out = nullptr;  // optional: device [n_states][4] (eps - mu, v)
+  float* lphi_out = nullptr;  // mode 2, optional: device [n_states][N_q] log of the shell factor
 };
 
 namespace phx {

@@ -3,14 +3,18 @@
 // q term of Eq. 29, so Gamma_nk = (1/N_q) sum_q c_nk(q).  Per initial k this file
 //   * scores every q for each active band with a small network z_nk(q) (7 -> 128 -> 128 ->
 //     128 -> 1, SiLU, BF16-rounded parameters, FP32 activations),
-//   * forms p_k(q) = (1 - alpha) mean_n softmax_q z_nk(q) + alpha / N_q and its FP64 running
-//     sum in q-index order,
+//   * weights every q by the shell factor phi_nk(q), the bracket of Eq. 29 with |g|^2 replaced by
+//     1/(hbar w_q nu) (zero exactly where every Gaussian of the q term is cut, so zero wherever
+//     c_nk(q) is), computed from the band and phonon tables alone,
+//   * forms p_k(q) = (1 - alpha) mean_n softmax_q (z_nk(q) + log phi_nk(q)) + alpha mean_n phi_nk(q) /
+//     sum_q phi_nk over the active bands with some phi > 0 (the shell proposal alone: phi / sum phi;
+//     the uniform proposal: 1/N_q) and its FP64 running sum in q-index order,
 //   * draws S q points i.i.d. by inverse CDF from Philox4x32-10 uniforms,
 //   * evaluates c_nk(q_j) at the drawn points only (R_p phase sum on the stage-1 output, band
 //     and mode rotations, Gaussian deltas) and accumulates (1/S) sum_j c/(N_q p).
 // It also trains the network: targets c_nk(q) / sum_q c_nk(q) from a full-grid run, loss the
-// per-state cross entropy against softmax_q z, gradients by hand-written backward kernels,
-// Adam updates.  All arithmetic runs in the kernels below; the host only orders them.
+// per-state cross entropy against softmax_q (z + log phi), gradients by hand-written backward
+// kernels, Adam updates.  All arithmetic runs in the kernels below; the host only orders them.
 #include <math.h>
 #include <string.h>
 
@@ -144,15 +148,23 @@ __global__ void k_head(const float* __restrict__ H3, const float* __restrict__ W
   if (lane == 0) z[r] = s + Wr[kOffB4];
 }
 
-// Targets of row r of group g: explicit per row, or c[state][q] of the training grid.
+// Targets of row r of group g: explicit per row, or c[state][q] of the training grid; the same for
+// the additive log prior of the softmax (log phi; none: 0).
 struct RowT {
   const float* t = nullptr;
   const float* c = nullptr;
+  const float* lp = nullptr;    // explicit prior per row
+  const float* lpc = nullptr;   // prior [state][q] of the training grid
   const int* states = nullptr;
   int64_t Nq = 1;
   __device__ __forceinline__ float get(int g, int64_t r, int64_t off_g) const {
     if (t) return t[r];
     return c[(int64_t)states[g] * Nq + (r - off_g)];
+  }
+  __device__ __forceinline__ float prior(int g, int64_t r, int64_t off_g) const {
+    if (lp) return lp[r];
+    if (lpc) return lpc[(int64_t)states[g] * Nq + (r - off_g)];
+    return 0.f;
   }
 };
 
@@ -178,7 +190,8 @@ __device__ __forceinline__ float block_reduce_max(float v, float* red) {
   return s;
 }
 
-// Per group: loss_g = lse(z) - sum t z / sum t, dz = (softmax(z) - t / sum t) * inv_G.
+// Per group, with y = z + prior (prior -inf where the target is 0): loss_g = lse(y) - sum t y / sum t
+// over the rows with t > 0, dz = (softmax(y) - t / sum t) * inv_G.
 __global__ void k_softmax_ce(const float* __restrict__ z, const int64_t* __restrict__ off, RowT T, float inv_G,
                              float* __restrict__ dz, double* __restrict__ loss) {
   __shared__ double redd[32];
@@ -186,14 +199,18 @@ __global__ void k_softmax_ce(const float* __restrict__ z, const int64_t* __restr
   const int g = blockIdx.x;
   const int64_t a = off[g], b = off[g + 1];
   float m = -INFINITY;
-  for (int64_t r = a + threadIdx.x; r < b; r += blockDim.x) m = fmaxf(m, z[r]);
+  for (int64_t r = a + threadIdx.x; r < b; r += blockDim.x) m = fmaxf(m, z[r] + T.prior(g, r, a));
   m = block_reduce_max(m, redf);
+  if (m == -INFINITY) {  // no row carries weight: nothing to learn from this group
+    for (int64_t r = a + threadIdx.x; r < b; r += blockDim.x) dz[r] = 0.f;
+    return;
+  }
   double se = 0.0, st = 0.0, stz = 0.0;
   for (int64_t r = a + threadIdx.x; r < b; r += blockDim.x) {
-    const float zr = z[r], tr = T.get(g, r, a);
-    se += (double)expf(zr - m);
+    const float yr = z[r] + T.prior(g, r, a), tr = T.get(g, r, a);
+    se += (double)expf(yr - m);
     st += (double)tr;
-    stz += (double)tr * (double)(zr - m);
+    if (tr > 0.f) stz += (double)tr * (double)(yr - m);
   }
   se = block_reduce_sum(se, redd);
   st = block_reduce_sum(st, redd);
@@ -206,7 +223,7 @@ __global__ void k_softmax_ce(const float* __restrict__ z, const int64_t* __restr
   const float lsef = (float)lse;
   const float inv_st = (float)(1.0 / st);
   for (int64_t r = a + threadIdx.x; r < b; r += blockDim.x)
-    dz[r] = (expf(z[r] - m - lsef) - T.get(g, r, a) * inv_st) * inv_G;
+    dz[r] = (expf(z[r] + T.prior(g, r, a) - m - lsef) - T.get(g, r, a) * inv_st) * inv_G;
   if (threadIdx.x == 0) atomicAdd(loss, (lse - stz / st) * (double)inv_G);
 }
 
@@ -438,40 +455,136 @@ __global__ void k_state_features(const int* __restrict__ st_k, const int* __rest
   }
 }
 
-// ------------------------------------------------------------------ proposal and draws
-// Per state: zmax = max_q z, zsum = sum_q expf(z - zmax) (FP64 sum).
-__global__ void k_logit_stats(const float* __restrict__ z, int64_t Nq, float* __restrict__ zmax,
-                              double* __restrict__ zsum) {
+// ------------------------------------------------------------------ shell factor, proposal and draws
+// lphi[s][q] = log phi_s(q), phi_s(q) = sum_{m'} sum_{nu: w >= omega_cut} [(n + 1 - f) D(e - w - e') +
+// (n + f) D(e + w - e')] / w with D(x) = exp(-x^2/sigma^2) for |x| < cut sigma (0 beyond), e = eps_nk,
+// e' = eps_m'k+q, f = f_m'k+q, (w, n) = (hbar w_q nu, n_q nu): the bracket of Eq. 29 with |g|^2 replaced by
+// 1/(hbar w).  Which terms are present is decided in FP64 as in Eq. 29's evaluation (a band with
+// |e - e'| >= reach = omega_max + cut sigma has none); the weights are summed in FP32 (phi is only a
+// proposal: its rounding changes the variance, never the expectation).  -inf where phi = 0.
+// Grid (q blocks, states).
+__global__ void k_shell_log(const int* __restrict__ st_k, const int* __restrict__ st_b, GridMap gm, int64_t Nq,
+                            const double* __restrict__ epsF, const double* __restrict__ fF,
+                            const double* __restrict__ omega, const double* __restrict__ nB, int nw, int nm,
+                            double omega_cut, double inv_sigma, double xcut, double reach, float* __restrict__ lphi) {
+  const int s = blockIdx.y;
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= Nq) return;
+  const int64_t k = st_k[s];
+  const double e = epsF[gm.k_to_fine(k) * nw + st_b[s]];
+  const int64_t kq = gm.kq_to_fine(k, q);
+  const float fis = (float)inv_sigma;
+  float phi = 0.f;
+  for (int mp = 0; mp < nw; ++mp) {
+    const double de = e - epsF[kq * nw + mp];
+    if (!(fabs(de) < reach)) continue;
+    const float f = (float)fF[kq * nw + mp];
+    for (int v = 0; v < nm; ++v) {
+      const double w = omega[q * nm + v];
+      if (!(w >= omega_cut)) continue;
+      const float n = (float)nB[q * nm + v];
+      const double x1 = de - w, x2 = de + w;
+      float d = 0.f;
+      if (fabs(x1) < xcut) {
+        const float t = (float)x1 * fis;
+        d = fmaf(n + 1.f - f, __expf(-t * t), d);
+      }
+      if (fabs(x2) < xcut) {
+        const float t = (float)x2 * fis;
+        d = fmaf(n + f, __expf(-t * t), d);
+      }
+      phi = fmaf(d, (float)(1.0 / w), phi);
+    }
+  }
+  lphi[(int64_t)s * Nq + q] = phi > 0.f ? logf(phi) : -INFINITY;
+}
+
+// The (state, q) rows with phi > 0 of S states, appended in chunks to rows[] (order across chunks
+// arbitrary); *nrows counts them.  One block per state.
+__global__ void k_shell_rows(const float* __restrict__ lphi, int64_t Nq, int2* __restrict__ rows,
+                             unsigned long long* __restrict__ nrows) {
+  __shared__ int wcount[32];
+  __shared__ unsigned long long base_s;
+  const int s = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int64_t c0 = 0; c0 < Nq; c0 += blockDim.x) {
+    const int64_t q = c0 + threadIdx.x;
+    const bool live = q < Nq && lphi[(int64_t)s * Nq + q] != -INFINITY;
+    const unsigned bal = __ballot_sync(0xffffffffu, live);
+    if (lane == 0) wcount[w] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int i = 0; i < nwarp; ++i) tot += wcount[i];
+      base_s = tot ? atomicAdd(nrows, (unsigned long long)tot) : 0ull;
+    }
+    __syncthreads();
+    if (live) {
+      int before = 0;
+      for (int i = 0; i < w; ++i) before += wcount[i];
+      rows[base_s + before + __popc(bal & ((1u << lane) - 1u))] = make_int2(s, (int)q);
+    }
+    __syncthreads();
+  }
+}
+
+// Per state: ymax = max_q y, ysum = sum_q expf(y - ymax) (FP64 sum) for y = z + lphi (z may be NULL:
+// y = lphi, or lphi NULL: y = z); ymax = -inf and ysum = 0 when every y is -inf.
+__global__ void k_logit_stats(const float* __restrict__ z, const float* __restrict__ lphi, int64_t Nq,
+                              float* __restrict__ ymax, double* __restrict__ ysum) {
   __shared__ double redd[32];
   __shared__ float redf[32];
   const int s = blockIdx.x;
-  const float* zs = z + (int64_t)s * Nq;
+  const float* zs = z ? z + (int64_t)s * Nq : nullptr;
+  const float* ls = lphi ? lphi + (int64_t)s * Nq : nullptr;
+  // where lphi is -inf the score is not read (the network may not have evaluated that q)
+  auto y = [&](int64_t q) -> float {
+    const float l = ls ? ls[q] : 0.f;
+    return l == -INFINITY ? -INFINITY : (zs ? zs[q] : 0.f) + l;
+  };
   float m = -INFINITY;
-  for (int64_t q = threadIdx.x; q < Nq; q += blockDim.x) m = fmaxf(m, zs[q]);
+  for (int64_t q = threadIdx.x; q < Nq; q += blockDim.x) m = fmaxf(m, y(q));
   m = block_reduce_max(m, redf);
   double a = 0.0;
-  for (int64_t q = threadIdx.x; q < Nq; q += blockDim.x) a += (double)expf(zs[q] - m);
+  if (m != -INFINITY)
+    for (int64_t q = threadIdx.x; q < Nq; q += blockDim.x) a += (double)expf(y(q) - m);
   a = block_reduce_sum(a, redd);
   if (threadIdx.x == 0) {
-    zmax[s] = m;
-    zsum[s] = a;
+    ymax[s] = m;
+    ysum[s] = a;
   }
 }
 
 struct Proposal {
-  const float* z = nullptr;       // [S][Nq] scores (NULL: uniform proposal)
-  const float* zmax = nullptr;    // [S]
-  const double* zsum = nullptr;   // [S]
+  int mode = PHOEBE_SAMPLER_UNIFORM;  // LEARNED, UNIFORM or SHELL
+  const float* z = nullptr;       // [S][Nq] network scores (LEARNED)
+  const float* lp = nullptr;      // [S][Nq] log phi (LEARNED, SHELL)
+  const float* zmax = nullptr;    // [S] stats of z + lp
+  const double* zsum = nullptr;
+  const float* pmax = nullptr;    // [S] stats of lp
+  const double* psum = nullptr;
   const int* kfirst = nullptr;    // [nkb + 1] first batch state of each batch k
   int64_t Nq = 1;
   double alpha = 1.0;
-  // p_k(q) = (1 - alpha) mean_{s of k} expf(z_s(q) - zmax_s) / zsum_s + alpha / N_q
+  // LEARNED: (1 - alpha) mean_s expf(z + lp - zmax_s) / zsum_s + alpha mean_s expf(lp - pmax_s) / psum_s,
+  // SHELL: mean_s expf(lp - pmax_s) / psum_s, both over the states of k with psum > 0 (some phi > 0);
+  // 1 / N_q when there is none, and for UNIFORM
   __device__ __forceinline__ double value(int kb, int64_t q) const {
-    if (!z) return 1.0 / (double)Nq;
+    if (mode == PHOEBE_SAMPLER_UNIFORM) return 1.0 / (double)Nq;
     const int s0 = kfirst[kb], s1 = kfirst[kb + 1];
-    double a = 0.0;
-    for (int s = s0; s < s1; ++s) a += (double)expf(z[(int64_t)s * Nq + q] - zmax[s]) / zsum[s];
-    return (1.0 - alpha) * a / (double)(s1 - s0) + alpha / (double)Nq;
+    double an = 0.0, as = 0.0;
+    int live = 0;
+    for (int s = s0; s < s1; ++s) {
+      if (!(psum[s] > 0.0)) continue;
+      ++live;
+      const float l = lp[(int64_t)s * Nq + q];
+      if (l == -INFINITY) continue;  // phi = 0: no weight (the score is not read)
+      as += (double)expf(l - pmax[s]) / psum[s];
+      if (mode == PHOEBE_SAMPLER_LEARNED) an += (double)expf(z[(int64_t)s * Nq + q] + l - zmax[s]) / zsum[s];
+    }
+    if (live == 0) return 1.0 / (double)Nq;
+    if (mode == PHOEBE_SAMPLER_SHELL) return as / (double)live;
+    return ((1.0 - alpha) * an + alpha * as) / (double)live;
   }
 };
 
@@ -790,9 +903,11 @@ static int mlp_backward(phoebe_gpu_ctx* c, const float* Wr, const RowX& X, int64
 }
 
 // Scores z[s][q] of S states over every q of a grid: tcgen05 kernel (FP16 operands, FP32
-// accumulation) or the CUDA-core forward pass (FP32 activations) in row chunks.
+// accumulation) or the CUDA-core forward pass (FP32 activations) in row chunks.  With a row list
+// (device rows[r] = (s, q), r < *nrows) the tensor-core kernel scores those rows only; the
+// CUDA-core pass scores every q regardless.
 static int network_scores(phoebe_gpu_ctx* c, const float* qt, const float* feat, int S, int64_t Nq, bool tensor_cores,
-                          float* z) {
+                          float* z, const int2* rows = nullptr, const unsigned long long* nrows = nullptr) {
   int st;
   float* Wr;
   TRY(round_params(c, &Wr));
@@ -825,6 +940,8 @@ static int network_scores(phoebe_gpu_ctx* c, const float* qt, const float* feat,
     ma.ntiles = (int64_t)S * ma.tiles_per_state;
     ma.z = z;
     ma.err = err;
+    ma.rows = rows;
+    ma.nrows = nrows;
     if (mlp_tc_launch(c->stream, c->num_sms, ma) != 0) {
       cudaGetLastError();
       return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the tensor-core network failed");
@@ -859,6 +976,7 @@ int is_batch(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& g
   const int S = b.S;
   int st;
   const bool learned = rq->mode == 1 && p->sampler == PHOEBE_SAMPLER_LEARNED;
+  const bool shell = rq->mode == 1 && (p->sampler == PHOEBE_SAMPLER_LEARNED || p->sampler == PHOEBE_SAMPLER_SHELL);
   Timer tm;
   tm.begin(c);
   // per-state features
@@ -911,6 +1029,18 @@ int is_batch(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& g
   a.pref = (float)(2.0 * kPi / (kSqrtPi * p->sigma_eV));
   a.s_base = b.s_base;
 
+  // log of the shell factor of every q for every state of the batch (proposal, or requested output)
+  float* lphi = nullptr;
+  if (shell || (rq->mode == 2 && rq->lphi_out)) {
+    lphi = rq->mode == 2 ? rq->lphi_out + b.s_base * Nq : (float*)ensure(c, "is_lphi", sizeof(float) * S * Nq, &st);
+    if (!lphi) return st;
+    dim3 g((unsigned)((Nq + 255) / 256), (unsigned)S);
+    const double xcut = p->delta_cut_sigmas * p->sigma_eV;
+    k_shell_log<<<g, 256, 0, c->stream>>>(b.st_k, b.st_b, gm, Nq, t.epsF, t.fF, t.omega, t.nB, NW, NM,
+                                          p->omega_cut_eV, 1.0 / p->sigma_eV, xcut,
+                                          (t.omega_max + xcut) * (1.0 + 1e-12), lphi);
+    TRY(launched(c, 1));
+  }
   if (rq->mode == 2) {
     a.draw_q = nullptr;
     a.draw_w = nullptr;
@@ -922,6 +1052,7 @@ int is_batch(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& g
     const int ndraw = (int)std::ceil(p->sample_fraction * (double)Nq - 1e-9);
     // scores of every q for every state of the batch
     Proposal P;
+    P.mode = p->sampler;
     P.Nq = Nq;
     P.alpha = learned ? p->mix_alpha : 1.0;
     std::vector<int> kfirst(b.nkb + 1, 0);
@@ -941,12 +1072,31 @@ int is_batch(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& g
       if (!qt) return st;
       k_wrapped_q<<<(unsigned)((Nq + 255) / 256), 256, 0, c->stream>>>(gm.nq[0], gm.nq[1], gm.nq[2], Nq, qt);
       TRY(launched(c, 1));
-      TRY(network_scores(c, qt, feat, S, Nq, c->cc >= 100 && !p->sampler_fp32_network, z));
-      k_logit_stats<<<S, 256, 0, c->stream>>>(z, Nq, zmax, zsum);
+      // the network runs on the rows with phi > 0 only (elsewhere the proposal is 0)
+      int2* rows = (int2*)ensure(c, "is_rows", sizeof(int2) * S * Nq, &st);
+      if (!rows) return st;
+      unsigned long long* nrows = (unsigned long long*)ensure(c, "is_nrows", 64, &st);
+      if (!nrows) return st;
+      CK(c, cudaMemsetAsync(nrows, 0, sizeof(unsigned long long), c->stream));
+      k_shell_rows<<<S, 1024, 0, c->stream>>>(lphi, Nq, rows, nrows);
+      TRY(launched(c, 1));
+      TRY(network_scores(c, qt, feat, S, Nq, c->cc >= 100 && !p->sampler_fp32_network, z, rows, nrows));
+      k_logit_stats<<<S, 256, 0, c->stream>>>(z, lphi, Nq, zmax, zsum);
       TRY(launched(c, 1));
       P.z = z;
       P.zmax = zmax;
       P.zsum = zsum;
+    }
+    if (shell) {
+      float* pmax = (float*)ensure(c, "is_pmax", sizeof(float) * S, &st);
+      if (!pmax) return st;
+      double* psum = (double*)ensure(c, "is_psum", sizeof(double) * S, &st);
+      if (!psum) return st;
+      k_logit_stats<<<S, 256, 0, c->stream>>>(nullptr, lphi, Nq, pmax, psum);
+      TRY(launched(c, 1));
+      P.lp = lphi;
+      P.pmax = pmax;
+      P.psum = psum;
     }
     double* cdf = (double*)ensure(c, "is_cdf", sizeof(double) * b.nkb * Nq, &st);
     if (!cdf) return st;
@@ -1006,10 +1156,12 @@ static int reset_optimiser(phoebe_gpu_ctx* c) {
   return PHOEBE_GPU_OK;
 }
 
-// Full-grid pass producing c_nk(q) and the features of every active state of `grid` into
-// device buffers "isc_c" [n][Nq] and "isc_feat" [n][4]; host copies of k and band.
+// Full-grid pass producing c_nk(q), the log shell factor and the features of every active state of
+// `grid` into device buffers "isc_c" [n][Nq], "isc_lphi" [n][Nq] and "isc_feat" [n][4]; host copies of
+// k and band.
 static int contributions_dev(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* grid, int* n_out,
-                             std::vector<int>* hk, std::vector<int>* hb, float** cdev, float** fdev) {
+                             std::vector<int>* hk, std::vector<int>* hb, float** cdev, float** fdev,
+                             float** ldev) {
   phoebe_gpu_rta_params p2 = *grid;
   p2.sampler = PHOEBE_SAMPLER_FULL;
   if (p2.precision == PHOEBE_PREC_FP64)
@@ -1023,6 +1175,8 @@ static int contributions_dev(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* gri
   if (!cd) return st;
   float* fd = (float*)ensure(c, "isc_feat", sizeof(float) * nn * 4, &st);
   if (!fd) return st;
+  float* ld = (float*)ensure(c, "isc_lphi", sizeof(float) * nn * Nq, &st);
+  if (!ld) return st;
   double* gd = (double*)ensure(c, "isc_gamma", sizeof(double) * nn, &st);
   if (!gd) return st;
   int* kd = (int*)ensure(c, "isc_k", sizeof(int) * nn, &st);
@@ -1034,6 +1188,7 @@ static int contributions_dev(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* gri
   req.mode = 2;
   req.c_out = cd;
   req.feat_out = fd;
+  req.lphi_out = ld;
   c->isreq = &req;
   int cap = n;
   const int r = linewidths(c, &p2, &cap, kd, bd, gd, true);
@@ -1049,6 +1204,7 @@ static int contributions_dev(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* gri
   *n_out = n;
   *cdev = cd;
   *fdev = fd;
+  *ldev = ld;
   return PHOEBE_GPU_OK;
 }
 
@@ -1155,8 +1311,8 @@ extern "C" int phoebe_gpu_sampler_train(phoebe_gpu_ctx* c, const phoebe_gpu_rta_
   if (!c->have_mlp) return fail(c, PHOEBE_GPU_ERR_ORDER, "sampler_train: call sampler_init or sampler_load first");
   int n = 0;
   std::vector<int> hk, hb;
-  float *cd, *fd;
-  TRY(contributions_dev(c, grid, &n, &hk, &hb, &cd, &fd));
+  float *cd, *fd, *ld;
+  TRY(contributions_dev(c, grid, &n, &hk, &hb, &cd, &fd, &ld));
   const int64_t Nq = (int64_t)grid->nq[0] * grid->nq[1] * grid->nq[2];
   int st;
   // states with a non-zero sum are the training set
@@ -1201,6 +1357,7 @@ extern "C" int phoebe_gpu_sampler_train(phoebe_gpu_ctx* c, const phoebe_gpu_rta_
       X.rows = (int64_t)G * Nq;
       RowT T;
       T.c = cd;
+      T.lpc = ld;
       T.states = (const int*)d_states;
       T.Nq = Nq;
       TRY(train_step(c, X, X.rows, (const int64_t*)d_off, G, T, loss_dev, o));
@@ -1215,7 +1372,8 @@ extern "C" int phoebe_gpu_sampler_train(phoebe_gpu_ctx* c, const phoebe_gpu_rta_
 }
 
 extern "C" int phoebe_gpu_q_contributions(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* params, int* n_states,
-                                          int32_t* k_index, int32_t* band, float* cq, float* features) {
+                                          int32_t* k_index, int32_t* band, float* cq, float* features,
+                                          float* log_shell) {
   if (!c) return PHOEBE_GPU_ERR_ARG;
   if (!n_states) return fail(c, PHOEBE_GPU_ERR_ARG, "n_states is NULL");
   if (!params) return fail(c, PHOEBE_GPU_ERR_ARG, "params is NULL");
@@ -1227,13 +1385,15 @@ extern "C" int phoebe_gpu_q_contributions(phoebe_gpu_ctx* c, const phoebe_gpu_rt
   const int cap = *n_states;
   int n = 0;
   std::vector<int> hk, hb;
-  float *cd, *fd;
-  TRY(contributions_dev(c, params, &n, &hk, &hb, &cd, &fd));
+  float *cd, *fd, *ld;
+  TRY(contributions_dev(c, params, &n, &hk, &hb, &cd, &fd, &ld));
   if (cap < n) return fail(c, PHOEBE_GPU_ERR_ARG, "output capacity %d is below the %d active states", cap, n);
   const int64_t Nq = (int64_t)params->nq[0] * params->nq[1] * params->nq[2];
   if (n > 0) {
     CK(c, cudaMemcpyAsync(cq, cd, sizeof(float) * (size_t)n * Nq, cudaMemcpyDeviceToHost, c->stream));
     if (features) CK(c, cudaMemcpyAsync(features, fd, sizeof(float) * n * 4, cudaMemcpyDeviceToHost, c->stream));
+    if (log_shell)
+      CK(c, cudaMemcpyAsync(log_shell, ld, sizeof(float) * (size_t)n * Nq, cudaMemcpyDeviceToHost, c->stream));
   }
   CK(c, cudaStreamSynchronize(c->stream));
   if (k_index) memcpy(k_index, hk.data(), sizeof(int) * n);
@@ -1243,8 +1403,8 @@ extern "C" int phoebe_gpu_q_contributions(phoebe_gpu_ctx* c, const phoebe_gpu_rt
 }
 
 extern "C" int phoebe_gpu_mlp_loss_grad(phoebe_gpu_ctx* c, int64_t n_rows, const float* x, int n_groups,
-                                        const int64_t* group_off, const float* target, float* logits, double* loss,
-                                        float* grad) {
+                                        const int64_t* group_off, const float* target, const float* log_prior,
+                                        float* logits, double* loss, float* grad) {
   if (!c) return PHOEBE_GPU_ERR_ARG;
   c->launches = 0;
   if (n_rows < 1 || !x || n_rows > kMaxRows) return fail(c, PHOEBE_GPU_ERR_ARG, "mlp_loss_grad: n_rows in 1..%lld",
@@ -1279,6 +1439,11 @@ extern "C" int phoebe_gpu_mlp_loss_grad(phoebe_gpu_ctx* c, int64_t n_rows, const
     CK(c, cudaMemsetAsync(loss_dev, 0, sizeof(double), c->stream));
     RowT T;
     T.t = (const float*)dt;
+    if (log_prior) {
+      void* dlp;
+      TRY(upload(c, "lg_lp", log_prior, sizeof(float) * n_rows, &dlp));
+      T.lp = (const float*)dlp;
+    }
     TRY(train_step(c, X, n_rows, (const int64_t*)doff, n_groups, T, loss_dev, nullptr));
     if (loss) CK(c, cudaMemcpyAsync(loss, loss_dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if (grad)

@@ -25,6 +25,7 @@ struct IsBatch {
 // FP32 tables of the epilogue (fine grid for electrons, q grid for phonons) and FP64 inputs.
 struct IsTables {
   const double* epsF = nullptr;   // [NF][nw]
+  const double* fF = nullptr;     // [NF][nw] Fermi-Dirac occupations
   const cplx* UF = nullptr;       // [NF][nw][nw]
   const float2* eps2 = nullptr;   // [NF][nw] (hi, lo)
   const float* f32 = nullptr;     // [NF][nw]

@@ -1141,13 +1141,14 @@ static int stage1_batch(phoebe_gpu_ctx* c, const GridMap& gm, const std::vector<
 template <int NW, int NM, int FMT, int NSPLIT, int NPROD>
 static int run_sampled(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& gm, int64_t ns,
                        const std::vector<int>& hk, const int* st_k, const int* st_b, const double* epsF,
-                       const cplx* UF, const double* omega, const double* nB, const cplx* Zq, double* raw,
-                       const float2* UH, const float* f32, const float2* eps2, double omega_max, const Parts& Pg,
-                       float sA1, const cplx* cis_k, const GridPhase& gk, int* err) {
+                       const double* fF, const cplx* UF, const double* omega, const double* nB, const cplx* Zq,
+                       double* raw, const float2* UH, const float* f32, const float2* eps2, double omega_max,
+                       const Parts& Pg, float sA1, const cplx* cis_k, const GridPhase& gk, int* err) {
   int st;
   Timer tm;
   IsTables it;
   it.epsF = epsF;
+  it.fF = fF;
   it.UF = UF;
   it.eps2 = eps2;
   it.f32 = f32;
@@ -1502,8 +1503,8 @@ static int run_tc_typed(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const
     double omega_max;
     memcpy(&omega_max, &ombits, sizeof(double));
     tm.end(c, &c->stats.stage1_ms);
-    return run_sampled<NW, NM, FMT, NSPLIT, NPROD>(c, p, gm, ns, hk, st_k, st_b, epsF, UF, omega, nB, Zq, raw, UH,
-                                                    f32, eps2, omega_max, Pg, sA1, cis_k, gk, err);
+    return run_sampled<NW, NM, FMT, NSPLIT, NPROD>(c, p, gm, ns, hk, st_k, st_b, epsF, fF, UF, omega, nB, Zq, raw,
+                                                    UH, f32, eps2, omega_max, Pg, sA1, cis_k, gk, err);
   }
   {
     const int shape[3] = {4, 4, 8};
@@ -2500,10 +2501,11 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
     i0 = i1;
   }
   int herr = 0;
-  unsigned long long n_x = 0;
+  unsigned long long n_xb[2] = {0, 0};
   CK(c, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  CK(c, cudaMemcpyAsync(&n_x, nq_eval, sizeof(n_x), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemcpyAsync(n_xb, nq_eval, sizeof(n_xb), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
+  const unsigned long long n_x = n_xb[0], n_b = n_xb[1];
   if (herr) return fail(c, PHOEBE_GPU_ERR_TIMEOUT, "a tensor-core pipeline wait ran out; results discarded");
   c->stats.pairs_executed = (int64_t)n_x;
   // complex MACs of the DFT: z sum over the entries, y sum over the pairs for every (jy, jz) line
@@ -2513,7 +2515,9 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
   // x sum: 4 FMA per complex value per residue pair or unpaired residue, 2 per real-factor residue
   double x_rows = 0.0;
   for (int k = 0; k < K; ++k) x_rows += xD[k] < 0 ? 0.5 : 1.0;
-  c->stats.stage2_flops = 8.0 * ((double)ns * zy_cmac + (double)n_x * x_rows * E);
+  // plus, per listed (state, q, band), the rotations U_{k+q}^dagger (nw x 3na complex MACs) and Z_q
+  // ((3na)^2); the Gaussians and occupations are not counted
+  c->stats.stage2_flops = 8.0 * ((double)ns * zy_cmac + (double)n_x * x_rows * E + (double)n_b * (E + nm * nm));
   return PHOEBE_GPU_OK;
 }
 

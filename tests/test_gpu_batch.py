@@ -75,3 +75,24 @@ def test_batch_rejects_fp64_and_reports_counts(batch):
     with pytest.raises(pg.PhoebeGPUError) as e:
         pg.binding.linewidths_rta_batch(jobs)
     assert e.value.status == -9
+
+
+def test_concurrent_planning_matches_one_thread(batch):
+    # phase 1 on several host threads (materials overlapping on the GPU) gives the results of
+    # planning one material after the other, to FP64 rounding of the atomic accumulation order
+    pg, mats, ctxs = batch
+    jobs = [(c, pg.make_params(prm, precision=5)) for c, (_, prm) in zip(ctxs, mats)]
+    r1, i1 = pg.binding.linewidths_rta_batch(jobs, autotune=0, plan_threads=1)
+    r8, i8 = pg.binding.linewidths_rta_batch(jobs, autotune=0, plan_threads=8)
+    assert i1["plan_threads"] == 1 and i8["plan_threads"] == 8
+    for (k1, b1, g1), (k8, b8, g8) in zip(r1, r8):
+        assert np.array_equal(k1, k8) and np.array_equal(b1, b8)
+        np.testing.assert_allclose(g8, g1, rtol=1e-12, atol=0)
+
+
+def test_batch_rejects_a_shared_context(batch):
+    pg, mats, ctxs = batch
+    jobs = [(ctxs[0], pg.make_params(mats[0][1], precision=5))] * 2
+    with pytest.raises(pg.PhoebeGPUError) as e:
+        pg.binding.linewidths_rta_batch(jobs, capacities=[10, 10])
+    assert e.value.status == -1

@@ -1,10 +1,12 @@
 """Learned q proposal on the GPU against the oracle (importance-sampled q sums of Eq. 29).
 
 Checks, each through the C ABI: the Philox draws (bit-exact), the network's logits, loss and
-gradient (1e-3 relative, the BF16-parameter / FP32-activation budget), the per-state features
-and the q-resolved terms c_nk(q) (split-FP16 contraction tolerance), and the sampled Gamma:
-draw for draw equal to the oracle's estimate with the same seed and parameters, and unbiased
-against the full q sum.
+gradient with and without the shell prior (1e-3 relative, the BF16-parameter / FP32-activation
+budget), the per-state features, the q-resolved terms c_nk(q) (split-FP16 contraction tolerance)
+and the shell factor, and the sampled Gamma of the learned, shell and uniform proposals: draw for
+draw equal to the oracle's estimate with the same seed and parameters, unbiased against the full
+q sum, and, trained on 20^3 and evaluated on 40^3 x 80^3, within 1% (L2 over the states) of the
+full sum at 5% of q.
 """
 import numpy as np
 import pytest
@@ -68,6 +70,19 @@ def test_network_logits_loss_gradient_vs_oracle(ctx):
     # logits only
     z2 = ctx.mlp_loss_grad(x[:130])
     assert np.max(np.abs(z2 - zo[:130])) <= 1e-3 * np.max(np.abs(zo))
+    # with an additive log prior (-inf where the target is 0)
+    lp = rng.normal(0, 2, n).astype(np.float32)
+    t2 = t.copy()
+    t2[::7] = 0.0
+    lp[::7] = -np.inf
+    z3, loss3, grad3 = ctx.mlp_loss_grad(x, off, t2, log_prior=lp)
+    lo3, go3, _ = S.loss_and_grad(blob, x.astype(np.float64), off, t2.astype(np.float64), lp.astype(np.float64))
+    assert np.isfinite(loss3) and loss3 == pytest.approx(lo3, rel=1e-3)
+    th_g, th_o = S.unpack(grad3), S.unpack(go3)
+    floor = 1e-6 * np.linalg.norm(go3)
+    for name, _ in S.SHAPES:
+        a, b = th_g[name].ravel(), th_o[name].ravel()
+        assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b) + floor, name
 
 
 @pytest.mark.parametrize("which", ["toy", "si_like"])
@@ -90,6 +105,13 @@ def test_features_and_q_terms_vs_oracle(ctx, which):
     assert np.max(np.abs(c - co)) <= C_RTOL * scale
     fo = S.state_features(mat, prm, ks, bs, table=tab)
     assert np.allclose(feat, fo, rtol=1e-5, atol=1e-6 * np.max(np.abs(fo)))
+    # the shell factor: the same zero pattern, log phi within FP32 rounding elsewhere
+    lp = ctx.q_contributions(prm, log_shell=True)[4]
+    lpo = S.log_shell(S.shell_factor(mat, prm, ks, bs, table=tab))
+    assert np.array_equal(np.isfinite(lp), np.isfinite(lpo)) and np.any(np.isfinite(lpo))
+    fin = np.isfinite(lpo)
+    assert np.max(np.abs(lp[fin] - lpo[fin])) <= 1e-5 * max(1.0, np.max(np.abs(lpo[fin])))
+    assert np.all(np.isfinite(lp)[c > 0])
     # the q terms average to the full-grid linewidth of the same precision (before degenerate averaging)
     st = ctx.linewidths_rta(prm)
     assert np.array_equal(st[0], ki)
@@ -98,8 +120,8 @@ def test_features_and_q_terms_vs_oracle(ctx, which):
     assert np.allclose(st[2][nondeg], raw[nondeg], rtol=1e-4)
 
 
-@pytest.mark.parametrize("uniform", [True, False])
-def test_sampled_gamma_equals_oracle_estimate(ctx, uniform):
+@pytest.mark.parametrize("mode", ["uniform", "learned", "shell"])
+def test_sampled_gamma_equals_oracle_estimate(ctx, mode):
     # same seed, same parameters: the same draws, so the estimates agree to the contraction tolerance
     mat, prm = W.toy(seed=0)
     kk = np.array([1, 22, 43, 130, 400])
@@ -107,10 +129,10 @@ def test_sampled_gamma_equals_oracle_estimate(ctx, uniform):
     ctx.set_material(mat)
     ctx.sampler_load(blob)
     frac, alpha, seed = 0.25, 0.1, 12345
-    prm2 = prm.with_(k_subset=kk, precision=PREC, sampler=2 if uniform else 1, sample_fraction=frac,
-                     mix_alpha=alpha, seed=seed, sampler_fp32_network=1)
+    prm2 = prm.with_(k_subset=kk, precision=PREC, sampler={"learned": 1, "uniform": 2, "shell": 3}[mode],
+                     sample_fraction=frac, mix_alpha=alpha, seed=seed, sampler_fp32_network=1)
     ki, bd, g = ctx.linewidths_rta(prm2)
-    ks, bs, go = S.linewidths_is(mat, prm, blob, frac, alpha, seed, k_indices=kk, uniform=uniform)
+    ks, bs, go = S.linewidths_is(mat, prm, blob, frac, alpha, seed, k_indices=kk, mode=mode)
     assert np.array_equal(ki, ks) and np.array_equal(bd, bs)
     rel = np.abs(g - go) / np.maximum(np.abs(go), 1e-6 * np.max(np.abs(go)))
     # a draw may differ where a uniform falls within rounding of a CDF step (FP32 vs FP64 network)
@@ -145,7 +167,7 @@ def test_sampled_gamma_is_unbiased(ctx):
     ctx.sampler_load(_blob(5, scale=3.0))
     base = prm.with_(k_subset=kk, precision=PREC)
     _, _, full = ctx.linewidths_rta(base)
-    for sampler in (1, 2):
+    for sampler in (1, 2, 3):
         runs = np.array([ctx.linewidths_rta(base.with_(sampler=sampler, sample_fraction=0.1, seed=s))[2]
                          for s in range(48)])
         mean, se = runs.mean(0), runs.std(0, ddof=1) / np.sqrt(len(runs))
@@ -168,23 +190,26 @@ def test_sampler_argument_errors(ctx):
     assert e.value.status == -1
 
 
-def test_trained_proposal_beats_uniform_sampling(ctx):
+def test_trained_proposal_meets_the_one_percent_gate(ctx):
     # trained on the q terms of a 20^3 full-grid run, evaluated on the 40^3 k x 80^3 q grid
-    # (a seeded subset of k): at 5% of q the learned proposal's squared error is several times
-    # below the uniform proposal's (the method without the network)
+    # (a seeded subset of k): at 5% of q the learned proposal's relative L2 error over the states is
+    # at most 1% for every seed, and its squared error is far below the uniform proposal's (the
+    # method without the network or the shell factor)
     mat20, p20 = W.si_like(seed=0, nk=20)
     ctx.set_material(mat20)
     ctx.sampler_init(1)
     loss = ctx.sampler_train(p20.with_(precision=PREC), epochs=20, states_per_step=64, lr=3e-3, seed=3)
-    assert loss[-1] < loss[0] < np.log(20 ** 3) + 0.5
+    assert loss[-1] < loss[0]
     mat, prm = W.si_like(seed=0, nk=40, nq=80)
     kk = np.sort(np.random.default_rng(0).choice(64000, 120, replace=False))
     pe = prm.with_(precision=PREC, k_subset=kk)
     ctx.set_material(mat)
     _, _, full = ctx.linewidths_rta(pe)
     err = {}
-    for sampler in (1, 2):
-        e = [np.linalg.norm(ctx.linewidths_rta(pe.with_(sampler=sampler, sample_fraction=0.05, seed=s))[2] - full)
-             for s in range(4)]
-        err[sampler] = np.mean(np.square(e)) / np.sum(full ** 2)
-    assert err[2] > 4 * err[1], err
+    for sampler in (1, 2, 3):
+        err[sampler] = np.array([np.linalg.norm(ctx.linewidths_rta(pe.with_(sampler=sampler, sample_fraction=0.05,
+                                                                            seed=s))[2] - full)
+                                 for s in range(4)]) / np.linalg.norm(full)
+    print("relative L2 errors at 5% of q: learned", err[1], "shell", err[3], "uniform", err[2])
+    assert np.max(err[1]) <= 0.01, err
+    assert np.mean(err[2] ** 2) > 100 * np.mean(err[1] ** 2), err
