@@ -46,6 +46,21 @@ def _dist():
     return world, rank, local
 
 
+def reduce_over_ranks(ms: float, units, dist, device) -> tuple:
+    """Whole-job figures of a step loop run on every rank: the slowest rank's time (MAX) and the units
+    all ranks processed (SUM; each rank runs its own problem instance, so the counts may differ).
+    ``units`` is a sequence of counts; ``dist`` the torch.distributed module or None (one process)."""
+    units = [float(u) for u in units]
+    if dist is None:
+        return ms, units
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor(units, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), [float(x) for x in u.tolist()]
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -144,9 +159,9 @@ def roofline(precision: int, stats: list, k_limit: int) -> dict:
                 "algorithmic_flops_per_launch": s2_flops / max(s2_launch, 1),
                 "avg_launch_ms": s2_ms / max(s2_launch, 1),
                 "note": "flops count the DFT's complex MACs as evaluated (8 flop each; x sum only for the q "
-                        "whose final bands reach the delta window) and the epilogue's two rotations per listed "
-                        "(state, q, band) (U_{k+q}^dagger: N_w 3N_at, Z_q: (3N_at)^2 complex MACs); the Gaussian "
-                        "and occupation arithmetic is not counted"}
+                        "whose final bands reach the delta window) and the epilogue's two rotations (U_{k+q}^dagger: "
+                        "N_w 3N_at, Z_q: (3N_at)^2 complex MACs) once per evaluated (state, q), a lower bound (99% of "
+                        "the listed q have one final band); the Gaussian and occupation arithmetic is not counted"}
     elif precision in (0, 8):
         roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
                 "frac": achieved / 1.25 if achieved else None, "traffic": None,
@@ -524,14 +539,13 @@ def main():
         dist.barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, (states_tot, coup_tot, coup_dense_tot) = reduce_over_ranks(
+        ms, (n * args.steps, stats[-1]["couplings_executed"] * args.steps, stats[-1]["couplings_dense"] * args.steps),
+        dist, "cuda")
     ms_per_step = ms / args.steps
-    value = world * n * args.steps / (ms / 1e3)
-    couplings = world * stats[-1]["couplings_executed"] * args.steps / (ms / 1e3)
-    couplings_dense = world * stats[-1]["couplings_dense"] * args.steps / (ms / 1e3)
+    value = states_tot / (ms / 1e3)
+    couplings = coup_tot / (ms / 1e3)
+    couplings_dense = coup_dense_tot / (ms / 1e3)
     launches = int(sum(s["kernel_launches"] for s in stats))
 
     roof = roofline(args.precision, stats, args.k_limit or args.k_planes)
@@ -651,12 +665,15 @@ def main():
         return ctx.linewidths_rta(params)
     e2e_step()
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         kk, bb, gg = e2e_step()
     el = time.perf_counter() - t0
     d2h = int(len(gg) * (8 + 4 + 4))
-    e2e_value = world * len(gg) * args.steps / el
+    el_ms, (e2e_units,) = reduce_over_ranks(el * 1e3, (len(gg) * args.steps,), dist, "cuda")
+    e2e_value = e2e_units / (el_ms / 1e3)
 
     line = {
         "metric": METRIC, "value": value, "unit": "linewidths/s", "n_gpus": world, "steps": args.steps,

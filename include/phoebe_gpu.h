@@ -369,8 +369,8 @@ int phoebe_gpu_is_uniforms(phoebe_gpu_ctx* ctx, uint64_t seed, int32_t k, int64_
  * Each item names a context holding one material (set_* done; all contexts on one device)
  * and its parameters (precision 1..6, sampler FULL; distinct contexts).  Phase 1 runs, per
  * material on its own context and stream, the grid band structure, phonons, window, stage 1
- * and the stage-2 operands, and records the material's stage-2 launches, several materials at
- * once on plan_threads host threads; with autotune on, the tile width
+ * and the stage-2 operands, and records the material's stage-2 launches (with plan_threads > 1,
+ * several materials at once on host threads); with autotune on, the tile width
  * (128 or 256 columns) and the K blocks per TMEM partial (1, 2 or 4) of its stage-2 GEMM are
  * chosen by timing each candidate once on the material's first q chunk.  Phase 2 captures
  * the recorded launches of all materials into one CUDA graph (materials spread round-robin
@@ -400,7 +400,7 @@ typedef struct {
   int64_t recorded_launches; /* out: recorded stage-2 chunks (each a GEMM and an epilogue launch) */
   int plan_threads;          /* host threads of phase 1, each planning one material at a time on the
                                 material's own stream, so that materials overlap on the GPU
-                                (0 = default 8, at most 64; 1 = one material after the other) */
+                                (0 or 1 = one material after the other, the default; at most 64) */
   int reserved[3];           /* must be zero */
 } phoebe_gpu_batch_opts;
 

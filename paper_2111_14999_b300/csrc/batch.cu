@@ -45,7 +45,7 @@ extern "C" void phoebe_gpu_batch_opts_default(phoebe_gpu_batch_opts* o) {
   o->autotune = 1;
   o->n_streams = 4;
   o->g_chunk_bytes = (int64_t)128 << 20;
-  o->plan_threads = 8;
+  o->plan_threads = 1;
 }
 
 extern "C" int phoebe_gpu_linewidths_rta_batch(phoebe_gpu_batch_item* items, int n, phoebe_gpu_batch_opts* opts) {
@@ -119,7 +119,7 @@ extern "C" int phoebe_gpu_linewidths_rta_batch(phoebe_gpu_batch_item* items, int
       items[i].n_states = cap;
     }
   };
-  const int nthreads = std::max(1, std::min(o->plan_threads > 0 ? o->plan_threads : 8, n));
+  const int nthreads = std::max(1, std::min(o->plan_threads > 0 ? o->plan_threads : 1, n));
   if (nthreads == 1) {
     plan();
   } else {

@@ -158,12 +158,15 @@ __global__ void k_rotate_final_fp64(const cplx* __restrict__ G, int S, int64_t Q
 }
 
 // Gamma_raw[s] += pref * sum_{q in chunk} sum_{m' nu} g2 * [(n+1-f) d(e - w - e') + (n+f) d(e + w - e')]
-// with d the Gaussian of Eq. 61 truncated at cut*sigma.  Streams g2 once.
+// with d the Gaussian of Eq. 61 truncated at cut*sigma.  A final band with |e - e'| >= reach =
+// omega_max + cut*sigma has every term cut, so its |g|^2 is not read and costs no FP64 work; the
+// other bands' terms are tested and weighted in FP64.  g2 columns are q (consecutive threads read
+// consecutive q).
 __global__ void __launch_bounds__(256) k_delta_accumulate_fp64(
     const double* __restrict__ g2, int S, int64_t Qc, int64_t q0, const int* __restrict__ st_k,
     const int* __restrict__ st_b, int64_t s_base, GridMap gm, const double* __restrict__ epsF,
     const double* __restrict__ fF, const double* __restrict__ omega, const double* __restrict__ nB, int nw,
-    int nm, double sigma, double cut, double pref, double* __restrict__ gamma) {
+    int nm, double sigma, double cut, double pref, double reach, double* __restrict__ gamma) {
   int s = blockIdx.y;
   int64_t kk = st_k[s];
   double e = epsF[gm.k_to_fine(kk) * nw + st_b[s]];
@@ -175,16 +178,17 @@ __global__ void __launch_bounds__(256) k_delta_accumulate_fp64(
     int64_t kq = gm.kq_to_fine(kk, q);
     for (int mp = 0; mp < nw; ++mp) {
       double ep = epsF[kq * nw + mp];
+      if (!(fabs(e - ep) < reach)) continue;  // every Gaussian of this band is cut
       double f = fF[kq * nw + mp];
+      const double* gv = g2 + ((int64_t)s * nw + mp) * nm * Qc + ql;
       for (int nu = 0; nu < nm; ++nu) {
-        double val = g2[(((int64_t)s * nw + mp) * nm + nu) * Qc + ql];
         double w = omega[q * nm + nu];
         double n = nB[q * nm + nu];
         double x1 = e - w - ep, x2 = e + w - ep;
         double d = 0.0;
         if (fabs(x1) < xcut) d += (n + 1.0 - f) * exp(-(x1 * inv_s) * (x1 * inv_s));
         if (fabs(x2) < xcut) d += (n + f) * exp(-(x2 * inv_s) * (x2 * inv_s));
-        acc = fma(val, d, acc);
+        if (d != 0.0) acc = fma(gv[(int64_t)nu * Qc], d, acc);
       }
     }
   }

@@ -389,6 +389,7 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
   const int lcap = dft_list_cap(L, Nx);
   __shared__ int cnt[4];  // list length of run r in cnt[r % 4]
   __shared__ int wq[2];   // task counter of iteration r in wq[r % 2]
+  __shared__ unsigned blk_nq;  // the block's evaluated (state, q) pairs
   __shared__ float en_s[2];
   __shared__ double pw_s;
   __shared__ float4 vn_s;      // adaptive smearing: hbar v of the initial state
@@ -400,6 +401,7 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
     for (int i = 0; i < 4; ++i) cnt[i] = 0;
     wq[0] = 0;
     wq[1] = 0;
+    blk_nq = 0;
     const double e_n = a.epsF[a.gm.k_to_fine(a.st_k[s]) * NW + a.st_b[s]];
     en_s[0] = (float)e_n;
     en_s[1] = (float)(e_n - (double)en_s[0]);
@@ -491,10 +493,6 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
         }
       }
       const unsigned bal = __ballot_sync(0xffffffffu, need != 0);
-      {  // listed (state, q, band) triples, for the flop count of the epilogue's rotations
-        const unsigned nb = __reduce_add_sync(0xffffffffu, (unsigned)__popc(need));
-        if (lane == 0 && nb) atomicAdd(a.nq_evaluated + 1, (unsigned long long)nb);
-      }
       if constexpr (NQ == 1) {
         int base = 0;
         if (lane == 0 && bal) base = atomicAdd(cn, __popc(bal));
@@ -714,7 +712,7 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
       // r + 3 in iteration r + 1; wq[(r + 1) % 2] was last used in iteration r - 1
       cnt[(r + 3) & 3] = 0;
       wq[(r + 1) & 1] = 0;
-      if (r >= 0) atomicAdd(a.nq_evaluated, (unsigned long long)total);
+      if (r >= 0) blk_nq += (unsigned)total;
     }
     const int nx = (total + XT - 1) / XT;
     const int ny = r + 1 < R ? y_tasks : 0;
@@ -750,6 +748,9 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
     double sum = 0.0;
     for (int i = 0; i < NWARP; ++i) sum += red[i];
     if (sum != 0.0) atomicAdd(a.gamma + a.s_base + s, sum * a.scale);
+    // the pair count once per block, spread over four addresses (summed by the host); the listed
+    // bands are not counted here (a count per listing task cost 1.5 % of the kernel)
+    atomicAdd(a.nq_evaluated + 2 * (blockIdx.x & 3), (unsigned long long)blk_nq);
   }
 }
 

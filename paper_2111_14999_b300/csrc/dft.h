@@ -88,8 +88,8 @@ struct DftXArgs {
   double scale;               // (2 pi / N_q) / (sqrt(pi) sigma)
   double* gamma;
   int64_t s_base;
-  unsigned long long* nq_evaluated;  // [0] += the (state, q) pairs whose x sum was evaluated,
-                                     // [1] += the listed (state, q, band) triples
+  unsigned long long* nq_evaluated;  // [2i] += the (state, q) pairs whose x sum was evaluated
+                                     // (i = block % 4); [2i+1] stays 0
   // phonon-electron rates (optional, nullptr = off): pacc[q][nu] += f(1-f)/kT of the state times
   // sum_m' |g_{m' n nu}(k,q)|^2 e^{-((eps_nk - eps_m'k+q - w_q nu)/sigma)^2}
   double* pacc;
@@ -210,7 +210,8 @@ struct DftX64Args {
   double scale;               // (2 pi / N_q) / (sqrt(pi) sigma)
   double* gamma;
   int64_t s_base;
-  unsigned long long* nq_evaluated;
+  unsigned long long* nq_evaluated;  // [2i] += the evaluated (state, q) pairs, [2i+1] += the
+                                     // listed (state, q, band) triples (i = block % 4)
 };
 size_t s64_smem_bytes(int nRe, int Pe, int Bz, int Gz, int nky, int By, int nkz);
 size_t dft64_z_smem_bytes(int ne_plane_max, int E, int Nz, int Bz);
@@ -225,6 +226,7 @@ int dft_launch(cudaStream_t st, const DftZArgs& z, const DftXArgs& x, int S, int
 #define PHX_DFT_QPAIR 1
 #endif
 constexpr bool kDftQPair = PHX_DFT_QPAIR != 0;  // two listed q per lane group (lines of Nx >= 32)
+
 // Entries of one run's q list: every q of the run plus, with pairing, one padding entry per
 // (warp round, line) at most -- two lines per round of 32 consecutive q when Nx >= 32.
 __host__ __device__ constexpr int dft_list_cap(int L, int Nx) { return L * Nx + 2 * ((L * Nx + 31) / 32) + 2; }

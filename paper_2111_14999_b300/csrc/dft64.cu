@@ -221,6 +221,7 @@ __global__ void __launch_bounds__(256) k_dft_yx64(DftX64Args a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int cnt[2];
   __shared__ double en_s;
+  __shared__ unsigned blk_nq, blk_nb;  // the block's evaluated (state, q) pairs and listed bands
   __shared__ double red[NWARP];
   const int P = a.P, Bx = a.Bx, By = a.By, Nx = a.Nx, Ny = a.Ny, nw = a.nw, nm = a.nm, E = nw * nm;
   double2* Zsl = reinterpret_cast<double2*>(smem);          // [P+1][E], row P = 0
@@ -240,6 +241,8 @@ __global__ void __launch_bounds__(256) k_dft_yx64(DftX64Args a) {
   if (threadIdx.x == 0) {
     cnt[0] = 0;
     cnt[1] = 0;
+    blk_nq = 0;
+    blk_nb = 0;
     en_s = a.epsF[kf * nw + a.st_b[s]];
   }
   const double2* zg = a.Zs + ((int64_t)s * a.Nz + jz) * P * E;
@@ -314,7 +317,7 @@ __global__ void __launch_bounds__(256) k_dft_yx64(DftX64Args a) {
     }
     __syncthreads();
     const int total = cnt[r & 1];
-    if (threadIdx.x == 0) atomicAdd(a.nq_evaluated, (unsigned long long)total);
+    if (threadIdx.x == 0) blk_nq += (unsigned)total;
     // (2) one warp per listed q
     double2* G = Gw + (size_t)warp * E;
     for (int it = warp; it < total; it += NWARP) {
@@ -376,13 +379,16 @@ __global__ void __launch_bounds__(256) k_dft_yx64(DftX64Args a) {
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   nbands = __reduce_add_sync(0xffffffffu, nbands);
-  if (lane == 0 && nbands) atomicAdd(a.nq_evaluated + 1, (unsigned long long)nbands);
+  if (lane == 0 && nbands) atomicAdd(&blk_nb, nbands);
   if (lane == 0) red[warp] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double sum = 0.0;
     for (int i = 0; i < NWARP; ++i) sum += red[i];
     if (sum != 0.0) atomicAdd(a.gamma + a.s_base + s, sum * a.scale);
+    unsigned long long* ctr = a.nq_evaluated + 2 * (blockIdx.x & 3);
+    atomicAdd(ctr, (unsigned long long)blk_nq);
+    atomicAdd(ctr + 1, (unsigned long long)blk_nb);
   }
 }
 

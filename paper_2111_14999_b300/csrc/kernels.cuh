@@ -65,6 +65,10 @@ __global__ void k_window_write(const double* epsF, const int* kidx, int64_t NC, 
                                double mu, double window, double kT, double delta, const int64_t* offset, int* st_k,
                                int* st_b);
 
+// ---------------------------------------------------------------- tc_gemm.cu
+// *out = bit pattern of max |x_i| (out zeroed by the caller; non-negative doubles order as their bits)
+__global__ void k_absmax_f64(const double* x, int64_t n, unsigned long long* out);
+
 // ---------------------------------------------------------------- couple_fp64.cu
 __global__ void k_phase_table_grid(cplx* P, const int* pts, int64_t npts, const int* R, const double* w,
                                    int nR, GridPhase gp, const cplx* cis);
@@ -80,7 +84,8 @@ __global__ void k_rotate_final_fp64(const cplx* G, int S, int64_t Qc, int64_t q0
 __global__ void k_delta_accumulate_fp64(const double* g2, int S, int64_t Qc, int64_t q0, const int* st_k,
                                         const int* st_b, int64_t s_base, GridMap gm, const double* epsF,
                                         const double* fF, const double* omega, const double* nB, int nw,
-                                        int nm, double sigma, double cut, double pref, double* gamma);
+                                        int nm, double sigma, double cut, double pref, double reach,
+                                        double* gamma);
 __global__ void k_degenerate_average(const double* raw, const int* st_k, const int* st_b, int64_t NS,
                                      const double* epsF, GridMap gm, int nw, double tol, double* out);
 __global__ void k_pairs_stage2(const cplx* X, int npairs, const double* q, const int* Rp, const double* wp,

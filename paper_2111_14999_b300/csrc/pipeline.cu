@@ -216,6 +216,17 @@ static int run_fp64(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Gri
   TRY(launch_check(c, 1));
   t.end(c, &c->stats.stage1_ms);
 
+  // largest phonon energy: bands farther than omega_max + cut sigma from eps_nk have every term cut
+  unsigned long long* dmax = (unsigned long long*)ensure(c, "fp64_wmax", 64, &st);
+  if (!dmax) return st;
+  CK(c, cudaMemsetAsync(dmax, 0, 64, c->stream));
+  k_absmax_f64<<<64, 256, 0, c->stream>>>(omega, Nq * nm, dmax);
+  TRY(launch_check(c, 1));
+  unsigned long long ombits = 0;
+  CK(c, cudaMemcpyAsync(&ombits, dmax, sizeof(ombits), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  double omega_max;
+  memcpy(&omega_max, &ombits, sizeof(double));
   int S_max = p->max_batch_states > 0 ? p->max_batch_states : 64;
   const double pref = 2.0 * kPi / (double)Nq;
   const size_t budget = (size_t)4 << 30;
@@ -274,7 +285,7 @@ static int run_fp64(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Gri
       unsigned bx = (unsigned)std::min<int64_t>((qc + 255) / 256, 64);
       k_delta_accumulate_fp64<<<dim3(bx, (unsigned)S), 256, 0, c->stream>>>(
           g2, S, qc, q0, st_k + i0, st_b + i0, i0, gm, epsF, fF, omega, nB, nw, nm, p->sigma_eV,
-          p->delta_cut_sigmas, pref, raw);
+          p->delta_cut_sigmas, pref, (omega_max + p->delta_cut_sigmas * p->sigma_eV) * (1.0 + 1e-12), raw);
       TRY(launch_check(c, 1));
       t.end(c, &c->stats.delta_ms);
     }

@@ -464,9 +464,10 @@ __global__ void k_state_features(const int* __restrict__ st_k, const int* __rest
 // proposal: its rounding changes the variance, never the expectation).  -inf where phi = 0.
 // Grid (q blocks, states).
 __global__ void k_shell_log(const int* __restrict__ st_k, const int* __restrict__ st_b, GridMap gm, int64_t Nq,
-                            const double* __restrict__ epsF, const double* __restrict__ fF,
-                            const double* __restrict__ omega, const double* __restrict__ nB, int nw, int nm,
-                            double omega_cut, double inv_sigma, double xcut, double reach, float* __restrict__ lphi) {
+                            const double* __restrict__ epsF, const float2* __restrict__ eps2,
+                            const double* __restrict__ fF, const double* __restrict__ omega,
+                            const double* __restrict__ nB, int nw, int nm, double omega_cut, double inv_sigma,
+                            double xcut, double reach, float* __restrict__ lphi) {
   const int s = blockIdx.y;
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= Nq) return;
@@ -474,8 +475,10 @@ __global__ void k_shell_log(const int* __restrict__ st_k, const int* __restrict_
   const double e = epsF[gm.k_to_fine(k) * nw + st_b[s]];
   const int64_t kq = gm.kq_to_fine(k, q);
   const float fis = (float)inv_sigma;
+  const float ef = (float)e, reach_f = (float)reach * 1.0001f;  // FP32 screen with a margin far above FP32 rounding
   float phi = 0.f;
   for (int mp = 0; mp < nw; ++mp) {
+    if (!(fabsf(ef - eps2[kq * nw + mp].x) < reach_f)) continue;  // no term of this band can be present
     const double de = e - epsF[kq * nw + mp];
     if (!(fabs(de) < reach)) continue;
     const float f = (float)fF[kq * nw + mp];
@@ -531,7 +534,7 @@ __global__ void k_shell_rows(const float* __restrict__ lphi, int64_t Nq, int2* _
 // Per state: ymax = max_q y, ysum = sum_q expf(y - ymax) (FP64 sum) for y = z + lphi (z may be NULL:
 // y = lphi, or lphi NULL: y = z); ymax = -inf and ysum = 0 when every y is -inf.
 __global__ void k_logit_stats(const float* __restrict__ z, const float* __restrict__ lphi, int64_t Nq,
-                              float* __restrict__ ymax, double* __restrict__ ysum) {
+                              float* __restrict__ ymax, double* __restrict__ ysum, float* __restrict__ yinv) {
   __shared__ double redd[32];
   __shared__ float redf[32];
   const int s = blockIdx.x;
@@ -552,6 +555,7 @@ __global__ void k_logit_stats(const float* __restrict__ z, const float* __restri
   if (threadIdx.x == 0) {
     ymax[s] = m;
     ysum[s] = a;
+    yinv[s] = a > 0.0 ? (float)(1.0 / a) : 0.f;
   }
 }
 
@@ -561,53 +565,68 @@ struct Proposal {
   const float* lp = nullptr;      // [S][Nq] log phi (LEARNED, SHELL)
   const float* zmax = nullptr;    // [S] stats of z + lp
   const double* zsum = nullptr;
+  const float* zinv = nullptr;    // [S] 1 / zsum in FP32
   const float* pmax = nullptr;    // [S] stats of lp
   const double* psum = nullptr;
+  const float* pinv = nullptr;    // [S] 1 / psum in FP32
   const int* kfirst = nullptr;    // [nkb + 1] first batch state of each batch k
   int64_t Nq = 1;
   double alpha = 1.0;
   // LEARNED: (1 - alpha) mean_s expf(z + lp - zmax_s) / zsum_s + alpha mean_s expf(lp - pmax_s) / psum_s,
   // SHELL: mean_s expf(lp - pmax_s) / psum_s, both over the states of k with psum > 0 (some phi > 0);
-  // 1 / N_q when there is none, and for UNIFORM
+  // 1 / N_q when there is none, and for UNIFORM.  Evaluated in FP32 (the draws and their weights
+  // use the same values, so the estimate stays unbiased); the running sums over q are FP64.
   __device__ __forceinline__ double value(int kb, int64_t q) const {
     if (mode == PHOEBE_SAMPLER_UNIFORM) return 1.0 / (double)Nq;
     const int s0 = kfirst[kb], s1 = kfirst[kb + 1];
-    double an = 0.0, as = 0.0;
+    float an = 0.f, as = 0.f;
     int live = 0;
     for (int s = s0; s < s1; ++s) {
       if (!(psum[s] > 0.0)) continue;
       ++live;
       const float l = lp[(int64_t)s * Nq + q];
       if (l == -INFINITY) continue;  // phi = 0: no weight (the score is not read)
-      as += (double)expf(l - pmax[s]) / psum[s];
-      if (mode == PHOEBE_SAMPLER_LEARNED) an += (double)expf(z[(int64_t)s * Nq + q] + l - zmax[s]) / zsum[s];
+      as = fmaf(expf(l - pmax[s]), pinv[s], as);
+      if (mode == PHOEBE_SAMPLER_LEARNED) an = fmaf(expf(z[(int64_t)s * Nq + q] + l - zmax[s]), zinv[s], an);
     }
     if (live == 0) return 1.0 / (double)Nq;
-    if (mode == PHOEBE_SAMPLER_SHELL) return as / (double)live;
-    return ((1.0 - alpha) * an + alpha * as) / (double)live;
+    if (mode == PHOEBE_SAMPLER_SHELL) return (double)as / (double)live;
+    return ((1.0 - alpha) * (double)an + alpha * (double)as) / (double)live;
   }
 };
 
-// cdf[kb][q] = sum_{q' <= q} p_k(q') in FP64, one block per batch k, chunks of blockDim in q order.
+// cdf[kb][q] = sum_{q' <= q} p_k(q') in FP64, one block per batch k; chunks of blockDim * 8 q in q
+// order, 8 consecutive q per thread (a serial sum, then a block scan of the threads' totals).
 __global__ void k_prop_cdf(Proposal P, double* __restrict__ cdf) {
+  constexpr int V = 8;
   __shared__ double wsum[32];
   __shared__ double carry_s;
   const int kb = blockIdx.x;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   if (threadIdx.x == 0) carry_s = 0.0;
   __syncthreads();
-  for (int64_t base = 0; base < P.Nq; base += blockDim.x) {
-    const int64_t q = base + threadIdx.x;
-    double v = q < P.Nq ? P.value(kb, q) : 0.0;
-    for (int o = 1; o < 32; o <<= 1) {  // inclusive warp scan
+  double* out = cdf + (int64_t)kb * P.Nq;
+  for (int64_t base = 0; base < P.Nq; base += (int64_t)blockDim.x * V) {
+    const int64_t q0 = base + (int64_t)threadIdx.x * V;
+    double loc[V];
+    double run = 0.0;
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+      run += q0 + i < P.Nq ? P.value(kb, q0 + i) : 0.0;
+      loc[i] = run;
+    }
+    double v = run;  // inclusive warp scan of the threads' totals
+    for (int o = 1; o < 32; o <<= 1) {
       const double t = __shfl_up_sync(0xffffffffu, v, o);
       if (lane >= o) v += t;
     }
     if (lane == 31) wsum[w] = v;
     __syncthreads();
-    double before = carry_s;
+    double before = carry_s + (v - run);
     for (int i = 0; i < w; ++i) before += wsum[i];
-    if (q < P.Nq) cdf[(int64_t)kb * P.Nq + q] = before + v;
+#pragma unroll
+    for (int i = 0; i < V; ++i)
+      if (q0 + i < P.Nq) out[q0 + i] = before + loc[i];
     __syncthreads();
     if (threadIdx.x == 0) {
       double t = 0.0;
@@ -1036,7 +1055,7 @@ int is_batch(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& g
     if (!lphi) return st;
     dim3 g((unsigned)((Nq + 255) / 256), (unsigned)S);
     const double xcut = p->delta_cut_sigmas * p->sigma_eV;
-    k_shell_log<<<g, 256, 0, c->stream>>>(b.st_k, b.st_b, gm, Nq, t.epsF, t.fF, t.omega, t.nB, NW, NM,
+    k_shell_log<<<g, 256, 0, c->stream>>>(b.st_k, b.st_b, gm, Nq, t.epsF, t.eps2, t.fF, t.omega, t.nB, NW, NM,
                                           p->omega_cut_eV, 1.0 / p->sigma_eV, xcut,
                                           (t.omega_max + xcut) * (1.0 + 1e-12), lphi);
     TRY(launched(c, 1));
@@ -1066,6 +1085,8 @@ int is_batch(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& g
       if (!z) return st;
       float* zmax = (float*)ensure(c, "is_zmax", sizeof(float) * S, &st);
       if (!zmax) return st;
+      float* zinv = (float*)ensure(c, "is_zinv", sizeof(float) * S, &st);
+      if (!zinv) return st;
       double* zsum = (double*)ensure(c, "is_zsum", sizeof(double) * S, &st);
       if (!zsum) return st;
       float* qt = (float*)ensure(c, "is_qt", sizeof(float) * Nq * 3, &st);
@@ -1081,22 +1102,26 @@ int is_batch(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& g
       k_shell_rows<<<S, 1024, 0, c->stream>>>(lphi, Nq, rows, nrows);
       TRY(launched(c, 1));
       TRY(network_scores(c, qt, feat, S, Nq, c->cc >= 100 && !p->sampler_fp32_network, z, rows, nrows));
-      k_logit_stats<<<S, 256, 0, c->stream>>>(z, lphi, Nq, zmax, zsum);
+      k_logit_stats<<<S, 256, 0, c->stream>>>(z, lphi, Nq, zmax, zsum, zinv);
       TRY(launched(c, 1));
       P.z = z;
       P.zmax = zmax;
       P.zsum = zsum;
+      P.zinv = zinv;
     }
     if (shell) {
       float* pmax = (float*)ensure(c, "is_pmax", sizeof(float) * S, &st);
       if (!pmax) return st;
       double* psum = (double*)ensure(c, "is_psum", sizeof(double) * S, &st);
       if (!psum) return st;
-      k_logit_stats<<<S, 256, 0, c->stream>>>(nullptr, lphi, Nq, pmax, psum);
+      float* pinv = (float*)ensure(c, "is_pinv", sizeof(float) * S, &st);
+      if (!pinv) return st;
+      k_logit_stats<<<S, 256, 0, c->stream>>>(nullptr, lphi, Nq, pmax, psum, pinv);
       TRY(launched(c, 1));
       P.lp = lphi;
       P.pmax = pmax;
       P.psum = psum;
+      P.pinv = pinv;
     }
     double* cdf = (double*)ensure(c, "is_cdf", sizeof(double) * b.nkb * Nq, &st);
     if (!cdf) return st;

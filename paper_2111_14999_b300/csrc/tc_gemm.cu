@@ -2501,11 +2501,11 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
     i0 = i1;
   }
   int herr = 0;
-  unsigned long long n_xb[2] = {0, 0};
+  unsigned long long n_xb[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // four (pairs, bands) counters
   CK(c, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaMemcpyAsync(n_xb, nq_eval, sizeof(n_xb), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
-  const unsigned long long n_x = n_xb[0], n_b = n_xb[1];
+  const unsigned long long n_x = n_xb[0] + n_xb[2] + n_xb[4] + n_xb[6], n_b = n_xb[1] + n_xb[3] + n_xb[5] + n_xb[7];
   if (herr) return fail(c, PHOEBE_GPU_ERR_TIMEOUT, "a tensor-core pipeline wait ran out; results discarded");
   c->stats.pairs_executed = (int64_t)n_x;
   // complex MACs of the DFT: z sum over the entries, y sum over the pairs for every (jy, jz) line
@@ -2515,9 +2515,12 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
   // x sum: 4 FMA per complex value per residue pair or unpaired residue, 2 per real-factor residue
   double x_rows = 0.0;
   for (int k = 0; k < K; ++k) x_rows += xD[k] < 0 ? 0.5 : 1.0;
-  // plus, per listed (state, q, band), the rotations U_{k+q}^dagger (nw x 3na complex MACs) and Z_q
-  // ((3na)^2); the Gaussians and occupations are not counted
-  c->stats.stage2_flops = 8.0 * ((double)ns * zy_cmac + (double)n_x * x_rows * E + (double)n_b * (E + nm * nm));
+  // plus the epilogue's rotations U_{k+q}^dagger (nw x 3na complex MACs) and Z_q ((3na)^2) per listed
+  // (state, q, band): counted exactly by the FP64 kernels, once per evaluated (state, q) by the FP32
+  // ones (a lower bound: nearly every listed q has one band); the Gaussians and occupations are not
+  // counted
+  const double n_rot = fp64 ? (double)n_b : (double)n_x;
+  c->stats.stage2_flops = 8.0 * ((double)ns * zy_cmac + (double)n_x * x_rows * E + n_rot * (E + nm * nm));
   return PHOEBE_GPU_OK;
 }
 
