@@ -549,6 +549,12 @@ def main():
     launches = int(sum(s["kernel_launches"] for s in stats))
 
     roof = roofline(args.precision, stats, args.k_limit or args.k_planes)
+    if args.precision == 7 and roof.get("achieved") and clocks.get("sm_mhz") and clocks.get("sm_max_mhz"):
+        # the FP32 peak scales with the SM clock: the fraction against the peak at the timed region's
+        # median clock, beside the one at the maximum clock
+        peak_med = roof["peak"] * clocks["sm_mhz"] / clocks["sm_max_mhz"]
+        roof["peak_at_median_clock"] = peak_med
+        roof["frac_at_median_clock"] = roof["achieved"] / peak_med
 
     extra = {}
     g_head = g_out.cpu().numpy().copy()

@@ -120,7 +120,14 @@ struct PolarArgs {
 // Stage 1 on grid k points as a separable DFT over the R_e box (dft_s1.cu): for the batch's k in
 // kx planes, X[row(k)][c] = sum_Re w_e e^{2 pi i k.R_e} g(R_e)[c] with the phase factorised per axis.
 // Entries = R_e sorted by (rz, ry) residue pair; pairs sorted by rz residue; z groups {rz, -rz}.
-constexpr int kS1Cols = 64;     // element columns per block
+#ifndef PHX_S1_COLS
+#define PHX_S1_COLS 64
+#endif
+constexpr int kS1Cols = PHX_S1_COLS;  // element columns per block
+#ifndef PHX_S1_LINES
+#define PHX_S1_LINES 1
+#endif
+constexpr int kS1Lines = PHX_S1_LINES;  // ky lines per barrier-delimited iteration
 struct S1Args {
   const float2* g;            // [nRe][C] g(R_e)[c] in FP32
   int64_t C;                  // element columns (nRp nw nw 3na)

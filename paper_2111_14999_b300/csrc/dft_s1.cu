@@ -19,8 +19,8 @@ __global__ void __launch_bounds__(256) k_s1_dft(S1Args a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int Pe = a.Pe, nRe = a.nRe, G = a.Gz, By = a.By;
   float2* W1 = reinterpret_cast<float2*>(smem);          // [Pe][CW]
-  float2* W2 = W1 + (size_t)Pe * CW;                     // [Bz][CW]
-  float2* exw = W2 + (size_t)a.Bz * CW;                  // [nRe] w Ex[kx][rx] per entry
+  float2* W2 = W1 + (size_t)Pe * CW;                     // [kS1Lines][Bz][CW]
+  float2* exw = W2 + (size_t)kS1Lines * a.Bz * CW;       // [nRe] w Ex[kx][rx] per entry
   float2* Eyk = exw + nRe;                               // [nky][By]
   float2* Ezg = Eyk + (size_t)a.nky * By;                // [nkz][G]
   int2* zg = reinterpret_cast<int2*>(Ezg + (size_t)a.nkz * G);  // [G]
@@ -44,70 +44,102 @@ __global__ void __launch_bounds__(256) k_s1_dft(S1Args a) {
   for (int i = threadIdx.x; i <= Pe; i += blockDim.x) peo[i] = a.pair_ent_off[i];
   for (int i = threadIdx.x; i < Pe; i += blockDim.x) pay[i] = a.pair_ay[i];
   for (int i = threadIdx.x; i <= a.Bz; i += blockDim.x) rzo[i] = a.rz_pair_off[i];
+  for (int i = threadIdx.x; i < Pe * CW; i += blockDim.x) W1[i] = make_float2(0.f, 0.f);
   __syncthreads();
-  // rx sum: W1[p][col] = sum over the entries of pair p of w Ex g
-  for (int p = t4; p < Pe; p += TPC) {
+  // rx sum: W1[p][col] = sum over the entries of pair p of w Ex g.  Each of the TPC threads of a
+  // column takes a contiguous chunk of the entries (sorted by pair) with 8 loads in flight, and adds
+  // its running pair sum into W1 when the pair changes (pairs split between chunks get two adds).
+  {
+    constexpr int U = 8;
+    const int per = (nRe + TPC - 1) / TPC;
+    const int e0 = t4 * per, e1 = min(nRe, e0 + per);
+    int p = 0;
+    while (p + 1 < Pe && peo[p + 1] <= e0) ++p;
     float2 acc = make_float2(0.f, 0.f);
-#pragma unroll 4
-    for (int e = peo[p]; e < peo[p + 1]; ++e) {
-      const float2 gv = live ? __ldg(a.g + (int64_t)erow[e] * a.C + c0 + col) : make_float2(0.f, 0.f);
-      const float2 x = exw[e];
-      acc.x = fmaf(x.x, gv.x, fmaf(-x.y, gv.y, acc.x));
-      acc.y = fmaf(x.x, gv.y, fmaf(x.y, gv.x, acc.y));
+    for (int eb = e0; eb < e1; eb += U) {
+      float2 gv[U];
+#pragma unroll
+      for (int i = 0; i < U; ++i)
+        gv[i] = (live && eb + i < e1) ? __ldg(a.g + (int64_t)erow[eb + i] * a.C + c0 + col) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < U; ++i) {
+        const int e = eb + i;
+        if (e >= e1) break;
+        if (e >= peo[p + 1]) {  // next pair: flush the running sum
+          atomicAdd(&W1[p * CW + col].x, acc.x);
+          atomicAdd(&W1[p * CW + col].y, acc.y);
+          acc = make_float2(0.f, 0.f);
+          while (e >= peo[p + 1]) ++p;
+        }
+        const float2 x = exw[e];
+        acc.x = fmaf(x.x, gv[i].x, fmaf(-x.y, gv[i].y, acc.x));
+        acc.y = fmaf(x.x, gv[i].y, fmaf(x.y, gv[i].x, acc.y));
+      }
     }
-    W1[p * CW + col] = acc;
+    if (e1 > e0) {
+      atomicAdd(&W1[p * CW + col].x, acc.x);
+      atomicAdd(&W1[p * CW + col].y, acc.y);
+    }
   }
   __syncthreads();
-  for (int li = a.plane_line_off[pl]; li < a.plane_line_off[pl + 1]; ++li) {
-    const float2* ey = Eyk + (size_t)a.line_ky[li] * By;
-    // ry sum: W2(r) = sum over the pairs with rz = r of Ey[ky][ry] W1[pair], one rz per item
-    for (int r = t4; r < a.Bz; r += TPC) {
+  // per iteration kS1Lines ky lines of the plane: their ry sums, one barrier, their rz sums and stores
+  const int lb = a.plane_line_off[pl], le = a.plane_line_off[pl + 1];
+  for (int li = lb; li < le; li += kS1Lines) {
+    const int nl = min(kS1Lines, le - li);
+    // ry sum: W2[line](r) = sum over the pairs with rz = r of Ey[ky][ry] W1[pair], one (line, rz) per item
+    for (int it = t4; it < nl * a.Bz; it += TPC) {
+      const int ll = it / a.Bz, r = it - ll * a.Bz;
+      const float2* ey = Eyk + (size_t)a.line_ky[li + ll] * By;
       float2 w = make_float2(0.f, 0.f);
       for (int p = rzo[r]; p < rzo[r + 1]; ++p) {
         const float2 e = ey[pay[p]], v = W1[p * CW + col];
         w.x = fmaf(e.x, v.x, fmaf(-e.y, v.y, w.x));
         w.y = fmaf(e.x, v.y, fmaf(e.y, v.x, w.y));
       }
-      W2[r * CW + col] = w;
+      W2[(ll * a.Bz + r) * CW + col] = w;
     }
     __syncthreads();
-    // rz sum for the batch's k on this line
-    float2 P[GZ], M[GZ];
-#pragma unroll
-    for (int g = 0; g < GZ; ++g) {
-      P[g] = M[g] = make_float2(0.f, 0.f);
-      if (g < G) {
-        const int2 z = zg[g];
-        const float2 u = W2[z.x * CW + col], v = z.y >= 0 ? W2[z.y * CW + col] : make_float2(0.f, 0.f);
-        P[g] = make_float2(u.x + v.x, u.y + v.y);
-        M[g] = make_float2(u.x - v.x, u.y - v.y);
-      }
-    }
-    for (int i = a.line_k_off[li] + t4; i < a.line_k_off[li + 1]; i += TPC) {
-      const int4 kr = a.kent[i];  // (kz, X row of kz, X row of -kz or -1)
-      const float2* ez = Ezg + (size_t)kr.x * G;
-      float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
+    for (int ll = 0; ll < nl; ++ll) {
+      const float2* w2 = W2 + (size_t)ll * a.Bz * CW;
+      // rz sum for the batch's k on this line
+      float2 P[GZ], M[GZ];
 #pragma unroll
       for (int g = 0; g < GZ; ++g) {
-        if (g >= G) break;
-        const float2 e = ez[g];
-        A.x = fmaf(e.x, P[g].x, A.x);
-        A.y = fmaf(e.x, P[g].y, A.y);
-        B.x = fmaf(-e.y, M[g].y, B.x);
-        B.y = fmaf(e.y, M[g].x, B.y);
+        P[g] = M[g] = make_float2(0.f, 0.f);
+        if (g < G) {
+          const int2 z = zg[g];
+          const float2 u = w2[z.x * CW + col], v = z.y >= 0 ? w2[z.y * CW + col] : make_float2(0.f, 0.f);
+          P[g] = make_float2(u.x + v.x, u.y + v.y);
+          M[g] = make_float2(u.x - v.x, u.y - v.y);
+        }
       }
-      if (live) {
-        *reinterpret_cast<float2*>(a.X + (int64_t)kr.y * a.ldx + 2 * (c0 + col)) = make_float2(A.x + B.x, A.y + B.y);
-        if (kr.z >= 0)
-          *reinterpret_cast<float2*>(a.X + (int64_t)kr.z * a.ldx + 2 * (c0 + col)) = make_float2(A.x - B.x, A.y - B.y);
+      for (int i = a.line_k_off[li + ll] + t4; i < a.line_k_off[li + ll + 1]; i += TPC) {
+        const int4 kr = a.kent[i];  // (kz, X row of kz, X row of -kz or -1)
+        const float2* ez = Ezg + (size_t)kr.x * G;
+        float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int g = 0; g < GZ; ++g) {
+          if (g >= G) break;
+          const float2 e = ez[g];
+          A.x = fmaf(e.x, P[g].x, A.x);
+          A.y = fmaf(e.x, P[g].y, A.y);
+          B.x = fmaf(-e.y, M[g].y, B.x);
+          B.y = fmaf(e.y, M[g].x, B.y);
+        }
+        if (live) {
+          *reinterpret_cast<float2*>(a.X + (int64_t)kr.y * a.ldx + 2 * (c0 + col)) = make_float2(A.x + B.x, A.y + B.y);
+          if (kr.z >= 0)
+            *reinterpret_cast<float2*>(a.X + (int64_t)kr.z * a.ldx + 2 * (c0 + col)) = make_float2(A.x - B.x, A.y - B.y);
+        }
       }
     }
-    __syncthreads();  // W2 is rewritten for the next line
+    __syncthreads();  // W2 is rewritten for the next lines
   }
 }
 
 size_t s1_smem_bytes(int nRe, int Pe, int Bz, int Gz, int nky, int By, int nkz) {
-  return sizeof(float2) * ((size_t)Pe * kS1Cols + (size_t)Bz * kS1Cols + nRe + (size_t)nky * By + (size_t)nkz * Gz) +
+  return sizeof(float2) * ((size_t)Pe * kS1Cols + (size_t)kS1Lines * Bz * kS1Cols + nRe + (size_t)nky * By +
+                           (size_t)nkz * Gz) +
          sizeof(int2) * (size_t)Gz + sizeof(int) * ((size_t)Pe + 1 + nRe + Pe + (size_t)Bz + 1);
 }
 
