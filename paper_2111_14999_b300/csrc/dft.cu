@@ -36,6 +36,41 @@ __global__ void __launch_bounds__(256) k_dft_z(DftZArgs a) {
   }
   __syncthreads();
   const float2* X = reinterpret_cast<const float2*>(a.X + (int64_t)a.st_kb[s] * a.ldx);
+  if (nw == 8 && nm == 6) {
+    // one warp per entry: the entry's 384 values X[R][m][n][sa] read in memory order as 16-byte
+    // vectors, lane L holding m = L / 4 and n = 2 (L % 4), 2 (L % 4) + 1 for every sa; the sum over n
+    // by two shuffle rounds among the four lanes of an m
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int m = lane >> 2, n0 = 2 * (lane & 3);
+    const float2 u0 = us[n0], u1 = us[n0 + 1];
+    for (int e = warp; e < ne; e += (int)(blockDim.x >> 5)) {
+      const int r = a.ent_r[e0 + e];
+      const float4* x4 = reinterpret_cast<const float4*>(X + (int64_t)r * 384 + lane * 12);
+      float2 t[6];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {  // n0: values 0..5, n1: values 6..11 of the lane's 12
+        const float4 va = __ldg(x4 + i), vb = __ldg(x4 + 3 + i);
+        const float2 a0 = make_float2(va.x, va.y), a1 = make_float2(va.z, va.w);
+        const float2 b0 = make_float2(vb.x, vb.y), b1 = make_float2(vb.z, vb.w);
+        t[2 * i].x = fmaf(a0.x, u0.x, fmaf(-a0.y, u0.y, fmaf(b0.x, u1.x, -b0.y * u1.y)));
+        t[2 * i].y = fmaf(a0.x, u0.y, fmaf(a0.y, u0.x, fmaf(b0.x, u1.y, b0.y * u1.x)));
+        t[2 * i + 1].x = fmaf(a1.x, u0.x, fmaf(-a1.y, u0.y, fmaf(b1.x, u1.x, -b1.y * u1.y)));
+        t[2 * i + 1].y = fmaf(a1.x, u0.y, fmaf(a1.y, u0.x, fmaf(b1.x, u1.y, b1.y * u1.x)));
+      }
+#pragma unroll
+      for (int o = 1; o < 4; o <<= 1)
+#pragma unroll
+        for (int sa = 0; sa < 6; ++sa) {
+          t[sa].x += __shfl_xor_sync(0xffffffffu, t[sa].x, o);
+          t[sa].y += __shfl_xor_sync(0xffffffffu, t[sa].y, o);
+        }
+      const float sc = a.w[r] * a.unscale;
+      const int j = lane & 3;  // lanes of an m write sa = j and j + 4
+#pragma unroll
+      for (int sa = 0; sa < 6; ++sa)
+        if (sa == j || sa == j + 4) Ts[e * E + sa * 8 + m] = make_float2(t[sa].x * sc, t[sa].y * sc);
+    }
+  } else
   for (int i = threadIdx.x; i < ne * E; i += blockDim.x) {  // i = (e, m, sa), sa fastest
     const int e = i / E, rem = i % E;
     const int m = rem / nm, sa = rem % nm;
