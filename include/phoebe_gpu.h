@@ -47,7 +47,7 @@ typedef enum {
   PHOEBE_GPU_ERR_NOMEM = -5,          /* device allocation failed or exceeds the memory cap */
   PHOEBE_GPU_ERR_CUDA = -6,           /* a CUDA runtime call failed (text in last_error) */
   PHOEBE_GPU_ERR_TIMEOUT = -7,        /* a bounded device-side wait ran out */
-  PHOEBE_GPU_ERR_NOTCONVERGED = -8,   /* a Jacobi eigensolve hit its sweep cap */
+  PHOEBE_GPU_ERR_NOTCONVERGED = -8,   /* an eigensolve hit its QR step cap */
   PHOEBE_GPU_ERR_UNSUPPORTED = -9     /* valid request the library does not implement */
 } phoebe_gpu_status;
 

@@ -1,11 +1,12 @@
 // Band structures on grids and point lists: Wannier/force-constant Fourier
-// sums (Sec. 3.2 Eq. 10, Sec. 3.1 Eq. 3), batched Hermitian Jacobi
-// eigensolves (Eqs. 4, 11), phonon mode factors (Eq. 7), occupations
+// sums (Sec. 3.2 Eq. 10, Sec. 3.1 Eq. 3), batched Hermitian eigensolves
+// (Eqs. 4, 11; Householder tridiagonalisation and shifted QR), phonon mode factors (Eq. 7), occupations
 // (Secs. 4.1-4.2) and the energy window compaction (Sec. 5.2).
 //
 // Matrices being diagonalised are kept "structure of arrays": element (i,j)
 // of matrix b lives at [(i*n + j) * B + b], so a warp touching 32 matrices
 // reads 32 consecutive complex numbers.
+#include "eigh.cuh"
 #include "kernels.cuh"
 
 namespace phx {
@@ -178,98 +179,29 @@ __global__ void k_dynmat_grid(const double* __restrict__ Phi, const int* __restr
   out[(int64_t)e * P + p] = {acc.re * s, acc.im * s};
 }
 
-// Cyclic complex Jacobi on B Hermitian n x n matrices (SoA, in place).
-// Rotation for the pair (p,q) with A_pq = r e^{i phi}: first remove the phase
-// (D = diag(1, e^{-i phi})), then the real symmetric 2x2 Schur rotation
-// (tau = (a_qq - a_pp)/(2r), t = sgn(tau)/(|tau| + sqrt(1+tau^2)), c = 1/sqrt(1+t^2),
-// s = t c), so Q = [[c, s], [-s e^{-i phi}, c e^{-i phi}]] and A <- Q^dagger A Q, V <- V Q.
-// Eigenvalues ascending -> evals[b][n]; eigenvectors as columns -> evecs[b][n][n].
-__global__ void k_jacobi_herm(cplx* __restrict__ A, cplx* __restrict__ V, int n, int64_t B,
-                              int max_sweeps, double* __restrict__ evals, cplx* __restrict__ evecs,
-                              int* __restrict__ status) {
-  int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// B Hermitian n x n matrices (SoA, in place; V is scratch) -> eigenvalues ascending in
+// evals[b][n], eigenvectors as columns in evecs[b][n][n]: one thread per matrix runs the
+// Householder tridiagonalisation and shifted QR of eigh_hermitian.
+__global__ void k_eigh_herm(cplx* __restrict__ A, cplx* __restrict__ V, int n, int64_t B,
+                            double* __restrict__ evals, cplx* __restrict__ evecs, int* __restrict__ status) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (b >= B) return;
-#define AE(i, j) A[((int64_t)(i) * n + (j)) * B + b]
-#define VE(i, j) V[((int64_t)(i) * n + (j)) * B + b]
-  for (int i = 0; i < n; ++i) {
-    for (int j = 0; j < n; ++j) VE(i, j) = {i == j ? 1.0 : 0.0, 0.0};
-    // exact Hermitian symmetry on entry
-    cplx d = AE(i, i);
-    AE(i, i) = {d.re, 0.0};
-    for (int j = i + 1; j < n; ++j) {
-      cplx u = AE(i, j), l = AE(j, i);
-      cplx m = {0.5 * (u.re + l.re), 0.5 * (u.im - l.im)};
-      AE(i, j) = m;
-      AE(j, i) = {m.re, -m.im};
-    }
-  }
-  // Rotate only entries above 1e-15 of the Frobenius norm (invariant under the
-  // rotations); below that they are rounding noise.  Converged when a whole
-  // sweep performs no rotation.
-  double norm2 = 0.0;
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) norm2 += cabs2(AE(i, j));
-  const double thr = 1e-15 * sqrt(norm2);
-  bool converged = norm2 == 0.0;
-  for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
-    bool rotated = false;
-    for (int p = 0; p < n - 1; ++p) {
-      for (int q = p + 1; q < n; ++q) {
-        cplx apq = AE(p, q);
-        double r = sqrt(cabs2(apq));
-        if (r <= thr) continue;
-        rotated = true;
-        double app = AE(p, p).re, aqq = AE(q, q).re;
-        double tau = (aqq - app) / (2.0 * r);
-        double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-        double c = 1.0 / sqrt(1.0 + t * t);
-        double s = t * c;
-        cplx phc = {apq.re / r, -apq.im / r};  // e^{-i phi}
-        for (int k = 0; k < n; ++k) {
-          if (k == p || k == q) continue;
-          cplx akp = AE(k, p), akq = AE(k, q);
-          cplx x = cmul(akq, phc);
-          cplx nkp = {c * akp.re - s * x.re, c * akp.im - s * x.im};
-          cplx nkq = {s * akp.re + c * x.re, s * akp.im + c * x.im};
-          AE(k, p) = nkp;
-          AE(p, k) = {nkp.re, -nkp.im};
-          AE(k, q) = nkq;
-          AE(q, k) = {nkq.re, -nkq.im};
-        }
-        AE(p, p) = {app - t * r, 0.0};
-        AE(q, q) = {aqq + t * r, 0.0};
-        AE(p, q) = {0.0, 0.0};
-        AE(q, p) = {0.0, 0.0};
-        for (int k = 0; k < n; ++k) {
-          cplx vkp = VE(k, p), vkq = VE(k, q);
-          cplx x = cmul(vkq, phc);
-          VE(k, p) = {c * vkp.re - s * x.re, c * vkp.im - s * x.im};
-          VE(k, q) = {s * vkp.re + c * x.re, s * vkp.im + c * x.im};
-        }
-      }
-    }
-    if (!rotated) converged = true;
-  }
-  if (!converged && status) atomicOr(status, 1);
-  // selection sort of eigenvalues (ascending) with their columns; output AoS
+  const Strided<cplx> a{A + b, n, B}, v{V + b, n, B};
+  double w[kMaxNw];
+  if (eigh_hermitian(a, v, n, w) && status) atomicOr(status, 1);
+  // insertion sort of the eigenvalues (ascending) with their columns; output AoS
   int order[kMaxNw];
-  for (int i = 0; i < n; ++i) order[i] = i;
   for (int i = 0; i < n; ++i) {
-    int best = i;
-    for (int j = i + 1; j < n; ++j)
-      if (AE(order[j], order[j]).re < AE(order[best], order[best]).re) best = j;
-    int tmp = order[i];
-    order[i] = order[best];
-    order[best] = tmp;
+    int j = i;
+    for (; j > 0 && w[order[j - 1]] > w[i]; --j) order[j] = order[j - 1];
+    order[j] = i;
   }
   for (int i = 0; i < n; ++i) {
-    int src = order[i];
-    evals[b * n + i] = AE(src, src).re;
+    const int src = order[i];
+    evals[b * n + i] = w[src];
     if (evecs)
-      for (int k = 0; k < n; ++k) evecs[(b * n + k) * n + i] = VE(k, src);
+      for (int k = 0; k < n; ++k) evecs[(b * n + k) * n + i] = v(k, src);
   }
-#undef AE
-#undef VE
 }
 
 // Phonon energies, Bose factors and mode factors Z = z sqrt(hbar^2/(2 M_s hbar w)) (Eq. 7);

@@ -52,8 +52,7 @@ __global__ void k_fourier_points_c(const cplx* in, const int* R, const double* w
 __global__ void k_dynmat_grid(const double* Phi, const int* R, const double* w, int nR, int nm,
                               const double* inv_sqrt_m, GridPhase gp, const cplx* cis, const double* qpts,
                               int64_t P, cplx* out);
-__global__ void k_jacobi_herm(cplx* A, cplx* V, int n, int64_t B, int max_sweeps, double* evals,
-                              cplx* evecs, int* status);
+__global__ void k_eigh_herm(cplx* A, cplx* V, int n, int64_t B, double* evals, cplx* evecs, int* status);
 __global__ void k_phonon_factors(const double* lam, const cplx* z, int nm, int64_t Q,
                                  const double* mass_of_row, double T, double omega_cut, double* omega,
                                  double* nB, cplx* Z);

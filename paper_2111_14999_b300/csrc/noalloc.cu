@@ -13,7 +13,7 @@
 
 namespace {
 
-// Work arrays of the Jacobi eigensolver (two complex n_k x nw x nw arrays) plus
+// Work arrays of the eigensolver (two complex n_k x nw x nw arrays) plus
 // a convergence word at the end.  Every GPU that loads the library keeps this
 // allocation until the process exits.
 constexpr size_t kNoallocScratchBytes = (size_t)16 << 20;  // 16 MiB
@@ -72,8 +72,7 @@ extern "C" int phoebe_gpu_bands_noalloc(int nw, int n_R, const int32_t* R, const
   const int E = nw * nw;
   dim3 g((unsigned)((n_k + 127) / 128), (unsigned)E);
   k_fourier_points_c<<<g, 128, 0, s>>>(reinterpret_cast<const cplx*>(H), R, w, n_R, E, k, n_k, A);
-  k_jacobi_herm<<<(unsigned)((n_k + 127) / 128), 128, 0, s>>>(A, V, nw, n_k, 40, eps, reinterpret_cast<cplx*>(U),
-                                                              status);
+  k_eigh_herm<<<(unsigned)((n_k + 127) / 128), 128, 0, s>>>(A, V, nw, n_k, eps, reinterpret_cast<cplx*>(U), status);
   if (cudaGetLastError() != cudaSuccess) return PHOEBE_GPU_ERR_CUDA;
   int hs = 0;
   if (cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

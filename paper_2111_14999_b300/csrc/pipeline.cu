@@ -37,12 +37,12 @@ static int electron_points(phoebe_gpu_ctx* c, const double* kdev, int64_t P, con
   dim3 g((unsigned)((P + 127) / 128), (unsigned)E);
   k_fourier_points_c<<<g, 128, 0, c->stream>>>((const cplx*)c->bufs["H"].p, (const int*)c->bufs["RH"].p,
                                                  (const double*)c->bufs["wH"].p, c->nRH, E, kdev, P, A);
-  k_jacobi_herm<<<(unsigned)((P + 127) / 128), 128, 0, c->stream>>>(A, V, nw, P, kJacobiSweeps, e, u, status);
+  k_eigh_herm<<<(unsigned)((P + 127) / 128), 128, 0, c->stream>>>(A, V, nw, P, e, u, status);
   TRY(launch_check(c, 2));
   int hs = 0;
   CK(c, cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
-  if (hs) return fail(c, PHOEBE_GPU_ERR_NOTCONVERGED, "Jacobi eigensolve of H(k) did not converge");
+  if (hs) return fail(c, PHOEBE_GPU_ERR_NOTCONVERGED, "eigensolve of H(k) did not converge");
   *eps = e;
   *U = u;
   return PHOEBE_GPU_OK;

@@ -84,8 +84,6 @@ struct IsRequest {
 
 namespace phx {
 
-constexpr int kJacobiSweeps = 40;
-
 int fail(phoebe_gpu_ctx* c, int code, const char* fmt, ...);
 int cuda_fail(phoebe_gpu_ctx* c, cudaError_t e, const char* what, int line);
 
