@@ -254,6 +254,10 @@ def learned_leg(pg, W, dev, stream, args) -> dict:
         res[name] = {"l2_rel_err": errs, "wall_s": float(np.median(walls)),
                      "sampler_ms": st["sampler_ms"], "pairs_ms": st["stage2_ms"], "total_ms": st["total_ms"]}
     n = len(full)
+    # the full q sum by the separable grid DFT in FP32 (the benchmarked mode) on the same states
+    p7 = prm.with_(precision=7, k_subset=kk)
+    timed(p7)
+    (_, _, g7), w7, st7 = timed(p7)
     f64k = kk[:6]
     (_, _, g64), w64, st64 = timed(prm.with_(precision=0, k_subset=f64k))
     ctx.close()
@@ -273,11 +277,14 @@ def learned_leg(pg, W, dev, stream, args) -> dict:
         "gate_l2_1pct_met": bool(np.mean(res["learned"]["l2_rel_err"]) <= 0.01),
         "linewidths_per_s_shell_only": n / res["shell"]["wall_s"],
         "linewidths_per_s_learned": lw, "linewidths_per_s_full_same_precision": n / full_s,
+        "linewidths_per_s_full_fp32_grid_dft": len(g7) / w7,
+        "max_rel_diff_fp32_grid_dft_vs_full_same_precision": float(np.max(np.abs(g7 - full) / np.abs(full))),
         "linewidths_per_s_fp64_gpu_full": len(g64) / w64,
         "speedup_learned_vs_fp64_gpu": lw / (len(g64) / w64),
         "learned_ms": {"network_proposal_draws": res["learned"]["sampler_ms"], "sampled_pairs": res["learned"]["pairs_ms"],
                        "total": res["learned"]["total_ms"]},
         "full_ms": {"stage2": full_st["stage2_ms"], "total": full_st["total_ms"]},
+        "full_fp32_grid_dft_ms": {"stage2": st7["stage2_ms"], "total": st7["total_ms"]},
     }
 
 

@@ -250,9 +250,8 @@ int phx::electron_grid(phoebe_gpu_ctx* c, const int n[3], double** eps, cplx** U
   CK(c, cudaMemsetAsync(status, 0, 64, c->stream));
   TRY(fourier_grid_sep(c, (const cplx*)c->bufs["H"].p, (const int*)c->bufs["RH"].p,
                        (const double*)c->bufs["wH"].p, c->nRH, E, n, A));
-  k_eigh_herm<<<(unsigned)((P + 127) / 128), 128, 0, c->stream>>>(A, V, nw, P, e, u, status);
+  if (eigh_launch(c->stream, A, V, nw, P, e, u, status)) return fail(c, PHOEBE_GPU_ERR_CUDA, "eigensolver launch failed");
   c->launches += 1;
-  CK(c, cudaGetLastError());
   int hs = 0;
   CK(c, cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
@@ -292,7 +291,7 @@ int phx::phonon_modes(phoebe_gpu_ctx* c, const int n[3], const double* qpts_dev,
   k_dynmat_grid<<<g, 128, 0, c->stream>>>((const double*)c->bufs["Phi"].p, (const int*)c->bufs["Rf"].p,
                                             (const double*)c->bufs["wf"].p, c->nRf, nm,
                                             (const double*)c->bufs["inv_sqrt_m"].p, gp, cis, qpts_dev, Q, A);
-  k_eigh_herm<<<(unsigned)((Q + 127) / 128), 128, 0, c->stream>>>(A, V, nm, Q, lam, z, status);
+  if (eigh_launch(c->stream, A, V, nm, Q, lam, z, status)) return fail(c, PHOEBE_GPU_ERR_CUDA, "eigensolver launch failed");
   k_phonon_factors<<<(unsigned)((Q * nm + 127) / 128), 128, 0, c->stream>>>(
       lam, z, nm, Q, (const double*)c->bufs["mass_of_row"].p, T, omega_cut, om, nb, Zq);
   c->launches += 3;

@@ -179,29 +179,35 @@ __global__ void k_dynmat_grid(const double* __restrict__ Phi, const int* __restr
   out[(int64_t)e * P + p] = {acc.re * s, acc.im * s};
 }
 
+// Solved matrix b (eigenvalues ascending on A's diagonal, eigenvectors as V's columns) ->
+// evals[b][n], evecs[b][n][n] (eigenvectors as columns).
+__device__ __forceinline__ void eigh_store(const Strided<cplx>& a, const Strided<cplx>& v, int n, int64_t b,
+                                           double* __restrict__ evals, cplx* __restrict__ evecs) {
+  for (int i = 0; i < n; ++i) {
+    evals[b * n + i] = a(i, i).re;
+    if (evecs)
+      for (int k = 0; k < n; ++k) evecs[(b * n + k) * n + i] = v(k, i);
+  }
+}
+
 // B Hermitian n x n matrices (SoA, in place; V is scratch) -> eigenvalues ascending in
 // evals[b][n], eigenvectors as columns in evecs[b][n][n]: one thread per matrix runs the
-// Householder tridiagonalisation and shifted QR of eigh_hermitian.
+// Householder tridiagonalisation and shifted QR of eigh_hermitian on its matrix in global memory.
 __global__ void k_eigh_herm(cplx* __restrict__ A, cplx* __restrict__ V, int n, int64_t B,
                             double* __restrict__ evals, cplx* __restrict__ evecs, int* __restrict__ status) {
   const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (b >= B) return;
   const Strided<cplx> a{A + b, n, B}, v{V + b, n, B};
-  double w[kMaxNw];
-  if (eigh_hermitian(a, v, n, w) && status) atomicOr(status, 1);
-  // insertion sort of the eigenvalues (ascending) with their columns; output AoS
-  int order[kMaxNw];
-  for (int i = 0; i < n; ++i) {
-    int j = i;
-    for (; j > 0 && w[order[j - 1]] > w[i]; --j) order[j] = order[j - 1];
-    order[j] = i;
-  }
-  for (int i = 0; i < n; ++i) {
-    const int src = order[i];
-    evals[b * n + i] = w[src];
-    if (evecs)
-      for (int k = 0; k < n; ++k) evecs[(b * n + k) * n + i] = v(k, src);
-  }
+  if (eigh_hermitian(a, v, n) && status) atomicOr(status, 1);
+  eigh_store(a, v, n, b, evals, evecs);
+}
+
+int eigh_launch(cudaStream_t st, cplx* A, cplx* V, int n, int64_t B, double* evals, cplx* evecs, int* status) {
+  if (B <= 0) return 0;
+  // one thread per matrix: small batches in narrow blocks, so that they spread over every SM
+  const int T = B <= 148 * 32 ? 32 : B <= 148 * 64 ? 64 : 128;
+  k_eigh_herm<<<(unsigned)((B + T - 1) / T), T, 0, st>>>(A, V, n, B, evals, evecs, status);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 // Phonon energies, Bose factors and mode factors Z = z sqrt(hbar^2/(2 M_s hbar w)) (Eq. 7);

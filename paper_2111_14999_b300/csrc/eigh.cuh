@@ -28,12 +28,13 @@ struct Strided {
   __host__ __device__ __forceinline__ T& operator()(int i, int j) const { return p[((int64_t)i * n + j) * s]; }
 };
 
-// A (n x n, overwritten) -> eigenvalues w[0..n) in no particular order, eigenvectors as the
-// columns of V (V(:, i) belongs to w[i]).  n <= kMaxNw.  Returns 0, or 1 if the QR iteration
-// did not converge within 30 n steps (w and V are then not eigenpairs).
-__host__ __device__ inline int eigh_hermitian(Strided<cplx> A, Strided<cplx> V, int n, double* w) {
-  double beta[kMaxNw], e[kMaxNw];
-  cplx off[kMaxNw];
+// A (n x n, overwritten) -> eigenvalues ascending in the real parts of A's diagonal, eigenvectors
+// as the columns of V (V(:, i) belongs to A(i, i).re).  n <= kMaxNw.  Every intermediate lives in
+// A and V, so the two matrices are the solver's only storage: the reflector of step k in column k
+// below the diagonal, its beta in A(k, k).im, the complex sub-diagonal t_k in A(k, k+1), the real
+// tridiagonal's off-diagonal e_k in A(k+1, k).re.  Returns 0, or 1 if the QR iteration did not
+// converge within 30 n steps (A and V then hold no eigenpairs).
+__host__ __device__ inline int eigh_hermitian(Strided<cplx> A, Strided<cplx> V, int n) {
   // exact Hermitian symmetry on entry
   for (int i = 0; i < n; ++i) {
     A(i, i).im = 0.0;
@@ -44,22 +45,19 @@ __host__ __device__ inline int eigh_hermitian(Strided<cplx> A, Strided<cplx> V, 
       A(j, i) = {m.re, -m.im};
     }
   }
-  // 1. tridiagonalisation; v_k is kept in column k below the diagonal, p and q in row k
+  // 1. tridiagonalisation; p and q of step k live in row k until the step ends
   for (int k = 0; k + 2 < n; ++k) {
     const cplx x0 = A(k + 1, k);
     double sig = 0.0;
     for (int i = k + 2; i < n; ++i) sig += cabs2(A(i, k));
     if (sig == 0.0) {  // already tridiagonal in this column
-      beta[k] = 0.0;
-      off[k] = x0;
-      continue;
+      A(k, k + 1) = x0;
+      continue;        // beta = A(k, k).im = 0
     }
     const double a0 = sqrt(cabs2(x0)), nx = sqrt(a0 * a0 + sig);
     const cplx ph = a0 > 0.0 ? cplx{x0.re / a0, x0.im / a0} : cplx{1.0, 0.0};
-    off[k] = {-ph.re * nx, -ph.im * nx};
     A(k + 1, k) = {ph.re * (a0 + nx), ph.im * (a0 + nx)};
     const double b = 1.0 / (nx * (nx + a0));
-    beta[k] = b;
     for (int i = k + 1; i < n; ++i) {  // p = beta A v
       cplx acc = {0.0, 0.0};
       for (int j = k + 1; j < n; ++j) cfma(acc, A(i, j), A(j, k));
@@ -89,18 +87,20 @@ __host__ __device__ inline int eigh_hermitian(Strided<cplx> A, Strided<cplx> V, 
       const cplx t = cmulc(vi, qi);
       A(i, i) = {A(i, i).re - 2.0 * t.re, 0.0};
     }
+    A(k, k + 1) = {-ph.re * nx, -ph.im * nx};  // t_k = alpha
+    A(k, k).im = b;
   }
-  for (int i = 0; i < n; ++i) w[i] = A(i, i).re;
-  if (n >= 2) off[n - 2] = A(n - 1, n - 2);
+  if (n >= 2) A(n - 2, n - 1) = A(n - 1, n - 2);
   // Q = H_0 ... H_{n-3} by backward accumulation into V
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) V(i, j) = {i == j ? 1.0 : 0.0, 0.0};
   for (int k = n - 3; k >= 0; --k) {
-    if (beta[k] == 0.0) continue;
+    const double b = A(k, k).im;
+    if (b == 0.0) continue;
     for (int j = k + 1; j < n; ++j) {
       cplx s = {0.0, 0.0};
       for (int i = k + 1; i < n; ++i) cfma_conja(s, A(i, k), V(i, j));  // v^H V(:, j)
-      s = {-beta[k] * s.re, -beta[k] * s.im};
+      s = {-b * s.re, -b * s.im};
       for (int i = k + 1; i < n; ++i) {
         cplx x = V(i, j);
         cfma(x, A(i, k), s);
@@ -108,51 +108,59 @@ __host__ __device__ inline int eigh_hermitian(Strided<cplx> A, Strided<cplx> V, 
       }
     }
   }
-  // 2. real tridiagonal: V <- Q D
+  // 2. real tridiagonal: V <- Q D, e_k = |t_k|
   cplx ph = {1.0, 0.0};
   for (int k = 0; k + 1 < n; ++k) {
-    const double r = sqrt(cabs2(off[k]));
-    e[k] = r;
-    if (r > 0.0) ph = cmul(ph, cplx{off[k].re / r, off[k].im / r});
+    const cplx t = A(k, k + 1);
+    const double r = sqrt(cabs2(t));
+    A(k + 1, k) = {r, 0.0};
+    if (r > 0.0) ph = cmul(ph, cplx{t.re / r, t.im / r});
     for (int i = 0; i < n; ++i) V(i, k + 1) = cmul(V(i, k + 1), ph);
   }
-  // 3. implicit QR with the Wilkinson shift; e[k] couples w[k] and w[k+1]
+  // 3. implicit QR with the Wilkinson shift on w_k = A(k, k).re, e_k = A(k+1, k).re
+#define EIGH_W(k) A(k, k).re
+#define EIGH_E(k) A((k) + 1, k).re
   constexpr double kEps = 2.220446049250313e-16;
   int hi = n - 1, steps = 0;
   while (hi > 0) {
     int lo = hi;
     while (lo > 0) {
-      const double t = fabs(e[lo - 1]);
-      if (t <= kEps * (fabs(w[lo - 1]) + fabs(w[lo])) || t < 1e-300) {
-        e[lo - 1] = 0.0;
+      const double t = fabs(EIGH_E(lo - 1));
+      if (t <= kEps * (fabs(EIGH_W(lo - 1)) + fabs(EIGH_W(lo))) || t < 1e-300) {
+        EIGH_E(lo - 1) = 0.0;
         break;
       }
       --lo;
     }
-    if (lo == hi) {  // w[hi] has converged
+    if (lo == hi) {  // w_hi has converged
       --hi;
       continue;
     }
     if (++steps > 30 * n) return 1;
     // shift: the eigenvalue of the trailing 2 x 2 block nearer its last diagonal entry
-    const double g = 0.5 * (w[hi - 1] - w[hi]), f = e[hi - 1];
+    const double g = 0.5 * (EIGH_W(hi - 1) - EIGH_W(hi)), f = EIGH_E(hi - 1);
     const double r = sqrt(g * g + f * f);
-    const double mu = w[hi] - f * f / (g + (g >= 0.0 ? r : -r));
-    double x = w[lo] - mu, z = e[lo];
+    const double mu = EIGH_W(hi) - f * f / (g + (g >= 0.0 ? r : -r));
+    double x = EIGH_W(lo) - mu, z = EIGH_E(lo);
+    double a = EIGH_W(lo), bb = EIGH_E(lo);
     for (int k = lo; k < hi; ++k) {
       // rotation [c s; -s c] on rows/columns (k, k+1) that zeroes z against x
       const double rr = sqrt(x * x + z * z);
       const double c = rr > 0.0 ? x / rr : 1.0, s = rr > 0.0 ? z / rr : 0.0;
-      if (k > lo) e[k - 1] = rr;
-      const double a = w[k], bb = e[k], dd = w[k + 1];
+      if (k > lo) EIGH_E(k - 1) = rr;
+      const double dd = EIGH_W(k + 1);
       const double cc = c * c, ss = s * s, cs = c * s;
-      w[k] = cc * a + 2.0 * cs * bb + ss * dd;
-      w[k + 1] = ss * a - 2.0 * cs * bb + cc * dd;
-      e[k] = cs * (dd - a) + (cc - ss) * bb;
+      EIGH_W(k) = cc * a + 2.0 * cs * bb + ss * dd;
+      const double ek = cs * (dd - a) + (cc - ss) * bb;
+      a = ss * a - 2.0 * cs * bb + cc * dd;  // the new w_{k+1}: the next rotation's a
+      EIGH_E(k) = ek;
       if (k + 1 < hi) {  // the bulge moves to (k+2, k)
-        z = s * e[k + 1];
-        e[k + 1] *= c;
-        x = e[k];
+        const double f1 = EIGH_E(k + 1);
+        z = s * f1;
+        bb = c * f1;  // the new e_{k+1}: the next rotation's b
+        x = ek;
+      } else {
+        EIGH_W(k + 1) = a;
       }
       for (int i = 0; i < n; ++i) {
         const cplx p = V(i, k), q = V(i, k + 1);
@@ -161,6 +169,24 @@ __host__ __device__ inline int eigh_hermitian(Strided<cplx> A, Strided<cplx> V, 
       }
     }
   }
+  // ascending order: selection sort of the diagonal with the columns of V
+  for (int i = 0; i + 1 < n; ++i) {
+    int best = i;
+    for (int j = i + 1; j < n; ++j)
+      if (EIGH_W(j) < EIGH_W(best)) best = j;
+    if (best != i) {
+      const double t = EIGH_W(i);
+      EIGH_W(i) = EIGH_W(best);
+      EIGH_W(best) = t;
+      for (int r = 0; r < n; ++r) {
+        const cplx u = V(r, i);
+        V(r, i) = V(r, best);
+        V(r, best) = u;
+      }
+    }
+  }
+#undef EIGH_W
+#undef EIGH_E
   return 0;
 }
 

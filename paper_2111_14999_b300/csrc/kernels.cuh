@@ -53,6 +53,8 @@ __global__ void k_dynmat_grid(const double* Phi, const int* R, const double* w, 
                               const double* inv_sqrt_m, GridPhase gp, const cplx* cis, const double* qpts,
                               int64_t P, cplx* out);
 __global__ void k_eigh_herm(cplx* A, cplx* V, int n, int64_t B, double* evals, cplx* evecs, int* status);
+// Batched Hermitian eigensolve (A, V: [n*n][B] SoA scratch, A overwritten); 0 or -1 on a launch error.
+int eigh_launch(cudaStream_t st, cplx* A, cplx* V, int n, int64_t B, double* evals, cplx* evecs, int* status);
 __global__ void k_phonon_factors(const double* lam, const cplx* z, int nm, int64_t Q,
                                  const double* mass_of_row, double T, double omega_cut, double* omega,
                                  double* nB, cplx* Z);

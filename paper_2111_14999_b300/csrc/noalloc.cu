@@ -72,8 +72,10 @@ extern "C" int phoebe_gpu_bands_noalloc(int nw, int n_R, const int32_t* R, const
   const int E = nw * nw;
   dim3 g((unsigned)((n_k + 127) / 128), (unsigned)E);
   k_fourier_points_c<<<g, 128, 0, s>>>(reinterpret_cast<const cplx*>(H), R, w, n_R, E, k, n_k, A);
-  k_eigh_herm<<<(unsigned)((n_k + 127) / 128), 128, 0, s>>>(A, V, nw, n_k, eps, reinterpret_cast<cplx*>(U), status);
-  if (cudaGetLastError() != cudaSuccess) return PHOEBE_GPU_ERR_CUDA;
+  if (eigh_launch(s, A, V, nw, n_k, eps, reinterpret_cast<cplx*>(U), status)) {
+    cudaGetLastError();
+    return PHOEBE_GPU_ERR_CUDA;
+  }
   int hs = 0;
   if (cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {

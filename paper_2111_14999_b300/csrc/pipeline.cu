@@ -37,7 +37,7 @@ static int electron_points(phoebe_gpu_ctx* c, const double* kdev, int64_t P, con
   dim3 g((unsigned)((P + 127) / 128), (unsigned)E);
   k_fourier_points_c<<<g, 128, 0, c->stream>>>((const cplx*)c->bufs["H"].p, (const int*)c->bufs["RH"].p,
                                                  (const double*)c->bufs["wH"].p, c->nRH, E, kdev, P, A);
-  k_eigh_herm<<<(unsigned)((P + 127) / 128), 128, 0, c->stream>>>(A, V, nw, P, e, u, status);
+  if (eigh_launch(c->stream, A, V, nw, P, e, u, status)) return fail(c, PHOEBE_GPU_ERR_CUDA, "eigensolver launch failed");
   TRY(launch_check(c, 2));
   int hs = 0;
   CK(c, cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
