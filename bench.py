@@ -482,6 +482,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the many-materials leg")
     ap.add_argument("--no-prate", action="store_true", help="skip the phonon-electron rate leg")
     ap.add_argument("--learned-only", action="store_true", help="only the learned-proposal leg (profiling case)")
+    ap.add_argument("--batch-only", action="store_true", help="only the many-materials leg (profiling case)")
     ap.add_argument("--learned-epochs", type=int, default=0, help="training epochs of the learned leg (0: default)")
     ap.add_argument("--batch-k", type=int, default=64, help="seeded k points per material in the many-materials leg")
     ap.add_argument("--learned-k", type=int, default=512, help="seeded k points of the learned-proposal evaluation")
@@ -499,6 +500,12 @@ def main():
         torch.cuda.set_device(dev)
         if rank == 0:
             print(json.dumps({"learned_sampler": learned_leg(pg, W, dev, torch.cuda.current_stream(), args)}), flush=True)
+        return
+    if args.batch_only:
+        dev = local if torch.cuda.is_available() else 0
+        torch.cuda.set_device(dev)
+        if rank == 0:
+            print(json.dumps({"batched_materials": batch_leg(pg, W, dev, args)}), flush=True)
         return
     dist = None
     if world > 1:

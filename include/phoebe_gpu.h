@@ -68,8 +68,8 @@ typedef enum {
                                   axis on a grid): stage 1 over the k grid (the SPLIT_FP16 GEMM when
                                   the R_e residue tables do not fit), stage 2 for the q whose final
                                   bands can reach the delta window, FP32 on the CUDA cores,
-                                  rotations and deltas fused; needs q-grid sizes Nx <= 256,
-                                  Nz <= 64, nw in {1, 2, 4, 8} and 3na in {3, 6} */,
+                                  rotations and deltas fused; needs q-grid size Nx <= 256,
+                                  nw in {1, 2, 4, 8} and 3na in {3, 6} */,
   PHOEBE_PREC_FP64_DFT = 8     /* linewidths only: the separable grid DFTs of PHOEBE_PREC_FP32_DFT in
                                   FP64 throughout (phase tables, both stages, rotations, Gaussians),
                                   the plain FP64 counterpart of the same algorithm; fixed smearing,

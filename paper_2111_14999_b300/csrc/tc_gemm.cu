@@ -2014,8 +2014,8 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
   if (!fp64 && !((nw == 1 || nw == 2 || nw == 4 || nw == 8) && (nm == 3 || nm == 6)))
     return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "the grid-DFT stage 2 is built for nw in {1, 2, 4, 8} and 3na in {3, 6}");
   const int Nx = gm.nq[0], Ny = gm.nq[1], Nz = gm.nq[2];
-  if (Nz * 16 > 1024 || Nx > 256)
-    return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "the grid-DFT stage 2 needs q-grid sizes Nx <= 256 and Nz <= 64");
+  if (Nx > 256)  // list entries hold jx in 8 bits
+    return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED, "the grid-DFT stage 2 needs q-grid sizes Nx <= 256");
   const int esz = 2, KB = 64;
   const int Kp1 = (2 * nRe + KB - 1) / KB * KB;
   const int64_t C = (int64_t)nRp * nw * nw * nm;

@@ -48,6 +48,15 @@ def test_coarse_k_grid(pg):
     assert err <= RTOL
 
 
+def test_long_z_q_grid(pg):
+    """q grid 4 x 4 x 72 (more than 64 points along z) under k on 2 x 2 x 8: the fused kernel's grid
+    holds one block column per jz, the z sum covers jz and 72 - jz together."""
+    mat, prm = W.toy(seed=2)
+    err = _run(pg, mat, prm.with_(nk=(2, 2, 8), nq=(4, 4, 72)), [0, 3, 9, 17, 26, 31])
+    print(f"long z q grid, grid DFT: max rel err {err:.3e}")
+    assert err <= RTOL
+
+
 def test_odd_k_grid(pg):
     """5^3 grids: no residue equals its own negative except 0."""
     mat, prm = W.toy(seed=1)
