@@ -459,15 +459,16 @@ __global__ void k_state_features(const int* __restrict__ st_k, const int* __rest
 // lphi[s][q] = log phi_s(q), phi_s(q) = sum_{m'} sum_{nu: w >= omega_cut} [(n + 1 - f) D(e - w - e') +
 // (n + f) D(e + w - e')] / w with D(x) = exp(-x^2/sigma^2) for |x| < cut sigma (0 beyond), e = eps_nk,
 // e' = eps_m'k+q, f = f_m'k+q, (w, n) = (hbar w_q nu, n_q nu): the bracket of Eq. 29 with |g|^2 replaced by
-// 1/(hbar w).  Which terms are present is decided in FP64 as in Eq. 29's evaluation (a band with
-// |e - e'| >= reach = omega_max + cut sigma has none); the weights are summed in FP32 (phi is only a
-// proposal: its rounding changes the variance, never the expectation).  -inf where phi = 0.
-// Grid (q blocks, states).
+// 1/(hbar w).  Which terms are present is decided as the FP64 evaluation of Eq. 29 decides it (a band
+// with |e - e'| >= reach = omega_max + cut sigma has none): in FP32 where the value is more than
+// 1e-6 eV from a cut, in FP64 within that margin.  The weights are FP32 (phi is only a proposal: its
+// rounding changes the variance, never the expectation).  -inf where phi = 0.  Grid (q blocks, states).
 __global__ void k_shell_log(const int* __restrict__ st_k, const int* __restrict__ st_b, GridMap gm, int64_t Nq,
                             const double* __restrict__ epsF, const float2* __restrict__ eps2,
                             const double* __restrict__ fF, const double* __restrict__ omega,
-                            const double* __restrict__ nB, int nw, int nm, double omega_cut, double inv_sigma,
-                            double xcut, double reach, float* __restrict__ lphi) {
+                            const float* __restrict__ omf, const float* __restrict__ nBf, int nw, int nm,
+                            double omega_cut, double inv_sigma, double xcut, double reach,
+                            float* __restrict__ lphi) {
   const int s = blockIdx.y;
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= Nq) return;
@@ -476,27 +477,37 @@ __global__ void k_shell_log(const int* __restrict__ st_k, const int* __restrict_
   const int64_t kq = gm.kq_to_fine(k, q);
   const float fis = (float)inv_sigma;
   const float ef = (float)e, reach_f = (float)reach * 1.0001f;  // FP32 screen with a margin far above FP32 rounding
+  // FP32 decisions with a margin: x = de -+ w and w are within 1e-7 eV of their FP64 values, so
+  // only a value within 1e-6 eV of a cut is decided again in FP64
+  constexpr float kTol = 1e-6f;
+  const float xcut_f = (float)xcut, cut_f = (float)omega_cut;
   float phi = 0.f;
   for (int mp = 0; mp < nw; ++mp) {
     if (!(fabsf(ef - eps2[kq * nw + mp].x) < reach_f)) continue;  // no term of this band can be present
     const double de = e - epsF[kq * nw + mp];
     if (!(fabs(de) < reach)) continue;
     const float f = (float)fF[kq * nw + mp];
+    const float de_f = (float)de;
     for (int v = 0; v < nm; ++v) {
-      const double w = omega[q * nm + v];
-      if (!(w >= omega_cut)) continue;
-      const float n = (float)nB[q * nm + v];
-      const double x1 = de - w, x2 = de + w;
+      const float wf = omf[q * nm + v];
+      bool alive = wf > cut_f + kTol;
+      if (!alive && !(wf < cut_f - kTol)) alive = omega[q * nm + v] >= omega_cut;
+      if (!alive) continue;
+      const float n = nBf[q * nm + v];
+      const float x1 = de_f - wf, x2 = de_f + wf;
+      bool in1 = fabsf(x1) < xcut_f - kTol, in2 = fabsf(x2) < xcut_f - kTol;
+      if (!in1 && !(fabsf(x1) > xcut_f + kTol)) in1 = fabs(de - omega[q * nm + v]) < xcut;
+      if (!in2 && !(fabsf(x2) > xcut_f + kTol)) in2 = fabs(de + omega[q * nm + v]) < xcut;
       float d = 0.f;
-      if (fabs(x1) < xcut) {
-        const float t = (float)x1 * fis;
+      if (in1) {
+        const float t = x1 * fis;
         d = fmaf(n + 1.f - f, __expf(-t * t), d);
       }
-      if (fabs(x2) < xcut) {
-        const float t = (float)x2 * fis;
+      if (in2) {
+        const float t = x2 * fis;
         d = fmaf(n + f, __expf(-t * t), d);
       }
-      phi = fmaf(d, (float)(1.0 / w), phi);
+      phi = fmaf(d, 1.f / wf, phi);
     }
   }
   lphi[(int64_t)s * Nq + q] = phi > 0.f ? logf(phi) : -INFINITY;
@@ -1055,8 +1066,8 @@ int is_batch(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& g
     if (!lphi) return st;
     dim3 g((unsigned)((Nq + 255) / 256), (unsigned)S);
     const double xcut = p->delta_cut_sigmas * p->sigma_eV;
-    k_shell_log<<<g, 256, 0, c->stream>>>(b.st_k, b.st_b, gm, Nq, t.epsF, t.eps2, t.fF, t.omega, t.nB, NW, NM,
-                                          p->omega_cut_eV, 1.0 / p->sigma_eV, xcut,
+    k_shell_log<<<g, 256, 0, c->stream>>>(b.st_k, b.st_b, gm, Nq, t.epsF, t.eps2, t.fF, t.omega, omf, nBf, NW,
+                                          NM, p->omega_cut_eV, 1.0 / p->sigma_eV, xcut,
                                           (t.omega_max + xcut) * (1.0 + 1e-12), lphi);
     TRY(launched(c, 1));
   }
