@@ -569,6 +569,13 @@ def main():
         peak_med = roof["peak"] * clocks["sm_mhz"] / clocks["sm_max_mhz"]
         roof["peak_at_median_clock"] = peak_med
         roof["frac_at_median_clock"] = roof["achieved"] / peak_med
+    if args.precision == 7 and roof.get("achieved"):
+        # the FP32 FMA rate measured on this GPU by the library's probe (8 independent FMA chains per
+        # thread, 8 blocks per SM), beside the rate from unit counts
+        tf, tms = ctx.fp32_rate()
+        roof["peak_measured_fp32_fma"] = tf
+        roof["frac_of_measured_fp32_fma"] = roof["achieved"] / tf if tf > 0 else None
+        roof["fp32_fma_probe_ms"] = tms
 
     extra = {}
     g_head = g_out.cpu().numpy().copy()

@@ -444,6 +444,13 @@ int phoebe_gpu_bands_noalloc(int nw, int n_R, const int32_t* R, const double* w,
  * counterpart. */
 int phoebe_gpu_selftest_wait(phoebe_gpu_ctx* ctx, int publish, int64_t limit_us);
 
+/* Measured FP32 FMA rate of the device (the denominator of the CUDA-core roofline): 8 blocks of
+ * 256 threads per SM, each thread 8 independent chains of 2^14 dependent FMAs; the fastest of three
+ * timed launches after a warm-up, by CUDA events on the context's stream.  tflops (host, required)
+ * = 2 flop x FMAs / time; ms (host, may be NULL) = that launch's time.  The paper has no
+ * counterpart. */
+int phoebe_gpu_selftest_fp32_rate(phoebe_gpu_ctx* ctx, double* tflops, double* ms);
+
 /* Physical constants compiled into the library: out[0] = k_B (eV/K),
  * out[1] = hbar*sqrt(eV/(A^2 amu)) (eV), out[2] = hbar^2/(amu eV A^2).  Needs no GPU. */
 void phoebe_gpu_constants(double out[3]);

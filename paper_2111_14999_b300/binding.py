@@ -38,7 +38,7 @@ EXPORTED = (
     "phoebe_gpu_train_opts_default", "phoebe_gpu_sampler_train", "phoebe_gpu_q_contributions",
     "phoebe_gpu_mlp_loss_grad", "phoebe_gpu_is_uniforms", "phoebe_gpu_mlp_scores",
     "phoebe_gpu_batch_opts_default", "phoebe_gpu_linewidths_rta_batch", "phoebe_gpu_transport_rta",
-    "phoebe_gpu_selftest_wait", "phoebe_gpu_phonon_rates_elph", "phoebe_gpu_set_lattice",
+    "phoebe_gpu_selftest_wait", "phoebe_gpu_selftest_fp32_rate", "phoebe_gpu_phonon_rates_elph", "phoebe_gpu_set_lattice",
     "phoebe_gpu_set_polar", "phoebe_gpu_set_force_constants3", "phoebe_gpu_three_phonon_rates",
 )
 
@@ -145,6 +145,7 @@ def _load() -> C.CDLL:
         "phoebe_gpu_set_force_constants3": (I, [P, C.c_int, P, P, P, P]),
         "phoebe_gpu_three_phonon_rates": (I, [P, C.POINTER(RTAParams), C.c_int64, P]),
         "phoebe_gpu_selftest_wait": (I, [P, I, I64]),
+        "phoebe_gpu_selftest_fp32_rate": (I, [P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -459,6 +460,12 @@ class PhoebeGPU:
         u = np.empty(int(n), dtype=np.float64)
         self._check(lib.phoebe_gpu_is_uniforms(self._ctx, int(seed), int(k), int(n), _ptr(u)))
         return u
+
+    def fp32_rate(self) -> tuple:
+        """Measured FP32 FMA rate of the device: (TFLOP/s, ms of the timed launch)."""
+        t, ms = C.c_double(0.0), C.c_double(0.0)
+        self._check(lib.phoebe_gpu_selftest_fp32_rate(self._ctx, C.byref(t), C.byref(ms)))
+        return t.value, ms.value
 
 
 def linewidths_rta_batch(jobs, capacities=None, **opts):
