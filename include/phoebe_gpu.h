@@ -427,7 +427,7 @@ int phoebe_gpu_linewidths_rta_batch(phoebe_gpu_batch_item* items, int n, phoebe_
  *                after the stream has finished it.
  * Returns PHOEBE_GPU_ERR_NOMEM without launching anything when 2 * n_k * nw^2 * 16
  * bytes exceed the 16 MiB scratch, PHOEBE_GPU_ERR_ARG for bad sizes or NULL
- * pointers, PHOEBE_GPU_ERR_NOTCONVERGED if an eigensolve hit its sweep cap.
+ * pointers, PHOEBE_GPU_ERR_NOTCONVERGED if an eigensolve hit its QR step cap.
  * The first call on each device looks up the scratch address on the current device
  * (one-time set-up); make that first call before any stream capture begins.  Every
  * call reads its convergence word back and synchronises the stream, so a call on a

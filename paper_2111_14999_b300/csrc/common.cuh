@@ -44,6 +44,23 @@ __host__ __device__ __forceinline__ void cfma_conja(cplx& acc, cplx a, cplx b) {
 }
 __host__ __device__ __forceinline__ double cabs2(cplx a) { return a.re * a.re + a.im * a.im; }
 
+// Lets `kernel` take as much dynamic shared memory as the device allows beside its static shared
+// memory.  The limit is one value per kernel for the whole process: setting each launch's own size
+// would let host threads that launch the same kernel with different sizes (concurrent planning of a
+// batch) lower it under one another's launches.  One value for every caller removes that race; how
+// much shared memory a block gets is still the launch's own size.
+template <typename K>
+inline cudaError_t allow_dynamic_smem(K kernel) {
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  return e;
+}
+
 __device__ __forceinline__ cplx ldc(const cplx* p) {
   double2 v = __ldg(reinterpret_cast<const double2*>(p));
   return {v.x, v.y};

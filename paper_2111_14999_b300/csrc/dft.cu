@@ -792,9 +792,7 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
 template <int NW, int NM, int SPLIT, bool PR, int NQ, bool AD, bool PL = false>
 static int launch_yx_t(cudaStream_t st, const DftXArgs& a, int S) {
   const size_t smem = dft_smem_bytes(a.P, a.Bx, a.By, NW, NM, a.Nx, a.Ny, a.K, a.G);
-  if (cudaFuncSetAttribute(k_dft_yx_elph<NW, NM, SPLIT, PR, NQ, AD, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess)
-    return -1;
+  if (allow_dynamic_smem(k_dft_yx_elph<NW, NM, SPLIT, PR, NQ, AD, PL>) != cudaSuccess) return -1;
   dim3 grid((unsigned)a.Nz, (unsigned)S);
   k_dft_yx_elph<NW, NM, SPLIT, PR, NQ, AD, PL><<<grid, kDftXThreads, smem, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
@@ -821,7 +819,7 @@ static int launch_yx(cudaStream_t st, const DftXArgs& a, int S) {
 
 int dft_launch(cudaStream_t st, const DftZArgs& z, const DftXArgs& x, int S, int nw, int nm, int ne_plane_max) {
   const size_t sm1 = dft_z_smem_bytes(ne_plane_max, z.E, z.Nz, z.Bz);
-  if (cudaFuncSetAttribute(k_dft_z, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1) != cudaSuccess) return -1;
+  if (allow_dynamic_smem(k_dft_z) != cudaSuccess) return -1;
   k_dft_z<<<dim3((unsigned)x.Bx, (unsigned)S), 256, sm1, st>>>(z);
   if (cudaGetLastError() != cudaSuccess) return -1;
   if (nw == 8 && nm == 6) return launch_yx<8, 6, dft_split(8)>(st, x, S);

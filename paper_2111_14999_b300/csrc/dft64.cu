@@ -119,7 +119,7 @@ template <int GZ>
 static int s64_launch_t(cudaStream_t st, const S64Args& a, int planes) {
   const S1Args& i = a.i;
   const size_t smem = s64_smem_bytes(i.nRe, i.Pe, i.Bz, i.Gz, i.nky, i.By, i.nkz);
-  if (cudaFuncSetAttribute(k_s1_dft64<GZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (allow_dynamic_smem(k_s1_dft64<GZ>) != cudaSuccess)
     return -1;
   dim3 grid((unsigned)((i.C + kS64Cols - 1) / kS64Cols), (unsigned)planes);
   k_s1_dft64<GZ><<<grid, 256, smem, st>>>(a);
@@ -400,11 +400,11 @@ size_t dft64_smem_bytes(int P, int Bx, int By, int E, int Nx, int Ny, int K, int
 
 int dft64_launch(cudaStream_t st, const DftZ64Args& z, const DftX64Args& x, int S, int ne_plane_max) {
   const size_t sm1 = dft64_z_smem_bytes(ne_plane_max, z.E, z.Nz, z.Bz);
-  if (cudaFuncSetAttribute(k_dft_z64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1) != cudaSuccess) return -1;
+  if (allow_dynamic_smem(k_dft_z64) != cudaSuccess) return -1;
   k_dft_z64<<<dim3((unsigned)x.Bx, (unsigned)S), 256, sm1, st>>>(z);
   if (cudaGetLastError() != cudaSuccess) return -1;
   const size_t sm2 = dft64_smem_bytes(x.P, x.Bx, x.By, x.nw * x.nm, x.Nx, x.Ny, x.K, x.G);
-  if (cudaFuncSetAttribute(k_dft_yx64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2) != cudaSuccess)
+  if (allow_dynamic_smem(k_dft_yx64) != cudaSuccess)
     return -1;
   k_dft_yx64<<<dim3((unsigned)x.Nz, (unsigned)S), 256, sm2, st>>>(x);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;

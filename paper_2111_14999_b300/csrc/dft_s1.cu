@@ -146,7 +146,7 @@ size_t s1_smem_bytes(int nRe, int Pe, int Bz, int Gz, int nky, int By, int nkz) 
 template <int GZ>
 static int s1_launch_t(cudaStream_t st, const S1Args& a, int planes) {
   const size_t smem = s1_smem_bytes(a.nRe, a.Pe, a.Bz, a.Gz, a.nky, a.By, a.nkz);
-  if (cudaFuncSetAttribute(k_s1_dft<GZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (allow_dynamic_smem(k_s1_dft<GZ>) != cudaSuccess)
     return -1;
   dim3 grid((unsigned)((a.C + kS1Cols - 1) / kS1Cols), (unsigned)planes);
   k_s1_dft<GZ><<<grid, 256, smem, st>>>(a);

@@ -109,7 +109,7 @@ size_t elph_generic_smem(int nw, int nm) {
 template <int MAXNM>
 static int launch_nm(cudaStream_t s, const ElphGenericArgs& a, int64_t rows) {
   const size_t smem = elph_generic_smem(a.nw, a.nm);
-  if (cudaFuncSetAttribute(k_elph_generic<MAXNM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  if (allow_dynamic_smem(k_elph_generic<MAXNM>) !=
       cudaSuccess)
     return -1;
   dim3 grid((unsigned)rows, (unsigned)((a.S + kGenericStatesPerBlock - 1) / kGenericStatesPerBlock));

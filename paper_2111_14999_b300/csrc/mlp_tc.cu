@@ -12,6 +12,7 @@
 // Every wait is bounded (2 s); on expiry the kernel raises an error flag and unwinds.
 #include <cuda_fp16.h>
 
+#include "common.cuh"
 #include "mlp_tc.h"
 #include "tc_ptx.cuh"
 
@@ -282,7 +283,7 @@ size_t mlp_tc_smem_bytes() {
 int mlp_tc_launch(cudaStream_t s, int num_sms, const MlpTcArgs& a) {
   if (a.ntiles <= 0) return 0;
   const size_t smem = mlp_tc_smem_bytes();
-  if (cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (allow_dynamic_smem(k_mlp_tc) != cudaSuccess)
     return -1;
   const int64_t grid = std::min<int64_t>(a.ntiles, num_sms > 0 ? num_sms : 148);
   k_mlp_tc<<<(unsigned)grid, kThreads, smem, s>>>(a);

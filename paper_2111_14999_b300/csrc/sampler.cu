@@ -1157,7 +1157,7 @@ int is_batch(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const GridMap& g
   if (smem > 227 * 1024)
     return fail(c, PHOEBE_GPU_ERR_UNSUPPORTED,
                 "sampled q sums keep one state's R_p sum in shared memory: %zu bytes needed, 227 KB available", smem);
-  CK(c, cudaFuncSetAttribute(k_pairs_sampled<NW, NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CK(c, allow_dynamic_smem(k_pairs_sampled<NW, NM>));
   tm.begin(c);
   dim3 grid((unsigned)((a.ndraw + kDrawChunk - 1) / kDrawChunk), (unsigned)S);
   k_pairs_sampled<NW, NM><<<grid, 256, smem, c->stream>>>(a);

@@ -938,7 +938,7 @@ static int launch_gemm(phoebe_gpu_ctx* c, const CUtensorMap* A, const CUtensorMa
   a.group_m = std::min(a.group_m, a.m_tiles);
   a.ntiles = a.m_tiles * a.n_tiles;
   int sm = a.stages * stage_bytes(Epi::BN, NSPLIT) + (int)((Epi::SMEM_BYTES + 1023u) & ~1023u) + 1024 + 512;
-  CK(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(c, allow_dynamic_smem(kern));
   int per_sm = 0;
   CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTcThreads, sm));
   if (per_sm <= 0) return fail(c, PHOEBE_GPU_ERR_CUDA, "the tensor-core GEMM (%d B smem) does not fit on an SM", sm);

@@ -208,7 +208,7 @@ template <int NM>
 static int launch_s2(cudaStream_t st, const Ph3S2Args& a) {
   const size_t smem = sizeof(float2) * ((size_t)a.NRp * NM * NM * NM + (size_t)kPh3Tile * a.NRp);
   if (smem > 227 * 1024) return -2;
-  if (cudaFuncSetAttribute(k_ph3_stage2<NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (allow_dynamic_smem(k_ph3_stage2<NM>) != cudaSuccess)
     return -1;
   dim3 grid((unsigned)((a.Q + kPh3Tile - 1) / kPh3Tile), (unsigned)a.Q);
   k_ph3_stage2<NM><<<grid, kPh3Tile * NM, smem, st>>>(a);
