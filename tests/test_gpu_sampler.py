@@ -120,6 +120,27 @@ def test_features_and_q_terms_vs_oracle(ctx, which):
     assert np.allclose(st[2][nondeg], raw[nondeg], rtol=1e-4)
 
 
+def test_shell_factor_decisions_within_the_fp32_margin(ctx):
+    """The shell factor decides which terms are present in FP32 only where the value is more than
+    1e-6 eV from a cut, in FP64 inside that margin.  On the Einstein crystal every mode has the one
+    frequency w0, so a mode cut 3e-7 eV below w0 and a Gaussian cut 4e-7 eV above |e - e'| = w0
+    (every q with e(k+q) = e(k)) put those decisions inside the margin: the zero pattern and the
+    values must still be the FP64 oracle's."""
+    mat, prm = W.tb_einstein(eps0=0.05, t=0.25, n=8, mu=0.1, hop_phase=0.3)
+    w0 = elph.HBAR_OMEGA_EV * np.sqrt(0.215)
+    prm = prm.with_(omega_cut_eV=w0 - 3e-7, delta_cut_sigmas=(w0 + 4e-7) / prm.sigma_eV,
+                    k_subset=np.array([0, 9, 73, 200, 511]), precision=PREC)
+    ctx.set_material(mat)
+    out = ctx.q_contributions(prm, log_shell=True)
+    ki, bd, lp = out[0], out[1], out[4]
+    tab = elph.electron_table(mat, prm)
+    lpo = S.log_shell(S.shell_factor(mat, prm, ki, bd, table=tab))
+    assert np.any(np.isfinite(lpo)) and not np.all(np.isfinite(lpo))
+    assert np.array_equal(np.isfinite(lp), np.isfinite(lpo))
+    fin = np.isfinite(lpo)
+    assert np.max(np.abs(lp[fin] - lpo[fin])) <= 1e-5 * max(1.0, np.max(np.abs(lpo[fin])))
+
+
 @pytest.mark.parametrize("mode", ["uniform", "learned", "shell"])
 def test_sampled_gamma_equals_oracle_estimate(ctx, mode):
     # same seed, same parameters: the same draws, so the estimates agree to the contraction tolerance
