@@ -1,14 +1,16 @@
 // Scores of the learned q proposal for every (state, q) row on the tensor cores (inference
 // only; training runs on the CUDA-core kernels of sampler.cu).  The network is
-// z = w4 . silu(W3 silu(W2 silu(W1 x + b1) + b2) + b3) + b4, x = (q~, eps - mu, v); the two
-// 128 x 128 layers run as tcgen05 MMAs (M = 128 rows, N = 128 neurons, K = 128) with FP16
-// operands (the BF16-rounded parameters are exact in FP16 apart from values below 2^-14,
-// which lose low bits) and FP32 accumulation in TMEM; the 7-input layer, SiLU and the head
-// run on the CUDA cores.
+// z = w4 . silu(W3 silu(W2 silu(W1 x + b1) + b2) + b3) + b4, x = (q~, eps - mu, v); the three
+// hidden layers run as tcgen05 MMAs (M = 128 rows, N = 128 neurons) with FP16 operands (the
+// BF16-rounded parameters are exact in FP16 apart from values below 2^-14, which lose low bits)
+// and FP32 accumulation in TMEM.  The 7-input layer is one MMA with K = 16: the row
+// (q~, eps - mu, v, 1, 0 ...) against (W1, b1, 0 ...), so its bias comes from the constant input.
+// SiLU, the other biases and the head run on the CUDA cores.
 //
 // One persistent CTA per SM: two groups of 4 warps (thread = row of a 128-row tile) work on
 // alternate tiles so that one group's SiLU overlaps the other's MMAs; warp 8 issues the MMAs.
-// Per tile and group: H1 -> smem, MMA layer 2 -> TMEM, H2 -> smem, MMA layer 3 -> TMEM, head.
+// Per tile and group: X -> smem, MMA layer 1 -> TMEM slot a, H1 -> smem, MMA layer 2 -> slot b,
+// H2 -> smem, MMA layer 3 -> slot a, head.
 // Every wait is bounded (2 s); on expiry the kernel raises an error flag and unwinds.
 #include <cuda_fp16.h>
 
@@ -56,7 +58,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(MlpTcArgs a) {
   uint8_t* W2s = smem;
   uint8_t* W3s = smem + kOpBytes;
   uint8_t* Hs = smem + 2 * kOpBytes;  // two operands, one per group
-  float* b2 = reinterpret_cast<float*>(smem + 4 * kOpBytes);  // 16-byte aligned
+  uint8_t* W1s = smem + 4 * kOpBytes;  // one swizzle atom: K chunks 0 and 1 of each neuron row
+  float* b2 = reinterpret_cast<float*>(smem + 4 * kOpBytes + kAtomBytes);  // 16-byte aligned
   float* b3 = b2 + 128;
   float* w4 = b3 + 128;
   float* b4 = w4 + 128;
@@ -74,6 +77,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(MlpTcArgs a) {
     const uint4 v3 = reinterpret_cast<const uint4*>(a.W3h)[idx];
     *reinterpret_cast<uint4*>(W2s + sw_offset(row, chunk)) = v2;
     *reinterpret_cast<uint4*>(W3s + sw_offset(row, chunk)) = v3;
+  }
+  for (int j = tid; j < 128; j += kThreads) {  // W1 row j: (W1[j][0..6], b1[j]) then 8 zeros
+    const float* wj = a.P + kMlpOffW1 + j * 7;
+    const uint4 c0 = make_uint4(h2_bits(__floats2half2_rn(wj[0], wj[1])), h2_bits(__floats2half2_rn(wj[2], wj[3])),
+                                h2_bits(__floats2half2_rn(wj[4], wj[5])),
+                                h2_bits(__floats2half2_rn(wj[6], a.P[kMlpOffB1 + j])));
+    *reinterpret_cast<uint4*>(W1s + sw_offset(j, 0)) = c0;
+    *reinterpret_cast<uint4*>(W1s + sw_offset(j, 1)) = make_uint4(0u, 0u, 0u, 0u);
   }
   for (int i = tid; i < 128; i += kThreads) {
     b2[i] = a.P[kMlpOffB2 + i];
@@ -109,27 +120,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(MlpTcArgs a) {
       const uint32_t idesc = idesc_m128(128u, 0u);  // FP16 A and B, FP32 accumulate
       uint32_t hph[2] = {0u, 0u};
       bool ok = true;
+      // layer l of tile i: l = 0 the 7-input layer (one K = 16 step) into slot a, l = 1 layer 2 into
+      // slot b, l = 2 layer 3 into slot a again (its layer-1 result was read before H1 was published)
       auto layer = [&](int64_t i, int l) -> bool {
         const int g = (int)(i & 1);
         if (!mbar_wait(hready + g, hph[g] & 1u, abort_flag)) return false;
         ++hph[g];
         tc_fence_after();
         const uint32_t abase = smem_u32(Hs + g * kOpBytes);
-        const uint32_t bbase = smem_u32(l == 0 ? W2s : W3s);
-        const uint32_t d = tmem_base + (uint32_t)(g * 2 + l) * 128u;
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
+        const uint32_t bbase = smem_u32(l == 0 ? W1s : l == 1 ? W2s : W3s);
+        const uint32_t d = tmem_base + (uint32_t)(g * 2 + (l == 1 ? 1 : 0)) * 128u;
+        const int nk = l == 0 ? 1 : 8;
+        for (int kk = 0; kk < nk; ++kk) {
           const uint32_t off = (uint32_t)(kk >> 2) * kAtomBytes + (uint32_t)(kk & 3) * 32u;
           mma<0>(d, sdesc_k128(abase + off), sdesc_k128(bbase + off), idesc, kk > 0 ? 1u : 0u);
         }
         mma_commit(dready + g);
         return true;
       };
-      for (int64_t i = 0; i < n_local && ok; ++i) {
-        ok = layer(i, 0);
-        if (ok && i >= 1) ok = layer(i - 1, 1);
-      }
-      if (ok && n_local > 0) layer(n_local - 1, 1);
+      // tiles in pairs, one per group, layer by layer: each group's three layers stay in order
+      for (int64_t p0 = 0; p0 < n_local && ok; p0 += 2)
+        for (int l = 0; l < 3 && ok; ++l)
+          for (int64_t i = p0; i < p0 + 2 && i < n_local && ok; ++i) ok = layer(i, l);
       // no MMA may be in flight when TMEM is released
       mma_commit(drain);
       const unsigned long long t0 = globaltimer();
@@ -162,34 +174,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(MlpTcArgs a) {
         q = (t % a.tiles_per_state) * 128 + row;
         valid = q < a.Nq;
       }
-      float qv[3] = {0.f, 0.f, 0.f};
-      if (valid)
+      float qv[3] = {0.f, 0.f, 0.f}, fv[4] = {0.f, 0.f, 0.f, 0.f};
+      if (valid) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) qv[d] = a.qt[q * 3 + d];
-      // layer 1 (7 inputs) and SiLU, 8 neurons per 16-byte chunk; the state's part of the
-      // 7-input layer is folded into w1c[s][j].w
-      const float4* wc = a.w1c + (int64_t)s * 128;
-#pragma unroll 2
-      for (int chunk = 0; chunk < 16; ++chunk) {
-        uint32_t w[4];
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          float x[2];
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const float4 c4 = __ldg(wc + chunk * 8 + p * 2 + e);
-            x[e] = fmaf(c4.x, qv[0], fmaf(c4.y, qv[1], fmaf(c4.z, qv[2], c4.w)));
-          }
-          w[p] = silu2(x[0], x[1]);
-        }
-        *reinterpret_cast<uint4*>(H + sw_offset(row, chunk)) = make_uint4(w[0], w[1], w[2], w[3]);
+        for (int d = 0; d < 4; ++d) fv[d] = a.feat[(int64_t)s * 4 + d];
       }
+      // the row of the 7-input layer's MMA: (q~, eps - mu, v, 1) in K chunk 0, zeros in chunk 1
+      *reinterpret_cast<uint4*>(H + sw_offset(row, 0)) =
+          make_uint4(h2_bits(__floats2half2_rn(qv[0], qv[1])), h2_bits(__floats2half2_rn(qv[2], fv[0])),
+                     h2_bits(__floats2half2_rn(fv[1], fv[2])), h2_bits(__floats2half2_rn(fv[3], 1.f)));
+      *reinterpret_cast<uint4*>(H + sw_offset(row, 1)) = make_uint4(0u, 0u, 0u, 0u);
       fence_async_smem();
       mbar_arrive(hready + g);
       bool ok = true;
       float z = 0.f;
 #pragma unroll 1
-      for (int l = 0; l < 2 && ok; ++l) {
+      for (int l = 0; l < 3 && ok; ++l) {  // layer-1, layer-2 and layer-3 results
         int wv = 1;
         if (lane == 0) wv = mbar_wait(dready + g, dph & 1u, abort_flag) ? 1 : 0;
         wv = __shfl_sync(0xffffffffu, wv, 0);
@@ -199,8 +201,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(MlpTcArgs a) {
           break;
         }
         tc_fence_after();
-        const uint32_t taddr = tmem_base + ((uint32_t)(wq * 32) << 16) + (uint32_t)(g * 2 + l) * 128u;
-        const float* bias = l == 0 ? b2 : b3;
+        const uint32_t taddr = tmem_base + ((uint32_t)(wq * 32) << 16) + (uint32_t)(g * 2 + (l == 1 ? 1 : 0)) * 128u;
+        const float* bias = l == 1 ? b2 : b3;  // layer 1 has its bias from the constant input
 #pragma unroll 1
         for (int c0 = 0; c0 < 128; c0 += 32) {
           float v[32];
@@ -208,13 +210,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(MlpTcArgs a) {
 #pragma unroll
           for (int cc = 0; cc < 4; ++cc) {
             const int j0 = c0 + cc * 8;
-            const float4 bA = reinterpret_cast<const float4*>(bias + j0)[0];
-            const float4 bB = reinterpret_cast<const float4*>(bias + j0)[1];
+            const float4 bA = l == 0 ? make_float4(0.f, 0.f, 0.f, 0.f) : reinterpret_cast<const float4*>(bias + j0)[0];
+            const float4 bB = l == 0 ? make_float4(0.f, 0.f, 0.f, 0.f) : reinterpret_cast<const float4*>(bias + j0)[1];
             const float bv[8] = {bA.x, bA.y, bA.z, bA.w, bB.x, bB.y, bB.z, bB.w};
             uint32_t w[4];
 #pragma unroll
             for (int p = 0; p < 4; ++p) w[p] = silu2(v[cc * 8 + p * 2] + bv[p * 2], v[cc * 8 + p * 2 + 1] + bv[p * 2 + 1]);
-            if (l == 0) {
+            if (l < 2) {
               *reinterpret_cast<uint4*>(H + sw_offset(row, (c0 >> 3) + cc)) = make_uint4(w[0], w[1], w[2], w[3]);
             } else {
               const float4 wA = reinterpret_cast<const float4*>(w4 + j0)[0];
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(MlpTcArgs a) {
           }
         }
         tc_fence_before();
-        if (l == 0) {
+        if (l < 2) {
           fence_async_smem();
           mbar_arrive(hready + g);
         }
@@ -248,27 +250,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(MlpTcArgs a) {
   if (tid == 0 && *abort_flag) atomicOr(a.err, 1);
 }
 
-// w1c[s][j] = (W1[j][0], W1[j][1], W1[j][2], b1[j] + sum_i W1[j][3+i] feat[s][i]): the 7-input layer
-// with the state's features folded in.
-__global__ void k_w1c(const float* __restrict__ P, const float* __restrict__ feat, int S, float4* __restrict__ w1c) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= S * 128) return;
-  const int s = t >> 7, j = t & 127;
-  const float* wj = P + kMlpOffW1 + j * 7;
-  const float* f = feat + (int64_t)s * 4;
-  float c = P[kMlpOffB1 + j];
-  c = fmaf(wj[3], f[0], c);
-  c = fmaf(wj[4], f[1], c);
-  c = fmaf(wj[5], f[2], c);
-  c = fmaf(wj[6], f[3], c);
-  w1c[t] = make_float4(wj[0], wj[1], wj[2], c);
-}
-
-int mlp_tc_w1c(cudaStream_t s, const float* P, const float* feat, int S, float4* w1c) {
-  k_w1c<<<(S * 128 + 255) / 256, 256, 0, s>>>(P, feat, S, w1c);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
-}
-
 __global__ void k_params_half(const float* __restrict__ P, __half* __restrict__ W2h, __half* __restrict__ W3h) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 128 * 128) return;
@@ -277,7 +258,7 @@ __global__ void k_params_half(const float* __restrict__ P, __half* __restrict__ 
 }
 
 size_t mlp_tc_smem_bytes() {
-  return 1024 + 4 * kOpBytes + sizeof(float) * (3 * 128 + 4) + 8 * 6 + 16;
+  return 1024 + 4 * kOpBytes + kAtomBytes + sizeof(float) * (3 * 128 + 4) + 8 * 6 + 16;
 }
 
 int mlp_tc_launch(cudaStream_t s, int num_sms, const MlpTcArgs& a) {

@@ -23,7 +23,7 @@ struct MlpTcArgs {
   const __half* W3h;       // [128][128]
   const float* P;          // parameter blob, BF16-rounded values
   const float* qt;         // [Nq][3] wrapped q
-  const float4* w1c;       // [S][128] 7-input layer with the state's features folded in
+  const float* feat;       // [S][4] the state features (eps - mu, hbar v)
   int64_t Nq;
   int64_t tiles_per_state; // ceil(Nq / 128)
   int64_t ntiles;          // S * tiles_per_state
@@ -39,6 +39,5 @@ struct MlpTcArgs {
 size_t mlp_tc_smem_bytes();
 int mlp_tc_params(cudaStream_t s, const float* P, __half* W2h, __half* W3h);
 int mlp_tc_launch(cudaStream_t s, int num_sms, const MlpTcArgs& a);
-int mlp_tc_w1c(cudaStream_t s, const float* P, const float* feat, int S, float4* w1c);
 
 }  // namespace phx

@@ -953,18 +953,12 @@ static int network_scores(phoebe_gpu_ctx* c, const float* qt, const float* feat,
       cudaGetLastError();
       return fail(c, PHOEBE_GPU_ERR_CUDA, "parameter conversion for the tensor-core network failed");
     }
-    float4* w1c = (float4*)ensure(c, "mlp_w1c", sizeof(float4) * (size_t)S * kNh, &st);
-    if (!w1c) return st;
-    if (mlp_tc_w1c(c->stream, Wr, feat, S, w1c) != 0) {
-      cudaGetLastError();
-      return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the first-layer fold failed");
-    }
     MlpTcArgs ma;
     ma.W2h = W2h;
     ma.W3h = W3h;
     ma.P = Wr;
     ma.qt = qt;
-    ma.w1c = w1c;
+    ma.feat = feat;
     ma.Nq = Nq;
     ma.tiles_per_state = (Nq + 127) / 128;
     ma.ntiles = (int64_t)S * ma.tiles_per_state;
@@ -976,7 +970,7 @@ static int network_scores(phoebe_gpu_ctx* c, const float* qt, const float* feat,
       cudaGetLastError();
       return fail(c, PHOEBE_GPU_ERR_CUDA, "launch of the tensor-core network failed");
     }
-    c->launches += 3;
+    c->launches += 2;
     int herr = 0;
     CK(c, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
