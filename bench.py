@@ -288,6 +288,28 @@ def learned_leg(pg, W, dev, stream, args) -> dict:
     }
 
 
+def mlp_leg(pg, dev, n_states: int = 49, n: int = 80, reps: int = 4) -> dict:
+    """The proposal network's tensor-core scoring alone: every q of an n^3 grid for n_states seeded
+    feature rows, randomly initialised parameters; device time of the scoring by CUDA events (the
+    fastest of reps calls after a warm-up)."""
+    ctx = pg.PhoebeGPU(dev)
+    ctx.sampler_init(1)
+    rng = np.random.default_rng(3)
+    feat = np.column_stack([rng.uniform(-0.5, 0.5, n_states), rng.normal(0, 1.5, (n_states, 3))]).astype(np.float32)
+    ctx.set_profiling(True)
+    ctx.mlp_scores(feat, (n, n, n), tensor_cores=True)
+    times = []
+    for _ in range(reps):
+        ctx.mlp_scores(feat, (n, n, n), tensor_cores=True)
+        times.append(ctx.stats()["sampler_ms"])
+    best = min(times)
+    ctx.close()
+    rows = n_states * n ** 3
+    return {"rows": rows, "ms": best, "rows_per_s": rows / (best / 1e3),
+            "network_tflops": rows * 2.0 * (2 * 128 * 128 + 8 * 128 + 128) / (best / 1e3) / 1e12,
+            "workload": f"{n_states} seeded feature rows x every q of {n}^3, tensor-core scoring"}
+
+
 def prate_leg(pg, ctx, prm, mat, ms_linewidths: float) -> dict:
     """Phonon-electron rates P_{q nu} (Sec. 4.3) of the same Si-like workload: one call runs the whole
     linewidth pipeline with the rate accumulated in the grid-DFT epilogue; timed against the
@@ -483,6 +505,7 @@ def main():
     ap.add_argument("--no-prate", action="store_true", help="skip the phonon-electron rate leg")
     ap.add_argument("--learned-only", action="store_true", help="only the learned-proposal leg (profiling case)")
     ap.add_argument("--batch-only", action="store_true", help="only the many-materials leg (profiling case)")
+    ap.add_argument("--mlp-only", action="store_true", help="only the proposal network's scoring rate (profiling case)")
     ap.add_argument("--learned-epochs", type=int, default=0, help="training epochs of the learned leg (0: default)")
     ap.add_argument("--batch-k", type=int, default=64, help="seeded k points per material in the many-materials leg")
     ap.add_argument("--learned-k", type=int, default=512, help="seeded k points of the learned-proposal evaluation")
@@ -500,6 +523,12 @@ def main():
         torch.cuda.set_device(dev)
         if rank == 0:
             print(json.dumps({"learned_sampler": learned_leg(pg, W, dev, torch.cuda.current_stream(), args)}), flush=True)
+        return
+    if args.mlp_only:
+        dev = local if torch.cuda.is_available() else 0
+        torch.cuda.set_device(dev)
+        if rank == 0:
+            print(json.dumps({"mlp_network": mlp_leg(pg, dev)}), flush=True)
         return
     if args.batch_only:
         dev = local if torch.cuda.is_available() else 0

@@ -1518,7 +1518,11 @@ extern "C" int phoebe_gpu_mlp_scores(phoebe_gpu_ctx* c, int n_states, const floa
   if (!zd) return st;
   k_wrapped_q<<<(unsigned)((Nq + 255) / 256), 256, 0, c->stream>>>(nq[0], nq[1], nq[2], Nq, qt);
   TRY(launched(c, 1));
+  c->stats.sampler_ms = 0.0;  // with profiling on: the device time of the scoring alone
+  Timer tm;
+  tm.begin(c);
   TRY(network_scores(c, qt, (const float*)dfeat, n_states, Nq, tensor_cores != 0, zd));
+  tm.end(c, &c->stats.sampler_ms);
   CK(c, cudaMemcpyAsync(z, zd, sizeof(float) * Nq * n_states, cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   return PHOEBE_GPU_OK;
