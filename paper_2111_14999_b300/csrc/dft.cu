@@ -43,6 +43,7 @@ __global__ void __launch_bounds__(256) k_dft_z(DftZArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int m = lane >> 2, n0 = 2 * (lane & 3);
     const float2 u0 = us[n0], u1 = us[n0 + 1];
+#pragma unroll 2  // two entries' 16-byte loads in flight per lane
     for (int e = warp; e < ne; e += (int)(blockDim.x >> 5)) {
       const int r = a.ent_r[e0 + e];
       const float4* x4 = reinterpret_cast<const float4*>(X + (int64_t)r * 384 + lane * 12);
