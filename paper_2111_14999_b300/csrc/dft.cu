@@ -187,6 +187,18 @@ __device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// 16 bytes global -> shared, bypassing L1, marked first to leave L2: for data read once (the Zs
+// slices), so that it does not push the epilogue's band and phonon tables out of L2.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void cp_async16_stream(void* sdst, const void* gsrc, uint64_t pol) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "l"(pol)
+               : "memory");
+}
 
 // N consecutive floats / complex values of a table row with the widest aligned vector loads (rows
 // start on multiples of N elements, so N % 4 == 0 floats or N % 2 == 0 complex values are 16-byte aligned).
@@ -455,7 +467,8 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
   {  // the Zs[jz] slice of this state: P * E contiguous complex values
     const float2* zg = a.Zs + ((int64_t)s * a.Nz + jz) * P * E;
     if ((P * E) % 2 == 0) {
-      for (int i = threadIdx.x; i < P * E / 2; i += blockDim.x) cp_async16(Zsl + 2 * i, zg + 2 * i);
+      const uint64_t pol = l2_evict_first_policy();
+      for (int i = threadIdx.x; i < P * E / 2; i += blockDim.x) cp_async16_stream(Zsl + 2 * i, zg + 2 * i, pol);
     } else {
       for (int i = threadIdx.x; i < P * E; i += blockDim.x) cp_async8(Zsl + i, zg + i);
     }
