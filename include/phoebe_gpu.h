@@ -355,9 +355,10 @@ int phoebe_gpu_mlp_loss_grad(phoebe_gpu_ctx* ctx, int64_t n_rows, const float* x
 
 /* Network scores z for n_states feature rows (host float [n_states][4]: eps - mu, v[3]) over
  * every q of the grid nq (host float output [n_states][N_q], q in grid-index order).
- * tensor_cores = 1: the tcgen05 inference kernel the learned sampler uses (FP16 operands,
- * FP32 accumulation, SiLU from tanh.approx.f16x2; sm_10x only); 0: the CUDA-core forward
- * pass of the training kernels (FP32 activations). */
+ * tensor_cores = 1: the tcgen05 inference kernel the learned sampler uses (all three hidden
+ * layers as MMAs with FP16 operands, the inputs rounded to FP16, FP32 accumulation, SiLU from
+ * tanh.approx.f16x2; sm_10x only); 0: the CUDA-core forward pass of the training kernels (FP32
+ * activations).  With profiling on, stats.sampler_ms holds the device time of the scoring. */
 int phoebe_gpu_mlp_scores(phoebe_gpu_ctx* ctx, int n_states, const float* features, const int32_t nq[3],
                           int tensor_cores, float* z);
 
