@@ -13,6 +13,7 @@
 #include <type_traits>
 
 #include "dft.h"
+#include "tc_ptx.cuh"
 
 namespace phx {
 
@@ -408,10 +409,11 @@ __device__ __forceinline__ float adaptive_width(const float4 va, const float4 vb
 //  - x (run r, 32 / SPLIT groups of SPLIT lanes, NQ listed q of one line each): sum over the rows
 //    (dft_x_line), apply U_{k+q}^dagger (partial sums over m combined by shuffles), Z_q and the delta
 //    weights of every listed m'.
-// Iteration r, closed by one block barrier, hands out from a shared counter the x tasks of run r,
-// the y tasks of run r+1 and the listing tasks of run r+2 (three lists), so that warps without x
-// work prepare the next runs instead of waiting.  q whose bands all miss the window contribute
-// nothing to Eq. 29 and are not evaluated.
+// Iteration r hands out from a shared counter the x tasks of run r, the y tasks of run r+1 and the
+// listing tasks of run r+2 (three lists), so that warps without x work prepare the next runs.  No
+// block barrier closes an iteration: each task waits for the tasks it depends on (counted per run),
+// and warps that finish early go on to the next iteration.  q whose bands all miss the window
+// contribute nothing to Eq. 29 and are not evaluated.
 template <int NW, int NM, int SPLIT, bool PR, int NQ, bool AD, bool PL>
 __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT_MINB2) k_dft_yx_elph(DftXArgs a) {
   constexpr int E = NW * NM, MW = NW / SPLIT, EP = dft_elem_stride(E);
@@ -435,9 +437,14 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
   int* xD = xS + a.K;                                              // [K]
   int* lists = xD + a.K;                                           // [3][lcap], run r in list r % 3
   const int lcap = dft_list_cap(L, Nx);
-  __shared__ int cnt[4];  // list length of run r in cnt[r % 4]
-  __shared__ int wq[2];   // task counter of iteration r in wq[r % 2]
-  __shared__ unsigned blk_nq;  // the block's evaluated (state, q) pairs
+  const int R = (Ny + L - 1) / L;
+  // per run r: list length, finished listing / y / x tasks; the task counters of the iterations
+  int* rc_cnt = lists + 3 * lcap;                                  // [R]
+  int* rc_ldone = rc_cnt + R;                                      // [R]
+  int* rc_ydone = rc_ldone + R;                                    // [R]
+  int* rc_xdone = rc_ydone + R;                                    // [R]
+  int* rc_task = rc_xdone + R;                                     // [R+1]: iteration r's counter at r + 1
+  __shared__ int abort_s;  // a wait ran out here or in another block: the rest is skipped
   __shared__ float en_s[2];
   __shared__ double pw_s;
   __shared__ float4 vn_s;      // adaptive smearing: hbar v of the initial state
@@ -446,10 +453,7 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
   const int s = blockIdx.y, jz = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 4; ++i) cnt[i] = 0;
-    wq[0] = 0;
-    wq[1] = 0;
-    blk_nq = 0;
+    abort_s = *reinterpret_cast<volatile int*>(a.err);
     const double e_n = a.epsF[a.gm.k_to_fine(a.st_k[s]) * NW + a.st_b[s]];
     en_s[0] = (float)e_n;
     en_s[1] = (float)(e_n - (double)en_s[0]);
@@ -486,6 +490,7 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
     cp_async4(xD + i, a.xD + i);
   }
   for (int i = threadIdx.x; i < E; i += blockDim.x) Zsl[(size_t)P * E + i] = make_float2(0.f, 0.f);
+  for (int i = threadIdx.x; i < 5 * R + 1; i += blockDim.x) rc_cnt[i] = 0;
   int kc[3];
   grid_coords(a.gm.k_to_fine(a.st_k[s]), a.gm.nf, kc);
   // fine-grid coordinates of k+q: k_d + j_d * s_d with k_d < nf_d and j_d * s_d < nf_d, so one
@@ -500,7 +505,6 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
   const float en_hi = en_s[0], en_lo = en_s[1];
   const double pw = PR ? pw_s : 0.0;
   const float4 vn = AD ? vn_s : make_float4(0.f, 0.f, 0.f, 0.f);
-  const int R = (Ny + L - 1) / L;
   auto list_tasks = [&](int rr) { return (min(L, Ny - rr * L) * Nx + 32 * QR - 1) / (32 * QR); };
 
   // listing task t of run rr: q = 32 QR t + 32 u + lane of the run (u < QR), energy rows loaded
@@ -509,7 +513,7 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
     const int jy0 = rr * L;
     const int nq_run = min(L, Ny - jy0) * Nx;
     int* list = lists + (rr % 3) * lcap;
-    int* cn = cnt + (rr & 3);
+    int* cn = rc_cnt + rr;
     const int q0 = t * 32 * QR;
     float ev[QR][NW];
     int64_t kqs[QR];
@@ -751,55 +755,106 @@ __global__ void __launch_bounds__(kDftXThreads, NQ == 1 ? PHX_DFT_MINB : PHX_DFT
 
   double accd = 0.0;  // this warp's x tasks (every lane holds the same value)
 
-  // Iteration r = -1 .. R-1: the x tasks of run r, the y tasks of run r+1, the listing tasks of run
-  // r+2 (and, at r = -1, of run 0).  A warp's first task of an iteration is its warp index, further
-  // ones come from the counter.
-  for (int r = -1; r < R; ++r) {
-    const int total = r >= 0 ? cnt[r & 3] : 0;
-    if (threadIdx.x == 0) {
-      // cnt[(r - 1) % 4] was read in iteration r - 1 and is next written by the listing of run
-      // r + 3 in iteration r + 1; wq[(r + 1) % 2] was last used in iteration r - 1
-      cnt[(r + 3) & 3] = 0;
-      wq[(r + 1) & 1] = 0;
-      if (r >= 0) blk_nq += (unsigned)total;
+  // Bounded wait until *c >= target.  Every lane reads the counter and then fences, so the shared-
+  // memory writes that the finished tasks made before counting themselves are visible to it.  False
+  // once the block gives up: the wait ran out (raising the abort flag and the error word), or
+  // another warp or block ran out first.
+  auto wait_for = [&](const int* c, int target) -> bool {
+    const volatile int* vc = c;
+    volatile int* ab = &abort_s;
+    if (*vc >= target) {
+      __threadfence_block();
+      return true;
+    }
+    const unsigned long long t0 = tc::globaltimer();
+    for (unsigned i = 1;; ++i) {
+      __nanosleep(32);
+      if (*vc >= target) {
+        __threadfence_block();
+        return true;
+      }
+      if ((i & 63u) == 0) {
+        if (*ab || *reinterpret_cast<volatile int*>(a.err)) {
+          *ab = 1;
+          return false;
+        }
+        if (tc::globaltimer() - t0 > tc::kWaitLimitNs) {
+          *ab = 1;
+          atomicOr(a.err, 1);
+          return false;
+        }
+      }
+    }
+  };
+  // a finished task counts itself once all its lanes' writes are fenced
+  auto finished = [&](int* c) {
+    __threadfence_block();
+    __syncwarp();
+    if (lane == 0) atomicAdd(c, 1);
+  };
+  auto x_tasks_of = [&](int r) {  // once run r's listing is finished
+    return (*reinterpret_cast<volatile int*>(rc_cnt + r) + XT - 1) / XT;
+  };
+
+  // Iteration r = -1 .. R-1 hands out, from its own counter, the x tasks of run r, the y tasks of
+  // run r+1 and the listing tasks of run r+2 (and, at r = -1, of run 0).  There is no block barrier
+  // between iterations: a task first waits (bounded) for the tasks it reads from or overwrites,
+  // counted per run:
+  //  - x of run r: the y tasks of run r (its listing is waited for before the iteration's count);
+  //  - y of run r+1 (Y buffer (r+1) % 2) and listing of run r+2 (list (r+2) % 3): the x tasks of run r-1.
+  // Those belong to earlier iterations, whose tasks were all handed out before any warp moved on,
+  // so no two warps wait on each other.
+  bool ok = abort_s == 0;
+  for (int r = -1; r < R && ok; ++r) {
+    int total = 0;
+    if (r >= 0) {
+      ok = wait_for(rc_ldone + r, list_tasks(r));
+      if (!ok) break;
+      total = *reinterpret_cast<volatile int*>(rc_cnt + r);
     }
     const int nx = (total + XT - 1) / XT;
     const int ny = r + 1 < R ? y_tasks : 0;
     const int np = r + 2 < R ? list_tasks(r + 2) : 0;
     const int n0 = r < 0 ? list_tasks(0) : 0;
     const int ntask = nx + ny + np + n0;
-    for (bool first = true;; first = false) {
-      int t = warp;
-      if (!first) {
-        int tn = 0;
-        if (lane == 0) tn = atomicAdd(wq + (r & 1), 1);
-        t = NWARP + __shfl_sync(0xffffffffu, tn, 0);
-      }
+    for (;;) {
+      int tn = 0;
+      if (lane == 0) tn = atomicAdd(rc_task + r + 1, 1);
+      const int t = __shfl_sync(0xffffffffu, tn, 0);
       if (t >= ntask) break;
       if (t < nx) {
+        if (!(ok = wait_for(rc_ydone + r, y_tasks))) break;
         // the task's sum in a fixed order, then FP64: which warp takes which task does not change
         // the result beyond FP64 rounding
         float part = x_task(r, t, total);
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
         accd += (double)part;
-      } else if (t < nx + ny) {
-        y_task(r + 1, t - nx);
+        finished(rc_xdone + r);
       } else {
-        const bool run0 = t >= nx + ny + np;  // the listing of run 0 (iteration -1)
-        list_task(run0 ? 0 : r + 2, t - nx - ny - (run0 ? np : 0));
+        if (r >= 1 && !(ok = wait_for(rc_xdone + r - 1, x_tasks_of(r - 1)))) break;
+        if (t < nx + ny) {
+          y_task(r + 1, t - nx);
+          finished(rc_ydone + r + 1);
+        } else {
+          const bool run0 = t >= nx + ny + np;  // the listing of run 0 (iteration -1)
+          const int rl = run0 ? 0 : r + 2;
+          list_task(rl, t - nx - ny - (run0 ? np : 0));
+          finished(rc_ldone + rl);
+        }
       }
     }
-    __syncthreads();
   }
   if (lane == 0) red[warp] = accd;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && !abort_s) {
     double sum = 0.0;
     for (int i = 0; i < NWARP; ++i) sum += red[i];
     if (sum != 0.0) atomicAdd(a.gamma + a.s_base + s, sum * a.scale);
     // the pair count once per block, spread over four addresses (summed by the host); the listed
     // bands are not counted here (a count per listing task cost 1.5 % of the kernel)
-    atomicAdd(a.nq_evaluated + 2 * (blockIdx.x & 3), (unsigned long long)blk_nq);
+    unsigned long long blk_nq = 0;
+    for (int r = 0; r < R; ++r) blk_nq += (unsigned)rc_cnt[r];
+    atomicAdd(a.nq_evaluated + 2 * (blockIdx.x & 3), blk_nq);
   }
 }
 
@@ -851,8 +906,9 @@ size_t dft_smem_bytes(int P, int Bx, int By, int nw, int nm, int Nx, int Ny, int
   const size_t E = (size_t)nw * nm;
   const size_t c2 = (P + 1) * E + ((P + 1) * E) % 2 + 2 * (size_t)kDftLines * dft_line_stride(Bx, (int)E, nw) +
                     (size_t)Nx * K + (size_t)Ny * By + ((size_t)Nx * K + (size_t)Ny * By) % 2;
+  const size_t runs = (size_t)(Ny + kDftLines - 1) / kDftLines;
   return sizeof(float2) * c2 + sizeof(int4) * (size_t)G +
-         sizeof(int) * ((size_t)K + 1 + (size_t)G + 2 * (size_t)K + 3 * (size_t)dft_list_cap(kDftLines, Nx));
+         sizeof(int) * ((size_t)K + 1 + (size_t)G + 2 * (size_t)K + 3 * (size_t)dft_list_cap(kDftLines, Nx) + 5 * runs + 1);
 }
 
 size_t dft_z_smem_bytes(int ne_plane_max, int E, int Nz, int Bz) {

@@ -90,6 +90,7 @@ struct DftXArgs {
   int64_t s_base;
   unsigned long long* nq_evaluated;  // [2i] += the (state, q) pairs whose x sum was evaluated
                                      // (i = block % 4); [2i+1] stays 0
+  int* err;                   // set to 1 if a bounded wait between the warps of a block ran out
   // phonon-electron rates (optional, nullptr = off): pacc[q][nu] += f(1-f)/kT of the state times
   // sum_m' |g_{m' n nu}(k,q)|^2 e^{-((eps_nk - eps_m'k+q - w_q nu)/sigma)^2}
   double* pacc;

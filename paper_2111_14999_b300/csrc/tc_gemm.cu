@@ -2465,6 +2465,7 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
     x.gamma = raw;
     x.s_base = i0;
     x.nq_evaluated = nq_eval;
+    x.err = err;
     x.pacc = c->prate_acc;
     x.mu = p->mu_eV;
     x.inv_kT = 1.0 / (kBoltzmannEV * p->T_K);
@@ -2506,7 +2507,7 @@ static int run_dft(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, const Grid
   CK(c, cudaMemcpyAsync(n_xb, nq_eval, sizeof(n_xb), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   const unsigned long long n_x = n_xb[0] + n_xb[2] + n_xb[4] + n_xb[6], n_b = n_xb[1] + n_xb[3] + n_xb[5] + n_xb[7];
-  if (herr) return fail(c, PHOEBE_GPU_ERR_TIMEOUT, "a tensor-core pipeline wait ran out; results discarded");
+  if (herr) return fail(c, PHOEBE_GPU_ERR_TIMEOUT, "a pipeline wait of stage 1 or 2 ran out; results discarded");
   c->stats.pairs_executed = (int64_t)n_x;
   // complex MACs of the DFT: z sum over the entries, y sum over the pairs for every (jy, jz) line
   // (the lines a last, partial run of the fused kernel pads with are not counted), x sum per
