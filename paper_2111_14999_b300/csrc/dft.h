@@ -141,6 +141,13 @@ struct S1Args {
   const int* pair_ent_off;    // [Pe+1]
   const int* pair_ay;         // [Pe] ry residue index of each pair
   const int* rz_pair_off;     // [Bz+1] pairs of each rz residue index
+  // y groups of each rz (FP32 form): the pairs of ry residues {r, -r mod Ny} (pair, partner pair),
+  // whose rows the kernel replaces by P = W1(r) + W1(-r) and M = W1(r) - W1(-r); a residue equal to
+  // its negative or without a partner is a group (pair, pair) of its own
+  int Gy;
+  const int2* ygrp;           // [Gy]
+  const int* ygrp_ay;         // [Gy] ry residue index of the group's first pair
+  const int* rz_grp_off;      // [Bz+1] groups of each rz residue index
   const int2* zgrp;           // [Gz] (rz index of r, rz index of -r or -1)
   const float2* Ex;           // [nkx][Bx] e^{2 pi i kx rx / nkx}
   const float2* Ey;           // [nky][By]
@@ -152,7 +159,7 @@ struct S1Args {
   const int4* kent;           // [entries] (kz, X row, X row of (kx, ky, -kz) or -1, 0); a k whose -kz
                               // partner is in the batch appears only in its partner's entry
 };
-size_t s1_smem_bytes(int nRe, int Pe, int Bz, int Gz, int nky, int By, int nkz);
+size_t s1_smem_bytes(int nRe, int Pe, int Bz, int Gz, int nky, int By, int nkz, int Gy);
 // Launches the stage-1 DFT for `planes` kx planes; -1 on a launch error, -2 if Gz > 16.
 int s1_launch(cudaStream_t st, const S1Args& a, int planes);
 // g(R_e)[c] (complex128, [nRe][C]) -> FP32 [nRe][C]

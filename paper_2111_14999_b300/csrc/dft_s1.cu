@@ -4,7 +4,9 @@
 //          = sum_rz Ez[kz][rz] sum_ry Ey[ky][ry] sum_rx Ex[kx][rx] w g(rx, ry, rz)[c],
 // r = R_e mod N per axis.  One block per (kx plane of the batch, chunk of element columns): the
 // rx sum into W1[(ry, rz) pair] (g streamed once per plane), then per ky line of the plane the
-// ry sum into W2(rz), then the rz sum for every k of the batch on that line by the z groups {r, -r}:
+// ry sum into W2(rz) by the y groups {r, -r} (the rows of a group replaced by their sum and
+// difference once per plane, as for z below), then the rz sum for every k of the batch on that
+// line by the z groups {r, -r}:
 // with P = W2(r) + W2(-r), M = W2(r) - W2(-r) and Ez = c + i s, Ez(r) W2(r) + Ez(-r) W2(-r) =
 // c P + i s M; the k (kz) and (-kz) of one line share A = sum c P and B = sum i s M, X = A +- B.
 // X rows are written in the layout the tensor-core GEMM writes (unscaled).
@@ -26,8 +28,9 @@ __global__ void __launch_bounds__(256) k_s1_dft(S1Args a) {
   int2* zg = reinterpret_cast<int2*>(Ezg + (size_t)a.nkz * G);  // [G]
   int* peo = reinterpret_cast<int*>(zg + G);             // [Pe+1]
   int* erow = peo + Pe + 1;                              // [nRe]
-  int* pay = erow + nRe;                                 // [Pe]
-  int* rzo = pay + Pe;                                   // [Bz+1]
+  int2* yg = reinterpret_cast<int2*>(erow + nRe + ((Pe + 1 + nRe) & 1));  // [Gy] (pair, partner pair), 8-byte aligned
+  int* yay = reinterpret_cast<int*>(yg + a.Gy);         // [Gy]
+  int* rzg = yay + a.Gy;                                 // [Bz+1]
   const int pl = blockIdx.y, kx = a.plane_kx[pl];
   const int64_t c0 = (int64_t)blockIdx.x * CW;
   const int col = threadIdx.x % CW, t4 = threadIdx.x / CW;
@@ -42,8 +45,11 @@ __global__ void __launch_bounds__(256) k_s1_dft(S1Args a) {
   for (int i = threadIdx.x; i < a.nkz * G; i += blockDim.x) Ezg[i] = a.Ezg[i];
   for (int i = threadIdx.x; i < G; i += blockDim.x) zg[i] = a.zgrp[i];
   for (int i = threadIdx.x; i <= Pe; i += blockDim.x) peo[i] = a.pair_ent_off[i];
-  for (int i = threadIdx.x; i < Pe; i += blockDim.x) pay[i] = a.pair_ay[i];
-  for (int i = threadIdx.x; i <= a.Bz; i += blockDim.x) rzo[i] = a.rz_pair_off[i];
+  for (int i = threadIdx.x; i < a.Gy; i += blockDim.x) {
+    yg[i] = a.ygrp[i];
+    yay[i] = a.ygrp_ay[i];
+  }
+  for (int i = threadIdx.x; i <= a.Bz; i += blockDim.x) rzg[i] = a.rz_grp_off[i];
   for (int i = threadIdx.x; i < Pe * CW; i += blockDim.x) W1[i] = make_float2(0.f, 0.f);
   __syncthreads();
   // rx sum: W1[p][col] = sum over the entries of pair p of w Ex g.  Each of the TPC threads of a
@@ -82,19 +88,33 @@ __global__ void __launch_bounds__(256) k_s1_dft(S1Args a) {
     }
   }
   __syncthreads();
+  // the rows of each y group {r, -r}: W1(r), W1(-r) -> P = W1(r) + W1(-r), M = W1(r) - W1(-r)
+  for (int gi = t4; gi < a.Gy; gi += TPC) {
+    const int2 pp = yg[gi];
+    if (pp.y != pp.x) {
+      const float2 u = W1[pp.x * CW + col], v = W1[pp.y * CW + col];
+      W1[pp.x * CW + col] = make_float2(u.x + v.x, u.y + v.y);
+      W1[pp.y * CW + col] = make_float2(u.x - v.x, u.y - v.y);
+    }
+  }
+  __syncthreads();
   // per iteration kS1Lines ky lines of the plane: their ry sums, one barrier, their rz sums and stores
   const int lb = a.plane_line_off[pl], le = a.plane_line_off[pl + 1];
   for (int li = lb; li < le; li += kS1Lines) {
     const int nl = min(kS1Lines, le - li);
-    // ry sum: W2[line](r) = sum over the pairs with rz = r of Ey[ky][ry] W1[pair], one (line, rz) per item
+    // ry sum: W2[line](r) = sum over the pairs with rz = r of Ey[ky][ry] W1[pair], one (line, rz) per
+    // item.  With Ey[ky][r] = c + i s and Ey[ky][-r] = c - i s a y group adds c P + i s M; a group of
+    // one pair (P = M = W1) adds Ey W1 in the same form.
     for (int it = t4; it < nl * a.Bz; it += TPC) {
       const int ll = it / a.Bz, r = it - ll * a.Bz;
       const float2* ey = Eyk + (size_t)a.line_ky[li + ll] * By;
       float2 w = make_float2(0.f, 0.f);
-      for (int p = rzo[r]; p < rzo[r + 1]; ++p) {
-        const float2 e = ey[pay[p]], v = W1[p * CW + col];
-        w.x = fmaf(e.x, v.x, fmaf(-e.y, v.y, w.x));
-        w.y = fmaf(e.x, v.y, fmaf(e.y, v.x, w.y));
+      const int g1 = rzg[r + 1];
+      for (int gi = rzg[r]; gi < g1; ++gi) {
+        const int2 pp = yg[gi];
+        const float2 e = ey[yay[gi]], v = W1[pp.x * CW + col], m = W1[pp.y * CW + col];
+        w.x = fmaf(e.x, v.x, fmaf(-e.y, m.y, w.x));
+        w.y = fmaf(e.x, v.y, fmaf(e.y, m.x, w.y));
       }
       W2[(ll * a.Bz + r) * CW + col] = w;
     }
@@ -113,7 +133,8 @@ __global__ void __launch_bounds__(256) k_s1_dft(S1Args a) {
           M[g] = make_float2(u.x - v.x, u.y - v.y);
         }
       }
-      for (int i = a.line_k_off[li + ll] + t4; i < a.line_k_off[li + ll + 1]; i += TPC) {
+      const int i1 = a.line_k_off[li + ll + 1];  // held: the X stores below may alias the table for the compiler
+      for (int i = a.line_k_off[li + ll] + t4; i < i1; i += TPC) {
         const int4 kr = a.kent[i];  // (kz, X row of kz, X row of -kz or -1)
         const float2* ez = Ezg + (size_t)kr.x * G;
         float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
@@ -137,15 +158,16 @@ __global__ void __launch_bounds__(256) k_s1_dft(S1Args a) {
   }
 }
 
-size_t s1_smem_bytes(int nRe, int Pe, int Bz, int Gz, int nky, int By, int nkz) {
+size_t s1_smem_bytes(int nRe, int Pe, int Bz, int Gz, int nky, int By, int nkz, int Gy) {
   return sizeof(float2) * ((size_t)Pe * kS1Cols + (size_t)kS1Lines * Bz * kS1Cols + nRe + (size_t)nky * By +
                            (size_t)nkz * Gz) +
-         sizeof(int2) * (size_t)Gz + sizeof(int) * ((size_t)Pe + 1 + nRe + Pe + (size_t)Bz + 1);
+         sizeof(int2) * (size_t)Gz + sizeof(int) * ((size_t)Pe + 1 + nRe + ((Pe + 1 + nRe) & 1)) + sizeof(int2) * (size_t)Gy +
+         sizeof(int) * ((size_t)Gy + Bz + 1);
 }
 
 template <int GZ>
 static int s1_launch_t(cudaStream_t st, const S1Args& a, int planes) {
-  const size_t smem = s1_smem_bytes(a.nRe, a.Pe, a.Bz, a.Gz, a.nky, a.By, a.nkz);
+  const size_t smem = s1_smem_bytes(a.nRe, a.Pe, a.Bz, a.Gz, a.nky, a.By, a.nkz, a.Gy);
   if (allow_dynamic_smem(k_s1_dft<GZ>) != cudaSuccess)
     return -1;
   dim3 grid((unsigned)((a.C + kS1Cols - 1) / kS1Cols), (unsigned)planes);

@@ -1836,8 +1836,25 @@ static int s1_setup(phoebe_gpu_ctx* c, const GridMap& gm, S1Args* a, bool* ok, S
     zres.push_back(res[2][z]);
   }
   const int Gz = (int)zres.size();
+  // y groups within each rz: the pairs whose ry residues are r and -r mod Ny; a residue equal to its
+  // negative, or whose negative has no pair at this rz, forms a group with itself
+  std::vector<int> ygrp, ygrp_ay, rzg(Bz + 1, 0);
+  for (int z = 0; z < Bz; ++z) {
+    for (int p = rzo[z]; p < rzo[z + 1]; ++p) {
+      const int rn = (N3[1] - res[1][pay[p]]) % N3[1];
+      int pn = p;
+      for (int p2 = rzo[z]; p2 < rzo[z + 1]; ++p2)
+        if (p2 != p && res[1][pay[p2]] == rn) pn = p2;
+      if (pn < p) continue;  // listed with its partner
+      ygrp.push_back(p);
+      ygrp.push_back(pn);
+      ygrp_ay.push_back(pay[p]);
+    }
+    rzg[z + 1] = (int)ygrp_ay.size();
+  }
+  const int Gy = (int)ygrp_ay.size();
   const size_t s1_smem = a64 ? s64_smem_bytes(nRe, Pe, Bz, Gz, N3[1], By, N3[2])
-                             : s1_smem_bytes(nRe, Pe, Bz, Gz, N3[1], By, N3[2]);
+                             : s1_smem_bytes(nRe, Pe, Bz, Gz, N3[1], By, N3[2], Gy);
   if (Gz > 16 || s1_smem > 200 * 1024) return PHOEBE_GPU_OK;
   int st;
   float2* g32 = nullptr;
@@ -1857,6 +1874,10 @@ static int s1_setup(phoebe_gpu_ctx* c, const GridMap& gm, S1Args* a, bool* ok, S
   TRY(upload(c, "s1_pay", pay.data(), sizeof(int) * Pe, &d_pay));
   TRY(upload(c, "s1_rzo", rzo.data(), sizeof(int) * (Bz + 1), &d_rzo));
   TRY(upload(c, "s1_zg", zgrp.data(), sizeof(int) * 2 * Gz, &d_zg));
+  void *d_yg, *d_yay, *d_rzg;
+  TRY(upload(c, "s1_yg", ygrp.data(), sizeof(int) * 2 * Gy, &d_yg));
+  TRY(upload(c, "s1_yay", ygrp_ay.data(), sizeof(int) * Gy, &d_yay));
+  TRY(upload(c, "s1_rzg", rzg.data(), sizeof(int) * (Bz + 1), &d_rzg));
   TRY(upload(c, "s1_rx", res[0].data(), sizeof(int) * Bx, &d_rx));
   TRY(upload(c, "s1_ry", res[1].data(), sizeof(int) * By, &d_ry));
   TRY(upload(c, "s1_rz", zres.data(), sizeof(int) * Gz, &d_rz));
@@ -1913,6 +1934,10 @@ static int s1_setup(phoebe_gpu_ctx* c, const GridMap& gm, S1Args* a, bool* ok, S
   a->pair_ay = (const int*)d_pay;
   a->rz_pair_off = (const int*)d_rzo;
   a->zgrp = (const int2*)d_zg;
+  a->Gy = Gy;
+  a->ygrp = (const int2*)d_yg;
+  a->ygrp_ay = (const int*)d_yay;
+  a->rz_grp_off = (const int*)d_rzg;
   a->Ex = Ex;
   a->Ey = Ey;
   a->Ezg = Ezg;
