@@ -160,7 +160,8 @@ struct S1Args {
                               // partner is in the batch appears only in its partner's entry
 };
 size_t s1_smem_bytes(int nRe, int Pe, int Bz, int Gz, int nky, int By, int nkz, int Gy);
-// Launches the stage-1 DFT for `planes` kx planes; -1 on a launch error, -2 if Gz > 16.
+// Launches the stage-1 DFT for `planes` kx planes; -1 on a launch error, -2 if Gz > 16 or an X row
+// (ldx floats) or g's C columns reach 2^31 elements.
 int s1_launch(cudaStream_t st, const S1Args& a, int planes);
 // g(R_e)[c] (complex128, [nRe][C]) -> FP32 [nRe][C]
 int s1_convert_g(cudaStream_t st, const cplx* g, int64_t n, float2* out);

@@ -11,15 +11,20 @@
 // c P + i s M; the k (kz) and (-kz) of one line share A = sum c P and B = sum i s M, X = A +- B.
 // X rows are written in the layout the tensor-core GEMM writes (unscaled).
 // FP32 on the CUDA cores.
+#include <stdint.h>
+
 #include "dft.h"
 
 namespace phx {
 
+// GZ <= 8: exactly GZ z groups; GZ = 16: up to 16.  Element columns and X row strides below 2^31.
 template <int GZ>
 __global__ void __launch_bounds__(256) k_s1_dft(S1Args a) {
   constexpr int CW = kS1Cols, TPC = 256 / CW;  // threads per column
+  constexpr bool EX = GZ <= 8;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int Pe = a.Pe, nRe = a.nRe, G = a.Gz, By = a.By;
+  const int Pe = a.Pe, nRe = a.nRe, G = EX ? GZ : a.Gz, By = a.By;
+  const int C32 = (int)a.C, ldx32 = (int)a.ldx;
   float2* W1 = reinterpret_cast<float2*>(smem);          // [Pe][CW]
   float2* W2 = W1 + (size_t)Pe * CW;                     // [kS1Lines][Bz][CW]
   float2* exw = W2 + (size_t)kS1Lines * a.Bz * CW;       // [nRe] w Ex[kx][rx] per entry
@@ -35,6 +40,8 @@ __global__ void __launch_bounds__(256) k_s1_dft(S1Args a) {
   const int64_t c0 = (int64_t)blockIdx.x * CW;
   const int col = threadIdx.x % CW, t4 = threadIdx.x / CW;
   const bool live = c0 + col < a.C;
+  const float2* gcol = a.g + c0 + col;  // this column of g and of the X rows
+  float* Xcol = a.X + 2 * (c0 + col);
   for (int i = threadIdx.x; i < nRe; i += blockDim.x) {
     const float2 e = a.Ex[kx * a.Bx + a.ent_ax[i]];
     const float w = a.ent_w[i];
@@ -61,21 +68,23 @@ __global__ void __launch_bounds__(256) k_s1_dft(S1Args a) {
     const int e0 = t4 * per, e1 = min(nRe, e0 + per);
     int p = 0;
     while (p + 1 < Pe && peo[p + 1] <= e0) ++p;
+    int pend = peo[p + 1];  // first entry past pair p
     float2 acc = make_float2(0.f, 0.f);
     for (int eb = e0; eb < e1; eb += U) {
       float2 gv[U];
 #pragma unroll
       for (int i = 0; i < U; ++i)
-        gv[i] = (live && eb + i < e1) ? __ldg(a.g + (int64_t)erow[eb + i] * a.C + c0 + col) : make_float2(0.f, 0.f);
+        gv[i] = (live && eb + i < e1) ? __ldg(gcol + (int64_t)erow[eb + i] * C32) : make_float2(0.f, 0.f);
 #pragma unroll
       for (int i = 0; i < U; ++i) {
         const int e = eb + i;
         if (e >= e1) break;
-        if (e >= peo[p + 1]) {  // next pair: flush the running sum
+        if (e >= pend) {  // next pair: flush the running sum
           atomicAdd(&W1[p * CW + col].x, acc.x);
           atomicAdd(&W1[p * CW + col].y, acc.y);
           acc = make_float2(0.f, 0.f);
           while (e >= peo[p + 1]) ++p;
+          pend = peo[p + 1];
         }
         const float2 x = exw[e];
         acc.x = fmaf(x.x, gv[i].x, fmaf(-x.y, gv[i].y, acc.x));
@@ -105,9 +114,10 @@ __global__ void __launch_bounds__(256) k_s1_dft(S1Args a) {
     // ry sum: W2[line](r) = sum over the pairs with rz = r of Ey[ky][ry] W1[pair], one (line, rz) per
     // item.  With Ey[ky][r] = c + i s and Ey[ky][-r] = c - i s a y group adds c P + i s M; a group of
     // one pair (P = M = W1) adds Ey W1 in the same form.
+    const int ky0 = a.line_ky[li];
     for (int it = t4; it < nl * a.Bz; it += TPC) {
-      const int ll = it / a.Bz, r = it - ll * a.Bz;
-      const float2* ey = Eyk + (size_t)a.line_ky[li + ll] * By;
+      const int ll = kS1Lines == 1 ? 0 : it / a.Bz, r = it - ll * a.Bz;
+      const float2* ey = Eyk + (size_t)(kS1Lines == 1 ? ky0 : a.line_ky[li + ll]) * By;
       float2 w = make_float2(0.f, 0.f);
       const int g1 = rzg[r + 1];
       for (int gi = rzg[r]; gi < g1; ++gi) {
@@ -126,7 +136,7 @@ __global__ void __launch_bounds__(256) k_s1_dft(S1Args a) {
 #pragma unroll
       for (int g = 0; g < GZ; ++g) {
         P[g] = M[g] = make_float2(0.f, 0.f);
-        if (g < G) {
+        if (EX || g < G) {
           const int2 z = zg[g];
           const float2 u = w2[z.x * CW + col], v = z.y >= 0 ? w2[z.y * CW + col] : make_float2(0.f, 0.f);
           P[g] = make_float2(u.x + v.x, u.y + v.y);
@@ -140,7 +150,7 @@ __global__ void __launch_bounds__(256) k_s1_dft(S1Args a) {
         float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
 #pragma unroll
         for (int g = 0; g < GZ; ++g) {
-          if (g >= G) break;
+          if (!EX && g >= G) break;
           const float2 e = ez[g];
           A.x = fmaf(e.x, P[g].x, A.x);
           A.y = fmaf(e.x, P[g].y, A.y);
@@ -148,9 +158,8 @@ __global__ void __launch_bounds__(256) k_s1_dft(S1Args a) {
           B.y = fmaf(e.y, M[g].x, B.y);
         }
         if (live) {
-          *reinterpret_cast<float2*>(a.X + (int64_t)kr.y * a.ldx + 2 * (c0 + col)) = make_float2(A.x + B.x, A.y + B.y);
-          if (kr.z >= 0)
-            *reinterpret_cast<float2*>(a.X + (int64_t)kr.z * a.ldx + 2 * (c0 + col)) = make_float2(A.x - B.x, A.y - B.y);
+          *reinterpret_cast<float2*>(Xcol + (int64_t)kr.y * ldx32) = make_float2(A.x + B.x, A.y + B.y);
+          if (kr.z >= 0) *reinterpret_cast<float2*>(Xcol + (int64_t)kr.z * ldx32) = make_float2(A.x - B.x, A.y - B.y);
         }
       }
     }
@@ -177,10 +186,18 @@ static int s1_launch_t(cudaStream_t st, const S1Args& a, int planes) {
 
 int s1_launch(cudaStream_t st, const S1Args& a, int planes) {
   if (planes <= 0) return 0;
-  if (a.Gz <= 4) return s1_launch_t<4>(st, a, planes);
-  if (a.Gz <= 8) return s1_launch_t<8>(st, a, planes);
-  if (a.Gz <= 16) return s1_launch_t<16>(st, a, planes);
-  return -2;
+  if (a.C > INT32_MAX || a.ldx > INT32_MAX) return -2;
+  switch (a.Gz) {
+    case 1: return s1_launch_t<1>(st, a, planes);
+    case 2: return s1_launch_t<2>(st, a, planes);
+    case 3: return s1_launch_t<3>(st, a, planes);
+    case 4: return s1_launch_t<4>(st, a, planes);
+    case 5: return s1_launch_t<5>(st, a, planes);
+    case 6: return s1_launch_t<6>(st, a, planes);
+    case 7: return s1_launch_t<7>(st, a, planes);
+    case 8: return s1_launch_t<8>(st, a, planes);
+    default: return a.Gz <= 16 ? s1_launch_t<16>(st, a, planes) : -2;
+  }
 }
 
 __global__ void k_s1_g32(const cplx* __restrict__ g, int64_t n, float2* __restrict__ out) {

@@ -1855,7 +1855,7 @@ static int s1_setup(phoebe_gpu_ctx* c, const GridMap& gm, S1Args* a, bool* ok, S
   const int Gy = (int)ygrp_ay.size();
   const size_t s1_smem = a64 ? s64_smem_bytes(nRe, Pe, Bz, Gz, N3[1], By, N3[2])
                              : s1_smem_bytes(nRe, Pe, Bz, Gz, N3[1], By, N3[2], Gy);
-  if (Gz > 16 || s1_smem > 200 * 1024) return PHOEBE_GPU_OK;
+  if (Gz > 16 || s1_smem > 200 * 1024 || (!a64 && 2 * C > INT32_MAX)) return PHOEBE_GPU_OK;  // the GEMM stage 1 serves
   int st;
   float2* g32 = nullptr;
   if (!a64) {
