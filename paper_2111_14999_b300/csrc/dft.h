@@ -125,10 +125,6 @@ struct PolarArgs {
 #define PHX_S1_COLS 64
 #endif
 constexpr int kS1Cols = PHX_S1_COLS;  // element columns per block
-#ifndef PHX_S1_LINES
-#define PHX_S1_LINES 1
-#endif
-constexpr int kS1Lines = PHX_S1_LINES;  // ky lines per barrier-delimited iteration
 struct S1Args {
   const float2* g;            // [nRe][C] g(R_e)[c] in FP32
   int64_t C;                  // element columns (nRp nw nw 3na)

@@ -26,8 +26,7 @@ __global__ void __launch_bounds__(256) k_s1_dft(S1Args a) {
   const int Pe = a.Pe, nRe = a.nRe, G = EX ? GZ : a.Gz, By = a.By;
   const int C32 = (int)a.C, ldx32 = (int)a.ldx;
   float2* W1 = reinterpret_cast<float2*>(smem);          // [Pe][CW]
-  float2* W2 = W1 + (size_t)Pe * CW;                     // [kS1Lines][Bz][CW]
-  float2* exw = W2 + (size_t)kS1Lines * a.Bz * CW;       // [nRe] w Ex[kx][rx] per entry
+  float2* exw = W1 + (size_t)Pe * CW;                    // [nRe] w Ex[kx][rx] per entry
   float2* Eyk = exw + nRe;                               // [nky][By]
   float2* Ezg = Eyk + (size_t)a.nky * By;                // [nkz][G]
   int2* zg = reinterpret_cast<int2*>(Ezg + (size_t)a.nkz * G);  // [G]
@@ -36,6 +35,7 @@ __global__ void __launch_bounds__(256) k_s1_dft(S1Args a) {
   int2* yg = reinterpret_cast<int2*>(erow + nRe + ((Pe + 1 + nRe) & 1));  // [Gy] (pair, partner pair), 8-byte aligned
   int* yay = reinterpret_cast<int*>(yg + a.Gy);         // [Gy]
   int* rzg = yay + a.Gy;                                 // [Bz+1]
+  int* line_ctr = rzg + a.Bz + 1;                        // [CW / 32] lines taken per column half
   const int pl = blockIdx.y, kx = a.plane_kx[pl];
   const int64_t c0 = (int64_t)blockIdx.x * CW;
   const int col = threadIdx.x % CW, t4 = threadIdx.x / CW;
@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(256) k_s1_dft(S1Args a) {
     yay[i] = a.ygrp_ay[i];
   }
   for (int i = threadIdx.x; i <= a.Bz; i += blockDim.x) rzg[i] = a.rz_grp_off[i];
+  for (int i = threadIdx.x; i < CW / 32; i += blockDim.x) line_ctr[i] = 0;
   for (int i = threadIdx.x; i < Pe * CW; i += blockDim.x) W1[i] = make_float2(0.f, 0.f);
   __syncthreads();
   // rx sum: W1[p][col] = sum over the entries of pair p of w Ex g.  Each of the TPC threads of a
@@ -107,71 +108,69 @@ __global__ void __launch_bounds__(256) k_s1_dft(S1Args a) {
     }
   }
   __syncthreads();
-  // per iteration kS1Lines ky lines of the plane: their ry sums, one barrier, their rz sums and stores
+  // Per ky line of the plane: the ry sums W2(rz) and the rz sums for the batch's k on the line.  A
+  // warp takes whole lines from its column half's counter; every value it needs after the rx sum is
+  // its own column's, so no barrier follows.  With Ez = c + i s, a z group {r, -r} adds
+  // c P + i s M with P = W2(r) + W2(-r), M = W2(r) - W2(-r); W2(r) sums over the y groups of rz = r
+  // as in the rx rows (c P' + i s M' with the group's Ey = c + i s).
   const int lb = a.plane_line_off[pl], le = a.plane_line_off[pl + 1];
-  for (int li = lb; li < le; li += kS1Lines) {
-    const int nl = min(kS1Lines, le - li);
-    // ry sum: W2[line](r) = sum over the pairs with rz = r of Ey[ky][ry] W1[pair], one (line, rz) per
-    // item.  With Ey[ky][r] = c + i s and Ey[ky][-r] = c - i s a y group adds c P + i s M; a group of
-    // one pair (P = M = W1) adds Ey W1 in the same form.
-    const int ky0 = a.line_ky[li];
-    for (int it = t4; it < nl * a.Bz; it += TPC) {
-      const int ll = kS1Lines == 1 ? 0 : it / a.Bz, r = it - ll * a.Bz;
-      const float2* ey = Eyk + (size_t)(kS1Lines == 1 ? ky0 : a.line_ky[li + ll]) * By;
-      float2 w = make_float2(0.f, 0.f);
-      const int g1 = rzg[r + 1];
-      for (int gi = rzg[r]; gi < g1; ++gi) {
-        const int2 pp = yg[gi];
-        const float2 e = ey[yay[gi]], v = W1[pp.x * CW + col], m = W1[pp.y * CW + col];
-        w.x = fmaf(e.x, v.x, fmaf(-e.y, m.y, w.x));
-        w.y = fmaf(e.x, v.y, fmaf(e.y, m.x, w.y));
-      }
-      W2[(ll * a.Bz + r) * CW + col] = w;
+  int* lctr = line_ctr + (threadIdx.x >> 5) % (CW / 32);  // this warp's column half
+  auto ry_sum = [&](const float2* ey, int r) {
+    float2 w = make_float2(0.f, 0.f);
+    const int g1 = rzg[r + 1];
+    for (int gi = rzg[r]; gi < g1; ++gi) {
+      const int2 pp = yg[gi];
+      const float2 e = ey[yay[gi]], v = W1[pp.x * CW + col], m = W1[pp.y * CW + col];
+      w.x = fmaf(e.x, v.x, fmaf(-e.y, m.y, w.x));
+      w.y = fmaf(e.x, v.y, fmaf(e.y, m.x, w.y));
     }
-    __syncthreads();
-    for (int ll = 0; ll < nl; ++ll) {
-      const float2* w2 = W2 + (size_t)ll * a.Bz * CW;
-      // rz sum for the batch's k on this line
-      float2 P[GZ], M[GZ];
+    return w;
+  };
+  for (;;) {
+    int li = 0;
+    if ((threadIdx.x & 31) == 0) li = lb + atomicAdd(lctr, 1);
+    li = __shfl_sync(0xffffffffu, li, 0);
+    if (li >= le) break;
+    const float2* ey = Eyk + (size_t)a.line_ky[li] * By;
+    float2 P[GZ], M[GZ];
+#pragma unroll
+    for (int g = 0; g < GZ; ++g) {
+      P[g] = M[g] = make_float2(0.f, 0.f);
+      if (EX || g < G) {
+        const int2 z = zg[g];
+        const float2 u = ry_sum(ey, z.x), v = z.y >= 0 ? ry_sum(ey, z.y) : make_float2(0.f, 0.f);
+        P[g] = make_float2(u.x + v.x, u.y + v.y);
+        M[g] = make_float2(u.x - v.x, u.y - v.y);
+      }
+    }
+    const int i0 = a.line_k_off[li], i1 = a.line_k_off[li + 1];
+    int4 kn = i0 < i1 ? __ldg(a.kent + i0) : make_int4(0, 0, 0, 0);  // the next k's entry, one ahead
+    for (int i = i0; i < i1; ++i) {
+      const int4 kr = kn;  // (kz, X row of kz, X row of -kz or -1)
+      if (i + 1 < i1) kn = __ldg(a.kent + i + 1);
+      const float2* ez = Ezg + (size_t)kr.x * G;
+      float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
 #pragma unroll
       for (int g = 0; g < GZ; ++g) {
-        P[g] = M[g] = make_float2(0.f, 0.f);
-        if (EX || g < G) {
-          const int2 z = zg[g];
-          const float2 u = w2[z.x * CW + col], v = z.y >= 0 ? w2[z.y * CW + col] : make_float2(0.f, 0.f);
-          P[g] = make_float2(u.x + v.x, u.y + v.y);
-          M[g] = make_float2(u.x - v.x, u.y - v.y);
-        }
+        if (!EX && g >= G) break;
+        const float2 e = ez[g];
+        A.x = fmaf(e.x, P[g].x, A.x);
+        A.y = fmaf(e.x, P[g].y, A.y);
+        B.x = fmaf(-e.y, M[g].y, B.x);
+        B.y = fmaf(e.y, M[g].x, B.y);
       }
-      const int i1 = a.line_k_off[li + ll + 1];  // held: the X stores below may alias the table for the compiler
-      for (int i = a.line_k_off[li + ll] + t4; i < i1; i += TPC) {
-        const int4 kr = a.kent[i];  // (kz, X row of kz, X row of -kz or -1)
-        const float2* ez = Ezg + (size_t)kr.x * G;
-        float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int g = 0; g < GZ; ++g) {
-          if (!EX && g >= G) break;
-          const float2 e = ez[g];
-          A.x = fmaf(e.x, P[g].x, A.x);
-          A.y = fmaf(e.x, P[g].y, A.y);
-          B.x = fmaf(-e.y, M[g].y, B.x);
-          B.y = fmaf(e.y, M[g].x, B.y);
-        }
-        if (live) {
-          *reinterpret_cast<float2*>(Xcol + (int64_t)kr.y * ldx32) = make_float2(A.x + B.x, A.y + B.y);
-          if (kr.z >= 0) *reinterpret_cast<float2*>(Xcol + (int64_t)kr.z * ldx32) = make_float2(A.x - B.x, A.y - B.y);
-        }
+      if (live) {
+        *reinterpret_cast<float2*>(Xcol + (int64_t)kr.y * ldx32) = make_float2(A.x + B.x, A.y + B.y);
+        if (kr.z >= 0) *reinterpret_cast<float2*>(Xcol + (int64_t)kr.z * ldx32) = make_float2(A.x - B.x, A.y - B.y);
       }
     }
-    __syncthreads();  // W2 is rewritten for the next lines
   }
 }
 
 size_t s1_smem_bytes(int nRe, int Pe, int Bz, int Gz, int nky, int By, int nkz, int Gy) {
-  return sizeof(float2) * ((size_t)Pe * kS1Cols + (size_t)kS1Lines * Bz * kS1Cols + nRe + (size_t)nky * By +
-                           (size_t)nkz * Gz) +
-         sizeof(int2) * (size_t)Gz + sizeof(int) * ((size_t)Pe + 1 + nRe + ((Pe + 1 + nRe) & 1)) + sizeof(int2) * (size_t)Gy +
-         sizeof(int) * ((size_t)Gy + Bz + 1);
+  return sizeof(float2) * ((size_t)Pe * kS1Cols + nRe + (size_t)nky * By + (size_t)nkz * Gz) + sizeof(int2) * (size_t)Gz +
+         sizeof(int) * ((size_t)Pe + 1 + nRe + ((Pe + 1 + nRe) & 1)) + sizeof(int2) * (size_t)Gy +
+         sizeof(int) * ((size_t)Gy + Bz + 1 + kS1Cols / 32);
 }
 
 template <int GZ>
