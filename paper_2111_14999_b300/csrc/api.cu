@@ -373,6 +373,7 @@ int phoebe_gpu_set_force_constants3(phoebe_gpu_ctx* c, int n, const int32_t* R, 
   if ((st = upload(c, "ph3_off", off.data(), sizeof(int) * (NRp + 1), &d))) return st;
   if ((st = upload(c, "ph3_Rpd", rpd.data(), sizeof(int) * 3 * NRp, &d))) return st;
   c->ph3_nrp = NRp;
+  c->ph3_rp = rpd;
   c->ph3_na = c->na;
   c->have_phi3 = true;
   return PHOEBE_GPU_OK;

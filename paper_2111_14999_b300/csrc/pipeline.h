@@ -54,6 +54,7 @@ struct phoebe_gpu_ctx {
   // third-order force constants, set by phoebe_gpu_set_force_constants3 (device buffers ph3_*)
   bool have_phi3 = false;
   int ph3_na = 0, ph3_nrp = 0;
+  std::vector<int> ph3_rp;  // [ph3_nrp][3] the distinct R' (lattice coordinates), host copy
   bool have_polar = false;
   std::vector<double> zstar;  // [na][3][3]
   double eps_inf[9] = {0};

@@ -7,7 +7,13 @@
 // W = V3(q nu, q~ nu', -(q + q~) nu''), Z the mode factors of Eq. 7.  The same two-stage form as
 // the el-ph couplings: stage 1 sums over R and the first mode at fixed q (FP64, stored FP32),
 // stage 2 sums over R' for every q~ of the grid, applies the other two modes and the delta weights
-// (FP32, partial sums of non-negative terms, FP64 atomics per (q, nu)).
+// (FP32, partial sums of non-negative terms, FP64 atomics per (q, nu)).  On the grid the phase of
+// the R' sum factorises per axis, e^{-2 pi i q~.R'} = Ex[jx][rx] Ey[jy][ry] Ez[jz][rz] with
+// r = R' mod N, so stage 2 forms, per (jx, jy) line of q~, XY[rz] = sum over the R' of each rz of
+// Ex Ey A[R'] once, and each q~ of the line sums over the rz residues only.
+#include <algorithm>
+#include <vector>
+
 #include "pipeline.h"
 
 namespace phx {
@@ -59,68 +65,85 @@ __global__ void k_ph3_stage1(Ph3S1Args a) {
   a.A[t] = make_float2((float)re, (float)im);
 }
 
-// e^{-2 pi i q~.R'} for every grid q~ and distinct R'.
-__global__ void k_ph3_phase(const int* __restrict__ Rp, int NRp, int64_t Q, int N0, int N1, int N2,
-                            float2* __restrict__ P2) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= Q * NRp) return;
-  const int r = (int)(t % NRp);
-  const int64_t q = t / NRp;
-  const int N[3] = {N0, N1, N2};
-  const int j[3] = {(int)(q / ((int64_t)N1 * N2)), (int)((q / N2) % N1), (int)(q % N2)};
-  double frac = 0.0;
-  for (int d = 0; d < 3; ++d) frac += (double)((((int64_t)j[d] * Rp[3 * r + d]) % N[d] + N[d]) % N[d]) / N[d];
-  double sn, cs;
-  sincospi(-2.0 * frac, &sn, &cs);
-  P2[t] = make_float2((float)cs, (float)sn);
-}
-
 struct Ph3S2Args {
   const float2* A;     // [Q][NRp][nm][nm*nm]
-  const float2* P2;    // [Q][NRp]
+  const float2* Ex;    // [N0][Bx] e^{-2 pi i jx rx / N0} of the R' residues along x (likewise y, z)
+  const float2* Ey;    // [N1][By]
+  const float2* Ez;    // [N2][Bz]
+  const int4* rres;    // [NRp] (x, y, z) residue indices of each R'
+  const int* zr_off;   // [Bz+1] R' of each z residue in zr_list
+  const int* zr_list;  // [NRp] the R' grouped by z residue
   const float2* Zf;    // [Q][nm][nm]
   const float2* onb;   // [Q][nm] (hbar w, n), hbar w < 0 for dead modes
   int64_t Q;
-  int NRp, N[3];
+  int NRp, N[3], Bx, By, Bz;
+  int L, Zc;           // (jx, jy) lines of q~ per block and jz per block (L Zc <= 32)
   float inv_sigma, cut2;
   double scale;        // 2 pi / (N_q sqrt(pi) sigma)
   double* acc;         // [Q][nm]
 };
 
-// One block per (tile of kPh3Tile q~, q); thread (q~ of the tile, nu).  The q row of stage 1 is
-// staged in shared memory; each thread sums over R' into B[s' b][s'' c], rotates by the two
-// other modes and adds the coalescence and decay weights of every (nu', nu'').
+// One block per (L consecutive (jx, jy) lines of q~, chunk of Zc jz, q); thread (q~ of the block, nu).  The q row of
+// stage 1 is staged in shared memory; the block forms XY[line][rz][nu][c] = sum over the R' of each
+// rz residue of Ex Ey A[R'][nu][c], then each thread sums B[s' b][s'' c] = sum_rz Ez XY, rotates by
+// the two other modes and adds the coalescence and decay weights of every (nu', nu'').
 template <int NM>
-__global__ void __launch_bounds__(kPh3Tile* NM) k_ph3_stage2(Ph3S2Args a) {
+__global__ void __launch_bounds__(32 * NM) k_ph3_stage2(Ph3S2Args a) {
   constexpr int NC = NM * NM;
   extern __shared__ __align__(16) unsigned char smem[];
+  const int N2 = a.N[2], L = a.L, Bz = a.Bz, Zc = a.Zc;
+  const int nzc = (N2 + Zc - 1) / Zc;
   float2* As = reinterpret_cast<float2*>(smem);        // [NRp][NM][NC]
-  float2* Ps = As + (size_t)a.NRp * NM * NC;           // [kPh3Tile][NRp]
+  float2* XY = As + (size_t)a.NRp * NM * NC;           // [L][Bz][NM][NC]
+  float2* pxy = XY + (size_t)L * Bz * NM * NC;         // [L][NRp] Ex Ey of each line and R'
   __shared__ float red[NM];
   const int64_t q = blockIdx.y;
-  const int64_t t0 = (int64_t)blockIdx.x * kPh3Tile;
+  const int line0 = (blockIdx.x / nzc) * L;             // line = jx N1 + jy
+  const int jz0 = (blockIdx.x % nzc) * Zc;
+  const int nlines = min(L, a.N[0] * a.N[1] - line0);
   const float2* Ag = a.A + q * a.NRp * NM * NC;
   for (int i = threadIdx.x; i < a.NRp * NM * NC; i += blockDim.x) As[i] = Ag[i];
-  for (int i = threadIdx.x; i < kPh3Tile * a.NRp; i += blockDim.x) {
-    const int64_t tq = t0 + i / a.NRp;
-    Ps[i] = tq < a.Q ? a.P2[tq * a.NRp + i % a.NRp] : make_float2(0.f, 0.f);
+  for (int i = threadIdx.x; i < nlines * a.NRp; i += blockDim.x) {
+    const int l = i / a.NRp, r = i - l * a.NRp;
+    const int line = line0 + l, jx = line / a.N[1], jy = line - jx * a.N[1];
+    const int4 ri = a.rres[r];
+    const float2 ex = a.Ex[jx * a.Bx + ri.x], ey = a.Ey[jy * a.By + ri.y];
+    pxy[i] = make_float2(ex.x * ey.x - ex.y * ey.y, ex.x * ey.y + ex.y * ey.x);
   }
   if (threadIdx.x < NM) red[threadIdx.x] = 0.f;
   __syncthreads();
+  {  // XY of every line of the block: the R' of each z residue with their Ex Ey
+    const int per_line = Bz * NM * NC;
+    for (int o = threadIdx.x; o < nlines * per_line; o += blockDim.x) {
+      const int l = o / per_line, rem = o - l * per_line;
+      const int b = rem / (NM * NC), e = rem - b * (NM * NC);
+      float2 s = make_float2(0.f, 0.f);
+      for (int i = a.zr_off[b]; i < a.zr_off[b + 1]; ++i) {
+        const int r = a.zr_list[i];
+        const float2 p = pxy[l * a.NRp + r], v = As[(size_t)r * NM * NC + e];
+        s.x = fmaf(p.x, v.x, fmaf(-p.y, v.y, s.x));
+        s.y = fmaf(p.x, v.y, fmaf(p.y, v.x, s.y));
+      }
+      XY[o] = s;
+    }
+  }
+  __syncthreads();
   const int lt = threadIdx.x / NM, nu = threadIdx.x % NM;
-  const int64_t tq = t0 + lt;
+  const int l = lt / Zc, jz = jz0 + lt - l * Zc;
   float acc = 0.f;  // every term is non-negative
   const float2 on0 = a.onb[q * NM + nu];
-  if (tq < a.Q && on0.x >= 0.f) {
+  if (l < nlines && jz < N2 && on0.x >= 0.f) {
+    const int line = line0 + l;
+    const int64_t tq = (int64_t)line * N2 + jz;
     float2 B[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) B[c] = make_float2(0.f, 0.f);
-    for (int r = 0; r < a.NRp; ++r) {
-      const float2 p = Ps[lt * a.NRp + r];
-      const float2* ar = As + ((size_t)r * NM + nu) * NC;
+    for (int b = 0; b < Bz; ++b) {
+      const float2 p = a.Ez[jz * Bz + b];
+      const float2* xr = XY + ((size_t)(l * Bz + b) * NM + nu) * NC;
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        const float2 v = ar[c];
+        const float2 v = xr[c];
         B[c].x = fmaf(p.x, v.x, fmaf(-p.y, v.y, B[c].x));
         B[c].y = fmaf(p.x, v.y, fmaf(p.y, v.x, B[c].y));
       }
@@ -206,12 +229,14 @@ __global__ void k_ph3_degenerate(const double* __restrict__ acc, const double* _
 
 template <int NM>
 static int launch_s2(cudaStream_t st, const Ph3S2Args& a) {
-  const size_t smem = sizeof(float2) * ((size_t)a.NRp * NM * NM * NM + (size_t)kPh3Tile * a.NRp);
+  const size_t smem = sizeof(float2) * ((size_t)a.NRp * NM * NM * NM + (size_t)a.L * a.Bz * NM * NM * NM +
+                                        (size_t)a.L * a.NRp);
   if (smem > 227 * 1024) return -2;
   if (allow_dynamic_smem(k_ph3_stage2<NM>) != cudaSuccess)
     return -1;
-  dim3 grid((unsigned)((a.Q + kPh3Tile - 1) / kPh3Tile), (unsigned)a.Q);
-  k_ph3_stage2<NM><<<grid, kPh3Tile * NM, smem, st>>>(a);
+  const int lines = a.N[0] * a.N[1], nzc = (a.N[2] + a.Zc - 1) / a.Zc;
+  dim3 grid((unsigned)((lines + a.L - 1) / a.L * nzc), (unsigned)a.Q);
+  k_ph3_stage2<NM><<<grid, a.L * a.Zc * NM, smem, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -235,10 +260,44 @@ int three_phonon(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, double* out_
   k_ph3_tables<<<(unsigned)((Q * nm * nm + 255) / 256), 256, 0, c->stream>>>(Zq, omega, nB, Q, nm, p->omega_cut_eV, Zf,
                                                                                onb);
   const int NRp = c->ph3_nrp;
-  float2* P2 = (float2*)ensure(c, "ph3_P2", sizeof(float2) * Q * NRp, &st);
-  if (!P2) return st;
-  k_ph3_phase<<<(unsigned)((Q * NRp + 255) / 256), 256, 0, c->stream>>>((const int*)c->bufs["ph3_Rpd"].p, NRp, Q, N[0],
-                                                                          N[1], N[2], P2);
+  // the R' residues r = R' mod N per axis, each R''s residue indices, and the per-axis phase tables
+  // e^{-2 pi i j r / N} (j r reduced modulo N in integers)
+  std::vector<int> res[3];
+  std::vector<int> rres((size_t)4 * NRp, 0);
+  for (int d = 0; d < 3; ++d) {
+    for (int r = 0; r < NRp; ++r) res[d].push_back(((c->ph3_rp[3 * r + d] % N[d]) + N[d]) % N[d]);
+    std::sort(res[d].begin(), res[d].end());
+    res[d].erase(std::unique(res[d].begin(), res[d].end()), res[d].end());
+    for (int r = 0; r < NRp; ++r) {
+      const int v = ((c->ph3_rp[3 * r + d] % N[d]) + N[d]) % N[d];
+      rres[4 * r + d] = (int)(std::lower_bound(res[d].begin(), res[d].end(), v) - res[d].begin());
+    }
+  }
+  void* d_tab[3];
+  for (int d = 0; d < 3; ++d) {
+    const int B = (int)res[d].size();
+    std::vector<float2> tab((size_t)N[d] * B);
+    for (int j = 0; j < N[d]; ++j)
+      for (int b = 0; b < B; ++b) {
+        const int64_t m = ((int64_t)j * res[d][b]) % N[d];
+        double sn, cs;
+        sincospi(-2.0 * (double)m / N[d], &sn, &cs);
+        tab[(size_t)j * B + b] = make_float2((float)cs, (float)sn);
+      }
+    const char* name[3] = {"ph3_Ex", "ph3_Ey", "ph3_Ez"};
+    TRY(upload(c, name[d], tab.data(), sizeof(float2) * tab.size(), &d_tab[d]));
+  }
+  std::vector<int> zr((size_t)res[2].size() + 1 + NRp, 0);  // offsets by z residue, then the R'
+  for (int r = 0; r < NRp; ++r) ++zr[rres[4 * r + 2] + 1];
+  for (size_t b = 1; b <= res[2].size(); ++b) zr[b] += zr[b - 1];
+  {
+    std::vector<int> fill(zr.begin(), zr.begin() + res[2].size());
+    for (int r = 0; r < NRp; ++r) zr[res[2].size() + 1 + fill[rres[4 * r + 2]]++] = r;
+  }
+  void *d_rres, *d_zr;
+  TRY(upload(c, "ph3_rres", rres.data(), sizeof(int) * rres.size(), &d_rres));
+  TRY(upload(c, "ph3_zr", zr.data(), sizeof(int) * zr.size(), &d_zr));
+  const int Zc = std::min(N[2], 32), L = std::max(1, 32 / Zc);  // L Zc <= 32 q~ per block
   float2* A = (float2*)ensure(c, "ph3_A", sizeof(float2) * Q * NRp * nm * nm * nm, &st);
   if (!A) return st;
   Ph3S1Args s1;
@@ -263,7 +322,17 @@ int three_phonon(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, double* out_
   CK(c, cudaGetLastError());
   Ph3S2Args s2;
   s2.A = A;
-  s2.P2 = P2;
+  s2.Ex = (const float2*)d_tab[0];
+  s2.Ey = (const float2*)d_tab[1];
+  s2.Ez = (const float2*)d_tab[2];
+  s2.rres = (const int4*)d_rres;
+  s2.zr_off = (const int*)d_zr;
+  s2.zr_list = (const int*)d_zr + res[2].size() + 1;
+  s2.Bx = (int)res[0].size();
+  s2.By = (int)res[1].size();
+  s2.Bz = (int)res[2].size();
+  s2.L = L;
+  s2.Zc = Zc;
   s2.Zf = Zf;
   s2.onb = onb;
   s2.Q = Q;
@@ -291,7 +360,11 @@ int three_phonon(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, double* out_
   c->stats.stage2_launches = 1;
   c->stats.kernel_launches = c->launches;
   c->stats.n_q = Q;
-  c->stats.stage2_flops = 8.0 * (double)Q * Q * nm * ((double)NRp * nm * nm + 2.0 * nm * nm * nm);
+  // per q: the XY sums of every (jx, jy) line (one complex MAC per R' and element), then per (q~, nu)
+  // the rz sum and the two mode rotations
+  c->stats.stage2_flops = 8.0 * (double)Q *
+                          ((double)N[0] * N[1] * NRp * nm * nm * nm +
+                           (double)Q * nm * ((double)s2.Bz * nm * nm + 2.0 * nm * nm * nm));
   total.end(c, &c->stats.total_ms);
   return PHOEBE_GPU_OK;
 }
