@@ -1,5 +1,7 @@
 """Three-phonon coupling and the three-phonon diagonal of the phonon scattering matrix (Sec. 3.1,
 Sec. 4.3) through the C ABI against the FP64 oracle: 1e-5 relative, floor 1e-6 of the maximum."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -43,6 +45,19 @@ def test_si_like_three_phonon(pg):
     ref = elph.three_phonon_diag(mat, anh, prm)
     err = rel_err(A, ref)
     print(f"Si-like 6^3 three-phonon diagonal: max rel err {err:.3e}")
+    assert err <= RTOL and np.max(A) > 0
+
+
+@pytest.mark.parametrize("nq", [(2, 3, 40), (5, 4, 3)])
+def test_si_like_three_phonon_uneven_grids(pg, nq):
+    """Grids whose z lines are longer than one block's 32 q~ (two chunks per line) or short enough
+    for ten lines per block, with different residue sets per axis."""
+    mat, anh, prm = W.three_phonon_si_like(seed=0, nq=6)
+    prm = dataclasses.replace(prm, nk=nq, nq=nq)
+    A = _run(pg, mat, anh, prm)
+    ref = elph.three_phonon_diag(mat, anh, prm)
+    err = rel_err(A, ref)
+    print(f"Si-like {nq} three-phonon diagonal: max rel err {err:.3e}")
     assert err <= RTOL and np.max(A) > 0
 
 
