@@ -96,13 +96,52 @@ __global__ void __launch_bounds__(32 * NM) k_ph3_stage2(Ph3S2Args a) {
   float2* As = reinterpret_cast<float2*>(smem);        // [NRp][NM][NC]
   float2* XY = As + (size_t)a.NRp * NM * NC;           // [L][Bz][NM][NC]
   float2* pxy = XY + (size_t)L * Bz * NM * NC;         // [L][NRp] Ex Ey of each line and R'
+  const int T = L * Zc;                                  // q~ per block
+  float2* Zs1 = pxy + (size_t)L * a.NRp;                 // [T][NC] Z of each q~ of the block
+  float2* Zs2 = Zs1 + (size_t)T * NC;                    // [T][NC] Z of its -q''
+  float2* ons = Zs2 + (size_t)T * NC;                    // [T][3][NM] (hbar w, n) at q~, q'', -q''
   __shared__ float red[NM];
   const int64_t q = blockIdx.y;
   const int line0 = (blockIdx.x / nzc) * L;             // line = jx N1 + jy
   const int jz0 = (blockIdx.x % nzc) * Zc;
   const int nlines = min(L, a.N[0] * a.N[1] - line0);
   const float2* Ag = a.A + q * a.NRp * NM * NC;
+  // q~ of tile position t (line l, jz), q'' = q + q~ and -q'' on the grid; false past the grid
+  const int jq[3] = {(int)(q / ((int64_t)a.N[1] * a.N[2])), (int)((q / a.N[2]) % a.N[1]), (int)(q % a.N[2])};
+  auto tile_q = [&](int t, int64_t& tq, int64_t& i2, int64_t& im) -> bool {
+    const int l = t / Zc, jz = jz0 + t - l * Zc;
+    if (l >= nlines || jz >= N2) return false;
+    const int line = line0 + l, jx = line / a.N[1], jy = line - jx * a.N[1];
+    tq = (int64_t)line * N2 + jz;
+    const int jt[3] = {jx, jy, jz};
+    int j2[3], jm[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      j2[d] = (jq[d] + jt[d]) % a.N[d];
+      jm[d] = (a.N[d] - j2[d]) % a.N[d];
+    }
+    i2 = ((int64_t)j2[0] * a.N[1] + j2[1]) * a.N[2] + j2[2];
+    im = ((int64_t)jm[0] * a.N[1] + jm[1]) * a.N[2] + jm[2];
+    return true;
+  };
   for (int i = threadIdx.x; i < a.NRp * NM * NC; i += blockDim.x) As[i] = Ag[i];
+  for (int i = threadIdx.x; i < T * NC; i += blockDim.x) {
+    int64_t tq, i2, im;
+    const int t = i / NC, e = i - t * NC;
+    if (tile_q(t, tq, i2, im)) {
+      Zs1[i] = a.Zf[tq * NC + e];
+      Zs2[i] = a.Zf[im * NC + e];
+    }
+  }
+  for (int i = threadIdx.x; i < T * NM; i += blockDim.x) {
+    int64_t tq, i2, im;
+    const int t = i / NM, v = i - t * NM;
+    if (tile_q(t, tq, i2, im)) {
+      ons[(t * 3) * NM + v] = a.onb[tq * NM + v];
+      ons[(t * 3 + 1) * NM + v] = a.onb[i2 * NM + v];
+      ons[(t * 3 + 2) * NM + v] = a.onb[im * NM + v];
+    }
+  }
   for (int i = threadIdx.x; i < nlines * a.NRp; i += blockDim.x) {
     const int l = i / a.NRp, r = i - l * a.NRp;
     const int line = line0 + l, jx = line / a.N[1], jy = line - jx * a.N[1];
@@ -133,8 +172,6 @@ __global__ void __launch_bounds__(32 * NM) k_ph3_stage2(Ph3S2Args a) {
   float acc = 0.f;  // every term is non-negative
   const float2 on0 = a.onb[q * NM + nu];
   if (l < nlines && jz < N2 && on0.x >= 0.f) {
-    const int line = line0 + l;
-    const int64_t tq = (int64_t)line * N2 + jz;
     float2 B[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) B[c] = make_float2(0.f, 0.f);
@@ -148,21 +185,12 @@ __global__ void __launch_bounds__(32 * NM) k_ph3_stage2(Ph3S2Args a) {
         B[c].y = fmaf(p.x, v.y, fmaf(p.y, v.x, B[c].y));
       }
     }
-    // q'' = q + q~ and -q'' on the grid
-    const int jq[3] = {(int)(q / ((int64_t)a.N[1] * a.N[2])), (int)((q / a.N[2]) % a.N[1]), (int)(q % a.N[2])};
-    const int jt[3] = {(int)(tq / ((int64_t)a.N[1] * a.N[2])), (int)((tq / a.N[2]) % a.N[1]), (int)(tq % a.N[2])};
-    int j2[3], jm[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      j2[d] = (jq[d] + jt[d]) % a.N[d];
-      jm[d] = (a.N[d] - j2[d]) % a.N[d];
-    }
-    const int64_t i2 = ((int64_t)j2[0] * a.N[1] + j2[1]) * a.N[2] + j2[2];
-    const int64_t im = ((int64_t)jm[0] * a.N[1] + jm[1]) * a.N[2] + jm[2];
-    const float2* Z1 = a.Zf + tq * NM * NM;
-    const float2* Z2 = a.Zf + im * NM * NM;
+    // the q~, q'' and -q'' tables staged above
+    const float2* Z1 = Zs1 + (size_t)lt * NC;
+    const float2* Z2 = Zs2 + (size_t)lt * NC;
+    const float2* o1 = ons + (size_t)(lt * 3) * NM;
     for (int n1 = 0; n1 < NM; ++n1) {
-      const float2 on1 = a.onb[tq * NM + n1];
+      const float2 on1 = o1[n1];
       if (on1.x < 0.f) continue;
       float2 tt[NM];  // sum_{s' b} B[s' b][s'' c] conj(Z_q~[s' b][nu'])
 #pragma unroll
@@ -178,8 +206,8 @@ __global__ void __launch_bounds__(32 * NM) k_ph3_stage2(Ph3S2Args a) {
         }
       }
       for (int n2 = 0; n2 < NM; ++n2) {
-        const float2 on2 = a.onb[i2 * NM + n2];
-        if (on2.x < 0.f || a.onb[im * NM + n2].x < 0.f) continue;
+        const float2 on2 = o1[NM + n2];
+        if (on2.x < 0.f || o1[2 * NM + n2].x < 0.f) continue;
         float2 W = make_float2(0.f, 0.f);
 #pragma unroll
         for (int k = 0; k < NM; ++k) {
@@ -229,8 +257,9 @@ __global__ void k_ph3_degenerate(const double* __restrict__ acc, const double* _
 
 template <int NM>
 static int launch_s2(cudaStream_t st, const Ph3S2Args& a) {
+  const size_t T = (size_t)a.L * a.Zc;
   const size_t smem = sizeof(float2) * ((size_t)a.NRp * NM * NM * NM + (size_t)a.L * a.Bz * NM * NM * NM +
-                                        (size_t)a.L * a.NRp);
+                                        (size_t)a.L * a.NRp + 2 * T * NM * NM + 3 * T * NM);
   if (smem > 227 * 1024) return -2;
   if (allow_dynamic_smem(k_ph3_stage2<NM>) != cudaSuccess)
     return -1;
