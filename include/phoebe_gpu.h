@@ -373,7 +373,8 @@ int phoebe_gpu_is_uniforms(phoebe_gpu_ctx* ctx, uint64_t seed, int32_t k, int64_
  * and the stage-2 operands, and records the material's stage-2 launches (with plan_threads > 1,
  * several materials at once on host threads); with autotune on, the tile width
  * (128 or 256 columns) and the K blocks per TMEM partial (1, 2 or 4) of its stage-2 GEMM are
- * chosen by timing each candidate once on the material's first q chunk.  Phase 2 captures
+ * chosen by timing each candidate once on the material's first q chunk; the context keeps the
+ * choice per GEMM problem, and later batch calls with the same problem reuse it untimed.  Phase 2 captures
  * the recorded launches of all materials into one CUDA graph (materials spread round-robin
  * over n_streams parallel branches) and launches it once.  Phase 3 averages degenerate
  * bands and writes each item's host outputs as linewidths_rta does.  Every shape uses the
@@ -391,7 +392,8 @@ typedef struct {
 } phoebe_gpu_batch_item;
 
 typedef struct {
-  int autotune;              /* 1: time the tile candidates per material (default 1) */
+  int autotune;              /* 1: time the tile candidates per material, once per context and
+                                GEMM problem (default 1) */
   int n_streams;             /* parallel branches of the graph, 1..64 (default 4) */
   int64_t g_chunk_bytes;     /* stage-2 result buffer per material and q chunk (default 128 MiB) */
   double plan_ms;            /* out: phase 1 wall time (including the autotuner) */

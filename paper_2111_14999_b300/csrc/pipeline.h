@@ -55,6 +55,9 @@ struct phoebe_gpu_ctx {
   bool have_phi3 = false;
   int ph3_na = 0, ph3_nrp = 0;
   std::vector<int> ph3_rp;  // [ph3_nrp][3] the distinct R' (lattice coordinates), host copy
+  // the autotuner's stage-2 tile choice (tile width, K blocks per partial) per GEMM problem
+  // (operand format, parts, products, K, columns, q rows, q rows per chunk), kept for later calls
+  std::map<std::vector<int64_t>, std::pair<int, int>> tuned_tiles;
   bool have_polar = false;
   std::vector<double> zstar;  // [na][3][3]
   double eps_inf[9] = {0};

@@ -1337,7 +1337,12 @@ static int run_tc_generic(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, con
       return PHOEBE_GPU_OK;
     };
     int bn = StoreEpi::BN, kbc = PHX_KB_PER_CHUNK;
-    if (df && df->autotune) {
+    const std::vector<int64_t> tune_key = {(int64_t)FMT, NSPLIT, NPROD, Kp2, ncols, Mrows, qc};
+    const auto tuned = c->tuned_tiles.find(tune_key);
+    if (df && df->autotune && tuned != c->tuned_tiles.end()) {  // tuned by an earlier call on this context
+      bn = tuned->second.first;
+      kbc = tuned->second.second;
+    } else if (df && df->autotune) {
       // autotuner: time every (tile width, K blocks per partial) candidate on the first q chunk
       static const int cand_bn[2] = {128, 256}, cand_kb[3] = {1, 2, 4};
       cudaEvent_t e0, e1;
@@ -1366,6 +1371,7 @@ static int run_tc_generic(phoebe_gpu_ctx* c, const phoebe_gpu_rta_params* p, con
         }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
+      c->tuned_tiles[tune_key] = {bn, kbc};
     } else if (df) {
       if (df->bn) bn = df->bn;
       if (df->kb) kbc = df->kb;
