@@ -436,9 +436,10 @@ def batch_leg(pg, W, dev, args) -> dict:
         "one_call_per_material": {"wall_s": eager_s, "linewidths_per_s": states / eager_s},
         "one_batch_call": {"wall_s": batch_s, "linewidths_per_s": states / batch_s, "plan_ms": info["plan_ms"],
                            "graph_ms": info["graph_ms"], "graph_nodes": info["graph_nodes"],
-                           "finish_ms": info["finish_ms"], "note": "tiles chosen by the first call, reused"},
+                           "finish_ms": info["finish_ms"], "graph_reused": info["graph_reused"],
+                           "note": "tiles chosen by the first call, reused"},
         "first_batch_call_with_autotuning": {"wall_s": first_s, "linewidths_per_s": states / first_s,
-                                             "plan_ms": info0["plan_ms"]},
+                                             "plan_ms": info0["plan_ms"], "graph_reused": info0["graph_reused"]},
         "per_material_stage_ms_sum": {k: v for k, v in agg.items() if k.endswith("_ms")},
         "stage2_algorithmic_tflops_in_graph": agg["stage2_flops"] / (info["graph_ms"] / 1e3) / 1e12,
         "autotuned_tiles_columns_x_kblocks": tiles,

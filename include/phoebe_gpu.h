@@ -376,7 +376,9 @@ int phoebe_gpu_is_uniforms(phoebe_gpu_ctx* ctx, uint64_t seed, int32_t k, int64_
  * chosen by timing each candidate once on the material's first q chunk; the context keeps the
  * choice per GEMM problem, and later batch calls with the same problem reuse it untimed.  Phase 2 captures
  * the recorded launches of all materials into one CUDA graph (materials spread round-robin
- * over n_streams parallel branches) and launches it once.  Phase 3 averages degenerate
+ * over n_streams parallel branches) and launches it once; items[0].ctx keeps the executable
+ * graph, and a later call whose graph has the same shape updates it in place instead of
+ * instantiating a new one (the kept graph is freed with that context).  Phase 3 averages degenerate
  * bands and writes each item's host outputs as linewidths_rta does.  Every shape uses the
  * stage 2 that writes G to HBM (the fused epilogue is not used in a batch); all of a
  * material's active states form one batch, so its operands must fit in device memory.
@@ -404,7 +406,9 @@ typedef struct {
   int plan_threads;          /* host threads of phase 1, each planning one material at a time on the
                                 material's own stream, so that materials overlap on the GPU
                                 (0 or 1 = one material after the other, the default; at most 64) */
-  int reserved[3];           /* must be zero */
+  int graph_reused;          /* out: 1 if the executable graph of an earlier batch call (kept on
+                                items[0].ctx) was updated in place instead of instantiated anew */
+  int reserved[2];           /* must be zero */
 } phoebe_gpu_batch_opts;
 
 void phoebe_gpu_batch_opts_default(phoebe_gpu_batch_opts* o);

@@ -88,7 +88,7 @@ class BatchOpts(C.Structure):
         ("autotune", C.c_int), ("n_streams", C.c_int), ("g_chunk_bytes", C.c_int64),
         ("plan_ms", C.c_double), ("graph_ms", C.c_double), ("finish_ms", C.c_double),
         ("graph_nodes", C.c_int64), ("recorded_launches", C.c_int64),
-        ("plan_threads", C.c_int), ("reserved", C.c_int * 3),
+        ("plan_threads", C.c_int), ("graph_reused", C.c_int), ("reserved", C.c_int * 2),
     ]
 
 

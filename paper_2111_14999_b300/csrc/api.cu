@@ -468,6 +468,7 @@ int phoebe_gpu_destroy(phoebe_gpu_ctx* c) {
   for (auto& kv : c->bufs)
     if (kv.second.p) cudaFree(kv.second.p);
   c->bufs.clear();
+  if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
   destroy_tc_state(c);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;

@@ -5,7 +5,8 @@
 // materials at once, each on its material's stream, so that small materials, host-side
 // planning and synchronisations of one material overlap the kernels of others.  Phase 2
 // captures every recorded launch of every material into one CUDA graph, materials spread over
-// parallel branches, and launches it once.  Phase 3 averages degenerate bands and copies each material's outputs.
+// parallel branches, and launches it once; the first item's context keeps the executable graph,
+// which a later call with a graph of the same shape updates in place instead of instantiating.  Phase 3 averages degenerate bands and copies each material's outputs.
 #include <string.h>
 #include <time.h>
 
@@ -55,8 +56,9 @@ extern "C" int phoebe_gpu_linewidths_rta_batch(phoebe_gpu_batch_item* items, int
   phoebe_gpu_batch_opts* o = opts ? opts : &dflt;
   if (o->n_streams < 1 || o->n_streams > 64 || o->g_chunk_bytes < ((int64_t)1 << 20)) return PHOEBE_GPU_ERR_ARG;
   if (o->plan_threads < 0 || o->plan_threads > 64) return PHOEBE_GPU_ERR_ARG;
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 2; ++i)
     if (o->reserved[i]) return PHOEBE_GPU_ERR_ARG;
+  o->graph_reused = 0;
   bool count_only = false;
   for (int i = 0; i < n; ++i) {
     if (!items[i].ctx || !items[i].params) return PHOEBE_GPU_ERR_ARG;
@@ -174,8 +176,25 @@ extern "C" int phoebe_gpu_linewidths_rta_batch(phoebe_gpu_batch_item* items, int
   }
   cudaGraph_t graph = nullptr;
   CK(c0, cudaStreamEndCapture(cs, &graph));
-  cudaGraphExec_t exec = nullptr;
-  cudaError_t ge = cudaGraphInstantiate(&exec, graph, 0);
+  // the executable graph kept on c0 by an earlier call, updated in place when this graph has its
+  // shape (same nodes and edges; kernel arguments and launch shapes may differ), else a new one
+  cudaGraphExec_t exec = c0->batch_exec;
+  cudaError_t ge = cudaErrorUnknown;
+  if (exec) {
+    cudaGraphExecUpdateResultInfo ui;
+    ge = cudaGraphExecUpdate(exec, graph, &ui);
+    if (ge != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(exec);
+      c0->batch_exec = exec = nullptr;
+    } else {
+      o->graph_reused = 1;
+    }
+  }
+  if (!exec) {
+    ge = cudaGraphInstantiate(&exec, graph, 0);
+    if (ge == cudaSuccess) c0->batch_exec = exec;
+  }
   size_t nodes = 0;
   cudaGraphGetNodes(graph, nullptr, &nodes);
   cudaGraphDestroy(graph);
@@ -187,8 +206,9 @@ extern "C" int phoebe_gpu_linewidths_rta_batch(phoebe_gpu_batch_item* items, int
   if (le == cudaSuccess) le = cudaGraphLaunch(exec, cs);
   if (le == cudaSuccess) le = cudaEventRecord(tb, cs);
   if (le == cudaSuccess) le = cudaStreamSynchronize(cs);
-  cudaGraphExecDestroy(exec);
   if (le != cudaSuccess) {
+    cudaGraphExecDestroy(exec);
+    c0->batch_exec = nullptr;
     cudaGetLastError();
     return fail(c0, PHOEBE_GPU_ERR_CUDA, "batch graph launch failed: %s", cudaGetErrorString(le));
   }

@@ -58,6 +58,8 @@ struct phoebe_gpu_ctx {
   // the autotuner's stage-2 tile choice (tile width, K blocks per partial) per GEMM problem
   // (operand format, parts, products, K, columns, q rows, q rows per chunk), kept for later calls
   std::map<std::vector<int64_t>, std::pair<int, int>> tuned_tiles;
+  // the executable graph of the last batch call that named this context first (batch.cu)
+  cudaGraphExec_t batch_exec = nullptr;
   bool have_polar = false;
   std::vector<double> zstar;  // [na][3][3]
   double eps_inf[9] = {0};

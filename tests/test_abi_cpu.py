@@ -63,7 +63,8 @@ def _c_layout(struct, fields, tmp_path):
 def test_ctypes_structs_mirror_the_header(tmp_path):
     import paper_2111_14999_b300 as pg
     for py, cname in ((pg.RTAParams, "phoebe_gpu_rta_params"), (pg.binding.Stats, "phoebe_gpu_stats"),
-                      (pg.binding.TrainOpts, "phoebe_gpu_train_opts")):
+                      (pg.binding.TrainOpts, "phoebe_gpu_train_opts"),
+                      (pg.binding.BatchOpts, "phoebe_gpu_batch_opts")):
         names = [f for f, _ in py._fields_]
         got = _c_layout(cname, names, tmp_path)
         assert got[0] == ctypes.sizeof(py), cname

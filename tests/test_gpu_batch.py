@@ -96,3 +96,18 @@ def test_batch_rejects_a_shared_context(batch):
     with pytest.raises(pg.PhoebeGPUError) as e:
         pg.binding.linewidths_rta_batch(jobs, capacities=[10, 10])
     assert e.value.status == -1
+
+
+def test_repeated_batch_call_updates_the_kept_graph(batch):
+    """A second identical batch call reuses the tile choices and updates the executable graph kept
+    on the first item's context; its linewidths equal the first call's up to the order of the FP64
+    atomic adds."""
+    pg, mats, ctxs = batch
+    jobs = [(c, pg.make_params(prm, precision=1)) for c, (_, prm) in zip(ctxs, mats)]
+    res0, info0 = pg.binding.linewidths_rta_batch(jobs)
+    res1, info1 = pg.binding.linewidths_rta_batch(jobs)
+    assert info1["graph_reused"] == 1
+    assert info1["graph_nodes"] == info0["graph_nodes"] and info1["tiles"] == info0["tiles"]
+    for (k0, b0, g0), (k1, b1, g1) in zip(res0, res1):
+        assert np.array_equal(k0, k1) and np.array_equal(b0, b1)
+        assert rel_err(g1, g0) <= 1e-12
