@@ -35,11 +35,6 @@ __global__ void __launch_bounds__(256) k_elph_generic(ElphGenericArgs a) {
   grid_coords(q, a.gm.nq, qc);
   const int s_end = min(a.S, (int)(blockIdx.y + 1) * kGenericStatesPerBlock);
   for (int s = blockIdx.y * kGenericStatesPerBlock + warp; s < s_end; s += 8) {
-    // stage the warp's G row (FP32 pairs) in shared memory
-    const float* grow = a.G + r * a.ldg + (int64_t)s * cps;
-    __syncwarp();
-    for (int i = lane; i < cps; i += 32) gs[i] = grow[i];
-    __syncwarp();
     const int64_t kf = a.gm.k_to_fine(a.st_k[s]);
     int kc[3];
     grid_coords(kf, a.gm.nf, kc);
@@ -57,6 +52,15 @@ __global__ void __launch_bounds__(256) k_elph_generic(ElphGenericArgs a) {
       const float2 e = a.eps2[kq * nw + mp];
       dm = (en_hi - e.x) + (en_lo - e.y);
       need = fabsf(dm) < a.reach;
+    }
+    // a pair none of whose final bands reaches the delta window contributes nothing: its G row
+    // is not read
+    if (!__any_sync(0xffffffffu, need)) continue;
+    {  // stage the warp's G row (FP32 pairs) in shared memory
+      const float* grow = a.G + r * a.ldg + (int64_t)s * cps;
+      __syncwarp();
+      for (int i = lane; i < cps; i += 32) gs[i] = grow[i];
+      __syncwarp();
     }
     if (need) {
       // t[sa] = sum_m conj(U_{k+q}[m][m']) G[sa][m]
