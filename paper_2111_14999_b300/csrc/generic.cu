@@ -9,8 +9,10 @@
 namespace phx {
 
 // One block per (q row, group of kGenericStatesPerBlock states); each warp takes every 8th
-// state of the group, one (q, state) pair at a time, lane = final band m'.  MAXNM bounds
-// the mode count; the loops over modes are unrolled to it (exact when MAXNM == nm).
+// state of the group, one (q, state) pair at a time: lane = final band m' for the window test,
+// then the whole warp on each final band in reach (lane = mode row sa for the U_{k+q}^dagger
+// rotation, lane = mode v for the Z_q rotation and the delta weights).  MAXNM: instantiations
+// below kGenericMaxModes are launched only for nm == MAXNM.
 template <int MAXNM>
 __global__ void __launch_bounds__(256) k_elph_generic(ElphGenericArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -19,8 +21,9 @@ __global__ void __launch_bounds__(256) k_elph_generic(ElphGenericArgs a) {
   const int nw = a.nw, nm = MAXNM < kGenericMaxModes ? MAXNM : a.nm;
   const int cps = 2 * nw * nm;
   float2* zs = reinterpret_cast<float2*>(smem);                 // [nm][nm] mode factors of this q
-  float* gs = reinterpret_cast<float*>(zs + nm * nm) + warp * cps;  // this warp's G row
-  float* oms = reinterpret_cast<float*>(zs + nm * nm) + 8 * cps;     // [nm] omega, then [nm] n_B
+  const int gstride = 2 * nw + 1;  // floats per mode row of a staged G row (odd: lanes sa hit distinct banks)
+  float* gs = reinterpret_cast<float*>(zs + nm * nm) + warp * nm * gstride;  // this warp's G row [sa][m][re, im]
+  float* oms = reinterpret_cast<float*>(zs + nm * nm) + 8 * nm * gstride;     // [nm] omega, then [nm] n_B
   float* nbs = oms + nm;
   const int64_t r = blockIdx.x;  // row of the chunk
   const int q = a.q_of_row[a.row0 + r];
@@ -55,46 +58,49 @@ __global__ void __launch_bounds__(256) k_elph_generic(ElphGenericArgs a) {
     }
     // a pair none of whose final bands reaches the delta window contributes nothing: its G row
     // is not read
-    if (!__any_sync(0xffffffffu, need)) continue;
+    const unsigned mask = __ballot_sync(0xffffffffu, need);
+    if (!mask) continue;
     {  // stage the warp's G row (FP32 pairs) in shared memory
       const float* grow = a.G + r * a.ldg + (int64_t)s * cps;
       __syncwarp();
-      for (int i = lane; i < cps; i += 32) gs[i] = grow[i];
+      for (int i = lane; i < cps; i += 32) {
+        const int sa = i / (2 * nw);
+        gs[i + sa] = grow[i];  // = gs[sa * gstride + i - sa * 2 nw]
+      }
       __syncwarp();
     }
-    if (need) {
-      // t[sa] = sum_m conj(U_{k+q}[m][m']) G[sa][m]
-      float2 t[MAXNM];
-#pragma unroll
-      for (int sa = 0; sa < MAXNM; ++sa) t[sa] = make_float2(0.f, 0.f);
-      const float2* uh = a.UH + (kq * nw + mp) * nw;
-      for (int m = 0; m < nw; ++m) {
-        const float2 u = uh[m];
-#pragma unroll
-        for (int sa = 0; sa < MAXNM; ++sa) {
-          if (sa < nm) {
-            const float gr = gs[2 * (sa * nw + m)], gi = gs[2 * (sa * nw + m) + 1];
-            t[sa].x = fmaf(u.x, gr, fmaf(-u.y, gi, t[sa].x));
-            t[sa].y = fmaf(u.x, gi, fmaf(u.y, gr, t[sa].y));
-          }
+    // each final band in reach in turn, the whole warp on it: lane sa forms
+    // t[sa] = sum_m conj(U_{k+q}[m][m']) G[sa][m], lane v then g_v = sum_sa t[sa] Z_q[sa][v]
+    for (unsigned mm = mask; mm; mm &= mm - 1) {
+      const int mpb = __ffs(mm) - 1;
+      const float dmb = __shfl_sync(0xffffffffu, dm, mpb);
+      float2 t = make_float2(0.f, 0.f);
+      if (lane < nm) {
+        const float2* uh = a.UH + (kq * nw + mpb) * nw;
+        const float* gl = gs + lane * gstride;
+        for (int m = 0; m < nw; ++m) {
+          const float2 u = uh[m];
+          const float gr = gl[2 * m], gi = gl[2 * m + 1];
+          t.x = fmaf(u.x, gr, fmaf(-u.y, gi, t.x));
+          t.y = fmaf(u.x, gi, fmaf(u.y, gr, t.y));
         }
       }
-      const float f = a.f32[kq * nw + mp];
-      for (int v = 0; v < nm; ++v) {
-        float2 g = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int sa = 0; sa < MAXNM; ++sa) {
-          if (sa < nm) {
-            const float2 z = zs[sa * nm + v];
-            g.x = fmaf(t[sa].x, z.x, fmaf(-t[sa].y, z.y, g.x));
-            g.y = fmaf(t[sa].x, z.y, fmaf(t[sa].y, z.x, g.y));
-          }
+      const float f = a.f32[kq * nw + mpb];
+      float2 g = make_float2(0.f, 0.f);
+      for (int sa = 0; sa < nm; ++sa) {
+        const float tx = __shfl_sync(0xffffffffu, t.x, sa), ty = __shfl_sync(0xffffffffu, t.y, sa);
+        if (lane < nm) {
+          const float2 z = zs[sa * nm + lane];
+          g.x = fmaf(tx, z.x, fmaf(-ty, z.y, g.x));
+          g.y = fmaf(tx, z.y, fmaf(ty, z.x, g.y));
         }
-        const float t1 = (dm - oms[v]) * a.inv_sigma;
-        const float t2 = (dm + oms[v]) * a.inv_sigma;
+      }
+      if (lane < nm) {
+        const float t1 = (dmb - oms[lane]) * a.inv_sigma;
+        const float t2 = (dmb + oms[lane]) * a.inv_sigma;
         float w = 0.f;
-        if (t1 * t1 < a.cut2) w += (nbs[v] + 1.f - f) * expf(-t1 * t1);
-        if (t2 * t2 < a.cut2) w += (nbs[v] + f) * expf(-t2 * t2);
+        if (t1 * t1 < a.cut2) w += (nbs[lane] + 1.f - f) * expf(-t1 * t1);
+        if (t2 * t2 < a.cut2) w += (nbs[lane] + f) * expf(-t2 * t2);
         part = fmaf(g.x * g.x + g.y * g.y, w, part);
       }
     }
@@ -107,7 +113,7 @@ __global__ void __launch_bounds__(256) k_elph_generic(ElphGenericArgs a) {
 }
 
 size_t elph_generic_smem(int nw, int nm) {
-  return sizeof(float2) * nm * nm + sizeof(float) * (8 * 2 * nw * nm + 2 * nm);
+  return sizeof(float2) * nm * nm + sizeof(float) * (8 * (size_t)nm * (2 * nw + 1) + 2 * nm);
 }
 
 template <int MAXNM>
