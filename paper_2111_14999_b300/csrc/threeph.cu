@@ -18,8 +18,6 @@
 
 namespace phx {
 
-constexpr int kPh3Tile = 32;  // q~ per block of stage 2
-
 struct Ph3S1Args {
   const double* phi;   // [n][nm][nm*nm] pairs sorted by R' index
   const int* R;        // [n][3]
